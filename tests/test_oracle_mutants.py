@@ -1,0 +1,47 @@
+"""Planted mistakes: each deliberately broken build of the oracle (the
+ORACLE_MUTANT hooks in oracle/fmm_oracle.c) must fail at least one of the
+pins, which shows the pins are sharp enough to catch that kind of error.
+CPU only; the mutants are compiled into a temporary directory."""
+import pytest
+
+import oracle
+import test_oracle_ops as ops
+import test_oracle_solve as solve
+
+MUTANTS = {
+    1: "M2L with R = source - target (sign of odd orders flipped)",
+    2: "M2L without the 1/alpha! factor",
+    3: "L2L with the displacement reversed",
+    4: "interaction list also takes the near neighbours",
+    5: "near field without the self cell",
+}
+
+PINS = [
+    ops.test_m2l_converges_geometrically,
+    ops.test_l2l_then_l2p_is_exact,
+    solve.test_converges_to_direct_sum_in_p,
+    solve.test_point_mass_closed_form,
+    lambda o: solve.test_equals_direct_sum_when_all_boxes_are_near(o, (8, 8, 8), 4),
+]
+
+
+def _failures(orc):
+    failed = []
+    for pin in PINS:
+        try:
+            pin(orc)
+        except AssertionError:
+            failed.append(getattr(pin, "__name__", "lambda"))
+    return failed
+
+
+def test_battery_passes_on_the_oracle(orc):
+    assert _failures(orc) == []
+
+
+@pytest.mark.parametrize("k", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(tmp_path, k):
+    path = oracle.build(str(tmp_path / f"liboracle_mutant{k}.so"), mutant=k, force=True)
+    mutant = oracle.Oracle(oracle.load(path))
+    failed = _failures(mutant)
+    assert failed, f"no pin caught mutant {k}: {MUTANTS[k]}"
