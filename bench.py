@@ -1,0 +1,417 @@
+"""Benchmark of the unigrid FMM Poisson solve on GB300.
+
+Workload (default): 512^3 isolated grid, expansion order p = 6, leaf boxes of
+4^3 cells, seeded lognormal density (P(k) ~ k^-2.5, outer 10% zeroed), one
+solve = P2M, M2M, M2L+L2L on every level, near field + L2P, and the 5-point
+force stencil.  Metric: Mcells/s = cells per solve / seconds per solve.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--n 512]
+    python bench.py --impl reference ...     # the FP64 CPU oracle on this host
+
+Multi-GPU (torchrun, one rank per GPU): every rank solves its own independent
+field (replicas, no collective on the data path); value = all ranks' cells /
+max-over-ranks time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM Mcells/s at 512^3 p=6 (mixed vs FP32 plain, rel err≤1e-5); % roofline"
+UNIT = "Mcells/s"
+DEFAULT_PRECISION = "fp32"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--order", type=int, default=6)
+    ap.add_argument("--leaf", type=int, default=4)
+    ap.add_argument("--precision", default=DEFAULT_PRECISION)
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32-plain and FP64 comparison solves")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- counts ---
+
+def m2l_pairs(p):
+    return math.comb(p + 6, 6)  # (alpha, beta) with |alpha| + |beta| <= p
+
+
+def il_total(n_axes):
+    """Sum over the boxes of a level of |interaction list| (Sec. 2.2), clipped
+    to the domain.  Separable per axis: |IL(T)| = prod A_q - prod B_q with A_q
+    the source indices among the children of the parent's neighbours and B_q
+    those within distance 1."""
+    A, B = 1, 1
+    for n in n_axes:
+        a = b = 0
+        for t in range(n):
+            par = t // 2
+            lo, hi = max(0, 2 * (par - 1)), min(n - 1, 2 * (par + 1) + 1)
+            a += hi - lo + 1
+            b += min(n - 1, t + 1) - max(0, t - 1) + 1
+        A *= a
+        B *= b
+    return A - B
+
+
+def hierarchy(dims, leaf):
+    ext = [tuple(d // leaf for d in dims)]
+    while any(e > 1 for e in ext[-1]):
+        ext.append(tuple((e + 1) // 2 for e in ext[-1]))
+    return ext[::-1]  # level 0 first
+
+
+def algorithmic_counts(dims, leaf, p):
+    lev = hierarchy(dims, leaf)
+    m2l_flop = sum(il_total(lev[l]) for l in range(2, len(lev))) * 2 * m2l_pairs(p)
+    # near field: every target cell against every cell of its 27 (clipped) neighbour leaf boxes
+    near = 1
+    for n in lev[-1]:
+        near *= sum(min(n - 1, t + 1) - max(0, t - 1) + 1 for t in range(n))
+    b3 = leaf ** 3
+    near_flop = near * b3 * b3 * 2
+    return {"m2l_flop": m2l_flop, "near_flop": near_flop}
+
+
+# ----------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (every 200 ms)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 8:
+                        rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        smax = [num(r[1]) for r in rows if num(r[1]) is not None]
+        pw = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_index_for_smi(torch):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    dev = torch.cuda.current_device()
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        return "GPU-" + uuid if not uuid.startswith("GPU-") else uuid
+    except Exception:
+        pass
+    if vis:
+        return vis.split(",")[dev]
+    return dev
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+def source_digest(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_key, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current source of that kernel (else None)."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None
+    with open(PROFILE_TRAFFIC) as f:
+        data = json.load(f)
+    ent = data.get(kernel_key)
+    if not ent or ent.get("workload") != workload:
+        return None
+    if ent.get("source_sha") != source_digest(ent.get("sources", [])):
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+# --------------------------------------------------------------- reference --
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle_sample(n, order, leaf, seed=2606):
+    """One full FP64 oracle solve on an n^3 grid of the benchmark's field recipe."""
+    import numpy as np
+
+    from oracle import Oracle
+    from paper_2606_13793_gb300 import inputs
+
+    orc = Oracle()
+    rho = inputs.lognormal(n, seed=seed).astype(np.float64)
+    t0 = time.perf_counter()
+    orc.fmm(rho, leaf, order, dx=1.0 / n, accel=True, threads=cpu_cores())
+    return time.perf_counter() - t0, orc.max_threads()
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    n_s = 64
+    for _ in range(args.warmup):
+        run_oracle_sample(n_s, args.order, args.leaf)
+    total = 0.0
+    thr = 1
+    for k in range(args.steps):
+        dt, thr = run_oracle_sample(n_s, args.order, args.leaf, seed=2606 + k)
+        total += dt
+    value = n_s ** 3 * args.steps / total / 1e6
+    sample = f"full FP64 oracle solve of a {n_s}^3 grid of the same field recipe per step (p={args.order}, leaf {args.leaf})"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"unigrid FMM {args.n}^3 p={args.order} leaf {args.leaf} lognormal",
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- ours --
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    import paper_2606_13793_gb300 as fmm
+    from paper_2606_13793_gb300 import _build, inputs
+
+    if rank == 0:
+        _build.build()
+    if dist:
+        dist.barrier()
+    n, p, b = args.n, args.order, args.leaf
+    dx = 1.0 / n
+    rho_np = inputs.lognormal(n, seed=2606 + rank)
+    rho = torch.from_numpy(rho_np).cuda()
+    plan = fmm.FMMPlan((n, n, n), p, b, args.precision, dx=dx)
+    phi = torch.empty_like(rho)
+    acc = torch.empty((3,) + rho.shape, dtype=rho.dtype, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.solve(rho, accel=True, phi_out=phi, accel_out=acc)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    plan.check()
+
+    # ---- timed region (device) ----
+    plan.timing(True)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_index_for_smi(torch)) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(args.steps):
+            step()
+        end.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    ms = start.elapsed_time(end)
+    stages = plan.timing_read()
+    plan.timing(False)
+    clocks = clk.summary()
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    cells = n ** 3
+    value = cells * args.steps * world / (ms_max / 1e3) / 1e6
+
+    # ---- e2e through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        rho_h = torch.from_numpy(rho_np).pin_memory()
+        phi_h = torch.empty(rho_h.shape, dtype=torch.float32).pin_memory()
+        acc_h = torch.empty((3,) + tuple(rho_h.shape), dtype=torch.float32).pin_memory()
+        plan.solve_host(rho_h, phi_h, acc_h)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.solve_host(rho_h, phi_h, acc_h)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        tt = torch.tensor([te], device="cuda", dtype=torch.float64)
+        if dist:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+        e2e = {"value": cells * args.steps * world / te / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(rho_h.numel() * 4),
+               "d2h_bytes_per_step": int((phi_h.numel() + acc_h.numel()) * 4)}
+        del rho_h, phi_h, acc_h
+
+    # ---- accuracy of this mode against the FP64 solve of the same field ----
+    compare = {}
+    if not args.no_compare and rank == 0:
+        phi_mode = phi.double().clone()
+        p64 = fmm.FMMPlan((n, n, n), p, b, "fp64", dx=dx)
+        phi64 = p64.solve(rho.double())
+        torch.cuda.synchronize()
+        compare["rel_err_vs_fp64"] = float(torch.linalg.vector_norm(phi_mode - phi64) /
+                                           torch.linalg.vector_norm(phi64))
+        p64.close()
+        del phi64
+        if args.precision != "fp32":
+            pp = fmm.FMMPlan((n, n, n), p, b, "fp32", dx=dx)
+            for _ in range(3):
+                pp.solve(rho, accel=True, phi_out=phi, accel_out=acc)
+            torch.cuda.synchronize()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            for _ in range(args.steps):
+                pp.solve(rho, accel=True, phi_out=phi, accel_out=acc)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            compare["fp32_plain_mcells_s"] = cells * args.steps / (s0.elapsed_time(s1) / 1e3) / 1e6
+            pp.close()
+
+    # ---- roofline of the dominant kernel ----
+    peaks, peak_src = measured_peaks()
+    counts = algorithmic_counts((n, n, n), b, p)
+    dom = max(("m2l", "near_field"), key=lambda k: stages[k][0])
+    dom_ms, dom_launches = stages[dom]
+    flop = (counts["m2l_flop"] if dom == "m2l" else counts["near_flop"]) * args.steps
+    achieved = flop / (dom_ms / 1e3) / 1e12
+    tc = args.precision in ("tf32", "bf16x3") and dom == "m2l"
+    if tc:
+        bound, peak_val, unit = "tensor", peaks["bf16_tflops_sustained"], "TFLOP/s"
+    else:
+        # FP32 FFMA: 152 SMs x 128 lanes x 2 flop x max SM clock
+        bound, peak_val, unit = "alu", 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, "TFLOP/s"
+    workload = f"{n}^3 p={p} leaf {b} {args.precision}"
+    kernel_key = {"m2l": "m2l", "near_field": "near_field"}[dom] + "/" + args.precision
+    traffic = profiled_traffic(kernel_key, workload)
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak_val, "unit": unit, "frac": achieved / peak_val,
+                "traffic": traffic, "kernel": dom, "peak_source": peak_src + (" (FP32 FFMA from unit counts)"
+                                                                              if bound == "alu" else "")}
+
+    # ---- CPU oracle baseline (rank 0, bounded sample) ----
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        n_s = 128 if n >= 128 else n
+        dt, thr = run_oracle_sample(n_s, p, b)
+        cpu = {"value": n_s ** 3 / dt / 1e6, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"one full FP64 oracle solve of a {n_s}^3 grid of the same lognormal recipe (p={p}, "
+                         f"leaf {b}); the method is O(N) so Mcells/s carries to {n}^3"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32/f32", "bf16x3": "bf16x3/f32"}[args.precision],
+                "data": "synthetic",
+                "config": {"workload": f"unigrid FMM {n}^3 isolated, p={p}, leaf {b}^3, lognormal P(k)~k^-2.5",
+                           "precision": args.precision, "l2": "inputs larger than L2 (rho 512 MiB, outputs 2 GiB)",
+                           "parallelism": f"replicas x{world}", **compare},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": plan.launches(True) * args.steps,
+                "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if v[1]},
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

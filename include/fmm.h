@@ -1,0 +1,192 @@
+/*
+ * fmm.h -- C ABI of the GB300-native unigrid fast-multipole Poisson solver.
+ *
+ * The solver computes the gravitational potential of a density sampled on an
+ * isolated (vacuum-boundary) uniform grid by the cell-based fast multipole
+ * method of Lee & Teyssier, "A Scalable Fast Multipole Method Poisson Solver
+ * for the RAMSES code: I. Unigrid Algorithm":
+ *
+ *   P2M    multipoles of each leaf box of b^3 cells        (Sec. 2.1, eq. multipole)
+ *   M2M    shift of multipoles up the FMM grid hierarchy   (Sec. 2.1, eq. M2M_general)
+ *   M2L    intermediate field over the fixed 189-box list  (Sec. 2.2; Sec. 2.3, eq. M2L)
+ *   L2L    far field moved from parent to child centres    (Sec. 2.3, eq. L2L)
+ *   L2P    local expansion evaluated at the cell centres   (Sec. 2.3)
+ *   P2P    softened cell-cell direct sum over the 27 near  (Sec. 2.3, eq. direct)
+ *          leaf boxes (self cell included: g(0) = -1/dx)
+ *   accel  a = -grad(phi) by the 5-point stencil            (App. C)
+ *
+ * so that   phi(x_i) = G dx^2 [ sum_far L2P + sum_{j near i} rho_j g(x_i - x_j) ]
+ * with rho a mass density (cell mass = rho dx^3) and g(r) = -1/|r| in cell
+ * units.  Expansions are Cartesian Taylor series truncated at
+ * |alpha| + |beta| <= order (multipole order + local order <= order), which
+ * makes the solve a symmetric linear operator.
+ *
+ * Conventions for every entry point:
+ *  - Arrays are C-contiguous [nz][ny][nx] (x fastest); accel is [3][nz][ny][nx]
+ *    (a_x block, then a_y, then a_z).
+ *  - Element type: double for FMM_FP64, float for every other precision.
+ *  - Device pointers are owned by the caller, must stay valid until the work
+ *    enqueued on `stream` has finished, and must be 16-byte aligned.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *    is asynchronous on that stream unless stated otherwise; none allocates
+ *    device memory after fmm_plan() (fmm_solve_host allocates its staging
+ *    buffers on first use, see there).
+ *  - Argument errors are reported synchronously by the return code; the text
+ *    of the most recent error of the calling thread is fmm_last_error().
+ *  - Device-side conditions (non-finite input, a spin-wait that gave up) are
+ *    latched in the plan and reported by fmm_check() after the stream has
+ *    been synchronised.
+ */
+#ifndef FMM_GB300_H
+#define FMM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_plan_s* fmm_plan_t;
+
+typedef enum {
+  FMM_OK = 0,
+  FMM_ERR_ARG = 1,          /* invalid argument (NULL, sizes, alignment, order) */
+  FMM_ERR_UNSUPPORTED = 2,  /* valid but not supported by this build/device */
+  FMM_ERR_ALLOC = 3,        /* device or host allocation failed */
+  FMM_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+  FMM_ERR_NONFINITE = 5,    /* the density held NaN or Inf (fmm_check) */
+  FMM_ERR_TIMEOUT = 6       /* a device spin-wait reached its limit (fmm_check) */
+} fmm_status;
+
+/* Arithmetic of the solve. */
+typedef enum {
+  FMM_FP64 = 0,        /* every step in FP64 on the CUDA cores; data are double */
+  FMM_FP32 = 1,        /* every step in FP32 on the CUDA cores ("plain")        */
+  FMM_M2L_TF32 = 2,    /* M2L on tcgen05 tensor cores, TF32 inputs, FP32
+                          accumulation; the n_fp64_levels coarsest M2L levels in
+                          FP64; everything else FP32                            */
+  FMM_M2L_BF16X3 = 3   /* as FMM_M2L_TF32 with the M2L operands split into
+                          bf16 hi + lo parts and three products
+                          (hi*hi + hi*lo + lo*hi), FP32 accumulation             */
+} fmm_precision;
+
+typedef struct {
+  int nx, ny, nz; /* cells per axis, each a multiple of `leaf`                    */
+  double dx;      /* cell size (physical units); phi scales as G dx^2, accel G dx */
+  double G;       /* gravitational constant                                      */
+} fmm_grid;
+
+typedef struct {
+  int precision;      /* fmm_precision                                          */
+  int n_fp64_levels;  /* mixed precisions: coarsest M2L levels kept in FP64
+                         (levels 2 .. 1+n_fp64_levels); default 3               */
+  int accel;          /* 1: fmm_solve may be given an accel output (FD5) */
+  int reserved[5];    /* must be zero */
+} fmm_opts;
+
+/* Default options: FMM_FP32, n_fp64_levels = 3, accel = 1. */
+void fmm_default_opts(fmm_opts* opts);
+
+/*
+ * fmm_plan -- build a solver for one grid shape.
+ *   grid   : grid extents, cell size and G (read during the call only).
+ *   order  : expansion order p, 0 <= p <= 8 (|alpha|+|beta| <= p).
+ *   leaf   : cells per leaf-box side b (the paper's 2^dl), one of 2, 4, 8.
+ *   opts   : NULL for fmm_default_opts().
+ *   stream : stream used for the table uploads.
+ *   out    : receives the plan; the plan owns its tables and workspace arena
+ *            (device memory sized by fmm_workspace_bytes()).
+ * The hierarchy follows Sec. 2: the finest FMM level has (n/b) boxes per axis,
+ * each coarser level halves the box count (rounding up; boxes past the domain
+ * carry no mass) until one box remains.  The M2L translation kernels are
+ * precomputed once, for the unit box, from the fixed interaction geometry
+ * (Sec. 2.2).  Errors: FMM_ERR_ARG, FMM_ERR_UNSUPPORTED (no sm_103 device for a
+ * tensor-core precision), FMM_ERR_ALLOC, FMM_ERR_CUDA.
+ */
+fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* opts, void* stream,
+                    fmm_plan_t* out);
+
+/*
+ * fmm_solve -- phi (and optionally accel) of the density rho.
+ *   rho   : device, [nz][ny][nx] density (read only).
+ *   phi   : device, [nz][ny][nx] potential (written).
+ *   accel : device, [3][nz][ny][nx] or NULL; -grad(phi) by the 4th-order
+ *           5-point central stencil (App. C), 2nd-order central one cell from
+ *           an edge and 2nd-order one-sided at the edge.
+ * Runs P2M, M2M, M2L+L2L per level, P2P+L2P and the stencil as kernels on
+ * `stream`; no host synchronisation, no allocation.  Errors: FMM_ERR_ARG,
+ * FMM_ERR_CUDA (launch failure).
+ */
+fmm_status fmm_solve(fmm_plan_t plan, const void* rho, void* phi, void* accel, void* stream);
+
+/*
+ * fmm_solve_adjoint -- gradient of a loss with respect to rho.
+ *   grad_phi   : device [nz][ny][nx], dLoss/dphi (read only).
+ *   grad_accel : device [3][nz][ny][nx] dLoss/daccel, or NULL.
+ *   grad_rho   : device [nz][ny][nx] (written): A^T (grad_phi - FD^T grad_accel/dx) G dx^2.
+ * With |alpha|+|beta| <= order the FMM operator A is symmetric (Green's
+ * function symmetry, Sec. 2.3), so A^T is the same chain of kernels applied to
+ * the adjoint source; the stencil transpose FD^T is its own kernel.
+ */
+fmm_status fmm_solve_adjoint(fmm_plan_t plan, const void* grad_phi, const void* grad_accel, void* grad_rho,
+                             void* stream);
+
+/*
+ * fmm_solve_host -- fmm_solve with HOST buffers: copies rho host->device,
+ * solves, copies phi (and accel) device->host, all on `stream`, then
+ * synchronises `stream` before returning.  Pinned host memory gives full
+ * copy bandwidth; pageable memory works but is slower.  The first call
+ * allocates device staging buffers owned by the plan (freed by
+ * fmm_plan_destroy).
+ */
+fmm_status fmm_solve_host(fmm_plan_t plan, const void* rho_host, void* phi_host, void* accel_host, void* stream);
+
+/* fmm_check -- synchronises the plan's last stream and reports device-side
+ * flags (FMM_ERR_NONFINITE, FMM_ERR_TIMEOUT), clearing them. */
+fmm_status fmm_check(fmm_plan_t plan);
+
+/* Bytes of device memory the plan holds (tables + workspace arena). */
+size_t fmm_workspace_bytes(fmm_plan_t plan);
+
+/* Number of kernel launches one fmm_solve() enqueues for this plan. */
+int fmm_solve_launches(fmm_plan_t plan, int with_accel);
+
+/*
+ * Per-stage timing with CUDA events recorded on the solve's own stream around
+ * every kernel launch (for benchmarks; off by default).
+ *   fmm_timing_enable : 1 starts recording (and clears totals), 0 stops.
+ *                       Creates its event pool here, not during solves.
+ *   fmm_timing_read   : synchronises, then writes for each stage i < nstages
+ *                       the summed milliseconds ms[i] and launch count
+ *                       launches[i] since the last enable/read, and clears them.
+ * Stages (index: name): see fmm_timing_stage_name().
+ */
+fmm_status fmm_timing_enable(fmm_plan_t plan, int enable);
+fmm_status fmm_timing_read(fmm_plan_t plan, double* ms, int* launches, int nstages);
+int fmm_timing_stage_count(void);
+const char* fmm_timing_stage_name(int stage);
+
+/* Frees every resource of the plan (synchronises the device first). */
+fmm_status fmm_plan_destroy(fmm_plan_t plan);
+
+/* Text of the most recent error on the calling thread ("" if none). */
+const char* fmm_last_error(void);
+
+/*
+ * fmm_debug_level -- copy one level's expansions to host memory in the
+ * canonical layout [box z][box y][box x][coef] (coefficients ordered by total
+ * order, then a descending, then b descending), as double, in cell units
+ * about each box centre (M_alpha = sum m (x-c)^alpha, L_beta as in eq. M2L).
+ *   what: 0 = multipoles M, 1 = local expansions L.  level: 2..L.
+ * Synchronises the device.  For tests that localise a mismatch.
+ */
+fmm_status fmm_debug_level(fmm_plan_t plan, int what, int level, double* host_out, size_t host_count);
+
+/* Number of FMM levels minus one (index of the leaf level), or -1. */
+int fmm_plan_leaf_level(fmm_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM_GB300_H */

@@ -1,1 +1,284 @@
-"""GB300-native unigrid FMM Poisson solver (package)."""
+"""GB300-native unigrid FMM Poisson solver (Lee & Teyssier's cell-based FMM).
+
+This package is a thin Python binding over the C ABI in ``include/fmm.h``
+(``libfmm_gb300.so``, built in-tree by ``_build.py``): it marshals pointers,
+shapes and the current CUDA stream; every step of the solve runs in the
+library's kernels.  PyTorch provides device memory, streams and autograd.
+
+There is no CPU fallback: without the compiled library every call raises.
+
+    plan = FMMPlan((nx, ny, nz), order=6, leaf=4, precision="fp32", dx=1/nx)
+    phi, accel = plan.solve(rho, accel=True)       # rho: cuda tensor [nz][ny][nx]
+    grad_rho = plan.solve_adjoint(grad_phi, grad_accel)
+    phi = FMMSolve.apply(rho, plan)                # differentiable
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfmm_gb300.so")
+
+FMM_OK = 0
+STATUS = {0: "FMM_OK", 1: "FMM_ERR_ARG", 2: "FMM_ERR_UNSUPPORTED", 3: "FMM_ERR_ALLOC", 4: "FMM_ERR_CUDA",
+          5: "FMM_ERR_NONFINITE", 6: "FMM_ERR_TIMEOUT"}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3}
+
+# every symbol include/fmm.h declares
+EXPORTS = ["fmm_default_opts", "fmm_plan", "fmm_solve", "fmm_solve_adjoint", "fmm_solve_host", "fmm_check",
+           "fmm_workspace_bytes", "fmm_solve_launches", "fmm_plan_destroy", "fmm_last_error", "fmm_debug_level",
+           "fmm_plan_leaf_level", "fmm_timing_enable", "fmm_timing_read", "fmm_timing_stage_count",
+           "fmm_timing_stage_name"]
+
+
+class FMMError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("dx", ctypes.c_double),
+                ("G", ctypes.c_double)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("n_fp64_levels", ctypes.c_int), ("accel", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load libfmm_gb300.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"{p} is missing: build it with paper_2606_13793_gb300._build.build() "
+                              "(there is no CPU fallback)")
+        lib = ctypes.CDLL(p)
+        vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        lib.fmm_default_opts.argtypes = [ctypes.POINTER(_Opts)]
+        lib.fmm_default_opts.restype = None
+        lib.fmm_plan.argtypes = [ctypes.POINTER(_Grid), i, i, ctypes.POINTER(_Opts), vp, ctypes.POINTER(vp)]
+        lib.fmm_plan.restype = i
+        lib.fmm_solve.argtypes = [vp, vp, vp, vp, vp]
+        lib.fmm_solve.restype = i
+        lib.fmm_solve_adjoint.argtypes = [vp, vp, vp, vp, vp]
+        lib.fmm_solve_adjoint.restype = i
+        lib.fmm_solve_host.argtypes = [vp, vp, vp, vp, vp]
+        lib.fmm_solve_host.restype = i
+        lib.fmm_check.argtypes = [vp]
+        lib.fmm_check.restype = i
+        lib.fmm_workspace_bytes.argtypes = [vp]
+        lib.fmm_workspace_bytes.restype = sz
+        lib.fmm_solve_launches.argtypes = [vp, i]
+        lib.fmm_solve_launches.restype = i
+        lib.fmm_plan_destroy.argtypes = [vp]
+        lib.fmm_plan_destroy.restype = i
+        lib.fmm_last_error.argtypes = []
+        lib.fmm_last_error.restype = ctypes.c_char_p
+        lib.fmm_debug_level.argtypes = [vp, i, i, ctypes.POINTER(ctypes.c_double), sz]
+        lib.fmm_debug_level.restype = i
+        lib.fmm_plan_leaf_level.argtypes = [vp]
+        lib.fmm_plan_leaf_level.restype = i
+        lib.fmm_timing_enable.argtypes = [vp, i]
+        lib.fmm_timing_enable.restype = i
+        lib.fmm_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), i]
+        lib.fmm_timing_read.restype = i
+        lib.fmm_timing_stage_count.argtypes = []
+        lib.fmm_timing_stage_count.restype = i
+        lib.fmm_timing_stage_name.argtypes = [i]
+        lib.fmm_timing_stage_name.restype = ctypes.c_char_p
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(lib, status):
+    if status != FMM_OK:
+        raise FMMError(status, lib.fmm_last_error().decode(errors="replace"))
+
+
+def _stream_handle(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class FMMPlan:
+    """One solver for a fixed grid shape, order, leaf size and precision."""
+
+    def __init__(self, shape, order: int = 6, leaf: int = 4, precision: str = "fp32", dx: float = 1.0,
+                 G: float = 1.0, n_fp64_levels: int = 3, accel: bool = True, stream=None):
+        import torch
+
+        self.lib = load()
+        nx, ny, nz = (int(v) for v in shape)
+        self.shape = (nx, ny, nz)
+        self.order, self.leaf, self.precision = int(order), int(leaf), precision
+        self.dx, self.G = float(dx), float(G)
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        if precision not in PRECISION:
+            raise ValueError(f"precision must be one of {sorted(PRECISION)}")
+        grid = _Grid(nx, ny, nz, self.dx, self.G)
+        opts = _Opts()
+        self.lib.fmm_default_opts(ctypes.byref(opts))
+        opts.precision = PRECISION[precision]
+        opts.n_fp64_levels = int(n_fp64_levels)
+        opts.accel = 1 if accel else 0
+        handle = ctypes.c_void_p()
+        _check(self.lib, self.lib.fmm_plan(ctypes.byref(grid), self.order, self.leaf, ctypes.byref(opts),
+                                           _stream_handle(stream), ctypes.byref(handle)))
+        self._h = handle
+
+    # -- helpers -------------------------------------------------------------
+    def _tensor(self, t, name, lead=()):
+        import torch
+
+        want = tuple(lead) + (self.shape[2], self.shape[1], self.shape[0])
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != self.dtype:
+            raise TypeError(f"{name} must be {self.dtype}, got {t.dtype}")
+        if tuple(t.shape) != want:
+            raise ValueError(f"{name} must have shape {want}, got {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def _empty(self, lead=()):
+        import torch
+
+        return torch.empty(tuple(lead) + (self.shape[2], self.shape[1], self.shape[0]), dtype=self.dtype,
+                           device="cuda")
+
+    # -- API -----------------------------------------------------------------
+    def solve(self, rho, accel: bool = False, phi_out=None, accel_out=None, stream=None):
+        """phi (and accel [3][nz][ny][nx] if asked) of the density rho."""
+        r = self._tensor(rho, "rho")
+        phi = phi_out if phi_out is not None else self._empty()
+        acc = None
+        if accel:
+            acc = accel_out if accel_out is not None else self._empty((3,))
+        _check(self.lib, self.lib.fmm_solve(self._h, r, self._tensor(phi, "phi"),
+                                            self._tensor(acc, "accel", (3,)) if acc is not None else None,
+                                            _stream_handle(stream)))
+        return (phi, acc) if accel else phi
+
+    def solve_adjoint(self, grad_phi=None, grad_accel=None, out=None, stream=None):
+        """dLoss/drho from dLoss/dphi and (optionally) dLoss/daccel."""
+        gp = self._tensor(grad_phi, "grad_phi") if grad_phi is not None else None
+        ga = self._tensor(grad_accel, "grad_accel", (3,)) if grad_accel is not None else None
+        g = out if out is not None else self._empty()
+        _check(self.lib, self.lib.fmm_solve_adjoint(self._h, gp, ga, self._tensor(g, "grad_rho"),
+                                                    _stream_handle(stream)))
+        return g
+
+    def solve_host(self, rho_host, phi_host, accel_host=None, stream=None):
+        """Host-buffer solve (numpy arrays or pinned CPU tensors); synchronous."""
+        def ptr(a):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                return ctypes.c_void_p(a.data_ptr())
+            return ctypes.c_void_p(a.ctypes.data)
+
+        _check(self.lib, self.lib.fmm_solve_host(self._h, ptr(rho_host), ptr(phi_host), ptr(accel_host),
+                                                 _stream_handle(stream)))
+
+    def timing(self, enable: bool = True):
+        """Start (clearing) or stop per-stage CUDA-event timing."""
+        _check(self.lib, self.lib.fmm_timing_enable(self._h, 1 if enable else 0))
+
+    def timing_read(self):
+        """{stage: (total_ms, launches)} since the last enable/read (synchronises)."""
+        n = int(self.lib.fmm_timing_stage_count())
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int * n)()
+        _check(self.lib, self.lib.fmm_timing_read(self._h, ms, cnt, n))
+        return {self.lib.fmm_timing_stage_name(i).decode(): (ms[i], cnt[i]) for i in range(n)}
+
+    def check(self):
+        _check(self.lib, self.lib.fmm_check(self._h))
+
+    def debug_level(self, what: str, level: int):
+        """One level's multipoles ('M') or locals ('L') as float64 [nbox, ncoef] (canonical order)."""
+        import numpy as np
+
+        lv = self.levels()[level]
+        nc = (self.order + 1) * (self.order + 2) * (self.order + 3) // 6
+        out = np.zeros((int(lv[0] * lv[1] * lv[2]), nc))
+        _check(self.lib, self.lib.fmm_debug_level(self._h, 0 if what == "M" else 1, int(level),
+                                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size))
+        return out
+
+    def levels(self):
+        ext = [tuple(v // self.leaf for v in self.shape)]
+        while any(e > 1 for e in ext[-1]):
+            ext.append(tuple((e + 1) // 2 for e in ext[-1]))
+        return ext[::-1]
+
+    @property
+    def leaf_level(self) -> int:
+        return int(self.lib.fmm_plan_leaf_level(self._h))
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self.lib.fmm_workspace_bytes(self._h))
+
+    def launches(self, accel: bool = True) -> int:
+        return int(self.lib.fmm_solve_launches(self._h, 1 if accel else 0))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.fmm_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _make_autograd():
+    import torch
+
+    class FMMSolve(torch.autograd.Function):
+        """phi, accel = FMMSolve.apply(rho, plan); backward runs fmm_solve_adjoint.
+
+        The solve is linear in rho, so nothing is saved for the backward pass."""
+
+        @staticmethod
+        def forward(ctx, rho, plan):
+            ctx.plan = plan
+            phi, acc = plan.solve(rho.contiguous(), accel=True)
+            return phi, acc
+
+        @staticmethod
+        def backward(ctx, grad_phi, grad_accel):
+            plan = ctx.plan
+            gp = grad_phi.contiguous() if grad_phi is not None else None
+            ga = grad_accel.contiguous() if grad_accel is not None else None
+            if gp is None and ga is None:
+                return None, None
+            return plan.solve_adjoint(gp, ga), None
+
+    return FMMSolve
+
+
+def __getattr__(name):
+    if name == "FMMSolve":
+        cls = _make_autograd()
+        globals()["FMMSolve"] = cls
+        return cls
+    raise AttributeError(name)

@@ -1,0 +1,780 @@
+// Plan construction and the C ABI (include/fmm.h).
+//
+// The plan precomputes everything that depends only on the geometry (Sec. 2.2:
+// the cell-centred scheme fixes the interaction displacements, so the
+// Green's-function derivatives are tabulated once):
+//  * the hierarchy extents (round-up halving, Sec. 2);
+//  * Taylor coefficients of 1/|u + t| at every unit box offset u of the
+//    interaction list, by the three-term recurrence
+//        n |u|^2 b_g = -(2n-1) sum_i u_i b_{g-e_i} - (n-1) sum_i b_{g-2e_i},
+//    n = |g| (derivatives of g = -1/r are then D_g = -g! b_g);
+//  * the unit-box M2L operator Wt_u[beta][alpha] = (-1)^|alpha|
+//    C(alpha+beta, alpha) (-b_{alpha+beta}(u)), laid out as column tiles of
+//    the neighbour contraction (k_gemm_simt.cu);
+//  * the near-field matrix g(x_t - x_s) per neighbour leaf box (eq. direct);
+//  * the M2M / L2L shift pair lists.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fmm_internal.h"
+
+using namespace fmmgb;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+fmm_status fail(fmm_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+#define CUDA_TRY(expr)                                                                           \
+  do {                                                                                           \
+    cudaError_t e__ = (expr);                                                                    \
+    if (e__ != cudaSuccess) return fail(FMM_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e__)); \
+  } while (0)
+
+struct MultiIndex {
+  int p = 0, nc = 0;
+  std::vector<int> a, b, c;  // components, canonical order
+  int index(int x, int y, int z) const {
+    const int n = x + y + z;
+    return n * (n + 1) * (n + 2) / 6 + (n - x) * (n - x + 1) / 2 + (n - x - y);
+  }
+  void init(int order) {
+    p = order;
+    a.clear(), b.clear(), c.clear();
+    for (int n = 0; n <= p; ++n)
+      for (int x = n; x >= 0; --x)
+        for (int y = n - x; y >= 0; --y) {
+          a.push_back(x), b.push_back(y), c.push_back(n - x - y);
+        }
+    nc = (int)a.size();
+  }
+};
+
+double binom(int n, int k) {
+  if (k < 0 || k > n) return 0.0;
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+
+// Taylor coefficients of 1/|u + t| in t for |g| <= p (canonical order).
+void taylor_inv_r(const double u[3], const MultiIndex& mi, std::vector<double>& out) {
+  out.assign(mi.nc, 0.0);
+  const double r2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  out[0] = 1.0 / std::sqrt(r2);
+  for (int k = 1; k < mi.nc; ++k) {
+    const int g[3] = {mi.a[k], mi.b[k], mi.c[k]};
+    const int n = g[0] + g[1] + g[2];
+    double s = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      int h[3] = {g[0], g[1], g[2]};
+      if (g[i] >= 1) {
+        h[i] = g[i] - 1;
+        s -= (2.0 * n - 1.0) * u[i] * out[mi.index(h[0], h[1], h[2])];
+      }
+      if (g[i] >= 2) {
+        h[i] = g[i] - 2;
+        s -= (n - 1.0) * out[mi.index(h[0], h[1], h[2])];
+      }
+    }
+    out[k] = s / (n * r2);
+  }
+}
+
+int level_of_order(const MultiIndex& mi, int k) { return mi.a[k] + mi.b[k] + mi.c[k]; }
+
+int ncoef(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+enum Stage { ST_CHECK = 0, ST_P2M, ST_M2M, ST_L2L, ST_M2L, ST_NEAR, ST_LEAF, ST_FD, ST_ADJ_SRC, ST_COUNT };
+const char* kStageNames[ST_COUNT] = {"finite_check", "p2m", "m2m", "l2l", "m2l", "near_field", "leaf_l2p",
+                                     "fd_accel", "adjoint_source"};
+constexpr int kEventPool = 8192;
+
+}  // namespace
+
+struct fmm_plan_s {
+  int dims[3] = {0, 0, 0};
+  double dx = 1.0, G = 1.0;
+  int p = 0, b = 0, nc = 0;
+  fmm_opts opts{};
+  int L = 0;
+  int lmin = 0;  // first level with stored expansions
+  Level lev[kMaxLevels];
+  MultiIndex mi;
+
+  // device memory
+  std::vector<void*> allocs;
+  size_t dev_bytes = 0;
+  unsigned char* arena = nullptr;
+  size_t arena_bytes = 0;
+  size_t rho_box_off = 0, near_off = 0, work_off = 0;
+  int* d_flag = nullptr;
+  int8_t* d_mi = nullptr;
+  int* d_m2m_start = nullptr;
+  ShiftEntry* d_m2m = nullptr;
+  int* d_l2l_start = nullptr;
+  ShiftEntry* d_l2l = nullptr;
+  // SIMT M2L weights (fp32 and/or fp64) and tile tables
+  void* d_w_m2l_f32 = nullptr;
+  void* d_w_m2l_f64 = nullptr;
+  int* d_m2l_tile_k = nullptr;
+  long long* d_m2l_tile_w = nullptr;
+  int m2l_ntiles = 0;
+  // near field
+  void* d_w_near = nullptr;
+  int* d_near_tile_k = nullptr;
+  long long* d_near_tile_w = nullptr;
+  int near_ntiles = 0;
+  // host-buffer staging for fmm_solve_host
+  void* d_io_rho = nullptr;
+  void* d_io_phi = nullptr;
+  void* d_io_acc = nullptr;
+  cudaStream_t last_stream = nullptr;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Rec {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+
+  bool f64_data() const { return opts.precision == FMM_FP64; }
+  size_t esize() const { return f64_data() ? 8 : 4; }
+  long long ncell() const { return (long long)dims[0] * dims[1] * dims[2]; }
+  TreeTables tables() const {
+    TreeTables t;
+    t.mi = d_mi;
+    t.m2m_start = d_m2m_start;
+    t.m2m = d_m2m;
+    t.l2l_start = d_l2l_start;
+    t.l2l = d_l2l;
+    t.p = p;
+    t.nc = nc;
+    t.b = b;
+    return t;
+  }
+  void* M(int l) const { return arena + lev[l].m_off; }
+  void* Lx(int l) const { return arena + lev[l].l_off; }
+
+  template <typename T>
+  fmm_status upload(const std::vector<T>& host, T** dptr, cudaStream_t s) {
+    const size_t bytes = std::max<size_t>(host.size(), 1) * sizeof(T);
+    void* d = nullptr;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) return fail(FMM_ERR_ALLOC, "cudaMalloc(%zu) failed", bytes);
+    allocs.push_back(d);
+    dev_bytes += bytes;
+    if (!host.empty()) CUDA_TRY(cudaMemcpyAsync(d, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    *dptr = static_cast<T*>(d);
+    return FMM_OK;
+  }
+  void release() {
+    cudaDeviceSynchronize();
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    ev_pool.clear();
+    for (void* d : allocs) cudaFree(d);
+    allocs.clear();
+    if (d_io_rho) cudaFree(d_io_rho);
+    if (d_io_phi) cudaFree(d_io_phi);
+    if (d_io_acc) cudaFree(d_io_acc);
+  }
+};
+
+namespace {
+
+// Build the per-level extents (Sec. 2: halve with round-up to one box).
+fmm_status build_levels(fmm_plan_t P) {
+  int ext[kMaxLevels][3];
+  int cnt = 1;
+  for (int q = 0; q < 3; ++q) ext[0][q] = P->dims[q] / P->b;
+  while (ext[cnt - 1][0] > 1 || ext[cnt - 1][1] > 1 || ext[cnt - 1][2] > 1) {
+    if (cnt >= kMaxLevels) return fail(FMM_ERR_ARG, "grid too deep");
+    for (int q = 0; q < 3; ++q) ext[cnt][q] = (ext[cnt - 1][q] + 1) / 2;
+    ++cnt;
+  }
+  P->L = cnt - 1;
+  for (int l = 0; l <= P->L; ++l) {
+    Level& lv = P->lev[l];
+    for (int q = 0; q < 3; ++q) {
+      lv.n[q] = ext[P->L - l][q];
+      lv.np[q] = (lv.n[q] + 1) / 2;
+    }
+    lv.nbox = (long long)lv.n[0] * lv.n[1] * lv.n[2];
+    lv.npar = (long long)lv.np[0] * lv.np[1] * lv.np[2];
+  }
+  return FMM_OK;
+}
+
+// Column tiles of the neighbour contraction for M2L: output column
+// n = beta*8 + child; tile t covers beta in [4t, 4t+4) whose lowest order
+// fixes the reduction prefix 8 * nc(p - order).
+template <typename T>
+void m2l_weights(const MultiIndex& mi, std::vector<T>& W, std::vector<int>& tile_k, std::vector<long long>& tile_w) {
+  const int p = mi.p, nc = mi.nc;
+  const int ncol = 8 * nc;
+  const int ntiles = (ncol + kNTile - 1) / kNTile;
+  tile_k.resize(ntiles);
+  tile_w.resize(ntiles);
+  long long off = 0;
+  for (int t = 0; t < ntiles; ++t) {
+    const int beta0 = (t * kNTile) / 8;
+    const int o = level_of_order(mi, beta0);
+    tile_k[t] = 8 * ncoef(p - o);
+    tile_w[t] = off;
+    off += 27LL * tile_k[t] * kNTile;
+  }
+  W.assign((size_t)off, T(0));
+  // unit offsets u in [-3,3]^3: Taylor coefficients of -1/|u + t|
+  std::vector<std::vector<double>> taylor(343);
+  for (int uz = -3; uz <= 3; ++uz)
+    for (int uy = -3; uy <= 3; ++uy)
+      for (int ux = -3; ux <= 3; ++ux) {
+        const int cheb = std::max(std::abs(ux), std::max(std::abs(uy), std::abs(uz)));
+        if (cheb < 2) continue;
+        const double u[3] = {(double)ux, (double)uy, (double)uz};
+        taylor_inv_r(u, mi, taylor[(uz + 3) * 49 + (uy + 3) * 7 + (ux + 3)]);
+      }
+  for (int t = 0; t < ntiles; ++t) {
+    const int K = tile_k[t];
+    for (int d = 0; d < 27; ++d) {
+      const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+      T* blk = W.data() + tile_w[t] + (long long)d * K * kNTile;
+      for (int j = 0; j < kNTile; ++j) {
+        const int n = t * kNTile + j;
+        const int be = n / 8, ct = n % 8;
+        if (be >= nc) continue;
+        const int ob = level_of_order(mi, be);
+        for (int k = 0; k < K; ++k) {
+          const int al = k / 8, cs = k % 8;
+          if (al >= nc) continue;
+          const int oa = level_of_order(mi, al);
+          if (oa + ob > p) continue;
+          int u[3];
+          for (int q = 0; q < 3; ++q) u[q] = ((ct >> q) & 1) - ((cs >> q) & 1) - 2 * D[q];
+          const int cheb = std::max(std::abs(u[0]), std::max(std::abs(u[1]), std::abs(u[2])));
+          if (cheb < 2) continue;  // near neighbours are handled one level down
+          const std::vector<double>& tb = taylor[(u[2] + 3) * 49 + (u[1] + 3) * 7 + (u[0] + 3)];
+          const int g = mi.index(mi.a[al] + mi.a[be], mi.b[al] + mi.b[be], mi.c[al] + mi.c[be]);
+          const double mult = binom(mi.a[al] + mi.a[be], mi.a[al]) * binom(mi.b[al] + mi.b[be], mi.b[al]) *
+                              binom(mi.c[al] + mi.c[be], mi.c[al]);
+          const double sgn = (oa & 1) ? -1.0 : 1.0;
+          blk[(long long)k * kNTile + j] = (T)(sgn * mult * (-tb[g]));
+        }
+      }
+    }
+  }
+}
+
+// Near-field matrices (eq. direct, cell units): W_d[s][t] = g(x_t - x_s) for
+// source cell s of neighbour leaf box d and target cell t.
+template <typename T>
+void near_weights(int b, std::vector<T>& W, std::vector<int>& tile_k, std::vector<long long>& tile_w) {
+  const int b3 = b * b * b;
+  const int ntiles = (b3 + kNTile - 1) / kNTile;
+  tile_k.assign(ntiles, b3);
+  tile_w.resize(ntiles);
+  for (int t = 0; t < ntiles; ++t) tile_w[t] = 27LL * b3 * kNTile * t;
+  W.assign((size_t)27 * b3 * kNTile * ntiles, T(0));
+  for (int t = 0; t < ntiles; ++t)
+    for (int d = 0; d < 27; ++d) {
+      const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+      T* blk = W.data() + tile_w[t] + (long long)d * b3 * kNTile;
+      for (int j = 0; j < kNTile; ++j) {
+        const int tc = t * kNTile + j;
+        if (tc >= b3) continue;
+        const int tp[3] = {tc % b, (tc / b) % b, tc / (b * b)};
+        for (int s = 0; s < b3; ++s) {
+          const int sp[3] = {s % b, (s / b) % b, s / (b * b)};
+          double r2 = 0.0;
+          for (int q = 0; q < 3; ++q) {
+            const double r = (double)(tp[q] - sp[q] - b * D[q]);
+            r2 += r * r;
+          }
+          blk[(long long)s * kNTile + j] = (T)(r2 == 0.0 ? -1.0 : -1.0 / std::sqrt(r2));
+        }
+      }
+    }
+}
+
+// M2M: Mt_alpha(P) += C(alpha,beta) 2^-|alpha| (+-1/2)^(alpha-beta) Mt_beta(C);
+// L2L: Lt_beta(C) += C(gamma,beta) 2^(-1-|gamma|) (+-1/2)^(gamma-beta) Lt_gamma(P).
+void shift_tables(const MultiIndex& mi, std::vector<int>& m2m_start, std::vector<ShiftEntry>& m2m,
+                  std::vector<int>& l2l_start, std::vector<ShiftEntry>& l2l) {
+  const int nc = mi.nc;
+  m2m_start.assign(nc + 1, 0);
+  l2l_start.assign(nc + 1, 0);
+  m2m.clear();
+  l2l.clear();
+  for (int o = 0; o < nc; ++o) {
+    m2m_start[o] = (int)m2m.size();
+    for (int i = 0; i < nc; ++i) {
+      const int d[3] = {mi.a[o] - mi.a[i], mi.b[o] - mi.b[i], mi.c[o] - mi.c[i]};
+      if (d[0] < 0 || d[1] < 0 || d[2] < 0) continue;
+      const int no = mi.a[o] + mi.b[o] + mi.c[o], nd = d[0] + d[1] + d[2];
+      ShiftEntry e;
+      e.src = i;
+      e.mask = (d[0] & 1) | ((d[1] & 1) << 1) | ((d[2] & 1) << 2);
+      e.coef = binom(mi.a[o], mi.a[i]) * binom(mi.b[o], mi.b[i]) * binom(mi.c[o], mi.c[i]) * std::ldexp(1.0, -no - nd);
+      m2m.push_back(e);
+    }
+    l2l_start[o] = (int)l2l.size();
+    for (int g = 0; g < nc; ++g) {
+      const int d[3] = {mi.a[g] - mi.a[o], mi.b[g] - mi.b[o], mi.c[g] - mi.c[o]};
+      if (d[0] < 0 || d[1] < 0 || d[2] < 0) continue;
+      const int ng = mi.a[g] + mi.b[g] + mi.c[g], nd = d[0] + d[1] + d[2];
+      ShiftEntry e;
+      e.src = g;
+      e.mask = (d[0] & 1) | ((d[1] & 1) << 1) | ((d[2] & 1) << 2);
+      e.coef = binom(mi.a[g], mi.a[o]) * binom(mi.b[g], mi.b[o]) * binom(mi.c[g], mi.c[o]) *
+               std::ldexp(1.0, -1 - ng - nd);
+      l2l.push_back(e);
+    }
+  }
+  m2m_start[nc] = (int)m2m.size();
+  l2l_start[nc] = (int)l2l.size();
+}
+
+bool tc_precision(int prec) { return prec == FMM_M2L_TF32 || prec == FMM_M2L_BF16X3; }
+
+}  // namespace
+
+extern "C" {
+
+void fmm_default_opts(fmm_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = FMM_FP32;
+  o->n_fp64_levels = 3;
+  o->accel = 1;
+}
+
+const char* fmm_last_error(void) { return g_last_error.c_str(); }
+
+fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* opts, void* stream, fmm_plan_t* out) {
+  g_last_error.clear();
+  if (!out) return fail(FMM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grid) return fail(FMM_ERR_ARG, "grid is NULL");
+  if (order < 0 || order > kMaxOrder) return fail(FMM_ERR_ARG, "order %d outside [0, %d]", order, kMaxOrder);
+  if (leaf != 2 && leaf != 4 && leaf != 8) return fail(FMM_ERR_ARG, "leaf %d not in {2, 4, 8}", leaf);
+  const int d3[3] = {grid->nx, grid->ny, grid->nz};
+  for (int q = 0; q < 3; ++q) {
+    if (d3[q] <= 0) return fail(FMM_ERR_ARG, "grid extent %d must be positive", d3[q]);
+    if (d3[q] % leaf) return fail(FMM_ERR_ARG, "grid extent %d is not a multiple of leaf %d", d3[q], leaf);
+    if (d3[q] > (1 << 14)) return fail(FMM_ERR_ARG, "grid extent %d too large", d3[q]);
+  }
+  if (!(grid->dx > 0.0) || !std::isfinite(grid->dx)) return fail(FMM_ERR_ARG, "dx must be positive and finite");
+  if (!std::isfinite(grid->G)) return fail(FMM_ERR_ARG, "G must be finite");
+  fmm_opts o;
+  if (opts) {
+    o = *opts;
+  } else {
+    fmm_default_opts(&o);
+  }
+  if (o.precision < FMM_FP64 || o.precision > FMM_M2L_BF16X3) return fail(FMM_ERR_ARG, "unknown precision %d", o.precision);
+  if (o.n_fp64_levels < 0 || o.n_fp64_levels > kMaxLevels) return fail(FMM_ERR_ARG, "bad n_fp64_levels");
+  for (int r : o.reserved)
+    if (r != 0) return fail(FMM_ERR_ARG, "reserved option fields must be zero");
+  if (tc_precision(o.precision)) return fail(FMM_ERR_UNSUPPORTED, "tensor-core precisions are not built yet");
+
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+
+  fmm_plan_t P = new (std::nothrow) fmm_plan_s();
+  if (!P) return fail(FMM_ERR_ALLOC, "host allocation failed");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  P->last_stream = s;
+  for (int q = 0; q < 3; ++q) P->dims[q] = d3[q];
+  P->dx = grid->dx;
+  P->G = grid->G;
+  P->p = order;
+  P->b = leaf;
+  P->opts = o;
+  P->mi.init(order);
+  P->nc = P->mi.nc;
+
+  fmm_status st = build_levels(P);
+  if (st != FMM_OK) {
+    delete P;
+    return st;
+  }
+  // level precisions
+  for (int l = 0; l <= P->L; ++l) P->lev[l].f64 = P->f64_data() ? 1 : 0;
+  // arena
+  P->lmin = P->L >= 2 ? 2 : P->L;
+  size_t off = 0;
+  auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  for (int l = P->lmin; l <= P->L; ++l) {
+    Level& lv = P->lev[l];
+    lv.bytes = (size_t)lv.npar * 8 * P->nc * (lv.f64 ? 8 : 4);
+    lv.m_off = off;
+    off = align(off + lv.bytes);
+    lv.l_off = off;
+    off = align(off + lv.bytes);
+  }
+  const size_t cells_bytes = (size_t)P->ncell() * P->esize();
+  P->rho_box_off = off;
+  off = align(off + cells_bytes);
+  P->near_off = off;
+  off = align(off + cells_bytes);
+  P->work_off = off;
+  off = align(off + cells_bytes);
+  P->arena_bytes = off;
+
+  auto cleanup = [&](fmm_status e) {
+    P->release();
+    delete P;
+    return e;
+  };
+  void* arena = nullptr;
+  if (cudaMalloc(&arena, P->arena_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(fail(FMM_ERR_ALLOC, "cudaMalloc(%zu) for the workspace arena failed", P->arena_bytes));
+  }
+  P->allocs.push_back(arena);
+  P->dev_bytes += P->arena_bytes;
+  P->arena = static_cast<unsigned char*>(arena);
+  if (cudaMemsetAsync(arena, 0, P->arena_bytes, s) != cudaSuccess) return cleanup(fail(FMM_ERR_CUDA, "memset failed"));
+
+  // tables
+  std::vector<int8_t> mi8(3 * P->nc);
+  for (int k = 0; k < P->nc; ++k) {
+    mi8[3 * k] = (int8_t)P->mi.a[k];
+    mi8[3 * k + 1] = (int8_t)P->mi.b[k];
+    mi8[3 * k + 2] = (int8_t)P->mi.c[k];
+  }
+  std::vector<int> m2m_start, l2l_start;
+  std::vector<ShiftEntry> m2m, l2l;
+  shift_tables(P->mi, m2m_start, m2m, l2l_start, l2l);
+  std::vector<int> one_flag(1, 0);
+  if ((st = P->upload(mi8, &P->d_mi, s)) || (st = P->upload(m2m_start, &P->d_m2m_start, s)) ||
+      (st = P->upload(m2m, &P->d_m2m, s)) || (st = P->upload(l2l_start, &P->d_l2l_start, s)) ||
+      (st = P->upload(l2l, &P->d_l2l, s)) || (st = P->upload(one_flag, &P->d_flag, s)))
+    return cleanup(st);
+  {
+    std::vector<int> tk;
+    std::vector<long long> tw;
+    if (P->f64_data()) {
+      std::vector<double> W;
+      m2l_weights<double>(P->mi, W, tk, tw);
+      double* d = nullptr;
+      if ((st = P->upload(W, &d, s))) return cleanup(st);
+      P->d_w_m2l_f64 = d;
+    } else {
+      std::vector<float> W;
+      m2l_weights<float>(P->mi, W, tk, tw);
+      float* d = nullptr;
+      if ((st = P->upload(W, &d, s))) return cleanup(st);
+      P->d_w_m2l_f32 = d;
+    }
+    P->m2l_ntiles = (int)tk.size();
+    if ((st = P->upload(tk, &P->d_m2l_tile_k, s)) || (st = P->upload(tw, &P->d_m2l_tile_w, s))) return cleanup(st);
+  }
+  {
+    std::vector<int> tk;
+    std::vector<long long> tw;
+    if (P->f64_data()) {
+      std::vector<double> W;
+      near_weights<double>(P->b, W, tk, tw);
+      double* d = nullptr;
+      if ((st = P->upload(W, &d, s))) return cleanup(st);
+      P->d_w_near = d;
+    } else {
+      std::vector<float> W;
+      near_weights<float>(P->b, W, tk, tw);
+      float* d = nullptr;
+      if ((st = P->upload(W, &d, s))) return cleanup(st);
+      P->d_w_near = d;
+    }
+    P->near_ntiles = (int)tk.size();
+    if ((st = P->upload(tk, &P->d_near_tile_k, s)) || (st = P->upload(tw, &P->d_near_tile_w, s))) return cleanup(st);
+  }
+  // uploads read host vectors that go out of scope here
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cleanup(fail(FMM_ERR_CUDA, "table upload failed"));
+  *out = P;
+  return FMM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Records a pair of events around one stage when timing is enabled.
+struct StageTimer {
+  fmm_plan_t P;
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t b = nullptr;
+  StageTimer(fmm_plan_t P_, int stage_, cudaStream_t s_) : P(P_), stage(stage_), s(s_) {
+    if (P->timing && P->ev_used + 2 <= P->ev_pool.size()) {
+      cudaEvent_t a = P->ev_pool[P->ev_used++];
+      b = P->ev_pool[P->ev_used++];
+      cudaEventRecord(a, s);
+      P->recs.push_back({stage, a, b});
+    }
+  }
+  ~StageTimer() {
+    if (b) cudaEventRecord(b, s);
+  }
+};
+
+template <typename T>
+fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t s) {
+  const TreeTables tt = P->tables();
+  const int L = P->L;
+  T* rho_box = reinterpret_cast<T*>(P->arena + P->rho_box_off);
+  T* near_box = reinterpret_cast<T*>(P->arena + P->near_off);
+  {
+    StageTimer st(P, ST_CHECK, s);
+    CUDA_TRY(launch_check_finite<T>(rho, (size_t)P->ncell(), P->d_flag, s));
+  }
+  // upward pass
+  {
+    StageTimer st(P, ST_P2M, s);
+    CUDA_TRY(launch_p2m<T>(tt, rho, P->dims, P->lev[L], static_cast<T*>(P->M(L)), rho_box, s));
+  }
+  for (int l = L; l >= 3; --l) {
+    StageTimer st(P, ST_M2M, s);
+    CUDA_TRY((launch_m2m<T, T>(tt, P->lev[l], static_cast<const T*>(P->M(l)), P->lev[l - 1],
+                               static_cast<T*>(P->M(l - 1)), s)));
+  }
+  // downward pass
+  if (L < 2) {
+    StageTimer st(P, ST_L2L, s);
+    CUDA_TRY(launch_zero<T>(static_cast<T*>(P->Lx(L)), P->lev[L].bytes / sizeof(T), s));
+  }
+  for (int l = 2; l <= L; ++l) {
+    {
+      StageTimer st(P, ST_L2L, s);
+      if (l == 2) {
+        CUDA_TRY(launch_zero<T>(static_cast<T*>(P->Lx(l)), P->lev[l].bytes / sizeof(T), s));
+      } else {
+        CUDA_TRY((launch_l2l<T, T>(tt, P->lev[l - 1], static_cast<const T*>(P->Lx(l - 1)), P->lev[l],
+                                   static_cast<T*>(P->Lx(l)), s)));
+      }
+    }
+    NbrGemm g;
+    g.A = P->M(l);
+    g.row_len = 8 * P->nc;
+    for (int q = 0; q < 3; ++q) g.grid[q] = P->lev[l].np[q];
+    g.W = P->f64_data() ? P->d_w_m2l_f64 : P->d_w_m2l_f32;
+    g.tile_k = P->d_m2l_tile_k;
+    g.tile_w = P->d_m2l_tile_w;
+    g.C = P->Lx(l);
+    g.n_cols = 8 * P->nc;
+    g.ntiles = P->m2l_ntiles;
+    g.accumulate = 1;
+    StageTimer st(P, ST_M2L, s);
+    CUDA_TRY(launch_nbr_gemm_simt<T>(g, s));
+  }
+  // near field over the 27 neighbour leaf boxes
+  {
+    NbrGemm g;
+    g.A = rho_box;
+    g.row_len = P->b * P->b * P->b;
+    for (int q = 0; q < 3; ++q) g.grid[q] = P->lev[L].n[q];
+    g.W = P->d_w_near;
+    g.tile_k = P->d_near_tile_k;
+    g.tile_w = P->d_near_tile_w;
+    g.C = near_box;
+    g.n_cols = P->b * P->b * P->b;
+    g.ntiles = P->near_ntiles;
+    g.accumulate = 0;
+    StageTimer st(P, ST_NEAR, s);
+    CUDA_TRY(launch_nbr_gemm_simt<T>(g, s));
+  }
+  {
+    StageTimer st(P, ST_LEAF, s);
+    CUDA_TRY(launch_leaf_finish<T>(tt, P->lev[L], static_cast<const T*>(P->Lx(L)), near_box, P->dims,
+                                   P->G * P->dx * P->dx, phi, s));
+  }
+  if (accel) {
+    StageTimer st(P, ST_FD, s);
+    CUDA_TRY(launch_fd_accel<T>(phi, P->dims, 1.0 / P->dx, accel, s));
+  }
+  return FMM_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+fmm_status fmm_solve(fmm_plan_t P, const void* rho, void* phi, void* accel, void* stream) {
+  if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
+  if (!rho || !phi) return fail(FMM_ERR_ARG, "rho and phi must be non-NULL");
+  if (!aligned16(rho) || !aligned16(phi) || (accel && !aligned16(accel)))
+    return fail(FMM_ERR_ARG, "device pointers must be 16-byte aligned");
+  if (accel && !P->opts.accel) return fail(FMM_ERR_ARG, "plan was built with accel = 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  P->last_stream = s;
+  if (P->f64_data())
+    return run_solve<double>(P, static_cast<const double*>(rho), static_cast<double*>(phi),
+                             static_cast<double*>(accel), s);
+  return run_solve<float>(P, static_cast<const float*>(rho), static_cast<float*>(phi), static_cast<float*>(accel), s);
+}
+
+fmm_status fmm_solve_adjoint(fmm_plan_t P, const void* grad_phi, const void* grad_accel, void* grad_rho, void* stream) {
+  if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
+  if (!grad_rho || (!grad_phi && !grad_accel)) return fail(FMM_ERR_ARG, "grad_rho and one gradient must be non-NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  P->last_stream = s;
+  void* w = P->arena + P->work_off;
+  {
+    StageTimer st(P, ST_ADJ_SRC, s);
+    if (P->f64_data()) {
+      CUDA_TRY(launch_adjoint_source<double>(static_cast<const double*>(grad_phi),
+                                             static_cast<const double*>(grad_accel), P->dims, 1.0 / P->dx,
+                                             static_cast<double*>(w), s));
+    } else {
+      CUDA_TRY(launch_adjoint_source<float>(static_cast<const float*>(grad_phi),
+                                            static_cast<const float*>(grad_accel), P->dims, 1.0 / P->dx,
+                                            static_cast<float*>(w), s));
+    }
+  }
+  if (P->f64_data())
+    return run_solve<double>(P, static_cast<const double*>(w), static_cast<double*>(grad_rho), nullptr, s);
+  return run_solve<float>(P, static_cast<const float*>(w), static_cast<float*>(grad_rho), nullptr, s);
+}
+
+fmm_status fmm_solve_host(fmm_plan_t P, const void* rho_host, void* phi_host, void* accel_host, void* stream) {
+  if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
+  if (!rho_host || !phi_host) return fail(FMM_ERR_ARG, "rho and phi must be non-NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)P->ncell() * P->esize();
+  if (!P->d_io_rho) {
+    if (cudaMalloc(&P->d_io_rho, bytes) != cudaSuccess || cudaMalloc(&P->d_io_phi, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FMM_ERR_ALLOC, "staging allocation failed");
+    }
+  }
+  if (accel_host && !P->d_io_acc) {
+    if (cudaMalloc(&P->d_io_acc, 3 * bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FMM_ERR_ALLOC, "staging allocation failed");
+    }
+  }
+  CUDA_TRY(cudaMemcpyAsync(P->d_io_rho, rho_host, bytes, cudaMemcpyHostToDevice, s));
+  fmm_status st = fmm_solve(P, P->d_io_rho, P->d_io_phi, accel_host ? P->d_io_acc : nullptr, stream);
+  if (st != FMM_OK) return st;
+  CUDA_TRY(cudaMemcpyAsync(phi_host, P->d_io_phi, bytes, cudaMemcpyDeviceToHost, s));
+  if (accel_host) CUDA_TRY(cudaMemcpyAsync(accel_host, P->d_io_acc, 3 * bytes, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return FMM_OK;
+}
+
+fmm_status fmm_check(fmm_plan_t P) {
+  if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
+  CUDA_TRY(cudaStreamSynchronize(P->last_stream));
+  int flag = 0;
+  CUDA_TRY(cudaMemcpy(&flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    CUDA_TRY(cudaMemset(P->d_flag, 0, sizeof(int)));
+    if (flag & 1) return fail(FMM_ERR_NONFINITE, "the density held a NaN or Inf");
+    return fail(FMM_ERR_TIMEOUT, "a device wait reached its iteration limit");
+  }
+  return FMM_OK;
+}
+
+size_t fmm_workspace_bytes(fmm_plan_t P) { return P ? P->dev_bytes : 0; }
+
+int fmm_plan_leaf_level(fmm_plan_t P) { return P ? P->L : -1; }
+
+int fmm_solve_launches(fmm_plan_t P, int with_accel) {
+  if (!P) return -1;
+  const int L = P->L;
+  int n = 2;                            // finite check + P2M
+  n += std::max(0, L - 2);              // M2M for l = L .. 3
+  if (L < 2) n += 1;                    // zero the leaf locals
+  for (int l = 2; l <= L; ++l) n += 2;  // L2L (or zero) + M2L
+  n += 2;                               // near field + leaf finish
+  if (with_accel) n += 1;
+  return n;
+}
+
+fmm_status fmm_timing_enable(fmm_plan_t P, int enable) {
+  if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
+  if (enable && P->ev_pool.empty()) {
+    P->ev_pool.resize(kEventPool);
+    for (auto& e : P->ev_pool) CUDA_TRY(cudaEventCreate(&e));
+  }
+  CUDA_TRY(cudaDeviceSynchronize());
+  P->recs.clear();
+  P->ev_used = 0;
+  P->timing = enable != 0;
+  return FMM_OK;
+}
+
+fmm_status fmm_timing_read(fmm_plan_t P, double* ms, int* launches, int nstages) {
+  if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
+  if (!ms || !launches || nstages <= 0) return fail(FMM_ERR_ARG, "bad output arrays");
+  CUDA_TRY(cudaDeviceSynchronize());
+  for (int i = 0; i < nstages; ++i) ms[i] = 0.0, launches[i] = 0;
+  for (const auto& r : P->recs) {
+    float t = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
+    if (r.stage < nstages) {
+      ms[r.stage] += t;
+      launches[r.stage] += 1;
+    }
+  }
+  P->recs.clear();
+  P->ev_used = 0;
+  return FMM_OK;
+}
+
+int fmm_timing_stage_count(void) { return ST_COUNT; }
+
+const char* fmm_timing_stage_name(int stage) {
+  return (stage >= 0 && stage < ST_COUNT) ? kStageNames[stage] : "";
+}
+
+fmm_status fmm_plan_destroy(fmm_plan_t P) {
+  if (!P) return FMM_OK;
+  P->release();
+  delete P;
+  return FMM_OK;
+}
+
+fmm_status fmm_debug_level(fmm_plan_t P, int what, int level, double* host_out, size_t host_count) {
+  if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
+  if (what != 0 && what != 1) return fail(FMM_ERR_ARG, "what must be 0 or 1");
+  if (level < P->lmin || level > P->L) return fail(FMM_ERR_ARG, "level %d not stored", level);
+  const Level& lv = P->lev[level];
+  const size_t count = (size_t)lv.nbox * P->nc;
+  if (!host_out || host_count < count) return fail(FMM_ERR_ARG, "host buffer too small (%zu needed)", count);
+  double* tmp = nullptr;
+  CUDA_TRY(cudaMalloc(&tmp, count * sizeof(double)));
+  const double h = (double)P->b * (double)(1LL << (P->L - level));
+  const void* src = what == 0 ? P->M(level) : P->Lx(level);
+  cudaError_t e = lv.f64 ? launch_export_level<double>(static_cast<const double*>(src), lv, what, h, P->d_mi, P->nc,
+                                                       tmp, nullptr)
+                         : launch_export_level<float>(static_cast<const float*>(src), lv, what, h, P->d_mi, P->nc, tmp,
+                                                      nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(host_out, tmp, count * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return fail(FMM_ERR_CUDA, "debug export failed: %s", cudaGetErrorString(e));
+  return FMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// Internal declarations of the GB300 FMM library: plan layout, level arena,
+// device tables and the kernel launchers shared between translation units.
+//
+// Data layout in HBM (one arena per plan):
+//  * Level l (2 <= l <= L) expansions are stored "parent-blocked": for each
+//    box of the parent grid (level l-1, x fastest), the 8 children's
+//    coefficients as [coef][child] with child = cx + 2 cy + 4 cz fastest.
+//    A parent block is 8*nc contiguous values, so every neighbour-block read
+//    of the M2L contraction is a contiguous row, and an order prefix
+//    (coefficients of order <= k) is a contiguous prefix of the row.
+//  * Children past the level's extent ("phantom" boxes of the round-up
+//    hierarchy) hold zeros: the arena is cleared once at plan time and those
+//    slots are never written.
+//  * Scaled variables: at a level of box side h (cells),
+//      Mt_alpha = M_alpha / h^|alpha|,   Lt_beta = h^(1+|beta|) L_beta / beta!
+//    so the M2L translation operator is the same for every level, the
+//    M2M/L2L shifts are pure numbers, and values stay O(mass).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/fmm.h"
+
+namespace fmmgb {
+
+constexpr int kMaxOrder = 8;
+constexpr int kMaxCoef = 165;  // C(8+3, 3)
+constexpr int kMaxLevels = 24;
+constexpr int kNTile = 32;     // output columns per SIMT GEMM tile
+constexpr int kKChunk = 32;    // reduction values per SIMT GEMM stage
+
+// Pair lists of the M2M / L2L shifts.  Entry: coefficient index `src`,
+// magnitude `coef`, and `mask`: bit q set when the shift exponent along
+// axis q is odd (its sign then depends on which side of the parent the
+// child sits).
+struct ShiftEntry {
+  double coef;
+  int src;
+  int mask;
+};
+
+struct Level {
+  int n[3];        // boxes per axis at this level
+  int np[3];       // boxes per axis of the parent grid (level l-1)
+  long long nbox;
+  long long npar;  // product of np
+  int f64;         // expansions of this level kept in FP64
+  size_t m_off;    // byte offset of the multipoles in the arena
+  size_t l_off;    // byte offset of the local expansions in the arena
+  size_t bytes;    // bytes of one of the two arrays
+};
+
+// Neighbour-contraction ("implicit GEMM") description for the SIMT kernel:
+//   C[row][n] (+)= sum_{d in 27 neighbours} sum_{k < K(tile(n))} A[row + d][k] * W_d[k][n]
+// rows live on a 3-D grid; a neighbour outside the grid contributes zero.
+struct NbrGemm {
+  const void* A;       // [rows][row_len]
+  int row_len;
+  int grid[3];         // row grid extents
+  const void* W;       // weights, see plan.cu (tile-major, then neighbour)
+  const int* tile_k;   // device [ntiles]: reduction length of each column tile
+  const long long* tile_w;  // device [ntiles]: offset of the tile's neighbour-0 block
+  void* C;             // [rows][n_cols]
+  int n_cols;
+  int ntiles;
+  int accumulate;      // 1: C += result, 0: C = result
+};
+
+template <typename T>
+cudaError_t launch_nbr_gemm_simt(const NbrGemm& g, cudaStream_t s);
+
+// Upward pass.
+struct TreeTables {
+  const int8_t* mi;          // [nc][3] multi-indices (canonical order)
+  const int* m2m_start;      // [nc+1] CSR over output alpha
+  const ShiftEntry* m2m;     // entries (src = beta)
+  const int* l2l_start;      // [nc+1] CSR over output beta
+  const ShiftEntry* l2l;     // entries (src = gamma)
+  int p, nc, b;
+};
+
+template <typename T>
+cudaError_t launch_p2m(const TreeTables& t, const T* rho, const int dims[3], const Level& leaf, T* Mleaf, T* rho_box,
+                       cudaStream_t s);
+template <typename Tc, typename Tp>
+cudaError_t launch_m2m(const TreeTables& t, const Level& child, const Tc* Mc, const Level& par, Tp* Mp, cudaStream_t s);
+template <typename Tp, typename Tc>
+cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, const Level& child, Tc* Lc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_zero(T* p, size_t count, cudaStream_t s);
+template <typename T>
+cudaError_t launch_leaf_finish(const TreeTables& t, const Level& leaf, const T* Lleaf, const T* near_box,
+                               const int dims[3], double scale, T* phi, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fd_accel(const T* phi, const int dims[3], double inv_dx, T* accel, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adjoint_source(const T* gphi, const T* gaccel, const int dims[3], double inv_dx, T* out,
+                                  cudaStream_t s);
+template <typename T>
+cudaError_t launch_check_finite(const T* x, size_t count, int* flag, cudaStream_t s);
+// Level copy into the canonical [box][coef] double layout with the
+// scaling undone (debug export).
+template <typename T>
+cudaError_t launch_export_level(const T* src, const Level& lv, int what, double h, const int8_t* mi, int nc,
+                                double* dst, cudaStream_t s);
+
+}  // namespace fmmgb

@@ -1,0 +1,130 @@
+// Force by finite differences (App. C): a = -grad(phi) with the 4th-order
+// 5-point central stencil, 2nd-order central one cell from an edge and
+// 2nd-order one-sided at an edge; and the transpose of that map for the
+// adjoint solve.  HBM-bound: one thread per cell, x fastest, so every
+// stencil read along x is coalesced and the y/z reads hit L2.
+#include "fmm_internal.h"
+
+namespace fmmgb {
+namespace {
+
+// Weight of f[j + off] in the cell-unit derivative at index j of a line of n.
+__device__ __forceinline__ double fd_weight(int j, int off, int n) {
+  if (n <= 1) return 0.0;
+  if (n == 2) {  // f[1] - f[0] at both points
+    const int m = j + off;
+    return m == 1 ? 1.0 : (m == 0 ? -1.0 : 0.0);
+  }
+  if (j >= 2 && j <= n - 3) {
+    switch (off) {
+      case 2: return -1.0 / 12.0;
+      case 1: return 8.0 / 12.0;
+      case -1: return -8.0 / 12.0;
+      case -2: return 1.0 / 12.0;
+      default: return 0.0;
+    }
+  }
+  if (j >= 1 && j <= n - 2) return off == 1 ? 0.5 : (off == -1 ? -0.5 : 0.0);
+  if (j == 0) return off == 0 ? -1.5 : (off == 1 ? 2.0 : (off == 2 ? -0.5 : 0.0));
+  return off == 0 ? 1.5 : (off == -1 ? -2.0 : (off == -2 ? 0.5 : 0.0));  // j == n-1
+}
+
+template <typename T>
+__global__ void fd_accel_kernel(const T* __restrict__ phi, int nx, int ny, int nz, T inv_dx, T* __restrict__ accel) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+    const int pos[3] = {x, y, z};
+    const int len[3] = {nx, ny, nz};
+    const long long stride[3] = {1, nx, (long long)nx * ny};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      T d = T(0);
+#pragma unroll
+      for (int off = -2; off <= 2; ++off) {
+        const int m = pos[q] + off;
+        if (m < 0 || m >= len[q]) continue;
+        const double w = fd_weight(pos[q], off, len[q]);
+        if (w != 0.0) d = fma(T(w), phi[c + off * stride[q]], d);
+      }
+      accel[q * n + c] = -d * inv_dx;
+    }
+  }
+}
+
+// w = gphi - inv_dx * FD^T(gaccel) (gather form of the transpose): the
+// adjoint source of the loss through accel = -inv_dx FD phi.
+template <typename T>
+__global__ void adjoint_source_kernel(const T* __restrict__ gphi, const T* __restrict__ gacc, int nx, int ny, int nz,
+                                      T inv_dx, T* __restrict__ out) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    T v = gphi ? gphi[c] : T(0);
+    if (gacc) {
+      const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+      const int pos[3] = {x, y, z};
+      const int len[3] = {nx, ny, nz};
+      const long long stride[3] = {1, nx, (long long)nx * ny};
+      T t = T(0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+#pragma unroll
+        for (int off = -2; off <= 2; ++off) {
+          const int j = pos[q] + off;  // stencil centre whose derivative reads this cell
+          if (j < 0 || j >= len[q]) continue;
+          const double w = fd_weight(j, -off, len[q]);
+          if (w != 0.0) t = fma(T(w), gacc[q * n + c + off * stride[q]], t);
+        }
+      }
+      v = fma(-inv_dx, t, v);
+    }
+    out[c] = v;
+  }
+}
+
+template <typename T>
+__global__ void check_finite_kernel(const T* __restrict__ x, size_t n, int* flag) {
+  int bad = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite((double)x[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+unsigned blocks_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 16) b = 152LL * 16;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_fd_accel(const T* phi, const int dims[3], double inv_dx, T* accel, cudaStream_t s) {
+  const long long n = (long long)dims[0] * dims[1] * dims[2];
+  fd_accel_kernel<T><<<blocks_for(n), 256, 0, s>>>(phi, dims[0], dims[1], dims[2], (T)inv_dx, accel);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adjoint_source(const T* gphi, const T* gaccel, const int dims[3], double inv_dx, T* out,
+                                  cudaStream_t s) {
+  const long long n = (long long)dims[0] * dims[1] * dims[2];
+  adjoint_source_kernel<T><<<blocks_for(n), 256, 0, s>>>(gphi, gaccel, dims[0], dims[1], dims[2], (T)inv_dx, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_check_finite(const T* x, size_t count, int* flag, cudaStream_t s) {
+  check_finite_kernel<T><<<blocks_for((long long)count), 256, 0, s>>>(x, count, flag);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_fd_accel<float>(const float*, const int*, double, float*, cudaStream_t);
+template cudaError_t launch_fd_accel<double>(const double*, const int*, double, double*, cudaStream_t);
+template cudaError_t launch_adjoint_source<float>(const float*, const float*, const int*, double, float*, cudaStream_t);
+template cudaError_t launch_adjoint_source<double>(const double*, const double*, const int*, double, double*,
+                                                   cudaStream_t);
+template cudaError_t launch_check_finite<float>(const float*, size_t, int*, cudaStream_t);
+template cudaError_t launch_check_finite<double>(const double*, size_t, int*, cudaStream_t);
+
+}  // namespace fmmgb

@@ -1,0 +1,116 @@
+// Neighbour contraction on the CUDA cores (FP32 / FP64).
+//
+// Both translation-invariant steps of the solve are the same contraction over
+// a 3-D grid of "rows" and their 27 neighbours:
+//
+//   C[r][n] (+)= sum_{d in {-1,0,1}^3} sum_{k < K(n)} A[r + d][k] * W_d[k][n]
+//
+//  * M2L (Sec. 2.3, eq. M2L) at level l: a row is a parent box of level l-1,
+//    A[r] its children's scaled multipoles [coef][child], n = (beta, target
+//    child) and W_d the unit-box translation operator restricted to the
+//    interaction list (Sec. 2.2: source children at Chebyshev distance >= 2
+//    from the target child).  Ordering coefficients by total order makes
+//    the truncation |alpha| + |beta| <= p a prefix K(n) of the reduction.
+//  * P2P (Sec. 2.3, eq. direct): a row is a leaf box, A[r] its b^3 cell
+//    masses and W_d[s][t] = g(x_t - x_s) for the neighbour box d.
+//
+// A neighbour outside the grid contributes zero: that is the isolated
+// boundary.  Tile: 64 rows (a 4x4x4 block of the row grid) x 32 columns,
+// 64 threads, each thread an 8x4 register tile.
+#include "fmm_internal.h"
+
+namespace fmmgb {
+namespace {
+
+constexpr int kRows = 64;
+constexpr int kPad = 1;
+
+template <typename T>
+__global__ void __launch_bounds__(64) nbr_gemm_simt_kernel(NbrGemm g) {
+  __shared__ T As[kKChunk][kRows + kPad];
+  __shared__ T Bs[kKChunk][kNTile];
+  const int tile = blockIdx.y;
+  const int tx = threadIdx.x;
+  const int rg = tx & 7;   // rows rg*8 .. rg*8+7
+  const int cg = tx >> 3;  // cols cg*4 .. cg*4+3
+  const int ntx = (g.grid[0] + 3) >> 2, nty = (g.grid[1] + 3) >> 2;
+  const int bt = blockIdx.x;
+  const int ox = (bt % ntx) * 4, oy = ((bt / ntx) % nty) * 4, oz = (bt / (ntx * nty)) * 4;
+  const int K = g.tile_k[tile];
+  const T* W0 = static_cast<const T*>(g.W) + g.tile_w[tile];
+  const T* A = static_cast<const T*>(g.A);
+
+  T acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+
+  for (int d = 0; d < 27; ++d) {
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    const T* Wd = W0 + (long long)d * K * kNTile;
+    for (int kc = 0; kc < K; kc += kKChunk) {
+      const int kn = min(kKChunk, K - kc);
+      for (int e = tx; e < kRows * kKChunk; e += 64) {
+        const int r = e / kKChunk, k = e % kKChunk;
+        T v = T(0);
+        if (k < kn) {
+          const int x = ox + (r & 3) + dx, y = oy + ((r >> 2) & 3) + dy, z = oz + (r >> 4) + dz;
+          if (x >= 0 && y >= 0 && z >= 0 && x < g.grid[0] && y < g.grid[1] && z < g.grid[2])
+            v = A[(((long long)z * g.grid[1] + y) * g.grid[0] + x) * g.row_len + kc + k];
+        }
+        As[k][r] = v;
+      }
+      for (int e = tx; e < kKChunk * kNTile; e += 64) {
+        const int k = e / kNTile, n = e % kNTile;
+        Bs[k][n] = (k < kn) ? Wd[(long long)(kc + k) * kNTile + n] : T(0);
+      }
+      __syncthreads();
+      for (int k = 0; k < kn; ++k) {
+        T a[8], b[4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = As[k][rg * 8 + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[k][cg * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+
+  T* C = static_cast<T*>(g.C);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = rg * 8 + i;
+    const int x = ox + (r & 3), y = oy + ((r >> 2) & 3), z = oz + (r >> 4);
+    if (x >= g.grid[0] || y >= g.grid[1] || z >= g.grid[2]) continue;
+    const long long row = ((long long)z * g.grid[1] + y) * g.grid[0] + x;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = tile * kNTile + cg * 4 + j;
+      if (n >= g.n_cols) continue;
+      T* dst = C + row * g.n_cols + n;
+      *dst = g.accumulate ? (*dst + acc[i][j]) : acc[i][j];
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_nbr_gemm_simt(const NbrGemm& g, cudaStream_t s) {
+  const long long tiles = (long long)((g.grid[0] + 3) / 4) * ((g.grid[1] + 3) / 4) * ((g.grid[2] + 3) / 4);
+  if (tiles <= 0 || g.ntiles <= 0) return cudaSuccess;
+  if (tiles > 0x7fffffffLL || g.ntiles > 65535) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)tiles, (unsigned)g.ntiles);
+  nbr_gemm_simt_kernel<T><<<grid, 64, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_nbr_gemm_simt<float>(const NbrGemm&, cudaStream_t);
+template cudaError_t launch_nbr_gemm_simt<double>(const NbrGemm&, cudaStream_t);
+
+}  // namespace fmmgb
