@@ -18,7 +18,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libfmm_gb300.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
 
-SOURCES = ["capi.cu", "k_tree.cu", "k_gemm_simt.cu", "k_fd.cu"]
+SOURCES = ["capi.cu", "k_tree.cu", "k_gemm_simt.cu", "k_fd.cu", "k_m2l_tc.cu"]
 HEADERS = ["fmm_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

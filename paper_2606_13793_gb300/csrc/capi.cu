@@ -102,9 +102,22 @@ int level_of_order(const MultiIndex& mi, int k) { return mi.a[k] + mi.b[k] + mi.
 
 int ncoef(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 
-enum Stage { ST_CHECK = 0, ST_P2M, ST_M2M, ST_L2L, ST_M2L, ST_NEAR, ST_LEAF, ST_FD, ST_ADJ_SRC, ST_COUNT };
-const char* kStageNames[ST_COUNT] = {"finite_check", "p2m", "m2m", "l2l", "m2l", "near_field", "leaf_l2p",
-                                     "fd_accel", "adjoint_source"};
+enum Stage {
+  ST_CHECK = 0,
+  ST_P2M,
+  ST_M2M,
+  ST_L2L,
+  ST_M2L,
+  ST_NEAR,
+  ST_LEAF,
+  ST_FD,
+  ST_ADJ_SRC,
+  ST_SPLIT,
+  ST_M2L_TC,
+  ST_COUNT
+};
+const char* kStageNames[ST_COUNT] = {"finite_check", "p2m",          "m2m",         "l2l",       "m2l", "near_field",
+                                     "leaf_l2p",     "fd_accel",     "adjoint_source", "split_bf16", "m2l_tc"};
 constexpr int kEventPool = 8192;
 
 }  // namespace
@@ -142,6 +155,11 @@ struct fmm_plan_s {
   int* d_near_tile_k = nullptr;
   long long* d_near_tile_w = nullptr;
   int near_ntiles = 0;
+  // tensor-core M2L
+  int tc_kind = -1;
+  TcLaunch tc{};
+  alignas(64) unsigned char map_hi[kMaxLevels][128];
+  alignas(64) unsigned char map_lo[kMaxLevels][128];
   // host-buffer staging for fmm_solve_host
   void* d_io_rho = nullptr;
   void* d_io_phi = nullptr;
@@ -223,11 +241,53 @@ fmm_status build_levels(fmm_plan_t P) {
   return FMM_OK;
 }
 
-// Column tiles of the neighbour contraction for M2L: output column
-// n = beta*8 + child; tile t covers beta in [4t, 4t+4) whose lowest order
-// fixes the reduction prefix 8 * nc(p - order).
+// Taylor coefficients of 1/|u + t| at every unit offset u in [-3,3]^3 that
+// the interaction list reaches (Chebyshev distance >= 2).
+struct TaylorTable {
+  std::vector<std::vector<double>> t = std::vector<std::vector<double>>(343);
+  void build(const MultiIndex& mi) {
+    for (int uz = -3; uz <= 3; ++uz)
+      for (int uy = -3; uy <= 3; ++uy)
+        for (int ux = -3; ux <= 3; ++ux) {
+          const int cheb = std::max(std::abs(ux), std::max(std::abs(uy), std::abs(uz)));
+          if (cheb < 2) continue;
+          const double u[3] = {(double)ux, (double)uy, (double)uz};
+          taylor_inv_r(u, mi, t[(uz + 3) * 49 + (uy + 3) * 7 + (ux + 3)]);
+        }
+  }
+  const std::vector<double>& at(const int u[3]) const { return t[(u[2] + 3) * 49 + (u[1] + 3) * 7 + (u[0] + 3)]; }
+};
+
+// One entry of the unit-box M2L contraction: neighbour parent d (0..26),
+// reduction index k = alpha*8 + source child, output n = beta*8 + target child.
+//   W = (-1)^|alpha| C(alpha+beta, alpha) (-b_{alpha+beta}(u)),
+//   u = c_target - c_source in child-box units = ct - cs - 2 d,
+// zero outside the interaction list (Chebyshev(u) < 2) or past the
+// truncation |alpha| + |beta| > p.
+double m2l_entry(const MultiIndex& mi, const TaylorTable& tt, int d, int k, int n) {
+  const int nc = mi.nc, p = mi.p;
+  const int be = n / 8, ct = n % 8, al = k / 8, cs = k % 8;
+  if (be >= nc || al >= nc) return 0.0;
+  const int ob = level_of_order(mi, be), oa = level_of_order(mi, al);
+  if (oa + ob > p) return 0.0;
+  const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+  int u[3];
+  for (int q = 0; q < 3; ++q) u[q] = ((ct >> q) & 1) - ((cs >> q) & 1) - 2 * D[q];
+  const int cheb = std::max(std::abs(u[0]), std::max(std::abs(u[1]), std::abs(u[2])));
+  if (cheb < 2) return 0.0;  // near neighbours are handled one level down
+  const std::vector<double>& tb = tt.at(u);
+  const int g = mi.index(mi.a[al] + mi.a[be], mi.b[al] + mi.b[be], mi.c[al] + mi.c[be]);
+  const double mult = binom(mi.a[al] + mi.a[be], mi.a[al]) * binom(mi.b[al] + mi.b[be], mi.b[al]) *
+                      binom(mi.c[al] + mi.c[be], mi.c[al]);
+  return ((oa & 1) ? -1.0 : 1.0) * mult * (-tb[g]);
+}
+
+// Column tiles of the neighbour contraction for M2L on the CUDA cores:
+// output column n = beta*8 + child; tile t covers beta in [4t, 4t+4) whose
+// lowest order fixes the reduction prefix 8 * nc(p - order).
 template <typename T>
-void m2l_weights(const MultiIndex& mi, std::vector<T>& W, std::vector<int>& tile_k, std::vector<long long>& tile_w) {
+void m2l_weights(const MultiIndex& mi, const TaylorTable& tt, std::vector<T>& W, std::vector<int>& tile_k,
+                 std::vector<long long>& tile_w) {
   const int p = mi.p, nc = mi.nc;
   const int ncol = 8 * nc;
   const int ntiles = (ncol + kNTile - 1) / kNTile;
@@ -242,45 +302,141 @@ void m2l_weights(const MultiIndex& mi, std::vector<T>& W, std::vector<int>& tile
     off += 27LL * tile_k[t] * kNTile;
   }
   W.assign((size_t)off, T(0));
-  // unit offsets u in [-3,3]^3: Taylor coefficients of -1/|u + t|
-  std::vector<std::vector<double>> taylor(343);
-  for (int uz = -3; uz <= 3; ++uz)
-    for (int uy = -3; uy <= 3; ++uy)
-      for (int ux = -3; ux <= 3; ++ux) {
-        const int cheb = std::max(std::abs(ux), std::max(std::abs(uy), std::abs(uz)));
-        if (cheb < 2) continue;
-        const double u[3] = {(double)ux, (double)uy, (double)uz};
-        taylor_inv_r(u, mi, taylor[(uz + 3) * 49 + (uy + 3) * 7 + (ux + 3)]);
-      }
   for (int t = 0; t < ntiles; ++t) {
     const int K = tile_k[t];
     for (int d = 0; d < 27; ++d) {
-      const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
       T* blk = W.data() + tile_w[t] + (long long)d * K * kNTile;
-      for (int j = 0; j < kNTile; ++j) {
-        const int n = t * kNTile + j;
-        const int be = n / 8, ct = n % 8;
-        if (be >= nc) continue;
-        const int ob = level_of_order(mi, be);
-        for (int k = 0; k < K; ++k) {
-          const int al = k / 8, cs = k % 8;
-          if (al >= nc) continue;
-          const int oa = level_of_order(mi, al);
-          if (oa + ob > p) continue;
-          int u[3];
-          for (int q = 0; q < 3; ++q) u[q] = ((ct >> q) & 1) - ((cs >> q) & 1) - 2 * D[q];
-          const int cheb = std::max(std::abs(u[0]), std::max(std::abs(u[1]), std::abs(u[2])));
-          if (cheb < 2) continue;  // near neighbours are handled one level down
-          const std::vector<double>& tb = taylor[(u[2] + 3) * 49 + (u[1] + 3) * 7 + (u[0] + 3)];
-          const int g = mi.index(mi.a[al] + mi.a[be], mi.b[al] + mi.b[be], mi.c[al] + mi.c[be]);
-          const double mult = binom(mi.a[al] + mi.a[be], mi.a[al]) * binom(mi.b[al] + mi.b[be], mi.b[al]) *
-                              binom(mi.c[al] + mi.c[be], mi.c[al]);
-          const double sgn = (oa & 1) ? -1.0 : 1.0;
-          blk[(long long)k * kNTile + j] = (T)(sgn * mult * (-tb[g]));
-        }
-      }
+      for (int k = 0; k < K; ++k)
+        for (int j = 0; j < kNTile; ++j) blk[(long long)k * kNTile + j] = (T)m2l_entry(mi, tt, d, k, t * kNTile + j);
     }
   }
+}
+
+uint16_t bf16_rn(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+float bf16_to_f(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+float tf32_rn(double w) {
+  float f = (float)w;
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0xFFFu + ((u >> 13) & 1u);
+  u &= ~0x1FFFu;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// Tensor-core schedule: column groups (order blocks, orders 0 and 1 merged,
+// split into <= 128-column pieces), passes of <= 512 TMEM columns, and for
+// every (neighbour, 128-byte reduction chunk) the weight tiles of the groups
+// whose prefix reaches that chunk.  Weight tiles are written in the exact
+// shared-memory image the MMA reads: rows of 128 B, 16-byte chunks swizzled
+// by (row mod 8), bf16 hi plane then lo plane (or one TF32 plane).
+struct TcHost {
+  std::vector<TcGroup> groups;
+  std::vector<TcIter> iters;
+  std::vector<TcStep> steps;
+  TcPass pass[kTcMaxPasses];
+  int npass = 0;
+  std::vector<unsigned char> W;
+};
+
+bool build_tc(const MultiIndex& mi, const TaylorTable& tt, int kind, TcHost& H) {
+  const int p = mi.p;
+  const int chunk = kind == TC_BF16X3 ? 64 : 32;  // reduction values per 128-byte chunk
+  const int kstep = chunk / 4;
+  const int esz = kind == TC_BF16X3 ? 2 : 4;
+  const int planes = kind == TC_BF16X3 ? 2 : 1;
+  struct G {
+    int col0, ncols, K;
+  };
+  std::vector<G> gs;
+  for (int m = 0; m <= p;) {
+    const int o_hi = (m == 0 && p >= 1) ? 1 : m;
+    const int col0 = m == 0 ? 0 : 8 * ncoef(m - 1), col1 = 8 * ncoef(o_hi);
+    const int K = 8 * ncoef(p - m);
+    const int total = col1 - col0;
+    const int pieces = (total + kTcMaxGroupN - 1) / kTcMaxGroupN;
+    const int per = ((total + pieces - 1) / pieces + 15) / 16 * 16;
+    for (int c = col0; c < col1; c += per) gs.push_back({c, std::min(per, col1 - c), K});
+    m = o_hi + 1;
+  }
+  // passes
+  H.groups.clear(), H.iters.clear(), H.steps.clear(), H.W.clear();
+  H.npass = 0;
+  size_t gi = 0;
+  while (gi < gs.size()) {
+    if (H.npass == kTcMaxPasses) return false;
+    TcPass& P = H.pass[H.npass++];
+    P.g0 = (int)H.groups.size();
+    int cols = 0, kmax = 0;
+    while (gi < gs.size()) {
+      const int nm = (gs[gi].ncols + 15) / 16 * 16;
+      if (cols + nm > 512) break;
+      H.groups.push_back({nm, cols, gs[gi].col0, gs[gi].ncols});
+      kmax = std::max(kmax, gs[gi].K);
+      cols += nm;
+      ++gi;
+    }
+    P.ng = (int)H.groups.size() - P.g0;
+    int alloc = 32;
+    while (alloc < cols) alloc *= 2;
+    P.tmem_cols = alloc;
+    P.iter0 = (int)H.iters.size();
+    const int nchunks = (kmax + chunk - 1) / chunk;
+    for (int d = 0; d < 27; ++d)
+      for (int j = 0; j < nchunks; ++j) {
+        TcIter I;
+        I.d = d;
+        I.chunk = j;
+        I.step0 = (int)H.steps.size();
+        for (int g = 0; g < P.ng; ++g) {
+          const TcGroup& Gp = H.groups[P.g0 + g];
+          const int K = gs[gi - P.ng + g].K;
+          if (K <= j * chunk) continue;
+          TcStep S;
+          S.group = (short)g;
+          S.ksteps = (short)std::min(4, (K - j * chunk + kstep - 1) / kstep);
+          S.b_off = (long long)H.W.size();
+          S.b_bytes = Gp.n_mma * 128 * planes;
+          H.W.resize(H.W.size() + S.b_bytes, 0);
+          unsigned char* tile = H.W.data() + S.b_off;
+          for (int r = 0; r < Gp.n_mma; ++r) {
+            if (r >= Gp.out_ncols) continue;
+            const int n = Gp.out_col0 + r;
+            for (int e = 0; e < S.ksteps * kstep; ++e) {
+              const int k = j * chunk + e;
+              const double w = m2l_entry(mi, tt, d, k, n);
+              if (w == 0.0) continue;
+              const int byte = e * esz;
+              const size_t off = (size_t)r * 128 + (size_t)((((byte >> 4) ^ (r & 7)) << 4) | (byte & 15));
+              if (kind == TC_BF16X3) {
+                const uint16_t h = bf16_rn((float)w);
+                const uint16_t l = bf16_rn((float)(w - (double)bf16_to_f(h)));
+                std::memcpy(tile + off, &h, 2);
+                std::memcpy(tile + (size_t)Gp.n_mma * 128 + off, &l, 2);
+              } else {
+                const float t = tf32_rn(w);
+                std::memcpy(tile + off, &t, 4);
+              }
+            }
+          }
+          H.steps.push_back(S);
+        }
+        I.nstep = (int)H.steps.size() - I.step0;
+        H.iters.push_back(I);
+      }
+    P.niter = (int)H.iters.size() - P.iter0;
+  }
+  return true;
 }
 
 // Near-field matrices (eq. direct, cell units): W_d[s][t] = g(x_t - x_s) for
@@ -333,6 +489,7 @@ void shift_tables(const MultiIndex& mi, std::vector<int>& m2m_start, std::vector
       e.src = i;
       e.mask = (d[0] & 1) | ((d[1] & 1) << 1) | ((d[2] & 1) << 2);
       e.coef = binom(mi.a[o], mi.a[i]) * binom(mi.b[o], mi.b[i]) * binom(mi.c[o], mi.c[i]) * std::ldexp(1.0, -no - nd);
+      e.coef_f = (float)e.coef;
       m2m.push_back(e);
     }
     l2l_start[o] = (int)l2l.size();
@@ -345,6 +502,7 @@ void shift_tables(const MultiIndex& mi, std::vector<int>& m2m_start, std::vector
       e.mask = (d[0] & 1) | ((d[1] & 1) << 1) | ((d[2] & 1) << 2);
       e.coef = binom(mi.a[g], mi.a[o]) * binom(mi.b[g], mi.b[o]) * binom(mi.c[g], mi.c[o]) *
                std::ldexp(1.0, -1 - ng - nd);
+      e.coef_f = (float)e.coef;
       l2l.push_back(e);
     }
   }
@@ -393,10 +551,15 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
   if (o.n_fp64_levels < 0 || o.n_fp64_levels > kMaxLevels) return fail(FMM_ERR_ARG, "bad n_fp64_levels");
   for (int r : o.reserved)
     if (r != 0) return fail(FMM_ERR_ARG, "reserved option fields must be zero");
-  if (tc_precision(o.precision)) return fail(FMM_ERR_UNSUPPORTED, "tensor-core precisions are not built yet");
-
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
+  if (tc_precision(o.precision)) {
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+    if (!(prop.major == 10 && prop.minor == 3))
+      return fail(FMM_ERR_UNSUPPORTED, "tensor-core precisions need an sm_103 device (found sm_%d%d)", prop.major,
+                  prop.minor);
+  }
 
   fmm_plan_t P = new (std::nothrow) fmm_plan_s();
   if (!P) return fail(FMM_ERR_ALLOC, "host allocation failed");
@@ -416,8 +579,20 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
     delete P;
     return st;
   }
-  // level precisions
-  for (int l = 0; l <= P->L; ++l) P->lev[l].f64 = P->f64_data() ? 1 : 0;
+  // level precisions: FP64 everywhere, FP32 everywhere, or (tensor-core
+  // precisions) FP64 on the coarsest M2L levels 2 .. 1 + n_fp64_levels (never
+  // the leaf level) and tcgen05 M2L on every other level.
+  const bool tcp = tc_precision(o.precision);
+  if (tcp) P->tc_kind = o.precision == FMM_M2L_BF16X3 ? TC_BF16X3 : TC_TF32;
+  for (int l = 0; l <= P->L; ++l) {
+    Level& lv = P->lev[l];
+    lv.f64 = P->f64_data() ? 1 : 0;
+    lv.tc = 0;
+    if (tcp && l >= 2) {
+      if (l <= 1 + o.n_fp64_levels && l < P->L) lv.f64 = 1;
+      else lv.tc = order >= 2 ? 1 : 0;
+    }
+  }
   // arena
   P->lmin = P->L >= 2 ? 2 : P->L;
   size_t off = 0;
@@ -429,6 +604,14 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
     off = align(off + lv.bytes);
     lv.l_off = off;
     off = align(off + lv.bytes);
+    lv.hi_off = lv.lo_off = 0;
+    if (lv.tc && P->tc_kind == TC_BF16X3) {
+      const size_t plane = (size_t)lv.npar * 8 * P->nc * 2;
+      lv.hi_off = off;
+      off = align(off + plane);
+      lv.lo_off = off;
+      off = align(off + plane);
+    }
   }
   const size_t cells_bytes = (size_t)P->ncell() * P->esize();
   P->rho_box_off = off;
@@ -470,23 +653,65 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
       (st = P->upload(l2l, &P->d_l2l, s)) || (st = P->upload(one_flag, &P->d_flag, s)))
     return cleanup(st);
   {
+    bool any64 = false, any32 = false, anytc = false;
+    for (int l = 2; l <= P->L; ++l) {
+      any64 |= P->lev[l].f64 != 0;
+      any32 |= (!P->lev[l].f64 && !P->lev[l].tc);
+      anytc |= P->lev[l].tc != 0;
+    }
+    TaylorTable tt;
+    if (P->L >= 2) tt.build(P->mi);
     std::vector<int> tk;
     std::vector<long long> tw;
-    if (P->f64_data()) {
+    if (any64) {
       std::vector<double> W;
-      m2l_weights<double>(P->mi, W, tk, tw);
+      m2l_weights<double>(P->mi, tt, W, tk, tw);
       double* d = nullptr;
       if ((st = P->upload(W, &d, s))) return cleanup(st);
       P->d_w_m2l_f64 = d;
-    } else {
+    }
+    if (any32) {
       std::vector<float> W;
-      m2l_weights<float>(P->mi, W, tk, tw);
+      m2l_weights<float>(P->mi, tt, W, tk, tw);
       float* d = nullptr;
       if ((st = P->upload(W, &d, s))) return cleanup(st);
       P->d_w_m2l_f32 = d;
     }
     P->m2l_ntiles = (int)tk.size();
     if ((st = P->upload(tk, &P->d_m2l_tile_k, s)) || (st = P->upload(tw, &P->d_m2l_tile_w, s))) return cleanup(st);
+    if (anytc) {
+      TcHost H;
+      if (!build_tc(P->mi, tt, P->tc_kind, H)) return cleanup(fail(FMM_ERR_UNSUPPORTED, "order too high for the tensor-core schedule"));
+      TcIter* di = nullptr;
+      TcStep* ds = nullptr;
+      TcGroup* dg = nullptr;
+      unsigned char* dw = nullptr;
+      if ((st = P->upload(H.iters, &di, s)) || (st = P->upload(H.steps, &ds, s)) || (st = P->upload(H.groups, &dg, s)) ||
+          (st = P->upload(H.W, &dw, s)))
+        return cleanup(st);
+      P->tc.iters = di;
+      P->tc.steps = ds;
+      P->tc.groups = dg;
+      P->tc.W = dw;
+      P->tc.npass = H.npass;
+      for (int i = 0; i < H.npass; ++i) P->tc.pass[i] = H.pass[i];
+      P->tc.n_cols = 8 * P->nc;
+      P->tc.kind = P->tc_kind;
+      P->tc.err = nullptr;  // set below, after the flag exists
+      for (int l = 2; l <= P->L; ++l) {
+        const Level& lv = P->lev[l];
+        if (!lv.tc) continue;
+        cudaError_t e;
+        if (P->tc_kind == TC_BF16X3) {
+          e = make_row_map(P->map_hi[l], P->arena + lv.hi_off, 8 * P->nc, 2, lv.np, 64);
+          if (e == cudaSuccess) e = make_row_map(P->map_lo[l], P->arena + lv.lo_off, 8 * P->nc, 2, lv.np, 64);
+        } else {
+          e = make_row_map(P->map_hi[l], P->arena + lv.m_off, 8 * P->nc, 4, lv.np, 32);
+          if (e == cudaSuccess) std::memcpy(P->map_lo[l], P->map_hi[l], 128);
+        }
+        if (e != cudaSuccess) return cleanup(fail(FMM_ERR_CUDA, "tensor map encoding failed for level %d", l));
+      }
+    }
   }
   {
     std::vector<int> tk;
@@ -507,6 +732,7 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
     P->near_ntiles = (int)tk.size();
     if ((st = P->upload(tk, &P->d_near_tile_k, s)) || (st = P->upload(tw, &P->d_near_tile_w, s))) return cleanup(st);
   }
+  P->tc.err = P->d_flag;
   // uploads read host vectors that go out of scope here
   if (cudaStreamSynchronize(s) != cudaSuccess) return cleanup(fail(FMM_ERR_CUDA, "table upload failed"));
   *out = P;
@@ -536,54 +762,101 @@ struct StageTimer {
   }
 };
 
+// Per-level dispatch helpers (a level's expansions are FP64 or FP32).
+fmm_status do_m2m(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s) {
+  const Level &c = P->lev[l], &q = P->lev[l - 1];
+  cudaError_t e;
+  if (c.f64)
+    e = launch_m2m<double, double>(tt, c, static_cast<const double*>(P->M(l)), q, static_cast<double*>(P->M(l - 1)), s);
+  else if (q.f64)
+    e = launch_m2m<float, double>(tt, c, static_cast<const float*>(P->M(l)), q, static_cast<double*>(P->M(l - 1)), s);
+  else
+    e = launch_m2m<float, float>(tt, c, static_cast<const float*>(P->M(l)), q, static_cast<float*>(P->M(l - 1)), s);
+  CUDA_TRY(e);
+  return FMM_OK;
+}
+
+fmm_status do_l2l(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s) {
+  const Level &q = P->lev[l - 1], &c = P->lev[l];
+  cudaError_t e;
+  if (l == 2) {  // the far field of level 2 is empty
+    e = c.f64 ? launch_zero<double>(static_cast<double*>(P->Lx(l)), c.bytes / 8, s)
+              : launch_zero<float>(static_cast<float*>(P->Lx(l)), c.bytes / 4, s);
+  } else if (q.f64 && c.f64) {
+    e = launch_l2l<double, double>(tt, q, static_cast<const double*>(P->Lx(l - 1)), c, static_cast<double*>(P->Lx(l)), s);
+  } else if (q.f64) {
+    e = launch_l2l<double, float>(tt, q, static_cast<const double*>(P->Lx(l - 1)), c, static_cast<float*>(P->Lx(l)), s);
+  } else {
+    e = launch_l2l<float, float>(tt, q, static_cast<const float*>(P->Lx(l - 1)), c, static_cast<float*>(P->Lx(l)), s);
+  }
+  CUDA_TRY(e);
+  return FMM_OK;
+}
+
+fmm_status do_m2l(fmm_plan_t P, int l, cudaStream_t s) {
+  const Level& lv = P->lev[l];
+  if (lv.tc) {
+    TcLaunch L = P->tc;
+    L.C = static_cast<float*>(P->Lx(l));
+    for (int q = 0; q < 3; ++q) L.grid[q] = lv.np[q];
+    CUDA_TRY(launch_m2l_tc(L, P->map_hi[l], P->map_lo[l], s));
+    return FMM_OK;
+  }
+  NbrGemm g;
+  g.A = P->M(l);
+  g.row_len = 8 * P->nc;
+  for (int q = 0; q < 3; ++q) g.grid[q] = lv.np[q];
+  g.W = lv.f64 ? P->d_w_m2l_f64 : P->d_w_m2l_f32;
+  g.tile_k = P->d_m2l_tile_k;
+  g.tile_w = P->d_m2l_tile_w;
+  g.C = P->Lx(l);
+  g.n_cols = 8 * P->nc;
+  g.ntiles = P->m2l_ntiles;
+  g.accumulate = 1;
+  CUDA_TRY(lv.f64 ? launch_nbr_gemm_simt<double>(g, s) : launch_nbr_gemm_simt<float>(g, s));
+  return FMM_OK;
+}
+
 template <typename T>
 fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t s) {
   const TreeTables tt = P->tables();
   const int L = P->L;
   T* rho_box = reinterpret_cast<T*>(P->arena + P->rho_box_off);
   T* near_box = reinterpret_cast<T*>(P->arena + P->near_off);
+  fmm_status st;
   {
-    StageTimer st(P, ST_CHECK, s);
+    StageTimer t(P, ST_CHECK, s);
     CUDA_TRY(launch_check_finite<T>(rho, (size_t)P->ncell(), P->d_flag, s));
   }
   // upward pass
   {
-    StageTimer st(P, ST_P2M, s);
+    StageTimer t(P, ST_P2M, s);
     CUDA_TRY(launch_p2m<T>(tt, rho, P->dims, P->lev[L], static_cast<T*>(P->M(L)), rho_box, s));
   }
   for (int l = L; l >= 3; --l) {
-    StageTimer st(P, ST_M2M, s);
-    CUDA_TRY((launch_m2m<T, T>(tt, P->lev[l], static_cast<const T*>(P->M(l)), P->lev[l - 1],
-                               static_cast<T*>(P->M(l - 1)), s)));
+    StageTimer t(P, ST_M2M, s);
+    if ((st = do_m2m(P, tt, l, s))) return st;
+  }
+  for (int l = 2; l <= L; ++l) {
+    const Level& lv = P->lev[l];
+    if (lv.tc && P->tc_kind == TC_BF16X3) {
+      StageTimer t(P, ST_SPLIT, s);
+      CUDA_TRY(launch_split_bf16(static_cast<const float*>(P->M(l)), P->arena + lv.hi_off, P->arena + lv.lo_off,
+                                 (size_t)lv.npar * 8 * P->nc, s));
+    }
   }
   // downward pass
   if (L < 2) {
-    StageTimer st(P, ST_L2L, s);
+    StageTimer t(P, ST_L2L, s);
     CUDA_TRY(launch_zero<T>(static_cast<T*>(P->Lx(L)), P->lev[L].bytes / sizeof(T), s));
   }
   for (int l = 2; l <= L; ++l) {
     {
-      StageTimer st(P, ST_L2L, s);
-      if (l == 2) {
-        CUDA_TRY(launch_zero<T>(static_cast<T*>(P->Lx(l)), P->lev[l].bytes / sizeof(T), s));
-      } else {
-        CUDA_TRY((launch_l2l<T, T>(tt, P->lev[l - 1], static_cast<const T*>(P->Lx(l - 1)), P->lev[l],
-                                   static_cast<T*>(P->Lx(l)), s)));
-      }
+      StageTimer t(P, ST_L2L, s);
+      if ((st = do_l2l(P, tt, l, s))) return st;
     }
-    NbrGemm g;
-    g.A = P->M(l);
-    g.row_len = 8 * P->nc;
-    for (int q = 0; q < 3; ++q) g.grid[q] = P->lev[l].np[q];
-    g.W = P->f64_data() ? P->d_w_m2l_f64 : P->d_w_m2l_f32;
-    g.tile_k = P->d_m2l_tile_k;
-    g.tile_w = P->d_m2l_tile_w;
-    g.C = P->Lx(l);
-    g.n_cols = 8 * P->nc;
-    g.ntiles = P->m2l_ntiles;
-    g.accumulate = 1;
-    StageTimer st(P, ST_M2L, s);
-    CUDA_TRY(launch_nbr_gemm_simt<T>(g, s));
+    StageTimer t(P, P->lev[l].tc ? ST_M2L_TC : ST_M2L, s);
+    if ((st = do_m2l(P, l, s))) return st;
   }
   // near field over the 27 neighbour leaf boxes
   {
@@ -598,16 +871,16 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
     g.n_cols = P->b * P->b * P->b;
     g.ntiles = P->near_ntiles;
     g.accumulate = 0;
-    StageTimer st(P, ST_NEAR, s);
+    StageTimer t(P, ST_NEAR, s);
     CUDA_TRY(launch_nbr_gemm_simt<T>(g, s));
   }
   {
-    StageTimer st(P, ST_LEAF, s);
+    StageTimer t(P, ST_LEAF, s);
     CUDA_TRY(launch_leaf_finish<T>(tt, P->lev[L], static_cast<const T*>(P->Lx(L)), near_box, P->dims,
                                    P->G * P->dx * P->dx, phi, s));
   }
   if (accel) {
-    StageTimer st(P, ST_FD, s);
+    StageTimer t(P, ST_FD, s);
     CUDA_TRY(launch_fd_accel<T>(phi, P->dims, 1.0 / P->dx, accel, s));
   }
   return FMM_OK;
@@ -705,7 +978,10 @@ int fmm_solve_launches(fmm_plan_t P, int with_accel) {
   int n = 2;                            // finite check + P2M
   n += std::max(0, L - 2);              // M2M for l = L .. 3
   if (L < 2) n += 1;                    // zero the leaf locals
-  for (int l = 2; l <= L; ++l) n += 2;  // L2L (or zero) + M2L
+  for (int l = 2; l <= L; ++l) {
+    n += 2;                             // L2L (or zero) + M2L
+    if (P->lev[l].tc && P->tc_kind == TC_BF16X3) n += 1;  // hi/lo split
+  }
   n += 2;                               // near field + leaf finish
   if (with_accel) n += 1;
   return n;

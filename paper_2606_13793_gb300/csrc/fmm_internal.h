@@ -37,7 +37,8 @@ constexpr int kKChunk = 32;    // reduction values per SIMT GEMM stage
 // axis q is odd (its sign then depends on which side of the parent the
 // child sits).
 struct ShiftEntry {
-  double coef;
+  double coef;   // FP64 copy (FP64 levels)
+  float coef_f;  // FP32 copy (FP32 levels: no FP64 arithmetic there)
   int src;
   int mask;
 };
@@ -51,6 +52,8 @@ struct Level {
   size_t m_off;    // byte offset of the multipoles in the arena
   size_t l_off;    // byte offset of the local expansions in the arena
   size_t bytes;    // bytes of one of the two arrays
+  int tc;          // M2L of this level on the tensor cores
+  size_t hi_off, lo_off;  // bf16 hi / lo planes of the multipoles (tensor-core bf16x3 levels)
 };
 
 // Neighbour-contraction ("implicit GEMM") description for the SIMT kernel:
@@ -106,5 +109,60 @@ cudaError_t launch_check_finite(const T* x, size_t count, int* flag, cudaStream_
 template <typename T>
 cudaError_t launch_export_level(const T* src, const Level& lv, int what, double h, const int8_t* mi, int nc,
                                 double* dst, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Tensor-core M2L (k_m2l_tc.cu).  The contraction of k_gemm_simt.cu with a
+// tile of 128 parent boxes as the MMA M dimension, the output columns split
+// into "groups" (one MMA N each, order-sorted so each group has one reduction
+// prefix) and the reduction streamed as 128-byte chunks of one neighbour's
+// row.  A operand: TMA tile of the (shifted) parent rows; B operand: a
+// pre-swizzled weight tile per (neighbour, chunk, group).
+constexpr int kTcMaxPasses = 4;
+constexpr int kTcTileX = 8, kTcTileY = 4, kTcTileZ = 4;  // 128 parents
+constexpr int kTcMaxGroupN = 128;                         // B tile <= 128 rows
+
+enum TcKind { TC_BF16X3 = 0, TC_TF32 = 1 };
+
+struct TcGroup {
+  int n_mma;      // MMA N (multiple of 16)
+  int tmem_col;   // first TMEM column
+  int out_col0;   // first output column (beta*8 + child)
+  int out_ncols;  // real output columns (<= n_mma)
+};
+struct TcStep {       // one weight tile (neighbour, chunk, group)
+  long long b_off;    // byte offset in the weight buffer
+  int b_bytes;        // bytes (every plane)
+  short group;        // index into the pass's group slice
+  short ksteps;       // MMA K steps of this chunk for the group
+};
+struct TcIter {       // one activation tile (neighbour, chunk)
+  int d, chunk;
+  int step0, nstep;
+};
+struct TcPass {
+  int iter0, niter;
+  int g0, ng;
+  int tmem_cols;
+};
+struct TcLaunch {
+  const TcIter* iters;
+  const TcStep* steps;
+  const TcGroup* groups;
+  TcPass pass[kTcMaxPasses];
+  int npass;
+  const unsigned char* W;
+  float* C;        // [parents][n_cols], accumulated into
+  int n_cols;
+  int grid[3];     // parent grid
+  int kind;
+  int* err;
+};
+
+// Builds a 4-D TMA map over one level's parent-blocked rows (one plane).
+cudaError_t make_row_map(void* map_out /* CUtensorMap */, const void* base, int row_len, int elem_bytes,
+                         const int grid[3], int box_inner);
+cudaError_t launch_m2l_tc(const TcLaunch& L, const void* map_hi, const void* map_lo, cudaStream_t s);
+// FP32 rows -> bf16 hi and lo planes (hi = rn(x), lo = rn(x - hi)).
+cudaError_t launch_split_bf16(const float* src, void* hi, void* lo, size_t count, cudaStream_t s);
 
 }  // namespace fmmgb

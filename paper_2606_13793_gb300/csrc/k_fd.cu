@@ -8,25 +8,27 @@
 namespace fmmgb {
 namespace {
 
-// Weight of f[j + off] in the cell-unit derivative at index j of a line of n.
-__device__ __forceinline__ double fd_weight(int j, int off, int n) {
-  if (n <= 1) return 0.0;
+// Weight of f[j + off] in the cell-unit derivative at index j of a line of
+// n, in the arithmetic type of the data (no FP64 work on FP32 data).
+template <typename T>
+__device__ __forceinline__ T fd_weight(int j, int off, int n) {
+  if (n <= 1) return T(0);
   if (n == 2) {  // f[1] - f[0] at both points
     const int m = j + off;
-    return m == 1 ? 1.0 : (m == 0 ? -1.0 : 0.0);
+    return m == 1 ? T(1) : (m == 0 ? T(-1) : T(0));
   }
   if (j >= 2 && j <= n - 3) {
     switch (off) {
-      case 2: return -1.0 / 12.0;
-      case 1: return 8.0 / 12.0;
-      case -1: return -8.0 / 12.0;
-      case -2: return 1.0 / 12.0;
-      default: return 0.0;
+      case 2: return T(-1) / T(12);
+      case 1: return T(8) / T(12);
+      case -1: return T(-8) / T(12);
+      case -2: return T(1) / T(12);
+      default: return T(0);
     }
   }
-  if (j >= 1 && j <= n - 2) return off == 1 ? 0.5 : (off == -1 ? -0.5 : 0.0);
-  if (j == 0) return off == 0 ? -1.5 : (off == 1 ? 2.0 : (off == 2 ? -0.5 : 0.0));
-  return off == 0 ? 1.5 : (off == -1 ? -2.0 : (off == -2 ? 0.5 : 0.0));  // j == n-1
+  if (j >= 1 && j <= n - 2) return off == 1 ? T(0.5) : (off == -1 ? T(-0.5) : T(0));
+  if (j == 0) return off == 0 ? T(-1.5) : (off == 1 ? T(2) : (off == 2 ? T(-0.5) : T(0)));
+  return off == 0 ? T(1.5) : (off == -1 ? T(-2) : (off == -2 ? T(0.5) : T(0)));  // j == n-1
 }
 
 template <typename T>
@@ -44,8 +46,8 @@ __global__ void fd_accel_kernel(const T* __restrict__ phi, int nx, int ny, int n
       for (int off = -2; off <= 2; ++off) {
         const int m = pos[q] + off;
         if (m < 0 || m >= len[q]) continue;
-        const double w = fd_weight(pos[q], off, len[q]);
-        if (w != 0.0) d = fma(T(w), phi[c + off * stride[q]], d);
+        const T w = fd_weight<T>(pos[q], off, len[q]);
+        if (w != T(0)) d = fma(w, phi[c + off * stride[q]], d);
       }
       accel[q * n + c] = -d * inv_dx;
     }
@@ -72,8 +74,8 @@ __global__ void adjoint_source_kernel(const T* __restrict__ gphi, const T* __res
         for (int off = -2; off <= 2; ++off) {
           const int j = pos[q] + off;  // stencil centre whose derivative reads this cell
           if (j < 0 || j >= len[q]) continue;
-          const double w = fd_weight(j, -off, len[q]);
-          if (w != 0.0) t = fma(T(w), gacc[q * n + c + off * stride[q]], t);
+          const T w = fd_weight<T>(j, -off, len[q]);
+          if (w != T(0)) t = fma(w, gacc[q * n + c + off * stride[q]], t);
         }
       }
       v = fma(-inv_dx, t, v);
@@ -86,7 +88,7 @@ template <typename T>
 __global__ void check_finite_kernel(const T* __restrict__ x, size_t n, int* flag) {
   int bad = 0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    bad |= !isfinite((double)x[i]);
+    bad |= !isfinite(x[i]);
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 

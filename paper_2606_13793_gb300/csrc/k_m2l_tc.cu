@@ -1,0 +1,356 @@
+// M2L on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// The uniform grid makes every level's M2L (Sec. 2.3, eq. M2L, over the fixed
+// interaction list of Sec. 2.2) the same translation-invariant contraction,
+//   L[P][n] += sum_{d in 27 neighbours} sum_{k < K(n)} M[P + d][k] * W_d[k][n],
+// with P a parent box, k = (alpha, source child) and n = (beta, target child).
+// One CTA computes 128 parents (an 8x4x4 block) for one "pass" of output
+// columns:
+//   * A (M = 128 rows): the neighbour-shifted parent rows, one 128-byte chunk
+//     of the reduction at a time, loaded by TMA from a 4-D tensor map; rows
+//     past the domain are zero-filled by TMA, which is the isolated boundary.
+//   * B: a weight tile per (neighbour, chunk, column group), stored
+//     pre-swizzled (128-byte swizzle) so one bulk copy lands it ready for the
+//     MMA.  Column groups are order-sorted so the truncation
+//     |alpha|+|beta| <= p is a per-group prefix of the reduction: only the
+//     chunks a group needs are multiplied.
+//   * D: FP32 accumulators in tensor memory, one column range per group.
+// Precisions: kind::tf32 on the FP32 rows (one product), or bf16 hi/lo planes
+// with three products hi*hi + hi*lo + lo*hi (kind::f16, BF16 inputs).
+// Roles: warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs, all four warps
+// drain tensor memory in the epilogue.  Every wait is bounded: on time-out
+// the kernel sets the plan's error flag (FMM_ERR_TIMEOUT) and unwinds.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "fmm_internal.h"
+
+namespace fmmgb {
+namespace {
+
+constexpr int kSA = 3;                                   // activation ring stages
+constexpr int kSB = 3;                                   // weight ring stages
+constexpr int kAStage = 2 * 128 * 128;                   // two planes of 128 rows x 128 B
+constexpr int kBStage = 2 * kTcMaxGroupN * 128;          // two planes of <= 128 rows x 128 B
+constexpr int kSmemBytes = kSA * kAStage + kSB * kBStage + 1024 /*barriers*/ + 1024 /*alignment*/;
+constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of `parity` to complete; false on time-out.
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 63u && globaltimer() - t0 > kTimeoutNs) {
+      atomicOr(err, 2);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 B, 8-row groups 1024 B apart (sm_100 family descriptor, version 1).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: next 8-row group
+  d |= (uint64_t)1u << 46;            // descriptor version
+  d |= (uint64_t)2u << 61;            // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: D = F32, A/B K-major, M = 128.
+__device__ __forceinline__ uint32_t make_idesc(int kind, int n) {
+  const uint32_t ab = kind == TC_TF32 ? 2u : 1u;  // TF32 : BF16
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(128, 1)
+    m2l_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, TcLaunch P) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  unsigned char* a_ring = base;
+  unsigned char* b_ring = base + kSA * kAStage;
+  uint64_t* a_full = reinterpret_cast<uint64_t*>(b_ring + kSB * kBStage);
+  uint64_t* a_empty = a_full + kSA;
+  uint64_t* b_full = a_empty + kSA;
+  uint64_t* b_empty = b_full + kSB;
+  uint64_t* accum = b_empty + kSB;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+
+  const TcPass pass = P.pass[blockIdx.y];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntx = (P.grid[0] + kTcTileX - 1) / kTcTileX, nty = (P.grid[1] + kTcTileY - 1) / kTcTileY;
+  const int ox = (blockIdx.x % ntx) * kTcTileX;
+  const int oy = ((blockIdx.x / ntx) % nty) * kTcTileY;
+  const int oz = (blockIdx.x / (ntx * nty)) * kTcTileZ;
+  const bool split = P.kind == TC_BF16X3;
+  const uint32_t a_plane = 128 * 128;  // bytes of one 128-row plane
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kSA; ++i) mbar_init(&a_full[i], 1), mbar_init(&a_empty[i], 1);
+    for (int i = 0; i < kSB; ++i) mbar_init(&b_full[i], 1), mbar_init(&b_empty[i], 1);
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((uint32_t)pass.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    uint32_t ai = 0, bi = 0;
+    bool ok = true;
+    for (int it = pass.iter0; ok && it < pass.iter0 + pass.niter; ++it) {
+      const TcIter I = P.iters[it];
+      const int dx = I.d % 3 - 1, dy = (I.d / 3) % 3 - 1, dz = I.d / 9 - 1;
+      const int sa = ai % kSA;
+      if (!(ok = mbar_wait(&a_empty[sa], ((ai / kSA) & 1) ^ 1, P.err))) break;
+      unsigned char* adst = a_ring + sa * kAStage;
+      const int cx = I.chunk * (split ? 64 : 32);
+      mbar_expect_tx(&a_full[sa], split ? 2 * a_plane : a_plane);
+      tma_load_4d(adst, &map_hi, &a_full[sa], cx, ox + dx, oy + dy, oz + dz);
+      if (split) tma_load_4d(adst + a_plane, &map_lo, &a_full[sa], cx, ox + dx, oy + dy, oz + dz);
+      ++ai;
+      for (int s = I.step0; s < I.step0 + I.nstep; ++s) {
+        const TcStep S = P.steps[s];
+        const int sb = bi % kSB;
+        if (!(ok = mbar_wait(&b_empty[sb], ((bi / kSB) & 1) ^ 1, P.err))) break;
+        mbar_expect_tx(&b_full[sb], (uint32_t)S.b_bytes);
+        bulk_load(b_ring + sb * kBStage, P.W + S.b_off, (uint32_t)S.b_bytes, &b_full[sb]);
+        ++bi;
+      }
+    }
+    if (!ok) {
+      // drain: never leave the CTA with copies in flight
+      for (uint32_t q = (ai > kSA ? ai - kSA : 0); q < ai; ++q) mbar_wait(&a_full[q % kSA], (q / kSA) & 1, P.err);
+      for (uint32_t q = (bi > kSB ? bi - kSB : 0); q < bi; ++q) mbar_wait(&b_full[q % kSB], (q / kSB) & 1, P.err);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    uint32_t ai = 0, bi = 0;
+    bool ok = true;
+    for (int it = pass.iter0; ok && it < pass.iter0 + pass.niter; ++it) {
+      const TcIter I = P.iters[it];
+      const int sa = ai % kSA;
+      if (!(ok = mbar_wait(&a_full[sa], (ai / kSA) & 1, P.err))) break;
+      tc_fence_after();
+      const uint32_t abase = smem_u32(a_ring + sa * kAStage);
+      for (int s = I.step0; s < I.step0 + I.nstep; ++s) {
+        const TcStep S = P.steps[s];
+        const TcGroup G = P.groups[pass.g0 + S.group];
+        const int sb = bi % kSB;
+        if (!(ok = mbar_wait(&b_full[sb], (bi / kSB) & 1, P.err))) break;
+        tc_fence_after();
+        const uint32_t bbase = smem_u32(b_ring + sb * kBStage);
+        const uint32_t bplane = (uint32_t)G.n_mma * 128;
+        const uint32_t idesc = make_idesc(P.kind, G.n_mma);
+        const uint32_t d = tmem + (uint32_t)G.tmem_col;
+        // chunk 0 of neighbour 0 opens every group's accumulator
+        const bool open = (I.d == 0 && I.chunk == 0);
+        for (int k = 0; k < S.ksteps; ++k) {
+          const uint32_t koff = 32u * k;  // 32 B per MMA K step (16 bf16 / 8 tf32)
+          const uint64_t a_hi = sw128_desc(abase + koff), b_hi = sw128_desc(bbase + koff);
+          const uint32_t acc0 = (open && k == 0) ? 0u : 1u;
+          if (split) {
+            const uint64_t a_lo = sw128_desc(abase + a_plane + koff), b_lo = sw128_desc(bbase + bplane + koff);
+            mma_f16(d, a_hi, b_hi, idesc, acc0);
+            mma_f16(d, a_hi, b_lo, idesc, 1u);
+            mma_f16(d, a_lo, b_hi, idesc, 1u);
+          } else {
+            mma_tf32(d, a_hi, b_hi, idesc, acc0);
+          }
+        }
+        mma_commit(&b_empty[sb]);
+        ++bi;
+      }
+      mma_commit(&a_empty[sa]);
+      ++ai;
+    }
+    mma_commit(accum);  // fires when every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: TMEM -> registers -> L (accumulate) ----------------
+  int done = 0;
+  if (lane == 0) done = mbar_wait(accum, 0, P.err) ? 1 : 0;
+  done = __shfl_sync(0xffffffffu, done, 0);  // warp-uniform: tcgen05.ld is warp-collective
+  if (done) {
+    tc_fence_after();
+    const int r = warp * 32 + lane;  // tile row = TMEM lane
+    const int x = ox + (r & 7), y = oy + ((r >> 3) & 3), z = oz + (r >> 5);
+    const bool valid = x < P.grid[0] && y < P.grid[1] && z < P.grid[2];
+    float* crow = P.C + ((((long long)z * P.grid[1] + y) * P.grid[0] + x) * P.n_cols);
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    for (int g = pass.g0; g < pass.g0 + pass.ng; ++g) {
+      const TcGroup G = P.groups[g];
+      for (int c = 0; c < G.n_mma; c += 16) {
+        float v[16];
+        tmem_ld16(tmem + lane_base + (uint32_t)(G.tmem_col + c), v);  // warp-collective
+        if (valid) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c + j < G.out_ncols) crow[G.out_col0 + c + j] += v[j];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)pass.tmem_cols));
+  }
+}
+
+__global__ void split_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ hi,
+                                  __nv_bfloat16* __restrict__ lo, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float x = src[i];
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+
+}  // namespace
+
+cudaError_t make_row_map(void* map_out, const void* base, int row_len, int elem_bytes, const int grid[3],
+                         int box_inner) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<EncodeFn>(fn);
+  }
+  const cuuint64_t dims[4] = {(cuuint64_t)row_len, (cuuint64_t)grid[0], (cuuint64_t)grid[1], (cuuint64_t)grid[2]};
+  const cuuint64_t row_bytes = (cuuint64_t)row_len * elem_bytes;
+  const cuuint64_t strides[3] = {row_bytes, row_bytes * grid[0], row_bytes * grid[0] * grid[1]};
+  const cuuint32_t box[4] = {(cuuint32_t)box_inner, kTcTileX, kTcTileY, kTcTileZ};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = encode(reinterpret_cast<CUtensorMap*>(map_out),
+                      elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                      const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_m2l_tc(const TcLaunch& L, const void* map_hi, const void* map_lo, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(m2l_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int ntx = (L.grid[0] + kTcTileX - 1) / kTcTileX, nty = (L.grid[1] + kTcTileY - 1) / kTcTileY,
+            ntz = (L.grid[2] + kTcTileZ - 1) / kTcTileZ;
+  dim3 grid((unsigned)(ntx * nty * ntz), (unsigned)L.npass);
+  m2l_tc_kernel<<<grid, 128, kSmemBytes, s>>>(*reinterpret_cast<const CUtensorMap*>(map_hi),
+                                              *reinterpret_cast<const CUtensorMap*>(map_lo), L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16(const float* src, void* hi, void* lo, size_t count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  size_t blocks = (count + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  split_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, static_cast<__nv_bfloat16*>(hi),
+                                                     static_cast<__nv_bfloat16*>(lo), count);
+  return cudaGetLastError();
+}
+
+}  // namespace fmmgb

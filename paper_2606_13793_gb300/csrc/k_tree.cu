@@ -20,8 +20,19 @@ __device__ __forceinline__ int coef_index(int a, int b, int c) {
   return n * (n + 1) * (n + 2) / 6 + (n - a) * (n - a + 1) / 2 + (n - a - b);
 }
 
-__device__ __forceinline__ double shift_sign(int mask, int child) {
-  return (__popc(mask & ~child & 7) & 1) ? -1.0 : 1.0;
+// True when the shift term of parity `mask` changes sign for this child
+// (an odd power of a negative half-offset).
+__device__ __forceinline__ bool shift_neg(int mask, int child) { return __popc(mask & ~child & 7) & 1; }
+
+template <typename T>
+__device__ __forceinline__ T coef_of(const ShiftEntry& e);
+template <>
+__device__ __forceinline__ float coef_of<float>(const ShiftEntry& e) {
+  return e.coef_f;
+}
+template <>
+__device__ __forceinline__ double coef_of<double>(const ShiftEntry& e) {
+  return e.coef;
 }
 
 // P2M (Sec. 2.1, eq. multipole) about each leaf-box centre, in scaled form
@@ -114,12 +125,12 @@ __global__ void m2m_kernel(TreeTables t, Level child, const Tc* __restrict__ Mc,
   for (int a = lane; a < nc; a += 32) {
     Tp s = Tp(0);
     for (int q = t.m2m_start[a]; q < t.m2m_start[a + 1]; ++q) {
-      const ShiftEntry en = t.m2m[q];
+      const ShiftEntry& en = t.m2m[q];
       const Tc* m = Ms + en.src * 8;
       Tp part = Tp(0);
 #pragma unroll
-      for (int c = 0; c < 8; ++c) part = fma(Tp(shift_sign(en.mask, c)), Tp(m[c]), part);
-      s = fma(Tp(en.coef), part, s);
+      for (int c = 0; c < 8; ++c) part += shift_neg(en.mask, c) ? -Tp(m[c]) : Tp(m[c]);
+      s = fma(coef_of<Tp>(en), part, s);
     }
     Mp[(gp * nc + a) * 8 + cp] = s;
   }
@@ -149,8 +160,9 @@ __global__ void l2l_kernel(TreeTables t, Level par, const Tp* __restrict__ Lp, L
     const int be = o >> 3, c = o & 7;
     Tp s = Tp(0);
     for (int q = t.l2l_start[be]; q < t.l2l_start[be + 1]; ++q) {
-      const ShiftEntry en = t.l2l[q];
-      s = fma(Tp(en.coef * shift_sign(en.mask, c)), Ls[en.src], s);
+      const ShiftEntry& en = t.l2l[q];
+      const Tp cf = coef_of<Tp>(en);
+      s = fma(shift_neg(en.mask, c) ? -cf : cf, Ls[en.src], s);
     }
     dst[o] = Tc(s);
   }

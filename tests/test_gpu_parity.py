@@ -2,8 +2,13 @@
 
 Tolerances (relative L2 over all cells, from the arithmetic of each mode):
   FP64         phi <= 1e-10, accel <= 1e-9   (rounding-order differences only)
-  FP32 plain   phi <= 1e-5,  accel <= 1e-4   (FP32 unit roundoff 6e-8 times the
+  FP32 plain   phi <= 1e-5                   (FP32 unit roundoff 6e-8 times the
                                               depth of the sums, with margin)
+               accel <= acc_tol(n)           the stencil differences phi over
+                                              one cell: an error e in phi becomes
+                                              about 1.5 e |phi| / |dphi/di| ~
+                                              0.4 n e relative in accel, so with
+                                              e <= 1e-6: 1e-4 * max(1, n / 256)
 """
 import numpy as np
 import pytest
@@ -20,6 +25,10 @@ from paper_2606_13793_gb300 import _build, inputs  # noqa: E402
 def built():
     _build.build()
     assert torch.cuda.is_available()
+
+
+def acc_tol(n):
+    return 1e-4 * max(1.0, n / 256.0)
 
 
 def rel_l2(a, b):
@@ -122,7 +131,7 @@ def test_fp32_full_size_sampled(orc, n):
     ref_phi, ref_acc = orc.fmm_sample(rho32.astype(np.float64), 4, 6, cells, dx=1.0 / n, accel=True)
     assert rel_l2(phi.ravel()[cells], ref_phi) <= 1e-5
     got_acc = np.stack([acc[q].ravel()[cells] for q in range(3)], 1)
-    assert rel_l2(got_acc, ref_acc) <= 1e-4
+    assert rel_l2(got_acc, ref_acc) <= acc_tol(n)
 
 
 def test_adjoint_fp64_matches_oracle(orc):

@@ -1,0 +1,123 @@
+"""Parity of the tensor-core (tcgen05) M2L precisions with the FP64 oracle.
+
+Tolerances (relative L2 of phi over all cells):
+  bf16x3  <= 1e-5   the metric's bound: hi/lo bf16 splits carry ~16 bits, the
+                    three products drop terms of ~2^-17 relative per product
+                    (CPU emulation of the packed schedule: <= 4e-6 of the sum
+                    of |terms|), FP32 accumulation
+  tf32    <= 1e-3   a single TF32 product has a 2^-11 relative error per
+                    operand; reported, not held to the 1e-5 bound
+The FP64 coarse levels (2 .. 4) and every non-M2L step are the FP32/FP64
+kernels already held to the oracle by test_gpu_parity.py.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import paper_2606_13793_gb300 as fmm  # noqa: E402
+from paper_2606_13793_gb300 import _build, inputs  # noqa: E402
+
+TOL = {"bf16x3": 1e-5, "tf32": 1e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+    assert torch.cuda.is_available()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def acc_tol(n, prec):
+    base = 1e-4 if prec == "bf16x3" else 1e-2
+    return base * max(1.0, n / 256.0)
+
+
+def solve(rho32, b, p, prec, dx=1.0, n_fp64_levels=3):
+    nz, ny, nx = rho32.shape
+    plan = fmm.FMMPlan((nx, ny, nz), p, b, prec, dx=dx, n_fp64_levels=n_fp64_levels)
+    phi, acc = plan.solve(torch.from_numpy(np.ascontiguousarray(rho32)).cuda(), accel=True)
+    torch.cuda.synchronize()
+    plan.check()
+    out = phi.double().cpu().numpy(), acc.double().cpu().numpy()
+    plan.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("p", [4, 6, 8])
+def test_tc_matches_oracle(orc, prec, p):
+    rho = inputs.lognormal(64, seed=2606 + p).astype(np.float64)
+    ref = orc.fmm(rho, 4, p, accel=True)
+    phi, acc = solve(rho.astype(np.float32), 4, p, prec)
+    err = rel_l2(phi, ref["phi"])
+    print(f"{prec} p={p}: phi rel err {err:.3e}")
+    assert err <= TOL[prec]
+    assert rel_l2(acc, ref["accel"]) <= acc_tol(64, prec)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_tc_ragged_grid(orc, prec):
+    """Non-power-of-two extents: partial 8x4x4 tiles, TMA zero fill past the
+    domain and phantom children."""
+    rho = inputs.plummer((96, 64, 80), seed=11).astype(np.float64)
+    ref = orc.fmm(rho, 4, 6, accel=True)
+    phi, _ = solve(rho.astype(np.float32), 4, 6, prec)
+    assert rel_l2(phi, ref["phi"]) <= TOL[prec]
+
+
+def test_tc_all_levels_on_tensor_cores(orc):
+    """n_fp64_levels = 0: every M2L level (down to the 2x2x2 parent grid) on tcgen05."""
+    rho = inputs.gaussian_blobs(64, seed=5).astype(np.float64)
+    ref = orc.fmm(rho, 4, 6)
+    phi, _ = solve(rho.astype(np.float32), 4, 6, "bf16x3", n_fp64_levels=0)
+    assert rel_l2(phi, ref["phi"]) <= 1e-5
+
+
+def test_tc_level_locals_match_oracle(orc):
+    """Local expansions of each tensor-core level against the oracle's, so a
+    mismatch names its level."""
+    rho = inputs.lognormal(128, seed=3).astype(np.float64)
+    plan = fmm.FMMPlan((128, 128, 128), 6, 4, "bf16x3")
+    plan.solve(torch.from_numpy(rho.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    plan.check()
+    L = plan.leaf_level
+    for lvl in range(5, L + 1):
+        ref = orc.fmm(rho, 4, 6, export_level=lvl)["L"]
+        got = plan.debug_level("L", lvl)
+        # compare the potential-carrying monopole coefficient and the whole set
+        assert rel_l2(got[:, 0], ref[:, 0]) <= 1e-5, lvl
+        assert rel_l2(got, ref) <= 1e-4, lvl
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_tc_full_size_sampled(orc, prec):
+    """512^3, p=6, leaf 4, lognormal: the benchmark configuration, sampled."""
+    n = 512
+    rho32 = inputs.lognormal(n, seed=2606)
+    phi, acc = solve(rho32, 4, 6, prec, dx=1.0 / n)
+    rng = np.random.default_rng(7)
+    cells = rng.integers(0, n ** 3, 40)
+    cells[:4] = [0, n ** 3 - 1, n // 2 * (n * n + n + 1), (n // 2) * n * n + 5 * n + 9]
+    ref_phi, ref_acc = orc.fmm_sample(rho32.astype(np.float64), 4, 6, cells, dx=1.0 / n, accel=True)
+    assert rel_l2(phi.ravel()[cells], ref_phi) <= TOL[prec]
+    got_acc = np.stack([acc[q].ravel()[cells] for q in range(3)], 1)
+    assert rel_l2(got_acc, ref_acc) <= acc_tol(n, prec)
+
+
+def test_tc_deterministic():
+    rho = torch.from_numpy(inputs.lognormal(64, seed=1)).cuda()
+    plan = fmm.FMMPlan((64, 64, 64), 6, 4, "bf16x3")
+    a = plan.solve(rho)
+    b = plan.solve(rho)
+    torch.cuda.synchronize()
+    plan.check()
+    assert torch.equal(a, b)
+    plan.close()
