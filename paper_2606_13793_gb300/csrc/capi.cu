@@ -114,10 +114,11 @@ enum Stage {
   ST_ADJ_SRC,
   ST_SPLIT,
   ST_M2L_TC,
+  ST_NEAR_TC,
   ST_COUNT
 };
 const char* kStageNames[ST_COUNT] = {"finite_check", "p2m",          "m2m",         "l2l",       "m2l", "near_field",
-                                     "leaf_l2p",     "fd_accel",     "adjoint_source", "split_bf16", "m2l_tc"};
+                                     "leaf_l2p",     "fd_accel",     "adjoint_source", "split_bf16", "m2l_tc", "near_field_tc"};
 constexpr int kEventPool = 8192;
 
 }  // namespace
@@ -155,9 +156,15 @@ struct fmm_plan_s {
   int* d_near_tile_k = nullptr;
   long long* d_near_tile_w = nullptr;
   int near_ntiles = 0;
-  // tensor-core M2L
+  // tensor-core M2L and near field
   int tc_kind = -1;
   TcLaunch tc{};
+  bool near_tc = false;
+  TcLaunch tcn{};
+  alignas(64) unsigned char map_near_hi[128];
+  alignas(64) unsigned char map_near_lo[128];
+  size_t rho_hi_off = 0, rho_lo_off = 0;
+  size_t part_off = 0;  // neighbour-split partial sums of the small SIMT levels
   alignas(64) unsigned char map_hi[kMaxLevels][128];
   alignas(64) unsigned char map_lo[kMaxLevels][128];
   // host-buffer staging for fmm_solve_host
@@ -176,6 +183,12 @@ struct fmm_plan_s {
   std::vector<Rec> recs;
 
   bool f64_data() const { return opts.precision == FMM_FP64; }
+  // SIMT M2L levels too small to fill the GPU run one CTA per neighbour.
+  bool split_level(int l) const {
+    const Level& lv = lev[l];
+    const long long tiles = (long long)((lv.np[0] + 3) / 4) * ((lv.np[1] + 3) / 4) * ((lv.np[2] + 3) / 4);
+    return !lv.tc && tiles * m2l_ntiles < 2 * 152;
+  }
   size_t esize() const { return f64_data() ? 8 : 4; }
   long long ncell() const { return (long long)dims[0] * dims[1] * dims[2]; }
   TreeTables tables() const {
@@ -349,27 +362,20 @@ struct TcHost {
   std::vector<unsigned char> W;
 };
 
-bool build_tc(const MultiIndex& mi, const TaylorTable& tt, int kind, TcHost& H) {
-  const int p = mi.p;
+// A column group before packing: output columns [col0, col0 + ncols) that
+// share one reduction prefix of length K.
+struct TcCols {
+  int col0, ncols, K;
+};
+
+// Packs passes, iterations and weight tiles for groups `gs`; `entry(d, k, n)`
+// gives one weight of the contraction.
+template <typename Entry>
+bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entry, TcHost& H) {
   const int chunk = kind == TC_BF16X3 ? 64 : 32;  // reduction values per 128-byte chunk
   const int kstep = chunk / 4;
   const int esz = kind == TC_BF16X3 ? 2 : 4;
   const int planes = kind == TC_BF16X3 ? 2 : 1;
-  struct G {
-    int col0, ncols, K;
-  };
-  std::vector<G> gs;
-  for (int m = 0; m <= p;) {
-    const int o_hi = (m == 0 && p >= 1) ? 1 : m;
-    const int col0 = m == 0 ? 0 : 8 * ncoef(m - 1), col1 = 8 * ncoef(o_hi);
-    const int K = 8 * ncoef(p - m);
-    const int total = col1 - col0;
-    const int pieces = (total + kTcMaxGroupN - 1) / kTcMaxGroupN;
-    const int per = ((total + pieces - 1) / pieces + 15) / 16 * 16;
-    for (int c = col0; c < col1; c += per) gs.push_back({c, std::min(per, col1 - c), K});
-    m = o_hi + 1;
-  }
-  // passes
   H.groups.clear(), H.iters.clear(), H.steps.clear(), H.W.clear();
   H.npass = 0;
   size_t gi = 0;
@@ -378,15 +384,18 @@ bool build_tc(const MultiIndex& mi, const TaylorTable& tt, int kind, TcHost& H) 
     TcPass& P = H.pass[H.npass++];
     P.g0 = (int)H.groups.size();
     int cols = 0, kmax = 0;
+    std::vector<int> Kg;
     while (gi < gs.size()) {
       const int nm = (gs[gi].ncols + 15) / 16 * 16;
       if (cols + nm > 512) break;
       H.groups.push_back({nm, cols, gs[gi].col0, gs[gi].ncols});
+      Kg.push_back(gs[gi].K);
       kmax = std::max(kmax, gs[gi].K);
       cols += nm;
       ++gi;
     }
     P.ng = (int)H.groups.size() - P.g0;
+    if (P.ng == 0) return false;
     int alloc = 32;
     while (alloc < cols) alloc *= 2;
     P.tmem_cols = alloc;
@@ -399,8 +408,8 @@ bool build_tc(const MultiIndex& mi, const TaylorTable& tt, int kind, TcHost& H) 
         I.chunk = j;
         I.step0 = (int)H.steps.size();
         for (int g = 0; g < P.ng; ++g) {
-          const TcGroup& Gp = H.groups[P.g0 + g];
-          const int K = gs[gi - P.ng + g].K;
+          const TcGroup Gp = H.groups[P.g0 + g];
+          const int K = Kg[g];
           if (K <= j * chunk) continue;
           TcStep S;
           S.group = (short)g;
@@ -409,12 +418,12 @@ bool build_tc(const MultiIndex& mi, const TaylorTable& tt, int kind, TcHost& H) 
           S.b_bytes = Gp.n_mma * 128 * planes;
           H.W.resize(H.W.size() + S.b_bytes, 0);
           unsigned char* tile = H.W.data() + S.b_off;
-          for (int r = 0; r < Gp.n_mma; ++r) {
-            if (r >= Gp.out_ncols) continue;
+          for (int r = 0; r < Gp.out_ncols; ++r) {
             const int n = Gp.out_col0 + r;
             for (int e = 0; e < S.ksteps * kstep; ++e) {
               const int k = j * chunk + e;
-              const double w = m2l_entry(mi, tt, d, k, n);
+              if (k >= K) continue;
+              const double w = entry(d, k, n);
               if (w == 0.0) continue;
               const int byte = e * esz;
               const size_t off = (size_t)r * 128 + (size_t)((((byte >> 4) ^ (r & 7)) << 4) | (byte & 15));
@@ -437,6 +446,45 @@ bool build_tc(const MultiIndex& mi, const TaylorTable& tt, int kind, TcHost& H) 
     P.niter = (int)H.iters.size() - P.iter0;
   }
   return true;
+}
+
+// M2L groups: order blocks (orders 0 and 1 merged), each with the prefix
+// 8 nc(p - lowest order), split into pieces of <= 128 columns.
+bool build_tc(const MultiIndex& mi, const TaylorTable& tt, int kind, TcHost& H) {
+  const int p = mi.p;
+  std::vector<TcCols> gs;
+  for (int m = 0; m <= p;) {
+    const int o_hi = (m == 0 && p >= 1) ? 1 : m;
+    const int col0 = m == 0 ? 0 : 8 * ncoef(m - 1), col1 = 8 * ncoef(o_hi);
+    const int K = 8 * ncoef(p - m);
+    const int total = col1 - col0;
+    const int pieces = (total + kTcMaxGroupN - 1) / kTcMaxGroupN;
+    const int per = ((total + pieces - 1) / pieces + 15) / 16 * 16;
+    for (int c = col0; c < col1; c += per) gs.push_back({c, std::min(per, col1 - c), K});
+    m = o_hi + 1;
+  }
+  return build_tc_generic(kind, gs, [&](int d, int k, int n) { return m2l_entry(mi, tt, d, k, n); }, H);
+}
+
+// Near field (eq. direct) as the same contraction over leaf boxes: column n =
+// target cell, reduction k = source cell of neighbour box d, weight
+// g(x_t - x_s) in cell units (-1 for the cell itself).
+bool build_tc_near(int b, int kind, TcHost& H) {
+  const int b3 = b * b * b;
+  std::vector<TcCols> gs;
+  for (int c = 0; c < b3; c += kTcMaxGroupN) gs.push_back({c, std::min(kTcMaxGroupN, b3 - c), b3});
+  auto entry = [b](int d, int k, int n) {
+    const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+    const int tp[3] = {n % b, (n / b) % b, n / (b * b)};
+    const int sp[3] = {k % b, (k / b) % b, k / (b * b)};
+    double r2 = 0.0;
+    for (int q = 0; q < 3; ++q) {
+      const double r = (double)(tp[q] - sp[q] - b * D[q]);
+      r2 += r * r;
+    }
+    return r2 == 0.0 ? -1.0 : -1.0 / std::sqrt(r2);
+  };
+  return build_tc_generic(kind, gs, entry, H);
 }
 
 // Near-field matrices (eq. direct, cell units): W_d[s][t] = g(x_t - x_s) for
@@ -620,6 +668,24 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
   off = align(off + cells_bytes);
   P->work_off = off;
   off = align(off + cells_bytes);
+  P->near_tc = tcp && (leaf == 4 || leaf == 8);
+  if (P->near_tc) {  // the near field always runs bf16x3 (hi/lo density planes)
+    P->rho_hi_off = off;
+    off = align(off + (size_t)P->ncell() * 2);
+    P->rho_lo_off = off;
+    off = align(off + (size_t)P->ncell() * 2);
+  }
+  {
+    // column tiles of the SIMT contraction (needed to size the split scratch)
+    const int ncol = 8 * P->nc;
+    P->m2l_ntiles = (ncol + kNTile - 1) / kNTile;
+    size_t part = 0;
+    for (int l = 2; l <= P->L; ++l)
+      if (P->split_level(l))
+        part = std::max(part, (size_t)27 * (size_t)P->lev[l].npar * (size_t)ncol * (size_t)(P->lev[l].f64 ? 8 : 4));
+    P->part_off = off;
+    off = align(off + part);
+  }
   P->arena_bytes = off;
 
   auto cleanup = [&](fmm_status e) {
@@ -732,7 +798,37 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
     P->near_ntiles = (int)tk.size();
     if ((st = P->upload(tk, &P->d_near_tile_k, s)) || (st = P->upload(tw, &P->d_near_tile_w, s))) return cleanup(st);
   }
+  if (P->near_tc) {
+    TcHost H;
+    // bf16x3 in both tensor-core precisions: a TF32 near field would carry
+    // ~3e-4 relative error on its (same-signed) sums
+    if (!build_tc_near(P->b, TC_BF16X3, H)) return cleanup(fail(FMM_ERR_UNSUPPORTED, "near-field schedule failed"));
+    TcIter* di = nullptr;
+    TcStep* ds = nullptr;
+    TcGroup* dg = nullptr;
+    unsigned char* dw = nullptr;
+    if ((st = P->upload(H.iters, &di, s)) || (st = P->upload(H.steps, &ds, s)) || (st = P->upload(H.groups, &dg, s)) ||
+        (st = P->upload(H.W, &dw, s)))
+      return cleanup(st);
+    TcLaunch& T = P->tcn;
+    T.iters = di;
+    T.steps = ds;
+    T.groups = dg;
+    T.W = dw;
+    T.npass = H.npass;
+    for (int i = 0; i < H.npass; ++i) T.pass[i] = H.pass[i];
+    T.n_cols = P->b * P->b * P->b;
+    T.kind = TC_BF16X3;
+    T.accumulate = 0;
+    for (int q = 0; q < 3; ++q) T.grid[q] = P->lev[P->L].n[q];
+    T.C = reinterpret_cast<float*>(P->arena + P->near_off);
+    T.err = P->d_flag;
+    cudaError_t e = make_row_map(P->map_near_hi, P->arena + P->rho_hi_off, T.n_cols, 2, T.grid, 64);
+    if (e == cudaSuccess) e = make_row_map(P->map_near_lo, P->arena + P->rho_lo_off, T.n_cols, 2, T.grid, 64);
+    if (e != cudaSuccess) return cleanup(fail(FMM_ERR_CUDA, "tensor map encoding failed for the near field"));
+  }
   P->tc.err = P->d_flag;
+  P->tc.accumulate = 1;
   // uploads read host vectors that go out of scope here
   if (cudaStreamSynchronize(s) != cudaSuccess) return cleanup(fail(FMM_ERR_CUDA, "table upload failed"));
   *out = P;
@@ -813,6 +909,8 @@ fmm_status do_m2l(fmm_plan_t P, int l, cudaStream_t s) {
   g.n_cols = 8 * P->nc;
   g.ntiles = P->m2l_ntiles;
   g.accumulate = 1;
+  g.dsplit = P->split_level(l) ? 27 : 1;
+  g.partial = P->arena + P->part_off;
   CUDA_TRY(lv.f64 ? launch_nbr_gemm_simt<double>(g, s) : launch_nbr_gemm_simt<float>(g, s));
   return FMM_OK;
 }
@@ -832,6 +930,11 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
   {
     StageTimer t(P, ST_P2M, s);
     CUDA_TRY(launch_p2m<T>(tt, rho, P->dims, P->lev[L], static_cast<T*>(P->M(L)), rho_box, s));
+  }
+  if (P->near_tc) {
+    StageTimer t(P, ST_SPLIT, s);
+    CUDA_TRY(launch_split_bf16(reinterpret_cast<const float*>(rho_box), P->arena + P->rho_hi_off,
+                               P->arena + P->rho_lo_off, (size_t)P->ncell(), s));
   }
   for (int l = L; l >= 3; --l) {
     StageTimer t(P, ST_M2M, s);
@@ -859,7 +962,10 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
     if ((st = do_m2l(P, l, s))) return st;
   }
   // near field over the 27 neighbour leaf boxes
-  {
+  if (P->near_tc) {
+    StageTimer t(P, ST_NEAR_TC, s);
+    CUDA_TRY(launch_m2l_tc(P->tcn, P->map_near_hi, P->map_near_lo, s));
+  } else {
     NbrGemm g;
     g.A = rho_box;
     g.row_len = P->b * P->b * P->b;
@@ -871,6 +977,8 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
     g.n_cols = P->b * P->b * P->b;
     g.ntiles = P->near_ntiles;
     g.accumulate = 0;
+    g.dsplit = 1;
+    g.partial = nullptr;
     StageTimer t(P, ST_NEAR, s);
     CUDA_TRY(launch_nbr_gemm_simt<T>(g, s));
   }
@@ -981,7 +1089,9 @@ int fmm_solve_launches(fmm_plan_t P, int with_accel) {
   for (int l = 2; l <= L; ++l) {
     n += 2;                             // L2L (or zero) + M2L
     if (P->lev[l].tc && P->tc_kind == TC_BF16X3) n += 1;  // hi/lo split
+    if (P->split_level(l)) n += 1;      // reduction of the neighbour partials
   }
+  if (P->near_tc) n += 1;  // density hi/lo split
   n += 2;                               // near field + leaf finish
   if (with_accel) n += 1;
   return n;

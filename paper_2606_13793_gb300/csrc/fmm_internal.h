@@ -70,6 +70,8 @@ struct NbrGemm {
   int n_cols;
   int ntiles;
   int accumulate;      // 1: C += result, 0: C = result
+  int dsplit;          // 1, or 27: one CTA per neighbour, partial sums reduced in a fixed order
+  void* partial;       // [27][rows][n_cols] scratch when dsplit == 27
 };
 
 template <typename T>
@@ -151,8 +153,9 @@ struct TcLaunch {
   TcPass pass[kTcMaxPasses];
   int npass;
   const unsigned char* W;
-  float* C;        // [parents][n_cols], accumulated into
+  float* C;        // [parents][n_cols]
   int n_cols;
+  int accumulate;  // 1: C += result, 0: C = result
   int grid[3];     // parent grid
   int kind;
   int* err;

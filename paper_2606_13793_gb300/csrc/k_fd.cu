@@ -31,11 +31,14 @@ __device__ __forceinline__ T fd_weight(int j, int off, int n) {
   return off == 0 ? T(1.5) : (off == -1 ? T(-2) : (off == -2 ? T(0.5) : T(0)));  // j == n-1
 }
 
+// Grid: x blocks over a row, y = row index, z = slice (32-bit indexing).
 template <typename T>
 __global__ void fd_accel_kernel(const T* __restrict__ phi, int nx, int ny, int nz, T inv_dx, T* __restrict__ accel) {
   const long long n = (long long)nx * ny * nz;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+  if (x >= nx) return;
+  const long long c = ((long long)z * ny + y) * nx + x;
+  {
     const int pos[3] = {x, y, z};
     const int len[3] = {nx, ny, nz};
     const long long stride[3] = {1, nx, (long long)nx * ny};
@@ -60,10 +63,12 @@ template <typename T>
 __global__ void adjoint_source_kernel(const T* __restrict__ gphi, const T* __restrict__ gacc, int nx, int ny, int nz,
                                       T inv_dx, T* __restrict__ out) {
   const long long n = (long long)nx * ny * nz;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+  if (x >= nx) return;
+  const long long c = ((long long)z * ny + y) * nx + x;
+  {
     T v = gphi ? gphi[c] : T(0);
     if (gacc) {
-      const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
       const int pos[3] = {x, y, z};
       const int len[3] = {nx, ny, nz};
       const long long stride[3] = {1, nx, (long long)nx * ny};
@@ -100,18 +105,22 @@ unsigned blocks_for(long long n) {
 
 }  // namespace
 
+dim3 row_grid(const int dims[3], int threads) {
+  return dim3((unsigned)((dims[0] + threads - 1) / threads), (unsigned)dims[1], (unsigned)dims[2]);
+}
+
 template <typename T>
 cudaError_t launch_fd_accel(const T* phi, const int dims[3], double inv_dx, T* accel, cudaStream_t s) {
-  const long long n = (long long)dims[0] * dims[1] * dims[2];
-  fd_accel_kernel<T><<<blocks_for(n), 256, 0, s>>>(phi, dims[0], dims[1], dims[2], (T)inv_dx, accel);
+  const int th = dims[0] >= 256 ? 256 : ((dims[0] + 31) / 32) * 32;
+  fd_accel_kernel<T><<<row_grid(dims, th), th, 0, s>>>(phi, dims[0], dims[1], dims[2], (T)inv_dx, accel);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_adjoint_source(const T* gphi, const T* gaccel, const int dims[3], double inv_dx, T* out,
                                   cudaStream_t s) {
-  const long long n = (long long)dims[0] * dims[1] * dims[2];
-  adjoint_source_kernel<T><<<blocks_for(n), 256, 0, s>>>(gphi, gaccel, dims[0], dims[1], dims[2], (T)inv_dx, out);
+  const int th = dims[0] >= 256 ? 256 : ((dims[0] + 31) / 32) * 32;
+  adjoint_source_kernel<T><<<row_grid(dims, th), th, 0, s>>>(gphi, gaccel, dims[0], dims[1], dims[2], (T)inv_dx, out);
   return cudaGetLastError();
 }
 

@@ -46,7 +46,9 @@ __global__ void __launch_bounds__(64) nbr_gemm_simt_kernel(NbrGemm g) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 
-  for (int d = 0; d < 27; ++d) {
+  const int d0 = g.dsplit > 1 ? (int)blockIdx.z : 0;
+  const int d1 = g.dsplit > 1 ? d0 + 1 : 27;
+  for (int d = d0; d < d1; ++d) {
     const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
     const T* Wd = W0 + (long long)d * K * kNTile;
     for (int kc = 0; kc < K; kc += kKChunk) {
@@ -82,6 +84,8 @@ __global__ void __launch_bounds__(64) nbr_gemm_simt_kernel(NbrGemm g) {
   }
 
   T* C = static_cast<T*>(g.C);
+  const long long rows = (long long)g.grid[0] * g.grid[1] * g.grid[2];
+  T* Pz = g.dsplit > 1 ? static_cast<T*>(g.partial) + (long long)blockIdx.z * rows * g.n_cols : nullptr;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int r = rg * 8 + i;
@@ -92,9 +96,23 @@ __global__ void __launch_bounds__(64) nbr_gemm_simt_kernel(NbrGemm g) {
     for (int j = 0; j < 4; ++j) {
       const int n = tile * kNTile + cg * 4 + j;
       if (n >= g.n_cols) continue;
-      T* dst = C + row * g.n_cols + n;
-      *dst = g.accumulate ? (*dst + acc[i][j]) : acc[i][j];
+      if (Pz) {
+        Pz[row * g.n_cols + n] = acc[i][j];
+      } else {
+        T* dst = C + row * g.n_cols + n;
+        *dst = g.accumulate ? (*dst + acc[i][j]) : acc[i][j];
+      }
     }
+  }
+}
+
+// C (+)= sum over the 27 neighbour partials, in neighbour order.
+template <typename T>
+__global__ void reduce_partials_kernel(const T* __restrict__ part, long long count, T* __restrict__ C, int accumulate) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    T s = accumulate ? C[i] : T(0);
+    for (int d = 0; d < 27; ++d) s += part[d * count + i];
+    C[i] = s;
   }
 }
 
@@ -105,8 +123,15 @@ cudaError_t launch_nbr_gemm_simt(const NbrGemm& g, cudaStream_t s) {
   const long long tiles = (long long)((g.grid[0] + 3) / 4) * ((g.grid[1] + 3) / 4) * ((g.grid[2] + 3) / 4);
   if (tiles <= 0 || g.ntiles <= 0) return cudaSuccess;
   if (tiles > 0x7fffffffLL || g.ntiles > 65535) return cudaErrorInvalidConfiguration;
-  dim3 grid((unsigned)tiles, (unsigned)g.ntiles);
+  dim3 grid((unsigned)tiles, (unsigned)g.ntiles, g.dsplit > 1 ? 27u : 1u);
   nbr_gemm_simt_kernel<T><<<grid, 64, 0, s>>>(g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || g.dsplit <= 1) return e;
+  const long long count = (long long)g.grid[0] * g.grid[1] * g.grid[2] * g.n_cols;
+  long long blocks = (count + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  reduce_partials_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const T*>(g.partial), count,
+                                                            static_cast<T*>(g.C), g.accumulate);
   return cudaGetLastError();
 }
 

@@ -279,7 +279,10 @@ __global__ void __launch_bounds__(128, 1)
         if (valid) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (c + j < G.out_ncols) crow[G.out_col0 + c + j] += v[j];
+            if (c + j < G.out_ncols) {
+              float* o = crow + G.out_col0 + c + j;
+              *o = P.accumulate ? *o + v[j] : v[j];
+            }
         }
       }
     }
