@@ -185,6 +185,13 @@ fmm_status fmm_debug_level(fmm_plan_t plan, int what, int level, double* host_ou
 /* Number of FMM levels minus one (index of the leaf level), or -1. */
 int fmm_plan_leaf_level(fmm_plan_t plan);
 
+/* How the M2L of one level runs: 0 none (levels 0, 1), 1 CUDA cores FP32,
+ * 2 CUDA cores FP64, 3 tcgen05 tensor cores; -1 for a bad plan or level. */
+int fmm_plan_level_kind(fmm_plan_t plan, int level);
+
+/* 1 when the near field runs on the tensor cores (bf16x3), else 0. */
+int fmm_plan_near_on_tensor_cores(fmm_plan_t plan);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3}
 EXPORTS = ["fmm_default_opts", "fmm_plan", "fmm_solve", "fmm_solve_adjoint", "fmm_solve_host", "fmm_check",
            "fmm_workspace_bytes", "fmm_solve_launches", "fmm_plan_destroy", "fmm_last_error", "fmm_debug_level",
            "fmm_plan_leaf_level", "fmm_timing_enable", "fmm_timing_read", "fmm_timing_stage_count",
-           "fmm_timing_stage_name"]
+           "fmm_timing_stage_name", "fmm_plan_level_kind", "fmm_plan_near_on_tensor_cores"]
 
 
 class FMMError(RuntimeError):
@@ -89,6 +89,10 @@ def load(path: str | None = None):
         lib.fmm_debug_level.restype = i
         lib.fmm_plan_leaf_level.argtypes = [vp]
         lib.fmm_plan_leaf_level.restype = i
+        lib.fmm_plan_level_kind.argtypes = [vp, i]
+        lib.fmm_plan_level_kind.restype = i
+        lib.fmm_plan_near_on_tensor_cores.argtypes = [vp]
+        lib.fmm_plan_near_on_tensor_cores.restype = i
         lib.fmm_timing_enable.argtypes = [vp, i]
         lib.fmm_timing_enable.restype = i
         lib.fmm_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), i]
@@ -230,6 +234,15 @@ class FMMPlan:
     @property
     def leaf_level(self) -> int:
         return int(self.lib.fmm_plan_leaf_level(self._h))
+
+    def level_kind(self, level: int) -> str:
+        """'none', 'fp32', 'fp64' or 'tensor': how the M2L of that level runs."""
+        return {0: "none", 1: "fp32", 2: "fp64", 3: "tensor"}.get(
+            int(self.lib.fmm_plan_level_kind(self._h, int(level))), "invalid")
+
+    @property
+    def near_on_tensor_cores(self) -> bool:
+        return bool(self.lib.fmm_plan_near_on_tensor_cores(self._h))
 
     @property
     def workspace_bytes(self) -> int:

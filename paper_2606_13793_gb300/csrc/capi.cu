@@ -1080,6 +1080,15 @@ size_t fmm_workspace_bytes(fmm_plan_t P) { return P ? P->dev_bytes : 0; }
 
 int fmm_plan_leaf_level(fmm_plan_t P) { return P ? P->L : -1; }
 
+int fmm_plan_level_kind(fmm_plan_t P, int level) {
+  if (!P || level < 0 || level > P->L) return -1;
+  if (level < 2) return 0;
+  const Level& lv = P->lev[level];
+  return lv.tc ? 3 : (lv.f64 ? 2 : 1);
+}
+
+int fmm_plan_near_on_tensor_cores(fmm_plan_t P) { return (P && P->near_tc) ? 1 : 0; }
+
 int fmm_solve_launches(fmm_plan_t P, int with_accel) {
   if (!P) return -1;
   const int L = P->L;
