@@ -312,6 +312,7 @@ def main():
             dist.barrier()
     ms = start.elapsed_time(end)
     stages = plan.timing_read()
+    plan.check()  # a device-side time-out or non-finite input voids the measurement
     plan.timing(False)
     clocks = clk.summary()
     t = torch.tensor([ms], device="cuda", dtype=torch.float64)

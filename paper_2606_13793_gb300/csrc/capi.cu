@@ -1071,7 +1071,7 @@ fmm_status fmm_check(fmm_plan_t P) {
   if (flag) {
     CUDA_TRY(cudaMemset(P->d_flag, 0, sizeof(int)));
     if (flag & 1) return fail(FMM_ERR_NONFINITE, "the density held a NaN or Inf");
-    return fail(FMM_ERR_TIMEOUT, "a device wait reached its iteration limit");
+    return fail(FMM_ERR_TIMEOUT, "a device wait reached its time limit (wait sites 0x%x)", (flag >> 8) & 0xff);
   }
   return FMM_OK;
 }

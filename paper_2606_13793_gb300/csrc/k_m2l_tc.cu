@@ -66,17 +66,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase of `parity` to complete; false on time-out.
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+// Bounded wait for the phase of `parity` to complete; false on time-out, after
+// recording FMM_ERR_TIMEOUT (bit 1) and the wait site (bits 8..15) in *err.
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int site) {
   const unsigned long long t0 = globaltimer();
   for (uint32_t i = 0;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 63u) == 63u && globaltimer() - t0 > kTimeoutNs) {
-      atomicOr(err, 2);
+      atomicOr(err, 2 | (1 << (8 + site)));
       return false;
     }
   }
 }
+
+enum WaitSite { W_PROD_A = 0, W_PROD_B, W_MMA_A, W_MMA_B, W_EPI, W_DRAIN };
 
 __device__ __forceinline__ void tma_load_4d(void* dst, const void* map, uint64_t* bar, int c0, int c1, int c2,
                                             int c3) {
@@ -177,6 +180,7 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
+    __syncwarp();  // tcgen05.alloc is warp-collective: reconverge after thread 0's block
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"((uint32_t)pass.tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -194,7 +198,7 @@ __global__ void __launch_bounds__(128, 1)
       const TcIter I = P.iters[it];
       const int dx = I.d % 3 - 1, dy = (I.d / 3) % 3 - 1, dz = I.d / 9 - 1;
       const int sa = ai % kSA;
-      if (!(ok = mbar_wait(&a_empty[sa], ((ai / kSA) & 1) ^ 1, P.err))) break;
+      if (!(ok = mbar_wait(&a_empty[sa], ((ai / kSA) & 1) ^ 1, P.err, W_PROD_A))) break;
       unsigned char* adst = a_ring + sa * kAStage;
       const int cx = I.chunk * (split ? 64 : 32);
       mbar_expect_tx(&a_full[sa], split ? 2 * a_plane : a_plane);
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(128, 1)
       for (int s = I.step0; s < I.step0 + I.nstep; ++s) {
         const TcStep S = P.steps[s];
         const int sb = bi % kSB;
-        if (!(ok = mbar_wait(&b_empty[sb], ((bi / kSB) & 1) ^ 1, P.err))) break;
+        if (!(ok = mbar_wait(&b_empty[sb], ((bi / kSB) & 1) ^ 1, P.err, W_PROD_B))) break;
         mbar_expect_tx(&b_full[sb], (uint32_t)S.b_bytes);
         bulk_load(b_ring + sb * kBStage, P.W + S.b_off, (uint32_t)S.b_bytes, &b_full[sb]);
         ++bi;
@@ -212,8 +216,8 @@ __global__ void __launch_bounds__(128, 1)
     }
     if (!ok) {
       // drain: never leave the CTA with copies in flight
-      for (uint32_t q = (ai > kSA ? ai - kSA : 0); q < ai; ++q) mbar_wait(&a_full[q % kSA], (q / kSA) & 1, P.err);
-      for (uint32_t q = (bi > kSB ? bi - kSB : 0); q < bi; ++q) mbar_wait(&b_full[q % kSB], (q / kSB) & 1, P.err);
+      for (uint32_t q = (ai > kSA ? ai - kSA : 0); q < ai; ++q) mbar_wait(&a_full[q % kSA], (q / kSA) & 1, P.err, W_DRAIN);
+      for (uint32_t q = (bi > kSB ? bi - kSB : 0); q < bi; ++q) mbar_wait(&b_full[q % kSB], (q / kSB) & 1, P.err, W_DRAIN);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
@@ -222,14 +226,14 @@ __global__ void __launch_bounds__(128, 1)
     for (int it = pass.iter0; ok && it < pass.iter0 + pass.niter; ++it) {
       const TcIter I = P.iters[it];
       const int sa = ai % kSA;
-      if (!(ok = mbar_wait(&a_full[sa], (ai / kSA) & 1, P.err))) break;
+      if (!(ok = mbar_wait(&a_full[sa], (ai / kSA) & 1, P.err, W_MMA_A))) break;
       tc_fence_after();
       const uint32_t abase = smem_u32(a_ring + sa * kAStage);
       for (int s = I.step0; s < I.step0 + I.nstep; ++s) {
         const TcStep S = P.steps[s];
         const TcGroup G = P.groups[pass.g0 + S.group];
         const int sb = bi % kSB;
-        if (!(ok = mbar_wait(&b_full[sb], (bi / kSB) & 1, P.err))) break;
+        if (!(ok = mbar_wait(&b_full[sb], (bi / kSB) & 1, P.err, W_MMA_B))) break;
         tc_fence_after();
         const uint32_t bbase = smem_u32(b_ring + sb * kBStage);
         const uint32_t bplane = (uint32_t)G.n_mma * 128;
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(128, 1)
 
   // ---------------- epilogue: TMEM -> registers -> L (accumulate) ----------------
   int done = 0;
-  if (lane == 0) done = mbar_wait(accum, 0, P.err) ? 1 : 0;
+  if (lane == 0) done = mbar_wait(accum, 0, P.err, W_EPI) ? 1 : 0;
   done = __shfl_sync(0xffffffffu, done, 0);  // warp-uniform: tcgen05.ld is warp-collective
   if (done) {
     tc_fence_after();
@@ -275,7 +279,8 @@ __global__ void __launch_bounds__(128, 1)
       const TcGroup G = P.groups[g];
       for (int c = 0; c < G.n_mma; c += 16) {
         float v[16];
-        tmem_ld16(tmem + lane_base + (uint32_t)(G.tmem_col + c), v);  // warp-collective
+        __syncwarp();  // tcgen05.ld is warp-collective: reconverge after the masked stores
+        tmem_ld16(tmem + lane_base + (uint32_t)(G.tmem_col + c), v);
         if (valid) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
