@@ -141,6 +141,46 @@ fmm_status fmm_solve_adjoint(fmm_plan_t plan, const void* grad_phi, const void* 
  */
 fmm_status fmm_solve_host(fmm_plan_t plan, const void* rho_host, void* phi_host, void* accel_host, void* stream);
 
+/*
+ * fmm_solve_static -- the same FP32 solve as fmm_solve (CUDA-core kernels,
+ * FMM_FP32 arithmetic, 5-point accel), for callers that cannot allocate
+ * device memory.  The paper has no counterpart: this entry point only
+ * changes where the solver's workspace lives.
+ *
+ * Who needs it: code that must not call cudaMalloc while it runs -- for
+ * example a hot loop with a latency budget (cudaMalloc may synchronise the
+ * whole device), code running inside a framework whose caching allocator
+ * owns the device memory budget, or a plug-in whose host application forbids
+ * device allocation after start-up.  Those callers cannot create a plan
+ * (fmm_plan allocates its tables and arena), so this call takes no plan and
+ * allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
+ *
+ * Workspace: one static device array of FMM_STATIC_WORKSPACE_BYTES (16 MiB)
+ * compiled into this library.  Every device on which the library is loaded
+ * holds that array until the process exits.  A solve fits when its tables
+ * plus its arena fit the array: at leaf 4 that is up to 64^3 cells for
+ * orders <= 6 (larger grids or orders return FMM_ERR_ARG with the byte count
+ * in fmm_last_error(), before any device work).
+ *
+ *   grid, order, leaf : as fmm_plan (order <= 6).
+ *   rho, phi, accel   : device float arrays as fmm_solve (accel may be NULL),
+ *                       16-byte aligned, owned by the caller.
+ *   stream            : cudaStream_t for every copy and kernel of the call.
+ *
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  The call keeps the array's tables from the
+ * previous call when order, leaf and grid are unchanged (otherwise it
+ * rebuilds them on the host and copies them in), and clears every part of
+ * the array that must start at zero.  All calls share one array: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and give
+ * wrong results; order them on one stream.  Device-side flags (non-finite
+ * input) are not reported: there is no plan to hold them.
+ */
+#define FMM_STATIC_WORKSPACE_BYTES (16u << 20)
+fmm_status fmm_solve_static(const fmm_grid* grid, int order, int leaf, const void* rho, void* phi, void* accel,
+                            void* stream);
+
 /* fmm_check -- synchronises the plan's last stream and reports device-side
  * flags (FMM_ERR_NONFINITE, FMM_ERR_TIMEOUT), clearing them. */
 fmm_status fmm_check(fmm_plan_t plan);

@@ -30,7 +30,7 @@ PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3}
 EXPORTS = ["fmm_default_opts", "fmm_plan", "fmm_solve", "fmm_solve_adjoint", "fmm_solve_host", "fmm_check",
            "fmm_workspace_bytes", "fmm_solve_launches", "fmm_plan_destroy", "fmm_last_error", "fmm_debug_level",
            "fmm_plan_leaf_level", "fmm_timing_enable", "fmm_timing_read", "fmm_timing_stage_count",
-           "fmm_timing_stage_name", "fmm_plan_level_kind", "fmm_plan_near_on_tensor_cores"]
+           "fmm_timing_stage_name", "fmm_plan_level_kind", "fmm_plan_near_on_tensor_cores", "fmm_solve_static"]
 
 
 class FMMError(RuntimeError):
@@ -89,6 +89,8 @@ def load(path: str | None = None):
         lib.fmm_debug_level.restype = i
         lib.fmm_plan_leaf_level.argtypes = [vp]
         lib.fmm_plan_leaf_level.restype = i
+        lib.fmm_solve_static.argtypes = [ctypes.POINTER(_Grid), i, i, vp, vp, vp, vp]
+        lib.fmm_solve_static.restype = i
         lib.fmm_plan_level_kind.argtypes = [vp, i]
         lib.fmm_plan_level_kind.restype = i
         lib.fmm_plan_near_on_tensor_cores.argtypes = [vp]
@@ -261,6 +263,35 @@ class FMMPlan:
             self.close()
         except Exception:
             pass
+
+
+def solve_static(rho, order: int = 6, leaf: int = 4, dx: float = 1.0, G: float = 1.0, accel: bool = False,
+                 phi_out=None, accel_out=None, stream=None):
+    """FP32 solve without a plan and without any device allocation by the
+    library (fmm_solve_static): for callers that must not allocate device
+    memory while they run.  The workspace is the library's fixed 16 MiB
+    static device array (about 64^3 cells at order 6, leaf 4); calls that
+    overlap on the GPU share it and race, so keep them on one stream.  The
+    output tensors may be passed in so that nothing is allocated here either."""
+    import torch
+
+    lib = load()
+    if not isinstance(rho, torch.Tensor) or not rho.is_cuda or rho.dtype != torch.float32 or rho.dim() != 3:
+        raise TypeError("rho must be a 3-D float32 CUDA tensor [nz][ny][nx]")
+    if not rho.is_contiguous():
+        raise ValueError("rho must be contiguous")
+    nz, ny, nx = rho.shape
+    phi = phi_out if phi_out is not None else torch.empty_like(rho)
+    acc = None
+    if accel:
+        acc = accel_out if accel_out is not None else torch.empty((3, nz, ny, nx), dtype=torch.float32,
+                                                                  device=rho.device)
+    grid = _Grid(nx, ny, nz, float(dx), float(G))
+    _check(lib, lib.fmm_solve_static(ctypes.byref(grid), int(order), int(leaf), ctypes.c_void_p(rho.data_ptr()),
+                                     ctypes.c_void_p(phi.data_ptr()),
+                                     ctypes.c_void_p(acc.data_ptr()) if acc is not None else None,
+                                     _stream_handle(stream)))
+    return (phi, acc) if accel else phi
 
 
 def _make_autograd():

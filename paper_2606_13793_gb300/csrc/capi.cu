@@ -20,6 +20,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -187,7 +189,7 @@ struct fmm_plan_s {
   bool split_level(int l) const {
     const Level& lv = lev[l];
     const long long tiles = (long long)((lv.np[0] + 3) / 4) * ((lv.np[1] + 3) / 4) * ((lv.np[2] + 3) / 4);
-    return !lv.tc && tiles * m2l_ntiles < 2 * 152;
+    return !no_split && !lv.tc && tiles * m2l_ntiles < 2 * 152;
   }
   size_t esize() const { return f64_data() ? 8 : 4; }
   long long ncell() const { return (long long)dims[0] * dims[1] * dims[2]; }
@@ -206,14 +208,43 @@ struct fmm_plan_s {
   void* M(int l) const { return arena + lev[l].m_off; }
   void* Lx(int l) const { return arena + lev[l].l_off; }
 
+  // Device placement: cudaMalloc (plans) or a bump pointer inside a caller
+  // supplied region (the allocation-free solve), where the tables can be
+  // left as the previous call wrote them.
+  unsigned char* static_base = nullptr;
+  size_t static_cap = 0, static_used = 0;
+  bool static_keep_tables = false;
+  bool no_split = false;
+
+  fmm_status dev_alloc(size_t bytes, void** out) {
+    if (static_base) {
+      const size_t off = (static_used + 255) & ~(size_t)255;
+      if (off + bytes > static_cap)
+        return fail(FMM_ERR_ARG, "workspace of more than %zu bytes does not fit the %zu-byte static array",
+                    off + bytes, static_cap);
+      static_used = off + bytes;
+      *out = static_base + off;
+      return FMM_OK;
+    }
+    void* d = nullptr;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FMM_ERR_ALLOC, "cudaMalloc(%zu) failed", bytes);
+    }
+    allocs.push_back(d);
+    dev_bytes += bytes;
+    *out = d;
+    return FMM_OK;
+  }
+
   template <typename T>
   fmm_status upload(const std::vector<T>& host, T** dptr, cudaStream_t s) {
     const size_t bytes = std::max<size_t>(host.size(), 1) * sizeof(T);
     void* d = nullptr;
-    if (cudaMalloc(&d, bytes) != cudaSuccess) return fail(FMM_ERR_ALLOC, "cudaMalloc(%zu) failed", bytes);
-    allocs.push_back(d);
-    dev_bytes += bytes;
-    if (!host.empty()) CUDA_TRY(cudaMemcpyAsync(d, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    fmm_status st = dev_alloc(bytes, &d);
+    if (st != FMM_OK) return st;
+    if (!host.empty() && !static_keep_tables)
+      CUDA_TRY(cudaMemcpyAsync(d, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, s));
     *dptr = static_cast<T*>(d);
     return FMM_OK;
   }
@@ -300,7 +331,7 @@ double m2l_entry(const MultiIndex& mi, const TaylorTable& tt, int d, int k, int 
 // lowest order fixes the reduction prefix 8 * nc(p - order).
 template <typename T>
 void m2l_weights(const MultiIndex& mi, const TaylorTable& tt, std::vector<T>& W, std::vector<int>& tile_k,
-                 std::vector<long long>& tile_w) {
+                 std::vector<long long>& tile_w, bool fill = true) {
   const int p = mi.p, nc = mi.nc;
   const int ncol = 8 * nc;
   const int ntiles = (ncol + kNTile - 1) / kNTile;
@@ -315,6 +346,7 @@ void m2l_weights(const MultiIndex& mi, const TaylorTable& tt, std::vector<T>& W,
     off += 27LL * tile_k[t] * kNTile;
   }
   W.assign((size_t)off, T(0));
+  if (!fill) return;
   for (int t = 0; t < ntiles; ++t) {
     const int K = tile_k[t];
     for (int d = 0; d < 27; ++d) {
@@ -490,13 +522,15 @@ bool build_tc_near(int b, int kind, TcHost& H) {
 // Near-field matrices (eq. direct, cell units): W_d[s][t] = g(x_t - x_s) for
 // source cell s of neighbour leaf box d and target cell t.
 template <typename T>
-void near_weights(int b, std::vector<T>& W, std::vector<int>& tile_k, std::vector<long long>& tile_w) {
+void near_weights(int b, std::vector<T>& W, std::vector<int>& tile_k, std::vector<long long>& tile_w,
+                  bool fill = true) {
   const int b3 = b * b * b;
   const int ntiles = (b3 + kNTile - 1) / kNTile;
   tile_k.assign(ntiles, b3);
   tile_w.resize(ntiles);
   for (int t = 0; t < ntiles; ++t) tile_w[t] = 27LL * b3 * kNTile * t;
   W.assign((size_t)27 * b3 * kNTile * ntiles, T(0));
+  if (!fill) return;
   for (int t = 0; t < ntiles; ++t)
     for (int d = 0; d < 27; ++d) {
       const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
@@ -562,60 +596,19 @@ bool tc_precision(int prec) { return prec == FMM_M2L_TF32 || prec == FMM_M2L_BF1
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-void fmm_default_opts(fmm_opts* o) {
-  if (!o) return;
-  std::memset(o, 0, sizeof(*o));
-  o->precision = FMM_FP32;
-  o->n_fp64_levels = 3;
-  o->accel = 1;
-}
-
-const char* fmm_last_error(void) { return g_last_error.c_str(); }
-
-fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* opts, void* stream, fmm_plan_t* out) {
-  g_last_error.clear();
-  if (!out) return fail(FMM_ERR_ARG, "out is NULL");
-  *out = nullptr;
-  if (!grid) return fail(FMM_ERR_ARG, "grid is NULL");
-  if (order < 0 || order > kMaxOrder) return fail(FMM_ERR_ARG, "order %d outside [0, %d]", order, kMaxOrder);
-  if (leaf != 2 && leaf != 4 && leaf != 8) return fail(FMM_ERR_ARG, "leaf %d not in {2, 4, 8}", leaf);
-  const int d3[3] = {grid->nx, grid->ny, grid->nz};
-  for (int q = 0; q < 3; ++q) {
-    if (d3[q] <= 0) return fail(FMM_ERR_ARG, "grid extent %d must be positive", d3[q]);
-    if (d3[q] % leaf) return fail(FMM_ERR_ARG, "grid extent %d is not a multiple of leaf %d", d3[q], leaf);
-    if (d3[q] > (1 << 14)) return fail(FMM_ERR_ARG, "grid extent %d too large", d3[q]);
-  }
-  if (!(grid->dx > 0.0) || !std::isfinite(grid->dx)) return fail(FMM_ERR_ARG, "dx must be positive and finite");
-  if (!std::isfinite(grid->G)) return fail(FMM_ERR_ARG, "G must be finite");
-  fmm_opts o;
-  if (opts) {
-    o = *opts;
-  } else {
-    fmm_default_opts(&o);
-  }
-  if (o.precision < FMM_FP64 || o.precision > FMM_M2L_BF16X3) return fail(FMM_ERR_ARG, "unknown precision %d", o.precision);
-  if (o.n_fp64_levels < 0 || o.n_fp64_levels > kMaxLevels) return fail(FMM_ERR_ARG, "bad n_fp64_levels");
-  for (int r : o.reserved)
-    if (r != 0) return fail(FMM_ERR_ARG, "reserved option fields must be zero");
-  int dev = 0;
-  CUDA_TRY(cudaGetDevice(&dev));
-  if (tc_precision(o.precision)) {
-    cudaDeviceProp prop;
-    CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
-    if (!(prop.major == 10 && prop.minor == 3))
-      return fail(FMM_ERR_UNSUPPORTED, "tensor-core precisions need an sm_103 device (found sm_%d%d)", prop.major,
-                  prop.minor);
-  }
-
-  fmm_plan_t P = new (std::nothrow) fmm_plan_s();
-  if (!P) return fail(FMM_ERR_ALLOC, "host allocation failed");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+// Everything of a plan after argument checks: hierarchy, level precisions,
+// arena layout, tables.  Device memory comes from P->dev_alloc (cudaMalloc
+// for plans, the static array for the allocation-free solve).  On failure
+// the caller releases P.
+fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int order, int leaf, const fmm_opts& o,
+                     cudaStream_t stream, int dev) {
+  cudaStream_t s = stream;
   P->last_stream = s;
   for (int q = 0; q < 3; ++q) P->dims[q] = d3[q];
-  P->dx = grid->dx;
-  P->G = grid->G;
+  P->dx = dx;
+  P->G = G;
   P->p = order;
   P->b = leaf;
   P->opts = o;
@@ -623,10 +616,7 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
   P->nc = P->mi.nc;
 
   fmm_status st = build_levels(P);
-  if (st != FMM_OK) {
-    delete P;
-    return st;
-  }
+  if (st != FMM_OK) return st;
   // level precisions: FP64 everywhere, FP32 everywhere, or (tensor-core
   // precisions) FP64 on the coarsest M2L levels 2 .. 1 + n_fp64_levels (never
   // the leaf level) and tcgen05 M2L on every other level.
@@ -688,18 +678,9 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
   }
   P->arena_bytes = off;
 
-  auto cleanup = [&](fmm_status e) {
-    P->release();
-    delete P;
-    return e;
-  };
+  auto cleanup = [](fmm_status e) { return e; };  // the caller releases the plan
   void* arena = nullptr;
-  if (cudaMalloc(&arena, P->arena_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return cleanup(fail(FMM_ERR_ALLOC, "cudaMalloc(%zu) for the workspace arena failed", P->arena_bytes));
-  }
-  P->allocs.push_back(arena);
-  P->dev_bytes += P->arena_bytes;
+  if ((st = P->dev_alloc(P->arena_bytes, &arena))) return st;
   P->arena = static_cast<unsigned char*>(arena);
   if (cudaMemsetAsync(arena, 0, P->arena_bytes, s) != cudaSuccess) return cleanup(fail(FMM_ERR_CUDA, "memset failed"));
 
@@ -726,19 +707,19 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
       anytc |= P->lev[l].tc != 0;
     }
     TaylorTable tt;
-    if (P->L >= 2) tt.build(P->mi);
+    if (P->L >= 2 && !P->static_keep_tables) tt.build(P->mi);
     std::vector<int> tk;
     std::vector<long long> tw;
     if (any64) {
       std::vector<double> W;
-      m2l_weights<double>(P->mi, tt, W, tk, tw);
+      m2l_weights<double>(P->mi, tt, W, tk, tw, !P->static_keep_tables);
       double* d = nullptr;
       if ((st = P->upload(W, &d, s))) return cleanup(st);
       P->d_w_m2l_f64 = d;
     }
     if (any32) {
       std::vector<float> W;
-      m2l_weights<float>(P->mi, tt, W, tk, tw);
+      m2l_weights<float>(P->mi, tt, W, tk, tw, !P->static_keep_tables);
       float* d = nullptr;
       if ((st = P->upload(W, &d, s))) return cleanup(st);
       P->d_w_m2l_f32 = d;
@@ -784,13 +765,13 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
     std::vector<long long> tw;
     if (P->f64_data()) {
       std::vector<double> W;
-      near_weights<double>(P->b, W, tk, tw);
+      near_weights<double>(P->b, W, tk, tw, !P->static_keep_tables);
       double* d = nullptr;
       if ((st = P->upload(W, &d, s))) return cleanup(st);
       P->d_w_near = d;
     } else {
       std::vector<float> W;
-      near_weights<float>(P->b, W, tk, tw);
+      near_weights<float>(P->b, W, tk, tw, !P->static_keep_tables);
       float* d = nullptr;
       if ((st = P->upload(W, &d, s))) return cleanup(st);
       P->d_w_near = d;
@@ -829,8 +810,70 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
   }
   P->tc.err = P->d_flag;
   P->tc.accumulate = 1;
-  // uploads read host vectors that go out of scope here
-  if (cudaStreamSynchronize(s) != cudaSuccess) return cleanup(fail(FMM_ERR_CUDA, "table upload failed"));
+  // uploads read host vectors that go out of scope here (plans only; the
+  // allocation-free solve orders its copies on the caller's stream)
+  if (!P->static_base && cudaStreamSynchronize(s) != cudaSuccess)
+    return cleanup(fail(FMM_ERR_CUDA, "table upload failed"));
+  return FMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fmm_default_opts(fmm_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = FMM_FP32;
+  o->n_fp64_levels = 3;
+  o->accel = 1;
+}
+
+const char* fmm_last_error(void) { return g_last_error.c_str(); }
+
+fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* opts, void* stream, fmm_plan_t* out) {
+  g_last_error.clear();
+  if (!out) return fail(FMM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grid) return fail(FMM_ERR_ARG, "grid is NULL");
+  if (order < 0 || order > kMaxOrder) return fail(FMM_ERR_ARG, "order %d outside [0, %d]", order, kMaxOrder);
+  if (leaf != 2 && leaf != 4 && leaf != 8) return fail(FMM_ERR_ARG, "leaf %d not in {2, 4, 8}", leaf);
+  const int d3[3] = {grid->nx, grid->ny, grid->nz};
+  for (int q = 0; q < 3; ++q) {
+    if (d3[q] <= 0) return fail(FMM_ERR_ARG, "grid extent %d must be positive", d3[q]);
+    if (d3[q] % leaf) return fail(FMM_ERR_ARG, "grid extent %d is not a multiple of leaf %d", d3[q], leaf);
+    if (d3[q] > (1 << 14)) return fail(FMM_ERR_ARG, "grid extent %d too large", d3[q]);
+  }
+  if (!(grid->dx > 0.0) || !std::isfinite(grid->dx)) return fail(FMM_ERR_ARG, "dx must be positive and finite");
+  if (!std::isfinite(grid->G)) return fail(FMM_ERR_ARG, "G must be finite");
+  fmm_opts o;
+  if (opts) {
+    o = *opts;
+  } else {
+    fmm_default_opts(&o);
+  }
+  if (o.precision < FMM_FP64 || o.precision > FMM_M2L_BF16X3) return fail(FMM_ERR_ARG, "unknown precision %d", o.precision);
+  if (o.n_fp64_levels < 0 || o.n_fp64_levels > kMaxLevels) return fail(FMM_ERR_ARG, "bad n_fp64_levels");
+  for (int r : o.reserved)
+    if (r != 0) return fail(FMM_ERR_ARG, "reserved option fields must be zero");
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (tc_precision(o.precision)) {
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+    if (!(prop.major == 10 && prop.minor == 3))
+      return fail(FMM_ERR_UNSUPPORTED, "tensor-core precisions need an sm_103 device (found sm_%d%d)", prop.major,
+                  prop.minor);
+  }
+
+  fmm_plan_t P = new (std::nothrow) fmm_plan_s();
+  if (!P) return fail(FMM_ERR_ALLOC, "host allocation failed");
+  fmm_status st = plan_init(P, d3, grid->dx, grid->G, order, leaf, o, static_cast<cudaStream_t>(stream), dev);
+  if (st != FMM_OK) {
+    P->release();
+    delete P;
+    return st;
+  }
   *out = P;
   return FMM_OK;
 }
@@ -1173,3 +1216,79 @@ fmm_status fmm_debug_level(fmm_plan_t P, int what, int level, double* host_out, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free solve: the workspace is a file-scope static device array.
+namespace {
+
+constexpr size_t kStaticWorkspaceBytes = FMM_STATIC_WORKSPACE_BYTES;
+constexpr int kStaticMaxOrder = 6;
+constexpr int kStaticMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_static_workspace[kStaticWorkspaceBytes];
+
+// Per device: the array's device address (looked up once, with the device
+// current) and the (order, leaf, nx, ny, nz) whose tables the array holds.
+struct StaticSlot {
+  unsigned char* ptr = nullptr;
+  int key[5] = {-1, -1, -1, -1, -1};
+};
+StaticSlot g_static_slots[kStaticMaxDevices];
+std::mutex g_static_mutex;
+
+}  // namespace
+
+extern "C" fmm_status fmm_solve_static(const fmm_grid* grid, int order, int leaf, const void* rho, void* phi,
+                                       void* accel, void* stream) {
+  g_last_error.clear();
+  if (!grid) return fail(FMM_ERR_ARG, "grid is NULL");
+  if (order < 0 || order > kStaticMaxOrder)
+    return fail(FMM_ERR_ARG, "order %d outside [0, %d] for the static workspace", order, kStaticMaxOrder);
+  if (leaf != 2 && leaf != 4 && leaf != 8) return fail(FMM_ERR_ARG, "leaf %d not in {2, 4, 8}", leaf);
+  const int d3[3] = {grid->nx, grid->ny, grid->nz};
+  for (int q = 0; q < 3; ++q) {
+    if (d3[q] <= 0) return fail(FMM_ERR_ARG, "grid extent %d must be positive", d3[q]);
+    if (d3[q] % leaf) return fail(FMM_ERR_ARG, "grid extent %d is not a multiple of leaf %d", d3[q], leaf);
+    if (d3[q] > 4096) return fail(FMM_ERR_ARG, "grid extent %d too large for the static workspace", d3[q]);
+  }
+  if (!(grid->dx > 0.0) || !std::isfinite(grid->dx)) return fail(FMM_ERR_ARG, "dx must be positive and finite");
+  if (!std::isfinite(grid->G)) return fail(FMM_ERR_ARG, "G must be finite");
+  if (!rho || !phi) return fail(FMM_ERR_ARG, "rho and phi must be non-NULL");
+  if (!aligned16(rho) || !aligned16(phi) || (accel && !aligned16(accel)))
+    return fail(FMM_ERR_ARG, "device pointers must be 16-byte aligned");
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) return fail(FMM_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  StaticSlot& slot = g_static_slots[dev];
+  if (!slot.ptr) {
+    void* addr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&addr, g_static_workspace);
+    if (e != cudaSuccess || !addr)
+      return fail(FMM_ERR_CUDA, "cudaGetSymbolAddress of the static workspace failed: %s", cudaGetErrorString(e));
+    slot.ptr = static_cast<unsigned char*>(addr);
+  }
+  std::unique_ptr<fmm_plan_s> P(new (std::nothrow) fmm_plan_s());
+  if (!P) return fail(FMM_ERR_ALLOC, "host allocation failed");
+  P->static_base = slot.ptr;
+  P->static_cap = kStaticWorkspaceBytes;
+  P->no_split = true;  // no neighbour-split scratch
+  const int key[5] = {order, leaf, d3[0], d3[1], d3[2]};
+  P->static_keep_tables = std::equal(key, key + 5, slot.key);
+  fmm_opts o;
+  fmm_default_opts(&o);  // FP32 on the CUDA cores
+  fmm_status st = plan_init(P.get(), d3, grid->dx, grid->G, order, leaf, o, s, dev);
+  if (st != FMM_OK) {
+    for (int& k : slot.key) k = -1;  // the tables may be half written
+    return st;
+  }
+  std::copy(key, key + 5, slot.key);
+  // plan_init cleared the arena; the flag word is kept with the tables
+  CUDA_TRY(cudaMemsetAsync(P->d_flag, 0, sizeof(int), s));
+  st = run_solve<float>(P.get(), static_cast<const float*>(rho), static_cast<float*>(phi),
+                        static_cast<float*>(accel), s);
+  // nothing of P was allocated on the device: no release
+  return st;
+}
