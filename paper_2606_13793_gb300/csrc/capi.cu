@@ -904,13 +904,19 @@ struct StageTimer {
 // Per-level dispatch helpers (a level's expansions are FP64 or FP32).
 fmm_status do_m2m(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s) {
   const Level &c = P->lev[l], &q = P->lev[l - 1];
+  const bool planes = q.tc && P->tc_kind == TC_BF16X3;
+  void* hi = planes ? P->arena + q.hi_off : nullptr;
+  void* lo = planes ? P->arena + q.lo_off : nullptr;
   cudaError_t e;
   if (c.f64)
-    e = launch_m2m<double, double>(tt, c, static_cast<const double*>(P->M(l)), q, static_cast<double*>(P->M(l - 1)), s);
+    e = launch_m2m<double, double>(tt, c, static_cast<const double*>(P->M(l)), q, static_cast<double*>(P->M(l - 1)),
+                                   nullptr, nullptr, s);
   else if (q.f64)
-    e = launch_m2m<float, double>(tt, c, static_cast<const float*>(P->M(l)), q, static_cast<double*>(P->M(l - 1)), s);
+    e = launch_m2m<float, double>(tt, c, static_cast<const float*>(P->M(l)), q, static_cast<double*>(P->M(l - 1)),
+                                  nullptr, nullptr, s);
   else
-    e = launch_m2m<float, float>(tt, c, static_cast<const float*>(P->M(l)), q, static_cast<float*>(P->M(l - 1)), s);
+    e = launch_m2m<float, float>(tt, c, static_cast<const float*>(P->M(l)), q, static_cast<float*>(P->M(l - 1)), hi,
+                                 lo, s);
   CUDA_TRY(e);
   return FMM_OK;
 }
@@ -972,24 +978,16 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
   // upward pass
   {
     StageTimer t(P, ST_P2M, s);
-    CUDA_TRY(launch_p2m<T>(tt, rho, P->dims, P->lev[L], static_cast<T*>(P->M(L)), rho_box, s));
-  }
-  if (P->near_tc) {
-    StageTimer t(P, ST_SPLIT, s);
-    CUDA_TRY(launch_split_bf16(reinterpret_cast<const float*>(rho_box), P->arena + P->rho_hi_off,
-                               P->arena + P->rho_lo_off, (size_t)P->ncell(), s));
+    const Level& lf = P->lev[L];
+    const bool mplanes = lf.tc && P->tc_kind == TC_BF16X3;
+    CUDA_TRY(launch_p2m<T>(tt, rho, P->dims, lf, static_cast<T*>(P->M(L)), P->near_tc ? nullptr : rho_box,
+                           mplanes ? P->arena + lf.hi_off : nullptr, mplanes ? P->arena + lf.lo_off : nullptr,
+                           P->near_tc ? P->arena + P->rho_hi_off : nullptr,
+                           P->near_tc ? P->arena + P->rho_lo_off : nullptr, s));
   }
   for (int l = L; l >= 3; --l) {
     StageTimer t(P, ST_M2M, s);
     if ((st = do_m2m(P, tt, l, s))) return st;
-  }
-  for (int l = 2; l <= L; ++l) {
-    const Level& lv = P->lev[l];
-    if (lv.tc && P->tc_kind == TC_BF16X3) {
-      StageTimer t(P, ST_SPLIT, s);
-      CUDA_TRY(launch_split_bf16(static_cast<const float*>(P->M(l)), P->arena + lv.hi_off, P->arena + lv.lo_off,
-                                 (size_t)lv.npar * 8 * P->nc, s));
-    }
   }
   // downward pass
   if (L < 2) {
@@ -1140,10 +1138,8 @@ int fmm_solve_launches(fmm_plan_t P, int with_accel) {
   if (L < 2) n += 1;                    // zero the leaf locals
   for (int l = 2; l <= L; ++l) {
     n += 2;                             // L2L (or zero) + M2L
-    if (P->lev[l].tc && P->tc_kind == TC_BF16X3) n += 1;  // hi/lo split
     if (P->split_level(l)) n += 1;      // reduction of the neighbour partials
   }
-  if (P->near_tc) n += 1;  // density hi/lo split
   n += 2;                               // near field + leaf finish
   if (with_accel) n += 1;
   return n;

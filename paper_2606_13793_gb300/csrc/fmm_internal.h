@@ -87,11 +87,16 @@ struct TreeTables {
   int p, nc, b;
 };
 
+// P2M: Mleaf always; rho_box (FP32/FP64 near field) and the bf16 hi/lo planes
+// (Mhi/Mlo for a tensor-core leaf level, rho_hi/rho_lo for the tensor-core
+// near field) when non-NULL.
 template <typename T>
 cudaError_t launch_p2m(const TreeTables& t, const T* rho, const int dims[3], const Level& leaf, T* Mleaf, T* rho_box,
-                       cudaStream_t s);
+                       void* Mhi, void* Mlo, void* rho_hi, void* rho_lo, cudaStream_t s);
+// M2M into the parent level; Mhi/Mlo (bf16 planes of the parent) when non-NULL.
 template <typename Tc, typename Tp>
-cudaError_t launch_m2m(const TreeTables& t, const Level& child, const Tc* Mc, const Level& par, Tp* Mp, cudaStream_t s);
+cudaError_t launch_m2m(const TreeTables& t, const Level& child, const Tc* Mc, const Level& par, Tp* Mp, void* Mhi,
+                       void* Mlo, cudaStream_t s);
 template <typename Tp, typename Tc>
 cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, const Level& child, Tc* Lc, cudaStream_t s);
 template <typename T>

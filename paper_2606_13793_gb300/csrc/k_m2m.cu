@@ -1,0 +1,80 @@
+// M2M on the CUDA cores (see tree_common.cuh for the layout and conventions).
+#include <cuda_bf16.h>
+
+#include "tree_common.cuh"
+
+namespace fmmgb {
+namespace {
+using namespace tree;
+
+// ---------------------------------------------------------------------------
+// M2M (Sec. 2.1, eq. M2M_general, child centre -> parent centre), scaled:
+//   Mt_alpha(P) = 2^-|alpha| sum_children sum_{beta <= alpha} C(alpha,beta) (+-1/2)^(alpha-beta) Mt_beta(C)
+// Each thread shifts one child; the 8 siblings are summed with shuffles.
+template <int P, typename Tc, typename Tp>
+__global__ void __launch_bounds__(kThreads) m2m_kernel(Level child, const Tc* __restrict__ Mc, Level par,
+                                                       Tp* __restrict__ Mp, __nv_bfloat16* __restrict__ Mhi,
+                                                       __nv_bfloat16* __restrict__ Mlo) {
+  constexpr int NC = ncoef_c(P);
+  const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long p = t >> 3;
+  const int c = (int)(t & 7);
+  const bool live = p < child.npar;  // child.npar == par.nbox
+  Tp M[NC];
+  const Tc* src = Mc + (live ? p : 0) * 8 * NC + c;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) M[k] = live ? Tp(src[k * 8]) : Tp(0);
+  Tp dp[P + 1];
+  powers<P, Tp>(half_offset<Tp>(c, 0), dp);
+  shift_up<P, 0, Tp>(M, dp);
+  powers<P, Tp>(half_offset<Tp>(c, 1), dp);
+  shift_up<P, 1, Tp>(M, dp);
+  powers<P, Tp>(half_offset<Tp>(c, 2), dp);
+  shift_up<P, 2, Tp>(M, dp);
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    Tp v = M[k];
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    M[k] = v;
+  }
+  if (!live) return;
+  // box p of the parent level, inside its own parent block
+  const int px = (int)(p % par.n[0]);
+  const int py = (int)((p / par.n[0]) % par.n[1]);
+  const int pz = (int)(p / ((long long)par.n[0] * par.n[1]));
+  const long long gp = ((long long)(pz >> 1) * par.np[1] + (py >> 1)) * par.np[0] + (px >> 1);
+  const int cp = (px & 1) | ((py & 1) << 1) | ((pz & 1) << 2);
+  Tp* dst = Mp + gp * 8 * NC + cp;
+  // sibling lanes share the writes: lane c stores coefficients c, c+8, ...
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    if ((k & 7) != c) continue;
+    const int n = (k >= 1) + (k >= 4) + (k >= 10) + (k >= 20) + (k >= 35) + (k >= 56) + (k >= 84) + (k >= 120);
+    const Tp v = M[k] * Tp(1.0 / (double)(1 << n));  // 2^-|alpha|
+    dst[k * 8] = v;
+    if (Mhi) store_split(Mhi, Mlo, (size_t)(gp * 8 * NC + cp + k * 8), v);
+  }
+}
+
+}  // namespace
+
+template <typename Tc, typename Tp>
+cudaError_t launch_m2m(const TreeTables& t, const Level& child, const Tc* Mc, const Level& par, Tp* Mp, void* Mhi,
+                       void* Mlo, cudaStream_t s) {
+  const long long threads = child.npar * 8;
+  if (threads == 0) return cudaSuccess;
+  FMM_ORDER_SWITCH(t.p, (m2m_kernel<PP, Tc, Tp><<<grid_threads(threads), kThreads, 0, s>>>(
+                            child, Mc, par, Mp, static_cast<__nv_bfloat16*>(Mhi), static_cast<__nv_bfloat16*>(Mlo))));
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_m2m<float, float>(const TreeTables&, const Level&, const float*, const Level&, float*,
+                                              void*, void*, cudaStream_t);
+template cudaError_t launch_m2m<double, double>(const TreeTables&, const Level&, const double*, const Level&,
+                                                double*, void*, void*, cudaStream_t);
+template cudaError_t launch_m2m<float, double>(const TreeTables&, const Level&, const float*, const Level&, double*,
+                                               void*, void*, cudaStream_t);
+
+}  // namespace fmmgb

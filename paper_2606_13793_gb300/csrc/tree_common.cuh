@@ -1,0 +1,140 @@
+// Shared helpers of the tree kernels (k_p2m.cu, k_m2m.cu, k_l2l.cu, k_leaf.cu):
+// P2M, M2M, L2L and the leaf evaluation on the CUDA cores.
+//
+// One thread owns one box and keeps its expansion in registers: the order p
+// is a template parameter, so every coefficient index is a compile-time
+// constant.  Threads are numbered (parent box, child) with the child fastest,
+// so a warp covers 4 parent blocks and the parent-blocked arrays
+// ([coef][child], 8*nc contiguous values per parent) are read and written as
+// full 32-byte sectors.  The translations are separable per axis:
+//   * P2M / L2P factorise (x - c)^alpha per axis (~b^3 (p+1) * 3 multiply-adds
+//     per box instead of b^3 * nc);
+//   * M2M / L2L shift one axis at a time, in place, with the half-box offset
+//     d = +-1/2 (child units), then siblings are summed by warp shuffles.
+// Optional bf16 hi/lo planes (hi = rn(x), lo = rn(x - hi)) are written next to
+// the FP32 values for levels whose M2L runs on the tensor cores, and for the
+// box-blocked density the tensor-core near field reads.
+#include <cuda_bf16.h>
+
+#pragma once
+#include "fmm_internal.h"
+
+namespace fmmgb {
+namespace tree {
+
+constexpr int kThreads = 256;  // 32 parents x 8 children
+
+__host__ __device__ constexpr int ncoef_c(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+// Index of multi-index (a, b, c) in the canonical order (total order n, then
+// a descending, then b descending).
+__host__ __device__ constexpr int cidx(int a, int b, int c) {
+  return (a + b + c) * (a + b + c + 1) * (a + b + c + 2) / 6 + (b + c) * (b + c + 1) / 2 + c;
+}
+
+__host__ __device__ constexpr int binom_c(int n, int k) {
+  int r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_split(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t i, T x) {
+  const float f = (float)x;
+  const __nv_bfloat16 h = __float2bfloat16_rn(f);
+  hi[i] = h;
+  lo[i] = __float2bfloat16_rn(f - __bfloat162float(h));
+}
+
+// In-place upward (multipole) shift along axis Q by d:
+//   M'_{..a..} = sum_{a' <= a} C(a, a') d^(a - a') M_{..a'..}
+template <int P, int Q, typename T>
+__device__ __forceinline__ void shift_up(T (&M)[ncoef_c(P)], const T (&dp)[P + 1]) {
+#pragma unroll
+  for (int u = 0; u <= P; ++u)
+#pragma unroll
+    for (int v = 0; u + v <= P; ++v)
+#pragma unroll
+      for (int a = P - u - v; a >= 1; --a) {
+        T s = M[Q == 0 ? cidx(a, u, v) : (Q == 1 ? cidx(u, a, v) : cidx(u, v, a))];
+#pragma unroll
+        for (int k = 0; k < a; ++k) {
+          const int id = Q == 0 ? cidx(k, u, v) : (Q == 1 ? cidx(u, k, v) : cidx(u, v, k));
+          s = fma(T(binom_c(a, k)) * dp[a - k], M[id], s);
+        }
+        M[Q == 0 ? cidx(a, u, v) : (Q == 1 ? cidx(u, a, v) : cidx(u, v, a))] = s;
+      }
+}
+
+// In-place downward (local) shift along axis Q by d:
+//   L'_{..a..} = sum_{a' >= a} C(a', a) d^(a' - a) L_{..a'..}
+template <int P, int Q, typename T>
+__device__ __forceinline__ void shift_down(T (&L)[ncoef_c(P)], const T (&dp)[P + 1]) {
+#pragma unroll
+  for (int u = 0; u <= P; ++u)
+#pragma unroll
+    for (int v = 0; u + v <= P; ++v)
+#pragma unroll
+      for (int a = 0; a < P - u - v; ++a) {
+        T s = L[Q == 0 ? cidx(a, u, v) : (Q == 1 ? cidx(u, a, v) : cidx(u, v, a))];
+#pragma unroll
+        for (int k = a + 1; k <= P - u - v; ++k) {
+          const int id = Q == 0 ? cidx(k, u, v) : (Q == 1 ? cidx(u, k, v) : cidx(u, v, k));
+          s = fma(T(binom_c(k, a)) * dp[k - a], L[id], s);
+        }
+        L[Q == 0 ? cidx(a, u, v) : (Q == 1 ? cidx(u, a, v) : cidx(u, v, a))] = s;
+      }
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void powers(T x, T (&dp)[P + 1]) {
+  dp[0] = T(1);
+#pragma unroll
+  for (int k = 1; k <= P; ++k) dp[k] = dp[k - 1] * x;
+}
+
+// Child c of a parent box sits at +-1/2 child box along each axis.
+template <typename T>
+__device__ __forceinline__ T half_offset(int c, int q) {
+  return ((c >> q) & 1) ? T(0.5) : T(-0.5);
+}
+
+struct Box {
+  long long par;  // parent block index
+  int c;          // child index
+  int x, y, z;    // box coordinates at the child level
+  bool real;      // inside the level's extent
+};
+
+__device__ __forceinline__ Box box_of(const Level& lv, long long t) {
+  Box B;
+  B.par = t >> 3;
+  B.c = (int)(t & 7);
+  const int px = (int)(B.par % lv.np[0]);
+  const int py = (int)((B.par / lv.np[0]) % lv.np[1]);
+  const int pz = (int)(B.par / ((long long)lv.np[0] * lv.np[1]));
+  B.x = 2 * px + (B.c & 1);
+  B.y = 2 * py + ((B.c >> 1) & 1);
+  B.z = 2 * pz + (B.c >> 2);
+  B.real = B.par < lv.npar && B.x < lv.n[0] && B.y < lv.n[1] && B.z < lv.n[2];
+  return B;
+}
+
+inline unsigned grid_threads(long long threads) { return (unsigned)((threads + kThreads - 1) / kThreads); }
+
+#define FMM_ORDER_SWITCH(p, ...)                          \
+  switch (p) {                                            \
+    case 0: { constexpr int PP = 0; __VA_ARGS__; } break; \
+    case 1: { constexpr int PP = 1; __VA_ARGS__; } break; \
+    case 2: { constexpr int PP = 2; __VA_ARGS__; } break; \
+    case 3: { constexpr int PP = 3; __VA_ARGS__; } break; \
+    case 4: { constexpr int PP = 4; __VA_ARGS__; } break; \
+    case 5: { constexpr int PP = 5; __VA_ARGS__; } break; \
+    case 6: { constexpr int PP = 6; __VA_ARGS__; } break; \
+    case 7: { constexpr int PP = 7; __VA_ARGS__; } break; \
+    case 8: { constexpr int PP = 8; __VA_ARGS__; } break; \
+    default: return cudaErrorInvalidValue;                \
+  }
+
+}  // namespace tree
+}  // namespace fmmgb
