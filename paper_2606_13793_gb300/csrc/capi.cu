@@ -386,96 +386,127 @@ float tf32_rn(double w) {
 // shared-memory image the MMA reads: rows of 128 B, 16-byte chunks swizzled
 // by (row mod 8), bf16 hi plane then lo plane (or one TF32 plane).
 struct TcHost {
-  std::vector<TcGroup> groups;
-  std::vector<TcIter> iters;
-  std::vector<TcStep> steps;
   TcPass pass[kTcMaxPasses];
   int npass = 0;
   std::vector<unsigned char> W;
 };
 
 // A column group before packing: output columns [col0, col0 + ncols) that
-// share one reduction prefix of length K.
+// share one reduction prefix of length K.  Groups come in non-increasing K.
 struct TcCols {
   int col0, ncols, K;
 };
 
-// Packs passes, iterations and weight tiles for groups `gs`; `entry(d, k, n)`
-// gives one weight of the contraction.
+// Packs passes and weight tiles for groups `gs`; `entry(d, k, n)` gives one
+// weight of the contraction.  Tiles are written in the exact shared-memory
+// image the MMA reads: rows of 128 B, 16-byte chunks swizzled by (row mod 8),
+// bf16 hi plane then lo plane (or one TF32 plane).
+uint32_t host_idesc(int kind, int n) {
+  const uint32_t ab = kind == TC_TF32 ? 2u : 1u;  // TF32 : BF16 operands, F32 accumulate, K-major, M = 128
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+// Packs passes, MMA spans and weight tiles for groups `gs`; `entry(d, k, n)`
+// gives one weight of the contraction.  Tiles are written in the exact
+// shared-memory image the MMA reads: rows of 128 B, 16-byte chunks swizzled by
+// (row mod 8), bf16 hi plane then lo plane (or one TF32 plane).
 template <typename Entry>
 bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entry, TcHost& H) {
   const int chunk = kind == TC_BF16X3 ? 64 : 32;  // reduction values per 128-byte chunk
   const int kstep = chunk / 4;
   const int esz = kind == TC_BF16X3 ? 2 : 4;
   const int planes = kind == TC_BF16X3 ? 2 : 1;
-  H.groups.clear(), H.iters.clear(), H.steps.clear(), H.W.clear();
+  H.W.clear();
   H.npass = 0;
   size_t gi = 0;
   while (gi < gs.size()) {
     if (H.npass == kTcMaxPasses) return false;
     TcPass& P = H.pass[H.npass++];
-    P.g0 = (int)H.groups.size();
+    std::memset(&P, 0, sizeof(P));
     int cols = 0, kmax = 0;
-    std::vector<int> Kg;
-    while (gi < gs.size()) {
+    std::vector<int> K;
+    while (gi < gs.size() && P.ng < kTcMaxGroups) {
       const int nm = (gs[gi].ncols + 15) / 16 * 16;
       if (cols + nm > 512) break;
-      H.groups.push_back({nm, cols, gs[gi].col0, gs[gi].ncols});
-      Kg.push_back(gs[gi].K);
+      if (P.ng > 0 && gs[gi].K > K.back()) return false;  // prefixes must shrink
+      P.out_tmem[P.ng] = cols;
+      P.out_col0[P.ng] = gs[gi].col0;
+      P.out_ncols[P.ng] = gs[gi].ncols;
+      P.out_nmma[P.ng] = nm;
+      K.push_back(gs[gi].K);
       kmax = std::max(kmax, gs[gi].K);
       cols += nm;
+      ++P.ng;
       ++gi;
     }
-    P.ng = (int)H.groups.size() - P.g0;
     if (P.ng == 0) return false;
     int alloc = 32;
     while (alloc < cols) alloc *= 2;
     P.tmem_cols = alloc;
-    P.iter0 = (int)H.iters.size();
-    const int nchunks = (kmax + chunk - 1) / chunk;
+    P.nchunks = (kmax + chunk - 1) / chunk;
+    if (P.nchunks > kTcMaxChunks) return false;
+    // spans per chunk, their tile offsets inside one neighbour block
+    int ns = 0, off = 0;
+    std::vector<std::vector<int>> span_groups;  // groups of each span (global span index)
+    for (int j = 0; j < P.nchunks; ++j) {
+      P.span0[j] = ns;
+      int g = 0;
+      while (g < P.ng && K[g] > j * chunk) {
+        const int ks = std::min(4, (K[g] - j * chunk + kstep - 1) / kstep);
+        if (ns == kTcMaxSpans) return false;
+        TcSpan& S = P.span[ns];
+        S.tmem_col = P.out_tmem[g];
+        S.n = 0;
+        S.ksteps = ks;
+        std::vector<int> members;
+        while (g < P.ng && K[g] > j * chunk && S.n + P.out_nmma[g] <= kTcMaxSpanN &&
+               std::min(4, (K[g] - j * chunk + kstep - 1) / kstep) == ks) {
+          S.n += P.out_nmma[g];
+          members.push_back(g);
+          ++g;
+        }
+        if (members.empty()) return false;
+        S.w_off = off;
+        S.idesc = host_idesc(kind, S.n);
+        off += S.n * 128 * planes;
+        span_groups.push_back(members);
+        ++ns;
+      }
+    }
+    P.span0[P.nchunks] = ns;
+    P.bytes_per_d = off;
+    P.w_base = (long long)H.W.size();
+    H.W.resize(H.W.size() + (size_t)27 * P.bytes_per_d, 0);
     for (int d = 0; d < 27; ++d)
-      for (int j = 0; j < nchunks; ++j) {
-        TcIter I;
-        I.d = d;
-        I.chunk = j;
-        I.step0 = (int)H.steps.size();
-        for (int g = 0; g < P.ng; ++g) {
-          const TcGroup Gp = H.groups[P.g0 + g];
-          const int K = Kg[g];
-          if (K <= j * chunk) continue;
-          TcStep S;
-          S.group = (short)g;
-          S.ksteps = (short)std::min(4, (K - j * chunk + kstep - 1) / kstep);
-          S.b_off = (long long)H.W.size();
-          S.b_bytes = Gp.n_mma * 128 * planes;
-          H.W.resize(H.W.size() + S.b_bytes, 0);
-          unsigned char* tile = H.W.data() + S.b_off;
-          for (int r = 0; r < Gp.out_ncols; ++r) {
-            const int n = Gp.out_col0 + r;
-            for (int e = 0; e < S.ksteps * kstep; ++e) {
-              const int k = j * chunk + e;
-              if (k >= K) continue;
-              const double w = entry(d, k, n);
-              if (w == 0.0) continue;
-              const int byte = e * esz;
-              const size_t off = (size_t)r * 128 + (size_t)((((byte >> 4) ^ (r & 7)) << 4) | (byte & 15));
-              if (kind == TC_BF16X3) {
-                const uint16_t h = bf16_rn((float)w);
-                const uint16_t l = bf16_rn((float)(w - (double)bf16_to_f(h)));
-                std::memcpy(tile + off, &h, 2);
-                std::memcpy(tile + (size_t)Gp.n_mma * 128 + off, &l, 2);
-              } else {
-                const float t = tf32_rn(w);
-                std::memcpy(tile + off, &t, 4);
+      for (int j = 0; j < P.nchunks; ++j)
+        for (int si = P.span0[j]; si < P.span0[j + 1]; ++si) {
+          const TcSpan& S = P.span[si];
+          unsigned char* tile = H.W.data() + P.w_base + (size_t)d * P.bytes_per_d + S.w_off;
+          int row0 = 0;
+          for (int g : span_groups[si]) {
+            for (int r = 0; r < P.out_ncols[g]; ++r) {
+              const int n = P.out_col0[g] + r, row = row0 + r;
+              for (int e = 0; e < S.ksteps * kstep; ++e) {
+                const int k = j * chunk + e;
+                if (k >= K[g]) continue;
+                const double w = entry(d, k, n);
+                if (w == 0.0) continue;
+                const int byte = e * esz;
+                const size_t o = (size_t)row * 128 + (size_t)((((byte >> 4) ^ (row & 7)) << 4) | (byte & 15));
+                if (kind == TC_BF16X3) {
+                  const uint16_t h = bf16_rn((float)w);
+                  const uint16_t l = bf16_rn((float)(w - (double)bf16_to_f(h)));
+                  std::memcpy(tile + o, &h, 2);
+                  std::memcpy(tile + (size_t)S.n * 128 + o, &l, 2);
+                } else {
+                  const float t = tf32_rn(w);
+                  std::memcpy(tile + o, &t, 4);
+                }
               }
             }
+            row0 += P.out_nmma[g];
           }
-          H.steps.push_back(S);
         }
-        I.nstep = (int)H.steps.size() - I.step0;
-        H.iters.push_back(I);
-      }
-    P.niter = (int)H.iters.size() - P.iter0;
   }
   return true;
 }
@@ -729,16 +760,8 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     if (anytc) {
       TcHost H;
       if (!build_tc(P->mi, tt, P->tc_kind, H)) return cleanup(fail(FMM_ERR_UNSUPPORTED, "order too high for the tensor-core schedule"));
-      TcIter* di = nullptr;
-      TcStep* ds = nullptr;
-      TcGroup* dg = nullptr;
       unsigned char* dw = nullptr;
-      if ((st = P->upload(H.iters, &di, s)) || (st = P->upload(H.steps, &ds, s)) || (st = P->upload(H.groups, &dg, s)) ||
-          (st = P->upload(H.W, &dw, s)))
-        return cleanup(st);
-      P->tc.iters = di;
-      P->tc.steps = ds;
-      P->tc.groups = dg;
+      if ((st = P->upload(H.W, &dw, s))) return cleanup(st);
       P->tc.W = dw;
       P->tc.npass = H.npass;
       for (int i = 0; i < H.npass; ++i) P->tc.pass[i] = H.pass[i];
@@ -784,17 +807,9 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     // bf16x3 in both tensor-core precisions: a TF32 near field would carry
     // ~3e-4 relative error on its (same-signed) sums
     if (!build_tc_near(P->b, TC_BF16X3, H)) return cleanup(fail(FMM_ERR_UNSUPPORTED, "near-field schedule failed"));
-    TcIter* di = nullptr;
-    TcStep* ds = nullptr;
-    TcGroup* dg = nullptr;
     unsigned char* dw = nullptr;
-    if ((st = P->upload(H.iters, &di, s)) || (st = P->upload(H.steps, &ds, s)) || (st = P->upload(H.groups, &dg, s)) ||
-        (st = P->upload(H.W, &dw, s)))
-      return cleanup(st);
+    if ((st = P->upload(H.W, &dw, s))) return cleanup(st);
     TcLaunch& T = P->tcn;
-    T.iters = di;
-    T.steps = ds;
-    T.groups = dg;
     T.W = dw;
     T.npass = H.npass;
     for (int i = 0; i < H.npass; ++i) T.pass[i] = H.pass[i];
@@ -971,10 +986,6 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
   T* rho_box = reinterpret_cast<T*>(P->arena + P->rho_box_off);
   T* near_box = reinterpret_cast<T*>(P->arena + P->near_off);
   fmm_status st;
-  {
-    StageTimer t(P, ST_CHECK, s);
-    CUDA_TRY(launch_check_finite<T>(rho, (size_t)P->ncell(), P->d_flag, s));
-  }
   // upward pass
   {
     StageTimer t(P, ST_P2M, s);
@@ -983,7 +994,7 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
     CUDA_TRY(launch_p2m<T>(tt, rho, P->dims, lf, static_cast<T*>(P->M(L)), P->near_tc ? nullptr : rho_box,
                            mplanes ? P->arena + lf.hi_off : nullptr, mplanes ? P->arena + lf.lo_off : nullptr,
                            P->near_tc ? P->arena + P->rho_hi_off : nullptr,
-                           P->near_tc ? P->arena + P->rho_lo_off : nullptr, s));
+                           P->near_tc ? P->arena + P->rho_lo_off : nullptr, P->d_flag, s));
   }
   for (int l = L; l >= 3; --l) {
     StageTimer t(P, ST_M2M, s);
@@ -1133,7 +1144,7 @@ int fmm_plan_near_on_tensor_cores(fmm_plan_t P) { return (P && P->near_tc) ? 1 :
 int fmm_solve_launches(fmm_plan_t P, int with_accel) {
   if (!P) return -1;
   const int L = P->L;
-  int n = 2;                            // finite check + P2M
+  int n = 1;                            // P2M (with the finite check)
   n += std::max(0, L - 2);              // M2M for l = L .. 3
   if (L < 2) n += 1;                    // zero the leaf locals
   for (int l = 2; l <= L; ++l) {

@@ -89,10 +89,10 @@ struct TreeTables {
 
 // P2M: Mleaf always; rho_box (FP32/FP64 near field) and the bf16 hi/lo planes
 // (Mhi/Mlo for a tensor-core leaf level, rho_hi/rho_lo for the tensor-core
-// near field) when non-NULL.
+// near field) when non-NULL.  Sets bit 0 of *flag for a non-finite density.
 template <typename T>
 cudaError_t launch_p2m(const TreeTables& t, const T* rho, const int dims[3], const Level& leaf, T* Mleaf, T* rho_box,
-                       void* Mhi, void* Mlo, void* rho_hi, void* rho_lo, cudaStream_t s);
+                       void* Mhi, void* Mlo, void* rho_hi, void* rho_lo, int* flag, cudaStream_t s);
 // M2M into the parent level; Mhi/Mlo (bf16 planes of the parent) when non-NULL.
 template <typename Tc, typename Tp>
 cudaError_t launch_m2m(const TreeTables& t, const Level& child, const Tc* Mc, const Level& par, Tp* Mp, void* Mhi,
@@ -125,36 +125,47 @@ cudaError_t launch_export_level(const T* src, const Level& lv, int what, double 
 // row.  A operand: TMA tile of the (shifted) parent rows; B operand: a
 // pre-swizzled weight tile per (neighbour, chunk, group).
 constexpr int kTcMaxPasses = 4;
-constexpr int kTcTileX = 8, kTcTileY = 4, kTcTileZ = 4;  // 128 parents
+// 128 rows per tile as 8 (x) x 16 (y) x 1 (z): the activation stage is an
+// 8 x 18 x 1 box (y halo of one row each side), in which the three y-shifts
+// of a neighbour column are contiguous 128-row windows.
+constexpr int kTcTileX = 8, kTcTileY = 16, kTcTileZ = 1;
+constexpr int kTcBoxY = kTcTileY + 2;
 constexpr int kTcMaxGroupN = 128;                         // B tile <= 128 rows
 
 enum TcKind { TC_BF16X3 = 0, TC_TF32 = 1 };
 
-struct TcGroup {
-  int n_mma;      // MMA N (multiple of 16)
-  int tmem_col;   // first TMEM column
-  int out_col0;   // first output column (beta*8 + child)
-  int out_ncols;  // real output columns (<= n_mma)
+constexpr int kTcMaxGroups = 8;     // column groups per pass
+constexpr int kTcMaxChunks = 48;    // 128-byte reduction chunks per neighbour
+constexpr int kTcMaxSpans = 96;     // MMA spans per pass (all chunks)
+constexpr int kTcMaxSpanN = 192;    // columns of one span (one MMA instruction)
+
+// One MMA instruction shape of a chunk: adjacent column groups that use the
+// chunk with the same number of K steps, merged so that each tcgen05.mma
+// carries as many columns as possible (an MMA costs at least ~55 issue
+// cycles, i.e. the math of N = 110 bf16 columns).
+struct TcSpan {
+  int tmem_col;    // first TMEM column
+  int n;           // MMA N (rows of the weight tile per plane)
+  int ksteps;      // MMA K steps in this chunk (1..4)
+  int w_off;       // byte offset of the tile inside the neighbour block
+  uint32_t idesc;  // instruction descriptor (kind, N, M = 128)
 };
-struct TcStep {       // one weight tile (neighbour, chunk, group)
-  long long b_off;    // byte offset in the weight buffer
-  int b_bytes;        // bytes (every plane)
-  short group;        // index into the pass's group slice
-  short ksteps;       // MMA K steps of this chunk for the group
-};
-struct TcIter {       // one activation tile (neighbour, chunk)
-  int d, chunk;
-  int step0, nstep;
-};
+
+// One pass of the schedule, passed by value (kernel parameter space), so the
+// producer and MMA threads never wait on a global load for their next step.
+// Weight tiles: offset(d, span) = w_base + d * bytes_per_d + span.w_off; one
+// tile = n rows x 128 B per plane (bf16 hi plane, then lo plane).
 struct TcPass {
-  int iter0, niter;
-  int g0, ng;
-  int tmem_cols;
+  int ng, nchunks, tmem_cols, bytes_per_d;
+  long long w_base;
+  int out_tmem[kTcMaxGroups];   // epilogue: TMEM column of the group
+  int out_col0[kTcMaxGroups];   // first output column (beta*8 + child)
+  int out_ncols[kTcMaxGroups];  // real output columns
+  int out_nmma[kTcMaxGroups];   // TMEM columns of the group (multiple of 16)
+  int span0[kTcMaxChunks + 1];  // spans of chunk j: span[span0[j] .. span0[j+1])
+  TcSpan span[kTcMaxSpans];
 };
 struct TcLaunch {
-  const TcIter* iters;
-  const TcStep* steps;
-  const TcGroup* groups;
   TcPass pass[kTcMaxPasses];
   int npass;
   const unsigned char* W;

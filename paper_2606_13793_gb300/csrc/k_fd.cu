@@ -31,6 +31,64 @@ __device__ __forceinline__ T fd_weight(int j, int off, int n) {
   return off == 0 ? T(1.5) : (off == -1 ? T(-2) : (off == -2 ? T(0.5) : T(0)));  // j == n-1
 }
 
+constexpr int kFdTX = 32, kFdTY = 8, kFdZC = 16;
+
+// 32 x 8 columns of cells per block, walking kFdZC cells along z: the x-y
+// neighbours come from a shared-memory tile with a 2-cell halo, the z
+// neighbours from a 5-value register window, so each value of phi is read
+// about 2.7 times from L2 and once from DRAM.
+template <typename T>
+__global__ void __launch_bounds__(kFdTX* kFdTY) fd_accel_tiled_kernel(const T* __restrict__ phi, int nx, int ny,
+                                                                      int nz, T inv_dx, T* __restrict__ accel) {
+  __shared__ T tile[kFdTY + 4][kFdTX + 4];
+  const long long n = (long long)nx * ny * nz;
+  const long long plane = (long long)nx * ny;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x0 = blockIdx.x * kFdTX, y0 = blockIdx.y * kFdTY, z0 = blockIdx.z * kFdZC;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool inside = x < nx && y < ny;
+  const long long col = (long long)y * nx + x;
+  T wx[5], wy[5];
+#pragma unroll
+  for (int o = -2; o <= 2; ++o) {
+    wx[o + 2] = fd_weight<T>(x, o, nx);
+    wy[o + 2] = fd_weight<T>(y, o, ny);
+  }
+  T w[5];  // phi at z-2 .. z+2 of this column
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int zz = z0 - 2 + q;
+    w[q + 1] = (inside && zz >= 0 && zz < nz) ? phi[(long long)zz * plane + col] : T(0);
+  }
+  const int z1 = min(z0 + kFdZC, nz);
+  for (int z = z0; z < z1; ++z) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w[q] = w[q + 1];
+    w[4] = (inside && z + 2 < nz) ? phi[(long long)(z + 2) * plane + col] : T(0);
+    for (int i = ty * kFdTX + tx; i < (kFdTY + 4) * (kFdTX + 4); i += kFdTX * kFdTY) {
+      const int lx = i % (kFdTX + 4), ly = i / (kFdTX + 4);
+      const int gx = x0 - 2 + lx, gy = y0 - 2 + ly;
+      tile[ly][lx] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? phi[(long long)z * plane + (long long)gy * nx + gx]
+                                                                 : T(0);
+    }
+    __syncthreads();
+    if (inside) {
+      T dx = T(0), dy = T(0), dz = T(0);
+#pragma unroll
+      for (int o = -2; o <= 2; ++o) {
+        dx = fma(wx[o + 2], tile[ty + 2][tx + 2 + o], dx);
+        dy = fma(wy[o + 2], tile[ty + 2 + o][tx + 2], dy);
+        dz = fma(fd_weight<T>(z, o, nz), w[o + 2], dz);
+      }
+      const long long c = (long long)z * plane + col;
+      accel[c] = -dx * inv_dx;
+      accel[n + c] = -dy * inv_dx;
+      accel[2 * n + c] = -dz * inv_dx;
+    }
+    __syncthreads();
+  }
+}
+
 // Grid: x blocks over a row, y = row index, z = slice (32-bit indexing).
 template <typename T>
 __global__ void fd_accel_kernel(const T* __restrict__ phi, int nx, int ny, int nz, T inv_dx, T* __restrict__ accel) {
@@ -111,8 +169,14 @@ dim3 row_grid(const int dims[3], int threads) {
 
 template <typename T>
 cudaError_t launch_fd_accel(const T* phi, const int dims[3], double inv_dx, T* accel, cudaStream_t s) {
-  const int th = dims[0] >= 256 ? 256 : ((dims[0] + 31) / 32) * 32;
-  fd_accel_kernel<T><<<row_grid(dims, th), th, 0, s>>>(phi, dims[0], dims[1], dims[2], (T)inv_dx, accel);
+  if (dims[1] > 65535 * kFdTY || dims[2] > 65535 * kFdZC) {
+    const int th = dims[0] >= 256 ? 256 : ((dims[0] + 31) / 32) * 32;
+    fd_accel_kernel<T><<<row_grid(dims, th), th, 0, s>>>(phi, dims[0], dims[1], dims[2], (T)inv_dx, accel);
+    return cudaGetLastError();
+  }
+  dim3 grid((unsigned)((dims[0] + kFdTX - 1) / kFdTX), (unsigned)((dims[1] + kFdTY - 1) / kFdTY),
+            (unsigned)((dims[2] + kFdZC - 1) / kFdZC));
+  fd_accel_tiled_kernel<T><<<grid, dim3(kFdTX, kFdTY), 0, s>>>(phi, dims[0], dims[1], dims[2], (T)inv_dx, accel);
   return cudaGetLastError();
 }
 

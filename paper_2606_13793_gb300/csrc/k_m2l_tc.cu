@@ -28,10 +28,12 @@
 namespace fmmgb {
 namespace {
 
-constexpr int kSA = 3;                                   // activation ring stages
-constexpr int kSB = 3;                                   // weight ring stages
-constexpr int kAStage = 2 * 128 * 128;                   // two planes of 128 rows x 128 B
-constexpr int kBStage = 2 * kTcMaxGroupN * 128;          // two planes of <= 128 rows x 128 B
+constexpr int kSA = 3;                                   // activation ring stages (both planes)
+constexpr int kSB = 4;                                   // weight ring slots (one plane each)
+constexpr int kARows = kTcTileX * kTcBoxY;               // 144 rows of one activation box
+constexpr int kAPlane = kARows * 128;                    // 18 KB, a multiple of 1024
+constexpr int kAStage = 2 * kAPlane;                     // hi and lo planes
+constexpr int kBStage = kTcMaxSpanN * 128;               // one plane of <= 192 rows x 128 B
 constexpr int kSmemBytes = kSA * kAStage + kSB * kBStage + 1024 /*barriers*/ + 1024 /*alignment*/;
 constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s per wait
 
@@ -110,12 +112,6 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: D = F32, A/B K-major, M = 128.
-__device__ __forceinline__ uint32_t make_idesc(int kind, int n) {
-  const uint32_t ab = kind == TC_TF32 ? 2u : 1u;  // TF32 : BF16
-  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-
 __device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -150,8 +146,30 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Issues the MMAs of one span: KS K steps of 32 bytes each (descriptor start
+// address + 2 per step), three products per step for bf16x3.
+template <int KIND, int KS>
+__device__ __forceinline__ void issue_span(uint32_t d, uint64_t a, uint64_t a_lo, uint64_t b, uint64_t b_lo,
+                                           uint32_t idesc, uint32_t acc0) {
+#pragma unroll
+  for (int k = 0; k < KS; ++k) {
+    const uint64_t o = 2ull * k;
+    if (KIND == TC_BF16X3) {
+      mma_f16(d, a + o, b + o, idesc, k == 0 ? acc0 : 1u);
+      mma_f16(d, a + o, b_lo + o, idesc, 1u);
+      mma_f16(d, a_lo + o, b + o, idesc, 1u);
+    } else {
+      mma_tf32(d, a + o, b + o, idesc, k == 0 ? acc0 : 1u);
+    }
+  }
+}
+
+template <int KIND>
 __global__ void __launch_bounds__(128, 1)
-    m2l_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, TcLaunch P) {
+    m2l_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
+                  const __grid_constant__ TcLaunch P) {
+  constexpr bool split = KIND == TC_BF16X3;
+  constexpr int chunk_elems = split ? 64 : 32;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -164,14 +182,12 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t* accum = b_empty + kSB;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
 
-  const TcPass pass = P.pass[blockIdx.y];
+  const TcPass& pass = P.pass[blockIdx.y];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntx = (P.grid[0] + kTcTileX - 1) / kTcTileX, nty = (P.grid[1] + kTcTileY - 1) / kTcTileY;
   const int ox = (blockIdx.x % ntx) * kTcTileX;
   const int oy = ((blockIdx.x / ntx) % nty) * kTcTileY;
   const int oz = (blockIdx.x / (ntx * nty)) * kTcTileZ;
-  const bool split = P.kind == TC_BF16X3;
-  const uint32_t a_plane = 128 * 128;  // bytes of one 128-row plane
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < kSA; ++i) mbar_init(&a_full[i], 1), mbar_init(&a_empty[i], 1);
@@ -192,101 +208,118 @@ __global__ void __launch_bounds__(128, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
+    // Order: neighbour column (dx, dz), chunk j, then dy and the chunk's spans.
+    // One activation box (rows y-1 .. y+16 of the shifted x/z column) serves
+    // the three dy neighbours.
     uint32_t ai = 0, bi = 0;
     bool ok = true;
-    for (int it = pass.iter0; ok && it < pass.iter0 + pass.niter; ++it) {
-      const TcIter I = P.iters[it];
-      const int dx = I.d % 3 - 1, dy = (I.d / 3) % 3 - 1, dz = I.d / 9 - 1;
-      const int sa = ai % kSA;
-      if (!(ok = mbar_wait(&a_empty[sa], ((ai / kSA) & 1) ^ 1, P.err, W_PROD_A))) break;
-      unsigned char* adst = a_ring + sa * kAStage;
-      const int cx = I.chunk * (split ? 64 : 32);
-      mbar_expect_tx(&a_full[sa], split ? 2 * a_plane : a_plane);
-      tma_load_4d(adst, &map_hi, &a_full[sa], cx, ox + dx, oy + dy, oz + dz);
-      if (split) tma_load_4d(adst + a_plane, &map_lo, &a_full[sa], cx, ox + dx, oy + dy, oz + dz);
-      ++ai;
-      for (int s = I.step0; s < I.step0 + I.nstep; ++s) {
-        const TcStep S = P.steps[s];
-        const int sb = bi % kSB;
-        if (!(ok = mbar_wait(&b_empty[sb], ((bi / kSB) & 1) ^ 1, P.err, W_PROD_B))) break;
-        mbar_expect_tx(&b_full[sb], (uint32_t)S.b_bytes);
-        bulk_load(b_ring + sb * kBStage, P.W + S.b_off, (uint32_t)S.b_bytes, &b_full[sb]);
-        ++bi;
+    const unsigned char* wpass = P.W + pass.w_base;
+    for (int xz = 0; ok && xz < 9; ++xz) {
+      const int dx = xz % 3 - 1, dz = xz / 3 - 1;
+      for (int j = 0; ok && j < pass.nchunks; ++j) {
+        const int sa = ai % kSA;
+        if (!(ok = mbar_wait(&a_empty[sa], ((ai / kSA) & 1) ^ 1, P.err, W_PROD_A))) break;
+        unsigned char* adst = a_ring + sa * kAStage;
+        mbar_expect_tx(&a_full[sa], split ? 2 * kAPlane : kAPlane);
+        tma_load_4d(adst, &map_hi, &a_full[sa], j * chunk_elems, ox + dx, oy - 1, oz + dz);
+        if (split) tma_load_4d(adst + kAPlane, &map_lo, &a_full[sa], j * chunk_elems, ox + dx, oy - 1, oz + dz);
+        ++ai;
+        const int s0 = pass.span0[j], s1 = pass.span0[j + 1];
+        for (int dy = 0; ok && dy < 3; ++dy) {
+          const unsigned char* wd = wpass + (long long)((dx + 1) + 3 * dy + 9 * (dz + 1)) * pass.bytes_per_d;
+          for (int si = s0; ok && si < s1; ++si) {
+            const uint32_t plane = (uint32_t)pass.span[si].n * 128;
+            const unsigned char* src = wd + pass.span[si].w_off;
+            for (int h = 0; h < (split ? 2 : 1); ++h) {  // hi plane, then lo plane: one slot each
+              const int sb = bi % kSB;
+              if (!(ok = mbar_wait(&b_empty[sb], ((bi / kSB) & 1) ^ 1, P.err, W_PROD_B))) break;
+              mbar_expect_tx(&b_full[sb], plane);
+              bulk_load(b_ring + sb * kBStage, src + h * plane, plane, &b_full[sb]);
+              ++bi;
+            }
+          }
+        }
       }
     }
     if (!ok) {
       // drain: never leave the CTA with copies in flight
-      for (uint32_t q = (ai > kSA ? ai - kSA : 0); q < ai; ++q) mbar_wait(&a_full[q % kSA], (q / kSA) & 1, P.err, W_DRAIN);
-      for (uint32_t q = (bi > kSB ? bi - kSB : 0); q < bi; ++q) mbar_wait(&b_full[q % kSB], (q / kSB) & 1, P.err, W_DRAIN);
+      for (uint32_t q = (ai > kSA ? ai - kSA : 0); q < ai; ++q)
+        mbar_wait(&a_full[q % kSA], (q / kSA) & 1, P.err, W_DRAIN);
+      for (uint32_t q = (bi > kSB ? bi - kSB : 0); q < bi; ++q)
+        mbar_wait(&b_full[q % kSB], (q / kSB) & 1, P.err, W_DRAIN);
     }
   } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer ----------------
+    // ---------------- MMA issuer (lean: descriptors precomputed per stage) ----------------
     uint32_t ai = 0, bi = 0;
     bool ok = true;
-    for (int it = pass.iter0; ok && it < pass.iter0 + pass.niter; ++it) {
-      const TcIter I = P.iters[it];
-      const int sa = ai % kSA;
-      if (!(ok = mbar_wait(&a_full[sa], (ai / kSA) & 1, P.err, W_MMA_A))) break;
-      tc_fence_after();
-      const uint32_t abase = smem_u32(a_ring + sa * kAStage);
-      for (int s = I.step0; s < I.step0 + I.nstep; ++s) {
-        const TcStep S = P.steps[s];
-        const TcGroup G = P.groups[pass.g0 + S.group];
-        const int sb = bi % kSB;
-        if (!(ok = mbar_wait(&b_full[sb], (bi / kSB) & 1, P.err, W_MMA_B))) break;
+    for (int xz = 0; ok && xz < 9; ++xz) {
+      for (int j = 0; ok && j < pass.nchunks; ++j) {
+        const int sa = ai % kSA;
+        if (!(ok = mbar_wait(&a_full[sa], (ai / kSA) & 1, P.err, W_MMA_A))) break;
         tc_fence_after();
-        const uint32_t bbase = smem_u32(b_ring + sb * kBStage);
-        const uint32_t bplane = (uint32_t)G.n_mma * 128;
-        const uint32_t idesc = make_idesc(P.kind, G.n_mma);
-        const uint32_t d = tmem + (uint32_t)G.tmem_col;
-        // chunk 0 of neighbour 0 opens every group's accumulator
-        const bool open = (I.d == 0 && I.chunk == 0);
-        for (int k = 0; k < S.ksteps; ++k) {
-          const uint32_t koff = 32u * k;  // 32 B per MMA K step (16 bf16 / 8 tf32)
-          const uint64_t a_hi = sw128_desc(abase + koff), b_hi = sw128_desc(bbase + koff);
-          const uint32_t acc0 = (open && k == 0) ? 0u : 1u;
-          if (split) {
-            const uint64_t a_lo = sw128_desc(abase + a_plane + koff), b_lo = sw128_desc(bbase + bplane + koff);
-            mma_f16(d, a_hi, b_hi, idesc, acc0);
-            mma_f16(d, a_hi, b_lo, idesc, 1u);
-            mma_f16(d, a_lo, b_hi, idesc, 1u);
-          } else {
-            mma_tf32(d, a_hi, b_hi, idesc, acc0);
+        const uint64_t a_desc = sw128_desc(smem_u32(a_ring + sa * kAStage));
+        const int s0 = pass.span0[j], s1 = pass.span0[j + 1];
+        for (int dy = 0; ok && dy < 3; ++dy) {
+          const uint64_t a = a_desc + (uint64_t)(dy * (kTcTileX * 128 / 16));  // 128-row window
+          const uint64_t a_lo = a + (uint64_t)(kAPlane / 16);
+          const uint32_t acc0 = (xz == 0 && j == 0 && dy == 0) ? 0u : 1u;  // the first step opens every group
+          for (int si = s0; ok && si < s1; ++si) {
+            const TcSpan& S = pass.span[si];
+            const int sb = bi % kSB;
+            const int sb2 = (bi + 1) % kSB;  // lo plane (bf16x3)
+            if (!(ok = mbar_wait(&b_full[sb], (bi / kSB) & 1, P.err, W_MMA_B))) break;
+            if (split && !(ok = mbar_wait(&b_full[sb2], ((bi + 1) / kSB) & 1, P.err, W_MMA_B))) break;
+            tc_fence_after();
+            const uint64_t b = sw128_desc(smem_u32(b_ring + sb * kBStage));
+            const uint64_t b_lo = sw128_desc(smem_u32(b_ring + sb2 * kBStage));
+            const uint32_t d = tmem + (uint32_t)S.tmem_col;
+            switch (S.ksteps) {
+              case 1: issue_span<KIND, 1>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
+              case 2: issue_span<KIND, 2>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
+              case 3: issue_span<KIND, 3>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
+              default: issue_span<KIND, 4>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
+            }
+            mma_commit(&b_empty[sb]);
+            if (split) mma_commit(&b_empty[sb2]);
+            bi += split ? 2 : 1;
           }
         }
-        mma_commit(&b_empty[sb]);
-        ++bi;
+        mma_commit(&a_empty[sa]);
+        ++ai;
       }
-      mma_commit(&a_empty[sa]);
-      ++ai;
     }
     mma_commit(accum);  // fires when every MMA issued above has completed
   }
   __syncwarp();
 
-  // ---------------- epilogue: TMEM -> registers -> L (accumulate) ----------------
+  // ---------------- epilogue: TMEM -> registers -> C ----------------
   int done = 0;
   if (lane == 0) done = mbar_wait(accum, 0, P.err, W_EPI) ? 1 : 0;
   done = __shfl_sync(0xffffffffu, done, 0);  // warp-uniform: tcgen05.ld is warp-collective
   if (done) {
     tc_fence_after();
     const int r = warp * 32 + lane;  // tile row = TMEM lane
-    const int x = ox + (r & 7), y = oy + ((r >> 3) & 3), z = oz + (r >> 5);
+    const int x = ox + (r & 7), y = oy + (r >> 3), z = oz;
     const bool valid = x < P.grid[0] && y < P.grid[1] && z < P.grid[2];
     float* crow = P.C + ((((long long)z * P.grid[1] + y) * P.grid[0] + x) * P.n_cols);
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    for (int g = pass.g0; g < pass.g0 + pass.ng; ++g) {
-      const TcGroup G = P.groups[g];
-      for (int c = 0; c < G.n_mma; c += 16) {
+    for (int g = 0; g < pass.ng; ++g) {
+      const int n_mma = pass.out_nmma[g], ncols = pass.out_ncols[g], col0 = pass.out_col0[g];
+      for (int c = 0; c < n_mma; c += 16) {
         float v[16];
         __syncwarp();  // tcgen05.ld is warp-collective: reconverge after the masked stores
-        tmem_ld16(tmem + lane_base + (uint32_t)(G.tmem_col + c), v);
-        if (valid) {
+        tmem_ld16(tmem + lane_base + (uint32_t)(pass.out_tmem[g] + c), v);
+        if (valid) {  // out_col0 and out_ncols are multiples of 8: whole float4s
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (c + j < G.out_ncols) {
-              float* o = crow + G.out_col0 + c + j;
-              *o = P.accumulate ? *o + v[j] : v[j];
+          for (int j = 0; j < 16; j += 4)
+            if (c + j < ncols) {
+              float4* o = reinterpret_cast<float4*>(crow + col0 + c + j);
+              float4 q = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+              if (P.accumulate) {
+                const float4 old = *o;
+                q.x += old.x, q.y += old.y, q.z += old.z, q.w += old.w;
+              }
+              *o = q;
             }
         }
       }
@@ -328,7 +361,7 @@ cudaError_t make_row_map(void* map_out, const void* base, int row_len, int elem_
   const cuuint64_t dims[4] = {(cuuint64_t)row_len, (cuuint64_t)grid[0], (cuuint64_t)grid[1], (cuuint64_t)grid[2]};
   const cuuint64_t row_bytes = (cuuint64_t)row_len * elem_bytes;
   const cuuint64_t strides[3] = {row_bytes, row_bytes * grid[0], row_bytes * grid[0] * grid[1]};
-  const cuuint32_t box[4] = {(cuuint32_t)box_inner, kTcTileX, kTcTileY, kTcTileZ};
+  const cuuint32_t box[4] = {(cuuint32_t)box_inner, kTcTileX, kTcBoxY, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = encode(reinterpret_cast<CUtensorMap*>(map_out),
                       elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
@@ -340,15 +373,22 @@ cudaError_t make_row_map(void* map_out, const void* base, int row_len, int elem_
 cudaError_t launch_m2l_tc(const TcLaunch& L, const void* map_hi, const void* map_lo, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(m2l_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(m2l_tc_kernel<TC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(m2l_tc_kernel<TC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int ntx = (L.grid[0] + kTcTileX - 1) / kTcTileX, nty = (L.grid[1] + kTcTileY - 1) / kTcTileY,
             ntz = (L.grid[2] + kTcTileZ - 1) / kTcTileZ;
   dim3 grid((unsigned)(ntx * nty * ntz), (unsigned)L.npass);
-  m2l_tc_kernel<<<grid, 128, kSmemBytes, s>>>(*reinterpret_cast<const CUtensorMap*>(map_hi),
-                                              *reinterpret_cast<const CUtensorMap*>(map_lo), L);
+  if (L.kind == TC_BF16X3)
+    m2l_tc_kernel<TC_BF16X3><<<grid, 128, kSmemBytes, s>>>(*reinterpret_cast<const CUtensorMap*>(map_hi),
+                                                           *reinterpret_cast<const CUtensorMap*>(map_lo), L);
+  else
+    m2l_tc_kernel<TC_TF32><<<grid, 128, kSmemBytes, s>>>(*reinterpret_cast<const CUtensorMap*>(map_hi),
+                                                         *reinterpret_cast<const CUtensorMap*>(map_lo), L);
   return cudaGetLastError();
 }
 
