@@ -28,8 +28,8 @@
 namespace fmmgb {
 namespace {
 
-constexpr int kSA = 3;                                   // activation ring stages (both planes)
-constexpr int kSB = 4;                                   // weight ring slots (one plane each)
+constexpr int kSA = 2;                                   // activation ring stages (both planes)
+constexpr int kSB = 6;                                   // weight ring slots (one plane each)
 constexpr int kARows = kTcTileX * kTcBoxY;               // 144 rows of one activation box
 constexpr int kAPlane = kARows * 128;                    // 18 KB, a multiple of 1024
 constexpr int kAStage = 2 * kAPlane;                     // hi and lo planes
