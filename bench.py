@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32-plain and FP64 comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="single", choices=["single", "batch"],
+                    help="single: one n^3 lognormal field; batch: --batch Plummer fields of uneven sizes "
+                         "(64/96/128/192)^3 solved as one CUDA graph")
+    ap.add_argument("--batch", type=int, default=64)
     return ap.parse_args()
 
 
@@ -279,6 +283,9 @@ def main():
         _build.build()
     if dist:
         dist.barrier()
+    if args.workload == "batch":
+        batch_main(args, fmm, inputs, torch, dist, rank, world)
+        return
     n, p, b = args.n, args.order, args.leaf
     dx = 1.0 / n
     rho_np = inputs.lognormal(n, seed=2606 + rank)
@@ -436,6 +443,103 @@ def main():
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     plan.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def batch_main(args, fmm, inputs, torch, dist, rank, world):
+    """Uneven batch: seeded sizes from {64, 96, 128, 192}^3, Plummer + 1% noise,
+    every field solved (phi and accel) by one graph launch per step.  Beside
+    it: the same fields solved one after another without the graph."""
+    prec = args.precision if args.precision != DEFAULT_PRECISION else "fp32"
+    p, b = args.order, args.leaf
+    sizes = inputs.batch_sizes(args.batch, seed=2606 + rank)
+    plans = [fmm.FMMPlan((s, s, s), p, b, prec, dx=1.0 / s) for s in sizes]
+    rhos = [torch.from_numpy(inputs.plummer(s, seed=3000 + 97 * rank + i)).cuda() for i, s in enumerate(sizes)]
+    phis = [q._empty() for q in plans]
+    accs = [q._empty((3,)) for q in plans]
+    cells = sum(s ** 3 for s in sizes)
+    batch = fmm.BatchSolver(plans)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        batch.solve(rhos, phis, accs)
+
+    def step_seq():
+        for q, r, f, a in zip(plans, rhos, phis, accs):
+            q.solve(r, accel=True, phi_out=f, accel_out=a)
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t = torch.tensor([e0.elapsed_time(e1)], device="cuda", dtype=torch.float64)
+        if dist:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    seq_ms = timed(step_seq)
+    with ClockSampler(gpu_index_for_smi(torch)) as clk:
+        ms = timed(step)
+    for q in plans:
+        q.check()
+    value = cells * args.steps * world / (ms / 1e3) / 1e6
+    # e2e: pinned host fields copied in and results copied out inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hr = [torch.from_numpy(r.cpu().numpy()).pin_memory() for r in rhos]
+        hf = [torch.empty(f.shape, dtype=f.dtype).pin_memory() for f in phis]
+        ha = [torch.empty(a.shape, dtype=a.dtype).pin_memory() for a in accs]
+
+        def step_e2e():
+            for r, h in zip(rhos, hr):
+                r.copy_(h, non_blocking=True)
+            batch.solve(rhos, phis, accs)
+            for f, h in zip(phis, hf):
+                h.copy_(f, non_blocking=True)
+            for a, h in zip(accs, ha):
+                h.copy_(a, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        step_e2e()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_e2e()
+        te = time.perf_counter() - t0
+        e2e = {"value": cells * args.steps * world / te / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(r.numel() for r in hr) * 4),
+               "d2h_bytes_per_step": int(sum(f.numel() + a.numel() for f, a in zip(hf, ha)) * 4)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32/f32", "bf16x3": "bf16x3/f32"}[prec],
+                "data": "synthetic",
+                "config": {"workload": f"batch of {args.batch} Plummer fields, sizes "
+                                       f"{{64,96,128,192}}^3 (seeded), p={p}, leaf {b}^3, one CUDA graph",
+                           "cells_per_step": cells, "size_counts": {str(s): sizes.count(s) for s in sorted(set(sizes))},
+                           "precision": prec, "sequential_no_graph_mcells_s":
+                               cells * args.steps * world / (seq_ms / 1e3) / 1e6,
+                           "l2": "inputs larger than L2 (all fields together)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": None, "cpu_baseline": None, "e2e": e2e,
+                "gpu_launches": batch.launches(True) * args.steps, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for q in plans:
+        q.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()

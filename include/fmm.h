@@ -181,6 +181,31 @@ fmm_status fmm_solve_host(fmm_plan_t plan, const void* rho_host, void* phi_host,
 fmm_status fmm_solve_static(const fmm_grid* grid, int order, int leaf, const void* rho, void* phi, void* accel,
                             void* stream);
 
+/*
+ * Batched solves (many independent densities, uneven grid sizes).
+ *   fmm_batch_create  : groups `count` existing plans (not copied, not owned;
+ *                       they must outlive the batch).
+ *   fmm_batch_solve   : solves every plan's density with one graph launch.
+ *                       rho[i], phi[i] (and accel[i] if `accel` is non-NULL and
+ *                       accel[i] is non-NULL) are plan i's device buffers as in
+ *                       fmm_solve.  The first call with a given set of buffers
+ *                       runs each solve once, then captures all of them into a
+ *                       CUDA graph -- each plan on its own branch, so small
+ *                       grids execute concurrently -- and launches it; later
+ *                       calls with the same buffers only launch the graph
+ *                       (new buffers: a new capture).  Asynchronous on `stream`.
+ *   fmm_batch_destroy : frees the graph and the batch's streams/events.
+ * The batch is the multi-field form of the solve; the paper solves one field
+ * per call (this is the data-parallel batch of many problems).
+ */
+typedef struct fmm_batch_s* fmm_batch_t;
+fmm_status fmm_batch_create(const fmm_plan_t* plans, int count, fmm_batch_t* out);
+fmm_status fmm_batch_solve(fmm_batch_t batch, const void* const* rho, void* const* phi, void* const* accel,
+                           void* stream);
+fmm_status fmm_batch_destroy(fmm_batch_t batch);
+/* Kernel launches one fmm_batch_solve graph holds (sum over the plans). */
+int fmm_batch_launches(fmm_batch_t batch, int with_accel);
+
 /* fmm_check -- synchronises the plan's last stream and reports device-side
  * flags (FMM_ERR_NONFINITE, FMM_ERR_TIMEOUT), clearing them. */
 fmm_status fmm_check(fmm_plan_t plan);

@@ -30,7 +30,8 @@ PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3}
 EXPORTS = ["fmm_default_opts", "fmm_plan", "fmm_solve", "fmm_solve_adjoint", "fmm_solve_host", "fmm_check",
            "fmm_workspace_bytes", "fmm_solve_launches", "fmm_plan_destroy", "fmm_last_error", "fmm_debug_level",
            "fmm_plan_leaf_level", "fmm_timing_enable", "fmm_timing_read", "fmm_timing_stage_count",
-           "fmm_timing_stage_name", "fmm_plan_level_kind", "fmm_plan_near_on_tensor_cores", "fmm_solve_static"]
+           "fmm_timing_stage_name", "fmm_plan_level_kind", "fmm_plan_near_on_tensor_cores", "fmm_solve_static", "fmm_batch_create",
+           "fmm_batch_solve", "fmm_batch_destroy", "fmm_batch_launches"]
 
 
 class FMMError(RuntimeError):
@@ -89,6 +90,14 @@ def load(path: str | None = None):
         lib.fmm_debug_level.restype = i
         lib.fmm_plan_leaf_level.argtypes = [vp]
         lib.fmm_plan_leaf_level.restype = i
+        lib.fmm_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
+        lib.fmm_batch_create.restype = i
+        lib.fmm_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+        lib.fmm_batch_solve.restype = i
+        lib.fmm_batch_destroy.argtypes = [vp]
+        lib.fmm_batch_destroy.restype = i
+        lib.fmm_batch_launches.argtypes = [vp, i]
+        lib.fmm_batch_launches.restype = i
         lib.fmm_solve_static.argtypes = [ctypes.POINTER(_Grid), i, i, vp, vp, vp, vp]
         lib.fmm_solve_static.restype = i
         lib.fmm_plan_level_kind.argtypes = [vp, i]
@@ -256,6 +265,44 @@ class FMMPlan:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             self.lib.fmm_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchSolver:
+    """Many independent solves (uneven grids) replayed as one CUDA graph
+    (fmm_batch_*).  The plans must outlive the solver."""
+
+    def __init__(self, plans):
+        self.lib = load()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(self.lib, self.lib.fmm_batch_create(arr, len(self.plans), ctypes.byref(h)))
+        self._h = h
+
+    def solve(self, rhos, phis, accels=None, stream=None):
+        n = len(self.plans)
+        if len(rhos) != n or len(phis) != n or (accels is not None and len(accels) != n):
+            raise ValueError("one rho / phi (/ accel) per plan")
+        r = (ctypes.c_void_p * n)(*[p._tensor(x, "rho").value for p, x in zip(self.plans, rhos)])
+        f = (ctypes.c_void_p * n)(*[p._tensor(x, "phi").value for p, x in zip(self.plans, phis)])
+        a = None
+        if accels is not None:
+            a = (ctypes.c_void_p * n)(*[p._tensor(x, "accel", (3,)).value for p, x in zip(self.plans, accels)])
+        _check(self.lib, self.lib.fmm_batch_solve(self._h, r, f, a, _stream_handle(stream)))
+
+    def launches(self, accel: bool = True) -> int:
+        return int(self.lib.fmm_batch_launches(self._h, 1 if accel else 0))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.fmm_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

@@ -1299,3 +1299,137 @@ extern "C" fmm_status fmm_solve_static(const fmm_grid* grid, int order, int leaf
   // nothing of P was allocated on the device: no release
   return st;
 }
+
+// ---------------------------------------------------------------------------
+// Batched solves under one CUDA graph.
+struct fmm_batch_s {
+  std::vector<fmm_plan_t> plans;
+  std::vector<cudaStream_t> side;  // one capture branch per plan (reused round-robin)
+  std::vector<cudaEvent_t> ev;     // fork / join events
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> key;    // buffers the graph was captured with
+  bool with_accel = false;
+};
+
+namespace {
+void batch_free_graph(fmm_batch_t B) {
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  B->exec = nullptr;
+  B->graph = nullptr;
+}
+}  // namespace
+
+extern "C" fmm_status fmm_batch_create(const fmm_plan_t* plans, int count, fmm_batch_t* out) {
+  g_last_error.clear();
+  if (!out) return fail(FMM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!plans || count <= 0) return fail(FMM_ERR_ARG, "need at least one plan");
+  for (int i = 0; i < count; ++i)
+    if (!plans[i]) return fail(FMM_ERR_ARG, "plan %d is NULL", i);
+  fmm_batch_t B = new (std::nothrow) fmm_batch_s();
+  if (!B) return fail(FMM_ERR_ALLOC, "host allocation failed");
+  B->plans.assign(plans, plans + count);
+  const int nside = std::min(count, 32);
+  B->side.resize(nside, nullptr);
+  for (auto& st : B->side)
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      fmm_batch_destroy(B);
+      return fail(FMM_ERR_CUDA, "stream creation failed");
+    }
+  B->ev.resize(nside + 1, nullptr);
+  for (auto& e : B->ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      fmm_batch_destroy(B);
+      return fail(FMM_ERR_CUDA, "event creation failed");
+    }
+  *out = B;
+  return FMM_OK;
+}
+
+extern "C" fmm_status fmm_batch_solve(fmm_batch_t B, const void* const* rho, void* const* phi, void* const* accel,
+                                      void* stream) {
+  if (!B) return fail(FMM_ERR_ARG, "batch is NULL");
+  if (!rho || !phi) return fail(FMM_ERR_ARG, "rho and phi arrays must be non-NULL");
+  const int n = (int)B->plans.size();
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<const void*> key;
+  key.reserve(3 * n);
+  for (int i = 0; i < n; ++i) {
+    if (!rho[i] || !phi[i]) return fail(FMM_ERR_ARG, "rho[%d] / phi[%d] is NULL", i, i);
+    key.push_back(rho[i]);
+    key.push_back(phi[i]);
+    key.push_back(accel ? accel[i] : nullptr);
+  }
+  if (!B->exec || key != B->key) {
+    batch_free_graph(B);
+    // one eager solve per plan: first-use set-up (kernel attributes, lazy
+    // module loading) must not happen inside a capture
+    for (int i = 0; i < n; ++i) {
+      fmm_plan_t P = B->plans[i];
+      const bool timing = P->timing;
+      P->timing = false;
+      fmm_status st = fmm_solve(P, rho[i], phi[i], accel ? accel[i] : nullptr, stream);
+      P->timing = timing;
+      if (st != FMM_OK) return st;
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    cudaStream_t cap = B->side[0];
+    CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    fmm_status st = FMM_OK;
+    const int nside = (int)B->side.size();
+    // fork: every side stream waits on the capture origin
+    if (cudaEventRecord(B->ev[0], cap) != cudaSuccess) st = fail(FMM_ERR_CUDA, "capture fork failed");
+    for (int k = 1; k < nside && st == FMM_OK; ++k)
+      if (cudaStreamWaitEvent(B->side[k], B->ev[0], 0) != cudaSuccess) st = fail(FMM_ERR_CUDA, "capture fork failed");
+    for (int i = 0; i < n && st == FMM_OK; ++i) {
+      fmm_plan_t P = B->plans[i];
+      const bool timing = P->timing;
+      P->timing = false;
+      st = fmm_solve(P, rho[i], phi[i], accel ? accel[i] : nullptr, B->side[i % nside]);
+      P->timing = timing;
+    }
+    // join
+    for (int k = 1; k < nside && st == FMM_OK; ++k) {
+      if (cudaEventRecord(B->ev[k], B->side[k]) != cudaSuccess ||
+          cudaStreamWaitEvent(cap, B->ev[k], 0) != cudaSuccess)
+        st = fail(FMM_ERR_CUDA, "capture join failed");
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cap, &g);
+    if (st != FMM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (ec != cudaSuccess) return fail(FMM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ec));
+    B->graph = g;
+    if (cudaGraphInstantiate(&B->exec, g, 0) != cudaSuccess) {
+      batch_free_graph(B);
+      return fail(FMM_ERR_CUDA, "graph instantiation failed");
+    }
+    B->key = key;
+    B->with_accel = accel != nullptr;
+  }
+  for (auto* P : B->plans) P->last_stream = s;  // fmm_check waits on the graph's stream
+  CUDA_TRY(cudaGraphLaunch(B->exec, s));
+  return FMM_OK;
+}
+
+extern "C" fmm_status fmm_batch_destroy(fmm_batch_t B) {
+  if (!B) return FMM_OK;
+  batch_free_graph(B);
+  for (auto& st : B->side)
+    if (st) cudaStreamDestroy(st);
+  for (auto& e : B->ev)
+    if (e) cudaEventDestroy(e);
+  delete B;
+  return FMM_OK;
+}
+
+extern "C" int fmm_batch_launches(fmm_batch_t B, int with_accel) {
+  if (!B) return -1;
+  int n = 0;
+  for (auto* P : B->plans) n += fmm_solve_launches(P, with_accel);
+  return n;
+}
