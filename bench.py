@@ -51,6 +51,7 @@ def parse():
                     help="single: one n^3 lognormal field; batch: --batch Plummer fields of uneven sizes "
                          "(64/96/128/192)^3 solved as one CUDA graph")
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default CUDA-core contraction variants")
     return ap.parse_args()
 
 
@@ -291,6 +292,11 @@ def main():
     rho_np = inputs.lognormal(n, seed=2606 + rank)
     rho = torch.from_numpy(rho_np).cuda()
     plan = fmm.FMMPlan((n, n, n), p, b, args.precision, dx=dx)
+    if not args.no_autotune:
+        plan.autotune()
+    tuning = {str(l): list(plan.tuning(l)) for l in range(2, plan.leaf_level + 1) if plan.level_kind(l) != "tensor"}
+    if not plan.near_on_tensor_cores:
+        tuning["near"] = list(plan.tuning(-1))
     phi = torch.empty_like(rho)
     acc = torch.empty((3,) + rho.shape, dtype=rho.dtype, device="cuda")
     stream = torch.cuda.current_stream()
@@ -366,6 +372,8 @@ def main():
         del phi64
         if args.precision != "fp32":
             pp = fmm.FMMPlan((n, n, n), p, b, "fp32", dx=dx)
+            if not args.no_autotune:
+                pp.autotune()
             for _ in range(3):
                 pp.solve(rho, accel=True, phi_out=phi, accel_out=acc)
             torch.cuda.synchronize()
@@ -436,7 +444,8 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": f"unigrid FMM {n}^3 isolated, p={p}, leaf {b}^3, lognormal P(k)~k^-2.5",
                            "precision": args.precision, "l2": "inputs larger than L2 (rho 512 MiB, outputs 2 GiB)",
-                           "parallelism": f"replicas x{world}", **compare},
+                           "parallelism": f"replicas x{world}", "cuda_core_variants": tuning,
+                           "autotuned": not args.no_autotune, **compare},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": plan.launches(True) * args.steps,
                 "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if v[1]},
@@ -460,7 +469,7 @@ def batch_main(args, fmm, inputs, torch, dist, rank, world):
     phis = [q._empty() for q in plans]
     accs = [q._empty((3,)) for q in plans]
     cells = sum(s ** 3 for s in sizes)
-    batch = fmm.BatchSolver(plans)
+    batch = fmm.BatchSolver(plans, autotune=not args.no_autotune)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -530,7 +539,8 @@ def batch_main(args, fmm, inputs, torch, dist, rank, world):
                 "config": {"workload": f"batch of {args.batch} Plummer fields, sizes "
                                        f"{{64,96,128,192}}^3 (seeded), p={p}, leaf {b}^3, one CUDA graph",
                            "cells_per_step": cells, "size_counts": {str(s): sizes.count(s) for s in sorted(set(sizes))},
-                           "precision": prec, "sequential_no_graph_mcells_s":
+                           "precision": prec, "autotuned": not args.no_autotune,
+                           "sequential_no_graph_mcells_s":
                                cells * args.steps * world / (seq_ms / 1e3) / 1e6,
                            "l2": "inputs larger than L2 (all fields together)",
                            "parallelism": f"replicas x{world}"},

@@ -182,6 +182,36 @@ fmm_status fmm_solve_static(const fmm_grid* grid, int order, int leaf, const voi
                             void* stream);
 
 /*
+ * Autotuning of the CUDA-core contractions: the M2L levels that are not on
+ * the tensor cores (Sec. 2.3, eq. M2L) and the near-field sum (Sec. 2.3, the
+ * direct cell-cell part), when it is not on the tensor cores.
+ *   fmm_plan_autotune   : times every applicable variant of each contraction
+ *                         on the plan's own workspace (3 timed launches after
+ *                         one warm-up) and keeps the fastest.  Overwrites the
+ *                         workspace (no solve state survives a solve anyway);
+ *                         synchronises `stream`.  Results are cached per
+ *                         process by contraction geometry (grid of rows, row
+ *                         length, columns, order, leaf), so further plans of
+ *                         the same shape only look the choice up.
+ *   fmm_plan_tuning     : reads the variant of level `level` (2..leaf level;
+ *                         -1 = near field): shape 0 = 4x4x4 rows per block,
+ *                         shapes 1 and 2 = z-run register tiles
+ *                         (8x4x8 / 8x4x4 rows for FP32, 8x4x4 / 8x4x2 for
+ *                         FP64), and the number of blocks sharing the 27
+ *                         neighbours of a row tile (shape 0: 1 or 27; shapes
+ *                         1, 2: 1, 3 or 9).
+ *   fmm_plan_set_tuning : sets it; FMM_ERR_ARG if the variant does not apply
+ *                         (level on the tensor cores, reduction lengths not a
+ *                         multiple of 8, split scratch too small).
+ * All variants compute the same sums; they differ in summation order only
+ * through the neighbour split (partials added in a fixed order).
+ * The paper has no counterpart (its M2L runs on CPU cores).
+ */
+fmm_status fmm_plan_autotune(fmm_plan_t plan, void* stream);
+fmm_status fmm_plan_tuning(fmm_plan_t plan, int level, int* shape, int* dsplit);
+fmm_status fmm_plan_set_tuning(fmm_plan_t plan, int level, int shape, int dsplit);
+
+/*
  * Batched solves (many independent densities, uneven grid sizes).
  *   fmm_batch_create  : groups `count` existing plans (not copied, not owned;
  *                       they must outlive the batch).

@@ -27,11 +27,34 @@ STATUS = {0: "FMM_OK", 1: "FMM_ERR_ARG", 2: "FMM_ERR_UNSUPPORTED", 3: "FMM_ERR_A
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3}
 
 # every symbol include/fmm.h declares
-EXPORTS = ["fmm_default_opts", "fmm_plan", "fmm_solve", "fmm_solve_adjoint", "fmm_solve_host", "fmm_check",
-           "fmm_workspace_bytes", "fmm_solve_launches", "fmm_plan_destroy", "fmm_last_error", "fmm_debug_level",
-           "fmm_plan_leaf_level", "fmm_timing_enable", "fmm_timing_read", "fmm_timing_stage_count",
-           "fmm_timing_stage_name", "fmm_plan_level_kind", "fmm_plan_near_on_tensor_cores", "fmm_solve_static", "fmm_batch_create",
-           "fmm_batch_solve", "fmm_batch_destroy", "fmm_batch_launches"]
+EXPORTS = [
+    "fmm_default_opts",
+    "fmm_plan",
+    "fmm_solve",
+    "fmm_solve_adjoint",
+    "fmm_solve_host",
+    "fmm_check",
+    "fmm_workspace_bytes",
+    "fmm_solve_launches",
+    "fmm_plan_destroy",
+    "fmm_last_error",
+    "fmm_debug_level",
+    "fmm_plan_leaf_level",
+    "fmm_timing_enable",
+    "fmm_timing_read",
+    "fmm_timing_stage_count",
+    "fmm_timing_stage_name",
+    "fmm_plan_level_kind",
+    "fmm_plan_near_on_tensor_cores",
+    "fmm_solve_static",
+    "fmm_batch_create",
+    "fmm_plan_autotune",
+    "fmm_plan_tuning",
+    "fmm_plan_set_tuning",
+    "fmm_batch_solve",
+    "fmm_batch_destroy",
+    "fmm_batch_launches",
+]
 
 
 class FMMError(RuntimeError):
@@ -90,6 +113,12 @@ def load(path: str | None = None):
         lib.fmm_debug_level.restype = i
         lib.fmm_plan_leaf_level.argtypes = [vp]
         lib.fmm_plan_leaf_level.restype = i
+        lib.fmm_plan_autotune.argtypes = [vp, vp]
+        lib.fmm_plan_autotune.restype = i
+        lib.fmm_plan_tuning.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+        lib.fmm_plan_tuning.restype = i
+        lib.fmm_plan_set_tuning.argtypes = [vp, i, i, i]
+        lib.fmm_plan_set_tuning.restype = i
         lib.fmm_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
         lib.fmm_batch_create.restype = i
         lib.fmm_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
@@ -259,6 +288,19 @@ class FMMPlan:
     def workspace_bytes(self) -> int:
         return int(self.lib.fmm_workspace_bytes(self._h))
 
+    def autotune(self, stream=None):
+        """Time the CUDA-core contraction variants and keep the fastest."""
+        _check(self.lib, self.lib.fmm_plan_autotune(self._h, _stream_handle(stream)))
+
+    def tuning(self, level: int):
+        """(shape, dsplit) of M2L level `level` (-1: near field)."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib, self.lib.fmm_plan_tuning(self._h, int(level), ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def set_tuning(self, level: int, shape: int, dsplit: int):
+        _check(self.lib, self.lib.fmm_plan_set_tuning(self._h, int(level), int(shape), int(dsplit)))
+
     def launches(self, accel: bool = True) -> int:
         return int(self.lib.fmm_solve_launches(self._h, 1 if accel else 0))
 
@@ -278,9 +320,12 @@ class BatchSolver:
     """Many independent solves (uneven grids) replayed as one CUDA graph
     (fmm_batch_*).  The plans must outlive the solver."""
 
-    def __init__(self, plans):
+    def __init__(self, plans, autotune: bool = True):
         self.lib = load()
         self.plans = list(plans)
+        if autotune:
+            for p in self.plans:
+                p.autotune()
         arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
         h = ctypes.c_void_p()
         _check(self.lib, self.lib.fmm_batch_create(arr, len(self.plans), ctypes.byref(h)))

@@ -18,7 +18,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libfmm_gb300.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
 
-SOURCES = ["capi.cu", "k_tree.cu", "k_p2m.cu", "k_m2m.cu", "k_l2l.cu", "k_leaf.cu", "k_gemm_simt.cu", "k_fd.cu",
+SOURCES = ["capi.cu", "k_tree.cu", "k_p2m.cu", "k_m2m.cu", "k_l2l.cu", "k_leaf.cu", "k_gemm_simt.cu", "k_gemm_zrun.cu", "k_fd.cu",
            "k_m2l_tc.cu"]
 HEADERS = ["fmm_internal.h", "tree_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -20,6 +20,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -167,6 +168,15 @@ struct fmm_plan_s {
   alignas(64) unsigned char map_near_lo[128];
   size_t rho_hi_off = 0, rho_lo_off = 0;
   size_t part_off = 0;  // neighbour-split partial sums of the small SIMT levels
+  size_t part_cap = 0;  // bytes there
+  // CUDA-core contraction variant of each M2L level and of the near field
+  // (shape / neighbour split; fmm_plan_autotune times the candidates)
+  struct SimtChoice {
+    int shape = 0, dsplit = 1;
+  };
+  SimtChoice m2l_choice[kMaxLevels];
+  SimtChoice near_choice;
+  std::vector<int> h_m2l_tile_k, h_near_tile_k;
   alignas(64) unsigned char map_hi[kMaxLevels][128];
   alignas(64) unsigned char map_lo[kMaxLevels][128];
   // host-buffer staging for fmm_solve_host
@@ -633,6 +643,9 @@ namespace {
 // arena layout, tables.  Device memory comes from P->dev_alloc (cudaMalloc
 // for plans, the static array for the allocation-free solve).  On failure
 // the caller releases P.
+NbrGemm m2l_gemm(fmm_plan_t P, int l);
+NbrGemm near_gemm(fmm_plan_t P);
+
 fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int order, int leaf, const fmm_opts& o,
                      cudaStream_t stream, int dev) {
   cudaStream_t s = stream;
@@ -700,13 +713,28 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     // column tiles of the SIMT contraction (needed to size the split scratch)
     const int ncol = 8 * P->nc;
     P->m2l_ntiles = (ncol + kNTile - 1) / kNTile;
-    size_t part = 0;
-    for (int l = 2; l <= P->L; ++l)
-      if (P->split_level(l))
-        part = std::max(part, (size_t)27 * (size_t)P->lev[l].npar * (size_t)ncol * (size_t)(P->lev[l].f64 ? 8 : 4));
+    size_t part = 0, want = 0;
+    for (int l = 2; l <= P->L; ++l) {
+      const size_t one = (size_t)P->lev[l].npar * (size_t)ncol * (size_t)(P->lev[l].f64 ? 8 : 4);
+      if (P->split_level(l)) part = std::max(part, 27 * one);
+      if (!P->lev[l].tc) want = std::max(want, 27 * one);
+    }
+    // room for the autotuner's neighbour-split candidates (M2L levels and the
+    // near field), up to 64 MiB
+    if (!P->near_tc)
+      want = std::max(want, (size_t)27 * (size_t)P->lev[P->L].nbox * (size_t)(P->b * P->b * P->b) * P->esize());
+    if (!P->no_split) part = std::max(part, std::min(want, (size_t)64 << 20));
     P->part_off = off;
+    P->part_cap = part;
     off = align(off + part);
+    for (int l = 2; l <= P->L; ++l) P->m2l_choice[l].dsplit = P->split_level(l) ? 27 : 1;
   }
+  // Default variants before any tuning: the small levels split over their 27
+  // neighbours (4x4x4 tiles), the rest on z-run tiles where they apply.
+  auto zrun_default = [&](NbrGemm g, const std::vector<int>& tk, fmm_plan_s::SimtChoice* c) {
+    g.dsplit = 1;
+    if (c->dsplit == 1 && zrun_eligible(g, tk.data(), (int)tk.size())) c->shape = 1;
+  };
   P->arena_bytes = off;
 
   auto cleanup = [](fmm_status e) { return e; };  // the caller releases the plan
@@ -756,6 +784,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
       P->d_w_m2l_f32 = d;
     }
     P->m2l_ntiles = (int)tk.size();
+    P->h_m2l_tile_k = tk;
     if ((st = P->upload(tk, &P->d_m2l_tile_k, s)) || (st = P->upload(tw, &P->d_m2l_tile_w, s))) return cleanup(st);
     if (anytc) {
       TcHost H;
@@ -800,6 +829,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
       P->d_w_near = d;
     }
     P->near_ntiles = (int)tk.size();
+    P->h_near_tile_k = tk;
     if ((st = P->upload(tk, &P->d_near_tile_k, s)) || (st = P->upload(tw, &P->d_near_tile_w, s))) return cleanup(st);
   }
   if (P->near_tc) {
@@ -825,6 +855,9 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
   }
   P->tc.err = P->d_flag;
   P->tc.accumulate = 1;
+  for (int l = 2; l <= P->L; ++l)
+    if (!P->lev[l].tc) zrun_default(m2l_gemm(P, l), P->h_m2l_tile_k, &P->m2l_choice[l]);
+  if (!P->near_tc) zrun_default(near_gemm(P), P->h_near_tile_k, &P->near_choice);
   // uploads read host vectors that go out of scope here (plans only; the
   // allocation-free solve orders its copies on the caller's stream)
   if (!P->static_base && cudaStreamSynchronize(s) != cudaSuccess)
@@ -953,15 +986,8 @@ fmm_status do_l2l(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s) {
   return FMM_OK;
 }
 
-fmm_status do_m2l(fmm_plan_t P, int l, cudaStream_t s) {
+NbrGemm m2l_gemm(fmm_plan_t P, int l) {
   const Level& lv = P->lev[l];
-  if (lv.tc) {
-    TcLaunch L = P->tc;
-    L.C = static_cast<float*>(P->Lx(l));
-    for (int q = 0; q < 3; ++q) L.grid[q] = lv.np[q];
-    CUDA_TRY(launch_m2l_tc(L, P->map_hi[l], P->map_lo[l], s));
-    return FMM_OK;
-  }
   NbrGemm g;
   g.A = P->M(l);
   g.row_len = 8 * P->nc;
@@ -973,9 +999,41 @@ fmm_status do_m2l(fmm_plan_t P, int l, cudaStream_t s) {
   g.n_cols = 8 * P->nc;
   g.ntiles = P->m2l_ntiles;
   g.accumulate = 1;
-  g.dsplit = P->split_level(l) ? 27 : 1;
+  g.shape = P->m2l_choice[l].shape;
+  g.dsplit = P->m2l_choice[l].dsplit;
   g.partial = P->arena + P->part_off;
-  CUDA_TRY(lv.f64 ? launch_nbr_gemm_simt<double>(g, s) : launch_nbr_gemm_simt<float>(g, s));
+  return g;
+}
+
+NbrGemm near_gemm(fmm_plan_t P) {
+  NbrGemm g;
+  g.A = P->arena + P->rho_box_off;
+  g.row_len = P->b * P->b * P->b;
+  for (int q = 0; q < 3; ++q) g.grid[q] = P->lev[P->L].n[q];
+  g.W = P->d_w_near;
+  g.tile_k = P->d_near_tile_k;
+  g.tile_w = P->d_near_tile_w;
+  g.C = P->arena + P->near_off;
+  g.n_cols = P->b * P->b * P->b;
+  g.ntiles = P->near_ntiles;
+  g.accumulate = 0;
+  g.shape = P->near_choice.shape;
+  g.dsplit = P->near_choice.dsplit;
+  g.partial = P->arena + P->part_off;
+  return g;
+}
+
+fmm_status do_m2l(fmm_plan_t P, int l, cudaStream_t s) {
+  const Level& lv = P->lev[l];
+  if (lv.tc) {
+    TcLaunch L = P->tc;
+    L.C = static_cast<float*>(P->Lx(l));
+    for (int q = 0; q < 3; ++q) L.grid[q] = lv.np[q];
+    CUDA_TRY(launch_m2l_tc(L, P->map_hi[l], P->map_lo[l], s));
+    return FMM_OK;
+  }
+  const NbrGemm g = m2l_gemm(P, l);
+  CUDA_TRY(lv.f64 ? launch_nbr_gemm<double>(g, s) : launch_nbr_gemm<float>(g, s));
   return FMM_OK;
 }
 
@@ -1018,21 +1076,8 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
     StageTimer t(P, ST_NEAR_TC, s);
     CUDA_TRY(launch_m2l_tc(P->tcn, P->map_near_hi, P->map_near_lo, s));
   } else {
-    NbrGemm g;
-    g.A = rho_box;
-    g.row_len = P->b * P->b * P->b;
-    for (int q = 0; q < 3; ++q) g.grid[q] = P->lev[L].n[q];
-    g.W = P->d_w_near;
-    g.tile_k = P->d_near_tile_k;
-    g.tile_w = P->d_near_tile_w;
-    g.C = near_box;
-    g.n_cols = P->b * P->b * P->b;
-    g.ntiles = P->near_ntiles;
-    g.accumulate = 0;
-    g.dsplit = 1;
-    g.partial = nullptr;
     StageTimer t(P, ST_NEAR, s);
-    CUDA_TRY(launch_nbr_gemm_simt<T>(g, s));
+    CUDA_TRY(launch_nbr_gemm<T>(near_gemm(P), s));
   }
   {
     StageTimer t(P, ST_LEAF, s);
@@ -1149,9 +1194,10 @@ int fmm_solve_launches(fmm_plan_t P, int with_accel) {
   if (L < 2) n += 1;                    // zero the leaf locals
   for (int l = 2; l <= L; ++l) {
     n += 2;                             // L2L (or zero) + M2L
-    if (P->split_level(l)) n += 1;      // reduction of the neighbour partials
+    if (!P->lev[l].tc && P->m2l_choice[l].dsplit > 1) n += 1;  // reduction of the neighbour partials
   }
   n += 2;                               // near field + leaf finish
+  if (!P->near_tc && P->near_choice.dsplit > 1) n += 1;
   if (with_accel) n += 1;
   return n;
 }
@@ -1432,4 +1478,147 @@ extern "C" int fmm_batch_launches(fmm_batch_t B, int with_accel) {
   int n = 0;
   for (auto* P : B->plans) n += fmm_solve_launches(P, with_accel);
   return n;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the CUDA-core contractions (M2L levels off the tensor cores and
+// the near field): each candidate tile shape / neighbour split is timed on the
+// plan's own buffers and the fastest kept.  Results are cached per process by
+// contraction geometry, so plans of the same shape tune once.
+namespace {
+
+using SimtChoice = fmm_plan_s::SimtChoice;
+std::mutex g_tune_mu;
+std::map<std::string, SimtChoice> g_tune_cache;
+
+bool choice_valid(fmm_plan_t P, NbrGemm g, const std::vector<int>& tk, size_t es, SimtChoice c) {
+  const size_t one = (size_t)g.grid[0] * g.grid[1] * g.grid[2] * (size_t)g.n_cols * es;
+  if (c.dsplit > 1 && (size_t)c.dsplit * one > P->part_cap) return false;
+  if (c.shape == 0) return c.dsplit == 1 || c.dsplit == 27;
+  if (c.shape != 1 && c.shape != 2) return false;
+  g.dsplit = c.dsplit;
+  return zrun_eligible(g, tk.data(), (int)tk.size());
+}
+
+template <typename T>
+fmm_status tune_one(fmm_plan_t P, NbrGemm g, const std::vector<int>& tk, const char* what, int reps, cudaStream_t s,
+                    SimtChoice* out) {
+  char key[160];
+  std::snprintf(key, sizeof key, "%s/%zu/%d,%d,%d/%d/%d/%d/%d/%d", what, sizeof(T), g.grid[0], g.grid[1], g.grid[2],
+                g.row_len, g.n_cols, g.ntiles, P->p, P->b);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end() && choice_valid(P, g, tk, sizeof(T), it->second)) {
+      *out = it->second;
+      return FMM_OK;
+    }
+  }
+  std::vector<SimtChoice> cand;
+  const SimtChoice all[] = {{0, 1}, {0, 27}, {1, 1}, {1, 3}, {1, 9}, {2, 1}, {2, 3}, {2, 9}};
+  for (const SimtChoice& c : all)
+    if (choice_valid(P, g, tk, sizeof(T), c)) cand.push_back(c);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(FMM_ERR_CUDA, "event creation failed");
+  }
+  fmm_status st = FMM_OK;
+  float best = 1e30f;
+  SimtChoice pick = *out;
+  for (const SimtChoice& c : cand) {
+    g.shape = c.shape;
+    g.dsplit = c.dsplit;
+    cudaError_t e = launch_nbr_gemm<T>(g, s);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_nbr_gemm<T>(g, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      st = fail(FMM_ERR_CUDA, "autotune launch failed: %s", cudaGetErrorString(e));
+      break;
+    }
+    if (ms < best) best = ms, pick = c;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != FMM_OK) return st;
+  *out = pick;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = pick;
+  return FMM_OK;
+}
+
+}  // namespace
+
+extern "C" fmm_status fmm_plan_autotune(fmm_plan_t P, void* stream) {
+  if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // defined inputs for the timed launches; every solve rewrites the arena
+  CUDA_TRY(cudaMemsetAsync(P->arena, 0, P->arena_bytes, s));
+  fmm_status st;
+  for (int l = 2; l <= P->L; ++l) {
+    if (P->lev[l].tc) continue;
+    const NbrGemm g = m2l_gemm(P, l);
+    st = P->lev[l].f64 ? tune_one<double>(P, g, P->h_m2l_tile_k, "m2l", 3, s, &P->m2l_choice[l])
+                       : tune_one<float>(P, g, P->h_m2l_tile_k, "m2l", 3, s, &P->m2l_choice[l]);
+    if (st) return st;
+  }
+  if (!P->near_tc) {
+    const NbrGemm g = near_gemm(P);
+    st = P->f64_data() ? tune_one<double>(P, g, P->h_near_tile_k, "near", 3, s, &P->near_choice)
+                       : tune_one<float>(P, g, P->h_near_tile_k, "near", 3, s, &P->near_choice);
+    if (st) return st;
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return FMM_OK;
+}
+
+namespace {
+fmm_status tuning_slot(fmm_plan_t P, int level, SimtChoice** c, NbrGemm* g, const std::vector<int>** tk, size_t* es) {
+  if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
+  if (level == -1) {
+    if (P->near_tc) return fail(FMM_ERR_ARG, "the near field of this plan runs on the tensor cores");
+    *c = &P->near_choice;
+    *g = near_gemm(P);
+    *tk = &P->h_near_tile_k;
+    *es = P->esize();
+    return FMM_OK;
+  }
+  if (level < 2 || level > P->L) return fail(FMM_ERR_ARG, "level %d outside 2..%d", level, P->L);
+  if (P->lev[level].tc) return fail(FMM_ERR_ARG, "level %d runs on the tensor cores", level);
+  *c = &P->m2l_choice[level];
+  *g = m2l_gemm(P, level);
+  *tk = &P->h_m2l_tile_k;
+  *es = P->lev[level].f64 ? 8 : 4;
+  return FMM_OK;
+}
+}  // namespace
+
+extern "C" fmm_status fmm_plan_tuning(fmm_plan_t P, int level, int* shape, int* dsplit) {
+  SimtChoice* c;
+  NbrGemm g;
+  const std::vector<int>* tk;
+  size_t es;
+  if (fmm_status st = tuning_slot(P, level, &c, &g, &tk, &es)) return st;
+  if (shape) *shape = c->shape;
+  if (dsplit) *dsplit = c->dsplit;
+  return FMM_OK;
+}
+
+extern "C" fmm_status fmm_plan_set_tuning(fmm_plan_t P, int level, int shape, int dsplit) {
+  SimtChoice* c;
+  NbrGemm g;
+  const std::vector<int>* tk;
+  size_t es;
+  if (fmm_status st = tuning_slot(P, level, &c, &g, &tk, &es)) return st;
+  const SimtChoice want{shape, dsplit};
+  if (!choice_valid(P, g, *tk, es, want))
+    return fail(FMM_ERR_ARG, "variant shape %d / split %d does not apply to this contraction (or its split scratch "
+                "does not fit the plan)", shape, dsplit);
+  *c = want;
+  return FMM_OK;
 }

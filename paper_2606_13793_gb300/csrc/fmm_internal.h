@@ -70,12 +70,26 @@ struct NbrGemm {
   int n_cols;
   int ntiles;
   int accumulate;      // 1: C += result, 0: C = result
-  int dsplit;          // 1, or 27: one CTA per neighbour, partial sums reduced in a fixed order
-  void* partial;       // [27][rows][n_cols] scratch when dsplit == 27
+  int dsplit;          // CTAs sharing the 27 neighbours of a row tile (partial sums reduced in a fixed order):
+                       // shape 0: 1 or 27; shapes 1, 2: 1, 3 or 9
+  void* partial;       // [dsplit][rows][n_cols] scratch when dsplit > 1
+  int shape = 0;       // 0: 4x4x4 rows per CTA (k_gemm_simt.cu); 1, 2: z-run tiles (k_gemm_zrun.cu)
 };
 
 template <typename T>
 cudaError_t launch_nbr_gemm_simt(const NbrGemm& g, cudaStream_t s);
+// z-run tiles: shape 0 = 8x4x8 (FP32) / 8x4x4 (FP64) rows per CTA, shape 1 = 8x4x4 / 8x4x2
+template <typename T>
+cudaError_t launch_nbr_gemm_zrun(const NbrGemm& g, int shape, cudaStream_t s);
+// Whether the z-run kernel handles this contraction (reduction lengths and
+// column counts multiples of 8, dsplit 1, 3 or 9).
+bool zrun_eligible(const NbrGemm& g, const int* tile_k_host, int ntiles);
+// Dispatch on g.shape.
+template <typename T>
+cudaError_t launch_nbr_gemm(const NbrGemm& g, cudaStream_t s);
+// C (+)= sum over nparts partial arrays of count values, in part order.
+template <typename T>
+cudaError_t launch_reduce_partials(const T* part, int nparts, long long count, T* C, int accumulate, cudaStream_t s);
 
 // Upward pass.
 struct TreeTables {

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(64) nbr_gemm_simt_kernel(NbrGemm g) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 
-  const int d0 = g.dsplit > 1 ? (int)blockIdx.z : 0;
+  const int d0 = g.dsplit > 1 ? (int)blockIdx.z : 0;  // dsplit is 1 or 27 here
   const int d1 = g.dsplit > 1 ? d0 + 1 : 27;
   for (int d = d0; d < d1; ++d) {
     const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
@@ -106,17 +106,32 @@ __global__ void __launch_bounds__(64) nbr_gemm_simt_kernel(NbrGemm g) {
   }
 }
 
-// C (+)= sum over the 27 neighbour partials, in neighbour order.
+// C (+)= sum over the neighbour-group partials, in group order.
 template <typename T>
-__global__ void reduce_partials_kernel(const T* __restrict__ part, long long count, T* __restrict__ C, int accumulate) {
+__global__ void reduce_partials_kernel(const T* __restrict__ part, int nparts, long long count, T* __restrict__ C,
+                                       int accumulate) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
     T s = accumulate ? C[i] : T(0);
-    for (int d = 0; d < 27; ++d) s += part[d * count + i];
+    for (int d = 0; d < nparts; ++d) s += part[d * count + i];
     C[i] = s;
   }
 }
 
 }  // namespace
+
+template <typename T>
+cudaError_t launch_reduce_partials(const T* part, int nparts, long long count, T* C, int accumulate, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  long long blocks = (count + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  reduce_partials_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(part, nparts, count, C, accumulate);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_nbr_gemm(const NbrGemm& g, cudaStream_t s) {
+  return g.shape == 0 ? launch_nbr_gemm_simt<T>(g, s) : launch_nbr_gemm_zrun<T>(g, g.shape - 1, s);
+}
 
 template <typename T>
 cudaError_t launch_nbr_gemm_simt(const NbrGemm& g, cudaStream_t s) {
@@ -127,15 +142,16 @@ cudaError_t launch_nbr_gemm_simt(const NbrGemm& g, cudaStream_t s) {
   nbr_gemm_simt_kernel<T><<<grid, 64, 0, s>>>(g);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || g.dsplit <= 1) return e;
-  const long long count = (long long)g.grid[0] * g.grid[1] * g.grid[2] * g.n_cols;
-  long long blocks = (count + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  reduce_partials_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const T*>(g.partial), count,
-                                                            static_cast<T*>(g.C), g.accumulate);
-  return cudaGetLastError();
+  return launch_reduce_partials<T>(static_cast<const T*>(g.partial), g.dsplit,
+                                   (long long)g.grid[0] * g.grid[1] * g.grid[2] * g.n_cols, static_cast<T*>(g.C),
+                                   g.accumulate, s);
 }
 
 template cudaError_t launch_nbr_gemm_simt<float>(const NbrGemm&, cudaStream_t);
 template cudaError_t launch_nbr_gemm_simt<double>(const NbrGemm&, cudaStream_t);
+template cudaError_t launch_nbr_gemm<float>(const NbrGemm&, cudaStream_t);
+template cudaError_t launch_nbr_gemm<double>(const NbrGemm&, cudaStream_t);
+template cudaError_t launch_reduce_partials<float>(const float*, int, long long, float*, int, cudaStream_t);
+template cudaError_t launch_reduce_partials<double>(const double*, int, long long, double*, int, cudaStream_t);
 
 }  // namespace fmmgb
