@@ -407,10 +407,7 @@ struct TcCols {
   int col0, ncols, K;
 };
 
-// Packs passes and weight tiles for groups `gs`; `entry(d, k, n)` gives one
-// weight of the contraction.  Tiles are written in the exact shared-memory
-// image the MMA reads: rows of 128 B, 16-byte chunks swizzled by (row mod 8),
-// bf16 hi plane then lo plane (or one TF32 plane).
+// Instruction descriptor of one MMA: M = 128, N = n, FP32 accumulators.
 uint32_t host_idesc(int kind, int n) {
   const uint32_t ab = kind == TC_TF32 ? 2u : 1u;  // TF32 : BF16 operands, F32 accumulate, K-major, M = 128
   return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
@@ -419,13 +416,16 @@ uint32_t host_idesc(int kind, int n) {
 // Packs passes, MMA spans and weight tiles for groups `gs`; `entry(d, k, n)`
 // gives one weight of the contraction.  Tiles are written in the exact
 // shared-memory image the MMA reads: rows of 128 B, 16-byte chunks swizzled by
-// (row mod 8), bf16 hi plane then lo plane (or one TF32 plane).
+// (row mod 8), bf16 hi plane then lo plane (or one TF32 plane).  The groups
+// of a pass are shared out between two MMA issuers (balanced MMA steps), each
+// with its own weight ring.
 template <typename Entry>
 bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entry, TcHost& H) {
   const int chunk = kind == TC_BF16X3 ? 64 : 32;  // reduction values per 128-byte chunk
   const int kstep = chunk / 4;
   const int esz = kind == TC_BF16X3 ? 2 : 4;
   const int planes = kind == TC_BF16X3 ? 2 : 1;
+  auto ksteps_of = [&](int K, int j) { return std::min(4, (K - j * chunk + kstep - 1) / kstep); };
   H.W.clear();
   H.npass = 0;
   size_t gi = 0;
@@ -433,57 +433,107 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
     if (H.npass == kTcMaxPasses) return false;
     TcPass& P = H.pass[H.npass++];
     std::memset(&P, 0, sizeof(P));
-    int cols = 0, kmax = 0;
-    std::vector<int> K;
-    while (gi < gs.size() && P.ng < kTcMaxGroups) {
+    // groups of this pass, in the given (non-increasing K) order, up to 512 TMEM columns
+    std::vector<int> take;
+    int cols = 0;
+    while (gi < gs.size() && (int)take.size() < kTcMaxGroups) {
       const int nm = (gs[gi].ncols + 15) / 16 * 16;
       if (cols + nm > 512) break;
-      if (P.ng > 0 && gs[gi].K > K.back()) return false;  // prefixes must shrink
-      P.out_tmem[P.ng] = cols;
-      P.out_col0[P.ng] = gs[gi].col0;
-      P.out_ncols[P.ng] = gs[gi].ncols;
-      P.out_nmma[P.ng] = nm;
-      K.push_back(gs[gi].K);
-      kmax = std::max(kmax, gs[gi].K);
+      if (!take.empty() && gs[gi].K > gs[take.back()].K) return false;  // prefixes must shrink
+      take.push_back((int)gi);
       cols += nm;
-      ++P.ng;
       ++gi;
     }
-    if (P.ng == 0) return false;
+    if (take.empty()) return false;
+    // issuer of each group: the heaviest groups (MMA steps) first, each to the
+    // issuer with fewer steps so far
+    std::vector<int> order = take;
+    auto steps = [&](int g) {
+      int n = 0;
+      for (int j = 0; j * chunk < gs[g].K; ++j) n += ksteps_of(gs[g].K, j);
+      return n;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return steps(a) > steps(b); });
+    std::vector<int> who(gs.size(), 0);
+    int load[2] = {0, 0};
+    for (int g : order) {
+      const int q = load[0] <= load[1] ? 0 : 1;
+      who[g] = q;
+      load[q] += steps(g);
+    }
+    // TMEM layout: issuer 0's groups, then issuer 1's, each in K order, so a
+    // span covers adjacent groups of one issuer
+    std::vector<int> K;
+    int nq0 = 0, kmax = 0, c = 0;
+    for (int q = 0; q < 2; ++q)
+      for (int g : take) {
+        if (who[g] != q) continue;
+        const int nm = (gs[g].ncols + 15) / 16 * 16;
+        P.out_tmem[P.ng] = c;
+        P.out_col0[P.ng] = gs[g].col0;
+        P.out_ncols[P.ng] = gs[g].ncols;
+        P.out_nmma[P.ng] = nm;
+        K.push_back(gs[g].K);
+        kmax = std::max(kmax, gs[g].K);
+        c += nm;
+        ++P.ng;
+        if (q == 0) ++nq0;
+      }
     int alloc = 32;
     while (alloc < cols) alloc *= 2;
     P.tmem_cols = alloc;
     P.nchunks = (kmax + chunk - 1) / chunk;
     if (P.nchunks > kTcMaxChunks) return false;
-    // spans per chunk, their tile offsets inside one neighbour block
+    // spans per chunk and issuer, their tile offsets inside one neighbour block
     int ns = 0, off = 0;
+    long long vol[2] = {0, 0};
+    int biggest[2] = {0, 0};
     std::vector<std::vector<int>> span_groups;  // groups of each span (global span index)
     for (int j = 0; j < P.nchunks; ++j) {
       P.span0[j] = ns;
-      int g = 0;
-      while (g < P.ng && K[g] > j * chunk) {
-        const int ks = std::min(4, (K[g] - j * chunk + kstep - 1) / kstep);
-        if (ns == kTcMaxSpans) return false;
-        TcSpan& S = P.span[ns];
-        S.tmem_col = P.out_tmem[g];
-        S.n = 0;
-        S.ksteps = ks;
-        std::vector<int> members;
-        while (g < P.ng && K[g] > j * chunk && S.n + P.out_nmma[g] <= kTcMaxSpanN &&
-               std::min(4, (K[g] - j * chunk + kstep - 1) / kstep) == ks) {
-          S.n += P.out_nmma[g];
-          members.push_back(g);
-          ++g;
+      for (int q = 0; q < 2; ++q) {
+        if (q == 1) P.span_mid[j] = ns;
+        int g = q == 0 ? 0 : nq0;
+        const int gend = q == 0 ? nq0 : P.ng;
+        while (g < gend && K[g] > j * chunk) {
+          const int ks = ksteps_of(K[g], j);
+          if (ns == kTcMaxSpans) return false;
+          TcSpan& S = P.span[ns];
+          S.tmem_col = P.out_tmem[g];
+          S.n = 0;
+          S.ksteps = ks;
+          std::vector<int> members;
+          while (g < gend && K[g] > j * chunk && S.n + P.out_nmma[g] <= kTcMaxSpanN && ksteps_of(K[g], j) == ks) {
+            S.n += P.out_nmma[g];
+            members.push_back(g);
+            ++g;
+          }
+          if (members.empty()) return false;
+          S.w_off = off;
+          S.idesc = host_idesc(kind, S.n);
+          const int bytes = S.n * 128 * planes;
+          off += bytes;
+          vol[q] += bytes;
+          biggest[q] = std::max(biggest[q], bytes);
+          span_groups.push_back(members);
+          ++ns;
         }
-        if (members.empty()) return false;
-        S.w_off = off;
-        S.idesc = host_idesc(kind, S.n);
-        off += S.n * 128 * planes;
-        span_groups.push_back(members);
-        ++ns;
       }
     }
     P.span0[P.nchunks] = ns;
+    P.span_mid[P.nchunks] = ns;
+    // weight rings in proportion to the bytes each issuer streams, each able
+    // to hold its largest span
+    int r0 = 0;
+    if (vol[0] > 0 && vol[1] > 0)
+      r0 = (int)((double)kTcBRingBytes * (double)vol[0] / (double)(vol[0] + vol[1])) / 1024 * 1024;
+    else if (vol[0] > 0)
+      r0 = kTcBRingBytes;
+    r0 = std::max(r0, biggest[0]);
+    r0 = std::min(r0, kTcBRingBytes - biggest[1]);
+    if (r0 < biggest[0] || kTcBRingBytes - r0 < biggest[1]) return false;
+    P.ring_bytes[0] = r0;
+    P.ring_bytes[1] = kTcBRingBytes - r0;
     P.bytes_per_d = off;
     P.w_base = (long long)H.W.size();
     H.W.resize(H.W.size() + (size_t)27 * P.bytes_per_d, 0);

@@ -150,8 +150,9 @@ enum TcKind { TC_BF16X3 = 0, TC_TF32 = 1 };
 
 constexpr int kTcMaxGroups = 8;     // column groups per pass
 constexpr int kTcMaxChunks = 48;    // 128-byte reduction chunks per neighbour
-constexpr int kTcMaxSpans = 96;     // MMA spans per pass (all chunks)
+constexpr int kTcMaxSpans = 128;    // MMA spans per pass (all chunks)
 constexpr int kTcMaxSpanN = 192;    // columns of one span (one MMA instruction)
+constexpr int kTcBRingBytes = 150 * 1024;  // shared memory of the two weight rings together
 
 // One MMA instruction shape of a chunk: adjacent column groups that use the
 // chunk with the same number of K steps, merged so that each tcgen05.mma
@@ -176,7 +177,11 @@ struct TcPass {
   int out_col0[kTcMaxGroups];   // first output column (beta*8 + child)
   int out_ncols[kTcMaxGroups];  // real output columns
   int out_nmma[kTcMaxGroups];   // TMEM columns of the group (multiple of 16)
-  int span0[kTcMaxChunks + 1];  // spans of chunk j: span[span0[j] .. span0[j+1])
+  // Two MMA issuers own disjoint column groups.  Spans of chunk j: issuer 0
+  // span[span0[j] .. span_mid[j]), issuer 1 span[span_mid[j] .. span0[j+1]).
+  int span0[kTcMaxChunks + 1];
+  int span_mid[kTcMaxChunks + 1];
+  int ring_bytes[2];            // weight ring of each issuer (multiples of 1024, sum <= kTcBRingBytes)
   TcSpan span[kTcMaxSpans];
 };
 struct TcLaunch {
@@ -195,7 +200,5 @@ struct TcLaunch {
 cudaError_t make_row_map(void* map_out /* CUtensorMap */, const void* base, int row_len, int elem_bytes,
                          const int grid[3], int box_inner);
 cudaError_t launch_m2l_tc(const TcLaunch& L, const void* map_hi, const void* map_lo, cudaStream_t s);
-// FP32 rows -> bf16 hi and lo planes (hi = rn(x), lo = rn(x - hi)).
-cudaError_t launch_split_bf16(const float* src, void* hi, void* lo, size_t count, cudaStream_t s);
 
 }  // namespace fmmgb

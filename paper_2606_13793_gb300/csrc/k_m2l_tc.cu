@@ -17,11 +17,17 @@
 //   * D: FP32 accumulators in tensor memory, one column range per group.
 // Precisions: kind::tf32 on the FP32 rows (one product), or bf16 hi/lo planes
 // with three products hi*hi + hi*lo + lo*hi (kind::f16, BF16 inputs).
-// Roles: warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs, all four warps
-// drain tensor memory in the epilogue.  Every wait is bounded: on time-out
-// the kernel sets the plan's error flag (FMM_ERR_TIMEOUT) and unwinds.
+// Roles: the column groups of a pass are shared out between two MMA issuers
+// (warp 1 and warp 2, lane 0), which accumulate into disjoint tensor-memory
+// columns; each issuer has its own weight ring, filled by its own producer
+// (warp 0 lane 0, which also loads the activations both issuers read, and
+// warp 3 lane 0).  A single issuing thread cannot keep the tensor pipe busy
+// with the narrow low-order spans; two can.  The rings are byte-granular
+// (1 KB units), so small spans do not hold a slot sized for the largest.
+// All four warps drain tensor memory in the epilogue.  Every wait is bounded:
+// on time-out the kernel sets the plan's error flag (FMM_ERR_TIMEOUT) and
+// unwinds; a CTA that sees the flag set by another gives up at once.
 #include <cuda.h>
-#include <cuda_bf16.h>
 
 #include "fmm_internal.h"
 
@@ -29,12 +35,12 @@ namespace fmmgb {
 namespace {
 
 constexpr int kSA = 2;                                   // activation ring stages (both planes)
-constexpr int kSB = 6;                                   // weight ring slots (one plane each)
 constexpr int kARows = kTcTileX * kTcBoxY;               // 144 rows of one activation box
 constexpr int kAPlane = kARows * 128;                    // 18 KB, a multiple of 1024
 constexpr int kAStage = 2 * kAPlane;                     // hi and lo planes
-constexpr int kBStage = kTcMaxSpanN * 128;               // one plane of <= 192 rows x 128 B
-constexpr int kSmemBytes = kSA * kAStage + kSB * kBStage + 1024 /*barriers*/ + 1024 /*alignment*/;
+constexpr int kRingE = 16;                               // spans in flight per weight ring
+constexpr int kSmemBytes = kSA * kAStage + kTcBRingBytes + 1024 /*barriers*/ + 1024 /*alignment*/;
+static_assert(kSmemBytes <= 227 * 1024, "shared memory of the tensor-core kernel");
 constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -74,11 +80,19 @@ __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err,
   const unsigned long long t0 = globaltimer();
   for (uint32_t i = 0;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63u) == 63u && globaltimer() - t0 > kTimeoutNs) {
-      atomicOr(err, 2 | (1 << (8 + site)));
-      return false;
+    if ((i & 63u) == 63u) {
+      if (*reinterpret_cast<volatile int*>(err) & 2) return false;  // another CTA timed out
+      if (globaltimer() - t0 > kTimeoutNs) {
+        atomicOr(err, 2 | (1 << (8 + site)));
+        return false;
+      }
     }
   }
+}
+
+// One inline probe first: most waits are already satisfied.
+__device__ __forceinline__ bool wait_fast(uint64_t* bar, uint32_t parity, int* err, int site) {
+  return mbar_try_wait(bar, parity) || mbar_wait(bar, parity, err, site);
 }
 
 enum WaitSite { W_PROD_A = 0, W_PROD_B, W_MMA_A, W_MMA_B, W_EPI, W_DRAIN };
@@ -170,16 +184,17 @@ __global__ void __launch_bounds__(128, 1)
                   const __grid_constant__ TcLaunch P) {
   constexpr bool split = KIND == TC_BF16X3;
   constexpr int chunk_elems = split ? 64 : 32;
+  constexpr uint32_t planes = split ? 2 : 1;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   unsigned char* a_ring = base;
-  unsigned char* b_ring = base + kSA * kAStage;
-  uint64_t* a_full = reinterpret_cast<uint64_t*>(b_ring + kSB * kBStage);
+  unsigned char* b_rings = base + kSA * kAStage;
+  uint64_t* a_full = reinterpret_cast<uint64_t*>(b_rings + kTcBRingBytes);
   uint64_t* a_empty = a_full + kSA;
-  uint64_t* b_full = a_empty + kSA;
-  uint64_t* b_empty = b_full + kSB;
-  uint64_t* accum = b_empty + kSB;
+  uint64_t* b_full = a_empty + kSA;     // [2][kRingE]
+  uint64_t* b_empty = b_full + 2 * kRingE;  // [2][kRingE]
+  uint64_t* accum = b_empty + 2 * kRingE;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
 
   const TcPass& pass = P.pass[blockIdx.y];
@@ -190,9 +205,9 @@ __global__ void __launch_bounds__(128, 1)
   const int oz = (blockIdx.x / (ntx * nty)) * kTcTileZ;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kSA; ++i) mbar_init(&a_full[i], 1), mbar_init(&a_empty[i], 1);
-    for (int i = 0; i < kSB; ++i) mbar_init(&b_full[i], 1), mbar_init(&b_empty[i], 1);
-    mbar_init(accum, 1);
+    for (int i = 0; i < kSA; ++i) mbar_init(&a_full[i], 1), mbar_init(&a_empty[i], 2);  // both issuers release
+    for (int i = 0; i < 2 * kRingE; ++i) mbar_init(&b_full[i], 1), mbar_init(&b_empty[i], 1);
+    mbar_init(accum, 2);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -206,72 +221,97 @@ __global__ void __launch_bounds__(128, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer ----------------
-    // Order: neighbour column (dx, dz), chunk j, then dy and the chunk's spans.
-    // One activation box (rows y-1 .. y+16 of the shifted x/z column) serves
-    // the three dy neighbours.
-    uint32_t ai = 0, bi = 0;
-    bool ok = true;
+  if ((warp == 0 || warp == 3) && lane == 0) {
+    // ---------------- producers ----------------
+    // Ring q = warp / 3.  Order: neighbour column (dx, dz), chunk j, then dy
+    // and the issuer's spans of the chunk.  Producer 0 also loads the
+    // activation box (rows y-1 .. y+16 of the shifted x/z column), which
+    // serves the three dy neighbours of both issuers.
+    const int q = warp == 3 ? 1 : 0;
+    const uint32_t RB = (uint32_t)pass.ring_bytes[q];
+    unsigned char* ring = b_rings + (q ? pass.ring_bytes[0] : 0);
+    uint64_t* full = b_full + q * kRingE;
+    uint64_t* empty = b_empty + q * kRingE;
+    // Byte ring in virtual positions: v = start of the next span, last =
+    // end of the last span written, freed = end of the spans released so far.
+    // A span that does not fit before the end of the ring starts at offset 0;
+    // it may be written once the live data [freed, last) no longer overlaps
+    // its physical range, i.e. freed >= min(last, v + bytes - RB).
+    uint32_t end_v[kRingE];
+    uint32_t ai = 0, e = 0, tail = 0, v = 0, off = 0, freed = 0, last = 0;
+    bool ok = !(*reinterpret_cast<volatile int*>(P.err) & 2);
     const unsigned char* wpass = P.W + pass.w_base;
     for (int xz = 0; ok && xz < 9; ++xz) {
       const int dx = xz % 3 - 1, dz = xz / 3 - 1;
       for (int j = 0; ok && j < pass.nchunks; ++j) {
-        const int sa = ai % kSA;
-        if (!(ok = mbar_wait(&a_empty[sa], ((ai / kSA) & 1) ^ 1, P.err, W_PROD_A))) break;
-        unsigned char* adst = a_ring + sa * kAStage;
-        mbar_expect_tx(&a_full[sa], split ? 2 * kAPlane : kAPlane);
-        tma_load_4d(adst, &map_hi, &a_full[sa], j * chunk_elems, ox + dx, oy - 1, oz + dz);
-        if (split) tma_load_4d(adst + kAPlane, &map_lo, &a_full[sa], j * chunk_elems, ox + dx, oy - 1, oz + dz);
-        ++ai;
-        const int s0 = pass.span0[j], s1 = pass.span0[j + 1];
+        if (q == 0) {
+          const int sa = ai % kSA;
+          if (!(ok = wait_fast(&a_empty[sa], ((ai / kSA) & 1) ^ 1, P.err, W_PROD_A))) break;
+          unsigned char* adst = a_ring + sa * kAStage;
+          mbar_expect_tx(&a_full[sa], split ? 2 * kAPlane : kAPlane);
+          tma_load_4d(adst, &map_hi, &a_full[sa], j * chunk_elems, ox + dx, oy - 1, oz + dz);
+          if (split) tma_load_4d(adst + kAPlane, &map_lo, &a_full[sa], j * chunk_elems, ox + dx, oy - 1, oz + dz);
+          ++ai;
+        }
+        const int s0 = q ? pass.span_mid[j] : pass.span0[j], s1 = q ? pass.span0[j + 1] : pass.span_mid[j];
         for (int dy = 0; ok && dy < 3; ++dy) {
           const unsigned char* wd = wpass + (long long)((dx + 1) + 3 * dy + 9 * (dz + 1)) * pass.bytes_per_d;
-          for (int si = s0; ok && si < s1; ++si) {
-            const uint32_t plane = (uint32_t)pass.span[si].n * 128;
-            const unsigned char* src = wd + pass.span[si].w_off;
-            for (int h = 0; h < (split ? 2 : 1); ++h) {  // hi plane, then lo plane: one slot each
-              const int sb = bi % kSB;
-              if (!(ok = mbar_wait(&b_empty[sb], ((bi / kSB) & 1) ^ 1, P.err, W_PROD_B))) break;
-              mbar_expect_tx(&b_full[sb], plane);
-              bulk_load(b_ring + sb * kBStage, src + h * plane, plane, &b_full[sb]);
-              ++bi;
+          for (int si = s0; si < s1; ++si) {
+            const uint32_t bytes = (uint32_t)pass.span[si].n * 128u * planes;
+            if (off + bytes > RB) v += RB - off, off = 0;  // a span never wraps
+            const uint32_t need = v + bytes > RB ? min(last, v + bytes - RB) : 0u;
+            while (freed < need || e - tail >= (uint32_t)kRingE) {  // release the oldest span
+              if (!(ok = wait_fast(&empty[tail % kRingE], (tail / kRingE) & 1, P.err, W_PROD_B))) break;
+              freed = end_v[tail % kRingE];
+              ++tail;
             }
+            if (!ok) break;
+            mbar_expect_tx(&full[e % kRingE], bytes);
+            bulk_load(ring + off, wd + pass.span[si].w_off, bytes, &full[e % kRingE]);
+            end_v[e % kRingE] = v + bytes;
+            v += bytes;
+            last = v;
+            off += bytes;
+            ++e;
           }
         }
       }
     }
     if (!ok) {
       // drain: never leave the CTA with copies in flight
-      for (uint32_t q = (ai > kSA ? ai - kSA : 0); q < ai; ++q)
-        mbar_wait(&a_full[q % kSA], (q / kSA) & 1, P.err, W_DRAIN);
-      for (uint32_t q = (bi > kSB ? bi - kSB : 0); q < bi; ++q)
-        mbar_wait(&b_full[q % kSB], (q / kSB) & 1, P.err, W_DRAIN);
+      if (q == 0)
+        for (uint32_t i = (ai > kSA ? ai - kSA : 0); i < ai; ++i)
+          mbar_wait(&a_full[i % kSA], (i / kSA) & 1, P.err, W_DRAIN);
+      for (uint32_t i = tail; i < e; ++i) mbar_wait(&full[i % kRingE], (i / kRingE) & 1, P.err, W_DRAIN);
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer (lean: descriptors precomputed per stage) ----------------
-    uint32_t ai = 0, bi = 0;
-    bool ok = true;
+  } else if ((warp == 1 || warp == 2) && lane == 0) {
+    // ---------------- MMA issuers ----------------
+    const int q = warp - 1;
+    const uint32_t RB = (uint32_t)pass.ring_bytes[q];
+    const uint64_t ring_desc = sw128_desc(smem_u32(b_rings + (q ? pass.ring_bytes[0] : 0)));
+    uint64_t* full = b_full + q * kRingE;
+    uint64_t* empty = b_empty + q * kRingE;
+    uint32_t ai = 0, e = 0, off = 0;
+    bool ok = !(*reinterpret_cast<volatile int*>(P.err) & 2);
     for (int xz = 0; ok && xz < 9; ++xz) {
       for (int j = 0; ok && j < pass.nchunks; ++j) {
         const int sa = ai % kSA;
-        if (!(ok = mbar_wait(&a_full[sa], (ai / kSA) & 1, P.err, W_MMA_A))) break;
+        if (!(ok = wait_fast(&a_full[sa], (ai / kSA) & 1, P.err, W_MMA_A))) break;
         tc_fence_after();
         const uint64_t a_desc = sw128_desc(smem_u32(a_ring + sa * kAStage));
-        const int s0 = pass.span0[j], s1 = pass.span0[j + 1];
+        const int s0 = q ? pass.span_mid[j] : pass.span0[j], s1 = q ? pass.span0[j + 1] : pass.span_mid[j];
         for (int dy = 0; ok && dy < 3; ++dy) {
           const uint64_t a = a_desc + (uint64_t)(dy * (kTcTileX * 128 / 16));  // 128-row window
           const uint64_t a_lo = a + (uint64_t)(kAPlane / 16);
           const uint32_t acc0 = (xz == 0 && j == 0 && dy == 0) ? 0u : 1u;  // the first step opens every group
-          for (int si = s0; ok && si < s1; ++si) {
+          for (int si = s0; si < s1; ++si) {
             const TcSpan& S = pass.span[si];
-            const int sb = bi % kSB;
-            const int sb2 = (bi + 1) % kSB;  // lo plane (bf16x3)
-            if (!(ok = mbar_wait(&b_full[sb], (bi / kSB) & 1, P.err, W_MMA_B))) break;
-            if (split && !(ok = mbar_wait(&b_full[sb2], ((bi + 1) / kSB) & 1, P.err, W_MMA_B))) break;
+            const uint32_t plane = (uint32_t)S.n * 128u;
+            if (off + plane * planes > RB) off = 0;
+            if (!(ok = wait_fast(&full[e % kRingE], (e / kRingE) & 1, P.err, W_MMA_B))) break;
             tc_fence_after();
-            const uint64_t b = sw128_desc(smem_u32(b_ring + sb * kBStage));
-            const uint64_t b_lo = sw128_desc(smem_u32(b_ring + sb2 * kBStage));
+            const uint64_t b = ring_desc + (uint64_t)(off >> 4);
+            const uint64_t b_lo = b + (uint64_t)(plane >> 4);
             const uint32_t d = tmem + (uint32_t)S.tmem_col;
             switch (S.ksteps) {
               case 1: issue_span<KIND, 1>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
@@ -279,16 +319,16 @@ __global__ void __launch_bounds__(128, 1)
               case 3: issue_span<KIND, 3>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
               default: issue_span<KIND, 4>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
             }
-            mma_commit(&b_empty[sb]);
-            if (split) mma_commit(&b_empty[sb2]);
-            bi += split ? 2 : 1;
+            mma_commit(&empty[e % kRingE]);
+            off += plane * planes;
+            ++e;
           }
         }
         mma_commit(&a_empty[sa]);
         ++ai;
       }
     }
-    mma_commit(accum);  // fires when every MMA issued above has completed
+    mma_commit(accum);  // fires when every MMA this thread issued has completed
   }
   __syncwarp();
 
@@ -330,16 +370,6 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)pass.tmem_cols));
-  }
-}
-
-__global__ void split_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ hi,
-                                  __nv_bfloat16* __restrict__ lo, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const float x = src[i];
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    hi[i] = h;
-    lo[i] = __float2bfloat16_rn(x - __bfloat162float(h));
   }
 }
 
@@ -392,13 +422,5 @@ cudaError_t launch_m2l_tc(const TcLaunch& L, const void* map_hi, const void* map
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_bf16(const float* src, void* hi, void* lo, size_t count, cudaStream_t s) {
-  if (count == 0) return cudaSuccess;
-  size_t blocks = (count + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
-  split_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, static_cast<__nv_bfloat16*>(hi),
-                                                     static_cast<__nv_bfloat16*>(lo), count);
-  return cudaGetLastError();
-}
 
 }  // namespace fmmgb
