@@ -184,6 +184,9 @@ struct fmm_plan_s {
   void* d_io_phi = nullptr;
   void* d_io_acc = nullptr;
   cudaStream_t last_stream = nullptr;
+  // side stream of the concurrent far field (CUDA-core M2L levels), fork/join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -262,6 +265,11 @@ struct fmm_plan_s {
     cudaDeviceSynchronize();
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     ev_pool.clear();
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
+    ev_fork = ev_join = nullptr;
+    side = nullptr;
     for (void* d : allocs) cudaFree(d);
     allocs.clear();
     if (d_io_rho) cudaFree(d_io_rho);
@@ -904,7 +912,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     if (e != cudaSuccess) return cleanup(fail(FMM_ERR_CUDA, "tensor map encoding failed for the near field"));
   }
   P->tc.err = P->d_flag;
-  P->tc.accumulate = 1;
+  P->tc.accumulate = 0;
   for (int l = 2; l <= P->L; ++l)
     if (!P->lev[l].tc) zrun_default(m2l_gemm(P, l), P->h_m2l_tile_k, &P->m2l_choice[l]);
   if (!P->near_tc) zrun_default(near_gemm(P), P->h_near_tile_k, &P->near_choice);
@@ -967,6 +975,11 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
   fmm_plan_t P = new (std::nothrow) fmm_plan_s();
   if (!P) return fail(FMM_ERR_ALLOC, "host allocation failed");
   fmm_status st = plan_init(P, d3, grid->dx, grid->G, order, leaf, o, static_cast<cudaStream_t>(stream), dev);
+  if (st == FMM_OK &&
+      (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
+       cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+       cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess))
+    st = fail(FMM_ERR_CUDA, "stream or event creation failed");
   if (st != FMM_OK) {
     P->release();
     delete P;
@@ -1019,18 +1032,19 @@ fmm_status do_m2m(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s) {
   return FMM_OK;
 }
 
+// L(l) += L2L(L(l - 1)) for l >= 3; the level's M2L has written L(l) (level 2
+// has no parent far field: its locals are its M2L alone).
 fmm_status do_l2l(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s) {
   const Level &q = P->lev[l - 1], &c = P->lev[l];
   cudaError_t e;
-  if (l == 2) {  // the far field of level 2 is empty
-    e = c.f64 ? launch_zero<double>(static_cast<double*>(P->Lx(l)), c.bytes / 8, s)
-              : launch_zero<float>(static_cast<float*>(P->Lx(l)), c.bytes / 4, s);
-  } else if (q.f64 && c.f64) {
-    e = launch_l2l<double, double>(tt, q, static_cast<const double*>(P->Lx(l - 1)), c, static_cast<double*>(P->Lx(l)), s);
+  if (q.f64 && c.f64) {
+    e = launch_l2l<double, double>(tt, q, static_cast<const double*>(P->Lx(l - 1)), c, static_cast<double*>(P->Lx(l)),
+                                   1, s);
   } else if (q.f64) {
-    e = launch_l2l<double, float>(tt, q, static_cast<const double*>(P->Lx(l - 1)), c, static_cast<float*>(P->Lx(l)), s);
+    e = launch_l2l<double, float>(tt, q, static_cast<const double*>(P->Lx(l - 1)), c, static_cast<float*>(P->Lx(l)), 1,
+                                  s);
   } else {
-    e = launch_l2l<float, float>(tt, q, static_cast<const float*>(P->Lx(l - 1)), c, static_cast<float*>(P->Lx(l)), s);
+    e = launch_l2l<float, float>(tt, q, static_cast<const float*>(P->Lx(l - 1)), c, static_cast<float*>(P->Lx(l)), 1, s);
   }
   CUDA_TRY(e);
   return FMM_OK;
@@ -1048,7 +1062,7 @@ NbrGemm m2l_gemm(fmm_plan_t P, int l) {
   g.C = P->Lx(l);
   g.n_cols = 8 * P->nc;
   g.ntiles = P->m2l_ntiles;
-  g.accumulate = 1;
+  g.accumulate = 0;  // M2L writes the level's locals; L2L adds the parent's
   g.shape = P->m2l_choice[l].shape;
   g.dsplit = P->m2l_choice[l].dsplit;
   g.partial = P->arena + P->part_off;
@@ -1108,26 +1122,53 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
     StageTimer t(P, ST_M2M, s);
     if ((st = do_m2m(P, tt, l, s))) return st;
   }
-  // downward pass
+  // Far and near field.  Each level's M2L reads only the multipoles, so all
+  // levels run at once: the CUDA-core levels (FP64 coarse levels, or every
+  // level of the FP32/FP64 precisions) on the plan's side stream, the
+  // tensor-core levels and the near field on `s`; the two use different
+  // units of the SM.  The L2L chain then adds the parents' locals, coarse to
+  // fine.  A near field split over neighbour groups shares the split scratch
+  // with the CUDA-core levels, so it runs after them on the same stream.
   if (L < 2) {
     StageTimer t(P, ST_L2L, s);
     CUDA_TRY(launch_zero<T>(static_cast<T*>(P->Lx(L)), P->lev[L].bytes / sizeof(T), s));
   }
+  bool any_simt = false;
+  for (int l = 2; l <= L; ++l) any_simt |= !P->lev[l].tc;
+  const bool near_side = !P->near_tc && P->near_choice.dsplit > 1;
+  const bool fork = P->side && (any_simt || near_side);
+  cudaStream_t sf = fork ? P->side : s;
+  if (fork) {
+    CUDA_TRY(cudaEventRecord(P->ev_fork, s));
+    CUDA_TRY(cudaStreamWaitEvent(sf, P->ev_fork, 0));
+  }
   for (int l = 2; l <= L; ++l) {
-    {
-      StageTimer t(P, ST_L2L, s);
-      if ((st = do_l2l(P, tt, l, s))) return st;
-    }
-    StageTimer t(P, P->lev[l].tc ? ST_M2L_TC : ST_M2L, s);
+    if (P->lev[l].tc) continue;
+    StageTimer t(P, ST_M2L, sf);
+    if ((st = do_m2l(P, l, sf))) return st;
+  }
+  if (near_side) {
+    StageTimer t(P, ST_NEAR, sf);
+    CUDA_TRY(launch_nbr_gemm<T>(near_gemm(P), sf));
+  }
+  if (fork) CUDA_TRY(cudaEventRecord(P->ev_join, sf));
+  for (int l = 2; l <= L; ++l) {
+    if (!P->lev[l].tc) continue;
+    StageTimer t(P, ST_M2L_TC, s);
     if ((st = do_m2l(P, l, s))) return st;
   }
   // near field over the 27 neighbour leaf boxes
   if (P->near_tc) {
     StageTimer t(P, ST_NEAR_TC, s);
     CUDA_TRY(launch_m2l_tc(P->tcn, P->map_near_hi, P->map_near_lo, s));
-  } else {
+  } else if (!near_side) {
     StageTimer t(P, ST_NEAR, s);
     CUDA_TRY(launch_nbr_gemm<T>(near_gemm(P), s));
+  }
+  if (fork) CUDA_TRY(cudaStreamWaitEvent(s, P->ev_join, 0));
+  for (int l = 3; l <= L; ++l) {
+    StageTimer t(P, ST_L2L, s);
+    if ((st = do_l2l(P, tt, l, s))) return st;
   }
   {
     StageTimer t(P, ST_LEAF, s);
@@ -1243,7 +1284,7 @@ int fmm_solve_launches(fmm_plan_t P, int with_accel) {
   n += std::max(0, L - 2);              // M2M for l = L .. 3
   if (L < 2) n += 1;                    // zero the leaf locals
   for (int l = 2; l <= L; ++l) {
-    n += 2;                             // L2L (or zero) + M2L
+    n += l >= 3 ? 2 : 1;                // M2L, and L2L below level 2
     if (!P->lev[l].tc && P->m2l_choice[l].dsplit > 1) n += 1;  // reduction of the neighbour partials
   }
   n += 2;                               // near field + leaf finish

@@ -112,7 +112,9 @@ template <typename Tc, typename Tp>
 cudaError_t launch_m2m(const TreeTables& t, const Level& child, const Tc* Mc, const Level& par, Tp* Mp, void* Mhi,
                        void* Mlo, cudaStream_t s);
 template <typename Tp, typename Tc>
-cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, const Level& child, Tc* Lc, cudaStream_t s);
+// accumulate = 1: child locals += shifted parent locals (after the level's M2L wrote them)
+cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, const Level& child, Tc* Lc, int accumulate,
+                       cudaStream_t s);
 template <typename T>
 cudaError_t launch_zero(T* p, size_t count, cudaStream_t s);
 template <typename T>
@@ -152,7 +154,10 @@ constexpr int kTcMaxGroups = 8;     // column groups per pass
 constexpr int kTcMaxChunks = 48;    // 128-byte reduction chunks per neighbour
 constexpr int kTcMaxSpans = 128;    // MMA spans per pass (all chunks)
 constexpr int kTcMaxSpanN = 192;    // columns of one span (one MMA instruction)
-constexpr int kTcBRingBytes = 150 * 1024;  // shared memory of the two weight rings together
+// Shared memory of the two weight rings together.  With it the tensor-core
+// kernel leaves room on its SM for one FP64 CUDA-core contraction block
+// (12.4 KB), so coarse FP64 levels run beside the tensor-core levels.
+constexpr int kTcBRingBytes = 138 * 1024;
 
 // One MMA instruction shape of a chunk: adjacent column groups that use the
 // chunk with the same number of K steps, merged so that each tcgen05.mma

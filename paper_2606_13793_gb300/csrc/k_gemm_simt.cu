@@ -25,10 +25,16 @@ namespace {
 constexpr int kRows = 64;
 constexpr int kPad = 1;
 
+// Reduction values per stage: 32 (FP32) or 16 (FP64), i.e. 12.4 KB of shared
+// memory for FP64, small enough to sit beside a tensor-core block.
+template <typename T>
+constexpr int kChunkOf = sizeof(T) == 8 ? kKChunk / 2 : kKChunk;
+
 template <typename T>
 __global__ void __launch_bounds__(64) nbr_gemm_simt_kernel(NbrGemm g) {
-  __shared__ T As[kKChunk][kRows + kPad];
-  __shared__ T Bs[kKChunk][kNTile];
+  constexpr int KC = kChunkOf<T>;
+  __shared__ T As[KC][kRows + kPad];
+  __shared__ T Bs[KC][kNTile];
   const int tile = blockIdx.y;
   const int tx = threadIdx.x;
   const int rg = tx & 7;   // rows rg*8 .. rg*8+7
@@ -51,10 +57,10 @@ __global__ void __launch_bounds__(64) nbr_gemm_simt_kernel(NbrGemm g) {
   for (int d = d0; d < d1; ++d) {
     const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
     const T* Wd = W0 + (long long)d * K * kNTile;
-    for (int kc = 0; kc < K; kc += kKChunk) {
-      const int kn = min(kKChunk, K - kc);
-      for (int e = tx; e < kRows * kKChunk; e += 64) {
-        const int r = e / kKChunk, k = e % kKChunk;
+    for (int kc = 0; kc < K; kc += KC) {
+      const int kn = min(KC, K - kc);
+      for (int e = tx; e < kRows * KC; e += 64) {
+        const int r = e / KC, k = e % KC;
         T v = T(0);
         if (k < kn) {
           const int x = ox + (r & 3) + dx, y = oy + ((r >> 2) & 3) + dy, z = oz + (r >> 4) + dz;
@@ -63,7 +69,7 @@ __global__ void __launch_bounds__(64) nbr_gemm_simt_kernel(NbrGemm g) {
         }
         As[k][r] = v;
       }
-      for (int e = tx; e < kKChunk * kNTile; e += 64) {
+      for (int e = tx; e < KC * kNTile; e += 64) {
         const int k = e / kNTile, n = e % kNTile;
         Bs[k][n] = (k < kn) ? Wd[(long long)(kc + k) * kNTile + n] : T(0);
       }

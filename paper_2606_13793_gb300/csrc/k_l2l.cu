@@ -10,10 +10,11 @@ using namespace tree;
 // ---------------------------------------------------------------------------
 // L2L (Sec. 2.3, eq. L2L, parent centre -> child centre), scaled:
 //   Lt_beta(C) = sum_{gamma >= beta} C(gamma,beta) 2^(-1-|gamma|) (+-1/2)^(gamma-beta) Lt_gamma(P)
-// Writes (overwrites) the children's block; the level's M2L then accumulates.
+// Adds to the children's block, which the level's M2L has already written
+// (accumulate = 0 overwrites it instead).
 template <int P, typename Tp, typename Tc>
 __global__ void __launch_bounds__(kThreads) l2l_kernel(Level par, const Tp* __restrict__ Lp, Level child,
-                                                       Tc* __restrict__ Lc) {
+                                                       Tc* __restrict__ Lc, int accumulate) {
   constexpr int NC = ncoef_c(P);
   const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
   const long long p = t >> 3;  // box of the parent level == parent block of the child level
@@ -40,24 +41,26 @@ __global__ void __launch_bounds__(kThreads) l2l_kernel(Level par, const Tp* __re
   shift_down<P, 2, Tp>(L, dp);
   Tc* dst = Lc + p * 8 * NC + c;
 #pragma unroll
-  for (int k = 0; k < NC; ++k) dst[k * 8] = Tc(L[k]);
+  for (int k = 0; k < NC; ++k) dst[k * 8] = accumulate ? Tc(dst[k * 8] + Tc(L[k])) : Tc(L[k]);
 }
 
 }  // namespace
 
 template <typename Tp, typename Tc>
-cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, const Level& child, Tc* Lc, cudaStream_t s) {
+cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, const Level& child, Tc* Lc, int accumulate,
+                       cudaStream_t s) {
   const long long threads = par.nbox * 8;
   if (threads == 0) return cudaSuccess;
-  FMM_ORDER_SWITCH(t.p, (l2l_kernel<PP, Tp, Tc><<<grid_threads(threads), kThreads, 0, s>>>(par, Lp, child, Lc)));
+  FMM_ORDER_SWITCH(t.p,
+                   (l2l_kernel<PP, Tp, Tc><<<grid_threads(threads), kThreads, 0, s>>>(par, Lp, child, Lc, accumulate)));
   return cudaGetLastError();
 }
 
-template cudaError_t launch_l2l<float, float>(const TreeTables&, const Level&, const float*, const Level&, float*,
+template cudaError_t launch_l2l<float, float>(const TreeTables&, const Level&, const float*, const Level&, float*, int,
                                               cudaStream_t);
 template cudaError_t launch_l2l<double, double>(const TreeTables&, const Level&, const double*, const Level&,
-                                                double*, cudaStream_t);
+                                                double*, int, cudaStream_t);
 template cudaError_t launch_l2l<double, float>(const TreeTables&, const Level&, const double*, const Level&, float*,
-                                               cudaStream_t);
+                                               int, cudaStream_t);
 
 }  // namespace fmmgb
