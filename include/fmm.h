@@ -197,9 +197,12 @@ fmm_status fmm_solve_static(const fmm_grid* grid, int order, int leaf, const voi
  *                         -1 = near field): shape 0 = 4x4x4 rows per block,
  *                         shapes 1 and 2 = z-run register tiles
  *                         (8x4x8 / 8x4x4 rows for FP32, 8x4x4 / 8x4x2 for
- *                         FP64), and the number of blocks sharing the 27
- *                         neighbours of a row tile (shape 0: 1 or 27; shapes
- *                         1, 2: 1, 3 or 9).
+ *                         FP64), shape 3 = one output column per lane, 16
+ *                         rows per block, no shared memory (the coarse FP64
+ *                         levels of the tensor-core precisions default to
+ *                         it; shapes 1 and 2 are not used there), and the
+ *                         number of blocks sharing the 27 neighbours of a row
+ *                         tile (shapes 0, 3: 1 or 27; shapes 1, 2: 1, 3 or 9).
  *   fmm_plan_set_tuning : sets it; FMM_ERR_ARG if the variant does not apply
  *                         (level on the tensor cores, reduction lengths not a
  *                         multiple of 8, split scratch too small).

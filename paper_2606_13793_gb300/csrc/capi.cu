@@ -789,8 +789,12 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
   }
   // Default variants before any tuning: the small levels split over their 27
   // neighbours (4x4x4 tiles), the rest on z-run tiles where they apply.
-  auto zrun_default = [&](NbrGemm g, const std::vector<int>& tk, fmm_plan_s::SimtChoice* c) {
+  auto zrun_default = [&](NbrGemm g, const std::vector<int>& tk, fmm_plan_s::SimtChoice* c, bool f64) {
     g.dsplit = 1;
+    if (f64 && P->tc_kind >= 0) {  // coarse FP64 levels beside the tensor-core levels
+      c->shape = 3;
+      return;
+    }
     if (c->dsplit == 1 && zrun_eligible(g, tk.data(), (int)tk.size())) c->shape = 1;
   };
   P->arena_bytes = off;
@@ -914,8 +918,8 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
   P->tc.err = P->d_flag;
   P->tc.accumulate = 0;
   for (int l = 2; l <= P->L; ++l)
-    if (!P->lev[l].tc) zrun_default(m2l_gemm(P, l), P->h_m2l_tile_k, &P->m2l_choice[l]);
-  if (!P->near_tc) zrun_default(near_gemm(P), P->h_near_tile_k, &P->near_choice);
+    if (!P->lev[l].tc) zrun_default(m2l_gemm(P, l), P->h_m2l_tile_k, &P->m2l_choice[l], P->lev[l].f64);
+  if (!P->near_tc) zrun_default(near_gemm(P), P->h_near_tile_k, &P->near_choice, P->f64_data());
   // uploads read host vectors that go out of scope here (plans only; the
   // allocation-free solve orders its copies on the caller's stream)
   if (!P->static_base && cudaStreamSynchronize(s) != cudaSuccess)
@@ -1583,9 +1587,12 @@ std::mutex g_tune_mu;
 std::map<std::string, SimtChoice> g_tune_cache;
 
 bool choice_valid(fmm_plan_t P, NbrGemm g, const std::vector<int>& tk, size_t es, SimtChoice c) {
+  // FP64 levels of a tensor-core plan keep the small-footprint tile that can
+  // share an SM with a tensor-core CTA
+  if ((c.shape == 1 || c.shape == 2) && es == 8 && P->tc_kind >= 0) return false;
   const size_t one = (size_t)g.grid[0] * g.grid[1] * g.grid[2] * (size_t)g.n_cols * es;
   if (c.dsplit > 1 && (size_t)c.dsplit * one > P->part_cap) return false;
-  if (c.shape == 0) return c.dsplit == 1 || c.dsplit == 27;
+  if (c.shape == 0 || c.shape == 3) return c.dsplit == 1 || c.dsplit == 27;
   if (c.shape != 1 && c.shape != 2) return false;
   g.dsplit = c.dsplit;
   return zrun_eligible(g, tk.data(), (int)tk.size());
@@ -1606,7 +1613,7 @@ fmm_status tune_one(fmm_plan_t P, NbrGemm g, const std::vector<int>& tk, const c
     }
   }
   std::vector<SimtChoice> cand;
-  const SimtChoice all[] = {{0, 1}, {0, 27}, {1, 1}, {1, 3}, {1, 9}, {2, 1}, {2, 3}, {2, 9}};
+  const SimtChoice all[] = {{0, 1}, {0, 27}, {1, 1}, {1, 3}, {1, 9}, {2, 1}, {2, 3}, {2, 9}, {3, 1}, {3, 27}};
   for (const SimtChoice& c : all)
     if (choice_valid(P, g, tk, sizeof(T), c)) cand.push_back(c);
   cudaEvent_t e0 = nullptr, e1 = nullptr;

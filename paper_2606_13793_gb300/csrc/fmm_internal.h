@@ -71,9 +71,11 @@ struct NbrGemm {
   int ntiles;
   int accumulate;      // 1: C += result, 0: C = result
   int dsplit;          // CTAs sharing the 27 neighbours of a row tile (partial sums reduced in a fixed order):
-                       // shape 0: 1 or 27; shapes 1, 2: 1, 3 or 9
+                       // shapes 0, 3: 1 or 27; shapes 1, 2: 1, 3 or 9
   void* partial;       // [dsplit][rows][n_cols] scratch when dsplit > 1
-  int shape = 0;       // 0: 4x4x4 rows per CTA (k_gemm_simt.cu); 1, 2: z-run tiles (k_gemm_zrun.cu)
+  int shape = 0;       // 0: 4x4x4 rows per CTA, 3: one column per lane (k_gemm_simt.cu);
+                       // 1, 2: z-run tiles (k_gemm_zrun.cu)
+  int max_blocks = 0;  // shape 0: at most this many CTAs, each looping over work items (0: one per item)
 };
 
 template <typename T>
@@ -155,7 +157,7 @@ constexpr int kTcMaxChunks = 48;    // 128-byte reduction chunks per neighbour
 constexpr int kTcMaxSpans = 128;    // MMA spans per pass (all chunks)
 constexpr int kTcMaxSpanN = 192;    // columns of one span (one MMA instruction)
 // Shared memory of the two weight rings together.  With it the tensor-core
-// kernel leaves room on its SM for one FP64 CUDA-core contraction block
+// kernel leaves room on its SM for an FP64 CUDA-core contraction block
 // (12.4 KB), so coarse FP64 levels run beside the tensor-core levels.
 constexpr int kTcBRingBytes = 138 * 1024;
 

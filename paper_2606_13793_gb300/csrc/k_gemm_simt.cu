@@ -16,7 +16,10 @@
 //
 // A neighbour outside the grid contributes zero: that is the isolated
 // boundary.  Tile: 64 rows (a 4x4x4 block of the row grid) x 32 columns,
-// 64 threads, each thread an 8x4 register tile.
+// 64 threads, each thread an 8x4 register tile.  A work item is one (row
+// tile, column tile, neighbour) combination; a launch may cap its CTAs, each
+// then looping over items (a few persistent CTAs that share SMs with other
+// kernels instead of flooding them).
 #include "fmm_internal.h"
 
 namespace fmmgb {
@@ -35,79 +38,152 @@ __global__ void __launch_bounds__(64) nbr_gemm_simt_kernel(NbrGemm g) {
   constexpr int KC = kChunkOf<T>;
   __shared__ T As[KC][kRows + kPad];
   __shared__ T Bs[KC][kNTile];
-  const int tile = blockIdx.y;
   const int tx = threadIdx.x;
   const int rg = tx & 7;   // rows rg*8 .. rg*8+7
   const int cg = tx >> 3;  // cols cg*4 .. cg*4+3
-  const int ntx = (g.grid[0] + 3) >> 2, nty = (g.grid[1] + 3) >> 2;
-  const int bt = blockIdx.x;
-  const int ox = (bt % ntx) * 4, oy = ((bt / ntx) % nty) * 4, oz = (bt / (ntx * nty)) * 4;
-  const int K = g.tile_k[tile];
-  const T* W0 = static_cast<const T*>(g.W) + g.tile_w[tile];
-  const T* A = static_cast<const T*>(g.A);
+  const int ntx = (g.grid[0] + 3) >> 2, nty = (g.grid[1] + 3) >> 2, ntz = (g.grid[2] + 3) >> 2;
+  const long long tiles = (long long)ntx * nty * ntz;
+  const long long items = tiles * g.ntiles * (g.dsplit > 1 ? 27 : 1);
+  for (long long w = blockIdx.x; w < items; w += gridDim.x) {
+    const int bt = (int)(w % tiles);
+    const int tile = (int)((w / tiles) % g.ntiles);
+    const int dgrp = (int)(w / (tiles * g.ntiles));
+    const int ox = (bt % ntx) * 4, oy = ((bt / ntx) % nty) * 4, oz = (bt / (ntx * nty)) * 4;
+    const int K = g.tile_k[tile];
+    const T* W0 = static_cast<const T*>(g.W) + g.tile_w[tile];
+    const T* A = static_cast<const T*>(g.A);
 
-  T acc[8][4];
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    T acc[8][4];
+  #pragma unroll
+    for (int i = 0; i < 8; ++i)
+  #pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 
+    const int d0 = g.dsplit > 1 ? dgrp : 0;  // dsplit is 1 or 27 here
+    const int d1 = g.dsplit > 1 ? d0 + 1 : 27;
+    for (int d = d0; d < d1; ++d) {
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      const T* Wd = W0 + (long long)d * K * kNTile;
+      for (int kc = 0; kc < K; kc += KC) {
+        const int kn = min(KC, K - kc);
+        for (int e = tx; e < kRows * KC; e += 64) {
+          const int r = e / KC, k = e % KC;
+          T v = T(0);
+          if (k < kn) {
+            const int x = ox + (r & 3) + dx, y = oy + ((r >> 2) & 3) + dy, z = oz + (r >> 4) + dz;
+            if (x >= 0 && y >= 0 && z >= 0 && x < g.grid[0] && y < g.grid[1] && z < g.grid[2])
+              v = A[(((long long)z * g.grid[1] + y) * g.grid[0] + x) * g.row_len + kc + k];
+          }
+          As[k][r] = v;
+        }
+        for (int e = tx; e < KC * kNTile; e += 64) {
+          const int k = e / kNTile, n = e % kNTile;
+          Bs[k][n] = (k < kn) ? Wd[(long long)(kc + k) * kNTile + n] : T(0);
+        }
+        __syncthreads();
+        for (int k = 0; k < kn; ++k) {
+          T a[8], b[4];
+  #pragma unroll
+          for (int i = 0; i < 8; ++i) a[i] = As[k][rg * 8 + i];
+  #pragma unroll
+          for (int j = 0; j < 4; ++j) b[j] = Bs[k][cg * 4 + j];
+  #pragma unroll
+          for (int i = 0; i < 8; ++i)
+  #pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
+    }
+
+    T* C = static_cast<T*>(g.C);
+    const long long rows = (long long)g.grid[0] * g.grid[1] * g.grid[2];
+    T* Pz = g.dsplit > 1 ? static_cast<T*>(g.partial) + (long long)dgrp * rows * g.n_cols : nullptr;
+  #pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = rg * 8 + i;
+      const int x = ox + (r & 3), y = oy + ((r >> 2) & 3), z = oz + (r >> 4);
+      if (x >= g.grid[0] || y >= g.grid[1] || z >= g.grid[2]) continue;
+      const long long row = ((long long)z * g.grid[1] + y) * g.grid[0] + x;
+  #pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = tile * kNTile + cg * 4 + j;
+        if (n >= g.n_cols) continue;
+        if (Pz) {
+          Pz[row * g.n_cols + n] = acc[i][j];
+        } else {
+          T* dst = C + row * g.n_cols + n;
+          *dst = g.accumulate ? (*dst + acc[i][j]) : acc[i][j];
+        }
+      }
+    }
+  }  // work items
+}
+
+// Column-per-lane variant (shape 3), for the FP64 levels: every lane owns one
+// output column and R consecutive rows of its warp, so a block is 4 warps x
+// 32 columns x R rows with no shared memory.  The 64-bit FMA pipe of an SM is
+// narrow (a warp instruction occupies it for many cycles), so what counts is
+// that every row computed is a real row, that the work comes in many small
+// blocks spread over all SMs and their four sub-partitions, and that no block
+// carries a long reduction alone; loads (one coalesced weight row per k, one
+// broadcast activation per row) are cheap beside the FMAs.
+constexpr int kColRows = 4;  // rows per warp
+
+template <typename T>
+__global__ void __launch_bounds__(128) nbr_gemm_col_kernel(NbrGemm g) {
+  constexpr int R = kColRows;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long rows = (long long)g.grid[0] * g.grid[1] * g.grid[2];
+  const int tile = blockIdx.y;
   const int d0 = g.dsplit > 1 ? (int)blockIdx.z : 0;  // dsplit is 1 or 27 here
   const int d1 = g.dsplit > 1 ? d0 + 1 : 27;
+  const int K = g.tile_k[tile];
+  const T* W0 = static_cast<const T*>(g.W) + g.tile_w[tile] + lane;
+  const T* A = static_cast<const T*>(g.A);
+  long long row[R];
+  int rx[R], ry[R], rz[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    row[i] = ((long long)blockIdx.x * 4 + warp) * R + i;
+    const long long rr = row[i] < rows ? row[i] : 0;
+    rx[i] = (int)(rr % g.grid[0]);
+    ry[i] = (int)((rr / g.grid[0]) % g.grid[1]);
+    rz[i] = (int)(rr / ((long long)g.grid[0] * g.grid[1]));
+  }
+  T acc[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) acc[i] = T(0);
   for (int d = d0; d < d1; ++d) {
     const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-    const T* Wd = W0 + (long long)d * K * kNTile;
-    for (int kc = 0; kc < K; kc += KC) {
-      const int kn = min(KC, K - kc);
-      for (int e = tx; e < kRows * KC; e += 64) {
-        const int r = e / KC, k = e % KC;
-        T v = T(0);
-        if (k < kn) {
-          const int x = ox + (r & 3) + dx, y = oy + ((r >> 2) & 3) + dy, z = oz + (r >> 4) + dz;
-          if (x >= 0 && y >= 0 && z >= 0 && x < g.grid[0] && y < g.grid[1] && z < g.grid[2])
-            v = A[(((long long)z * g.grid[1] + y) * g.grid[0] + x) * g.row_len + kc + k];
-        }
-        As[k][r] = v;
-      }
-      for (int e = tx; e < KC * kNTile; e += 64) {
-        const int k = e / kNTile, n = e % kNTile;
-        Bs[k][n] = (k < kn) ? Wd[(long long)(kc + k) * kNTile + n] : T(0);
-      }
-      __syncthreads();
-      for (int k = 0; k < kn; ++k) {
-        T a[8], b[4];
+    const T* ap[R];
+    bool av[R];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) a[i] = As[k][rg * 8 + i];
+    for (int i = 0; i < R; ++i) {
+      const int x = rx[i] + dx, y = ry[i] + dy, z = rz[i] + dz;
+      av[i] = row[i] < rows && x >= 0 && y >= 0 && z >= 0 && x < g.grid[0] && y < g.grid[1] && z < g.grid[2];
+      ap[i] = A + (av[i] ? (((long long)z * g.grid[1] + y) * g.grid[0] + x) * g.row_len : 0);
+    }
+    const T* w = W0 + (long long)d * K * kNTile;
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+      const T wk = __ldg(w + (long long)k * kNTile);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Bs[k][cg * 4 + j];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-      }
-      __syncthreads();
+      for (int i = 0; i < R; ++i) acc[i] = fma(av[i] ? __ldg(ap[i] + k) : T(0), wk, acc[i]);
     }
   }
-
+  const int col = tile * kNTile + lane;
+  if (col >= g.n_cols) return;
+  T* Pz = g.dsplit > 1 ? static_cast<T*>(g.partial) + (long long)d0 * rows * g.n_cols : nullptr;
   T* C = static_cast<T*>(g.C);
-  const long long rows = (long long)g.grid[0] * g.grid[1] * g.grid[2];
-  T* Pz = g.dsplit > 1 ? static_cast<T*>(g.partial) + (long long)blockIdx.z * rows * g.n_cols : nullptr;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int r = rg * 8 + i;
-    const int x = ox + (r & 3), y = oy + ((r >> 2) & 3), z = oz + (r >> 4);
-    if (x >= g.grid[0] || y >= g.grid[1] || z >= g.grid[2]) continue;
-    const long long row = ((long long)z * g.grid[1] + y) * g.grid[0] + x;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int n = tile * kNTile + cg * 4 + j;
-      if (n >= g.n_cols) continue;
-      if (Pz) {
-        Pz[row * g.n_cols + n] = acc[i][j];
-      } else {
-        T* dst = C + row * g.n_cols + n;
-        *dst = g.accumulate ? (*dst + acc[i][j]) : acc[i][j];
-      }
+  for (int i = 0; i < R; ++i) {
+    if (row[i] >= rows) continue;
+    if (Pz) {
+      Pz[row[i] * g.n_cols + col] = acc[i];
+    } else {
+      T* dst = C + row[i] * g.n_cols + col;
+      *dst = g.accumulate ? (*dst + acc[i]) : acc[i];
     }
   }
 }
@@ -135,7 +211,21 @@ cudaError_t launch_reduce_partials(const T* part, int nparts, long long count, T
 }
 
 template <typename T>
+cudaError_t launch_nbr_gemm_col(const NbrGemm& g, cudaStream_t s) {
+  const long long rows = (long long)g.grid[0] * g.grid[1] * g.grid[2];
+  const long long blocks = (rows + 4 * kColRows - 1) / (4 * kColRows);
+  if (blocks <= 0 || g.ntiles <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL || g.ntiles > 65535) return cudaErrorInvalidConfiguration;
+  nbr_gemm_col_kernel<T><<<dim3((unsigned)blocks, (unsigned)g.ntiles, g.dsplit > 1 ? 27u : 1u), 128, 0, s>>>(g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || g.dsplit <= 1) return e;
+  return launch_reduce_partials<T>(static_cast<const T*>(g.partial), g.dsplit, rows * g.n_cols,
+                                   static_cast<T*>(g.C), g.accumulate, s);
+}
+
+template <typename T>
 cudaError_t launch_nbr_gemm(const NbrGemm& g, cudaStream_t s) {
+  if (g.shape == 3) return launch_nbr_gemm_col<T>(g, s);
   return g.shape == 0 ? launch_nbr_gemm_simt<T>(g, s) : launch_nbr_gemm_zrun<T>(g, g.shape - 1, s);
 }
 
@@ -143,9 +233,10 @@ template <typename T>
 cudaError_t launch_nbr_gemm_simt(const NbrGemm& g, cudaStream_t s) {
   const long long tiles = (long long)((g.grid[0] + 3) / 4) * ((g.grid[1] + 3) / 4) * ((g.grid[2] + 3) / 4);
   if (tiles <= 0 || g.ntiles <= 0) return cudaSuccess;
-  if (tiles > 0x7fffffffLL || g.ntiles > 65535) return cudaErrorInvalidConfiguration;
-  dim3 grid((unsigned)tiles, (unsigned)g.ntiles, g.dsplit > 1 ? 27u : 1u);
-  nbr_gemm_simt_kernel<T><<<grid, 64, 0, s>>>(g);
+  long long items = tiles * g.ntiles * (g.dsplit > 1 ? 27 : 1);
+  if (g.max_blocks > 0 && items > g.max_blocks) items = g.max_blocks;
+  if (items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  nbr_gemm_simt_kernel<T><<<(unsigned)items, 64, 0, s>>>(g);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || g.dsplit <= 1) return e;
   return launch_reduce_partials<T>(static_cast<const T*>(g.partial), g.dsplit,

@@ -1,7 +1,7 @@
 """CUDA-core contraction variants and their autotuner.
 
-Every variant (tile shape 0 = 4x4x4 rows, 1 and 2 = z-run register tiles;
-neighbour split 1 / 3 / 9 / 27) is forced on every M2L level off the tensor
+Every variant (tile shape 0 = 4x4x4 rows, 1 and 2 = z-run register tiles,
+3 = one column per lane; neighbour split 1 / 3 / 9 / 27) is forced on every M2L level off the tensor
 cores and on the near field, and the solve is held to the oracle at the
 precision's parity tolerance (FP64 1e-10, FP32 1e-5 relative L2 on phi).
 The autotuner's picks must be valid variants and give the same answer.
@@ -16,7 +16,7 @@ torch = pytest.importorskip("torch")
 import paper_2606_13793_gb300 as fmm  # noqa: E402
 from paper_2606_13793_gb300 import _build, inputs  # noqa: E402
 
-VARIANTS = [(0, 1), (0, 27), (1, 1), (1, 3), (1, 9), (2, 1), (2, 3), (2, 9)]
+VARIANTS = [(0, 1), (0, 27), (1, 1), (1, 3), (1, 9), (2, 1), (2, 3), (2, 9), (3, 1), (3, 27)]
 TOL = {"fp64": 1e-10, "fp32": 1e-5}
 
 
@@ -74,7 +74,11 @@ def test_variant_rejected_where_it_does_not_apply():
     with pytest.raises(fmm.FMMError):
         plan.set_tuning(3, 1, 27)  # z-run tiles split 1, 3 or 9 ways
     with pytest.raises(fmm.FMMError):
-        plan.set_tuning(3, 3, 1)
+        plan.set_tuning(3, 1, 1)  # FP64 levels of a tensor-core plan keep small-footprint tiles
+    with pytest.raises(fmm.FMMError):
+        plan.set_tuning(3, 4, 1)
+    plan.set_tuning(3, 3, 27)
+    assert plan.tuning(3) == (3, 27)
     plan.close()
 
 
