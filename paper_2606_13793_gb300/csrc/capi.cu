@@ -406,6 +406,7 @@ float tf32_rn(double w) {
 struct TcHost {
   TcPass pass[kTcMaxPasses];
   int npass = 0;
+  int a_stages = 2;
   std::vector<unsigned char> W;
 };
 
@@ -424,16 +425,39 @@ uint32_t host_idesc(int kind, int n) {
 // Packs passes, MMA spans and weight tiles for groups `gs`; `entry(d, k, n)`
 // gives one weight of the contraction.  Tiles are written in the exact
 // shared-memory image the MMA reads: rows of 128 B, 16-byte chunks swizzled by
-// (row mod 8), bf16 hi plane then lo plane (or one TF32 plane).  The groups
-// of a pass are shared out between two MMA issuers (balanced MMA steps), each
-// with its own weight ring.
+// (row mod 8), bf16 hi plane then lo plane (or one TF32 plane).
+//
+// Issue balance: a tcgen05.mma costs tens of cycles to issue whatever its N,
+// and narrow low-order groups with long reductions need the most of them.
+// The accumulators of a pass are therefore shared out between kTcIssuers
+// issuing threads (heaviest first, to the least-loaded issuer), and a group
+// whose MMA steps exceed an even share is split along the reduction at a chunk
+// boundary into two accumulators, which the epilogue adds in a fixed order.
 template <typename Entry>
-bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entry, TcHost& H) {
+bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entry, TcHost& H, int a_stages) {
+  const int ring_budget = tc_ring_budget(kind, a_stages);
+  H.a_stages = a_stages;
   const int chunk = kind == TC_BF16X3 ? 64 : 32;  // reduction values per 128-byte chunk
   const int kstep = chunk / 4;
   const int esz = kind == TC_BF16X3 ? 2 : 4;
   const int planes = kind == TC_BF16X3 ? 2 : 1;
-  auto ksteps_of = [&](int K, int j) { return std::min(4, (K - j * chunk + kstep - 1) / kstep); };
+  // MMA K steps of reduction range [k0, k1) (k0 chunk-aligned) in chunk j
+  auto ksteps_in = [&](int k0, int k1, int j) {
+    if (k1 <= j * chunk || k0 >= (j + 1) * chunk) return 0;
+    return std::min(4, (k1 - j * chunk + kstep - 1) / kstep);
+  };
+  struct VGroup {
+    int out;     // output group
+    int k0, k1;  // reduction range
+    int nm;      // TMEM columns
+    int q = 0;   // issuer
+    int tmem = 0;
+  };
+  auto vsteps = [&](const VGroup& v) {
+    int n = 0;
+    for (int j = v.k0 / chunk; j * chunk < v.k1; ++j) n += ksteps_in(v.k0, v.k1, j);
+    return n;
+  };
   H.W.clear();
   H.npass = 0;
   size_t gi = 0;
@@ -441,80 +465,118 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
     if (H.npass == kTcMaxPasses) return false;
     TcPass& P = H.pass[H.npass++];
     std::memset(&P, 0, sizeof(P));
-    // groups of this pass, in the given (non-increasing K) order, up to 512 TMEM columns
-    std::vector<int> take;
+    // output groups of this pass, in the given (non-increasing K) order, up to 512 TMEM columns
     int cols = 0;
-    while (gi < gs.size() && (int)take.size() < kTcMaxGroups) {
+    std::vector<VGroup> V;
+    while (gi < gs.size() && P.ng < kTcMaxGroups) {
       const int nm = (gs[gi].ncols + 15) / 16 * 16;
       if (cols + nm > 512) break;
-      if (!take.empty() && gs[gi].K > gs[take.back()].K) return false;  // prefixes must shrink
-      take.push_back((int)gi);
+      if (P.ng > 0 && gs[gi].K > gs[gi - 1].K) return false;  // prefixes must shrink
+      P.out_col0[P.ng] = gs[gi].col0;
+      P.out_ncols[P.ng] = gs[gi].ncols;
+      P.out_nmma[P.ng] = nm;
+      P.out_tmem2[P.ng] = -1;
+      V.push_back({P.ng, 0, gs[gi].K, nm});
       cols += nm;
+      ++P.ng;
       ++gi;
     }
-    if (take.empty()) return false;
-    // issuer of each group: the heaviest groups (MMA steps) first, each to the
-    // issuer with fewer steps so far
-    std::vector<int> order = take;
-    auto steps = [&](int g) {
-      int n = 0;
-      for (int j = 0; j * chunk < gs[g].K; ++j) n += ksteps_of(gs[g].K, j);
-      return n;
-    };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return steps(a) > steps(b); });
-    std::vector<int> who(gs.size(), 0);
-    int load[2] = {0, 0};
-    for (int g : order) {
-      const int q = load[0] <= load[1] ? 0 : 1;
-      who[g] = q;
-      load[q] += steps(g);
-    }
-    // TMEM layout: issuer 0's groups, then issuer 1's, each in K order, so a
-    // span covers adjacent groups of one issuer
-    std::vector<int> K;
-    int nq0 = 0, kmax = 0, c = 0;
-    for (int q = 0; q < 2; ++q)
-      for (int g : take) {
-        if (who[g] != q) continue;
-        const int nm = (gs[g].ncols + 15) / 16 * 16;
-        P.out_tmem[P.ng] = c;
-        P.out_col0[P.ng] = gs[g].col0;
-        P.out_ncols[P.ng] = gs[g].ncols;
-        P.out_nmma[P.ng] = nm;
-        K.push_back(gs[g].K);
-        kmax = std::max(kmax, gs[g].K);
-        c += nm;
-        ++P.ng;
-        if (q == 0) ++nq0;
+    if (P.ng == 0) return false;
+    // split the heaviest accumulators along the reduction while one exceeds an even share
+    int total = 0;
+    for (const VGroup& v : V) total += vsteps(v);
+    const int share = (total + kTcIssuers - 1) / kTcIssuers;
+    for (bool again = true; again;) {
+      again = false;
+      int h = -1;
+      for (int i = 0; i < (int)V.size(); ++i)
+        if (P.out_tmem2[V[i].out] == -1 && V[i].k0 == 0 && (h < 0 || vsteps(V[i]) > vsteps(V[h]))) h = i;
+      if (h < 0 || vsteps(V[h]) <= share || cols + V[h].nm > 512) break;
+      // chunk boundary that halves the steps best
+      int best = -1, bestd = 1 << 30;
+      const int hs = vsteps(V[h]);
+      for (int kb = chunk; kb < V[h].k1; kb += chunk) {
+        VGroup a = V[h];
+        a.k1 = kb;
+        const int d = std::abs(2 * vsteps(a) - hs);
+        if (d < bestd) bestd = d, best = kb;
       }
-    int alloc = 32;
-    while (alloc < cols) alloc *= 2;
-    P.tmem_cols = alloc;
-    P.nchunks = (kmax + chunk - 1) / chunk;
-    if (P.nchunks > kTcMaxChunks) return false;
+      if (best < 0) break;
+      VGroup b = V[h];
+      b.k0 = best;
+      V[h].k1 = best;
+      P.out_tmem2[V[h].out] = 0;  // marked; placed below
+      V.push_back(b);
+      cols += b.nm;
+      again = true;
+    }
+    // issuers: heaviest first, each to the least-loaded issuer
+    {
+      std::vector<int> order(V.size());
+      for (size_t i = 0; i < V.size(); ++i) order[i] = (int)i;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return vsteps(V[a]) > vsteps(V[b]); });
+      int load[kTcIssuers] = {};
+      for (int i : order) {
+        int q = 0;
+        for (int t = 1; t < kTcIssuers; ++t)
+          if (load[t] < load[q]) q = t;
+        V[i].q = q;
+        load[q] += vsteps(V[i]);
+      }
+    }
+    // TMEM layout: issuer by issuer; within an issuer, by reduction start, then K (adjacent
+    // accumulators with the same start and K steps merge into one span)
+    std::stable_sort(V.begin(), V.end(), [&](const VGroup& a, const VGroup& b) {
+      if (a.q != b.q) return a.q < b.q;
+      if (a.k0 != b.k0) return a.k0 < b.k0;
+      return a.k1 > b.k1;
+    });
+    {
+      int c = 0, kmax = 0;
+      for (VGroup& v : V) {
+        v.tmem = c;
+        c += v.nm;
+        kmax = std::max(kmax, v.k1);
+        if (v.k0 == 0)
+          P.out_tmem[v.out] = v.tmem;
+        else
+          P.out_tmem2[v.out] = v.tmem;
+      }
+      int alloc = 32;
+      while (alloc < c) alloc *= 2;
+      if (alloc > 512) return false;
+      P.tmem_cols = alloc;
+      P.nchunks = (kmax + chunk - 1) / chunk;
+      if (P.nchunks > kTcMaxChunks) return false;
+    }
     // spans per chunk and issuer, their tile offsets inside one neighbour block
     int ns = 0, off = 0;
-    long long vol[2] = {0, 0};
-    int biggest[2] = {0, 0};
-    std::vector<std::vector<int>> span_groups;  // groups of each span (global span index)
+    long long vol[kTcIssuers] = {};
+    int biggest[kTcIssuers] = {};
+    std::vector<std::vector<int>> span_v;  // accumulators of each span
     for (int j = 0; j < P.nchunks; ++j) {
-      P.span0[j] = ns;
-      for (int q = 0; q < 2; ++q) {
-        if (q == 1) P.span_mid[j] = ns;
-        int g = q == 0 ? 0 : nq0;
-        const int gend = q == 0 ? nq0 : P.ng;
-        while (g < gend && K[g] > j * chunk) {
-          const int ks = ksteps_of(K[g], j);
+      for (int q = 0; q < kTcIssuers; ++q) {
+        P.span_idx[j][q] = ns;
+        size_t i = 0;
+        while (i < V.size()) {
+          if (V[i].q != q || ksteps_in(V[i].k0, V[i].k1, j) == 0) {
+            ++i;
+            continue;
+          }
+          const int ks = ksteps_in(V[i].k0, V[i].k1, j);
           if (ns == kTcMaxSpans) return false;
           TcSpan& S = P.span[ns];
-          S.tmem_col = P.out_tmem[g];
+          S.tmem_col = V[i].tmem;
           S.n = 0;
           S.ksteps = ks;
+          S.first = V[i].k0 / chunk;
           std::vector<int> members;
-          while (g < gend && K[g] > j * chunk && S.n + P.out_nmma[g] <= kTcMaxSpanN && ksteps_of(K[g], j) == ks) {
-            S.n += P.out_nmma[g];
-            members.push_back(g);
-            ++g;
+          const int k0 = V[i].k0;
+          while (i < V.size() && V[i].q == q && V[i].k0 == k0 && ksteps_in(V[i].k0, V[i].k1, j) == ks &&
+                 V[i].tmem == S.tmem_col + S.n && S.n + V[i].nm <= kTcMaxSpanN) {
+            S.n += V[i].nm;
+            members.push_back((int)i);
+            ++i;
           }
           if (members.empty()) return false;
           S.w_off = off;
@@ -523,40 +585,48 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
           off += bytes;
           vol[q] += bytes;
           biggest[q] = std::max(biggest[q], bytes);
-          span_groups.push_back(members);
+          span_v.push_back(members);
           ++ns;
         }
       }
+      P.span_idx[j][kTcIssuers] = ns;
     }
-    P.span0[P.nchunks] = ns;
-    P.span_mid[P.nchunks] = ns;
-    // weight rings in proportion to the bytes each issuer streams, each able
-    // to hold its largest span
-    int r0 = 0;
-    if (vol[0] > 0 && vol[1] > 0)
-      r0 = (int)((double)kTcBRingBytes * (double)vol[0] / (double)(vol[0] + vol[1])) / 1024 * 1024;
-    else if (vol[0] > 0)
-      r0 = kTcBRingBytes;
-    r0 = std::max(r0, biggest[0]);
-    r0 = std::min(r0, kTcBRingBytes - biggest[1]);
-    if (r0 < biggest[0] || kTcBRingBytes - r0 < biggest[1]) return false;
-    P.ring_bytes[0] = r0;
-    P.ring_bytes[1] = kTcBRingBytes - r0;
+    for (int q = 0; q <= kTcIssuers; ++q) P.span_idx[P.nchunks][q] = ns;
+    // weight rings in proportion to the bytes each issuer streams, each able to hold its largest span
+    {
+      long long vt = 0;
+      int need = 0;
+      for (int q = 0; q < kTcIssuers; ++q) vt += vol[q], need += (biggest[q] + 1023) / 1024 * 1024;
+      if (need > ring_budget) return false;
+      int spare = ring_budget - need, given = 0;
+      for (int q = 0; q < kTcIssuers; ++q) {
+        const int base = (biggest[q] + 1023) / 1024 * 1024;
+        const int extra = vt > 0 ? (int)((double)spare * (double)vol[q] / (double)vt) / 1024 * 1024 : 0;
+        P.ring_bytes[q] = vol[q] > 0 ? base + extra : 0;
+        given += P.ring_bytes[q];
+      }
+      for (int q = 0; q < kTcIssuers && given < ring_budget; ++q)  // leftover to the busiest ring
+        if (vol[q] > 0 && vol[q] == *std::max_element(vol, vol + kTcIssuers)) {
+          P.ring_bytes[q] += (ring_budget - given) / 1024 * 1024;
+          break;
+        }
+    }
     P.bytes_per_d = off;
     P.w_base = (long long)H.W.size();
     H.W.resize(H.W.size() + (size_t)27 * P.bytes_per_d, 0);
     for (int d = 0; d < 27; ++d)
       for (int j = 0; j < P.nchunks; ++j)
-        for (int si = P.span0[j]; si < P.span0[j + 1]; ++si) {
+        for (int si = P.span_idx[j][0]; si < P.span_idx[j][kTcIssuers]; ++si) {
           const TcSpan& S = P.span[si];
           unsigned char* tile = H.W.data() + P.w_base + (size_t)d * P.bytes_per_d + S.w_off;
           int row0 = 0;
-          for (int g : span_groups[si]) {
-            for (int r = 0; r < P.out_ncols[g]; ++r) {
-              const int n = P.out_col0[g] + r, row = row0 + r;
+          for (int vi : span_v[si]) {
+            const VGroup& v = V[vi];
+            for (int r = 0; r < P.out_ncols[v.out]; ++r) {
+              const int n = P.out_col0[v.out] + r, row = row0 + r;
               for (int e = 0; e < S.ksteps * kstep; ++e) {
                 const int k = j * chunk + e;
-                if (k >= K[g]) continue;
+                if (k < v.k0 || k >= v.k1) continue;
                 const double w = entry(d, k, n);
                 if (w == 0.0) continue;
                 const int byte = e * esz;
@@ -572,7 +642,7 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
                 }
               }
             }
-            row0 += P.out_nmma[g];
+            row0 += v.nm;
           }
         }
   }
@@ -594,7 +664,11 @@ bool build_tc(const MultiIndex& mi, const TaylorTable& tt, int kind, TcHost& H) 
     for (int c = col0; c < col1; c += per) gs.push_back({c, std::min(per, col1 - c), K});
     m = o_hi + 1;
   }
-  return build_tc_generic(kind, gs, [&](int d, int k, int n) { return m2l_entry(mi, tt, d, k, n); }, H);
+  // Two activation stages (the boxes have a producer thread of their own);
+  // the weight rings take the rest of shared memory: the kernel is bound by
+  // the number of weight tiles in flight against the L2 round trip.
+  auto entry = [&](int d, int k, int n) { return m2l_entry(mi, tt, d, k, n); };
+  return build_tc_generic(kind, gs, entry, H, 2);
 }
 
 // Near field (eq. direct) as the same contraction over leaf boxes: column n =
@@ -603,6 +677,8 @@ bool build_tc(const MultiIndex& mi, const TaylorTable& tt, int kind, TcHost& H) 
 bool build_tc_near(int b, int kind, TcHost& H) {
   const int b3 = b * b * b;
   std::vector<TcCols> gs;
+  // groups of up to 128 columns: an MMA narrower than 64 columns holds the
+  // tensor pipe as long as a 64-column one, so b = 4 stays one group
   for (int c = 0; c < b3; c += kTcMaxGroupN) gs.push_back({c, std::min(kTcMaxGroupN, b3 - c), b3});
   auto entry = [b](int d, int k, int n) {
     const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
@@ -615,7 +691,7 @@ bool build_tc_near(int b, int kind, TcHost& H) {
     }
     return r2 == 0.0 ? -1.0 : -1.0 / std::sqrt(r2);
   };
-  return build_tc_generic(kind, gs, entry, H);
+  return build_tc_generic(kind, gs, entry, H, 2);
 }
 
 // Near-field matrices (eq. direct, cell units): W_d[s][t] = g(x_t - x_s) for
@@ -855,6 +931,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
       if ((st = P->upload(H.W, &dw, s))) return cleanup(st);
       P->tc.W = dw;
       P->tc.npass = H.npass;
+      P->tc.a_stages = H.a_stages;
       for (int i = 0; i < H.npass; ++i) P->tc.pass[i] = H.pass[i];
       P->tc.n_cols = 8 * P->nc;
       P->tc.kind = P->tc_kind;
@@ -904,6 +981,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     TcLaunch& T = P->tcn;
     T.W = dw;
     T.npass = H.npass;
+    T.a_stages = H.a_stages;
     for (int i = 0; i < H.npass; ++i) T.pass[i] = H.pass[i];
     T.n_cols = P->b * P->b * P->b;
     T.kind = TC_BF16X3;

@@ -152,14 +152,20 @@ constexpr int kTcMaxGroupN = 128;                         // B tile <= 128 rows
 
 enum TcKind { TC_BF16X3 = 0, TC_TF32 = 1 };
 
-constexpr int kTcMaxGroups = 8;     // column groups per pass
+constexpr int kTcIssuers = 4;       // MMA-issuing threads per CTA, each with its own weight ring
+constexpr int kTcMaxGroups = 12;    // output column groups per pass
 constexpr int kTcMaxChunks = 48;    // 128-byte reduction chunks per neighbour
 constexpr int kTcMaxSpans = 128;    // MMA spans per pass (all chunks)
-constexpr int kTcMaxSpanN = 192;    // columns of one span (one MMA instruction)
-// Shared memory of the two weight rings together.  With it the tensor-core
-// kernel leaves room on its SM for an FP64 CUDA-core contraction block
-// (12.4 KB), so coarse FP64 levels run beside the tensor-core levels.
-constexpr int kTcBRingBytes = 138 * 1024;
+constexpr int kTcMaxSpanN = 128;    // columns of one span (one MMA instruction)
+// Shared memory of the tensor-core kernel: barriers (2 KB), then the
+// activation stages (one 144-row box per plane, 18 KB a plane), then the
+// weight rings, which take what the stages leave.
+constexpr int kTcSmemUsable = 226 * 1024;
+constexpr int kTcMaxAStages = 8;
+constexpr int kTcAPlaneBytes = kTcTileX * kTcBoxY * 128;
+inline int tc_ring_budget(int kind, int a_stages) {
+  return kTcSmemUsable - 2048 - a_stages * kTcAPlaneBytes * (kind == 0 ? 2 : 1);
+}
 
 // One MMA instruction shape of a chunk: adjacent column groups that use the
 // chunk with the same number of K steps, merged so that each tcgen05.mma
@@ -171,6 +177,7 @@ struct TcSpan {
   int ksteps;      // MMA K steps in this chunk (1..4)
   int w_off;       // byte offset of the tile inside the neighbour block
   uint32_t idesc;  // instruction descriptor (kind, N, M = 128)
+  int first;       // chunk in which the span's accumulators open (first MMA overwrites)
 };
 
 // One pass of the schedule, passed by value (kernel parameter space), so the
@@ -180,20 +187,22 @@ struct TcSpan {
 struct TcPass {
   int ng, nchunks, tmem_cols, bytes_per_d;
   long long w_base;
-  int out_tmem[kTcMaxGroups];   // epilogue: TMEM column of the group
+  int out_tmem[kTcMaxGroups];   // epilogue: TMEM column of the group's accumulator
+  int out_tmem2[kTcMaxGroups];  // second accumulator of a reduction-split group, or -1
   int out_col0[kTcMaxGroups];   // first output column (beta*8 + child)
   int out_ncols[kTcMaxGroups];  // real output columns
   int out_nmma[kTcMaxGroups];   // TMEM columns of the group (multiple of 16)
-  // Two MMA issuers own disjoint column groups.  Spans of chunk j: issuer 0
-  // span[span0[j] .. span_mid[j]), issuer 1 span[span_mid[j] .. span0[j+1]).
-  int span0[kTcMaxChunks + 1];
-  int span_mid[kTcMaxChunks + 1];
-  int ring_bytes[2];            // weight ring of each issuer (multiples of 1024, sum <= kTcBRingBytes)
+  // Accumulators are shared out between kTcIssuers MMA issuers (disjoint TMEM
+  // columns).  Spans of issuer q in chunk j: span[span_idx[j][q] ..
+  // span_idx[j][q + 1]); span_idx[j][kTcIssuers] == span_idx[j + 1][0].
+  int span_idx[kTcMaxChunks + 1][kTcIssuers + 1];
+  int ring_bytes[kTcIssuers];   // weight ring of each issuer (multiples of 1024, sum <= the ring budget)
   TcSpan span[kTcMaxSpans];
 };
 struct TcLaunch {
   TcPass pass[kTcMaxPasses];
   int npass;
+  int a_stages;    // activation stages in flight (2 .. kTcMaxAStages)
   const unsigned char* W;
   float* C;        // [parents][n_cols]
   int n_cols;

@@ -17,14 +17,16 @@
 //   * D: FP32 accumulators in tensor memory, one column range per group.
 // Precisions: kind::tf32 on the FP32 rows (one product), or bf16 hi/lo planes
 // with three products hi*hi + hi*lo + lo*hi (kind::f16, BF16 inputs).
-// Roles: the column groups of a pass are shared out between two MMA issuers
-// (warp 1 and warp 2, lane 0), which accumulate into disjoint tensor-memory
-// columns; each issuer has its own weight ring, filled by its own producer
-// (warp 0 lane 0, which also loads the activations both issuers read, and
-// warp 3 lane 0).  A single issuing thread cannot keep the tensor pipe busy
-// with the narrow low-order spans; two can.  The rings are byte-granular
+// Roles (9 warps, lane 0 of each): warp 0 loads the activation boxes all
+// issuers read; the accumulators of a pass are shared out between four MMA
+// issuers (warps 5..8), which write disjoint tensor-memory columns; issuer q
+// has its own weight ring, filled by its own producer (warp 1 + q).  A single
+// issuing thread cannot keep the tensor pipe busy with the narrow low-order
+// spans; four can.  The activation loads have a thread of their own so that
+// a full weight ring never delays the next box.  The rings are byte-granular
 // (1 KB units), so small spans do not hold a slot sized for the largest.
-// All four warps drain tensor memory in the epilogue.  Every wait is bounded:
+// Warps 0..7 drain tensor memory in the epilogue (warps w and w + 4 share
+// TMEM lanes and split the columns).  Every wait is bounded:
 // on time-out the kernel sets the plan's error flag (FMM_ERR_TIMEOUT) and
 // unwinds; a CTA that sees the flag set by another gives up at once.
 #include <cuda.h>
@@ -34,13 +36,13 @@
 namespace fmmgb {
 namespace {
 
-constexpr int kSA = 2;                                   // activation ring stages (both planes)
-constexpr int kARows = kTcTileX * kTcBoxY;               // 144 rows of one activation box
-constexpr int kAPlane = kARows * 128;                    // 18 KB, a multiple of 1024
-constexpr int kAStage = 2 * kAPlane;                     // hi and lo planes
+constexpr int kAPlane = kTcAPlaneBytes;                  // 144 rows x 128 B, a multiple of 1024
 constexpr int kRingE = 16;                               // spans in flight per weight ring
-constexpr int kSmemBytes = kSA * kAStage + kTcBRingBytes + 1024 /*barriers*/ + 1024 /*alignment*/;
+constexpr int kThreads = 32 * (1 + 2 * kTcIssuers);      // activation producer, ring producers, issuers
+constexpr int kSmemBytes = kTcSmemUsable + 1024 /*alignment*/;
+static_assert((2 * kTcMaxAStages + 2 * kTcIssuers * kRingE + 1) * 8 + 4 <= 2048, "barrier region");
 static_assert(kSmemBytes <= 227 * 1024, "shared memory of the tensor-core kernel");
+static_assert(kAPlane % 1024 == 0, "activation planes keep the 1 KB swizzle alignment");
 constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -179,22 +181,25 @@ __device__ __forceinline__ void issue_span(uint32_t d, uint64_t a, uint64_t a_lo
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     m2l_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
                   const __grid_constant__ TcLaunch P) {
   constexpr bool split = KIND == TC_BF16X3;
   constexpr int chunk_elems = split ? 64 : 32;
   constexpr uint32_t planes = split ? 2 : 1;
+  constexpr int NQ = kTcIssuers;
+  constexpr uint32_t kAStage = planes * kAPlane;
+  const uint32_t nA = (uint32_t)P.a_stages;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  unsigned char* a_ring = base;
-  unsigned char* b_rings = base + kSA * kAStage;
-  uint64_t* a_full = reinterpret_cast<uint64_t*>(b_rings + kTcBRingBytes);
-  uint64_t* a_empty = a_full + kSA;
-  uint64_t* b_full = a_empty + kSA;     // [2][kRingE]
-  uint64_t* b_empty = b_full + 2 * kRingE;  // [2][kRingE]
-  uint64_t* accum = b_empty + 2 * kRingE;
+  uint64_t* a_full = reinterpret_cast<uint64_t*>(base);  // barriers: first 2 KB
+  unsigned char* a_ring = base + 2048;
+  unsigned char* b_rings = a_ring + nA * kAStage;
+  uint64_t* a_empty = a_full + kTcMaxAStages;
+  uint64_t* b_full = a_empty + kTcMaxAStages;  // [NQ][kRingE]
+  uint64_t* b_empty = b_full + NQ * kRingE;  // [NQ][kRingE]
+  uint64_t* accum = b_empty + NQ * kRingE;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
 
   const TcPass& pass = P.pass[blockIdx.y];
@@ -204,11 +209,17 @@ __global__ void __launch_bounds__(128, 1)
   const int oy = ((blockIdx.x / ntx) % nty) * kTcTileY;
   const int oz = (blockIdx.x / (ntx * nty)) * kTcTileZ;
 
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < kSA; ++i) mbar_init(&a_full[i], 1), mbar_init(&a_empty[i], 2);  // both issuers release
-    for (int i = 0; i < 2 * kRingE; ++i) mbar_init(&b_full[i], 1), mbar_init(&b_empty[i], 1);
-    mbar_init(accum, 2);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  {
+    // one barrier per thread: a_full, a_empty (every issuer releases a stage),
+    // the ring barriers, the accumulator barrier
+    constexpr int kBars = 2 * kTcMaxAStages + 2 * NQ * kRingE + 1;
+    static_assert(kBars <= kThreads, "barrier initialisation");
+    const int i = threadIdx.x;
+    if (i < kBars) {
+      const uint32_t count = (i >= kTcMaxAStages && i < 2 * kTcMaxAStages) || i == kBars - 1 ? NQ : 1;
+      mbar_init(a_full + i, count);  // the barriers are contiguous from a_full on
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
   }
   if (warp == 0) {
     __syncwarp();  // tcgen05.alloc is warp-collective: reconverge after thread 0's block
@@ -221,15 +232,36 @@ __global__ void __launch_bounds__(128, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if ((warp == 0 || warp == 3) && lane == 0) {
-    // ---------------- producers ----------------
-    // Ring q = warp / 3.  Order: neighbour column (dx, dz), chunk j, then dy
-    // and the issuer's spans of the chunk.  Producer 0 also loads the
-    // activation box (rows y-1 .. y+16 of the shifted x/z column), which
-    // serves the three dy neighbours of both issuers.
-    const int q = warp == 3 ? 1 : 0;
+  if (warp == 0 && lane == 0) {
+    // ---------------- activation producer ----------------
+    // One box per (neighbour column (dx, dz), chunk j): rows y-1 .. y+16 of
+    // the shifted x/z column, which serve the three dy neighbours.
+    uint32_t ai = 0;
+    bool ok = !(*reinterpret_cast<volatile int*>(P.err) & 2);
+    for (int xz = 0; ok && xz < 9; ++xz) {
+      const int dx = xz % 3 - 1, dz = xz / 3 - 1;
+      for (int j = 0; ok && j < pass.nchunks; ++j) {
+        const uint32_t sa = ai % nA;
+        if (!(ok = wait_fast(&a_empty[sa], ((ai / nA) & 1) ^ 1, P.err, W_PROD_A))) break;
+        unsigned char* adst = a_ring + sa * kAStage;
+        mbar_expect_tx(&a_full[sa], split ? 2 * kAPlane : kAPlane);
+        tma_load_4d(adst, &map_hi, &a_full[sa], j * chunk_elems, ox + dx, oy - 1, oz + dz);
+        if (split) tma_load_4d(adst + kAPlane, &map_lo, &a_full[sa], j * chunk_elems, ox + dx, oy - 1, oz + dz);
+        ++ai;
+      }
+    }
+    if (!ok)  // drain: never leave the CTA with copies in flight
+      for (uint32_t i = (ai > nA ? ai - nA : 0); i < ai; ++i)
+        mbar_wait(&a_full[i % nA], (i / nA) & 1, P.err, W_DRAIN);
+  } else if (warp >= 1 && warp <= NQ && lane == 0) {
+    // ---------------- weight producers ----------------
+    // Ring q = warp - 1, in the order its issuer consumes: neighbour column
+    // (dx, dz), chunk j, then dy and the issuer's spans of the chunk.
+    const int q = warp - 1;
     const uint32_t RB = (uint32_t)pass.ring_bytes[q];
-    unsigned char* ring = b_rings + (q ? pass.ring_bytes[0] : 0);
+    uint32_t rbase = 0;
+    for (int t = 0; t < q; ++t) rbase += (uint32_t)pass.ring_bytes[t];
+    unsigned char* ring = b_rings + rbase;
     uint64_t* full = b_full + q * kRingE;
     uint64_t* empty = b_empty + q * kRingE;
     // Byte ring in virtual positions: v = start of the next span, last =
@@ -238,22 +270,13 @@ __global__ void __launch_bounds__(128, 1)
     // it may be written once the live data [freed, last) no longer overlaps
     // its physical range, i.e. freed >= min(last, v + bytes - RB).
     uint32_t end_v[kRingE];
-    uint32_t ai = 0, e = 0, tail = 0, v = 0, off = 0, freed = 0, last = 0;
+    uint32_t e = 0, tail = 0, v = 0, off = 0, freed = 0, last = 0;
     bool ok = !(*reinterpret_cast<volatile int*>(P.err) & 2);
     const unsigned char* wpass = P.W + pass.w_base;
     for (int xz = 0; ok && xz < 9; ++xz) {
       const int dx = xz % 3 - 1, dz = xz / 3 - 1;
       for (int j = 0; ok && j < pass.nchunks; ++j) {
-        if (q == 0) {
-          const int sa = ai % kSA;
-          if (!(ok = wait_fast(&a_empty[sa], ((ai / kSA) & 1) ^ 1, P.err, W_PROD_A))) break;
-          unsigned char* adst = a_ring + sa * kAStage;
-          mbar_expect_tx(&a_full[sa], split ? 2 * kAPlane : kAPlane);
-          tma_load_4d(adst, &map_hi, &a_full[sa], j * chunk_elems, ox + dx, oy - 1, oz + dz);
-          if (split) tma_load_4d(adst + kAPlane, &map_lo, &a_full[sa], j * chunk_elems, ox + dx, oy - 1, oz + dz);
-          ++ai;
-        }
-        const int s0 = q ? pass.span_mid[j] : pass.span0[j], s1 = q ? pass.span0[j + 1] : pass.span_mid[j];
+        const int s0 = pass.span_idx[j][q], s1 = pass.span_idx[j][q + 1];
         for (int dy = 0; ok && dy < 3; ++dy) {
           const unsigned char* wd = wpass + (long long)((dx + 1) + 3 * dy + 9 * (dz + 1)) * pass.bytes_per_d;
           for (int si = s0; si < s1; ++si) {
@@ -277,33 +300,29 @@ __global__ void __launch_bounds__(128, 1)
         }
       }
     }
-    if (!ok) {
-      // drain: never leave the CTA with copies in flight
-      if (q == 0)
-        for (uint32_t i = (ai > kSA ? ai - kSA : 0); i < ai; ++i)
-          mbar_wait(&a_full[i % kSA], (i / kSA) & 1, P.err, W_DRAIN);
+    if (!ok)  // drain: never leave the CTA with copies in flight
       for (uint32_t i = tail; i < e; ++i) mbar_wait(&full[i % kRingE], (i / kRingE) & 1, P.err, W_DRAIN);
-    }
-  } else if ((warp == 1 || warp == 2) && lane == 0) {
+  } else if (warp > NQ && lane == 0) {
     // ---------------- MMA issuers ----------------
-    const int q = warp - 1;
+    const int q = warp - 1 - NQ;
     const uint32_t RB = (uint32_t)pass.ring_bytes[q];
-    const uint64_t ring_desc = sw128_desc(smem_u32(b_rings + (q ? pass.ring_bytes[0] : 0)));
+    uint32_t rbase = 0;
+    for (int t = 0; t < q; ++t) rbase += (uint32_t)pass.ring_bytes[t];
+    const uint64_t ring_desc = sw128_desc(smem_u32(b_rings + rbase));
     uint64_t* full = b_full + q * kRingE;
     uint64_t* empty = b_empty + q * kRingE;
     uint32_t ai = 0, e = 0, off = 0;
     bool ok = !(*reinterpret_cast<volatile int*>(P.err) & 2);
     for (int xz = 0; ok && xz < 9; ++xz) {
       for (int j = 0; ok && j < pass.nchunks; ++j) {
-        const int sa = ai % kSA;
-        if (!(ok = wait_fast(&a_full[sa], (ai / kSA) & 1, P.err, W_MMA_A))) break;
+        const int sa = ai % nA;
+        if (!(ok = wait_fast(&a_full[sa], (ai / nA) & 1, P.err, W_MMA_A))) break;
         tc_fence_after();
         const uint64_t a_desc = sw128_desc(smem_u32(a_ring + sa * kAStage));
-        const int s0 = q ? pass.span_mid[j] : pass.span0[j], s1 = q ? pass.span0[j + 1] : pass.span_mid[j];
+        const int s0 = pass.span_idx[j][q], s1 = pass.span_idx[j][q + 1];
         for (int dy = 0; ok && dy < 3; ++dy) {
           const uint64_t a = a_desc + (uint64_t)(dy * (kTcTileX * 128 / 16));  // 128-row window
           const uint64_t a_lo = a + (uint64_t)(kAPlane / 16);
-          const uint32_t acc0 = (xz == 0 && j == 0 && dy == 0) ? 0u : 1u;  // the first step opens every group
           for (int si = s0; si < s1; ++si) {
             const TcSpan& S = pass.span[si];
             const uint32_t plane = (uint32_t)S.n * 128u;
@@ -313,6 +332,7 @@ __global__ void __launch_bounds__(128, 1)
             const uint64_t b = ring_desc + (uint64_t)(off >> 4);
             const uint64_t b_lo = b + (uint64_t)(plane >> 4);
             const uint32_t d = tmem + (uint32_t)S.tmem_col;
+            const uint32_t acc0 = (xz == 0 && dy == 0 && j == S.first) ? 0u : 1u;  // the first step opens
             switch (S.ksteps) {
               case 1: issue_span<KIND, 1>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
               case 2: issue_span<KIND, 2>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
@@ -333,22 +353,33 @@ __global__ void __launch_bounds__(128, 1)
   __syncwarp();
 
   // ---------------- epilogue: TMEM -> registers -> C ----------------
+  // Warp w reads TMEM lanes 32 (w mod 4) ..; warps w and w + 4 take
+  // alternate 16-column blocks.  A reduction-split group adds its second
+  // accumulator (fixed order: first + second).
   int done = 0;
-  if (lane == 0) done = mbar_wait(accum, 0, P.err, W_EPI) ? 1 : 0;
+  if (lane == 0 && warp < 8) done = mbar_wait(accum, 0, P.err, W_EPI) ? 1 : 0;
   done = __shfl_sync(0xffffffffu, done, 0);  // warp-uniform: tcgen05.ld is warp-collective
   if (done) {
     tc_fence_after();
-    const int r = warp * 32 + lane;  // tile row = TMEM lane
+    const int wq = warp & 3, half = warp >> 2;
+    const int r = wq * 32 + lane;  // tile row = TMEM lane
     const int x = ox + (r & 7), y = oy + (r >> 3), z = oz;
     const bool valid = x < P.grid[0] && y < P.grid[1] && z < P.grid[2];
     float* crow = P.C + ((((long long)z * P.grid[1] + y) * P.grid[0] + x) * P.n_cols);
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
     for (int g = 0; g < pass.ng; ++g) {
       const int n_mma = pass.out_nmma[g], ncols = pass.out_ncols[g], col0 = pass.out_col0[g];
-      for (int c = 0; c < n_mma; c += 16) {
+      const int t2 = pass.out_tmem2[g];
+      for (int c = half * 16; c < n_mma; c += 32) {
         float v[16];
         __syncwarp();  // tcgen05.ld is warp-collective: reconverge after the masked stores
         tmem_ld16(tmem + lane_base + (uint32_t)(pass.out_tmem[g] + c), v);
+        if (t2 >= 0) {
+          float w2[16];
+          tmem_ld16(tmem + lane_base + (uint32_t)(t2 + c), w2);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += w2[i];
+        }
         if (valid) {  // out_col0 and out_ncols are multiples of 8: whole float4s
 #pragma unroll
           for (int j = 0; j < 16; j += 4)
@@ -414,10 +445,10 @@ cudaError_t launch_m2l_tc(const TcLaunch& L, const void* map_hi, const void* map
             ntz = (L.grid[2] + kTcTileZ - 1) / kTcTileZ;
   dim3 grid((unsigned)(ntx * nty * ntz), (unsigned)L.npass);
   if (L.kind == TC_BF16X3)
-    m2l_tc_kernel<TC_BF16X3><<<grid, 128, kSmemBytes, s>>>(*reinterpret_cast<const CUtensorMap*>(map_hi),
+    m2l_tc_kernel<TC_BF16X3><<<grid, kThreads, kSmemBytes, s>>>(*reinterpret_cast<const CUtensorMap*>(map_hi),
                                                            *reinterpret_cast<const CUtensorMap*>(map_lo), L);
   else
-    m2l_tc_kernel<TC_TF32><<<grid, 128, kSmemBytes, s>>>(*reinterpret_cast<const CUtensorMap*>(map_hi),
+    m2l_tc_kernel<TC_TF32><<<grid, kThreads, kSmemBytes, s>>>(*reinterpret_cast<const CUtensorMap*>(map_hi),
                                                          *reinterpret_cast<const CUtensorMap*>(map_lo), L);
   return cudaGetLastError();
 }
