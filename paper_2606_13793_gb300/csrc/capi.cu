@@ -871,7 +871,13 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
       c->shape = 3;
       return;
     }
-    if (c->dsplit == 1 && zrun_eligible(g, tk.data(), (int)tk.size())) c->shape = 1;
+    if (c->dsplit != 1 || !zrun_eligible(g, tk.data(), (int)tk.size())) return;
+    c->shape = 1;
+    // fewer than four blocks per SM: split the neighbours three ways if the
+    // partial sums fit the scratch
+    const long long blocks = (long long)((g.grid[0] + 7) / 8) * ((g.grid[1] + 3) / 4) * ((g.grid[2] + 7) / 8) * g.ntiles;
+    const size_t part3 = (size_t)3 * g.grid[0] * g.grid[1] * g.grid[2] * (size_t)g.n_cols * (f64 ? 8 : 4);
+    if (blocks < 4 * 152 && part3 <= P->part_cap) c->dsplit = 3;
   };
   P->arena_bytes = off;
 
