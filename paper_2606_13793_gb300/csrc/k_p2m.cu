@@ -11,6 +11,151 @@ using namespace tree;
 // P2M (Sec. 2.1, eq. multipole) about each leaf-box centre, scaled:
 //   Mt_alpha = sum_cells m ((x - c)/b)^alpha
 // plus the box-blocked copy of the density for the near field.
+//
+// Two threads per box, in adjacent warps: the thread of parity h accumulates
+// the coefficients whose z power c has parity h (50 and 34 of the 84 at
+// p = 6), so a thread holds about half the expansion in registers and twice
+// as many warps fit on an SM to hide the density loads (the second warp's
+// reads of the same cells hit L1).  The parity is warp-uniform and selects a
+// body instantiated for it, so every register index stays compile-time.
+constexpr int kP2mParents = kThreads / 16;  // 2 threads per box, 8 boxes per parent
+
+template <int P>
+__host__ __device__ constexpr int ncoef_parity(int h) {
+  int n = 0;
+  for (int c = h; c <= P; c += 2) n += (P - c + 1) * (P - c + 2) / 2;
+  return n;
+}
+
+template <int P, typename T, int h>
+__device__ __forceinline__ void p2m_body(const Box& B, const T* __restrict__ rho, int nx, int ny, int b,
+                                         const Level& leaf, T* __restrict__ Ms, T* __restrict__ rho_box,
+                                         __nv_bfloat16* __restrict__ rhi, __nv_bfloat16* __restrict__ rlo,
+                                         int* __restrict__ flag) {
+  constexpr int NC = ncoef_c(P);
+  constexpr int NH = ncoef_parity<P>(h);
+  T acc[NH > 0 ? NH : 1];  // this thread's coefficients, in canonical order restricted to parity h of c
+#pragma unroll
+  for (int k = 0; k < NH; ++k) acc[k] = T(0);
+  bool bad = false;  // non-finite density (reported through the plan's flag)
+  // One z-plane of the box: rows j = 0 .. b-1 of cells m[j][i] -> partial sums
+  // t2[(a, bb)] = sum_j yj^bb sum_i m xi^a, then acc += t2 zk^c (this parity).
+  auto plane = [&](const T* mrow, int k, const T inv_b) {
+    T t2[(P + 1) * (P + 2) / 2];
+#pragma unroll
+    for (int q = 0; q < (P + 1) * (P + 2) / 2; ++q) t2[q] = T(0);
+    for (int j = 0; j < b; ++j) {
+      const T yj = (T(j) + T(0.5)) * inv_b - T(0.5);
+      T t1[P + 1];
+#pragma unroll
+      for (int a = 0; a <= P; ++a) t1[a] = T(0);
+      for (int i = 0; i < b; ++i) {
+        const T mi = mrow[j * b + i];
+        bad |= !isfinite(mi);
+        const T xi = (T(i) + T(0.5)) * inv_b - T(0.5);
+        T w = mi;
+#pragma unroll
+        for (int a = 0; a <= P; ++a) {
+          t1[a] += w;
+          w *= xi;
+        }
+      }
+      T ypow[P + 1];
+      powers<P, T>(yj, ypow);
+#pragma unroll
+      for (int a = 0; a <= P; ++a)
+#pragma unroll
+        for (int bb = 0; a + bb <= P; ++bb) t2[(a + bb) * (a + bb + 1) / 2 + bb] += t1[a] * ypow[bb];
+    }
+    const T zk = (T(k) + T(0.5)) * inv_b - T(0.5);
+    T zpow[P + 1];
+    powers<P, T>(zk, zpow);
+    int q = 0;
+#pragma unroll
+    for (int n = 0; n <= P; ++n)
+#pragma unroll
+      for (int bc = 0; bc <= n; ++bc)  // canonical order: a descending, then b descending
+#pragma unroll
+        for (int cc = 0; cc <= bc; ++cc) {
+          const int a = n - bc, bb = bc - cc;
+          if ((cc & 1) != h) continue;
+          acc[q] = fma(t2[(a + bb) * (a + bb + 1) / 2 + bb], zpow[cc], acc[q]);
+          ++q;
+        }
+  };
+  if (B.real) {
+    const T inv_b = T(1) / T(b);
+    const long long box = ((long long)B.z * leaf.n[1] + B.y) * leaf.n[0] + B.x;
+    const int b3 = b * b * b;
+    if (sizeof(T) == 4 && b == 4) {
+      // two z-planes (8 rows of 16 bytes) in flight per thread before any use
+      for (int k0 = 0; k0 < 4; k0 += 2) {
+        float4 v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+          v[r] = __ldg(reinterpret_cast<const float4*>(
+              rho + ((long long)(B.z * 4 + k0 + (r >> 2)) * ny + (B.y * 4 + (r & 3))) * nx + (long long)B.x * 4));
+        if (h == 0) {
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const long long e0 = box * 64 + (k0 * 4 + r) * 4;
+            if (rho_box) *reinterpret_cast<float4*>(rho_box + e0) = v[r];
+            if (rhi) {
+              const float m4[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
+              __nv_bfloat16 hh[4], ll[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                hh[i] = __float2bfloat16_rn(m4[i]);
+                ll[i] = __float2bfloat16_rn(m4[i] - __bfloat162float(hh[i]));
+              }
+              *reinterpret_cast<uint2*>(rhi + e0) = *reinterpret_cast<const uint2*>(hh);
+              *reinterpret_cast<uint2*>(rlo + e0) = *reinterpret_cast<const uint2*>(ll);
+            }
+          }
+        }
+        plane(reinterpret_cast<const T*>(&v[0]), k0, inv_b);
+        plane(reinterpret_cast<const T*>(&v[4]), k0 + 1, inv_b);
+      }
+    } else {
+      for (int k = 0; k < b; ++k) {
+        T mrow[64];  // b <= 8: one plane of b x b cells
+        for (int j = 0; j < b; ++j) {
+          const T* row = rho + ((long long)(B.z * b + k) * ny + (B.y * b + j)) * nx + (long long)B.x * b;
+          const long long e0 = box * b3 + (k * b + j) * b;
+          for (int i = 0; i < b; ++i) {
+            const T m = row[i];
+            mrow[j * b + i] = m;
+            if (h == 0) {
+              if (rho_box) rho_box[e0 + i] = m;
+              if (rhi) store_split(rhi, rlo, (size_t)(e0 + i), m);
+            }
+          }
+        }
+        plane(mrow, k, inv_b);
+      }
+    }
+  }
+  if (bad && h == 0) atomicOr(flag, 1);
+  // into the block's staged parent rows [parent][coef][child] (rows padded
+  // by 8 values so the four parents of a warp fall in different banks)
+  T* dst = Ms + (B.par & (kP2mParents - 1)) * (8 * NC + 8) + B.c;
+  int q = 0;
+#pragma unroll
+  for (int n = 0; n <= P; ++n)
+#pragma unroll
+    for (int bc = 0; bc <= n; ++bc)
+#pragma unroll
+      for (int cc = 0; cc <= bc; ++cc) {
+        const int a = n - bc, bb = bc - cc;
+        if ((cc & 1) != h) continue;
+        dst[cidx(a, bb, cc) * 8] = acc[q];
+        ++q;
+      }
+}
+
+// A block (256 threads, 128 boxes) covers kP2mParents whole parents, so its
+// output is one contiguous run of parent rows: staged in shared memory and
+// written with 16-byte stores (FP32 rows, and the bf16 hi/lo planes).
 template <int P, typename T>
 __global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho, int nx, int ny, int b, Level leaf,
                                                        T* __restrict__ Mleaf, __nv_bfloat16* __restrict__ Mhi,
@@ -18,89 +163,60 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho
                                                        __nv_bfloat16* __restrict__ rhi,
                                                        __nv_bfloat16* __restrict__ rlo, int* __restrict__ flag) {
   constexpr int NC = ncoef_c(P);
+  constexpr int ROW = 8 * NC;     // values per parent row
+  constexpr int ROWP = ROW + 8;   // staged row pitch
+  extern __shared__ __align__(16) unsigned char p2m_smem[];
+  T* Ms = reinterpret_cast<T*>(p2m_smem);
   const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
-  const Box B = box_of(leaf, t);
-  if (B.par >= leaf.npar) return;
-  T acc[NC];
+  const long long w = t >> 5;
+  const Box B = box_of(leaf, (w >> 1) * 32 + (t & 31));
+  if (B.par < leaf.npar) {
+    if (w & 1)
+      p2m_body<P, T, 1>(B, rho, nx, ny, b, leaf, Ms, rho_box, rhi, rlo, flag);
+    else
+      p2m_body<P, T, 0>(B, rho, nx, ny, b, leaf, Ms, rho_box, rhi, rlo, flag);
+  }
+  __syncthreads();
+  const long long p0 = (long long)blockIdx.x * kP2mParents;
+  const long long np = min((long long)kP2mParents, leaf.npar - p0);
+  if (np <= 0) return;
+  const int count = (int)np * ROW;  // a multiple of 8
+  const long long g0 = p0 * ROW;
+  if (sizeof(T) == 4) {
+    float4* out = reinterpret_cast<float4*>(Mleaf + g0);
+    for (int i = threadIdx.x; i < count / 4; i += kThreads) {
+      const int pr = i / (ROW / 4), wi = i % (ROW / 4);
+      out[i] = *reinterpret_cast<const float4*>(Ms + pr * ROWP + wi * 4);
+    }
+  } else {
+    for (int i = threadIdx.x; i < count; i += kThreads) Mleaf[g0 + i] = Ms[(i / ROW) * ROWP + i % ROW];
+  }
+  if (Mhi) {  // 8 values -> 16 bytes of hi and 16 bytes of lo
+    for (int i = threadIdx.x; i < count / 8; i += kThreads) {
+      const T* v = Ms + (i / (ROW / 8)) * ROWP + (i % (ROW / 8)) * 8;
+      __nv_bfloat16 hh[8], ll[8];
 #pragma unroll
-  for (int k = 0; k < NC; ++k) acc[k] = T(0);
-  bool bad = false;  // non-finite density (reported through the plan's flag)
-  if (B.real) {
-    const T inv_b = T(1) / T(b);
-    const long long box = ((long long)B.z * leaf.n[1] + B.y) * leaf.n[0] + B.x;
-    const int b3 = b * b * b;
-    for (int k = 0; k < b; ++k) {
-      const T zk = (T(k) + T(0.5)) * inv_b - T(0.5);
-      T t2[(P + 1) * (P + 2) / 2];
-#pragma unroll
-      for (int q = 0; q < (P + 1) * (P + 2) / 2; ++q) t2[q] = T(0);
-      for (int j = 0; j < b; ++j) {
-        const T yj = (T(j) + T(0.5)) * inv_b - T(0.5);
-        const T* row = rho + ((long long)(B.z * b + k) * ny + (B.y * b + j)) * nx + (long long)B.x * b;
-        const long long e0 = box * b3 + (k * b + j) * b;  // first cell of this row in the box-blocked copy
-        T m[8];
-        if (sizeof(T) == 4 && b == 4) {  // one 16-byte load, packed stores
-          const float4 v = *reinterpret_cast<const float4*>(row);
-          m[0] = v.x, m[1] = v.y, m[2] = v.z, m[3] = v.w;
-          if (rho_box) *reinterpret_cast<float4*>(rho_box + e0) = v;
-          if (rhi) {
-            __nv_bfloat16 h[4], l[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              h[i] = __float2bfloat16_rn((float)m[i]);
-              l[i] = __float2bfloat16_rn((float)m[i] - __bfloat162float(h[i]));
-            }
-            *reinterpret_cast<uint2*>(rhi + e0) = *reinterpret_cast<const uint2*>(h);
-            *reinterpret_cast<uint2*>(rlo + e0) = *reinterpret_cast<const uint2*>(l);
-          }
-        } else {
-          for (int i = 0; i < b; ++i) {
-            m[i] = row[i];
-            if (rho_box) rho_box[e0 + i] = m[i];
-            if (rhi) store_split(rhi, rlo, (size_t)(e0 + i), m[i]);
-          }
-        }
-        T t1[P + 1];
-#pragma unroll
-        for (int a = 0; a <= P; ++a) t1[a] = T(0);
-        for (int i = 0; i < b; ++i) {
-          bad |= !isfinite(m[i]);
-          const T xi = (T(i) + T(0.5)) * inv_b - T(0.5);
-          T w = m[i];
-#pragma unroll
-          for (int a = 0; a <= P; ++a) {
-            t1[a] += w;
-            w *= xi;
-          }
-        }
-        // t2[(a, bb)] += t1[a] * yj^bb, packed by (a + bb) blocks
-        T ypow[P + 1];
-        powers<P, T>(yj, ypow);
-#pragma unroll
-        for (int a = 0; a <= P; ++a)
-#pragma unroll
-          for (int bb = 0; a + bb <= P; ++bb) t2[(a + bb) * (a + bb + 1) / 2 + bb] += t1[a] * ypow[bb];
+      for (int q = 0; q < 8; ++q) {
+        const float x = (float)v[q];
+        hh[q] = __float2bfloat16_rn(x);
+        ll[q] = __float2bfloat16_rn(x - __bfloat162float(hh[q]));
       }
-      T zpow[P + 1];
-      powers<P, T>(zk, zpow);
-#pragma unroll
-      for (int a = 0; a <= P; ++a)
-#pragma unroll
-        for (int bb = 0; a + bb <= P; ++bb)
-#pragma unroll
-          for (int cc = 0; a + bb + cc <= P; ++cc)
-            acc[cidx(a, bb, cc)] = fma(t2[(a + bb) * (a + bb + 1) / 2 + bb], zpow[cc], acc[cidx(a, bb, cc)]);
+      reinterpret_cast<uint4*>(Mhi + g0)[i] = *reinterpret_cast<const uint4*>(hh);
+      reinterpret_cast<uint4*>(Mlo + g0)[i] = *reinterpret_cast<const uint4*>(ll);
     }
   }
-  if (bad) atomicOr(flag, 1);
-  T* dst = Mleaf + B.par * 8 * NC + B.c;
-#pragma unroll
-  for (int k = 0; k < NC; ++k) dst[k * 8] = acc[k];
-  if (Mhi) {
-    const size_t base = (size_t)B.par * 8 * NC + B.c;
-#pragma unroll
-    for (int k = 0; k < NC; ++k) store_split(Mhi, Mlo, base + (size_t)k * 8, acc[k]);
+}
+
+template <int P, typename T>
+void p2m_launch(unsigned blocks, cudaStream_t s, const T* rho, int nx, int ny, int b, Level leaf, T* Mleaf,
+                __nv_bfloat16* Mhi, __nv_bfloat16* Mlo, T* rho_box, __nv_bfloat16* rhi, __nv_bfloat16* rlo, int* flag) {
+  constexpr size_t smem = (size_t)kP2mParents * (8 * ncoef_c(P) + 8) * sizeof(T);
+  static bool attr = false;
+  if (!attr && smem > 48 * 1024) {
+    cudaFuncSetAttribute(p2m_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
   }
+  p2m_kernel<P, T><<<blocks, kThreads, smem, s>>>(rho, nx, ny, b, leaf, Mleaf, Mhi, Mlo, rho_box, rhi, rlo, flag);
 }
 
 }  // namespace
@@ -108,9 +224,9 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho
 template <typename T>
 cudaError_t launch_p2m(const TreeTables& t, const T* rho, const int dims[3], const Level& leaf, T* Mleaf, T* rho_box,
                        void* Mhi, void* Mlo, void* rho_hi, void* rho_lo, int* flag, cudaStream_t s) {
-  const long long threads = leaf.npar * 8;
+  const long long threads = leaf.npar * 16;  // two threads per box
   if (threads == 0) return cudaSuccess;
-  FMM_ORDER_SWITCH(t.p, (p2m_kernel<PP, T><<<grid_threads(threads), kThreads, 0, s>>>(
+  FMM_ORDER_SWITCH(t.p, (p2m_launch<PP, T>(grid_threads(threads), s,
                             rho, dims[0], dims[1], t.b, leaf, Mleaf, static_cast<__nv_bfloat16*>(Mhi),
                             static_cast<__nv_bfloat16*>(Mlo), rho_box, static_cast<__nv_bfloat16*>(rho_hi),
                             static_cast<__nv_bfloat16*>(rho_lo), flag)));
