@@ -31,23 +31,45 @@ __device__ __forceinline__ T fd_weight(int j, int off, int n) {
   return off == 0 ? T(1.5) : (off == -1 ? T(-2) : (off == -2 ? T(0.5) : T(0)));  // j == n-1
 }
 
-constexpr int kFdTX = 32, kFdTY = 8, kFdZC = 16;
+constexpr int kFdTX = 32, kFdTY = 8, kFdZC = 32;
 
-// 32 x 8 columns of cells per block, walking kFdZC cells along z: the x-y
-// neighbours come from a shared-memory tile with a 2-cell halo, the z
-// neighbours from a 5-value register window, so each value of phi is read
-// about 2.7 times from L2 and once from DRAM.
+// 32 x 8 columns of cells per block, walking kFdZC cells along z: the z
+// neighbours come from a 5-value register window per column, the x-y
+// neighbours from a shared-memory tile with a 2-cell halo whose centre is the
+// window's middle value (only the halo is read from memory); the tile is
+// double-buffered, so one barrier per plane.
 template <typename T>
 __global__ void __launch_bounds__(kFdTX* kFdTY) fd_accel_tiled_kernel(const T* __restrict__ phi, int nx, int ny,
                                                                       int nz, T inv_dx, T* __restrict__ accel) {
-  __shared__ T tile[kFdTY + 4][kFdTX + 4];
+  constexpr int HX = kFdTX + 4, HY = kFdTY + 4;
+  constexpr int kHalo = HX * HY - kFdTX * kFdTY;  // 176 halo cells per plane
+  __shared__ T tile[2][HY][HX];
   const long long n = (long long)nx * ny * nz;
   const long long plane = (long long)nx * ny;
   const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * kFdTX + tx;
   const int x0 = blockIdx.x * kFdTX, y0 = blockIdx.y * kFdTY, z0 = blockIdx.z * kFdZC;
   const int x = x0 + tx, y = y0 + ty;
   const bool inside = x < nx && y < ny;
   const long long col = (long long)y * nx + x;
+  // halo cell of this thread (threads 0 .. kHalo-1): the tile's two-cell frame
+  int hx = 0, hy = 0;
+  long long hoff = -1;
+  if (tid < kHalo) {
+    int r = tid;
+    if (r < 2 * HX) {
+      hy = r / HX, hx = r % HX;  // top two rows
+    } else if ((r -= 2 * HX) < 2 * HX) {
+      hy = HY - 2 + r / HX, hx = r % HX;  // bottom two rows
+    } else {
+      r -= 2 * HX;  // side columns of the middle rows: 4 per row
+      hy = 2 + r / 4;
+      const int c = r % 4;
+      hx = c < 2 ? c : kFdTX + c;
+    }
+    const int gx = x0 - 2 + hx, gy = y0 - 2 + hy;
+    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) hoff = (long long)gy * nx + gx;
+  }
   T wx[5], wy[5];
 #pragma unroll
   for (int o = -2; o <= 2; ++o) {
@@ -62,22 +84,19 @@ __global__ void __launch_bounds__(kFdTX* kFdTY) fd_accel_tiled_kernel(const T* _
   }
   const int z1 = min(z0 + kFdZC, nz);
   for (int z = z0; z < z1; ++z) {
+    const int buf = (z - z0) & 1;
 #pragma unroll
     for (int q = 0; q < 4; ++q) w[q] = w[q + 1];
     w[4] = (inside && z + 2 < nz) ? phi[(long long)(z + 2) * plane + col] : T(0);
-    for (int i = ty * kFdTX + tx; i < (kFdTY + 4) * (kFdTX + 4); i += kFdTX * kFdTY) {
-      const int lx = i % (kFdTX + 4), ly = i / (kFdTX + 4);
-      const int gx = x0 - 2 + lx, gy = y0 - 2 + ly;
-      tile[ly][lx] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? phi[(long long)z * plane + (long long)gy * nx + gx]
-                                                                 : T(0);
-    }
+    tile[buf][ty + 2][tx + 2] = w[2];
+    if (tid < kHalo) tile[buf][hy][hx] = hoff >= 0 ? phi[(long long)z * plane + hoff] : T(0);
     __syncthreads();
     if (inside) {
       T dx = T(0), dy = T(0), dz = T(0);
 #pragma unroll
       for (int o = -2; o <= 2; ++o) {
-        dx = fma(wx[o + 2], tile[ty + 2][tx + 2 + o], dx);
-        dy = fma(wy[o + 2], tile[ty + 2 + o][tx + 2], dy);
+        dx = fma(wx[o + 2], tile[buf][ty + 2][tx + 2 + o], dx);
+        dy = fma(wy[o + 2], tile[buf][ty + 2 + o][tx + 2], dy);
         dz = fma(fd_weight<T>(z, o, nz), w[o + 2], dz);
       }
       const long long c = (long long)z * plane + col;
@@ -85,7 +104,8 @@ __global__ void __launch_bounds__(kFdTX* kFdTY) fd_accel_tiled_kernel(const T* _
       accel[n + c] = -dy * inv_dx;
       accel[2 * n + c] = -dz * inv_dx;
     }
-    __syncthreads();
+    // the next plane writes the other buffer; the one after this waits for
+    // the barrier above of the next iteration
   }
 }
 

@@ -39,6 +39,38 @@ __global__ void __launch_bounds__(kThreads) leaf_finish_kernel(Level leaf, const
         for (int cc = 0; a + bb + cc <= P; ++cc) s = fma(L[cidx(a, bb, cc)], zpow[cc], s);
         u2[(a + bb) * (a + bb + 1) / 2 + bb] = s;
       }
+    if (sizeof(T) == 4 && b == 4) {
+      // the plane's four near rows in flight at once; 16-byte loads and stores
+      float4 nr[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) nr[j] = __ldg(reinterpret_cast<const float4*>(near_box + box * 64 + (k * 4 + j) * 4));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        T ypow[P + 1];
+        powers<P, T>((T(j) + T(0.5)) * inv_b - T(0.5), ypow);
+        T u1[P + 1];
+#pragma unroll
+        for (int a = 0; a <= P; ++a) {
+          T s = T(0);
+#pragma unroll
+          for (int bb = 0; a + bb <= P; ++bb) s = fma(u2[(a + bb) * (a + bb + 1) / 2 + bb], ypow[bb], s);
+          u1[a] = s;
+        }
+        float out[4];
+        const float nv[4] = {nr[j].x, nr[j].y, nr[j].z, nr[j].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const T xi = (T(i) + T(0.5)) * inv_b - T(0.5);
+          T s = u1[P];
+#pragma unroll
+          for (int a = P - 1; a >= 0; --a) s = fma(s, xi, u1[a]);  // Horner in x
+          out[i] = (float)(scale * fma(s, inv_b, (T)nv[i]));
+        }
+        *reinterpret_cast<float4*>(phi + ((long long)(B.z * 4 + k) * ny + (B.y * 4 + j)) * nx + (long long)B.x * 4) =
+            make_float4(out[0], out[1], out[2], out[3]);
+      }
+      continue;
+    }
     for (int j = 0; j < b; ++j) {
       T ypow[P + 1];
       powers<P, T>((T(j) + T(0.5)) * inv_b - T(0.5), ypow);
