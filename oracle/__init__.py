@@ -86,6 +86,9 @@ def _bind(lib):
         "oracle_direct": (I, [DP, I, I, I, D, D, DP, I]),
         "oracle_fmm_sample": (I, [DP, I, I, I, I, I, D, D, L, LP, DP, DP, I]),
         "oracle_adjoint": (I, [DP, DP, I, I, I, I, I, D, D, DP, I]),
+        "oracle_fmm_accel": (I, [DP, I, I, I, I, I, D, D, DP, I]),
+        "oracle_direct_accel": (I, [DP, I, I, I, D, D, DP, I]),
+        "oracle_fmm_sample_accel": (I, [DP, I, I, I, I, I, D, D, L, LP, DP, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -231,6 +234,35 @@ class Oracle:
         phi = np.zeros_like(rho)
         self.lib.oracle_direct(_dp(rho), nx, ny, nz, dx, G, _dp(phi), threads)
         return phi
+
+    def fmm_accel(self, rho, b: int, p: int, dx: float = 1.0, G: float = 1.0, threads: int = 0) -> np.ndarray:
+        """Analytic acceleration [3][nz][ny][nx]: gradient of the leaf local
+        expansions plus the near-field pair forces."""
+        rho = _f64(rho)
+        nz, ny, nx = rho.shape
+        acc = np.zeros((3,) + rho.shape)
+        if self.lib.oracle_fmm_accel(_dp(rho), nx, ny, nz, b, p, dx, G, _dp(acc), threads) != 0:
+            raise ValueError("oracle_fmm_accel rejected its arguments")
+        return acc
+
+    def direct_accel(self, rho, dx: float = 1.0, G: float = 1.0, threads: int = 0) -> np.ndarray:
+        """O(N^2) pair forces [3][nz][ny][nx]."""
+        rho = _f64(rho)
+        nz, ny, nx = rho.shape
+        acc = np.zeros((3,) + rho.shape)
+        self.lib.oracle_direct_accel(_dp(rho), nx, ny, nz, dx, G, _dp(acc), threads)
+        return acc
+
+    def fmm_sample_accel(self, rho, b, p, cells, dx=1.0, G=1.0, threads: int = 0) -> np.ndarray:
+        """Analytic acceleration at flat cell indices, (n, 3)."""
+        rho = _f64(rho)
+        nz, ny, nx = rho.shape
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        acc = np.zeros((cells.shape[0], 3))
+        if self.lib.oracle_fmm_sample_accel(_dp(rho), nx, ny, nz, b, p, dx, G, cells.shape[0],
+                                            cells.ctypes.data_as(_c_long_p), _dp(acc), threads) != 0:
+            raise ValueError("oracle_fmm_sample_accel rejected its arguments")
+        return acc
 
     def fmm_sample(self, rho, b, p, cells, dx=1.0, G=1.0, accel=False, threads: int = 0):
         """phi (and accel as (n,3)) at the flat cell indices ``cells``."""

@@ -264,6 +264,25 @@ static double or_l2p(const or_index* ix, const double* L, const double e[3]) {
   return s;
 }
 
+/* Gradient of the local expansion (the derivative of L2P): d/de_q of
+ * sum_beta L_beta e^beta / beta! = sum_{beta_q >= 1} L_beta e^(beta - e_q) / (beta - e_q)!.
+ * Used by the analytic acceleration (the force read off the expansions). */
+static void or_l2p_grad(const or_index* ix, const double* L, const double e[3], double g[3]) {
+  g[0] = g[1] = g[2] = 0.0;
+  for (int k = 0; k < ix->nc; ++k) {
+    const int* b = ix->mi[k];
+    for (int q = 0; q < 3; ++q) {
+      if (b[q] == 0) continue;
+      double w = 1.0;
+      for (int r = 0; r < 3; ++r) {
+        const int pw = b[r] - (r == q);
+        w *= or_ipow(e[r], pw) / or_fact(pw);
+      }
+      g[q] += w * L[k];
+    }
+  }
+}
+
 /* Public single-operator entry points (used by the operator pins). */
 int oracle_m2m(const double* Mc, const double* d, int p, double* Mp) {
   or_index* ix = (or_index*)malloc(sizeof(or_index));
@@ -299,6 +318,23 @@ static double or_g(double rx, double ry, double rz) {
   double r = sqrt(rx * rx + ry * ry + rz * rz);
   if (r <= 1.0) return -1.0; /* |r| <= dx: -1/dx (only the self cell on a grid) */
   return -1.0 / r;
+}
+
+/* Gradient in x of g(x - y) for the cell pair force: r / |r|^3 with r = x - y
+ * for distinct cells, and no self force (the softened kernel is constant at
+ * the self cell; reading of the force between distinct cells). */
+static void or_grad_g(double rx, double ry, double rz, double g[3]) {
+  const double r2 = rx * rx + ry * ry + rz * rz;
+  if (r2 == 0.0) {
+    g[0] = g[1] = g[2] = 0.0;
+    return;
+  }
+  const double inv = 1.0 / (r2 * sqrt(r2));
+#if ORACLE_MUTANT == 6 /* planted mistake: near-field force pointing away from the mass */
+  g[0] = -rx * inv, g[1] = -ry * inv, g[2] = -rz * inv;
+#else
+  g[0] = rx * inv, g[1] = ry * inv, g[2] = rz * inv;
+#endif
 }
 
 /* ------------------------------------------------------------------------ */
@@ -590,6 +626,40 @@ static double or_near_cell(const or_hier* H, const double* rho, int x, int y, in
     }
   }
   return s;
+}
+
+/* Gradient of the near-field potential of one cell (same near region). */
+static void or_near_grad(const or_hier* H, const double* rho, int x, int y, int z, double out[3]) {
+  const or_level* lf = &H->lev[H->L];
+  const int b = H->b;
+  int bi = x / b, bj = y / b, bk = z / b;
+  out[0] = out[1] = out[2] = 0.0;
+  for (int qk = bk - 1; qk <= bk + 1; ++qk) {
+    if (qk < 0 || qk >= lf->n[2]) continue;
+    for (int qj = bj - 1; qj <= bj + 1; ++qj) {
+      if (qj < 0 || qj >= lf->n[1]) continue;
+      for (int qi = bi - 1; qi <= bi + 1; ++qi) {
+        if (qi < 0 || qi >= lf->n[0]) continue;
+        for (int sz = qk * b; sz < qk * b + b; ++sz)
+          for (int sy = qj * b; sy < qj * b + b; ++sy)
+            for (int sx = qi * b; sx < qi * b + b; ++sx) {
+              double m = rho[((long)sz * H->N[1] + sy) * H->N[0] + sx];
+              double g[3];
+              or_grad_g((double)(x - sx), (double)(y - sy), (double)(z - sz), g);
+              for (int q = 0; q < 3; ++q) out[q] += m * g[q];
+            }
+      }
+    }
+  }
+}
+
+static void or_far_grad(const or_hier* H, const or_index* ix, double** L, int x, int y, int z, double g[3]) {
+  const or_level* lf = &H->lev[H->L];
+  int bi = x / H->b, bj = y / H->b, bk = z / H->b;
+  double c[3];
+  or_bcentre(lf, bi, bj, bk, c);
+  double e[3] = {x + 0.5 - c[0], y + 0.5 - c[1], z + 0.5 - c[2]};
+  or_l2p_grad(ix, L[H->L] + or_bidx(lf, bi, bj, bk) * ix->nc, e, g);
 }
 
 static double or_far_cell(const or_hier* H, const or_index* ix, double** L, int x, int y, int z) {
@@ -1004,6 +1074,93 @@ int oracle_adjoint(const double* gphi, const double* gaccel, int nx, int ny, int
   or_free_levels(&H, Lam);
   or_free_levels(&H, Mu);
   free(w);
+  free(ix);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Analytic acceleration (the force read off the expansions and the near    */
+/* pair forces, instead of the stencil of App. C):                          */
+/*   accel = -G dx ( grad L2P(L_leaf) + sum_near m (x - y) / |x - y|^3 )    */
+/* in cell units for the gradients (physical accel = -grad_phys phi).       */
+/* ------------------------------------------------------------------------ */
+
+int oracle_fmm_accel(const double* rho, int nx, int ny, int nz, int b, int p, double dx, double G, double* accel,
+                     int nthreads) {
+  or_hier H;
+  if (or_hier_init(&H, nx, ny, nz, b, p)) return -1;
+  or_set_threads(nthreads);
+  or_index* ix = (or_index*)malloc(sizeof(or_index));
+  or_index_init(ix, p);
+  double** M = or_upward(&H, ix, rho);
+  double** L = or_downward(&H, ix, M);
+  const long n = (long)nx * ny * nz;
+  const double scale = -G * dx;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (long c = 0; c < n; ++c) {
+    int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long)nx * ny));
+    double gf[3], gn[3];
+    or_far_grad(&H, ix, L, x, y, z, gf);
+    or_near_grad(&H, rho, x, y, z, gn);
+    for (int q = 0; q < 3; ++q) accel[q * n + c] = scale * (gf[q] + gn[q]);
+  }
+  or_free_levels(&H, M);
+  or_free_levels(&H, L);
+  free(ix);
+  return 0;
+}
+
+/* O(N^2) pair forces: accel(x) = -G dx sum_{y != x} m_y (x - y) / |x - y|^3. */
+int oracle_direct_accel(const double* rho, int nx, int ny, int nz, double dx, double G, double* accel, int nthreads) {
+  or_set_threads(nthreads);
+  const long n = (long)nx * ny * nz;
+  const double scale = -G * dx;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long c = 0; c < n; ++c) {
+    int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long)nx * ny));
+    double s[3] = {0.0, 0.0, 0.0};
+    for (long d = 0; d < n; ++d) {
+      double m = rho[d];
+      if (m == 0.0) continue;
+      int sx = (int)(d % nx), sy = (int)((d / nx) % ny), sz = (int)(d / ((long)nx * ny));
+      double g[3];
+      or_grad_g((double)(x - sx), (double)(y - sy), (double)(z - sz), g);
+      for (int q = 0; q < 3; ++q) s[q] += m * g[q];
+    }
+    for (int q = 0; q < 3; ++q) accel[q * n + c] = scale * s[q];
+  }
+  return 0;
+}
+
+/* Analytic acceleration at a sample of cells (any grid size): ancestor chain
+ * of local expansions as oracle_fmm_sample, then the gradients. */
+int oracle_fmm_sample_accel(const double* rho, int nx, int ny, int nz, int b, int p, double dx, double G,
+                            long nsample, const long* cells, double* accel_out /* [nsample][3] */, int nthreads) {
+  or_hier H;
+  if (or_hier_init(&H, nx, ny, nz, b, p)) return -1;
+  or_set_threads(nthreads);
+  or_index* ix = (or_index*)malloc(sizeof(or_index));
+  or_index_init(ix, p);
+  double** M = or_upward(&H, ix, rho);
+  const double scale = -G * dx;
+  const or_level* lf = &H.lev[H.L];
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long s = 0; s < nsample; ++s) {
+    long c = cells[s];
+    int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long)nx * ny));
+    int bi = x / H.b, bj = y / H.b, bk = z / H.b;
+    double* Lb = (double*)malloc(sizeof(double) * ix->nc);
+    or_local_chain(&H, ix, M, H.L, bi, bj, bk, Lb);
+    double cc[3];
+    or_bcentre(lf, bi, bj, bk, cc);
+    double e[3] = {x + 0.5 - cc[0], y + 0.5 - cc[1], z + 0.5 - cc[2]};
+    double gf[3], gn[3];
+    or_l2p_grad(ix, Lb, e, gf);
+    free(Lb);
+    or_near_grad(&H, rho, x, y, z, gn);
+    for (int q = 0; q < 3; ++q) accel_out[3 * s + q] = scale * (gf[q] + gn[q]);
+  }
+  or_free_levels(&H, M);
   free(ix);
   return 0;
 }

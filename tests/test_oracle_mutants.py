@@ -5,6 +5,7 @@ CPU only; the mutants are compiled into a temporary directory."""
 import pytest
 
 import oracle
+import test_oracle_accel as accel
 import test_oracle_ops as ops
 import test_oracle_solve as solve
 
@@ -14,6 +15,7 @@ MUTANTS = {
     3: "L2L with the displacement reversed",
     4: "interaction list also takes the near neighbours",
     5: "near field without the self cell",
+    6: "near-field pair force pointing away from the mass",
 }
 
 PINS = [
@@ -22,6 +24,8 @@ PINS = [
     solve.test_converges_to_direct_sum_in_p,
     solve.test_point_mass_closed_form,
     lambda o: solve.test_equals_direct_sum_when_all_boxes_are_near(o, (8, 8, 8), 4),
+    accel.test_accel_converges_to_direct_in_p,
+    accel.test_direct_pair_forces_obey_the_third_law,
 ]
 
 
