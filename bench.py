@@ -52,6 +52,8 @@ def parse():
                          "(64/96/128/192)^3 solved as one CUDA graph")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default CUDA-core contraction variants")
+    ap.add_argument("--accel", default="fd", choices=["fd", "analytic"],
+                    help="acceleration by the 5-point stencil of phi (fd) or from the expansions and pair forces")
     return ap.parse_args()
 
 
@@ -291,7 +293,8 @@ def main():
     dx = 1.0 / n
     rho_np = inputs.lognormal(n, seed=2606 + rank)
     rho = torch.from_numpy(rho_np).cuda()
-    plan = fmm.FMMPlan((n, n, n), p, b, args.precision, dx=dx)
+    plan = fmm.FMMPlan((n, n, n), p, b, args.precision, dx=dx,
+                       accel="analytic" if args.accel == "analytic" else True)
     if not args.no_autotune:
         plan.autotune()
     tuning = {str(l): list(plan.tuning(l)) for l in range(2, plan.leaf_level + 1) if plan.level_kind(l) != "tensor"}
@@ -448,7 +451,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": f"unigrid FMM {n}^3 isolated, p={p}, leaf {b}^3, lognormal P(k)~k^-2.5",
                            "precision": args.precision, "l2": "inputs larger than L2 (rho 512 MiB, outputs 2 GiB)",
-                           "parallelism": f"replicas x{world}", "cuda_core_variants": tuning,
+                           "parallelism": f"replicas x{world}", "cuda_core_variants": tuning, "accel": args.accel,
                            "autotuned": not args.no_autotune, **compare},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": plan.launches(True) * args.steps,

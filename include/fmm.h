@@ -80,7 +80,14 @@ typedef struct {
   int precision;      /* fmm_precision                                          */
   int n_fp64_levels;  /* mixed precisions: coarsest M2L levels kept in FP64
                          (levels 2 .. 1+n_fp64_levels); default 3               */
-  int accel;          /* 1: fmm_solve may be given an accel output (FD5) */
+  int accel;          /* 0: no accel output; 1: accel = -grad(phi) by the
+                         5-point stencil (App. C); 2: analytic accel, the
+                         gradient of the leaf local expansions plus the
+                         near-field pair forces m (x - y)/|x - y|^3 between
+                         distinct cells (no self force).  With 2, the near
+                         field computes four columns per cell and
+                         fmm_solve_adjoint rejects grad_accel
+                         (FMM_ERR_UNSUPPORTED)                                  */
   int reserved[5];    /* must be zero */
 } fmm_opts;
 

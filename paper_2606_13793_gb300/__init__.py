@@ -162,7 +162,7 @@ class FMMPlan:
     """One solver for a fixed grid shape, order, leaf size and precision."""
 
     def __init__(self, shape, order: int = 6, leaf: int = 4, precision: str = "fp32", dx: float = 1.0,
-                 G: float = 1.0, n_fp64_levels: int = 3, accel: bool = True, stream=None):
+                 G: float = 1.0, n_fp64_levels: int = 3, accel=True, stream=None):
         import torch
 
         self.lib = load()
@@ -178,7 +178,9 @@ class FMMPlan:
         self.lib.fmm_default_opts(ctypes.byref(opts))
         opts.precision = PRECISION[precision]
         opts.n_fp64_levels = int(n_fp64_levels)
-        opts.accel = 1 if accel else 0
+        # accel: False (none), True (5-point stencil of phi), "analytic" (gradient
+        # of the expansions plus near-field pair forces)
+        opts.accel = 2 if accel == "analytic" else (1 if accel else 0)
         handle = ctypes.c_void_p()
         _check(self.lib, self.lib.fmm_plan(ctypes.byref(grid), self.order, self.leaf, ctypes.byref(opts),
                                            _stream_handle(stream), ctypes.byref(handle)))

@@ -186,6 +186,7 @@ struct fmm_plan_s {
   cudaStream_t last_stream = nullptr;
   // side stream of the concurrent far field (CUDA-core M2L levels), fork/join events
   cudaStream_t side = nullptr;
+  int near_comps = 1;  // near-field columns per cell: potential, + 3 force components (analytic accel)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // timing
   bool timing = false;
@@ -671,36 +672,52 @@ bool build_tc(const MultiIndex& mi, const TaylorTable& tt, int kind, TcHost& H) 
   return build_tc_generic(kind, gs, entry, H, 2);
 }
 
+// One near-field weight (eq. direct, cell units) between source cell s of the
+// neighbour leaf box at offset D and output column n = q * b^3 + t (target
+// cell t): q = 0 the potential kernel g(r) (-1 for the cell itself); q = 1..3
+// the force kernel d/dx_q g(r) = r_q / |r|^3 (0 for the cell itself), with
+// r = x_t - x_s.
+double near_entry(int b, const int D[3], int s, int n) {
+  const int b3 = b * b * b;
+  const int q = n / b3, t = n % b3;
+  const int tp[3] = {t % b, (t / b) % b, t / (b * b)};
+  const int sp[3] = {s % b, (s / b) % b, s / (b * b)};
+  double r[3], r2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    r[a] = (double)(tp[a] - sp[a] - b * D[a]);
+    r2 += r[a] * r[a];
+  }
+  if (q == 0) return r2 == 0.0 ? -1.0 : -1.0 / std::sqrt(r2);
+  return r2 == 0.0 ? 0.0 : r[q - 1] / (r2 * std::sqrt(r2));
+}
+
 // Near field (eq. direct) as the same contraction over leaf boxes: column n =
-// target cell, reduction k = source cell of neighbour box d, weight
-// g(x_t - x_s) in cell units (-1 for the cell itself).
-bool build_tc_near(int b, int kind, TcHost& H) {
+// (component, target cell), reduction k = source cell of neighbour box d,
+// weight near_entry(d, k, n).
+bool build_tc_near(int b, int comps, int kind, TcHost& H) {
   const int b3 = b * b * b;
   std::vector<TcCols> gs;
   // groups of up to 128 columns: an MMA narrower than 64 columns holds the
-  // tensor pipe as long as a 64-column one, so b = 4 stays one group
-  for (int c = 0; c < b3; c += kTcMaxGroupN) gs.push_back({c, std::min(kTcMaxGroupN, b3 - c), b3});
+  // tensor pipe as long as a 64-column one, so each b = 4 component is one group
+  const int per = std::min(kTcMaxGroupN, b3);
+  for (int c = 0; c < comps * b3; c += per) gs.push_back({c, std::min(per, comps * b3 - c), b3});
   auto entry = [b](int d, int k, int n) {
     const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
-    const int tp[3] = {n % b, (n / b) % b, n / (b * b)};
-    const int sp[3] = {k % b, (k / b) % b, k / (b * b)};
-    double r2 = 0.0;
-    for (int q = 0; q < 3; ++q) {
-      const double r = (double)(tp[q] - sp[q] - b * D[q]);
-      r2 += r * r;
-    }
-    return r2 == 0.0 ? -1.0 : -1.0 / std::sqrt(r2);
+    return near_entry(b, D, k, n);
   };
   return build_tc_generic(kind, gs, entry, H, 2);
 }
 
-// Near-field matrices (eq. direct, cell units): W_d[s][t] = g(x_t - x_s) for
-// source cell s of neighbour leaf box d and target cell t.
+// Near-field matrices (eq. direct, cell units) for the CUDA-core contraction:
+// W_d[s][n] = near_entry(d, s, n) for source cell s of neighbour leaf box d
+// and output column n (potential, then the force components).
+
 template <typename T>
-void near_weights(int b, std::vector<T>& W, std::vector<int>& tile_k, std::vector<long long>& tile_w,
+void near_weights(int b, int comps, std::vector<T>& W, std::vector<int>& tile_k, std::vector<long long>& tile_w,
                   bool fill = true) {
   const int b3 = b * b * b;
-  const int ntiles = (b3 + kNTile - 1) / kNTile;
+  const int ncols = comps * b3;
+  const int ntiles = (ncols + kNTile - 1) / kNTile;
   tile_k.assign(ntiles, b3);
   tile_w.resize(ntiles);
   for (int t = 0; t < ntiles; ++t) tile_w[t] = 27LL * b3 * kNTile * t;
@@ -711,18 +728,9 @@ void near_weights(int b, std::vector<T>& W, std::vector<int>& tile_k, std::vecto
       const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
       T* blk = W.data() + tile_w[t] + (long long)d * b3 * kNTile;
       for (int j = 0; j < kNTile; ++j) {
-        const int tc = t * kNTile + j;
-        if (tc >= b3) continue;
-        const int tp[3] = {tc % b, (tc / b) % b, tc / (b * b)};
-        for (int s = 0; s < b3; ++s) {
-          const int sp[3] = {s % b, (s / b) % b, s / (b * b)};
-          double r2 = 0.0;
-          for (int q = 0; q < 3; ++q) {
-            const double r = (double)(tp[q] - sp[q] - b * D[q]);
-            r2 += r * r;
-          }
-          blk[(long long)s * kNTile + j] = (T)(r2 == 0.0 ? -1.0 : -1.0 / std::sqrt(r2));
-        }
+        const int n = t * kNTile + j;
+        if (n >= ncols) continue;
+        for (int s = 0; s < b3; ++s) blk[(long long)s * kNTile + j] = (T)near_entry(b, D, s, n);
       }
     }
 }
@@ -792,6 +800,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
   P->opts = o;
   P->mi.init(order);
   P->nc = P->mi.nc;
+  P->near_comps = o.accel == 2 ? 4 : 1;
 
   fmm_status st = build_levels(P);
   if (st != FMM_OK) return st;
@@ -833,7 +842,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
   P->rho_box_off = off;
   off = align(off + cells_bytes);
   P->near_off = off;
-  off = align(off + cells_bytes);
+  off = align(off + cells_bytes * (size_t)P->near_comps);
   P->work_off = off;
   off = align(off + cells_bytes);
   P->near_tc = tcp && (leaf == 4 || leaf == 8);
@@ -856,7 +865,8 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     // room for the autotuner's neighbour-split candidates (M2L levels and the
     // near field), up to 64 MiB
     if (!P->near_tc)
-      want = std::max(want, (size_t)27 * (size_t)P->lev[P->L].nbox * (size_t)(P->b * P->b * P->b) * P->esize());
+      want = std::max(want, (size_t)27 * (size_t)P->lev[P->L].nbox * (size_t)(P->b * P->b * P->b) *
+                                (size_t)P->near_comps * P->esize());
     if (!P->no_split) part = std::max(part, std::min(want, (size_t)64 << 20));
     P->part_off = off;
     P->part_cap = part;
@@ -962,13 +972,13 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     std::vector<long long> tw;
     if (P->f64_data()) {
       std::vector<double> W;
-      near_weights<double>(P->b, W, tk, tw, !P->static_keep_tables);
+      near_weights<double>(P->b, P->near_comps, W, tk, tw, !P->static_keep_tables);
       double* d = nullptr;
       if ((st = P->upload(W, &d, s))) return cleanup(st);
       P->d_w_near = d;
     } else {
       std::vector<float> W;
-      near_weights<float>(P->b, W, tk, tw, !P->static_keep_tables);
+      near_weights<float>(P->b, P->near_comps, W, tk, tw, !P->static_keep_tables);
       float* d = nullptr;
       if ((st = P->upload(W, &d, s))) return cleanup(st);
       P->d_w_near = d;
@@ -981,7 +991,8 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     TcHost H;
     // bf16x3 in both tensor-core precisions: a TF32 near field would carry
     // ~3e-4 relative error on its (same-signed) sums
-    if (!build_tc_near(P->b, TC_BF16X3, H)) return cleanup(fail(FMM_ERR_UNSUPPORTED, "near-field schedule failed"));
+    if (!build_tc_near(P->b, P->near_comps, TC_BF16X3, H))
+      return cleanup(fail(FMM_ERR_UNSUPPORTED, "near-field schedule failed"));
     unsigned char* dw = nullptr;
     if ((st = P->upload(H.W, &dw, s))) return cleanup(st);
     TcLaunch& T = P->tcn;
@@ -989,14 +1000,17 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     T.npass = H.npass;
     T.a_stages = H.a_stages;
     for (int i = 0; i < H.npass; ++i) T.pass[i] = H.pass[i];
-    T.n_cols = P->b * P->b * P->b;
+    T.n_cols = P->b * P->b * P->b * P->near_comps;
     T.kind = TC_BF16X3;
     T.accumulate = 0;
     for (int q = 0; q < 3; ++q) T.grid[q] = P->lev[P->L].n[q];
     T.C = reinterpret_cast<float*>(P->arena + P->near_off);
     T.err = P->d_flag;
-    cudaError_t e = make_row_map(P->map_near_hi, P->arena + P->rho_hi_off, T.n_cols, 2, T.grid, 64);
-    if (e == cudaSuccess) e = make_row_map(P->map_near_lo, P->arena + P->rho_lo_off, T.n_cols, 2, T.grid, 64);
+    // activation rows: the b^3 cell values of a leaf box (the output rows carry
+    // near_comps x b^3 columns)
+    const int b3 = P->b * P->b * P->b;
+    cudaError_t e = make_row_map(P->map_near_hi, P->arena + P->rho_hi_off, b3, 2, T.grid, 64);
+    if (e == cudaSuccess) e = make_row_map(P->map_near_lo, P->arena + P->rho_lo_off, b3, 2, T.grid, 64);
     if (e != cudaSuccess) return cleanup(fail(FMM_ERR_CUDA, "tensor map encoding failed for the near field"));
   }
   P->tc.err = P->d_flag;
@@ -1048,6 +1062,7 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
   }
   if (o.precision < FMM_FP64 || o.precision > FMM_M2L_BF16X3) return fail(FMM_ERR_ARG, "unknown precision %d", o.precision);
   if (o.n_fp64_levels < 0 || o.n_fp64_levels > kMaxLevels) return fail(FMM_ERR_ARG, "bad n_fp64_levels");
+  if (o.accel < 0 || o.accel > 2) return fail(FMM_ERR_ARG, "accel %d not in {0, 1, 2}", o.accel);
   for (int r : o.reserved)
     if (r != 0) return fail(FMM_ERR_ARG, "reserved option fields must be zero");
   int dev = 0;
@@ -1166,7 +1181,7 @@ NbrGemm near_gemm(fmm_plan_t P) {
   g.tile_k = P->d_near_tile_k;
   g.tile_w = P->d_near_tile_w;
   g.C = P->arena + P->near_off;
-  g.n_cols = P->b * P->b * P->b;
+  g.n_cols = P->b * P->b * P->b * P->near_comps;
   g.ntiles = P->near_ntiles;
   g.accumulate = 0;
   g.shape = P->near_choice.shape;
@@ -1258,10 +1273,16 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
     StageTimer t(P, ST_L2L, s);
     if ((st = do_l2l(P, tt, l, s))) return st;
   }
+  if (accel && P->near_comps == 4) {  // analytic acceleration, read off the expansions
+    StageTimer t(P, ST_LEAF, s);
+    CUDA_TRY(launch_leaf_finish_grad<T>(tt, P->lev[L], static_cast<const T*>(P->Lx(L)), near_box, P->dims,
+                                        P->G * P->dx * P->dx, -P->G * P->dx, phi, accel, s));
+    return FMM_OK;
+  }
   {
     StageTimer t(P, ST_LEAF, s);
-    CUDA_TRY(launch_leaf_finish<T>(tt, P->lev[L], static_cast<const T*>(P->Lx(L)), near_box, P->dims,
-                                   P->G * P->dx * P->dx, phi, s));
+    CUDA_TRY(launch_leaf_finish<T>(tt, P->lev[L], static_cast<const T*>(P->Lx(L)), near_box,
+                                   P->b * P->b * P->b * P->near_comps, P->dims, P->G * P->dx * P->dx, phi, s));
   }
   if (accel) {
     StageTimer t(P, ST_FD, s);
@@ -1293,6 +1314,8 @@ fmm_status fmm_solve(fmm_plan_t P, const void* rho, void* phi, void* accel, void
 fmm_status fmm_solve_adjoint(fmm_plan_t P, const void* grad_phi, const void* grad_accel, void* grad_rho, void* stream) {
   if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
   if (!grad_rho || (!grad_phi && !grad_accel)) return fail(FMM_ERR_ARG, "grad_rho and one gradient must be non-NULL");
+  if (grad_accel && P->near_comps == 4)
+    return fail(FMM_ERR_UNSUPPORTED, "the adjoint of the analytic acceleration is not built (use accel = 1)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   P->last_stream = s;
   void* w = P->arena + P->work_off;
@@ -1377,7 +1400,7 @@ int fmm_solve_launches(fmm_plan_t P, int with_accel) {
   }
   n += 2;                               // near field + leaf finish
   if (!P->near_tc && P->near_choice.dsplit > 1) n += 1;
-  if (with_accel) n += 1;
+  if (with_accel && P->near_comps == 1) n += 1;  // FD stencil (the analytic force comes with the leaf kernel)
   return n;
 }
 

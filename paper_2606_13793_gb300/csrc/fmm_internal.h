@@ -119,9 +119,15 @@ cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, cons
                        cudaStream_t s);
 template <typename T>
 cudaError_t launch_zero(T* p, size_t count, cudaStream_t s);
+// near_box rows hold near_stride values per leaf box, the potential sums first.
 template <typename T>
 cudaError_t launch_leaf_finish(const TreeTables& t, const Level& leaf, const T* Lleaf, const T* near_box,
-                               const int dims[3], double scale, T* phi, cudaStream_t s);
+                               int near_stride, const int dims[3], double scale, T* phi, cudaStream_t s);
+// With the analytic acceleration: near_box rows are [potential, d/dx, d/dy,
+// d/dz] x b^3; accel = ascale (far gradient + near gradient).
+template <typename T>
+cudaError_t launch_leaf_finish_grad(const TreeTables& t, const Level& leaf, const T* Lleaf, const T* near_box,
+                                    const int dims[3], double scale, double ascale, T* phi, T* accel, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fd_accel(const T* phi, const int dims[3], double inv_dx, T* accel, cudaStream_t s);
 template <typename T>

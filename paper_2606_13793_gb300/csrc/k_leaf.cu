@@ -11,10 +11,11 @@ using namespace tree;
 // Leaf evaluation (Sec. 2.3):
 //   phi = G dx^2 [ h^-1 sum_beta Lt_beta ((x - c)/h)^beta + near ]
 // near_box holds the near-field sums per leaf box ([box][b^3] cells).
+// near_box rows have near_stride values per box (the potential first).
 template <int P, typename T>
 __global__ void __launch_bounds__(kThreads) leaf_finish_kernel(Level leaf, const T* __restrict__ Lleaf,
-                                                               const T* __restrict__ near_box, int nx, int ny, int b,
-                                                               T scale, T* __restrict__ phi) {
+                                                               const T* __restrict__ near_box, int near_stride, int nx,
+                                                               int ny, int b, T scale, T* __restrict__ phi) {
   constexpr int NC = ncoef_c(P);
   const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
   const Box B = box_of(leaf, t);
@@ -25,7 +26,6 @@ __global__ void __launch_bounds__(kThreads) leaf_finish_kernel(Level leaf, const
   for (int k = 0; k < NC; ++k) L[k] = src[k * 8];
   const T inv_b = T(1) / T(b);
   const long long box = ((long long)B.z * leaf.n[1] + B.y) * leaf.n[0] + B.x;
-  const int b3 = b * b * b;
   for (int k = 0; k < b; ++k) {
     T zpow[P + 1];
     powers<P, T>((T(k) + T(0.5)) * inv_b - T(0.5), zpow);
@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(kThreads) leaf_finish_kernel(Level leaf, const
       // the plane's four near rows in flight at once; 16-byte loads and stores
       float4 nr[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) nr[j] = __ldg(reinterpret_cast<const float4*>(near_box + box * 64 + (k * 4 + j) * 4));
+      for (int j = 0; j < 4; ++j)
+        nr[j] = __ldg(reinterpret_cast<const float4*>(near_box + box * near_stride + (k * 4 + j) * 4));
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         T ypow[P + 1];
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(kThreads) leaf_finish_kernel(Level leaf, const
         u1[a] = s;
       }
       T* row = phi + ((long long)(B.z * b + k) * ny + (B.y * b + j)) * nx + (long long)B.x * b;
-      const T* nrow = near_box + box * b3 + (k * b + j) * b;
+      const T* nrow = near_box + box * near_stride + (k * b + j) * b;
       for (int i = 0; i < b; ++i) {
         const T xi = (T(i) + T(0.5)) * inv_b - T(0.5);
         T s = u1[P];
@@ -95,21 +96,124 @@ __global__ void __launch_bounds__(kThreads) leaf_finish_kernel(Level leaf, const
   }
 }
 
+// Leaf evaluation with the analytic acceleration: also the gradient of the
+// local expansion (derivatives of the separable powers) and the near-field
+// force columns (near_box row = potential, then d/dx, d/dy, d/dz sums of
+// b^3 values each):
+//   accel_q = -G dx [ h^-2 sum_beta Lt_beta d/dxi_q ((x - c)/h)^beta + near_q ]
+template <int P, typename T>
+__global__ void __launch_bounds__(kThreads) leaf_finish_grad_kernel(Level leaf, const T* __restrict__ Lleaf,
+                                                                    const T* __restrict__ near_box, int nx, int ny,
+                                                                    int nz, int b, T scale, T ascale,
+                                                                    T* __restrict__ phi, T* __restrict__ accel) {
+  constexpr int NC = ncoef_c(P);
+  constexpr int N2 = (P + 1) * (P + 2) / 2;
+  const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const Box B = box_of(leaf, t);
+  if (!B.real) return;
+  T L[NC];
+  const T* src = Lleaf + B.par * 8 * NC + B.c;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) L[k] = src[k * 8];
+  const T inv_b = T(1) / T(b);
+  const long long ncell = (long long)nx * ny * nz;
+  const long long box = ((long long)B.z * leaf.n[1] + B.y) * leaf.n[0] + B.x;
+  const int b3 = b * b * b;
+  const T* nb = near_box + box * 4 * b3;
+  for (int k = 0; k < b; ++k) {
+    const T zk = (T(k) + T(0.5)) * inv_b - T(0.5);
+    T zpow[P + 1], dzpow[P + 1];
+    powers<P, T>(zk, zpow);
+    dzpow[0] = T(0);
+#pragma unroll
+    for (int c = 1; c <= P; ++c) dzpow[c] = T(c) * zpow[c - 1];
+    T u2[N2], u2z[N2];  // (a, bb) with a + bb <= P: sums over c of L zk^c and of L d/dz zk^c
+#pragma unroll
+    for (int a = 0; a <= P; ++a)
+#pragma unroll
+      for (int bb = 0; a + bb <= P; ++bb) {
+        T s = T(0), sz = T(0);
+#pragma unroll
+        for (int cc = 0; a + bb + cc <= P; ++cc) {
+          s = fma(L[cidx(a, bb, cc)], zpow[cc], s);
+          sz = fma(L[cidx(a, bb, cc)], dzpow[cc], sz);
+        }
+        u2[(a + bb) * (a + bb + 1) / 2 + bb] = s;
+        u2z[(a + bb) * (a + bb + 1) / 2 + bb] = sz;
+      }
+    for (int j = 0; j < b; ++j) {
+      const T yj = (T(j) + T(0.5)) * inv_b - T(0.5);
+      T ypow[P + 1], dypow[P + 1];
+      powers<P, T>(yj, ypow);
+      dypow[0] = T(0);
+#pragma unroll
+      for (int c = 1; c <= P; ++c) dypow[c] = T(c) * ypow[c - 1];
+      T u1[P + 1], u1y[P + 1], u1z[P + 1];
+#pragma unroll
+      for (int a = 0; a <= P; ++a) {
+        T s = T(0), sy = T(0), sz = T(0);
+#pragma unroll
+        for (int bb = 0; a + bb <= P; ++bb) {
+          const int q = (a + bb) * (a + bb + 1) / 2 + bb;
+          s = fma(u2[q], ypow[bb], s);
+          sy = fma(u2[q], dypow[bb], sy);
+          sz = fma(u2z[q], ypow[bb], sz);
+        }
+        u1[a] = s, u1y[a] = sy, u1z[a] = sz;
+      }
+      const long long row = ((long long)(B.z * b + k) * ny + (B.y * b + j)) * nx + (long long)B.x * b;
+      const int e0 = (k * b + j) * b;
+      for (int i = 0; i < b; ++i) {
+        const T xi = (T(i) + T(0.5)) * inv_b - T(0.5);
+        // Horner in x for the value, the x-derivative and the y/z-derivative polynomials
+        T s = u1[P], sx = T(0), sy = u1y[P], sz = u1z[P];
+#pragma unroll
+        for (int a = P - 1; a >= 0; --a) {
+          sx = fma(sx, xi, s);
+          s = fma(s, xi, u1[a]);
+          sy = fma(sy, xi, u1y[a]);
+          sz = fma(sz, xi, u1z[a]);
+        }
+        phi[row + i] = scale * fma(s, inv_b, nb[e0 + i]);
+        const T ib2 = inv_b * inv_b;
+        accel[row + i] = ascale * fma(sx, ib2, nb[b3 + e0 + i]);
+        accel[ncell + row + i] = ascale * fma(sy, ib2, nb[2 * b3 + e0 + i]);
+        accel[2 * ncell + row + i] = ascale * fma(sz, ib2, nb[3 * b3 + e0 + i]);
+      }
+    }
+  }
+}
+
 }  // namespace
 
 template <typename T>
-cudaError_t launch_leaf_finish(const TreeTables& t, const Level& leaf, const T* Lleaf, const T* near_box,
-                               const int dims[3], double scale, T* phi, cudaStream_t s) {
+cudaError_t launch_leaf_finish_grad(const TreeTables& t, const Level& leaf, const T* Lleaf, const T* near_box,
+                                    const int dims[3], double scale, double ascale, T* phi, T* accel, cudaStream_t s) {
   const long long threads = leaf.npar * 8;
   if (threads == 0) return cudaSuccess;
-  FMM_ORDER_SWITCH(t.p, (leaf_finish_kernel<PP, T><<<grid_threads(threads), kThreads, 0, s>>>(
-                            leaf, Lleaf, near_box, dims[0], dims[1], t.b, (T)scale, phi)));
+  FMM_ORDER_SWITCH(t.p, (leaf_finish_grad_kernel<PP, T><<<grid_threads(threads), kThreads, 0, s>>>(
+                            leaf, Lleaf, near_box, dims[0], dims[1], dims[2], t.b, (T)scale, (T)ascale, phi, accel)));
   return cudaGetLastError();
 }
 
-template cudaError_t launch_leaf_finish<float>(const TreeTables&, const Level&, const float*, const float*,
+template cudaError_t launch_leaf_finish_grad<float>(const TreeTables&, const Level&, const float*, const float*,
+                                                    const int*, double, double, float*, float*, cudaStream_t);
+template cudaError_t launch_leaf_finish_grad<double>(const TreeTables&, const Level&, const double*, const double*,
+                                                     const int*, double, double, double*, double*, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_leaf_finish(const TreeTables& t, const Level& leaf, const T* Lleaf, const T* near_box,
+                               int near_stride, const int dims[3], double scale, T* phi, cudaStream_t s) {
+  const long long threads = leaf.npar * 8;
+  if (threads == 0) return cudaSuccess;
+  FMM_ORDER_SWITCH(t.p, (leaf_finish_kernel<PP, T><<<grid_threads(threads), kThreads, 0, s>>>(
+                            leaf, Lleaf, near_box, near_stride, dims[0], dims[1], t.b, (T)scale, phi)));
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_leaf_finish<float>(const TreeTables&, const Level&, const float*, const float*, int,
                                                const int*, double, float*, cudaStream_t);
-template cudaError_t launch_leaf_finish<double>(const TreeTables&, const Level&, const double*, const double*,
+template cudaError_t launch_leaf_finish<double>(const TreeTables&, const Level&, const double*, const double*, int,
                                                 const int*, double, double*, cudaStream_t);
 
 }  // namespace fmmgb
