@@ -141,6 +141,64 @@ __global__ void __launch_bounds__(kThreads) leaf_finish_grad_kernel(Level leaf, 
         u2[(a + bb) * (a + bb + 1) / 2 + bb] = s;
         u2z[(a + bb) * (a + bb + 1) / 2 + bb] = sz;
       }
+    if (sizeof(T) == 4 && b == 4) {
+      // 16-byte loads of the four near columns and 16-byte stores of the
+      // potential and the three force rows; the plane unrolled so the loads
+      // of one row issue ahead of the previous row's arithmetic
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int e0 = (k * 4 + j) * 4;
+        const float4 n0 = __ldg(reinterpret_cast<const float4*>(nb + e0));
+        const float4 n1 = __ldg(reinterpret_cast<const float4*>(nb + 64 + e0));
+        const float4 n2 = __ldg(reinterpret_cast<const float4*>(nb + 128 + e0));
+        const float4 n3 = __ldg(reinterpret_cast<const float4*>(nb + 192 + e0));
+        const T yj = (T(j) + T(0.5)) * inv_b - T(0.5);
+        T ypow[P + 1], dypow[P + 1];
+        powers<P, T>(yj, ypow);
+        dypow[0] = T(0);
+#pragma unroll
+        for (int c = 1; c <= P; ++c) dypow[c] = T(c) * ypow[c - 1];
+        T u1[P + 1], u1y[P + 1], u1z[P + 1];
+#pragma unroll
+        for (int a = 0; a <= P; ++a) {
+          T sv = T(0), sy = T(0), sz = T(0);
+#pragma unroll
+          for (int bb = 0; a + bb <= P; ++bb) {
+            const int q = (a + bb) * (a + bb + 1) / 2 + bb;
+            sv = fma(u2[q], ypow[bb], sv);
+            sy = fma(u2[q], dypow[bb], sy);
+            sz = fma(u2z[q], ypow[bb], sz);
+          }
+          u1[a] = sv, u1y[a] = sy, u1z[a] = sz;
+        }
+        const float nv0[4] = {n0.x, n0.y, n0.z, n0.w}, nv1[4] = {n1.x, n1.y, n1.z, n1.w};
+        const float nv2[4] = {n2.x, n2.y, n2.z, n2.w}, nv3[4] = {n3.x, n3.y, n3.z, n3.w};
+        float o0[4], o1[4], o2[4], o3[4];
+        const T ib2 = inv_b * inv_b;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const T xi = (T(i) + T(0.5)) * inv_b - T(0.5);
+          T sv = u1[P], sx = T(0), sy = u1y[P], sz = u1z[P];
+#pragma unroll
+          for (int a = P - 1; a >= 0; --a) {
+            sx = fma(sx, xi, sv);
+            sv = fma(sv, xi, u1[a]);
+            sy = fma(sy, xi, u1y[a]);
+            sz = fma(sz, xi, u1z[a]);
+          }
+          o0[i] = (float)(scale * fma(sv, inv_b, (T)nv0[i]));
+          o1[i] = (float)(ascale * fma(sx, ib2, (T)nv1[i]));
+          o2[i] = (float)(ascale * fma(sy, ib2, (T)nv2[i]));
+          o3[i] = (float)(ascale * fma(sz, ib2, (T)nv3[i]));
+        }
+        const long long row = ((long long)(B.z * 4 + k) * ny + (B.y * 4 + j)) * nx + (long long)B.x * 4;
+        *reinterpret_cast<float4*>(phi + row) = make_float4(o0[0], o0[1], o0[2], o0[3]);
+        *reinterpret_cast<float4*>(accel + row) = make_float4(o1[0], o1[1], o1[2], o1[3]);
+        *reinterpret_cast<float4*>(accel + ncell + row) = make_float4(o2[0], o2[1], o2[2], o2[3]);
+        *reinterpret_cast<float4*>(accel + 2 * ncell + row) = make_float4(o3[0], o3[1], o3[2], o3[3]);
+      }
+      continue;
+    }
     for (int j = 0; j < b; ++j) {
       const T yj = (T(j) + T(0.5)) * inv_b - T(0.5);
       T ypow[P + 1], dypow[P + 1];
