@@ -1039,6 +1039,15 @@ void fmm_default_opts(fmm_opts* o) {
 
 const char* fmm_last_error(void) { return g_last_error.c_str(); }
 
+// The side stream (CUDA-core M2L levels) gets the highest priority: its few
+// small blocks are then scheduled ahead of queued tensor-core blocks and
+// finish early instead of trickling through the whole far-field phase.
+static int side_priority() {
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return 0;
+  return greatest;
+}
+
 fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* opts, void* stream, fmm_plan_t* out) {
   g_last_error.clear();
   if (!out) return fail(FMM_ERR_ARG, "out is NULL");
@@ -1079,7 +1088,7 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
   if (!P) return fail(FMM_ERR_ALLOC, "host allocation failed");
   fmm_status st = plan_init(P, d3, grid->dx, grid->G, order, leaf, o, static_cast<cudaStream_t>(stream), dev);
   if (st == FMM_OK &&
-      (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
+      (cudaStreamCreateWithPriority(&P->side, cudaStreamNonBlocking, side_priority()) != cudaSuccess ||
        cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
        cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess))
     st = fail(FMM_ERR_CUDA, "stream or event creation failed");
