@@ -260,6 +260,19 @@ def reference_arm(args, rank):
 
 # -------------------------------------------------------------------- ours --
 
+def replica_aggregate(ms_local, units_per_step, steps, world, dist, device):
+    """Whole-job rate of N independent replicas: the slowest rank's time (MAX
+    over ranks) against the units all ranks processed.  Returns (ms_max, value
+    in units/s / 1e6)."""
+    import torch
+
+    t = torch.tensor([float(ms_local)], device=device, dtype=torch.float64)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, units_per_step * steps * world / (ms_max / 1e3) / 1e6
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -331,12 +344,8 @@ def main():
     plan.check()  # a device-side time-out or non-finite input voids the measurement
     plan.timing(False)
     clocks = clk.summary()
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     cells = n ** 3
-    value = cells * args.steps * world / (ms_max / 1e3) / 1e6
+    ms_max, value = replica_aggregate(ms, cells, args.steps, world, dist, "cuda")
 
     # ---- e2e through the C ABI with host buffers ----
     e2e = None
