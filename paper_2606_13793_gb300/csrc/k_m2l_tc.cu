@@ -17,19 +17,26 @@
 //   * D: FP32 accumulators in tensor memory, one column range per group.
 // Precisions: kind::tf32 on the FP32 rows (one product), or bf16 hi/lo planes
 // with three products hi*hi + hi*lo + lo*hi (kind::f16, BF16 inputs).
-// Roles (9 warps, lane 0 of each): warp 0 loads the activation boxes all
-// issuers read; the accumulators of a pass are shared out between four MMA
-// issuers (warps 5..8), which write disjoint tensor-memory columns; issuer q
-// has its own weight ring, filled by its own producer (warp 1 + q).  A single
-// issuing thread cannot keep the tensor pipe busy with the narrow low-order
-// spans; four can.  The activation loads have a thread of their own so that
-// a full weight ring never delays the next box.  The rings are byte-granular
-// (1 KB units), so small spans do not hold a slot sized for the largest.
-// Warps 0..7 drain tensor memory in the epilogue (warps w and w + 4 share
-// TMEM lanes and split the columns).  Every wait is bounded:
+// Roles (13 warps): lane 0 of warp 0 loads the activation boxes all issuers
+// read; the accumulators of a pass are shared out between four MMA issuers
+// (lane 0 of warps 5..8), which write disjoint tensor-memory columns; issuer
+// q has its own weight ring, filled by its own producer (lane 0 of warp
+// 1 + q).  A single issuing thread cannot keep the tensor pipe busy with the
+// narrow low-order spans; four can.  The activation loads have a thread of
+// their own so that a full weight ring never delays the next box.  The rings
+// are byte-granular (1 KB units), so small spans do not hold a slot sized for
+// the largest.  Warps 9..12 drain tensor memory (warp w reads TMEM lanes
+// 32 (w mod 4) ..).
+//
+// Persistent tiles: a CTA takes row tiles blockIdx.x, blockIdx.x + gridDim.x,
+// ... of pass blockIdx.y, so the rings keep streaming from one tile to the
+// next; when two accumulator sets fit in tensor memory the epilogue of a tile
+// overlaps the MMAs of the next (acc_full / acc_empty barriers per set).  Every wait is bounded:
 // on time-out the kernel sets the plan's error flag (FMM_ERR_TIMEOUT) and
 // unwinds; a CTA that sees the flag set by another gives up at once.
 #include <cuda.h>
+
+#include <algorithm>
 
 #include "fmm_internal.h"
 
@@ -38,9 +45,10 @@ namespace {
 
 constexpr int kAPlane = kTcAPlaneBytes;                  // 144 rows x 128 B, a multiple of 1024
 constexpr int kRingE = 16;                               // spans in flight per weight ring
-constexpr int kThreads = 32 * (1 + 2 * kTcIssuers);      // activation producer, ring producers, issuers
+constexpr int kEpiWarps = 4;                             // one per TMEM lane quarter
+constexpr int kThreads = 32 * (1 + 2 * kTcIssuers + kEpiWarps);  // producers, issuers, epilogue
 constexpr int kSmemBytes = kTcSmemUsable + 1024 /*alignment*/;
-static_assert((2 * kTcMaxAStages + 2 * kTcIssuers * kRingE + 1) * 8 + 4 <= 2048, "barrier region");
+static_assert((2 * kTcMaxAStages + 2 * kTcIssuers * kRingE + 4) * 8 + 4 <= 2048, "barrier region");
 static_assert(kSmemBytes <= 227 * 1024, "shared memory of the tensor-core kernel");
 static_assert(kAPlane % 1024 == 0, "activation planes keep the 1 KB swizzle alignment");
 constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s per wait
@@ -97,7 +105,7 @@ __device__ __forceinline__ bool wait_fast(uint64_t* bar, uint32_t parity, int* e
   return mbar_try_wait(bar, parity) || mbar_wait(bar, parity, err, site);
 }
 
-enum WaitSite { W_PROD_A = 0, W_PROD_B, W_MMA_A, W_MMA_B, W_EPI, W_DRAIN };
+enum WaitSite { W_PROD_A = 0, W_PROD_B, W_MMA_A, W_MMA_B, W_EPI, W_DRAIN, W_MMA_ACC };
 
 __device__ __forceinline__ void tma_load_4d(void* dst, const void* map, uint64_t* bar, int c0, int c1, int c2,
                                             int c3) {
@@ -140,6 +148,10 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -198,25 +210,29 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* b_rings = a_ring + nA * kAStage;
   uint64_t* a_empty = a_full + kTcMaxAStages;
   uint64_t* b_full = a_empty + kTcMaxAStages;  // [NQ][kRingE]
-  uint64_t* b_empty = b_full + NQ * kRingE;  // [NQ][kRingE]
-  uint64_t* accum = b_empty + NQ * kRingE;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* b_empty = b_full + NQ * kRingE;    // [NQ][kRingE]
+  uint64_t* acc_full = b_empty + NQ * kRingE;  // [2]
+  uint64_t* acc_empty = acc_full + 2;          // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
 
   const TcPass& pass = P.pass[blockIdx.y];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntx = (P.grid[0] + kTcTileX - 1) / kTcTileX, nty = (P.grid[1] + kTcTileY - 1) / kTcTileY;
-  const int ox = (blockIdx.x % ntx) * kTcTileX;
-  const int oy = ((blockIdx.x / ntx) % nty) * kTcTileY;
-  const int oz = (blockIdx.x / (ntx * nty)) * kTcTileZ;
+  const int ntiles = ntx * nty * ((P.grid[2] + kTcTileZ - 1) / kTcTileZ);
+  const uint32_t nbuf = 2 * pass.tmem_cols <= 512 ? 2u : 1u;  // accumulator sets
 
   {
-    // one barrier per thread: a_full, a_empty (every issuer releases a stage),
-    // the ring barriers, the accumulator barrier
-    constexpr int kBars = 2 * kTcMaxAStages + 2 * NQ * kRingE + 1;
+    // one barrier per thread: a_full, a_empty (every issuer releases a
+    // stage), the ring barriers, acc_full (every issuer commits) and
+    // acc_empty (every epilogue warp releases)
+    constexpr int kBars = 2 * kTcMaxAStages + 2 * NQ * kRingE + 4;
     static_assert(kBars <= kThreads, "barrier initialisation");
     const int i = threadIdx.x;
     if (i < kBars) {
-      const uint32_t count = (i >= kTcMaxAStages && i < 2 * kTcMaxAStages) || i == kBars - 1 ? NQ : 1;
+      uint32_t count = 1;
+      if (i >= kTcMaxAStages && i < 2 * kTcMaxAStages) count = NQ;      // a_empty
+      if (i == kBars - 4 || i == kBars - 3) count = NQ;                 // acc_full
+      if (i == kBars - 2 || i == kBars - 1) count = kEpiWarps;          // acc_empty
       mbar_init(a_full + i, count);  // the barriers are contiguous from a_full on
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -224,30 +240,36 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     __syncwarp();  // tcgen05.alloc is warp-collective: reconverge after thread 0's block
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"((uint32_t)pass.tmem_cols));
+                 "r"((uint32_t)pass.tmem_cols * nbuf));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const unsigned char* wpass = P.W + pass.w_base;
 
   if (warp == 0 && lane == 0) {
     // ---------------- activation producer ----------------
-    // One box per (neighbour column (dx, dz), chunk j): rows y-1 .. y+16 of
-    // the shifted x/z column, which serve the three dy neighbours.
+    // One box per (tile, neighbour column (dx, dz), chunk j): rows y-1 .. y+16
+    // of the shifted x/z column, which serve the three dy neighbours.
     uint32_t ai = 0;
     bool ok = !(*reinterpret_cast<volatile int*>(P.err) & 2);
-    for (int xz = 0; ok && xz < 9; ++xz) {
-      const int dx = xz % 3 - 1, dz = xz / 3 - 1;
-      for (int j = 0; ok && j < pass.nchunks; ++j) {
-        const uint32_t sa = ai % nA;
-        if (!(ok = wait_fast(&a_empty[sa], ((ai / nA) & 1) ^ 1, P.err, W_PROD_A))) break;
-        unsigned char* adst = a_ring + sa * kAStage;
-        mbar_expect_tx(&a_full[sa], split ? 2 * kAPlane : kAPlane);
-        tma_load_4d(adst, &map_hi, &a_full[sa], j * chunk_elems, ox + dx, oy - 1, oz + dz);
-        if (split) tma_load_4d(adst + kAPlane, &map_lo, &a_full[sa], j * chunk_elems, ox + dx, oy - 1, oz + dz);
-        ++ai;
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+      const int ox = (tile % ntx) * kTcTileX, oy = ((tile / ntx) % nty) * kTcTileY;
+      const int oz = (tile / (ntx * nty)) * kTcTileZ;
+      for (int xz = 0; ok && xz < 9; ++xz) {
+        const int dx = xz % 3 - 1, dz = xz / 3 - 1;
+        for (int j = 0; ok && j < pass.nchunks; ++j) {
+          const uint32_t sa = ai % nA;
+          if (!(ok = wait_fast(&a_empty[sa], ((ai / nA) & 1) ^ 1, P.err, W_PROD_A))) break;
+          unsigned char* adst = a_ring + sa * kAStage;
+          mbar_expect_tx(&a_full[sa], split ? 2 * kAPlane : kAPlane);
+          tma_load_4d(adst, &map_hi, &a_full[sa], j * chunk_elems, ox + dx, oy - 1, oz + dz);
+          if (split)
+            tma_load_4d(adst + kAPlane, &map_lo, &a_full[sa], j * chunk_elems, ox + dx, oy - 1, oz + dz);
+          ++ai;
+        }
       }
     }
     if (!ok)  // drain: never leave the CTA with copies in flight
@@ -255,8 +277,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_wait(&a_full[i % nA], (i / nA) & 1, P.err, W_DRAIN);
   } else if (warp >= 1 && warp <= NQ && lane == 0) {
     // ---------------- weight producers ----------------
-    // Ring q = warp - 1, in the order its issuer consumes: neighbour column
-    // (dx, dz), chunk j, then dy and the issuer's spans of the chunk.
+    // Ring q = warp - 1, in the order its issuer consumes: tile, neighbour
+    // column (dx, dz), chunk j, then dy and the issuer's spans of the chunk.
     const int q = warp - 1;
     const uint32_t RB = (uint32_t)pass.ring_bytes[q];
     uint32_t rbase = 0;
@@ -272,37 +294,38 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t end_v[kRingE];
     uint32_t e = 0, tail = 0, v = 0, off = 0, freed = 0, last = 0;
     bool ok = !(*reinterpret_cast<volatile int*>(P.err) & 2);
-    const unsigned char* wpass = P.W + pass.w_base;
-    for (int xz = 0; ok && xz < 9; ++xz) {
-      const int dx = xz % 3 - 1, dz = xz / 3 - 1;
-      for (int j = 0; ok && j < pass.nchunks; ++j) {
-        const int s0 = pass.span_idx[j][q], s1 = pass.span_idx[j][q + 1];
-        for (int dy = 0; ok && dy < 3; ++dy) {
-          const unsigned char* wd = wpass + (long long)((dx + 1) + 3 * dy + 9 * (dz + 1)) * pass.bytes_per_d;
-          for (int si = s0; si < s1; ++si) {
-            const uint32_t bytes = (uint32_t)pass.span[si].n * 128u * planes;
-            if (off + bytes > RB) v += RB - off, off = 0;  // a span never wraps
-            const uint32_t need = v + bytes > RB ? min(last, v + bytes - RB) : 0u;
-            while (freed < need || e - tail >= (uint32_t)kRingE) {  // release the oldest span
-              if (!(ok = wait_fast(&empty[tail % kRingE], (tail / kRingE) & 1, P.err, W_PROD_B))) break;
-              freed = end_v[tail % kRingE];
-              ++tail;
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+      for (int xz = 0; ok && xz < 9; ++xz) {
+        const int dx = xz % 3 - 1, dz = xz / 3 - 1;
+        for (int j = 0; ok && j < pass.nchunks; ++j) {
+          const int s0 = pass.span_idx[j][q], s1 = pass.span_idx[j][q + 1];
+          for (int dy = 0; ok && dy < 3; ++dy) {
+            const unsigned char* wd = wpass + (long long)((dx + 1) + 3 * dy + 9 * (dz + 1)) * pass.bytes_per_d;
+            for (int si = s0; si < s1; ++si) {
+              const uint32_t bytes = (uint32_t)pass.span[si].n * 128u * planes;
+              if (off + bytes > RB) v += RB - off, off = 0;  // a span never wraps
+              const uint32_t need = v + bytes > RB ? min(last, v + bytes - RB) : 0u;
+              while (freed < need || e - tail >= (uint32_t)kRingE) {  // release the oldest span
+                if (!(ok = wait_fast(&empty[tail % kRingE], (tail / kRingE) & 1, P.err, W_PROD_B))) break;
+                freed = end_v[tail % kRingE];
+                ++tail;
+              }
+              if (!ok) break;
+              mbar_expect_tx(&full[e % kRingE], bytes);
+              bulk_load(ring + off, wd + pass.span[si].w_off, bytes, &full[e % kRingE]);
+              end_v[e % kRingE] = v + bytes;
+              v += bytes;
+              last = v;
+              off += bytes;
+              ++e;
             }
-            if (!ok) break;
-            mbar_expect_tx(&full[e % kRingE], bytes);
-            bulk_load(ring + off, wd + pass.span[si].w_off, bytes, &full[e % kRingE]);
-            end_v[e % kRingE] = v + bytes;
-            v += bytes;
-            last = v;
-            off += bytes;
-            ++e;
           }
         }
       }
     }
     if (!ok)  // drain: never leave the CTA with copies in flight
       for (uint32_t i = tail; i < e; ++i) mbar_wait(&full[i % kRingE], (i / kRingE) & 1, P.err, W_DRAIN);
-  } else if (warp > NQ && lane == 0) {
+  } else if (warp > NQ && warp <= 2 * NQ && lane == 0) {
     // ---------------- MMA issuers ----------------
     const int q = warp - 1 - NQ;
     const uint32_t RB = (uint32_t)pass.ring_bytes[q];
@@ -311,96 +334,110 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint64_t ring_desc = sw128_desc(smem_u32(b_rings + rbase));
     uint64_t* full = b_full + q * kRingE;
     uint64_t* empty = b_empty + q * kRingE;
-    uint32_t ai = 0, e = 0, off = 0;
+    uint32_t ai = 0, e = 0, off = 0, it = 0;
     bool ok = !(*reinterpret_cast<volatile int*>(P.err) & 2);
-    for (int xz = 0; ok && xz < 9; ++xz) {
-      for (int j = 0; ok && j < pass.nchunks; ++j) {
-        const int sa = ai % nA;
-        if (!(ok = wait_fast(&a_full[sa], (ai / nA) & 1, P.err, W_MMA_A))) break;
-        tc_fence_after();
-        const uint64_t a_desc = sw128_desc(smem_u32(a_ring + sa * kAStage));
-        const int s0 = pass.span_idx[j][q], s1 = pass.span_idx[j][q + 1];
-        for (int dy = 0; ok && dy < 3; ++dy) {
-          const uint64_t a = a_desc + (uint64_t)(dy * (kTcTileX * 128 / 16));  // 128-row window
-          const uint64_t a_lo = a + (uint64_t)(kAPlane / 16);
-          for (int si = s0; si < s1; ++si) {
-            const TcSpan& S = pass.span[si];
-            const uint32_t plane = (uint32_t)S.n * 128u;
-            if (off + plane * planes > RB) off = 0;
-            if (!(ok = wait_fast(&full[e % kRingE], (e / kRingE) & 1, P.err, W_MMA_B))) break;
-            tc_fence_after();
-            const uint64_t b = ring_desc + (uint64_t)(off >> 4);
-            const uint64_t b_lo = b + (uint64_t)(plane >> 4);
-            const uint32_t d = tmem + (uint32_t)S.tmem_col;
-            const uint32_t acc0 = (xz == 0 && dy == 0 && j == S.first) ? 0u : 1u;  // the first step opens
-            switch (S.ksteps) {
-              case 1: issue_span<KIND, 1>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
-              case 2: issue_span<KIND, 2>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
-              case 3: issue_span<KIND, 3>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
-              default: issue_span<KIND, 4>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++it) {
+      const uint32_t buf = it % nbuf, use = it / nbuf;
+      // this accumulator set must have been drained by the epilogue
+      if (!(ok = wait_fast(&acc_empty[buf], (use & 1) ^ 1, P.err, W_MMA_ACC))) break;
+      tc_fence_after();
+      const uint32_t tbase = tmem + buf * (uint32_t)pass.tmem_cols;
+      for (int xz = 0; ok && xz < 9; ++xz) {
+        for (int j = 0; ok && j < pass.nchunks; ++j) {
+          const uint32_t sa = ai % nA;
+          if (!(ok = wait_fast(&a_full[sa], (ai / nA) & 1, P.err, W_MMA_A))) break;
+          tc_fence_after();
+          const uint64_t a_desc = sw128_desc(smem_u32(a_ring + sa * kAStage));
+          const int s0 = pass.span_idx[j][q], s1 = pass.span_idx[j][q + 1];
+          for (int dy = 0; ok && dy < 3; ++dy) {
+            const uint64_t a = a_desc + (uint64_t)(dy * (kTcTileX * 128 / 16));  // 128-row window
+            const uint64_t a_lo = a + (uint64_t)(kAPlane / 16);
+            for (int si = s0; si < s1; ++si) {
+              const TcSpan& S = pass.span[si];
+              const uint32_t plane = (uint32_t)S.n * 128u;
+              if (off + plane * planes > RB) off = 0;
+              if (!(ok = wait_fast(&full[e % kRingE], (e / kRingE) & 1, P.err, W_MMA_B))) break;
+              tc_fence_after();
+              const uint64_t b = ring_desc + (uint64_t)(off >> 4);
+              const uint64_t b_lo = b + (uint64_t)(plane >> 4);
+              const uint32_t d = tbase + (uint32_t)S.tmem_col;
+              const uint32_t acc0 = (xz == 0 && dy == 0 && j == S.first) ? 0u : 1u;  // the first step opens
+              switch (S.ksteps) {
+                case 1: issue_span<KIND, 1>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
+                case 2: issue_span<KIND, 2>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
+                case 3: issue_span<KIND, 3>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
+                default: issue_span<KIND, 4>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
+              }
+              mma_commit(&empty[e % kRingE]);
+              off += plane * planes;
+              ++e;
             }
-            mma_commit(&empty[e % kRingE]);
-            off += plane * planes;
-            ++e;
+          }
+          mma_commit(&a_empty[sa]);
+          ++ai;
+        }
+      }
+      mma_commit(&acc_full[buf]);  // fires when every MMA of this tile has completed
+    }
+  } else if (warp > 2 * NQ) {
+    // ---------------- epilogue: TMEM -> registers -> C ----------------
+    const int wq = warp & 3;
+    const int r = wq * 32 + lane;  // tile row = TMEM lane
+    const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
+    uint32_t it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      const uint32_t buf = it % nbuf, use = it / nbuf;
+      int done = 0;
+      if (lane == 0) done = mbar_wait(&acc_full[buf], use & 1, P.err, W_EPI) ? 1 : 0;
+      done = __shfl_sync(0xffffffffu, done, 0);  // warp-uniform: tcgen05.ld is warp-collective
+      if (!done) break;
+      tc_fence_after();
+      const int ox = (tile % ntx) * kTcTileX, oy = ((tile / ntx) % nty) * kTcTileY;
+      const int oz = (tile / (ntx * nty)) * kTcTileZ;
+      const int x = ox + (r & 7), y = oy + (r >> 3), z = oz;
+      const bool valid = x < P.grid[0] && y < P.grid[1] && z < P.grid[2];
+      float* crow = P.C + ((((long long)z * P.grid[1] + y) * P.grid[0] + x) * P.n_cols);
+      const uint32_t tbase = tmem + buf * (uint32_t)pass.tmem_cols;
+      for (int g = 0; g < pass.ng; ++g) {
+        const int n_mma = pass.out_nmma[g], ncols = pass.out_ncols[g], col0 = pass.out_col0[g];
+        const int t2 = pass.out_tmem2[g];
+        for (int c = 0; c < n_mma; c += 16) {
+          float vv[16];
+          __syncwarp();  // tcgen05.ld is warp-collective: reconverge after the masked stores
+          tmem_ld16(tbase + lane_base + (uint32_t)(pass.out_tmem[g] + c), vv);
+          if (t2 >= 0) {  // reduction-split group: first + second accumulator
+            float w2[16];
+            tmem_ld16(tbase + lane_base + (uint32_t)(t2 + c), w2);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) vv[i] += w2[i];
+          }
+          if (valid) {  // out_col0 and out_ncols are multiples of 8: whole float4s
+#pragma unroll
+            for (int jj = 0; jj < 16; jj += 4)
+              if (c + jj < ncols) {
+                float4* o = reinterpret_cast<float4*>(crow + col0 + c + jj);
+                float4 q4 = make_float4(vv[jj], vv[jj + 1], vv[jj + 2], vv[jj + 3]);
+                if (P.accumulate) {
+                  const float4 old = *o;
+                  q4.x += old.x, q4.y += old.y, q4.z += old.z, q4.w += old.w;
+                }
+                *o = q4;
+              }
           }
         }
-        mma_commit(&a_empty[sa]);
-        ++ai;
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);  // this warp's reads of the set are done
     }
-    mma_commit(accum);  // fires when every MMA this thread issued has completed
   }
   __syncwarp();
-
-  // ---------------- epilogue: TMEM -> registers -> C ----------------
-  // Warp w reads TMEM lanes 32 (w mod 4) ..; warps w and w + 4 take
-  // alternate 16-column blocks.  A reduction-split group adds its second
-  // accumulator (fixed order: first + second).
-  int done = 0;
-  if (lane == 0 && warp < 8) done = mbar_wait(accum, 0, P.err, W_EPI) ? 1 : 0;
-  done = __shfl_sync(0xffffffffu, done, 0);  // warp-uniform: tcgen05.ld is warp-collective
-  if (done) {
-    tc_fence_after();
-    const int wq = warp & 3, half = warp >> 2;
-    const int r = wq * 32 + lane;  // tile row = TMEM lane
-    const int x = ox + (r & 7), y = oy + (r >> 3), z = oz;
-    const bool valid = x < P.grid[0] && y < P.grid[1] && z < P.grid[2];
-    float* crow = P.C + ((((long long)z * P.grid[1] + y) * P.grid[0] + x) * P.n_cols);
-    const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
-    for (int g = 0; g < pass.ng; ++g) {
-      const int n_mma = pass.out_nmma[g], ncols = pass.out_ncols[g], col0 = pass.out_col0[g];
-      const int t2 = pass.out_tmem2[g];
-      for (int c = half * 16; c < n_mma; c += 32) {
-        float v[16];
-        __syncwarp();  // tcgen05.ld is warp-collective: reconverge after the masked stores
-        tmem_ld16(tmem + lane_base + (uint32_t)(pass.out_tmem[g] + c), v);
-        if (t2 >= 0) {
-          float w2[16];
-          tmem_ld16(tmem + lane_base + (uint32_t)(t2 + c), w2);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] += w2[i];
-        }
-        if (valid) {  // out_col0 and out_ncols are multiples of 8: whole float4s
-#pragma unroll
-          for (int j = 0; j < 16; j += 4)
-            if (c + j < ncols) {
-              float4* o = reinterpret_cast<float4*>(crow + col0 + c + j);
-              float4 q = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-              if (P.accumulate) {
-                const float4 old = *o;
-                q.x += old.x, q.y += old.y, q.z += old.z, q.w += old.w;
-              }
-              *o = q;
-            }
-        }
-      }
-    }
-  }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)pass.tmem_cols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)pass.tmem_cols * nbuf));
   }
 }
 
@@ -443,7 +480,15 @@ cudaError_t launch_m2l_tc(const TcLaunch& L, const void* map_hi, const void* map
   }
   const int ntx = (L.grid[0] + kTcTileX - 1) / kTcTileX, nty = (L.grid[1] + kTcTileY - 1) / kTcTileY,
             ntz = (L.grid[2] + kTcTileZ - 1) / kTcTileZ;
-  dim3 grid((unsigned)(ntx * nty * ntz), (unsigned)L.npass);
+  const int tiles = ntx * nty * ntz;
+  // single-pass launches run persistent CTAs (one per SM, shared memory allows
+  // no more); with several passes each CTA takes one tile, so that the light
+  // passes do not leave SMs idle while the heavy pass finishes
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 148;
+  const int ctas = L.npass == 1 ? std::min(tiles, sms) : tiles;
+  dim3 grid((unsigned)ctas, (unsigned)L.npass);
   if (L.kind == TC_BF16X3)
     m2l_tc_kernel<TC_BF16X3><<<grid, kThreads, kSmemBytes, s>>>(*reinterpret_cast<const CUtensorMap*>(map_hi),
                                                            *reinterpret_cast<const CUtensorMap*>(map_lo), L);
