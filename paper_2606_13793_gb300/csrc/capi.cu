@@ -434,6 +434,9 @@ uint32_t host_idesc(int kind, int n) {
 // issuing threads (heaviest first, to the least-loaded issuer), and a group
 // whose MMA steps exceed an even share is split along the reduction at a chunk
 // boundary into two accumulators, which the epilogue adds in a fixed order.
+// A bf16x3 pass with a single group (the near field) is split by product
+// instead: hi*hi, hi*lo and lo*hi go to three issuers with their own
+// accumulators and one weight plane each.
 template <typename Entry>
 bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entry, TcHost& H, int a_stages) {
   const int ring_budget = tc_ring_budget(kind, a_stages);
@@ -448,10 +451,11 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
     return std::min(4, (k1 - j * chunk + kstep - 1) / kstep);
   };
   struct VGroup {
-    int out;     // output group
-    int k0, k1;  // reduction range
-    int nm;      // TMEM columns
-    int q = 0;   // issuer
+    int out;       // output group
+    int k0, k1;    // reduction range
+    int nm;        // TMEM columns
+    int prod = 0;  // TcSpan::prod
+    int q = 0;     // issuer
     int tmem = 0;
   };
   auto vsteps = [&](const VGroup& v) {
@@ -477,17 +481,30 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
       P.out_ncols[P.ng] = gs[gi].ncols;
       P.out_nmma[P.ng] = nm;
       P.out_tmem2[P.ng] = -1;
+      P.out_tmem3[P.ng] = -1;
       V.push_back({P.ng, 0, gs[gi].K, nm});
       cols += nm;
       ++P.ng;
       ++gi;
     }
     if (P.ng == 0) return false;
+    // a single bf16x3 group: one accumulator per product
+    const bool prod_split = kind == TC_BF16X3 && V.size() == 1 && 3 * cols <= 512;
+    if (prod_split) {
+      V[0].prod = 1;
+      VGroup v2 = V[0], v3 = V[0];
+      v2.prod = 2;
+      v3.prod = 3;
+      V.push_back(v2);
+      V.push_back(v3);
+      cols *= 3;
+      P.out_tmem2[0] = P.out_tmem3[0] = 0;  // marked; placed below
+    }
     // split the heaviest accumulators along the reduction while one exceeds an even share
     int total = 0;
     for (const VGroup& v : V) total += vsteps(v);
     const int share = (total + kTcIssuers - 1) / kTcIssuers;
-    for (bool again = true; again;) {
+    for (bool again = !prod_split; again;) {
       again = false;
       int h = -1;
       for (int i = 0; i < (int)V.size(); ++i)
@@ -538,7 +555,9 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
         v.tmem = c;
         c += v.nm;
         kmax = std::max(kmax, v.k1);
-        if (v.k0 == 0)
+        if (v.prod >= 2)
+          (v.prod == 2 ? P.out_tmem2 : P.out_tmem3)[v.out] = v.tmem;
+        else if (v.k0 == 0)
           P.out_tmem[v.out] = v.tmem;
         else
           P.out_tmem2[v.out] = v.tmem;
@@ -571,10 +590,12 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
           S.n = 0;
           S.ksteps = ks;
           S.first = V[i].k0 / chunk;
+          S.prod = V[i].prod;
           std::vector<int> members;
           const int k0 = V[i].k0;
-          while (i < V.size() && V[i].q == q && V[i].k0 == k0 && ksteps_in(V[i].k0, V[i].k1, j) == ks &&
-                 V[i].tmem == S.tmem_col + S.n && S.n + V[i].nm <= kTcMaxSpanN) {
+          while (i < V.size() && V[i].q == q && V[i].k0 == k0 && V[i].prod == S.prod &&
+                 ksteps_in(V[i].k0, V[i].k1, j) == ks && V[i].tmem == S.tmem_col + S.n &&
+                 S.n + V[i].nm <= kTcMaxSpanN) {
             S.n += V[i].nm;
             members.push_back((int)i);
             ++i;
@@ -582,7 +603,7 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
           if (members.empty()) return false;
           S.w_off = off;
           S.idesc = host_idesc(kind, S.n);
-          const int bytes = S.n * 128 * planes;
+          const int bytes = S.n * 128 * (S.prod ? 1 : planes);
           off += bytes;
           vol[q] += bytes;
           biggest[q] = std::max(biggest[q], bytes);
@@ -635,8 +656,12 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
                 if (kind == TC_BF16X3) {
                   const uint16_t h = bf16_rn((float)w);
                   const uint16_t l = bf16_rn((float)(w - (double)bf16_to_f(h)));
-                  std::memcpy(tile + o, &h, 2);
-                  std::memcpy(tile + (size_t)S.n * 128 + o, &l, 2);
+                  if (S.prod == 0) {
+                    std::memcpy(tile + o, &h, 2);
+                    std::memcpy(tile + (size_t)S.n * 128 + o, &l, 2);
+                  } else {  // the one plane this product multiplies
+                    std::memcpy(tile + o, S.prod == 2 ? &l : &h, 2);
+                  }
                 } else {
                   const float t = tf32_rn(w);
                   std::memcpy(tile + o, &t, 4);

@@ -184,6 +184,8 @@ struct TcSpan {
   int w_off;       // byte offset of the tile inside the neighbour block
   uint32_t idesc;  // instruction descriptor (kind, N, M = 128)
   int first;       // chunk in which the span's accumulators open (first MMA overwrites)
+  int prod;        // bf16x3 products: 0 all three (hi and lo weight planes in the tile);
+                   // 1 A_hi x B (B = hi plane), 2 A_hi x B (B = lo plane), 3 A_lo x B (B = hi plane)
 };
 
 // One pass of the schedule, passed by value (kernel parameter space), so the
@@ -194,7 +196,8 @@ struct TcPass {
   int ng, nchunks, tmem_cols, bytes_per_d;
   long long w_base;
   int out_tmem[kTcMaxGroups];   // epilogue: TMEM column of the group's accumulator
-  int out_tmem2[kTcMaxGroups];  // second accumulator of a reduction-split group, or -1
+  int out_tmem2[kTcMaxGroups];  // second accumulator (reduction- or product-split group), or -1
+  int out_tmem3[kTcMaxGroups];  // third accumulator (product-split group), or -1
   int out_col0[kTcMaxGroups];   // first output column (beta*8 + child)
   int out_ncols[kTcMaxGroups];  // real output columns
   int out_nmma[kTcMaxGroups];   // TMEM columns of the group (multiple of 16)

@@ -192,6 +192,13 @@ __device__ __forceinline__ void issue_span(uint32_t d, uint64_t a, uint64_t a_lo
   }
 }
 
+// One product per K step (a product-split span): A (hi or lo plane) x B.
+template <int KS>
+__device__ __forceinline__ void issue_span1(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc0) {
+#pragma unroll
+  for (int k = 0; k < KS; ++k) mma_f16(d, a + 2ull * k, b + 2ull * k, idesc, k == 0 ? acc0 : 1u);
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
     m2l_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
@@ -302,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int dy = 0; ok && dy < 3; ++dy) {
             const unsigned char* wd = wpass + (long long)((dx + 1) + 3 * dy + 9 * (dz + 1)) * pass.bytes_per_d;
             for (int si = s0; si < s1; ++si) {
-              const uint32_t bytes = (uint32_t)pass.span[si].n * 128u * planes;
+              const uint32_t bytes = (uint32_t)pass.span[si].n * 128u * (pass.span[si].prod ? 1u : planes);
               if (off + bytes > RB) v += RB - off, off = 0;  // a span never wraps
               const uint32_t need = v + bytes > RB ? min(last, v + bytes - RB) : 0u;
               while (freed < need || e - tail >= (uint32_t)kRingE) {  // release the oldest span
@@ -355,21 +362,32 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int si = s0; si < s1; ++si) {
               const TcSpan& S = pass.span[si];
               const uint32_t plane = (uint32_t)S.n * 128u;
-              if (off + plane * planes > RB) off = 0;
+              const uint32_t bytes = plane * (S.prod ? 1u : planes);
+              if (off + bytes > RB) off = 0;
               if (!(ok = wait_fast(&full[e % kRingE], (e / kRingE) & 1, P.err, W_MMA_B))) break;
               tc_fence_after();
               const uint64_t b = ring_desc + (uint64_t)(off >> 4);
               const uint64_t b_lo = b + (uint64_t)(plane >> 4);
               const uint32_t d = tbase + (uint32_t)S.tmem_col;
               const uint32_t acc0 = (xz == 0 && dy == 0 && j == S.first) ? 0u : 1u;  // the first step opens
-              switch (S.ksteps) {
-                case 1: issue_span<KIND, 1>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
-                case 2: issue_span<KIND, 2>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
-                case 3: issue_span<KIND, 3>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
-                default: issue_span<KIND, 4>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
+              if (KIND == TC_BF16X3 && S.prod) {
+                const uint64_t as = S.prod == 3 ? a_lo : a;
+                switch (S.ksteps) {
+                  case 1: issue_span1<1>(d, as, b, S.idesc, acc0); break;
+                  case 2: issue_span1<2>(d, as, b, S.idesc, acc0); break;
+                  case 3: issue_span1<3>(d, as, b, S.idesc, acc0); break;
+                  default: issue_span1<4>(d, as, b, S.idesc, acc0); break;
+                }
+              } else {
+                switch (S.ksteps) {
+                  case 1: issue_span<KIND, 1>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
+                  case 2: issue_span<KIND, 2>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
+                  case 3: issue_span<KIND, 3>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
+                  default: issue_span<KIND, 4>(d, a, a_lo, b, b_lo, S.idesc, acc0); break;
+                }
               }
               mma_commit(&empty[e % kRingE]);
-              off += plane * planes;
+              off += bytes;
               ++e;
             }
           }
@@ -400,16 +418,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t tbase = tmem + buf * (uint32_t)pass.tmem_cols;
       for (int g = 0; g < pass.ng; ++g) {
         const int n_mma = pass.out_nmma[g], ncols = pass.out_ncols[g], col0 = pass.out_col0[g];
-        const int t2 = pass.out_tmem2[g];
+        const int t2 = pass.out_tmem2[g], t3 = pass.out_tmem3[g];
         for (int c = 0; c < n_mma; c += 16) {
           float vv[16];
           __syncwarp();  // tcgen05.ld is warp-collective: reconverge after the masked stores
           tmem_ld16(tbase + lane_base + (uint32_t)(pass.out_tmem[g] + c), vv);
-          if (t2 >= 0) {  // reduction-split group: first + second accumulator
+          if (t2 >= 0) {  // split group: accumulators added in a fixed order
             float w2[16];
             tmem_ld16(tbase + lane_base + (uint32_t)(t2 + c), w2);
 #pragma unroll
             for (int i = 0; i < 16; ++i) vv[i] += w2[i];
+          }
+          if (t3 >= 0) {
+            float w3[16];
+            tmem_ld16(tbase + lane_base + (uint32_t)(t3 + c), w3);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) vv[i] += w3[i];
           }
           if (valid) {  // out_col0 and out_ncols are multiples of 8: whole float4s
 #pragma unroll
