@@ -89,6 +89,7 @@ def _bind(lib):
         "oracle_fmm_accel": (I, [DP, I, I, I, I, I, D, D, DP, I]),
         "oracle_direct_accel": (I, [DP, I, I, I, D, D, DP, I]),
         "oracle_fmm_sample_accel": (I, [DP, I, I, I, I, I, D, D, L, LP, DP, I]),
+        "oracle_fmm_m2p": (I, [DP, I, I, I, I, I, D, D, DP, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -244,6 +245,16 @@ class Oracle:
         if self.lib.oracle_fmm_accel(_dp(rho), nx, ny, nz, b, p, dx, G, _dp(acc), threads) != 0:
             raise ValueError("oracle_fmm_accel rejected its arguments")
         return acc
+
+    def fmm_m2p(self, rho, b: int, p: int, dx: float = 1.0, G: float = 1.0, threads: int = 0) -> np.ndarray:
+        """Potential with the paper's final stage: M2P at the cell centres for the
+        leaf interaction list (instead of M2L + L2P at the leaf level)."""
+        rho = _f64(rho)
+        nz, ny, nx = rho.shape
+        phi = np.zeros_like(rho)
+        if self.lib.oracle_fmm_m2p(_dp(rho), nx, ny, nz, b, p, dx, G, _dp(phi), threads) != 0:
+            raise ValueError("oracle_fmm_m2p rejected its arguments")
+        return phi
 
     def direct_accel(self, rho, dx: float = 1.0, G: float = 1.0, threads: int = 0) -> np.ndarray:
         """O(N^2) pair forces [3][nz][ny][nx]."""

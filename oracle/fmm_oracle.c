@@ -229,6 +229,27 @@ static void or_m2l(const or_index* ix, const double* M, const double R[3], doubl
   }
 }
 
+/* M2P, the paper's final-stage evaluation (Sec. 4): the potential of the
+ * multipoles M about a source centre at a point R = x - c_source, i.e. eq. M2L
+ * with beta = 0 evaluated at the point itself:
+ *   phi(x) = sum_alpha (-1)^|alpha| / alpha! D_alpha(R) M_alpha. */
+static double or_m2p(const or_index* ix, const double* M, const double R[3]) {
+  double D[1000];
+  or_dtensor_ix(ix, R, ix->p, D);
+  double s = 0.0;
+  for (int ka = 0; ka < ix->nc; ++ka) {
+    const int* a = ix->mi[ka];
+    const int na = a[0] + a[1] + a[2];
+    const double afact = or_fact(a[0]) * or_fact(a[1]) * or_fact(a[2]);
+#if ORACLE_MUTANT == 7 /* planted mistake: M2P without the (-1)^|alpha| factor */
+    s += 1.0 / afact * D[ka] * M[ka];
+#else
+    s += ((na & 1) ? -1.0 : 1.0) / afact * D[ka] * M[ka];
+#endif
+  }
+  return s;
+}
+
 /* L2L, Sec. 2.3 eq. L2L, a = c_child - c_parent:
  *   L_beta(child) += sum_{gamma >= beta} a^(gamma-beta)/(gamma-beta)! L_gamma(parent). */
 static void or_l2l(const or_index* ix, const double* Lp, const double a[3], double* Lc) {
@@ -567,7 +588,9 @@ int oracle_upward_origin(const double* rho, int nx, int ny, int nz, int b, int p
 /* Downward pass and leaf evaluation (Sec. 2.3).                            */
 /* ------------------------------------------------------------------------ */
 
-static double** or_downward(const or_hier* H, const or_index* ix, double** M) {
+/* Downward pass; with leaf_m2l = 0 the leaf level gets only its parent's
+ * local expansion (the final-stage M2P evaluates the leaf interaction list). */
+static double** or_downward_ex(const or_hier* H, const or_index* ix, double** M, int leaf_m2l) {
   const int nc = ix->nc;
   double** L = (double**)calloc(H->L + 1, sizeof(double*));
   for (int l = 0; l <= H->L; ++l) L[l] = (double*)calloc((size_t)H->lev[l].nbox * nc, sizeof(double));
@@ -587,6 +610,7 @@ static double** or_downward(const or_hier* H, const or_index* ix, double** M) {
       double a[3] = {ct[0] - cp[0], ct[1] - cp[1], ct[2] - cp[2]};
       or_l2l(ix, L[l - 1] + or_bidx(pl, i / 2, j / 2, k / 2) * nc, a, Lt);
       /* intermediate field: M2L over the interaction list (eq. M2L) */
+      if (l == H->L && !leaf_m2l) continue;
       int il[216][3];
       int n = or_ilist(H, l, i, j, k, il);
       for (int s = 0; s < n; ++s) {
@@ -598,6 +622,10 @@ static double** or_downward(const or_hier* H, const or_index* ix, double** M) {
     }
   }
   return L;
+}
+
+static double** or_downward(const or_hier* H, const or_index* ix, double** M) {
+  return or_downward_ex(H, ix, M, 1);
 }
 
 /* Near field of one cell: all cells of the leaf boxes at Chebyshev distance
@@ -1161,6 +1189,48 @@ int oracle_fmm_sample_accel(const double* rho, int nx, int ny, int nz, int b, in
     for (int q = 0; q < 3; ++q) accel_out[3 * s + q] = scale * (gf[q] + gn[q]);
   }
   or_free_levels(&H, M);
+  free(ix);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The paper's own final stage (Sec. 4): at the leaf level the interaction  */
+/* list is evaluated by M2P at the cell centres instead of M2L + L2P:       */
+/*   phi(x) = L2P(L2L(L_parent)) + sum_{S in IL(B)} M2P(M_S, x - c_S)      */
+/*            + near(x)                                                     */
+/* ------------------------------------------------------------------------ */
+
+int oracle_fmm_m2p(const double* rho, int nx, int ny, int nz, int b, int p, double dx, double G, double* phi,
+                   int nthreads) {
+  or_hier H;
+  if (or_hier_init(&H, nx, ny, nz, b, p)) return -1;
+  or_set_threads(nthreads);
+  or_index* ix = (or_index*)malloc(sizeof(or_index));
+  or_index_init(ix, p);
+  double** M = or_upward(&H, ix, rho);
+  double** L = or_downward_ex(&H, ix, M, 0);
+  const long n = (long)nx * ny * nz;
+  const double scale = G * dx * dx;
+  const or_level* lf = &H.lev[H.L];
+#pragma omp parallel for schedule(dynamic, 64)
+  for (long c = 0; c < n; ++c) {
+    int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long)nx * ny));
+    double s = or_far_cell(&H, ix, L, x, y, z);
+    if (H.L >= 2) {
+      int il[216][3];
+      int m = or_ilist(&H, H.L, x / b, y / b, z / b, il);
+      for (int q = 0; q < m; ++q) {
+        double cs[3];
+        or_bcentre(lf, il[q][0], il[q][1], il[q][2], cs);
+        double R[3] = {x + 0.5 - cs[0], y + 0.5 - cs[1], z + 0.5 - cs[2]};
+        s += or_m2p(ix, M[H.L] + or_bidx(lf, il[q][0], il[q][1], il[q][2]) * ix->nc, R);
+      }
+    }
+    s += or_near_cell(&H, rho, x, y, z);
+    phi[c] = scale * s;
+  }
+  or_free_levels(&H, M);
+  or_free_levels(&H, L);
   free(ix);
   return 0;
 }

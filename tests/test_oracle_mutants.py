@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 import test_oracle_accel as accel
+import test_oracle_m2p as m2p
 import test_oracle_ops as ops
 import test_oracle_solve as solve
 
@@ -16,6 +17,7 @@ MUTANTS = {
     4: "interaction list also takes the near neighbours",
     5: "near field without the self cell",
     6: "near-field pair force pointing away from the mass",
+    7: "final-stage M2P without the (-1)^|alpha| factor",
 }
 
 PINS = [
@@ -26,6 +28,7 @@ PINS = [
     lambda o: solve.test_equals_direct_sum_when_all_boxes_are_near(o, (8, 8, 8), 4),
     accel.test_accel_converges_to_direct_in_p,
     accel.test_direct_pair_forces_obey_the_third_law,
+    m2p.test_m2p_converges_and_beats_m2l_l2p,
 ]
 
 
