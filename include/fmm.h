@@ -88,7 +88,13 @@ typedef struct {
                          field computes four columns per cell and
                          fmm_solve_adjoint rejects grad_accel
                          (FMM_ERR_UNSUPPORTED)                                  */
-  int reserved[5];    /* must be zero */
+  int final_stage;    /* 0: M2L + L2P at the leaf level too; 1: the paper's own
+                         final stage (Sec. 4): the leaf interaction list is
+                         evaluated by M2P at the cell centres (more accurate,
+                         ~6x the leaf-level work).  With 1, accel must not be 2
+                         and fmm_solve_adjoint returns FMM_ERR_UNSUPPORTED
+                         (the truncated M2P operator is not symmetric)          */
+  int reserved[4];    /* must be zero */
 } fmm_opts;
 
 /* Default options: FMM_FP32, n_fp64_levels = 3, accel = 1. */

@@ -70,7 +70,7 @@ class _Grid(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_fp64_levels", ctypes.c_int), ("accel", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("final_stage", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 _lib = None
@@ -162,7 +162,7 @@ class FMMPlan:
     """One solver for a fixed grid shape, order, leaf size and precision."""
 
     def __init__(self, shape, order: int = 6, leaf: int = 4, precision: str = "fp32", dx: float = 1.0,
-                 G: float = 1.0, n_fp64_levels: int = 3, accel=True, stream=None):
+                 G: float = 1.0, n_fp64_levels: int = 3, accel=True, final_stage: str = "m2l", stream=None):
         import torch
 
         self.lib = load()
@@ -181,6 +181,9 @@ class FMMPlan:
         # accel: False (none), True (5-point stencil of phi), "analytic" (gradient
         # of the expansions plus near-field pair forces)
         opts.accel = 2 if accel == "analytic" else (1 if accel else 0)
+        # final_stage: "m2l" (M2L + L2P at the leaf level) or "m2p" (the
+        # paper's final stage: M2P at the cell centres)
+        opts.final_stage = 1 if final_stage == "m2p" else 0
         handle = ctypes.c_void_p()
         _check(self.lib, self.lib.fmm_plan(ctypes.byref(grid), self.order, self.leaf, ctypes.byref(opts),
                                            _stream_handle(stream), ctypes.byref(handle)))

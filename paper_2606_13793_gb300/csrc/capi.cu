@@ -163,7 +163,7 @@ struct fmm_plan_s {
   int tc_kind = -1;
   TcLaunch tc{};
   bool near_tc = false;
-  TcLaunch tcn{};
+  std::vector<TcLaunch> tcn;  // near field: kTcMaxPasses passes per launch
   alignas(64) unsigned char map_near_hi[128];
   alignas(64) unsigned char map_near_lo[128];
   size_t rho_hi_off = 0, rho_lo_off = 0;
@@ -187,6 +187,15 @@ struct fmm_plan_s {
   // side stream of the concurrent far field (CUDA-core M2L levels), fork/join events
   cudaStream_t side = nullptr;
   int near_comps = 1;  // near-field columns per cell: potential, + 3 force components (analytic accel)
+  // final-stage M2P (the paper's own final stage): leaf interaction list at the cell centres
+  bool m2p = false, m2p_tc = false;
+  size_t m2p_off = 0;  // [leaf parent][child][b^3] potentials (scaled, x 1/b in the leaf kernel)
+  void* d_w_m2p = nullptr;
+  int* d_m2p_tile_k = nullptr;
+  long long* d_m2p_tile_w = nullptr;
+  int m2p_ntiles = 0;
+  std::vector<int> h_m2p_tile_k;
+  TcLaunch tcm{};
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // timing
   bool timing = false;
@@ -405,7 +414,7 @@ float tf32_rn(double w) {
 // shared-memory image the MMA reads: rows of 128 B, 16-byte chunks swizzled
 // by (row mod 8), bf16 hi plane then lo plane (or one TF32 plane).
 struct TcHost {
-  TcPass pass[kTcMaxPasses];
+  std::vector<TcPass> pass;  // kTcMaxPasses per launch
   int npass = 0;
   int a_stages = 2;
   std::vector<unsigned char> W;
@@ -436,9 +445,19 @@ uint32_t host_idesc(int kind, int n) {
 // boundary into two accumulators, which the epilogue adds in a fixed order.
 // A bf16x3 pass with a single group (the near field) is split by product
 // instead: hi*hi, hi*lo and lo*hi go to three issuers with their own
-// accumulators and one weight plane each.
+// accumulators and one weight plane each; where TMEM leaves room, the hi*hi
+// reduction is also halved at a chunk boundary onto the fourth issuer.
+//
+// `long_sums`: one group per pass, so that every group is product-split, and
+// one neighbour column (dx, dz) per accumulation segment.  The tensor cores
+// add into their FP32 accumulators with truncation (round toward zero), which
+// on a long same-signed sum (the near field of a large leaf box: 27 x b^3
+// terms) leaves a bias of about half an ulp per MMA; short reductions per
+// accumulator, summed by the epilogue with rounding to nearest, bound it.
+// `max_passes`: passes the caller can launch (kTcMaxPasses per launch).
 template <typename Entry>
-bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entry, TcHost& H, int a_stages) {
+bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entry, TcHost& H, int a_stages,
+                      bool long_sums = false, int max_passes = kTcMaxPasses) {
   const int ring_budget = tc_ring_budget(kind, a_stages);
   H.a_stages = a_stages;
   const int chunk = kind == TC_BF16X3 ? 64 : 32;  // reduction values per 128-byte chunk
@@ -464,16 +483,20 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
     return n;
   };
   H.W.clear();
+  H.pass.clear();
   H.npass = 0;
   size_t gi = 0;
   while (gi < gs.size()) {
-    if (H.npass == kTcMaxPasses) return false;
-    TcPass& P = H.pass[H.npass++];
+    if (H.npass == max_passes) return false;
+    H.pass.emplace_back();
+    ++H.npass;
+    TcPass& P = H.pass.back();
     std::memset(&P, 0, sizeof(P));
+    P.seg_xz = long_sums ? 1 : 9;
     // output groups of this pass, in the given (non-increasing K) order, up to 512 TMEM columns
     int cols = 0;
     std::vector<VGroup> V;
-    while (gi < gs.size() && P.ng < kTcMaxGroups) {
+    while (gi < gs.size() && P.ng < kTcMaxGroups && !(long_sums && P.ng == 1)) {
       const int nm = (gs[gi].ncols + 15) / 16 * 16;
       if (cols + nm > 512) break;
       if (P.ng > 0 && gs[gi].K > gs[gi - 1].K) return false;  // prefixes must shrink
@@ -482,6 +505,7 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
       P.out_nmma[P.ng] = nm;
       P.out_tmem2[P.ng] = -1;
       P.out_tmem3[P.ng] = -1;
+      P.out_tmem4[P.ng] = -1;
       V.push_back({P.ng, 0, gs[gi].K, nm});
       cols += nm;
       ++P.ng;
@@ -499,6 +523,23 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
       V.push_back(v3);
       cols *= 3;
       P.out_tmem2[0] = P.out_tmem3[0] = 0;  // marked; placed below
+      // hi*hi in two halves (chunk boundary nearest the middle of its steps)
+      const int hs = vsteps(V[0]);
+      int best = -1, bestd = 1 << 30;
+      for (int kb = chunk; kb < V[0].k1; kb += chunk) {
+        VGroup a = V[0];
+        a.k1 = kb;
+        const int d = std::abs(2 * vsteps(a) - hs);
+        if (d < bestd) bestd = d, best = kb;
+      }
+      if (best > 0 && cols + V[0].nm <= 512) {
+        VGroup v4 = V[0];
+        v4.k0 = best;
+        V[0].k1 = best;
+        V.push_back(v4);
+        cols += v4.nm;
+        P.out_tmem4[0] = 0;  // marked; placed below
+      }
     }
     // split the heaviest accumulators along the reduction while one exceeds an even share
     int total = 0;
@@ -560,7 +601,7 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
         else if (v.k0 == 0)
           P.out_tmem[v.out] = v.tmem;
         else
-          P.out_tmem2[v.out] = v.tmem;
+          (v.prod == 1 ? P.out_tmem4 : P.out_tmem2)[v.out] = v.tmem;
       }
       int alloc = 32;
       while (alloc < c) alloc *= 2;
@@ -730,7 +771,85 @@ bool build_tc_near(int b, int comps, int kind, TcHost& H) {
     const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
     return near_entry(b, D, k, n);
   };
+  // b >= 8: 27 x 512 same-signed terms per potential, too long a sum for one
+  // truncating accumulator (bias ~3e-5); one product-split group per pass,
+  // drained after every neighbour column, over as many launches as it takes
+  const bool long_sums = b3 > 64;
+  return build_tc_generic(kind, gs, entry, H, 2, long_sums, long_sums ? kTcMaxNearLaunches * kTcMaxPasses : kTcMaxPasses);
+}
+
+// Final-stage M2P (Sec. 4) as the same neighbour contraction over the leaf
+// parents: reduction k = alpha*8 + source child (the parent-blocked multipole
+// row), output n = target child * b^3 + cell, weight
+//   W = (-1)^|alpha| (-b_alpha(u + e)),
+// u = c_target - c_source in leaf-box units (ct - cs - 2d, interaction list
+// only: Chebyshev(u) >= 2), e = the cell centre in the target box (box
+// units), b_alpha the Taylor coefficients of 1/|r|; the result, times 1/h,
+// is the cell potential of the source box's scaled multipoles.
+struct M2pTable {
+  int b = 0;
+  std::vector<std::vector<double>> t;  // [u (7^3)][cell] -> nc coefficients
+  void build(const MultiIndex& mi, int bb) {
+    b = bb;
+    const int b3 = b * b * b;
+    t.assign((size_t)343 * b3, {});
+    for (int uz = -3; uz <= 3; ++uz)
+      for (int uy = -3; uy <= 3; ++uy)
+        for (int ux = -3; ux <= 3; ++ux) {
+          if (std::max(std::abs(ux), std::max(std::abs(uy), std::abs(uz))) < 2) continue;
+          for (int c = 0; c < b3; ++c) {
+            const int ci[3] = {c % b, (c / b) % b, c / (b * b)};
+            double u[3] = {(double)ux, (double)uy, (double)uz};
+            for (int q = 0; q < 3; ++q) u[q] += (ci[q] + 0.5) / b - 0.5;
+            taylor_inv_r(u, mi, t[(size_t)((uz + 3) * 49 + (uy + 3) * 7 + (ux + 3)) * b3 + c]);
+          }
+        }
+  }
+};
+
+double m2p_entry(const MultiIndex& mi, const M2pTable& tab, int d, int k, int n) {
+  const int b3 = tab.b * tab.b * tab.b;
+  const int al = k / 8, cs = k % 8, ct = n / b3, cell = n % b3;
+  if (al >= mi.nc || ct >= 8) return 0.0;
+  const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+  int u[3];
+  for (int q = 0; q < 3; ++q) u[q] = ((ct >> q) & 1) - ((cs >> q) & 1) - 2 * D[q];
+  if (std::max(std::abs(u[0]), std::max(std::abs(u[1]), std::abs(u[2]))) < 2) return 0.0;
+  const std::vector<double>& tb = tab.t[(size_t)((u[2] + 3) * 49 + (u[1] + 3) * 7 + (u[0] + 3)) * b3 + cell];
+  return (((mi.a[al] + mi.b[al] + mi.c[al]) & 1) ? -1.0 : 1.0) * (-tb[al]);
+}
+
+// Tensor-core schedule of the M2P contraction: every output column needs the
+// whole reduction (no truncation prefix), so groups of up to 128 columns
+// share one K = 8 nc; one pass for b <= 4.
+bool build_tc_m2p(const MultiIndex& mi, const M2pTable& tab, int kind, TcHost& H) {
+  const int ncol = 8 * tab.b * tab.b * tab.b;
+  std::vector<TcCols> gs;
+  for (int c = 0; c < ncol; c += kTcMaxGroupN) gs.push_back({c, std::min(kTcMaxGroupN, ncol - c), 8 * mi.nc});
+  auto entry = [&](int d, int k, int n) { return m2p_entry(mi, tab, d, k, n); };
   return build_tc_generic(kind, gs, entry, H, 2);
+}
+
+// Weights of a CUDA-core contraction whose column tiles all reduce over K:
+// W[tile][d][k][32].
+template <typename T, typename Entry>
+void full_weights(int ncols, int K, const Entry& entry, std::vector<T>& W, std::vector<int>& tile_k,
+                  std::vector<long long>& tile_w, bool fill = true) {
+  const int ntiles = (ncols + kNTile - 1) / kNTile;
+  tile_k.assign(ntiles, K);
+  tile_w.resize(ntiles);
+  for (int t = 0; t < ntiles; ++t) tile_w[t] = 27LL * K * kNTile * t;
+  W.assign((size_t)27 * K * kNTile * ntiles, T(0));
+  if (!fill) return;
+  for (int t = 0; t < ntiles; ++t)
+    for (int d = 0; d < 27; ++d) {
+      T* blk = W.data() + tile_w[t] + (long long)d * K * kNTile;
+      for (int j = 0; j < kNTile; ++j) {
+        const int n = t * kNTile + j;
+        if (n >= ncols) continue;
+        for (int k = 0; k < K; ++k) blk[(long long)k * kNTile + j] = (T)entry(d, k, n);
+      }
+    }
 }
 
 // Near-field matrices (eq. direct, cell units) for the CUDA-core contraction:
@@ -826,9 +945,11 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
   P->mi.init(order);
   P->nc = P->mi.nc;
   P->near_comps = o.accel == 2 ? 4 : 1;
+  P->m2p = o.final_stage == 1;
 
   fmm_status st = build_levels(P);
   if (st != FMM_OK) return st;
+  if (P->L < 2) P->m2p = false;  // no interaction list at the leaf level
   // level precisions: FP64 everywhere, FP32 everywhere, or (tensor-core
   // precisions) FP64 on the coarsest M2L levels 2 .. 1 + n_fp64_levels (never
   // the leaf level) and tcgen05 M2L on every other level.
@@ -868,6 +989,10 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
   off = align(off + cells_bytes);
   P->near_off = off;
   off = align(off + cells_bytes * (size_t)P->near_comps);
+  if (P->m2p) {  // every cell of every leaf parent block, phantom children included
+    P->m2p_off = off;
+    off = align(off + (size_t)P->lev[P->L].npar * 8 * (size_t)(P->b * P->b * P->b) * P->esize());
+  }
   P->work_off = off;
   off = align(off + cells_bytes);
   P->near_tc = tcp && (leaf == 4 || leaf == 8);
@@ -1012,6 +1137,51 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     P->h_near_tile_k = tk;
     if ((st = P->upload(tk, &P->d_near_tile_k, s)) || (st = P->upload(tw, &P->d_near_tile_w, s))) return cleanup(st);
   }
+  if (P->m2p) {
+    M2pTable tab;
+    tab.build(P->mi, P->b);
+    const Level& lf = P->lev[P->L];
+    if (lf.tc) {
+      TcHost H;
+      if (build_tc_m2p(P->mi, tab, P->tc_kind, H)) {
+        unsigned char* dw = nullptr;
+        if ((st = P->upload(H.W, &dw, s))) return cleanup(st);
+        TcLaunch& T = P->tcm;
+        T.W = dw;
+        T.npass = H.npass;
+        T.a_stages = H.a_stages;
+        for (int i = 0; i < H.npass; ++i) T.pass[i] = H.pass[i];
+        T.n_cols = 8 * P->b * P->b * P->b;
+        T.kind = P->tc_kind;
+        T.accumulate = 0;
+        for (int q = 0; q < 3; ++q) T.grid[q] = lf.np[q];
+        T.C = reinterpret_cast<float*>(P->arena + P->m2p_off);
+        P->m2p_tc = true;
+      }
+    }
+    if (!P->m2p_tc) {
+      const int ncol = 8 * P->b * P->b * P->b;
+      auto entry = [&](int d, int k, int n) { return m2p_entry(P->mi, tab, d, k, n); };
+      std::vector<int> tk;
+      std::vector<long long> tw;
+      if (lf.f64) {
+        std::vector<double> W;
+        full_weights<double>(ncol, 8 * P->nc, entry, W, tk, tw);
+        double* d = nullptr;
+        if ((st = P->upload(W, &d, s))) return cleanup(st);
+        P->d_w_m2p = d;
+      } else {
+        std::vector<float> W;
+        full_weights<float>(ncol, 8 * P->nc, entry, W, tk, tw);
+        float* d = nullptr;
+        if ((st = P->upload(W, &d, s))) return cleanup(st);
+        P->d_w_m2p = d;
+      }
+      P->m2p_ntiles = (int)tk.size();
+      P->h_m2p_tile_k = tk;
+      if ((st = P->upload(tk, &P->d_m2p_tile_k, s)) || (st = P->upload(tw, &P->d_m2p_tile_w, s))) return cleanup(st);
+    }
+  }
   if (P->near_tc) {
     TcHost H;
     // bf16x3 in both tensor-core precisions: a TF32 near field would carry
@@ -1020,26 +1190,31 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
       return cleanup(fail(FMM_ERR_UNSUPPORTED, "near-field schedule failed"));
     unsigned char* dw = nullptr;
     if ((st = P->upload(H.W, &dw, s))) return cleanup(st);
-    TcLaunch& T = P->tcn;
-    T.W = dw;
-    T.npass = H.npass;
-    T.a_stages = H.a_stages;
-    for (int i = 0; i < H.npass; ++i) T.pass[i] = H.pass[i];
-    T.n_cols = P->b * P->b * P->b * P->near_comps;
-    T.kind = TC_BF16X3;
-    T.accumulate = 0;
-    for (int q = 0; q < 3; ++q) T.grid[q] = P->lev[P->L].n[q];
-    T.C = reinterpret_cast<float*>(P->arena + P->near_off);
-    T.err = P->d_flag;
+    // every launch writes its own columns of the same rows
+    P->tcn.assign((H.npass + kTcMaxPasses - 1) / kTcMaxPasses, TcLaunch{});
+    for (size_t li = 0; li < P->tcn.size(); ++li) {
+      TcLaunch& T = P->tcn[li];
+      T.W = dw;
+      T.npass = std::min(kTcMaxPasses, H.npass - (int)li * kTcMaxPasses);
+      T.a_stages = H.a_stages;
+      for (int i = 0; i < T.npass; ++i) T.pass[i] = H.pass[li * kTcMaxPasses + i];
+      T.n_cols = P->b * P->b * P->b * P->near_comps;
+      T.kind = TC_BF16X3;
+      T.accumulate = 0;
+      for (int q = 0; q < 3; ++q) T.grid[q] = P->lev[P->L].n[q];
+      T.C = reinterpret_cast<float*>(P->arena + P->near_off);
+      T.err = P->d_flag;
+    }
     // activation rows: the b^3 cell values of a leaf box (the output rows carry
     // near_comps x b^3 columns)
     const int b3 = P->b * P->b * P->b;
-    cudaError_t e = make_row_map(P->map_near_hi, P->arena + P->rho_hi_off, b3, 2, T.grid, 64);
-    if (e == cudaSuccess) e = make_row_map(P->map_near_lo, P->arena + P->rho_lo_off, b3, 2, T.grid, 64);
+    cudaError_t e = make_row_map(P->map_near_hi, P->arena + P->rho_hi_off, b3, 2, P->tcn[0].grid, 64);
+    if (e == cudaSuccess) e = make_row_map(P->map_near_lo, P->arena + P->rho_lo_off, b3, 2, P->tcn[0].grid, 64);
     if (e != cudaSuccess) return cleanup(fail(FMM_ERR_CUDA, "tensor map encoding failed for the near field"));
   }
   P->tc.err = P->d_flag;
   P->tc.accumulate = 0;
+  P->tcm.err = P->d_flag;
   for (int l = 2; l <= P->L; ++l)
     if (!P->lev[l].tc) zrun_default(m2l_gemm(P, l), P->h_m2l_tile_k, &P->m2l_choice[l], P->lev[l].f64);
   if (!P->near_tc) zrun_default(near_gemm(P), P->h_near_tile_k, &P->near_choice, P->f64_data());
@@ -1097,6 +1272,9 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
   if (o.precision < FMM_FP64 || o.precision > FMM_M2L_BF16X3) return fail(FMM_ERR_ARG, "unknown precision %d", o.precision);
   if (o.n_fp64_levels < 0 || o.n_fp64_levels > kMaxLevels) return fail(FMM_ERR_ARG, "bad n_fp64_levels");
   if (o.accel < 0 || o.accel > 2) return fail(FMM_ERR_ARG, "accel %d not in {0, 1, 2}", o.accel);
+  if (o.final_stage < 0 || o.final_stage > 1) return fail(FMM_ERR_ARG, "final_stage %d not in {0, 1}", o.final_stage);
+  if (o.final_stage == 1 && o.accel == 2)
+    return fail(FMM_ERR_UNSUPPORTED, "the analytic acceleration is built for final_stage = 0 only");
   for (int r : o.reserved)
     if (r != 0) return fail(FMM_ERR_ARG, "reserved option fields must be zero");
   int dev = 0;
@@ -1171,17 +1349,18 @@ fmm_status do_m2m(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s) {
 
 // L(l) += L2L(L(l - 1)) for l >= 3; the level's M2L has written L(l) (level 2
 // has no parent far field: its locals are its M2L alone).
-fmm_status do_l2l(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s) {
+fmm_status do_l2l(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s, int accumulate) {
   const Level &q = P->lev[l - 1], &c = P->lev[l];
   cudaError_t e;
   if (q.f64 && c.f64) {
     e = launch_l2l<double, double>(tt, q, static_cast<const double*>(P->Lx(l - 1)), c, static_cast<double*>(P->Lx(l)),
-                                   1, s);
+                                   accumulate, s);
   } else if (q.f64) {
-    e = launch_l2l<double, float>(tt, q, static_cast<const double*>(P->Lx(l - 1)), c, static_cast<float*>(P->Lx(l)), 1,
-                                  s);
+    e = launch_l2l<double, float>(tt, q, static_cast<const double*>(P->Lx(l - 1)), c, static_cast<float*>(P->Lx(l)),
+                                  accumulate, s);
   } else {
-    e = launch_l2l<float, float>(tt, q, static_cast<const float*>(P->Lx(l - 1)), c, static_cast<float*>(P->Lx(l)), 1, s);
+    e = launch_l2l<float, float>(tt, q, static_cast<const float*>(P->Lx(l - 1)), c, static_cast<float*>(P->Lx(l)),
+                                 accumulate, s);
   }
   CUDA_TRY(e);
   return FMM_OK;
@@ -1222,6 +1401,32 @@ NbrGemm near_gemm(fmm_plan_t P) {
   g.dsplit = P->near_choice.dsplit;
   g.partial = P->arena + P->part_off;
   return g;
+}
+
+// Final-stage M2P of the leaf level (tensor cores when the leaf level is on
+// them and the schedule fits, else the CUDA-core contraction).
+fmm_status do_m2p(fmm_plan_t P, cudaStream_t s) {
+  const Level& lf = P->lev[P->L];
+  if (P->m2p_tc) {
+    CUDA_TRY(launch_m2l_tc(P->tcm, P->map_hi[P->L], P->map_lo[P->L], s));
+    return FMM_OK;
+  }
+  NbrGemm g;
+  g.A = P->M(P->L);
+  g.row_len = 8 * P->nc;
+  for (int q = 0; q < 3; ++q) g.grid[q] = lf.np[q];
+  g.W = P->d_w_m2p;
+  g.tile_k = P->d_m2p_tile_k;
+  g.tile_w = P->d_m2p_tile_w;
+  g.C = P->arena + P->m2p_off;
+  g.n_cols = 8 * P->b * P->b * P->b;
+  g.ntiles = P->m2p_ntiles;
+  g.accumulate = 0;
+  g.dsplit = 1;
+  g.partial = nullptr;
+  g.shape = zrun_eligible(g, P->h_m2p_tile_k.data(), P->m2p_ntiles) ? 1 : 0;
+  CUDA_TRY(lf.f64 ? launch_nbr_gemm<double>(g, s) : launch_nbr_gemm<float>(g, s));
+  return FMM_OK;
 }
 
 fmm_status do_m2l(fmm_plan_t P, int l, cudaStream_t s) {
@@ -1282,7 +1487,7 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
   for (int l = 2; l <= L; ++l) {
     if (P->lev[l].tc) continue;
     StageTimer t(P, ST_M2L, sf);
-    if ((st = do_m2l(P, l, sf))) return st;
+    if ((st = (l == L && P->m2p) ? do_m2p(P, sf) : do_m2l(P, l, sf))) return st;
   }
   if (near_side) {
     StageTimer t(P, ST_NEAR, sf);
@@ -1292,12 +1497,12 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
   for (int l = 2; l <= L; ++l) {
     if (!P->lev[l].tc) continue;
     StageTimer t(P, ST_M2L_TC, s);
-    if ((st = do_m2l(P, l, s))) return st;
+    if ((st = (l == L && P->m2p) ? do_m2p(P, s) : do_m2l(P, l, s))) return st;
   }
   // near field over the 27 neighbour leaf boxes
   if (P->near_tc) {
     StageTimer t(P, ST_NEAR_TC, s);
-    CUDA_TRY(launch_m2l_tc(P->tcn, P->map_near_hi, P->map_near_lo, s));
+    for (const TcLaunch& NL : P->tcn) CUDA_TRY(launch_m2l_tc(NL, P->map_near_hi, P->map_near_lo, s));
   } else if (!near_side) {
     StageTimer t(P, ST_NEAR, s);
     CUDA_TRY(launch_nbr_gemm<T>(near_gemm(P), s));
@@ -1305,7 +1510,8 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
   if (fork) CUDA_TRY(cudaStreamWaitEvent(s, P->ev_join, 0));
   for (int l = 3; l <= L; ++l) {
     StageTimer t(P, ST_L2L, s);
-    if ((st = do_l2l(P, tt, l, s))) return st;
+    // with the final-stage M2P the leaf locals are the parent's shifted locals alone
+    if ((st = do_l2l(P, tt, l, s, (l == L && P->m2p) ? 0 : 1))) return st;
   }
   if (accel && P->near_comps == 4) {  // analytic acceleration, read off the expansions
     StageTimer t(P, ST_LEAF, s);
@@ -1316,7 +1522,9 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
   {
     StageTimer t(P, ST_LEAF, s);
     CUDA_TRY(launch_leaf_finish<T>(tt, P->lev[L], static_cast<const T*>(P->Lx(L)), near_box,
-                                   P->b * P->b * P->b * P->near_comps, P->dims, P->G * P->dx * P->dx, phi, s));
+                                   P->b * P->b * P->b * P->near_comps,
+                                   P->m2p ? reinterpret_cast<const T*>(P->arena + P->m2p_off) : nullptr, P->dims,
+                                   P->G * P->dx * P->dx, phi, s));
   }
   if (accel) {
     StageTimer t(P, ST_FD, s);
@@ -1348,6 +1556,8 @@ fmm_status fmm_solve(fmm_plan_t P, const void* rho, void* phi, void* accel, void
 fmm_status fmm_solve_adjoint(fmm_plan_t P, const void* grad_phi, const void* grad_accel, void* grad_rho, void* stream) {
   if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
   if (!grad_rho || (!grad_phi && !grad_accel)) return fail(FMM_ERR_ARG, "grad_rho and one gradient must be non-NULL");
+  if (P->m2p)
+    return fail(FMM_ERR_UNSUPPORTED, "no adjoint with the final-stage M2P (its truncated operator is not symmetric)");
   if (grad_accel && P->near_comps == 4)
     return fail(FMM_ERR_UNSUPPORTED, "the adjoint of the analytic acceleration is not built (use accel = 1)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1430,9 +1640,9 @@ int fmm_solve_launches(fmm_plan_t P, int with_accel) {
   if (L < 2) n += 1;                    // zero the leaf locals
   for (int l = 2; l <= L; ++l) {
     n += l >= 3 ? 2 : 1;                // M2L, and L2L below level 2
-    if (!P->lev[l].tc && P->m2l_choice[l].dsplit > 1) n += 1;  // reduction of the neighbour partials
+    if (!P->lev[l].tc && P->m2l_choice[l].dsplit > 1 && !(l == L && P->m2p)) n += 1;  // partial-sum reduction
   }
-  n += 2;                               // near field + leaf finish
+  n += P->near_tc ? (int)P->tcn.size() + 1 : 2;  // near field + leaf finish
   if (!P->near_tc && P->near_choice.dsplit > 1) n += 1;
   if (with_accel && P->near_comps == 1) n += 1;  // FD stencil (the analytic force comes with the leaf kernel)
   return n;

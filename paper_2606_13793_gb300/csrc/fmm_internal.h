@@ -121,8 +121,10 @@ template <typename T>
 cudaError_t launch_zero(T* p, size_t count, cudaStream_t s);
 // near_box rows hold near_stride values per leaf box, the potential sums first.
 template <typename T>
+// m2p (nullable): final-stage M2P potentials, parent-blocked [parent][child][b^3], in the
+// leaf level's scaled units (multiplied by 1/b like the L2P term).
 cudaError_t launch_leaf_finish(const TreeTables& t, const Level& leaf, const T* Lleaf, const T* near_box,
-                               int near_stride, const int dims[3], double scale, T* phi, cudaStream_t s);
+                               int near_stride, const T* m2p, const int dims[3], double scale, T* phi, cudaStream_t s);
 // With the analytic acceleration: near_box rows are [potential, d/dx, d/dy,
 // d/dz] x b^3; accel = ascale (far gradient + near gradient).
 template <typename T>
@@ -148,7 +150,8 @@ cudaError_t launch_export_level(const T* src, const Level& lv, int what, double 
 // prefix) and the reduction streamed as 128-byte chunks of one neighbour's
 // row.  A operand: TMA tile of the (shifted) parent rows; B operand: a
 // pre-swizzled weight tile per (neighbour, chunk, group).
-constexpr int kTcMaxPasses = 4;
+constexpr int kTcMaxPasses = 4;        // passes of one launch (kernel parameter space)
+constexpr int kTcMaxNearLaunches = 4;  // near-field launches of a plan
 // 128 rows per tile as 8 (x) x 16 (y) x 1 (z): the activation stage is an
 // 8 x 18 x 1 box (y halo of one row each side), in which the three y-shifts
 // of a neighbour column are contiguous 128-row windows.
@@ -194,10 +197,15 @@ struct TcSpan {
 // tile = n rows x 128 B per plane (bf16 hi plane, then lo plane).
 struct TcPass {
   int ng, nchunks, tmem_cols, bytes_per_d;
+  // neighbour columns (dx, dz) per accumulation segment (1..9): after each
+  // segment the epilogue drains the accumulators into C (FP32, rounded to
+  // nearest) and the next segment reopens them
+  int seg_xz;
   long long w_base;
   int out_tmem[kTcMaxGroups];   // epilogue: TMEM column of the group's accumulator
   int out_tmem2[kTcMaxGroups];  // second accumulator (reduction- or product-split group), or -1
   int out_tmem3[kTcMaxGroups];  // third accumulator (product-split group), or -1
+  int out_tmem4[kTcMaxGroups];  // second half of a product-split group's hi*hi reduction, or -1
   int out_col0[kTcMaxGroups];   // first output column (beta*8 + child)
   int out_ncols[kTcMaxGroups];  // real output columns
   int out_nmma[kTcMaxGroups];   // TMEM columns of the group (multiple of 16)

@@ -12,10 +12,13 @@ using namespace tree;
 //   phi = G dx^2 [ h^-1 sum_beta Lt_beta ((x - c)/h)^beta + near ]
 // near_box holds the near-field sums per leaf box ([box][b^3] cells).
 // near_box rows have near_stride values per box (the potential first).
+// m2p (nullable): final-stage M2P potentials [parent][child][b^3], added to
+// the L2P sum before its 1/h scaling.
 template <int P, typename T>
 __global__ void __launch_bounds__(kThreads) leaf_finish_kernel(Level leaf, const T* __restrict__ Lleaf,
-                                                               const T* __restrict__ near_box, int near_stride, int nx,
-                                                               int ny, int b, T scale, T* __restrict__ phi) {
+                                                               const T* __restrict__ near_box, int near_stride,
+                                                               const T* __restrict__ m2p, int nx, int ny, int b,
+                                                               T scale, T* __restrict__ phi) {
   constexpr int NC = ncoef_c(P);
   const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
   const Box B = box_of(leaf, t);
@@ -26,6 +29,7 @@ __global__ void __launch_bounds__(kThreads) leaf_finish_kernel(Level leaf, const
   for (int k = 0; k < NC; ++k) L[k] = src[k * 8];
   const T inv_b = T(1) / T(b);
   const long long box = ((long long)B.z * leaf.n[1] + B.y) * leaf.n[0] + B.x;
+  const T* mp = m2p ? m2p + (B.par * 8 + B.c) * (long long)(b * b * b) : nullptr;
   for (int k = 0; k < b; ++k) {
     T zpow[P + 1];
     powers<P, T>((T(k) + T(0.5)) * inv_b - T(0.5), zpow);
@@ -59,13 +63,18 @@ __global__ void __launch_bounds__(kThreads) leaf_finish_kernel(Level leaf, const
         }
         float out[4];
         const float nv[4] = {nr[j].x, nr[j].y, nr[j].z, nr[j].w};
+        float mv[4] = {0.f, 0.f, 0.f, 0.f};
+        if (mp) {
+          const float4 m4 = __ldg(reinterpret_cast<const float4*>(mp + (k * 4 + j) * 4));
+          mv[0] = m4.x, mv[1] = m4.y, mv[2] = m4.z, mv[3] = m4.w;
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const T xi = (T(i) + T(0.5)) * inv_b - T(0.5);
           T s = u1[P];
 #pragma unroll
           for (int a = P - 1; a >= 0; --a) s = fma(s, xi, u1[a]);  // Horner in x
-          out[i] = (float)(scale * fma(s, inv_b, (T)nv[i]));
+          out[i] = (float)(scale * fma(s + (T)mv[i], inv_b, (T)nv[i]));
         }
         *reinterpret_cast<float4*>(phi + ((long long)(B.z * 4 + k) * ny + (B.y * 4 + j)) * nx + (long long)B.x * 4) =
             make_float4(out[0], out[1], out[2], out[3]);
@@ -90,6 +99,7 @@ __global__ void __launch_bounds__(kThreads) leaf_finish_kernel(Level leaf, const
         T s = u1[P];
 #pragma unroll
         for (int a = P - 1; a >= 0; --a) s = fma(s, xi, u1[a]);  // Horner in x
+        if (mp) s += mp[(k * b + j) * b + i];
         row[i] = scale * fma(s, inv_b, nrow[i]);
       }
     }
@@ -261,17 +271,17 @@ template cudaError_t launch_leaf_finish_grad<double>(const TreeTables&, const Le
 
 template <typename T>
 cudaError_t launch_leaf_finish(const TreeTables& t, const Level& leaf, const T* Lleaf, const T* near_box,
-                               int near_stride, const int dims[3], double scale, T* phi, cudaStream_t s) {
+                               int near_stride, const T* m2p, const int dims[3], double scale, T* phi, cudaStream_t s) {
   const long long threads = leaf.npar * 8;
   if (threads == 0) return cudaSuccess;
   FMM_ORDER_SWITCH(t.p, (leaf_finish_kernel<PP, T><<<grid_threads(threads), kThreads, 0, s>>>(
-                            leaf, Lleaf, near_box, near_stride, dims[0], dims[1], t.b, (T)scale, phi)));
+                            leaf, Lleaf, near_box, near_stride, m2p, dims[0], dims[1], t.b, (T)scale, phi)));
   return cudaGetLastError();
 }
 
 template cudaError_t launch_leaf_finish<float>(const TreeTables&, const Level&, const float*, const float*, int,
-                                               const int*, double, float*, cudaStream_t);
+                                               const float*, const int*, double, float*, cudaStream_t);
 template cudaError_t launch_leaf_finish<double>(const TreeTables&, const Level&, const double*, const double*, int,
-                                                const int*, double, double*, cudaStream_t);
+                                                const double*, const int*, double, double*, cudaStream_t);
 
 }  // namespace fmmgb

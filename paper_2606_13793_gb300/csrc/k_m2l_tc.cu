@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int ntx = (P.grid[0] + kTcTileX - 1) / kTcTileX, nty = (P.grid[1] + kTcTileY - 1) / kTcTileY;
   const int ntiles = ntx * nty * ((P.grid[2] + kTcTileZ - 1) / kTcTileZ);
   const uint32_t nbuf = 2 * pass.tmem_cols <= 512 ? 2u : 1u;  // accumulator sets
+  const int seg = pass.seg_xz >= 1 && pass.seg_xz <= 9 ? pass.seg_xz : 9;  // neighbour columns per segment
 
   {
     // one barrier per thread: a_full, a_empty (every issuer releases a
@@ -343,13 +344,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* empty = b_empty + q * kRingE;
     uint32_t ai = 0, e = 0, off = 0, it = 0;
     bool ok = !(*reinterpret_cast<volatile int*>(P.err) & 2);
-    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++it) {
+    // one accumulation segment (seg neighbour columns of a tile) per accumulator set
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x)
+     for (int xz0 = 0; ok && xz0 < 9; xz0 += seg, ++it) {
       const uint32_t buf = it % nbuf, use = it / nbuf;
       // this accumulator set must have been drained by the epilogue
       if (!(ok = wait_fast(&acc_empty[buf], (use & 1) ^ 1, P.err, W_MMA_ACC))) break;
       tc_fence_after();
       const uint32_t tbase = tmem + buf * (uint32_t)pass.tmem_cols;
-      for (int xz = 0; ok && xz < 9; ++xz) {
+      for (int xz = xz0; ok && xz < xz0 + seg && xz < 9; ++xz) {
         for (int j = 0; ok && j < pass.nchunks; ++j) {
           const uint32_t sa = ai % nA;
           if (!(ok = wait_fast(&a_full[sa], (ai / nA) & 1, P.err, W_MMA_A))) break;
@@ -369,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint64_t b = ring_desc + (uint64_t)(off >> 4);
               const uint64_t b_lo = b + (uint64_t)(plane >> 4);
               const uint32_t d = tbase + (uint32_t)S.tmem_col;
-              const uint32_t acc0 = (xz == 0 && dy == 0 && j == S.first) ? 0u : 1u;  // the first step opens
+              const uint32_t acc0 = (xz == xz0 && dy == 0 && j == S.first) ? 0u : 1u;  // the first step opens
               if (KIND == TC_BF16X3 && S.prod) {
                 const uint64_t as = S.prod == 3 ? a_lo : a;
                 switch (S.ksteps) {
@@ -395,7 +398,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++ai;
         }
       }
-      mma_commit(&acc_full[buf]);  // fires when every MMA of this tile has completed
+      mma_commit(&acc_full[buf]);  // fires when every MMA of this segment has completed
     }
   } else if (warp > 2 * NQ) {
     // ---------------- epilogue: TMEM -> registers -> C ----------------
@@ -403,22 +406,29 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int r = wq * 32 + lane;  // tile row = TMEM lane
     const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
     uint32_t it = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    bool live = true;
+    for (int tile = blockIdx.x; live && tile < ntiles; tile += gridDim.x)
+     for (int xz0 = 0; live && xz0 < 9; xz0 += seg, ++it) {
       const uint32_t buf = it % nbuf, use = it / nbuf;
       int done = 0;
       if (lane == 0) done = mbar_wait(&acc_full[buf], use & 1, P.err, W_EPI) ? 1 : 0;
       done = __shfl_sync(0xffffffffu, done, 0);  // warp-uniform: tcgen05.ld is warp-collective
-      if (!done) break;
+      if (!done) {
+        live = false;
+        break;
+      }
       tc_fence_after();
       const int ox = (tile % ntx) * kTcTileX, oy = ((tile / ntx) % nty) * kTcTileY;
       const int oz = (tile / (ntx * nty)) * kTcTileZ;
       const int x = ox + (r & 7), y = oy + (r >> 3), z = oz;
       const bool valid = x < P.grid[0] && y < P.grid[1] && z < P.grid[2];
+      // later segments add to what this thread stored for the earlier ones
+      const bool add = P.accumulate || xz0 > 0;
       float* crow = P.C + ((((long long)z * P.grid[1] + y) * P.grid[0] + x) * P.n_cols);
       const uint32_t tbase = tmem + buf * (uint32_t)pass.tmem_cols;
       for (int g = 0; g < pass.ng; ++g) {
         const int n_mma = pass.out_nmma[g], ncols = pass.out_ncols[g], col0 = pass.out_col0[g];
-        const int t2 = pass.out_tmem2[g], t3 = pass.out_tmem3[g];
+        const int t2 = pass.out_tmem2[g], t3 = pass.out_tmem3[g], t4 = pass.out_tmem4[g];
         for (int c = 0; c < n_mma; c += 16) {
           float vv[16];
           __syncwarp();  // tcgen05.ld is warp-collective: reconverge after the masked stores
@@ -435,13 +445,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int i = 0; i < 16; ++i) vv[i] += w3[i];
           }
+          if (t4 >= 0) {
+            float w4[16];
+            tmem_ld16(tbase + lane_base + (uint32_t)(t4 + c), w4);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) vv[i] += w4[i];
+          }
           if (valid) {  // out_col0 and out_ncols are multiples of 8: whole float4s
 #pragma unroll
             for (int jj = 0; jj < 16; jj += 4)
               if (c + jj < ncols) {
                 float4* o = reinterpret_cast<float4*>(crow + col0 + c + jj);
                 float4 q4 = make_float4(vv[jj], vv[jj + 1], vv[jj + 2], vv[jj + 3]);
-                if (P.accumulate) {
+                if (add) {
                   const float4 old = *o;
                   q4.x += old.x, q4.y += old.y, q4.z += old.z, q4.w += old.w;
                 }

@@ -4,11 +4,10 @@ force, at every precision, on tensor cores and CUDA cores.
 
 Tolerances (relative L2 over all components): FP64 1e-10 (rounding order);
 FP32 1e-5 (no stencil here, so the force carries the potential's relative
-error rather than the stencil's amplification of it); bf16x3 5e-5: the split
-products are accurate to ~4e-6 of the sum of |terms| (CPU emulation of the
-schedule), and the force, unlike the potential, is a sum of terms of both
-signs -- with leaf 8 the near force of a cell sums 27 x 512 pair forces that
-largely cancel (measured: 4.9e-6 with leaf 4, 2.4e-5 with leaf 8); TF32 1e-3.
+error rather than the stencil's amplification of it); bf16x3 1e-5, the
+metric's bound (the split products are accurate to ~4e-6 of the sum of
+|terms|; the tensor cores' truncating FP32 accumulation is bounded by the
+near field's per-column accumulation segments at leaf 8); TF32 1e-3.
 """
 import numpy as np
 import pytest
@@ -20,7 +19,7 @@ torch = pytest.importorskip("torch")
 import paper_2606_13793_gb300 as fmm  # noqa: E402
 from paper_2606_13793_gb300 import _build, inputs  # noqa: E402
 
-TOL = {"fp64": 1e-10, "fp32": 1e-5, "bf16x3": 5e-5, "tf32": 1e-3}
+TOL = {"fp64": 1e-10, "fp32": 1e-5, "bf16x3": 1e-5, "tf32": 1e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -63,7 +62,9 @@ def test_analytic_accel_other_leaf_sizes(orc, leaf):
     ref = orc.fmm_accel(rho, leaf, 4)
     for prec in ("fp64", "bf16x3"):
         _, acc = solve(rho, leaf, 4, prec)
-        assert rel(acc, ref) <= TOL[prec], (leaf, prec)
+        err = rel(acc, ref)
+        print(f"leaf {leaf} {prec}: analytic accel rel err {err:.2e}")
+        assert err <= TOL[prec], (leaf, prec)
 
 
 def test_analytic_accel_full_size_sampled(orc):

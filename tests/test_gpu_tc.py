@@ -4,7 +4,10 @@ Tolerances (relative L2 of phi over all cells):
   bf16x3  <= 1e-5   the metric's bound: hi/lo bf16 splits carry ~16 bits, the
                     three products drop terms of ~2^-17 relative per product
                     (CPU emulation of the packed schedule: <= 4e-6 of the sum
-                    of |terms|), FP32 accumulation
+                    of |terms|), FP32 accumulation.  The tensor cores add into
+                    FP32 with truncation, so a same-signed sum loses about half
+                    an ulp per MMA: the near field of leaf 8 (27 x 512 terms a
+                    cell) gets one accumulator per product and two for hi*hi
   tf32    <= 1e-3   a single TF32 product has a 2^-11 relative error per
                     operand; reported, not held to the 1e-5 bound
 The FP64 coarse levels (2 .. 4) and every non-M2L step are the FP32/FP64
@@ -128,3 +131,16 @@ def test_tc_deterministic():
     plan.check()
     assert torch.equal(a, b)
     plan.close()
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (32, 48, 64)])
+def test_tc_leaf8_near_field(orc, shape):
+    """Leaf 8 on the tensor cores: 16^3 has no far field (the solve is the near
+    field alone), (32, 48, 64) adds two M2L levels.  A Plummer sphere's
+    same-signed sums are the case truncating accumulation hurts most."""
+    rho = inputs.plummer(shape, seed=6).astype(np.float64)
+    ref = orc.fmm(rho, 8, 4)["phi"]
+    phi, _ = solve(rho.astype(np.float32), 8, 4, "bf16x3")
+    err = rel_l2(phi, ref)
+    print(f"leaf 8 bf16x3 {shape}: {err:.2e}")
+    assert err <= TOL["bf16x3"]
