@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default CUDA-core contraction variants")
     ap.add_argument("--accel", default="fd", choices=["fd", "analytic"],
                     help="acceleration by the 5-point stencil of phi (fd) or from the expansions and pair forces")
+    ap.add_argument("--final-stage", default="m2l", choices=["m2l", "m2p"],
+                    help="leaf level by M2L + L2P (m2l) or by the interaction list evaluated at the cells (m2p)")
     return ap.parse_args()
 
 
@@ -92,6 +94,12 @@ def m2l_flop_level(dims, leaf, p, level):
     """Algorithmic M2L flops of one level: one multiply-add per (alpha, beta)
     pair with |alpha|+|beta| <= p per interaction-list pair (Sec. 2.3, eq. M2L)."""
     return il_total(hierarchy(dims, leaf)[level]) * 2 * m2l_pairs(p)
+
+
+def m2p_flop_leaf(dims, leaf, p):
+    """Algorithmic flops of the final-stage M2P (Sec. 4): one multiply-add per
+    multipole coefficient per cell of the target box, per interaction-list pair."""
+    return il_total(hierarchy(dims, leaf)[-1]) * 2 * math.comb(p + 3, 3) * leaf ** 3
 
 
 def algorithmic_counts(dims, leaf, p):
@@ -307,7 +315,7 @@ def main():
     rho_np = inputs.lognormal(n, seed=2606 + rank)
     rho = torch.from_numpy(rho_np).cuda()
     plan = fmm.FMMPlan((n, n, n), p, b, args.precision, dx=dx,
-                       accel="analytic" if args.accel == "analytic" else True)
+                       accel="analytic" if args.accel == "analytic" else True, final_stage=args.final_stage)
     if not args.no_autotune:
         plan.autotune()
     tuning = {str(l): list(plan.tuning(l)) for l in range(2, plan.leaf_level + 1) if plan.level_kind(l) != "tensor"}
@@ -375,7 +383,7 @@ def main():
     compare = {}
     if not args.no_compare and rank == 0:
         phi_mode = phi.double().clone()
-        p64 = fmm.FMMPlan((n, n, n), p, b, "fp64", dx=dx)
+        p64 = fmm.FMMPlan((n, n, n), p, b, "fp64", dx=dx, final_stage=args.final_stage)
         phi64 = p64.solve(rho.double())
         torch.cuda.synchronize()
         compare["rel_err_vs_fp64"] = float(torch.linalg.vector_norm(phi_mode - phi64) /
@@ -383,7 +391,7 @@ def main():
         p64.close()
         del phi64
         if args.precision != "fp32":
-            pp = fmm.FMMPlan((n, n, n), p, b, "fp32", dx=dx)
+            pp = fmm.FMMPlan((n, n, n), p, b, "fp32", dx=dx, final_stage=args.final_stage)
             if not args.no_autotune:
                 pp.autotune()
             for _ in range(3):
@@ -405,7 +413,9 @@ def main():
     kinds = {l: plan.level_kind(l) for l in range(2, L + 1)}
     flop_by = {"m2l_tc": 0, "m2l": 0}
     for l, k in kinds.items():
-        flop_by["m2l_tc" if k == "tensor" else "m2l"] += m2l_flop_level((n, n, n), b, p, l)
+        f = m2p_flop_leaf((n, n, n), b, p) if (l == L and args.final_stage == "m2p") else \
+            m2l_flop_level((n, n, n), b, p, l)
+        flop_by["m2l_tc" if k == "tensor" else "m2l"] += f
     simt64 = any(k == "fp64" for k in kinds.values())
     bf16_peak = peaks["bf16_tflops_sustained"]
     fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -434,7 +444,7 @@ def main():
     # (the FP64 levels run beside it on a side stream, so their event span
     # overstates their share); else the largest stage.
     dom = "m2l_tc" if "m2l_tc" in per_kernel else max(per_kernel, key=lambda k: per_kernel[k]["ms_per_step"])
-    workload = f"{n}^3 p={p} leaf {b} {args.precision}"
+    workload = f"{n}^3 p={p} leaf {b} {args.precision}" + (" m2p" if args.final_stage == "m2p" else "")
     traffic = profiled_traffic(dom + "/" + args.precision, workload)
     d = per_kernel[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": "TFLOP/s",
@@ -461,6 +471,7 @@ def main():
                 "config": {"workload": f"unigrid FMM {n}^3 isolated, p={p}, leaf {b}^3, lognormal P(k)~k^-2.5",
                            "precision": args.precision, "l2": "inputs larger than L2 (rho 512 MiB, outputs 2 GiB)",
                            "parallelism": f"replicas x{world}", "cuda_core_variants": tuning, "accel": args.accel,
+                           "final_stage": args.final_stage,
                            "autotuned": not args.no_autotune, **compare},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": plan.launches(True) * args.steps,
