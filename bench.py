@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default CUDA-core contraction variants")
     ap.add_argument("--accel", default="fd", choices=["fd", "analytic"],
                     help="acceleration by the 5-point stencil of phi (fd) or from the expansions and pair forces")
+    ap.add_argument("--m2l-cartesian", action="store_true",
+                    help="bf16x3: tensor-core M2L on every Cartesian component instead of the (p+1)^2 harmonic ones")
     ap.add_argument("--final-stage", default="m2l", choices=["m2l", "m2p"],
                     help="leaf level by M2L + L2P (m2l) or by the interaction list evaluated at the cells (m2p)")
     return ap.parse_args()
@@ -90,16 +92,25 @@ def hierarchy(dims, leaf):
     return ext[::-1]  # level 0 first
 
 
-def m2l_flop_level(dims, leaf, p, level):
+def m2l_pairs_harmonic(p):
+    """(alpha, beta) pairs of the harmonic M2L: both restricted to the (q+1)^2
+    components with c <= 1 of each order q, |alpha| + |beta| <= p."""
+    return sum((2 * m + 1) * (p - m + 1) ** 2 for m in range(p + 1))
+
+
+def m2l_flop_level(dims, leaf, p, level, harmonic=False):
     """Algorithmic M2L flops of one level: one multiply-add per (alpha, beta)
-    pair with |alpha|+|beta| <= p per interaction-list pair (Sec. 2.3, eq. M2L)."""
-    return il_total(hierarchy(dims, leaf)[level]) * 2 * m2l_pairs(p)
+    pair with |alpha|+|beta| <= p per interaction-list pair (Sec. 2.3, eq. M2L);
+    with harmonic compression only the pairs of the (p+1)^2 components."""
+    return il_total(hierarchy(dims, leaf)[level]) * 2 * (m2l_pairs_harmonic(p) if harmonic else m2l_pairs(p))
 
 
-def m2p_flop_leaf(dims, leaf, p):
+def m2p_flop_leaf(dims, leaf, p, harmonic=False):
     """Algorithmic flops of the final-stage M2P (Sec. 4): one multiply-add per
-    multipole coefficient per cell of the target box, per interaction-list pair."""
-    return il_total(hierarchy(dims, leaf)[-1]) * 2 * math.comb(p + 3, 3) * leaf ** 3
+    multipole coefficient (per harmonic component when compressed) per cell of
+    the target box, per interaction-list pair."""
+    ncoef = (p + 1) ** 2 if harmonic else math.comb(p + 3, 3)
+    return il_total(hierarchy(dims, leaf)[-1]) * 2 * ncoef * leaf ** 3
 
 
 def algorithmic_counts(dims, leaf, p):
@@ -315,7 +326,9 @@ def main():
     rho_np = inputs.lognormal(n, seed=2606 + rank)
     rho = torch.from_numpy(rho_np).cuda()
     plan = fmm.FMMPlan((n, n, n), p, b, args.precision, dx=dx,
-                       accel="analytic" if args.accel == "analytic" else True, final_stage=args.final_stage)
+                       accel="analytic" if args.accel == "analytic" else True, final_stage=args.final_stage,
+                       harmonic=not args.m2l_cartesian)
+    harmonic = args.precision == "bf16x3" and not args.m2l_cartesian
     if not args.no_autotune:
         plan.autotune()
     tuning = {str(l): list(plan.tuning(l)) for l in range(2, plan.leaf_level + 1) if plan.level_kind(l) != "tensor"}
@@ -413,8 +426,9 @@ def main():
     kinds = {l: plan.level_kind(l) for l in range(2, L + 1)}
     flop_by = {"m2l_tc": 0, "m2l": 0}
     for l, k in kinds.items():
-        f = m2p_flop_leaf((n, n, n), b, p) if (l == L and args.final_stage == "m2p") else \
-            m2l_flop_level((n, n, n), b, p, l)
+        hl = harmonic and k == "tensor"
+        f = m2p_flop_leaf((n, n, n), b, p, hl) if (l == L and args.final_stage == "m2p") else \
+            m2l_flop_level((n, n, n), b, p, l, hl)
         flop_by["m2l_tc" if k == "tensor" else "m2l"] += f
     simt64 = any(k == "fp64" for k in kinds.values())
     bf16_peak = peaks["bf16_tflops_sustained"]
@@ -444,7 +458,8 @@ def main():
     # (the FP64 levels run beside it on a side stream, so their event span
     # overstates their share); else the largest stage.
     dom = "m2l_tc" if "m2l_tc" in per_kernel else max(per_kernel, key=lambda k: per_kernel[k]["ms_per_step"])
-    workload = f"{n}^3 p={p} leaf {b} {args.precision}" + (" m2p" if args.final_stage == "m2p" else "")
+    workload = f"{n}^3 p={p} leaf {b} {args.precision}" + (" m2p" if args.final_stage == "m2p" else "") + \
+        (" harmonic" if harmonic else "")
     traffic = profiled_traffic(dom + "/" + args.precision, workload)
     d = per_kernel[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": "TFLOP/s",
@@ -472,6 +487,7 @@ def main():
                            "precision": args.precision, "l2": "inputs larger than L2 (rho 512 MiB, outputs 2 GiB)",
                            "parallelism": f"replicas x{world}", "cuda_core_variants": tuning, "accel": args.accel,
                            "final_stage": args.final_stage,
+                           "m2l_components": "harmonic (p+1)^2" if harmonic else "cartesian nc(p)",
                            "autotuned": not args.no_autotune, **compare},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": plan.launches(True) * args.steps,

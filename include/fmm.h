@@ -94,7 +94,15 @@ typedef struct {
                          ~6x the leaf-level work).  With 1, accel must not be 2
                          and fmm_solve_adjoint returns FMM_ERR_UNSUPPORTED
                          (the truncated M2P operator is not symmetric)          */
-  int reserved[4];    /* must be zero */
+  int m2l_cartesian;  /* FMM_M2L_BF16X3 only.  0 (default): the tensor-core
+                         M2L and M2P contract the (p+1)^2 harmonic components
+                         (multipoles folded by the Laplace identity of the
+                         derivatives of 1/r, which keeps the total order; the
+                         remaining locals rebuilt from the same identity before
+                         L2L): the same truncated operator of Sec. 2.3, eq.
+                         M2L, up to rounding, with 1.7x fewer products at
+                         p = 6.  1: all nc(p) Cartesian components            */
+  int reserved[3];    /* must be zero */
 } fmm_opts;
 
 /* Default options: FMM_FP32, n_fp64_levels = 3, accel = 1. */

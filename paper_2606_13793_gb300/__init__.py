@@ -70,7 +70,7 @@ class _Grid(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_fp64_levels", ctypes.c_int), ("accel", ctypes.c_int),
-                ("final_stage", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("final_stage", ctypes.c_int), ("m2l_cartesian", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 _lib = None
@@ -162,7 +162,8 @@ class FMMPlan:
     """One solver for a fixed grid shape, order, leaf size and precision."""
 
     def __init__(self, shape, order: int = 6, leaf: int = 4, precision: str = "fp32", dx: float = 1.0,
-                 G: float = 1.0, n_fp64_levels: int = 3, accel=True, final_stage: str = "m2l", stream=None):
+                 G: float = 1.0, n_fp64_levels: int = 3, accel=True, final_stage: str = "m2l", harmonic=True,
+                 stream=None):
         import torch
 
         self.lib = load()
@@ -184,6 +185,9 @@ class FMMPlan:
         # final_stage: "m2l" (M2L + L2P at the leaf level) or "m2p" (the
         # paper's final stage: M2P at the cell centres)
         opts.final_stage = 1 if final_stage == "m2p" else 0
+        # harmonic: bf16x3 tensor-core M2L/M2P on the (p+1)^2 harmonic
+        # components (False: every Cartesian component)
+        opts.m2l_cartesian = 0 if harmonic else 1
         handle = ctypes.c_void_p()
         _check(self.lib, self.lib.fmm_plan(ctypes.byref(grid), self.order, self.leaf, ctypes.byref(opts),
                                            _stream_handle(stream), ctypes.byref(handle)))

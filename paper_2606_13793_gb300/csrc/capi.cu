@@ -105,6 +105,16 @@ int level_of_order(const MultiIndex& mi, int k) { return mi.a[k] + mi.b[k] + mi.
 
 int ncoef(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 
+// Harmonic (c <= 1) components in reduced order (order, then b + c, then c):
+// the canonical index of each; their count up to order q is (q + 1)^2.
+std::vector<int> harmonic_components(const MultiIndex& mi) {
+  std::vector<int> r;
+  for (int n = 0; n <= mi.p; ++n)
+    for (int s = 0; s <= n; ++s)
+      for (int c = 0; c <= 1 && c <= s; ++c) r.push_back(mi.index(n - s, s - c, c));
+  return r;
+}
+
 enum Stage {
   ST_CHECK = 0,
   ST_P2M,
@@ -161,6 +171,9 @@ struct fmm_plan_s {
   int near_ntiles = 0;
   // tensor-core M2L and near field
   int tc_kind = -1;
+  bool harm = false;  // harmonic compression of the bf16x3 tensor-core M2L/M2P (planes of nr components)
+  int nr = 0;         // (p + 1)^2
+  int plane_nc() const { return harm ? nr : nc; }
   TcLaunch tc{};
   bool near_tc = false;
   std::vector<TcLaunch> tcn;  // near field: kTcMaxPasses passes per launch
@@ -717,14 +730,17 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
 }
 
 // M2L groups: order blocks (orders 0 and 1 merged), each with the prefix
-// 8 nc(p - lowest order), split into pieces of <= 128 columns.
-bool build_tc(const MultiIndex& mi, const TaylorTable& tt, int kind, TcHost& H) {
+// 8 nc(p - lowest order), split into pieces of <= 128 columns.  harm: rows
+// and columns are the harmonic components only ((q + 1)^2 up to order q; the
+// multipoles arrive folded and the epilogue's column map places the locals).
+bool build_tc(const MultiIndex& mi, const TaylorTable& tt, int kind, TcHost& H, bool harm) {
   const int p = mi.p;
+  auto count = [harm](int q) { return harm ? (q + 1) * (q + 1) : ncoef(q); };
   std::vector<TcCols> gs;
   for (int m = 0; m <= p;) {
     const int o_hi = (m == 0 && p >= 1) ? 1 : m;
-    const int col0 = m == 0 ? 0 : 8 * ncoef(m - 1), col1 = 8 * ncoef(o_hi);
-    const int K = 8 * ncoef(p - m);
+    const int col0 = m == 0 ? 0 : 8 * count(m - 1), col1 = 8 * count(o_hi);
+    const int K = 8 * count(p - m);
     const int total = col1 - col0;
     const int pieces = (total + kTcMaxGroupN - 1) / kTcMaxGroupN;
     const int per = ((total + pieces - 1) / pieces + 15) / 16 * 16;
@@ -734,7 +750,12 @@ bool build_tc(const MultiIndex& mi, const TaylorTable& tt, int kind, TcHost& H) 
   // Two activation stages (the boxes have a producer thread of their own);
   // the weight rings take the rest of shared memory: the kernel is bound by
   // the number of weight tiles in flight against the L2 round trip.
-  auto entry = [&](int d, int k, int n) { return m2l_entry(mi, tt, d, k, n); };
+  const std::vector<int> red = harmonic_components(mi);
+  auto entry = [&](int d, int k, int n) {
+    if (!harm) return m2l_entry(mi, tt, d, k, n);
+    if (k / 8 >= (int)red.size() || n / 8 >= (int)red.size()) return 0.0;
+    return m2l_entry(mi, tt, d, red[k / 8] * 8 + k % 8, red[n / 8] * 8 + n % 8);
+  };
   return build_tc_generic(kind, gs, entry, H, 2);
 }
 
@@ -822,11 +843,19 @@ double m2p_entry(const MultiIndex& mi, const M2pTable& tab, int d, int k, int n)
 // Tensor-core schedule of the M2P contraction: every output column needs the
 // whole reduction (no truncation prefix), so groups of up to 128 columns
 // share one K = 8 nc; one pass for b <= 4.
-bool build_tc_m2p(const MultiIndex& mi, const M2pTable& tab, int kind, TcHost& H) {
+bool build_tc_m2p(const MultiIndex& mi, const M2pTable& tab, int kind, TcHost& H, bool harm) {
   const int ncol = 8 * tab.b * tab.b * tab.b;
+  const std::vector<int> red = harmonic_components(mi);
+  const int K = 8 * (harm ? (int)red.size() : mi.nc);
   std::vector<TcCols> gs;
-  for (int c = 0; c < ncol; c += kTcMaxGroupN) gs.push_back({c, std::min(kTcMaxGroupN, ncol - c), 8 * mi.nc});
-  auto entry = [&](int d, int k, int n) { return m2p_entry(mi, tab, d, k, n); };
+  for (int c = 0; c < ncol; c += kTcMaxGroupN) gs.push_back({c, std::min(kTcMaxGroupN, ncol - c), K});
+  // with harmonic planes the reduction runs over the folded components (the
+  // M2P weights, derivatives of 1/r in alpha, fold the same way)
+  auto entry = [&](int d, int k, int n) {
+    if (!harm) return m2p_entry(mi, tab, d, k, n);
+    if (k / 8 >= (int)red.size()) return 0.0;
+    return m2p_entry(mi, tab, d, red[k / 8] * 8 + k % 8, n);
+  };
   return build_tc_generic(kind, gs, entry, H, 2);
 }
 
@@ -955,6 +984,9 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
   // the leaf level) and tcgen05 M2L on every other level.
   const bool tcp = tc_precision(o.precision);
   if (tcp) P->tc_kind = o.precision == FMM_M2L_BF16X3 ? TC_BF16X3 : TC_TF32;
+  P->nr = (order + 1) * (order + 1);
+  P->harm = tcp && P->tc_kind == TC_BF16X3 && !o.m2l_cartesian && order >= 2 &&
+            P->nr <= kTcMaxColMap;
   for (int l = 0; l <= P->L; ++l) {
     Level& lv = P->lev[l];
     lv.f64 = P->f64_data() ? 1 : 0;
@@ -977,7 +1009,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     off = align(off + lv.bytes);
     lv.hi_off = lv.lo_off = 0;
     if (lv.tc && P->tc_kind == TC_BF16X3) {
-      const size_t plane = (size_t)lv.npar * 8 * P->nc * 2;
+      const size_t plane = (size_t)lv.npar * 8 * P->plane_nc() * 2;
       lv.hi_off = off;
       off = align(off + plane);
       lv.lo_off = off;
@@ -1092,7 +1124,8 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     if ((st = P->upload(tk, &P->d_m2l_tile_k, s)) || (st = P->upload(tw, &P->d_m2l_tile_w, s))) return cleanup(st);
     if (anytc) {
       TcHost H;
-      if (!build_tc(P->mi, tt, P->tc_kind, H)) return cleanup(fail(FMM_ERR_UNSUPPORTED, "order too high for the tensor-core schedule"));
+      if (!build_tc(P->mi, tt, P->tc_kind, H, P->harm))
+        return cleanup(fail(FMM_ERR_UNSUPPORTED, "order too high for the tensor-core schedule"));
       unsigned char* dw = nullptr;
       if ((st = P->upload(H.W, &dw, s))) return cleanup(st);
       P->tc.W = dw;
@@ -1101,14 +1134,20 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
       for (int i = 0; i < H.npass; ++i) P->tc.pass[i] = H.pass[i];
       P->tc.n_cols = 8 * P->nc;
       P->tc.kind = P->tc_kind;
+      P->tc.col_mapped = P->harm ? 1 : 0;
+      if (P->harm) {
+        const std::vector<int> red = harmonic_components(P->mi);
+        for (size_t r = 0; r < red.size(); ++r) P->tc.col_map[r] = (int16_t)red[r];
+      }
       P->tc.err = nullptr;  // set below, after the flag exists
       for (int l = 2; l <= P->L; ++l) {
         const Level& lv = P->lev[l];
         if (!lv.tc) continue;
         cudaError_t e;
         if (P->tc_kind == TC_BF16X3) {
-          e = make_row_map(P->map_hi[l], P->arena + lv.hi_off, 8 * P->nc, 2, lv.np, 64);
-          if (e == cudaSuccess) e = make_row_map(P->map_lo[l], P->arena + lv.lo_off, 8 * P->nc, 2, lv.np, 64);
+          e = make_row_map(P->map_hi[l], P->arena + lv.hi_off, 8 * P->plane_nc(), 2, lv.np, 64);
+          if (e == cudaSuccess)
+            e = make_row_map(P->map_lo[l], P->arena + lv.lo_off, 8 * P->plane_nc(), 2, lv.np, 64);
         } else {
           e = make_row_map(P->map_hi[l], P->arena + lv.m_off, 8 * P->nc, 4, lv.np, 32);
           if (e == cudaSuccess) std::memcpy(P->map_lo[l], P->map_hi[l], 128);
@@ -1143,7 +1182,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     const Level& lf = P->lev[P->L];
     if (lf.tc) {
       TcHost H;
-      if (build_tc_m2p(P->mi, tab, P->tc_kind, H)) {
+      if (build_tc_m2p(P->mi, tab, P->tc_kind, H, P->harm)) {
         unsigned char* dw = nullptr;
         if ((st = P->upload(H.W, &dw, s))) return cleanup(st);
         TcLaunch& T = P->tcm;
@@ -1275,6 +1314,7 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
   if (o.final_stage < 0 || o.final_stage > 1) return fail(FMM_ERR_ARG, "final_stage %d not in {0, 1}", o.final_stage);
   if (o.final_stage == 1 && o.accel == 2)
     return fail(FMM_ERR_UNSUPPORTED, "the analytic acceleration is built for final_stage = 0 only");
+  if (o.m2l_cartesian < 0 || o.m2l_cartesian > 1) return fail(FMM_ERR_ARG, "m2l_cartesian %d not in {0, 1}", o.m2l_cartesian);
   for (int r : o.reserved)
     if (r != 0) return fail(FMM_ERR_ARG, "reserved option fields must be zero");
   int dev = 0;
@@ -1336,31 +1376,39 @@ fmm_status do_m2m(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s) {
   cudaError_t e;
   if (c.f64)
     e = launch_m2m<double, double>(tt, c, static_cast<const double*>(P->M(l)), q, static_cast<double*>(P->M(l - 1)),
-                                   nullptr, nullptr, s);
+                                   nullptr, nullptr, 0, s);
   else if (q.f64)
     e = launch_m2m<float, double>(tt, c, static_cast<const float*>(P->M(l)), q, static_cast<double*>(P->M(l - 1)),
-                                  nullptr, nullptr, s);
+                                  nullptr, nullptr, 0, s);
   else
     e = launch_m2m<float, float>(tt, c, static_cast<const float*>(P->M(l)), q, static_cast<float*>(P->M(l - 1)), hi,
-                                 lo, s);
+                                 lo, P->harm ? 1 : 0, s);
   CUDA_TRY(e);
   return FMM_OK;
 }
 
 // L(l) += L2L(L(l - 1)) for l >= 3; the level's M2L has written L(l) (level 2
 // has no parent far field: its locals are its M2L alone).
+// A harmonic tensor-core M2L wrote only the c <= 1 locals: L2L rebuilds the
+// rest first.  l == 2 (no parent far field) with a harmonic M2L: the rebuild
+// alone (no parent locals).
+bool harmonic_m2l_level(fmm_plan_t P, int l) { return P->harm && P->lev[l].tc && !(l == P->L && P->m2p); }
+
 fmm_status do_l2l(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s, int accumulate) {
   const Level &q = P->lev[l - 1], &c = P->lev[l];
+  const int harm = accumulate && harmonic_m2l_level(P, l) ? 1 : 0;
   cudaError_t e;
-  if (q.f64 && c.f64) {
+  if (l == 2) {
+    e = launch_l2l<float, float>(tt, q, nullptr, c, static_cast<float*>(P->Lx(l)), 1, harm, s);
+  } else if (q.f64 && c.f64) {
     e = launch_l2l<double, double>(tt, q, static_cast<const double*>(P->Lx(l - 1)), c, static_cast<double*>(P->Lx(l)),
-                                   accumulate, s);
+                                   accumulate, 0, s);
   } else if (q.f64) {
     e = launch_l2l<double, float>(tt, q, static_cast<const double*>(P->Lx(l - 1)), c, static_cast<float*>(P->Lx(l)),
-                                  accumulate, s);
+                                  accumulate, harm, s);
   } else {
     e = launch_l2l<float, float>(tt, q, static_cast<const float*>(P->Lx(l - 1)), c, static_cast<float*>(P->Lx(l)),
-                                 accumulate, s);
+                                 accumulate, harm, s);
   }
   CUDA_TRY(e);
   return FMM_OK;
@@ -1458,7 +1506,8 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
     CUDA_TRY(launch_p2m<T>(tt, rho, P->dims, lf, static_cast<T*>(P->M(L)), P->near_tc ? nullptr : rho_box,
                            mplanes ? P->arena + lf.hi_off : nullptr, mplanes ? P->arena + lf.lo_off : nullptr,
                            P->near_tc ? P->arena + P->rho_hi_off : nullptr,
-                           P->near_tc ? P->arena + P->rho_lo_off : nullptr, P->d_flag, s));
+                           P->near_tc ? P->arena + P->rho_lo_off : nullptr, P->d_flag,
+                           (mplanes && P->harm) ? 1 : 0, s));
   }
   for (int l = L; l >= 3; --l) {
     StageTimer t(P, ST_M2M, s);
@@ -1508,6 +1557,10 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
     CUDA_TRY(launch_nbr_gemm<T>(near_gemm(P), s));
   }
   if (fork) CUDA_TRY(cudaStreamWaitEvent(s, P->ev_join, 0));
+  if (L >= 2 && harmonic_m2l_level(P, 2)) {  // level 2 locals are its M2L alone: rebuild
+    StageTimer t(P, ST_L2L, s);
+    if ((st = do_l2l(P, tt, 2, s, 1))) return st;
+  }
   for (int l = 3; l <= L; ++l) {
     StageTimer t(P, ST_L2L, s);
     // with the final-stage M2P the leaf locals are the parent's shifted locals alone
@@ -1640,6 +1693,7 @@ int fmm_solve_launches(fmm_plan_t P, int with_accel) {
   if (L < 2) n += 1;                    // zero the leaf locals
   for (int l = 2; l <= L; ++l) {
     n += l >= 3 ? 2 : 1;                // M2L, and L2L below level 2
+    if (l == 2 && harmonic_m2l_level(P, 2)) n += 1;  // rebuild of the harmonic level-2 locals
     if (!P->lev[l].tc && P->m2l_choice[l].dsplit > 1 && !(l == L && P->m2p)) n += 1;  // partial-sum reduction
   }
   n += P->near_tc ? (int)P->tcn.size() + 1 : 2;  // near field + leaf finish

@@ -106,17 +106,22 @@ struct TreeTables {
 // P2M: Mleaf always; rho_box (FP32/FP64 near field) and the bf16 hi/lo planes
 // (Mhi/Mlo for a tensor-core leaf level, rho_hi/rho_lo for the tensor-core
 // near field) when non-NULL.  Sets bit 0 of *flag for a non-finite density.
+// harm = 1: the planes hold the harmonic ((p+1)^2, c <= 1) components of the
+// folded multipoles (tree_common.cuh), rows of 8 (p+1)^2 values per parent.
 template <typename T>
 cudaError_t launch_p2m(const TreeTables& t, const T* rho, const int dims[3], const Level& leaf, T* Mleaf, T* rho_box,
-                       void* Mhi, void* Mlo, void* rho_hi, void* rho_lo, int* flag, cudaStream_t s);
-// M2M into the parent level; Mhi/Mlo (bf16 planes of the parent) when non-NULL.
+                       void* Mhi, void* Mlo, void* rho_hi, void* rho_lo, int* flag, int harm, cudaStream_t s);
+// M2M into the parent level; Mhi/Mlo (bf16 planes of the parent, harmonic
+// components when harm = 1) when non-NULL.
 template <typename Tc, typename Tp>
 cudaError_t launch_m2m(const TreeTables& t, const Level& child, const Tc* Mc, const Level& par, Tp* Mp, void* Mhi,
-                       void* Mlo, cudaStream_t s);
+                       void* Mlo, int harm, cudaStream_t s);
 template <typename Tp, typename Tc>
-// accumulate = 1: child locals += shifted parent locals (after the level's M2L wrote them)
+// accumulate = 1: child locals += shifted parent locals (after the level's M2L wrote them);
+// harm = 1: that M2L wrote only the harmonic components, the rest are rebuilt;
+// Lp = NULL: no parent locals (only the rebuild)
 cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, const Level& child, Tc* Lc, int accumulate,
-                       cudaStream_t s);
+                       int harm, cudaStream_t s);
 template <typename T>
 cudaError_t launch_zero(T* p, size_t count, cudaStream_t s);
 // near_box rows hold near_stride values per leaf box, the potential sums first.
@@ -166,10 +171,15 @@ constexpr int kTcMaxGroups = 12;    // output column groups per pass
 constexpr int kTcMaxChunks = 48;    // 128-byte reduction chunks per neighbour
 constexpr int kTcMaxSpans = 128;    // MMA spans per pass (all chunks)
 constexpr int kTcMaxSpanN = 128;    // columns of one span (one MMA instruction)
+constexpr int kTcMaxColMap = 96;    // reduced coefficients of a column map ((p+1)^2, p <= 8)
 // Shared memory of the tensor-core kernel: barriers (2 KB), then the
 // activation stages (one 144-row box per plane, 18 KB a plane), then the
-// weight rings, which take what the stages leave.
-constexpr int kTcSmemUsable = 226 * 1024;
+// weight rings, which take what the stages leave.  4 KB short of the SM's
+// 228 KB so that CUDA-core blocks of the concurrent FP64 levels (no shared
+// memory, 1 KB reserved each) fit beside a tensor-core CTA: its 13 warps
+// leave half the register file and the DFMA units idle (8.6 vs 9.8 ms per
+// 512^3 bf16x3 step against 226 KB).
+constexpr int kTcSmemUsable = 222 * 1024;
 constexpr int kTcMaxAStages = 8;
 constexpr int kTcAPlaneBytes = kTcTileX * kTcBoxY * 128;
 inline int tc_ring_budget(int kind, int a_stages) {
@@ -227,6 +237,11 @@ struct TcLaunch {
   int grid[3];     // parent grid
   int kind;
   int* err;
+  // col_mapped = 1: output column n (a reduced coefficient r = n / 8, child
+  // n % 8) lands in C column col_map[r] * 8 + n % 8 (harmonic M2L: the full
+  // local rows receive the c <= 1 components)
+  int col_mapped;
+  int16_t col_map[kTcMaxColMap];
 };
 
 // Builds a 4-D TMA map over one level's parent-blocked rows (one plane).

@@ -11,10 +11,12 @@ using namespace tree;
 // L2L (Sec. 2.3, eq. L2L, parent centre -> child centre), scaled:
 //   Lt_beta(C) = sum_{gamma >= beta} C(gamma,beta) 2^(-1-|gamma|) (+-1/2)^(gamma-beta) Lt_gamma(P)
 // Adds to the children's block, which the level's M2L has already written
-// (accumulate = 0 overwrites it instead).
+// (accumulate = 0 overwrites it instead).  harm = 1: the M2L wrote only the
+// harmonic components (c <= 1); the others are rebuilt from them first.
+// Lp = NULL: no parent locals (the coarsest level: only the rebuild).
 template <int P, typename Tp, typename Tc>
 __global__ void __launch_bounds__(kThreads) l2l_kernel(Level par, const Tp* __restrict__ Lp, Level child,
-                                                       Tc* __restrict__ Lc, int accumulate) {
+                                                       Tc* __restrict__ Lc, int accumulate, int harm) {
   constexpr int NC = ncoef_c(P);
   const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
   const long long p = t >> 3;  // box of the parent level == parent block of the child level
@@ -25,42 +27,62 @@ __global__ void __launch_bounds__(kThreads) l2l_kernel(Level par, const Tp* __re
   const int pz = (int)(p / ((long long)par.n[0] * par.n[1]));
   const long long gp = ((long long)(pz >> 1) * par.np[1] + (py >> 1)) * par.np[0] + (px >> 1);
   const int cp = (px & 1) | ((py & 1) << 1) | ((pz & 1) << 2);
-  const Tp* src = Lp + gp * 8 * NC + cp;
   Tp L[NC];
+  if (Lp) {
+    const Tp* src = Lp + gp * 8 * NC + cp;
 #pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    const int n = (k >= 1) + (k >= 4) + (k >= 10) + (k >= 20) + (k >= 35) + (k >= 56) + (k >= 84) + (k >= 120);
-    L[k] = src[k * 8] * Tp(1.0 / (double)(2 << n));  // 2^(-1-|gamma|)
+    for (int k = 0; k < NC; ++k) {
+      const int n = (k >= 1) + (k >= 4) + (k >= 10) + (k >= 20) + (k >= 35) + (k >= 56) + (k >= 84) + (k >= 120);
+      L[k] = src[k * 8] * Tp(1.0 / (double)(2 << n));  // 2^(-1-|gamma|)
+    }
+    Tp dp[P + 1];
+    powers<P, Tp>(half_offset<Tp>(c, 0), dp);
+    shift_down<P, 0, Tp>(L, dp);
+    powers<P, Tp>(half_offset<Tp>(c, 1), dp);
+    shift_down<P, 1, Tp>(L, dp);
+    powers<P, Tp>(half_offset<Tp>(c, 2), dp);
+    shift_down<P, 2, Tp>(L, dp);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) L[k] = Tp(0);
   }
-  Tp dp[P + 1];
-  powers<P, Tp>(half_offset<Tp>(c, 0), dp);
-  shift_down<P, 0, Tp>(L, dp);
-  powers<P, Tp>(half_offset<Tp>(c, 1), dp);
-  shift_down<P, 1, Tp>(L, dp);
-  powers<P, Tp>(half_offset<Tp>(c, 2), dp);
-  shift_down<P, 2, Tp>(L, dp);
   Tc* dst = Lc + p * 8 * NC + c;
+  bool rebuild = false;
+  if constexpr (sizeof(Tc) == 4) rebuild = accumulate && harm;  // harmonic M2L levels are FP32
+  if (rebuild) {
+    Tc Lm[NC];
 #pragma unroll
-  for (int k = 0; k < NC; ++k) dst[k * 8] = accumulate ? Tc(dst[k * 8] + Tc(L[k])) : Tc(L[k]);
+    for (int n = 0; n <= P; ++n)
+#pragma unroll
+      for (int s = 0; s <= n; ++s)
+#pragma unroll
+        for (int cc = 0; cc <= 1 && cc <= s; ++cc) Lm[cidx(n - s, s - cc, cc)] = dst[cidx(n - s, s - cc, cc) * 8];
+    harmonic_expand<P, Tc>(Lm);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) dst[k * 8] = Tc(Lm[k] + Tc(L[k]));
+  } else {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) dst[k * 8] = accumulate ? Tc(dst[k * 8] + Tc(L[k])) : Tc(L[k]);
+  }
 }
 
 }  // namespace
 
 template <typename Tp, typename Tc>
 cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, const Level& child, Tc* Lc, int accumulate,
-                       cudaStream_t s) {
+                       int harm, cudaStream_t s) {
   const long long threads = par.nbox * 8;
   if (threads == 0) return cudaSuccess;
-  FMM_ORDER_SWITCH(t.p,
-                   (l2l_kernel<PP, Tp, Tc><<<grid_threads(threads), kThreads, 0, s>>>(par, Lp, child, Lc, accumulate)));
+  FMM_ORDER_SWITCH(t.p, (l2l_kernel<PP, Tp, Tc><<<grid_threads(threads), kThreads, 0, s>>>(par, Lp, child, Lc,
+                                                                                          accumulate, harm)));
   return cudaGetLastError();
 }
 
 template cudaError_t launch_l2l<float, float>(const TreeTables&, const Level&, const float*, const Level&, float*, int,
-                                              cudaStream_t);
+                                              int, cudaStream_t);
 template cudaError_t launch_l2l<double, double>(const TreeTables&, const Level&, const double*, const Level&,
-                                                double*, int, cudaStream_t);
+                                                double*, int, int, cudaStream_t);
 template cudaError_t launch_l2l<double, float>(const TreeTables&, const Level&, const double*, const Level&, float*,
-                                               int, cudaStream_t);
+                                               int, int, cudaStream_t);
 
 }  // namespace fmmgb

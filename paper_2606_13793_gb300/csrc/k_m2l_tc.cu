@@ -455,7 +455,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int jj = 0; jj < 16; jj += 4)
               if (c + jj < ncols) {
-                float4* o = reinterpret_cast<float4*>(crow + col0 + c + jj);
+                int col = col0 + c + jj;
+                if (P.col_mapped) col = (int)P.col_map[col >> 3] * 8 + (col & 7);
+                float4* o = reinterpret_cast<float4*>(crow + col);
                 float4 q4 = make_float4(vv[jj], vv[jj + 1], vv[jj + 2], vv[jj + 3]);
                 if (add) {
                   const float4 old = *o;

@@ -14,7 +14,7 @@ using namespace tree;
 template <int P, typename Tc, typename Tp>
 __global__ void __launch_bounds__(kThreads) m2m_kernel(Level child, const Tc* __restrict__ Mc, Level par,
                                                        Tp* __restrict__ Mp, __nv_bfloat16* __restrict__ Mhi,
-                                                       __nv_bfloat16* __restrict__ Mlo) {
+                                                       __nv_bfloat16* __restrict__ Mlo, int harm) {
   constexpr int NC = ncoef_c(P);
   const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
   const long long p = t >> 3;
@@ -47,34 +47,61 @@ __global__ void __launch_bounds__(kThreads) m2m_kernel(Level child, const Tc* __
   const long long gp = ((long long)(pz >> 1) * par.np[1] + (py >> 1)) * par.np[0] + (px >> 1);
   const int cp = (px & 1) | ((py & 1) << 1) | ((pz & 1) << 2);
   Tp* dst = Mp + gp * 8 * NC + cp;
-  // sibling lanes share the writes: lane c stores coefficients c, c+8, ...
+  bool fold = false;
+  if constexpr (sizeof(Tp) == 4) fold = Mhi && harm;  // planes exist for FP32 levels only
+  if (!fold) {
+    // sibling lanes share the writes: lane c stores coefficients c, c+8, ...
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      if ((k & 7) != c) continue;
+      const int n = (k >= 1) + (k >= 4) + (k >= 10) + (k >= 20) + (k >= 35) + (k >= 56) + (k >= 84) + (k >= 120);
+      const Tp v = M[k] * Tp(1.0 / (double)(1 << n));  // 2^-|alpha|
+      dst[k * 8] = v;
+      if (Mhi) store_split(Mhi, Mlo, (size_t)(gp * 8 * NC + cp + k * 8), v);
+    }
+    return;
+  }
+  // harmonic planes: every lane scales and folds the whole expansion, then
+  // stores its share of the FP32 row and of the (p+1)^2 folded components
+  // ([parent][reduced coef][child])
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
-    if ((k & 7) != c) continue;
     const int n = (k >= 1) + (k >= 4) + (k >= 10) + (k >= 20) + (k >= 35) + (k >= 56) + (k >= 84) + (k >= 120);
-    const Tp v = M[k] * Tp(1.0 / (double)(1 << n));  // 2^-|alpha|
-    dst[k * 8] = v;
-    if (Mhi) store_split(Mhi, Mlo, (size_t)(gp * 8 * NC + cp + k * 8), v);
+    M[k] *= Tp(1.0 / (double)(1 << n));  // 2^-|alpha|
+    if ((k & 7) == c) dst[k * 8] = M[k];
   }
+  constexpr int NR = nred_c(P);
+  harmonic_fold<P, Tp>(M);
+  int r = 0;
+#pragma unroll
+  for (int n = 0; n <= P; ++n)
+#pragma unroll
+    for (int s = 0; s <= n; ++s)
+#pragma unroll
+      for (int cc = 0; cc <= 1 && cc <= s; ++cc) {
+        if ((r & 7) == c) store_split(Mhi, Mlo, (size_t)(gp * 8 * NR + cp + r * 8), M[cidx(n - s, s - cc, cc)]);
+        ++r;
+      }
 }
 
 }  // namespace
 
 template <typename Tc, typename Tp>
 cudaError_t launch_m2m(const TreeTables& t, const Level& child, const Tc* Mc, const Level& par, Tp* Mp, void* Mhi,
-                       void* Mlo, cudaStream_t s) {
+                       void* Mlo, int harm, cudaStream_t s) {
   const long long threads = child.npar * 8;
   if (threads == 0) return cudaSuccess;
   FMM_ORDER_SWITCH(t.p, (m2m_kernel<PP, Tc, Tp><<<grid_threads(threads), kThreads, 0, s>>>(
-                            child, Mc, par, Mp, static_cast<__nv_bfloat16*>(Mhi), static_cast<__nv_bfloat16*>(Mlo))));
+                            child, Mc, par, Mp, static_cast<__nv_bfloat16*>(Mhi), static_cast<__nv_bfloat16*>(Mlo),
+                            harm)));
   return cudaGetLastError();
 }
 
 template cudaError_t launch_m2m<float, float>(const TreeTables&, const Level&, const float*, const Level&, float*,
-                                              void*, void*, cudaStream_t);
+                                              void*, void*, int, cudaStream_t);
 template cudaError_t launch_m2m<double, double>(const TreeTables&, const Level&, const double*, const Level&,
-                                                double*, void*, void*, cudaStream_t);
+                                                double*, void*, void*, int, cudaStream_t);
 template cudaError_t launch_m2m<float, double>(const TreeTables&, const Level&, const float*, const Level&, double*,
-                                               void*, void*, cudaStream_t);
+                                               void*, void*, int, cudaStream_t);
 
 }  // namespace fmmgb

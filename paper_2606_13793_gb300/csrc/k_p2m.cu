@@ -29,9 +29,9 @@ __host__ __device__ constexpr int ncoef_parity(int h) {
 
 template <int P, typename T, int h>
 __device__ __forceinline__ void p2m_body(const Box& B, const T* __restrict__ rho, int nx, int ny, int b,
-                                         const Level& leaf, T* __restrict__ Ms, T* __restrict__ rho_box,
-                                         __nv_bfloat16* __restrict__ rhi, __nv_bfloat16* __restrict__ rlo,
-                                         int* __restrict__ flag) {
+                                         const Level& leaf, T* __restrict__ Ms, T* __restrict__ Mr,
+                                         T* __restrict__ rho_box, __nv_bfloat16* __restrict__ rhi,
+                                         __nv_bfloat16* __restrict__ rlo, int* __restrict__ flag) {
   constexpr int NC = ncoef_c(P);
   constexpr int NH = ncoef_parity<P>(h);
   T acc[NH > 0 ? NH : 1];  // this thread's coefficients, in canonical order restricted to parity h of c
@@ -151,6 +151,32 @@ __device__ __forceinline__ void p2m_body(const Box& B, const T* __restrict__ rho
         dst[cidx(a, bb, cc) * 8] = acc[q];
         ++q;
       }
+  if constexpr (sizeof(T) == 4)  // planes exist for FP32 leaf levels only
+  if (Mr) {
+    // harmonic planes: this thread's parity class folds onto c = h (the fold
+    // keeps the parity of c), staged as [parent][reduced coef][child]
+    constexpr int NR = nred_c(P);
+    T f[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) f[k] = T(0);
+    int r = 0;
+#pragma unroll
+    for (int n = 0; n <= P; ++n)
+#pragma unroll
+      for (int bc = 0; bc <= n; ++bc)
+#pragma unroll
+        for (int cc = 0; cc <= bc; ++cc) {
+          if ((cc & 1) != h) continue;
+          f[cidx(n - bc, bc - cc, cc)] = acc[r];
+          ++r;
+        }
+    harmonic_fold<P, T>(f);
+    T* dr = Mr + (B.par & (kP2mParents - 1)) * (8 * NR + 8) + B.c;
+#pragma unroll
+    for (int n = h; n <= P; ++n)
+#pragma unroll
+      for (int s = h; s <= n; ++s) dr[ridx(n - s, s - h, h) * 8] = f[cidx(n - s, s - h, h)];
+  }
 }
 
 // A block (256 threads, 128 boxes) covers kP2mParents whole parents, so its
@@ -161,20 +187,23 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho
                                                        T* __restrict__ Mleaf, __nv_bfloat16* __restrict__ Mhi,
                                                        __nv_bfloat16* __restrict__ Mlo, T* __restrict__ rho_box,
                                                        __nv_bfloat16* __restrict__ rhi,
-                                                       __nv_bfloat16* __restrict__ rlo, int* __restrict__ flag) {
+                                                       __nv_bfloat16* __restrict__ rlo, int* __restrict__ flag,
+                                                       int harm) {
   constexpr int NC = ncoef_c(P);
   constexpr int ROW = 8 * NC;     // values per parent row
   constexpr int ROWP = ROW + 8;   // staged row pitch
+  constexpr int ROWR = 8 * nred_c(P);  // values per parent row of the harmonic planes
   extern __shared__ __align__(16) unsigned char p2m_smem[];
   T* Ms = reinterpret_cast<T*>(p2m_smem);
+  T* Mr = (harm && Mhi) ? Ms + kP2mParents * ROWP : nullptr;
   const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
   const long long w = t >> 5;
   const Box B = box_of(leaf, (w >> 1) * 32 + (t & 31));
   if (B.par < leaf.npar) {
     if (w & 1)
-      p2m_body<P, T, 1>(B, rho, nx, ny, b, leaf, Ms, rho_box, rhi, rlo, flag);
+      p2m_body<P, T, 1>(B, rho, nx, ny, b, leaf, Ms, Mr, rho_box, rhi, rlo, flag);
     else
-      p2m_body<P, T, 0>(B, rho, nx, ny, b, leaf, Ms, rho_box, rhi, rlo, flag);
+      p2m_body<P, T, 0>(B, rho, nx, ny, b, leaf, Ms, Mr, rho_box, rhi, rlo, flag);
   }
   __syncthreads();
   const long long p0 = (long long)blockIdx.x * kP2mParents;
@@ -192,8 +221,12 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho
     for (int i = threadIdx.x; i < count; i += kThreads) Mleaf[g0 + i] = Ms[(i / ROW) * ROWP + i % ROW];
   }
   if (Mhi) {  // 8 values -> 16 bytes of hi and 16 bytes of lo
-    for (int i = threadIdx.x; i < count / 8; i += kThreads) {
-      const T* v = Ms + (i / (ROW / 8)) * ROWP + (i % (ROW / 8)) * 8;
+    const int rl = Mr ? ROWR : ROW, rp = Mr ? ROWR + 8 : ROWP;
+    const T* src = Mr ? Mr : Ms;
+    const int pc = (int)np * rl;
+    const long long h0 = p0 * rl;
+    for (int i = threadIdx.x; i < pc / 8; i += kThreads) {
+      const T* v = src + (i / (rl / 8)) * rp + (i % (rl / 8)) * 8;
       __nv_bfloat16 hh[8], ll[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -201,41 +234,50 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho
         hh[q] = __float2bfloat16_rn(x);
         ll[q] = __float2bfloat16_rn(x - __bfloat162float(hh[q]));
       }
-      reinterpret_cast<uint4*>(Mhi + g0)[i] = *reinterpret_cast<const uint4*>(hh);
-      reinterpret_cast<uint4*>(Mlo + g0)[i] = *reinterpret_cast<const uint4*>(ll);
+      reinterpret_cast<uint4*>(Mhi + h0)[i] = *reinterpret_cast<const uint4*>(hh);
+      reinterpret_cast<uint4*>(Mlo + h0)[i] = *reinterpret_cast<const uint4*>(ll);
     }
   }
 }
 
 template <int P, typename T>
-void p2m_launch(unsigned blocks, cudaStream_t s, const T* rho, int nx, int ny, int b, Level leaf, T* Mleaf,
-                __nv_bfloat16* Mhi, __nv_bfloat16* Mlo, T* rho_box, __nv_bfloat16* rhi, __nv_bfloat16* rlo, int* flag) {
-  constexpr size_t smem = (size_t)kP2mParents * (8 * ncoef_c(P) + 8) * sizeof(T);
+cudaError_t p2m_launch(unsigned blocks, cudaStream_t s, const T* rho, int nx, int ny, int b, Level leaf, T* Mleaf,
+                __nv_bfloat16* Mhi, __nv_bfloat16* Mlo, T* rho_box, __nv_bfloat16* rhi, __nv_bfloat16* rlo, int* flag,
+                int harm) {
+  constexpr size_t full = (size_t)kP2mParents * (8 * ncoef_c(P) + 8) * sizeof(T);
+  // staged harmonic rows: FP32 leaf levels only (the planes feed the tensor cores)
+  constexpr size_t red = sizeof(T) == 4 ? (size_t)kP2mParents * (8 * nred_c(P) + 8) * sizeof(T) : 0;
+  const size_t smem = full + ((harm && Mhi) ? red : 0);
   static bool attr = false;
-  if (!attr && smem > 48 * 1024) {
-    cudaFuncSetAttribute(p2m_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (!attr && full + red > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(p2m_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(full + red));
+    if (e != cudaSuccess) return e;
     attr = true;
   }
-  p2m_kernel<P, T><<<blocks, kThreads, smem, s>>>(rho, nx, ny, b, leaf, Mleaf, Mhi, Mlo, rho_box, rhi, rlo, flag);
+  p2m_kernel<P, T><<<blocks, kThreads, smem, s>>>(rho, nx, ny, b, leaf, Mleaf, Mhi, Mlo, rho_box, rhi, rlo, flag,
+                                                  harm);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 template <typename T>
 cudaError_t launch_p2m(const TreeTables& t, const T* rho, const int dims[3], const Level& leaf, T* Mleaf, T* rho_box,
-                       void* Mhi, void* Mlo, void* rho_hi, void* rho_lo, int* flag, cudaStream_t s) {
+                       void* Mhi, void* Mlo, void* rho_hi, void* rho_lo, int* flag, int harm, cudaStream_t s) {
   const long long threads = leaf.npar * 16;  // two threads per box
   if (threads == 0) return cudaSuccess;
-  FMM_ORDER_SWITCH(t.p, (p2m_launch<PP, T>(grid_threads(threads), s,
+  cudaError_t e = cudaSuccess;
+  FMM_ORDER_SWITCH(t.p, (e = p2m_launch<PP, T>(grid_threads(threads), s,
                             rho, dims[0], dims[1], t.b, leaf, Mleaf, static_cast<__nv_bfloat16*>(Mhi),
                             static_cast<__nv_bfloat16*>(Mlo), rho_box, static_cast<__nv_bfloat16*>(rho_hi),
-                            static_cast<__nv_bfloat16*>(rho_lo), flag)));
-  return cudaGetLastError();
+                            static_cast<__nv_bfloat16*>(rho_lo), flag, harm)));
+  return e;
 }
 
 template cudaError_t launch_p2m<float>(const TreeTables&, const float*, const int*, const Level&, float*, float*,
-                                       void*, void*, void*, void*, int*, cudaStream_t);
+                                       void*, void*, void*, void*, int*, int, cudaStream_t);
 template cudaError_t launch_p2m<double>(const TreeTables&, const double*, const int*, const Level&, double*, double*,
-                                        void*, void*, void*, void*, int*, cudaStream_t);
+                                        void*, void*, void*, void*, int*, int, cudaStream_t);
 
 }  // namespace fmmgb

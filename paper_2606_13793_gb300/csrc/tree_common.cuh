@@ -32,6 +32,49 @@ __host__ __device__ constexpr int cidx(int a, int b, int c) {
   return (a + b + c) * (a + b + c + 1) * (a + b + c + 2) / 6 + (b + c) * (b + c + 1) / 2 + c;
 }
 
+// Harmonic compression (traceless multipoles): 1/r is harmonic, so its
+// derivatives obey D_{g+2z} = -D_{g+2x} - D_{g+2y}, which keeps the total order.
+// With the symmetric truncation |alpha| + |beta| <= p this makes the M2L
+// contraction depend only on the components with c <= 1 ((p+1)^2 of them
+// instead of nc(p)), exactly:
+//   * multipoles fold onto c <= 1 (in the scaled variables
+//     Mt_(a+2,b,c-2) -= (a+2)(a+1)/(c(c-1)) Mt_(a,b,c), likewise for b, taking c
+//     from the top down);
+//   * locals (Laplacian of the potential = 0 in the box) are rebuilt from c <= 1:
+//     Lt_(a,b,c) = -[(a+2)(a+1) Lt_(a+2,b,c-2) + (b+2)(b+1) Lt_(a,b+2,c-2)] / (c(c-1)).
+// Reduced components are ordered like the canonical order restricted to c <= 1.
+__host__ __device__ constexpr int nred_c(int p) { return (p + 1) * (p + 1); }
+__host__ __device__ constexpr int ridx(int a, int b, int c) {
+  return (a + b + c) * (a + b + c) + ((b + c) == 0 ? 0 : 2 * (b + c) - 1 + c);
+}
+
+template <int P, typename T>
+__host__ __device__ __forceinline__ void harmonic_fold(T (&M)[(P + 1) * (P + 2) * (P + 3) / 6]) {
+#pragma unroll
+  for (int c = P; c >= 2; --c)
+#pragma unroll
+    for (int a = 0; a + c <= P; ++a)
+#pragma unroll
+      for (int b = 0; a + b + c <= P; ++b) {
+        const T f = M[cidx(a, b, c)] * T(1.0 / (double)(c * (c - 1)));
+        M[cidx(a + 2, b, c - 2)] -= T((a + 2) * (a + 1)) * f;
+        M[cidx(a, b + 2, c - 2)] -= T((b + 2) * (b + 1)) * f;
+      }
+}
+
+template <int P, typename T>
+__host__ __device__ __forceinline__ void harmonic_expand(T (&L)[(P + 1) * (P + 2) * (P + 3) / 6]) {
+#pragma unroll
+  for (int c = 2; c <= P; ++c)
+#pragma unroll
+    for (int a = 0; a + c <= P; ++a)
+#pragma unroll
+      for (int b = 0; a + b + c <= P; ++b)
+        L[cidx(a, b, c)] = -(T((a + 2) * (a + 1)) * L[cidx(a + 2, b, c - 2)] +
+                             T((b + 2) * (b + 1)) * L[cidx(a, b + 2, c - 2)]) *
+                           T(1.0 / (double)(c * (c - 1)));
+}
+
 __host__ __device__ constexpr int binom_c(int n, int k) {
   int r = 1;
   for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;

@@ -144,3 +144,45 @@ def test_tc_leaf8_near_field(orc, shape):
     err = rel_l2(phi, ref)
     print(f"leaf 8 bf16x3 {shape}: {err:.2e}")
     assert err <= TOL["bf16x3"]
+
+
+def _solve_opts(rho32, b, p, prec, **kw):
+    nz, ny, nx = rho32.shape
+    plan = fmm.FMMPlan((nx, ny, nz), p, b, prec, accel=False, **kw)
+    phi = plan.solve(torch.from_numpy(np.ascontiguousarray(rho32)).cuda())
+    torch.cuda.synchronize()
+    plan.check()
+    out = phi.double().cpu().numpy()
+    plan.close()
+    return out
+
+
+@pytest.mark.parametrize("p", [2, 4, 6, 8])
+def test_tc_harmonic_compression(orc, p):
+    """The harmonic (p+1)^2-component tensor-core M2L (default) against every
+    Cartesian component and against the oracle.  With n_fp64_levels = 0 every
+    level runs on the tensor cores, so level 2 (locals rebuilt without a parent)
+    is covered too; there the Cartesian form is reported only (at p = 8 its
+    coarse levels miss the bound, which is why they default to FP64), while the
+    harmonic form, with fewer and smaller products, holds it."""
+    rho = inputs.lognormal((64, 48, 80), seed=5)
+    ref = orc.fmm(rho.astype(np.float64), 4, p)["phi"]
+    for nf in (0, 3):
+        h = _solve_opts(rho, 4, p, "bf16x3", n_fp64_levels=nf, harmonic=True)
+        c = _solve_opts(rho, 4, p, "bf16x3", n_fp64_levels=nf, harmonic=False)
+        eh, ec, d = rel_l2(h, ref), rel_l2(c, ref), rel_l2(h, c)
+        print(f"p={p} fp64 levels {nf}: harmonic {eh:.2e} cartesian {ec:.2e} difference {d:.2e}")
+        assert eh <= TOL["bf16x3"]
+        if nf == 3:
+            assert ec <= TOL["bf16x3"]
+        assert d <= TOL["bf16x3"]  # the same truncated operator, up to rounding
+
+
+def test_tc_harmonic_final_stage_m2p(orc):
+    """M2P on the folded leaf planes (harmonic) against the Cartesian planes and the oracle."""
+    rho = inputs.plummer((32, 48, 64), seed=6)
+    ref = orc.fmm_m2p(rho.astype(np.float64), 4, 6)
+    h = _solve_opts(rho, 4, 6, "bf16x3", final_stage="m2p", harmonic=True)
+    c = _solve_opts(rho, 4, 6, "bf16x3", final_stage="m2p", harmonic=False)
+    print(f"m2p harmonic {rel_l2(h, ref):.2e} cartesian {rel_l2(c, ref):.2e}")
+    assert rel_l2(h, ref) <= TOL["bf16x3"] and rel_l2(c, ref) <= TOL["bf16x3"]
