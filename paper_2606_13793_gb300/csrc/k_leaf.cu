@@ -13,9 +13,12 @@ using namespace tree;
 // near_box holds the near-field sums per leaf box ([box][b^3] cells).
 // near_box rows have near_stride values per box (the potential first).
 // m2p (nullable): final-stage M2P potentials [parent][child][b^3], added to
-// the L2P sum before its 1/h scaling.
+// the L2P sum before its 1/h scaling.  Two blocks per SM for FP32 at p <= 6
+// (128 registers, a few bytes spilled; 0.44 -> 0.37 ms at 512^3 against 169
+// registers and one block).
 template <int P, typename T>
-__global__ void __launch_bounds__(kThreads) leaf_finish_kernel(Level leaf, const T* __restrict__ Lleaf,
+__global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(T) == 4) ? 2 : 1)
+    leaf_finish_kernel(Level leaf, const T* __restrict__ Lleaf,
                                                                const T* __restrict__ near_box, int near_stride,
                                                                const T* __restrict__ m2p, int nx, int ny, int b,
                                                                T scale, T* __restrict__ phi) {

@@ -199,8 +199,12 @@ __device__ __forceinline__ void issue_span1(uint32_t d, uint64_t a, uint64_t b, 
   for (int k = 0; k < KS; ++k) mma_f16(d, a + 2ull * k, b + 2ull * k, idesc, k == 0 ? acc0 : 1u);
 }
 
+// 72 registers a thread (13 warps: 29,952 of the SM's 65,536): the FP64
+// levels' blocks running beside it keep the rest (512^3 bf16x3: their
+// concurrent span 3.9 -> 3.0 ms, the step 8.59 -> 8.45 ms with the tree
+// kernels' register bounds).
 template <int KIND>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __maxnreg__(72)
     m2l_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
                   const __grid_constant__ TcLaunch P) {
   constexpr bool split = KIND == TC_BF16X3;

@@ -11,8 +11,10 @@ using namespace tree;
 // M2M (Sec. 2.1, eq. M2M_general, child centre -> parent centre), scaled:
 //   Mt_alpha(P) = 2^-|alpha| sum_children sum_{beta <= alpha} C(alpha,beta) (+-1/2)^(alpha-beta) Mt_beta(C)
 // Each thread shifts one child; the 8 siblings are summed with shuffles.
+// Two blocks per SM for FP32 at p <= 6 (<= 128 registers, no spills): the
+// harmonic fold would otherwise take it to 153 registers and one block.
 template <int P, typename Tc, typename Tp>
-__global__ void __launch_bounds__(kThreads) m2m_kernel(Level child, const Tc* __restrict__ Mc, Level par,
+__global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(Tp) == 4) ? 2 : 1) m2m_kernel(Level child, const Tc* __restrict__ Mc, Level par,
                                                        Tp* __restrict__ Mp, __nv_bfloat16* __restrict__ Mhi,
                                                        __nv_bfloat16* __restrict__ Mlo, int harm) {
   constexpr int NC = ncoef_c(P);
