@@ -90,6 +90,7 @@ def _bind(lib):
         "oracle_direct_accel": (I, [DP, I, I, I, D, D, DP, I]),
         "oracle_fmm_sample_accel": (I, [DP, I, I, I, I, I, D, D, L, LP, DP, I]),
         "oracle_fmm_m2p": (I, [DP, I, I, I, I, I, D, D, DP, I]),
+        "oracle_fmm_orders": (I, [DP, I, I, I, I, I, I, I, I, D, D, DP, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -254,6 +255,19 @@ class Oracle:
         phi = np.zeros_like(rho)
         if self.lib.oracle_fmm_m2p(_dp(rho), nx, ny, nz, b, p, dx, G, _dp(phi), threads) != 0:
             raise ValueError("oracle_fmm_m2p rejected its arguments")
+        return phi
+
+    def fmm_orders(self, rho, b: int, p: int, mult_order: int, local_order: int, final_stage: str = "m2l",
+                   dx: float = 1.0, G: float = 1.0, threads: int = 0) -> np.ndarray:
+        """Potential with multipoles to order mult_order and locals to order
+        local_order inside |alpha| + |beta| <= p; final_stage "m2l" or "m2p"."""
+        rho = _f64(rho)
+        nz, ny, nx = rho.shape
+        phi = np.zeros_like(rho)
+        fs = {"m2l": 0, "m2p": 1}[final_stage]
+        if self.lib.oracle_fmm_orders(_dp(rho), nx, ny, nz, b, p, mult_order, local_order, fs, dx, G, _dp(phi),
+                                      threads) != 0:
+            raise ValueError("oracle_fmm_orders rejected its arguments")
         return phi
 
     def direct_accel(self, rho, dx: float = 1.0, G: float = 1.0, threads: int = 0) -> np.ndarray:

@@ -83,12 +83,14 @@ int oracle_ncoef(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 /* Canonical multi-index list for order p: writes 3*ncoef(p) ints. */
 typedef struct {
   int p, nc;
+  int mo, lo;            /* multipole / local order limits inside |alpha| + |beta| <= p (default p) */
   int mi[1000][3];       /* ncoef(12) = 455 < 1000 */
   int lut[OR_MAXP + 1][OR_MAXP + 1][OR_MAXP + 1];
 } or_index;
 
 static void or_index_init(or_index* ix, int p) {
   ix->p = p;
+  ix->mo = ix->lo = p;
   int k = 0;
   for (int a = 0; a <= OR_MAXP; ++a)
     for (int b = 0; b <= OR_MAXP; ++b)
@@ -213,7 +215,11 @@ static void or_m2l(const or_index* ix, const double* M, const double R[3], doubl
     for (int ka = 0; ka < ix->nc; ++ka) {
       const int* a = ix->mi[ka];
       const int na = a[0] + a[1] + a[2];
-      if (na + nb > p) continue;
+#if ORACLE_MUTANT == 8 /* planted mistake: the two order limits applied to the wrong sides */
+      if (na + nb > p || na > ix->lo || nb > ix->mo) continue;
+#else
+      if (na + nb > p || na > ix->mo || nb > ix->lo) continue;
+#endif
       const int kg = ix->lut[a[0] + b[0]][a[1] + b[1]][a[2] + b[2]];
       double afact = or_fact(a[0]) * or_fact(a[1]) * or_fact(a[2]);
       double sgn = (na & 1) ? -1.0 : 1.0;
@@ -240,6 +246,7 @@ static double or_m2p(const or_index* ix, const double* M, const double R[3]) {
   for (int ka = 0; ka < ix->nc; ++ka) {
     const int* a = ix->mi[ka];
     const int na = a[0] + a[1] + a[2];
+    if (na > ix->mo) continue;
     const double afact = or_fact(a[0]) * or_fact(a[1]) * or_fact(a[2]);
 #if ORACLE_MUTANT == 7 /* planted mistake: M2P without the (-1)^|alpha| factor */
     s += 1.0 / afact * D[ka] * M[ka];
@@ -1200,15 +1207,25 @@ int oracle_fmm_sample_accel(const double* rho, int nx, int ny, int nz, int b, in
 /*            + near(x)                                                     */
 /* ------------------------------------------------------------------------ */
 
-int oracle_fmm_m2p(const double* rho, int nx, int ny, int nz, int b, int p, double dx, double G, double* phi,
-                   int nthreads) {
+/* Potential with separate order limits: multipoles to order mo and locals to
+ * order lo inside |alpha| + |beta| <= p (the paper keeps multipoles to order
+ * 2 and locals to order 3, Sec. 2.1 and 2.3), final stage M2L + L2P
+ * (final_stage = 0) or M2P at the cell centres (1, Sec. 4).  Multipole
+ * components above mo and local components above lo take no part: M2L and
+ * M2P skip them, so L2L and L2P see zeros there.  mo = lo = p gives
+ * oracle_fmm's potential (final_stage 0) and oracle_fmm_m2p's (1). */
+int oracle_fmm_orders(const double* rho, int nx, int ny, int nz, int b, int p, int mo, int lo, int final_stage,
+                      double dx, double G, double* phi, int nthreads) {
   or_hier H;
   if (or_hier_init(&H, nx, ny, nz, b, p)) return -1;
+  if (mo < 0 || mo > p || lo < 0 || lo > p || final_stage < 0 || final_stage > 1) return -1;
   or_set_threads(nthreads);
   or_index* ix = (or_index*)malloc(sizeof(or_index));
   or_index_init(ix, p);
+  ix->mo = mo;
+  ix->lo = lo;
   double** M = or_upward(&H, ix, rho);
-  double** L = or_downward_ex(&H, ix, M, 0);
+  double** L = or_downward_ex(&H, ix, M, final_stage ? 0 : 1);
   const long n = (long)nx * ny * nz;
   const double scale = G * dx * dx;
   const or_level* lf = &H.lev[H.L];
@@ -1216,7 +1233,7 @@ int oracle_fmm_m2p(const double* rho, int nx, int ny, int nz, int b, int p, doub
   for (long c = 0; c < n; ++c) {
     int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long)nx * ny));
     double s = or_far_cell(&H, ix, L, x, y, z);
-    if (H.L >= 2) {
+    if (final_stage && H.L >= 2) {
       int il[216][3];
       int m = or_ilist(&H, H.L, x / b, y / b, z / b, il);
       for (int q = 0; q < m; ++q) {
@@ -1233,4 +1250,9 @@ int oracle_fmm_m2p(const double* rho, int nx, int ny, int nz, int b, int p, doub
   or_free_levels(&H, L);
   free(ix);
   return 0;
+}
+
+int oracle_fmm_m2p(const double* rho, int nx, int ny, int nz, int b, int p, double dx, double G, double* phi,
+                   int nthreads) {
+  return oracle_fmm_orders(rho, nx, ny, nz, b, p, p, p, 1, dx, G, phi, nthreads);
 }

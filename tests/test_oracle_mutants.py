@@ -8,6 +8,7 @@ import oracle
 import test_oracle_accel as accel
 import test_oracle_m2p as m2p
 import test_oracle_ops as ops
+import test_oracle_orders as orders
 import test_oracle_solve as solve
 
 MUTANTS = {
@@ -18,6 +19,7 @@ MUTANTS = {
     5: "near field without the self cell",
     6: "near-field pair force pointing away from the mass",
     7: "final-stage M2P without the (-1)^|alpha| factor",
+    8: "multipole and local order limits applied to the wrong sides",
 }
 
 PINS = [
@@ -29,6 +31,8 @@ PINS = [
     accel.test_accel_converges_to_direct_in_p,
     accel.test_direct_pair_forces_obey_the_third_law,
     m2p.test_m2p_converges_and_beats_m2l_l2p,
+    orders.test_monopole_only_far_field_ignores_mass_moved_inside_boxes,
+    orders.test_order_zero_locals_give_a_constant_far_field_per_box,
 ]
 
 
