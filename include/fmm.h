@@ -102,10 +102,19 @@ typedef struct {
                          L2L): the same truncated operator of Sec. 2.3, eq.
                          M2L, up to rounding, with 1.7x fewer products at
                          p = 6.  1: all nc(p) Cartesian components            */
-  int reserved[3];    /* must be zero */
+  int mult_order;     /* -1 (default) or >= order: multipoles to `order`, the
+                         symmetric truncation |alpha| + |beta| <= order.  0 ..
+                         order-1: multipole components above mult_order take
+                         no part in M2L / M2P (locals stay to `order`): the
+                         paper keeps multipoles to 2 and locals to 3 (Sec. 2.1,
+                         2.3), i.e. order 3, mult_order 2.  Not symmetric, so
+                         fmm_solve_adjoint returns FMM_ERR_UNSUPPORTED; start
+                         from fmm_default_opts (a zeroed struct means
+                         monopoles only)                                      */
+  int reserved[2];    /* must be zero */
 } fmm_opts;
 
-/* Default options: FMM_FP32, n_fp64_levels = 3, accel = 1. */
+/* Default options: FMM_FP32, n_fp64_levels = 3, accel = 1, mult_order = -1. */
 void fmm_default_opts(fmm_opts* opts);
 
 /*

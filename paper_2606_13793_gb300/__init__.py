@@ -70,7 +70,8 @@ class _Grid(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_fp64_levels", ctypes.c_int), ("accel", ctypes.c_int),
-                ("final_stage", ctypes.c_int), ("m2l_cartesian", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("final_stage", ctypes.c_int), ("m2l_cartesian", ctypes.c_int), ("mult_order", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 _lib = None
@@ -163,7 +164,7 @@ class FMMPlan:
 
     def __init__(self, shape, order: int = 6, leaf: int = 4, precision: str = "fp32", dx: float = 1.0,
                  G: float = 1.0, n_fp64_levels: int = 3, accel=True, final_stage: str = "m2l", harmonic=True,
-                 stream=None):
+                 mult_order=None, stream=None):
         import torch
 
         self.lib = load()
@@ -188,6 +189,9 @@ class FMMPlan:
         # harmonic: bf16x3 tensor-core M2L/M2P on the (p+1)^2 harmonic
         # components (False: every Cartesian component)
         opts.m2l_cartesian = 0 if harmonic else 1
+        # mult_order: multipoles kept to this order (None: the order itself;
+        # the paper's split is order 3 with mult_order 2)
+        opts.mult_order = -1 if mult_order is None else int(mult_order)
         handle = ctypes.c_void_p()
         _check(self.lib, self.lib.fmm_plan(ctypes.byref(grid), self.order, self.leaf, ctypes.byref(opts),
                                            _stream_handle(stream), ctypes.byref(handle)))

@@ -53,13 +53,14 @@ fmm_status fail(fmm_status st, const char* fmt, ...) {
 
 struct MultiIndex {
   int p = 0, nc = 0;
+  int mo = 0;  // multipole order limit (components above it take no part in M2L / M2P); p by default
   std::vector<int> a, b, c;  // components, canonical order
   int index(int x, int y, int z) const {
     const int n = x + y + z;
     return n * (n + 1) * (n + 2) / 6 + (n - x) * (n - x + 1) / 2 + (n - x - y);
   }
   void init(int order) {
-    p = order;
+    p = mo = order;
     a.clear(), b.clear(), c.clear();
     for (int n = 0; n <= p; ++n)
       for (int x = n; x >= 0; --x)
@@ -354,7 +355,7 @@ double m2l_entry(const MultiIndex& mi, const TaylorTable& tt, int d, int k, int 
   const int be = n / 8, ct = n % 8, al = k / 8, cs = k % 8;
   if (be >= nc || al >= nc) return 0.0;
   const int ob = level_of_order(mi, be), oa = level_of_order(mi, al);
-  if (oa + ob > p) return 0.0;
+  if (oa + ob > p || oa > mi.mo) return 0.0;
   const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
   int u[3];
   for (int q = 0; q < 3; ++q) u[q] = ((ct >> q) & 1) - ((cs >> q) & 1) - 2 * D[q];
@@ -382,7 +383,7 @@ void m2l_weights(const MultiIndex& mi, const TaylorTable& tt, std::vector<T>& W,
   for (int t = 0; t < ntiles; ++t) {
     const int beta0 = (t * kNTile) / 8;
     const int o = level_of_order(mi, beta0);
-    tile_k[t] = 8 * ncoef(p - o);
+    tile_k[t] = 8 * ncoef(std::min(p - o, mi.mo));
     tile_w[t] = off;
     off += 27LL * tile_k[t] * kNTile;
   }
@@ -740,7 +741,7 @@ bool build_tc(const MultiIndex& mi, const TaylorTable& tt, int kind, TcHost& H, 
   for (int m = 0; m <= p;) {
     const int o_hi = (m == 0 && p >= 1) ? 1 : m;
     const int col0 = m == 0 ? 0 : 8 * count(m - 1), col1 = 8 * count(o_hi);
-    const int K = 8 * count(p - m);
+    const int K = 8 * count(std::min(p - m, mi.mo));
     const int total = col1 - col0;
     const int pieces = (total + kTcMaxGroupN - 1) / kTcMaxGroupN;
     const int per = ((total + pieces - 1) / pieces + 15) / 16 * 16;
@@ -831,7 +832,7 @@ struct M2pTable {
 double m2p_entry(const MultiIndex& mi, const M2pTable& tab, int d, int k, int n) {
   const int b3 = tab.b * tab.b * tab.b;
   const int al = k / 8, cs = k % 8, ct = n / b3, cell = n % b3;
-  if (al >= mi.nc || ct >= 8) return 0.0;
+  if (al >= mi.nc || ct >= 8 || level_of_order(mi, al) > mi.mo) return 0.0;
   const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
   int u[3];
   for (int q = 0; q < 3; ++q) u[q] = ((ct >> q) & 1) - ((cs >> q) & 1) - 2 * D[q];
@@ -846,7 +847,7 @@ double m2p_entry(const MultiIndex& mi, const M2pTable& tab, int d, int k, int n)
 bool build_tc_m2p(const MultiIndex& mi, const M2pTable& tab, int kind, TcHost& H, bool harm) {
   const int ncol = 8 * tab.b * tab.b * tab.b;
   const std::vector<int> red = harmonic_components(mi);
-  const int K = 8 * (harm ? (int)red.size() : mi.nc);
+  const int K = 8 * (harm ? (mi.mo + 1) * (mi.mo + 1) : ncoef(mi.mo));
   std::vector<TcCols> gs;
   for (int c = 0; c < ncol; c += kTcMaxGroupN) gs.push_back({c, std::min(kTcMaxGroupN, ncol - c), K});
   // with harmonic planes the reduction runs over the folded components (the
@@ -972,6 +973,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
   P->b = leaf;
   P->opts = o;
   P->mi.init(order);
+  if (o.mult_order >= 0 && o.mult_order < order) P->mi.mo = o.mult_order;
   P->nc = P->mi.nc;
   P->near_comps = o.accel == 2 ? 4 : 1;
   P->m2p = o.final_stage == 1;
@@ -1205,13 +1207,13 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
       std::vector<long long> tw;
       if (lf.f64) {
         std::vector<double> W;
-        full_weights<double>(ncol, 8 * P->nc, entry, W, tk, tw);
+        full_weights<double>(ncol, 8 * ncoef(P->mi.mo), entry, W, tk, tw);
         double* d = nullptr;
         if ((st = P->upload(W, &d, s))) return cleanup(st);
         P->d_w_m2p = d;
       } else {
         std::vector<float> W;
-        full_weights<float>(ncol, 8 * P->nc, entry, W, tk, tw);
+        full_weights<float>(ncol, 8 * ncoef(P->mi.mo), entry, W, tk, tw);
         float* d = nullptr;
         if ((st = P->upload(W, &d, s))) return cleanup(st);
         P->d_w_m2p = d;
@@ -1274,6 +1276,7 @@ void fmm_default_opts(fmm_opts* o) {
   o->precision = FMM_FP32;
   o->n_fp64_levels = 3;
   o->accel = 1;
+  o->mult_order = -1;
 }
 
 const char* fmm_last_error(void) { return g_last_error.c_str(); }
@@ -1315,6 +1318,7 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
   if (o.final_stage == 1 && o.accel == 2)
     return fail(FMM_ERR_UNSUPPORTED, "the analytic acceleration is built for final_stage = 0 only");
   if (o.m2l_cartesian < 0 || o.m2l_cartesian > 1) return fail(FMM_ERR_ARG, "m2l_cartesian %d not in {0, 1}", o.m2l_cartesian);
+  if (o.mult_order < -1) return fail(FMM_ERR_ARG, "mult_order %d below -1", o.mult_order);
   for (int r : o.reserved)
     if (r != 0) return fail(FMM_ERR_ARG, "reserved option fields must be zero");
   int dev = 0;
@@ -1611,6 +1615,8 @@ fmm_status fmm_solve_adjoint(fmm_plan_t P, const void* grad_phi, const void* gra
   if (!grad_rho || (!grad_phi && !grad_accel)) return fail(FMM_ERR_ARG, "grad_rho and one gradient must be non-NULL");
   if (P->m2p)
     return fail(FMM_ERR_UNSUPPORTED, "no adjoint with the final-stage M2P (its truncated operator is not symmetric)");
+  if (P->mi.mo < P->p)
+    return fail(FMM_ERR_UNSUPPORTED, "no adjoint with mult_order < order (the transpose swaps the two orders)");
   if (grad_accel && P->near_comps == 4)
     return fail(FMM_ERR_UNSUPPORTED, "the adjoint of the analytic acceleration is not built (use accel = 1)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
