@@ -528,7 +528,20 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
     if (P.ng == 0) return false;
     // a single bf16x3 group: one accumulator per product
     const bool prod_split = kind == TC_BF16X3 && V.size() == 1 && 3 * cols <= 512;
-    if (prod_split) {
+    // hi*hi and hi*lo share A_hi, and a tile's lo plane follows its hi plane:
+    // one MMA of N = 2n over both planes computes them into adjacent
+    // accumulators (an N = 64 MMA holds the tensor pipe about as long as an
+    // N = 128 one, so this is two pipe slots a K step instead of three)
+    const bool pair_hilo = prod_split && !long_sums && 2 * V[0].nm <= 256;
+    if (pair_hilo) {
+      VGroup v3 = V[0];
+      v3.prod = 3;
+      V[0].prod = 4;
+      V[0].nm *= 2;
+      V.push_back(v3);
+      cols *= 3;
+      P.out_tmem2[0] = P.out_tmem3[0] = 0;  // marked; placed below
+    } else if (prod_split) {
       V[0].prod = 1;
       VGroup v2 = V[0], v3 = V[0];
       v2.prod = 2;
@@ -610,7 +623,10 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
         v.tmem = c;
         c += v.nm;
         kmax = std::max(kmax, v.k1);
-        if (v.prod >= 2)
+        if (v.prod == 4) {  // hi*hi in the first half, hi*lo in the second
+          P.out_tmem[v.out] = v.tmem;
+          P.out_tmem2[v.out] = v.tmem + v.nm / 2;
+        } else if (v.prod >= 2)
           (v.prod == 2 ? P.out_tmem2 : P.out_tmem3)[v.out] = v.tmem;
         else if (v.k0 == 0)
           P.out_tmem[v.out] = v.tmem;
@@ -714,6 +730,9 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
                   if (S.prod == 0) {
                     std::memcpy(tile + o, &h, 2);
                     std::memcpy(tile + (size_t)S.n * 128 + o, &l, 2);
+                  } else if (S.prod == 4) {  // hi rows, then the lo rows (half a multiple of 8: same swizzle)
+                    std::memcpy(tile + o, &h, 2);
+                    std::memcpy(tile + (size_t)(v.nm / 2) * 128 + o, &l, 2);
                   } else {  // the one plane this product multiplies
                     std::memcpy(tile + o, S.prod == 2 ? &l : &h, 2);
                   }

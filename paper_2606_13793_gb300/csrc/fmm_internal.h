@@ -198,7 +198,8 @@ struct TcSpan {
   uint32_t idesc;  // instruction descriptor (kind, N, M = 128)
   int first;       // chunk in which the span's accumulators open (first MMA overwrites)
   int prod;        // bf16x3 products: 0 all three (hi and lo weight planes in the tile);
-                   // 1 A_hi x B (B = hi plane), 2 A_hi x B (B = lo plane), 3 A_lo x B (B = hi plane)
+                   // 1 A_hi x B (B = hi plane), 2 A_hi x B (B = lo plane), 3 A_lo x B (B = hi plane);
+                   // 4 A_hi x [B_hi; B_lo]: one MMA of N = n over n/2 hi rows then n/2 lo rows
 };
 
 // One pass of the schedule, passed by value (kernel parameter space), so the

@@ -18,7 +18,7 @@ template <int P, typename Tp, typename Tc>
 __global__ void __launch_bounds__(kThreads) l2l_kernel(Level par, const Tp* __restrict__ Lp, Level child,
                                                        Tc* __restrict__ Lc, int accumulate, int harm) {
   constexpr int NC = ncoef_c(P);
-  const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long p = t >> 3;  // box of the parent level == parent block of the child level
   const int c = (int)(t & 7);
   if (p >= par.nbox) return;
@@ -73,7 +73,8 @@ cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, cons
                        int harm, cudaStream_t s) {
   const long long threads = par.nbox * 8;
   if (threads == 0) return cudaSuccess;
-  FMM_ORDER_SWITCH(t.p, (l2l_kernel<PP, Tp, Tc><<<grid_threads(threads), kThreads, 0, s>>>(par, Lp, child, Lc,
+  const int bs = small_grid_block(threads);
+  FMM_ORDER_SWITCH(t.p, (l2l_kernel<PP, Tp, Tc><<<(unsigned)((threads + bs - 1) / bs), bs, 0, s>>>(par, Lp, child, Lc,
                                                                                           accumulate, harm)));
   return cudaGetLastError();
 }

@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(Tp) == 4) ? 2 : 1)
                                                        Tp* __restrict__ Mp, __nv_bfloat16* __restrict__ Mhi,
                                                        __nv_bfloat16* __restrict__ Mlo, int harm) {
   constexpr int NC = ncoef_c(P);
-  const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long p = t >> 3;
   const int c = (int)(t & 7);
   const bool live = p < child.npar;  // child.npar == par.nbox
@@ -93,7 +93,8 @@ cudaError_t launch_m2m(const TreeTables& t, const Level& child, const Tc* Mc, co
                        void* Mlo, int harm, cudaStream_t s) {
   const long long threads = child.npar * 8;
   if (threads == 0) return cudaSuccess;
-  FMM_ORDER_SWITCH(t.p, (m2m_kernel<PP, Tc, Tp><<<grid_threads(threads), kThreads, 0, s>>>(
+  const int bs = small_grid_block(threads);
+  FMM_ORDER_SWITCH(t.p, (m2m_kernel<PP, Tc, Tp><<<(unsigned)((threads + bs - 1) / bs), bs, 0, s>>>(
                             child, Mc, par, Mp, static_cast<__nv_bfloat16*>(Mhi), static_cast<__nv_bfloat16*>(Mlo),
                             harm)));
   return cudaGetLastError();

@@ -165,6 +165,12 @@ __device__ __forceinline__ Box box_of(const Level& lv, long long t) {
 
 inline unsigned grid_threads(long long threads) { return (unsigned)((threads + kThreads - 1) / kThreads); }
 
+// Block size of the coarse-level shifts (M2M / L2L): a grid that would not
+// give every SM a block of kThreads runs warp-sized blocks instead, so its few
+// warps spread over the SMs (the FP64 levels are bound by each SM's DFMA rate:
+// at 512^3 their launches drop from ~50 to a few microseconds).
+inline int small_grid_block(long long threads) { return threads < 152LL * kThreads ? 32 : kThreads; }
+
 #define FMM_ORDER_SWITCH(p, ...)                          \
   switch (p) {                                            \
     case 0: { constexpr int PP = 0; __VA_ARGS__; } break; \
