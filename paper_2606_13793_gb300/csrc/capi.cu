@@ -209,6 +209,13 @@ struct fmm_plan_s {
   long long* d_m2p_tile_w = nullptr;
   int m2p_ntiles = 0;
   std::vector<int> h_m2p_tile_k;
+  // transpose of the final-stage M2P (the adjoint solve): P2L from the
+  // adjoint source's cells into the leaf locals, CUDA cores
+  void* d_w_p2l = nullptr;
+  int* d_p2l_tile_k = nullptr;
+  long long* d_p2l_tile_w = nullptr;
+  int p2l_ntiles = 0;
+  std::vector<int> h_p2l_tile_k;
   TcLaunch tcm{};
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // timing
@@ -1241,6 +1248,32 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
       P->h_m2p_tile_k = tk;
       if ((st = P->upload(tk, &P->d_m2p_tile_k, s)) || (st = P->upload(tw, &P->d_m2p_tile_w, s))) return cleanup(st);
     }
+    {
+      // P2L = M2P transposed: rows are source parents, the reduction runs over
+      // the cells (target child, cell) of neighbour d, the columns are the
+      // source's (alpha, child) locals; W'_d[k][n] = W_{-d}[n][k] (26 - d is
+      // the opposite neighbour)
+      const int K = 8 * P->b * P->b * P->b;
+      auto entry = [&](int d, int k, int n) { return m2p_entry(P->mi, tab, 26 - d, n, k); };
+      std::vector<int> tk;
+      std::vector<long long> tw;
+      if (lf.f64) {
+        std::vector<double> W;
+        full_weights<double>(8 * P->nc, K, entry, W, tk, tw);
+        double* d = nullptr;
+        if ((st = P->upload(W, &d, s))) return cleanup(st);
+        P->d_w_p2l = d;
+      } else {
+        std::vector<float> W;
+        full_weights<float>(8 * P->nc, K, entry, W, tk, tw);
+        float* d = nullptr;
+        if ((st = P->upload(W, &d, s))) return cleanup(st);
+        P->d_w_p2l = d;
+      }
+      P->p2l_ntiles = (int)tk.size();
+      P->h_p2l_tile_k = tk;
+      if ((st = P->upload(tk, &P->d_p2l_tile_k, s)) || (st = P->upload(tw, &P->d_p2l_tile_w, s))) return cleanup(st);
+    }
   }
   if (P->near_tc) {
     TcHost H;
@@ -1500,6 +1533,28 @@ fmm_status do_m2p(fmm_plan_t P, cudaStream_t s) {
   return FMM_OK;
 }
 
+// Adjoint of the final-stage M2P: the leaf locals from the adjoint source's
+// cells (parent-blocked in the M2P buffer), L2P then evaluates them.
+fmm_status do_p2l(fmm_plan_t P, cudaStream_t s) {
+  const Level& lf = P->lev[P->L];
+  NbrGemm g;
+  g.A = P->arena + P->m2p_off;
+  g.row_len = 8 * P->b * P->b * P->b;
+  for (int q = 0; q < 3; ++q) g.grid[q] = lf.np[q];
+  g.W = P->d_w_p2l;
+  g.tile_k = P->d_p2l_tile_k;
+  g.tile_w = P->d_p2l_tile_w;
+  g.C = P->Lx(P->L);
+  g.n_cols = 8 * P->nc;
+  g.ntiles = P->p2l_ntiles;
+  g.accumulate = 0;
+  g.dsplit = 1;
+  g.partial = nullptr;
+  g.shape = zrun_eligible(g, P->h_p2l_tile_k.data(), P->p2l_ntiles) ? 1 : 0;
+  CUDA_TRY(lf.f64 ? launch_nbr_gemm<double>(g, s) : launch_nbr_gemm<float>(g, s));
+  return FMM_OK;
+}
+
 fmm_status do_m2l(fmm_plan_t P, int l, cudaStream_t s) {
   const Level& lv = P->lev[l];
   if (lv.tc) {
@@ -1514,8 +1569,12 @@ fmm_status do_m2l(fmm_plan_t P, int l, cudaStream_t s) {
   return FMM_OK;
 }
 
+// adjoint = true (fmm_solve_adjoint): the same chain on the adjoint source,
+// except that with the final-stage M2P the leaf level runs its transpose
+// (P2L into the leaf locals, then L2L adds the parents' and L2P evaluates);
+// the coarser levels and the near field are symmetric.
 template <typename T>
-fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t s) {
+fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t s, bool adjoint = false) {
   const TreeTables tt = P->tables();
   const int L = P->L;
   T* rho_box = reinterpret_cast<T*>(P->arena + P->rho_box_off);
@@ -1532,6 +1591,10 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
                            P->near_tc ? P->arena + P->rho_lo_off : nullptr, P->d_flag,
                            (mplanes && P->harm) ? 1 : 0, s));
   }
+  const bool p2l = adjoint && P->m2p;  // leaf level by the transpose of M2P
+  if (p2l)
+    CUDA_TRY(launch_cells_to_parent_blocks<T>(rho, P->dims, P->lev[L], P->b,
+                                              reinterpret_cast<T*>(P->arena + P->m2p_off), s));
   for (int l = L; l >= 3; --l) {
     StageTimer t(P, ST_M2M, s);
     if ((st = do_m2m(P, tt, l, s))) return st;
@@ -1557,9 +1620,13 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
     CUDA_TRY(cudaStreamWaitEvent(sf, P->ev_fork, 0));
   }
   for (int l = 2; l <= L; ++l) {
-    if (P->lev[l].tc) continue;
+    if (P->lev[l].tc || (p2l && l == L)) continue;
     StageTimer t(P, ST_M2L, sf);
     if ((st = (l == L && P->m2p) ? do_m2p(P, sf) : do_m2l(P, l, sf))) return st;
+  }
+  if (p2l) {
+    StageTimer t(P, ST_M2L, sf);
+    if ((st = do_p2l(P, sf))) return st;
   }
   if (near_side) {
     StageTimer t(P, ST_NEAR, sf);
@@ -1567,7 +1634,7 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
   }
   if (fork) CUDA_TRY(cudaEventRecord(P->ev_join, sf));
   for (int l = 2; l <= L; ++l) {
-    if (!P->lev[l].tc) continue;
+    if (!P->lev[l].tc || (p2l && l == L)) continue;
     StageTimer t(P, ST_M2L_TC, s);
     if ((st = (l == L && P->m2p) ? do_m2p(P, s) : do_m2l(P, l, s))) return st;
   }
@@ -1586,8 +1653,13 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
   }
   for (int l = 3; l <= L; ++l) {
     StageTimer t(P, ST_L2L, s);
-    // with the final-stage M2P the leaf locals are the parent's shifted locals alone
-    if ((st = do_l2l(P, tt, l, s, (l == L && P->m2p) ? 0 : 1))) return st;
+    // with the final-stage M2P the leaf locals are the parent's shifted locals
+    // alone (the adjoint's P2L wrote them first)
+    if ((st = do_l2l(P, tt, l, s, (l == L && P->m2p && !p2l) ? 0 : 1))) return st;
+  }
+  if (L == 2 && P->m2p && !p2l) {  // no parent far field: the leaf locals are zero
+    StageTimer t(P, ST_L2L, s);
+    CUDA_TRY(launch_zero<T>(static_cast<T*>(P->Lx(L)), P->lev[L].bytes / sizeof(T), s));
   }
   if (accel && P->near_comps == 4) {  // analytic acceleration, read off the expansions
     StageTimer t(P, ST_LEAF, s);
@@ -1599,7 +1671,8 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
     StageTimer t(P, ST_LEAF, s);
     CUDA_TRY(launch_leaf_finish<T>(tt, P->lev[L], static_cast<const T*>(P->Lx(L)), near_box,
                                    P->b * P->b * P->b * P->near_comps,
-                                   P->m2p ? reinterpret_cast<const T*>(P->arena + P->m2p_off) : nullptr, P->dims,
+                                   (P->m2p && !p2l) ? reinterpret_cast<const T*>(P->arena + P->m2p_off) : nullptr,
+                                   P->dims,
                                    P->G * P->dx * P->dx, phi, s));
   }
   if (accel) {
@@ -1632,8 +1705,6 @@ fmm_status fmm_solve(fmm_plan_t P, const void* rho, void* phi, void* accel, void
 fmm_status fmm_solve_adjoint(fmm_plan_t P, const void* grad_phi, const void* grad_accel, void* grad_rho, void* stream) {
   if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
   if (!grad_rho || (!grad_phi && !grad_accel)) return fail(FMM_ERR_ARG, "grad_rho and one gradient must be non-NULL");
-  if (P->m2p)
-    return fail(FMM_ERR_UNSUPPORTED, "no adjoint with the final-stage M2P (its truncated operator is not symmetric)");
   if (P->mi.mo < P->p)
     return fail(FMM_ERR_UNSUPPORTED, "no adjoint with mult_order < order (the transpose swaps the two orders)");
   if (grad_accel && P->near_comps == 4)
@@ -1654,8 +1725,8 @@ fmm_status fmm_solve_adjoint(fmm_plan_t P, const void* grad_phi, const void* gra
     }
   }
   if (P->f64_data())
-    return run_solve<double>(P, static_cast<const double*>(w), static_cast<double*>(grad_rho), nullptr, s);
-  return run_solve<float>(P, static_cast<const float*>(w), static_cast<float*>(grad_rho), nullptr, s);
+    return run_solve<double>(P, static_cast<const double*>(w), static_cast<double*>(grad_rho), nullptr, s, true);
+  return run_solve<float>(P, static_cast<const float*>(w), static_cast<float*>(grad_rho), nullptr, s, true);
 }
 
 fmm_status fmm_solve_host(fmm_plan_t P, const void* rho_host, void* phi_host, void* accel_host, void* stream) {
@@ -1719,6 +1790,7 @@ int fmm_solve_launches(fmm_plan_t P, int with_accel) {
   for (int l = 2; l <= L; ++l) {
     n += l >= 3 ? 2 : 1;                // M2L, and L2L below level 2
     if (l == 2 && harmonic_m2l_level(P, 2)) n += 1;  // rebuild of the harmonic level-2 locals
+    if (l == 2 && L == 2 && P->m2p) n += 1;          // zero leaf locals (final-stage M2P, no parent far field)
     if (!P->lev[l].tc && P->m2l_choice[l].dsplit > 1 && !(l == L && P->m2p)) n += 1;  // partial-sum reduction
   }
   n += P->near_tc ? (int)P->tcn.size() + 1 : 2;  // near field + leaf finish

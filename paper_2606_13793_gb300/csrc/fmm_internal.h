@@ -124,6 +124,11 @@ cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, cons
                        int harm, cudaStream_t s);
 template <typename T>
 cudaError_t launch_zero(T* p, size_t count, cudaStream_t s);
+// Copy of a cell grid in the leaf level's parent-blocked box order
+// [parent][child][b^3] (phantom boxes zero).
+template <typename T>
+cudaError_t launch_cells_to_parent_blocks(const T* src, const int dims[3], const Level& leaf, int b, T* dst,
+                                          cudaStream_t s);
 // near_box rows hold near_stride values per leaf box, the potential sums first.
 template <typename T>
 // m2p (nullable): final-stage M2P potentials, parent-blocked [parent][child][b^3], in the

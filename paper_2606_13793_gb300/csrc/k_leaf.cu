@@ -287,4 +287,35 @@ template cudaError_t launch_leaf_finish<float>(const TreeTables&, const Level&, 
 template cudaError_t launch_leaf_finish<double>(const TreeTables&, const Level&, const double*, const double*, int,
                                                 const double*, const int*, double, double*, cudaStream_t);
 
+// Cells of every leaf box in parent-blocked order, [parent][child][b^3]
+// (phantom boxes zero): the rows of the final-stage M2P's transpose.
+template <typename T>
+__global__ void cells_to_parent_blocks_kernel(const T* __restrict__ src, int nx, int ny, Level leaf, int b,
+                                              T* __restrict__ dst) {
+  const long long b3 = (long long)b * b * b;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= leaf.npar * 8 * b3) return;
+  const Box B = box_of(leaf, i / b3);
+  const int cell = (int)(i % b3);
+  T v = T(0);
+  if (B.real) {
+    const int x = B.x * b + cell % b, y = B.y * b + (cell / b) % b, z = B.z * b + cell / (b * b);
+    v = src[((long long)z * ny + y) * nx + x];
+  }
+  dst[i] = v;
+}
+
+template <typename T>
+cudaError_t launch_cells_to_parent_blocks(const T* src, const int dims[3], const Level& leaf, int b, T* dst,
+                                          cudaStream_t s) {
+  const long long n = leaf.npar * 8 * (long long)b * b * b;
+  if (n == 0) return cudaSuccess;
+  cells_to_parent_blocks_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dims[0], dims[1], leaf, b, dst);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cells_to_parent_blocks<float>(const float*, const int*, const Level&, int, float*,
+                                                          cudaStream_t);
+template cudaError_t launch_cells_to_parent_blocks<double>(const double*, const int*, const Level&, int, double*,
+                                                           cudaStream_t);
+
 }  // namespace fmmgb
