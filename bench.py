@@ -484,7 +484,9 @@ def main():
                 "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32/f32", "bf16x3": "bf16x3/f32"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": f"unigrid FMM {n}^3 isolated, p={p}, leaf {b}^3, lognormal P(k)~k^-2.5",
-                           "precision": args.precision, "l2": "inputs larger than L2 (rho 512 MiB, outputs 2 GiB)",
+                           "precision": args.precision, "l2": (f"inputs larger than L2 (rho {n ** 3 * 4 / 2 ** 20:.0f} MiB, phi and accel "
+                                  f"{n ** 3 * 16 / 2 ** 20:.0f} MiB)") if n ** 3 * 4 > 129e6 else
+                                 f"rho ({n ** 3 * 4 / 2 ** 20:.0f} MiB) fits in L2: not a bandwidth-valid size",
                            "parallelism": f"replicas x{world}", "cuda_core_variants": tuning, "accel": args.accel,
                            "final_stage": args.final_stage,
                            "m2l_components": "harmonic (p+1)^2" if harmonic else "cartesian nc(p)",

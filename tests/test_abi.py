@@ -39,12 +39,14 @@ def test_binary_targets_sm103a():
     assert "arch=compute_103a,code=sm_103a" in _build.ARCH
 
 
-def _plan(lib, nx=32, ny=32, nz=32, dx=1.0, G=1.0, order=4, leaf=4, prec=1, reserved0=0):
+def _plan(lib, nx=32, ny=32, nz=32, dx=1.0, G=1.0, order=4, leaf=4, prec=1, reserved0=0, **fields):
     grid = fmm._Grid(nx, ny, nz, dx, G)
     opts = fmm._Opts()
     lib.fmm_default_opts(ctypes.byref(opts))
     opts.precision = prec
     opts.reserved[0] = reserved0
+    for k, v in fields.items():
+        setattr(opts, k, v)
     h = ctypes.c_void_p()
     st = lib.fmm_plan(ctypes.byref(grid), order, leaf, ctypes.byref(opts), None, ctypes.byref(h))
     return st, lib.fmm_last_error().decode()
@@ -61,6 +63,10 @@ def test_argument_validation_without_gpu(lib):
         (dict(dx=float("nan")), "dx"),
         (dict(prec=7), "precision"),
         (dict(reserved0=1), "reserved"),
+        (dict(accel=3), "accel"),
+        (dict(final_stage=2), "final_stage"),
+        (dict(m2l_cartesian=2), "m2l_cartesian"),
+        (dict(mult_order=-2), "mult_order"),
     ]
     for kw, word in cases:
         st, msg = _plan(lib, **kw)
