@@ -328,7 +328,9 @@ def main():
     plan = fmm.FMMPlan((n, n, n), p, b, args.precision, dx=dx,
                        accel="analytic" if args.accel == "analytic" else True, final_stage=args.final_stage,
                        harmonic=not args.m2l_cartesian)
-    harmonic = args.precision == "bf16x3" and not args.m2l_cartesian
+    harmonic = args.precision == "bf16x3" and not args.m2l_cartesian  # tensor-core levels
+    harmonic_cc = (not args.m2l_cartesian and args.order >= 2         # CUDA-core levels (FP32 / FP64 plans)
+                   and args.precision in ("fp32", "fp64"))
     if not args.no_autotune:
         plan.autotune()
     tuning = {str(l): list(plan.tuning(l)) for l in range(2, plan.leaf_level + 1) if plan.level_kind(l) != "tensor"}
@@ -426,7 +428,7 @@ def main():
     kinds = {l: plan.level_kind(l) for l in range(2, L + 1)}
     flop_by = {"m2l_tc": 0, "m2l": 0}
     for l, k in kinds.items():
-        hl = harmonic and k == "tensor"
+        hl = harmonic if k == "tensor" else harmonic_cc
         f = m2p_flop_leaf((n, n, n), b, p, hl) if (l == L and args.final_stage == "m2p") else \
             m2l_flop_level((n, n, n), b, p, l, hl)
         flop_by["m2l_tc" if k == "tensor" else "m2l"] += f
@@ -489,7 +491,7 @@ def main():
                                  f"rho ({n ** 3 * 4 / 2 ** 20:.0f} MiB) fits in L2: not a bandwidth-valid size",
                            "parallelism": f"replicas x{world}", "cuda_core_variants": tuning, "accel": args.accel,
                            "final_stage": args.final_stage,
-                           "m2l_components": "harmonic (p+1)^2" if harmonic else "cartesian nc(p)",
+                           "m2l_components": "harmonic (p+1)^2" if (harmonic or harmonic_cc) else "cartesian nc(p)",
                            "autotuned": not args.no_autotune, **compare},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": plan.launches(True) * args.steps,

@@ -173,6 +173,7 @@ struct fmm_plan_s {
   // tensor-core M2L and near field
   int tc_kind = -1;
   bool harm = false;  // harmonic compression of the bf16x3 tensor-core M2L/M2P (planes of nr components)
+  bool harm_cc = false;  // harmonic compression of the CUDA-core M2L (Level::fold_off / lred_off)
   int nr = 0;         // (p + 1)^2
   int plane_nc() const { return harm ? nr : nc; }
   TcLaunch tc{};
@@ -377,20 +378,25 @@ double m2l_entry(const MultiIndex& mi, const TaylorTable& tt, int d, int k, int 
 
 // Column tiles of the neighbour contraction for M2L on the CUDA cores:
 // output column n = beta*8 + child; tile t covers beta in [4t, 4t+4) whose
-// lowest order fixes the reduction prefix 8 * nc(p - order).
+// lowest order fixes the reduction prefix 8 * nc(p - order).  harm: rows
+// and columns are the harmonic components ((q + 1)^2 up to order q: the
+// folded multipoles in, the c <= 1 locals out).
 template <typename T>
 void m2l_weights(const MultiIndex& mi, const TaylorTable& tt, std::vector<T>& W, std::vector<int>& tile_k,
-                 std::vector<long long>& tile_w, bool fill = true) {
-  const int p = mi.p, nc = mi.nc;
-  const int ncol = 8 * nc;
+                 std::vector<long long>& tile_w, bool fill = true, bool harm = false) {
+  const int p = mi.p;
+  const std::vector<int> red = harmonic_components(mi);
+  const int nk = harm ? (int)red.size() : mi.nc;
+  auto count = [harm](int q) { return harm ? (q + 1) * (q + 1) : ncoef(q); };
+  const int ncol = 8 * nk;
   const int ntiles = (ncol + kNTile - 1) / kNTile;
   tile_k.resize(ntiles);
   tile_w.resize(ntiles);
   long long off = 0;
   for (int t = 0; t < ntiles; ++t) {
     const int beta0 = (t * kNTile) / 8;
-    const int o = level_of_order(mi, beta0);
-    tile_k[t] = 8 * ncoef(std::min(p - o, mi.mo));
+    const int o = level_of_order(mi, harm ? red[beta0] : beta0);
+    tile_k[t] = 8 * count(std::min(p - o, mi.mo));
     tile_w[t] = off;
     off += 27LL * tile_k[t] * kNTile;
   }
@@ -401,7 +407,15 @@ void m2l_weights(const MultiIndex& mi, const TaylorTable& tt, std::vector<T>& W,
     for (int d = 0; d < 27; ++d) {
       T* blk = W.data() + tile_w[t] + (long long)d * K * kNTile;
       for (int k = 0; k < K; ++k)
-        for (int j = 0; j < kNTile; ++j) blk[(long long)k * kNTile + j] = (T)m2l_entry(mi, tt, d, k, t * kNTile + j);
+        for (int j = 0; j < kNTile; ++j) {
+          const int n = t * kNTile + j;
+          if (!harm) {
+            blk[(long long)k * kNTile + j] = (T)m2l_entry(mi, tt, d, k, n);
+          } else if (n / 8 < nk && k / 8 < nk) {
+            blk[(long long)k * kNTile + j] =
+                (T)m2l_entry(mi, tt, d, red[k / 8] * 8 + k % 8, red[n / 8] * 8 + n % 8);
+          }
+        }
     }
   }
 }
@@ -1015,6 +1029,15 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
   P->nr = (order + 1) * (order + 1);
   P->harm = tcp && P->tc_kind == TC_BF16X3 && !o.m2l_cartesian && order >= 2 &&
             P->nr <= kTcMaxColMap;
+  {
+    // CUDA-core precisions only: in the mixed ones the CUDA-core (FP64) levels
+    // run beside the tensor-core levels and, compressed, their denser DFMA
+    // work slows those (512^3 bf16x3 step 8.35 ms against 8.11 ms).  P2M
+    // stages a box row's full and folded components in shared memory.
+    const size_t esz = o.precision == FMM_FP64 ? 8 : 4;
+    const size_t stage = (size_t)16 * (8 * P->nc + 8 + 8 * P->nr + 8) * esz;
+    P->harm_cc = !tcp && !o.m2l_cartesian && order >= 2 && stage <= 227 * 1024;
+  }
   for (int l = 0; l <= P->L; ++l) {
     Level& lv = P->lev[l];
     lv.f64 = P->f64_data() ? 1 : 0;
@@ -1036,6 +1059,14 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     lv.l_off = off;
     off = align(off + lv.bytes);
     lv.hi_off = lv.lo_off = 0;
+    lv.fold_off = lv.lred_off = 0;
+    if (P->harm_cc && !lv.tc && l >= 2 && !(l == P->L && P->m2p)) {
+      const size_t red = (size_t)lv.npar * 8 * P->nr * (lv.f64 ? 8 : 4);
+      lv.fold_off = off;
+      off = align(off + red);
+      lv.lred_off = off;
+      off = align(off + red);
+    }
     if (lv.tc && P->tc_kind == TC_BF16X3) {
       const size_t plane = (size_t)lv.npar * 8 * P->plane_nc() * 2;
       lv.hi_off = off;
@@ -1065,7 +1096,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
   {
     // column tiles of the SIMT contraction (needed to size the split scratch)
     const int ncol = 8 * P->nc;
-    P->m2l_ntiles = (ncol + kNTile - 1) / kNTile;
+    P->m2l_ntiles = (8 * (P->harm_cc ? P->nr : P->nc) + kNTile - 1) / kNTile;
     size_t part = 0, want = 0;
     for (int l = 2; l <= P->L; ++l) {
       const size_t one = (size_t)P->lev[l].npar * (size_t)ncol * (size_t)(P->lev[l].f64 ? 8 : 4);
@@ -1135,14 +1166,14 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     std::vector<long long> tw;
     if (any64) {
       std::vector<double> W;
-      m2l_weights<double>(P->mi, tt, W, tk, tw, !P->static_keep_tables);
+      m2l_weights<double>(P->mi, tt, W, tk, tw, !P->static_keep_tables, P->harm_cc);
       double* d = nullptr;
       if ((st = P->upload(W, &d, s))) return cleanup(st);
       P->d_w_m2l_f64 = d;
     }
     if (any32) {
       std::vector<float> W;
-      m2l_weights<float>(P->mi, tt, W, tk, tw, !P->static_keep_tables);
+      m2l_weights<float>(P->mi, tt, W, tk, tw, !P->static_keep_tables, P->harm_cc);
       float* d = nullptr;
       if ((st = P->upload(W, &d, s))) return cleanup(st);
       P->d_w_m2l_f32 = d;
@@ -1429,16 +1460,18 @@ fmm_status do_m2m(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s) {
   const bool planes = q.tc && P->tc_kind == TC_BF16X3;
   void* hi = planes ? P->arena + q.hi_off : nullptr;
   void* lo = planes ? P->arena + q.lo_off : nullptr;
+  void* fold = q.fold_off ? P->arena + q.fold_off : nullptr;
+  const int harm = (planes && P->harm) || fold ? 1 : 0;
   cudaError_t e;
   if (c.f64)
     e = launch_m2m<double, double>(tt, c, static_cast<const double*>(P->M(l)), q, static_cast<double*>(P->M(l - 1)),
-                                   nullptr, nullptr, 0, s);
+                                   nullptr, nullptr, harm, static_cast<double*>(fold), s);
   else if (q.f64)
     e = launch_m2m<float, double>(tt, c, static_cast<const float*>(P->M(l)), q, static_cast<double*>(P->M(l - 1)),
-                                  nullptr, nullptr, 0, s);
+                                  nullptr, nullptr, harm, static_cast<double*>(fold), s);
   else
     e = launch_m2m<float, float>(tt, c, static_cast<const float*>(P->M(l)), q, static_cast<float*>(P->M(l - 1)), hi,
-                                 lo, P->harm ? 1 : 0, s);
+                                 lo, harm, static_cast<float*>(fold), s);
   CUDA_TRY(e);
   return FMM_OK;
 }
@@ -1448,23 +1481,30 @@ fmm_status do_m2m(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s) {
 // A harmonic tensor-core M2L wrote only the c <= 1 locals: L2L rebuilds the
 // rest first.  l == 2 (no parent far field) with a harmonic M2L: the rebuild
 // alone (no parent locals).
-bool harmonic_m2l_level(fmm_plan_t P, int l) { return P->harm && P->lev[l].tc && !(l == P->L && P->m2p); }
+bool harmonic_m2l_level(fmm_plan_t P, int l) {
+  return ((P->harm && P->lev[l].tc) || P->lev[l].fold_off) && !(l == P->L && P->m2p);
+}
 
 fmm_status do_l2l(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s, int accumulate) {
   const Level &q = P->lev[l - 1], &c = P->lev[l];
   const int harm = accumulate && harmonic_m2l_level(P, l) ? 1 : 0;
+  const void* red = harm && c.lred_off ? P->arena + c.lred_off : nullptr;  // CUDA-core harmonic: compact rows
   cudaError_t e;
-  if (l == 2) {
-    e = launch_l2l<float, float>(tt, q, nullptr, c, static_cast<float*>(P->Lx(l)), 1, harm, s);
+  if (l == 2 && c.f64) {
+    e = launch_l2l<double, double>(tt, q, nullptr, c, static_cast<double*>(P->Lx(l)), 1, harm,
+                                   static_cast<const double*>(red), s);
+  } else if (l == 2) {
+    e = launch_l2l<float, float>(tt, q, nullptr, c, static_cast<float*>(P->Lx(l)), 1, harm,
+                                 static_cast<const float*>(red), s);
   } else if (q.f64 && c.f64) {
     e = launch_l2l<double, double>(tt, q, static_cast<const double*>(P->Lx(l - 1)), c, static_cast<double*>(P->Lx(l)),
-                                   accumulate, 0, s);
+                                   accumulate, harm, static_cast<const double*>(red), s);
   } else if (q.f64) {
     e = launch_l2l<double, float>(tt, q, static_cast<const double*>(P->Lx(l - 1)), c, static_cast<float*>(P->Lx(l)),
-                                  accumulate, harm, s);
+                                  accumulate, harm, static_cast<const float*>(red), s);
   } else {
     e = launch_l2l<float, float>(tt, q, static_cast<const float*>(P->Lx(l - 1)), c, static_cast<float*>(P->Lx(l)),
-                                 accumulate, harm, s);
+                                 accumulate, harm, static_cast<const float*>(red), s);
   }
   CUDA_TRY(e);
   return FMM_OK;
@@ -1473,14 +1513,16 @@ fmm_status do_l2l(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s, int
 NbrGemm m2l_gemm(fmm_plan_t P, int l) {
   const Level& lv = P->lev[l];
   NbrGemm g;
-  g.A = P->M(l);
-  g.row_len = 8 * P->nc;
+  // harmonic: folded multipoles in, the c <= 1 locals out (compact rows)
+  const int nk = lv.fold_off ? P->nr : P->nc;
+  g.A = lv.fold_off ? static_cast<void*>(P->arena + lv.fold_off) : P->M(l);
+  g.row_len = 8 * nk;
   for (int q = 0; q < 3; ++q) g.grid[q] = lv.np[q];
   g.W = lv.f64 ? P->d_w_m2l_f64 : P->d_w_m2l_f32;
   g.tile_k = P->d_m2l_tile_k;
   g.tile_w = P->d_m2l_tile_w;
-  g.C = P->Lx(l);
-  g.n_cols = 8 * P->nc;
+  g.C = lv.lred_off ? static_cast<void*>(P->arena + lv.lred_off) : P->Lx(l);
+  g.n_cols = 8 * nk;
   g.ntiles = P->m2l_ntiles;
   g.accumulate = 0;  // M2L writes the level's locals; L2L adds the parent's
   g.shape = P->m2l_choice[l].shape;
@@ -1589,7 +1631,8 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
                            mplanes ? P->arena + lf.hi_off : nullptr, mplanes ? P->arena + lf.lo_off : nullptr,
                            P->near_tc ? P->arena + P->rho_hi_off : nullptr,
                            P->near_tc ? P->arena + P->rho_lo_off : nullptr, P->d_flag,
-                           (mplanes && P->harm) ? 1 : 0, s));
+                           ((mplanes && P->harm) || lf.fold_off) ? 1 : 0,
+                           lf.fold_off ? reinterpret_cast<T*>(P->arena + lf.fold_off) : nullptr, s));
   }
   const bool p2l = adjoint && P->m2p;  // leaf level by the transpose of M2P
   if (p2l)
@@ -1929,6 +1972,7 @@ extern "C" fmm_status fmm_solve_static(const fmm_grid* grid, int order, int leaf
   P->static_keep_tables = std::equal(key, key + 5, slot.key);
   fmm_opts o;
   fmm_default_opts(&o);  // FP32 on the CUDA cores
+  o.m2l_cartesian = 1;     // no folded arrays: the workspace limit stays that of the plain contraction
   fmm_status st = plan_init(P.get(), d3, grid->dx, grid->G, order, leaf, o, s, dev);
   if (st != FMM_OK) {
     for (int& k : slot.key) k = -1;  // the tables may be half written

@@ -54,6 +54,9 @@ struct Level {
   size_t bytes;    // bytes of one of the two arrays
   int tc;          // M2L of this level on the tensor cores
   size_t hi_off, lo_off;  // bf16 hi / lo planes of the multipoles (tensor-core bf16x3 levels)
+  // CUDA-core harmonic M2L: folded multipoles and the M2L's c <= 1 locals,
+  // rows of 8 (p+1)^2 values in the level's type (0: none)
+  size_t fold_off, lred_off;
 };
 
 // Neighbour-contraction ("implicit GEMM") description for the SIMT kernel:
@@ -109,19 +112,24 @@ struct TreeTables {
 // harm = 1: the planes hold the harmonic ((p+1)^2, c <= 1) components of the
 // folded multipoles (tree_common.cuh), rows of 8 (p+1)^2 values per parent.
 template <typename T>
+// Mfold (nullable, with harm): the folded components in the level's type,
+// rows of 8 (p+1)^2 values (the CUDA-core harmonic M2L reads them).
 cudaError_t launch_p2m(const TreeTables& t, const T* rho, const int dims[3], const Level& leaf, T* Mleaf, T* rho_box,
-                       void* Mhi, void* Mlo, void* rho_hi, void* rho_lo, int* flag, int harm, cudaStream_t s);
+                       void* Mhi, void* Mlo, void* rho_hi, void* rho_lo, int* flag, int harm, T* Mfold,
+                       cudaStream_t s);
 // M2M into the parent level; Mhi/Mlo (bf16 planes of the parent, harmonic
 // components when harm = 1) when non-NULL.
 template <typename Tc, typename Tp>
 cudaError_t launch_m2m(const TreeTables& t, const Level& child, const Tc* Mc, const Level& par, Tp* Mp, void* Mhi,
-                       void* Mlo, int harm, cudaStream_t s);
+                       void* Mlo, int harm, Tp* Mfold, cudaStream_t s);
 template <typename Tp, typename Tc>
 // accumulate = 1: child locals += shifted parent locals (after the level's M2L wrote them);
 // harm = 1: that M2L wrote only the harmonic components, the rest are rebuilt;
-// Lp = NULL: no parent locals (only the rebuild)
+// Lp = NULL: no parent locals (only the rebuild); Lred (nullable): the
+// M2L's c <= 1 locals in compact rows [parent][reduced coef][child] instead
+// of in the full rows
 cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, const Level& child, Tc* Lc, int accumulate,
-                       int harm, cudaStream_t s);
+                       int harm, const Tc* Lred, cudaStream_t s);
 template <typename T>
 cudaError_t launch_zero(T* p, size_t count, cudaStream_t s);
 // Copy of a cell grid in the leaf level's parent-blocked box order

@@ -16,7 +16,8 @@ using namespace tree;
 // Lp = NULL: no parent locals (the coarsest level: only the rebuild).
 template <int P, typename Tp, typename Tc>
 __global__ void __launch_bounds__(kThreads) l2l_kernel(Level par, const Tp* __restrict__ Lp, Level child,
-                                                       Tc* __restrict__ Lc, int accumulate, int harm) {
+                                                       Tc* __restrict__ Lc, int accumulate, int harm,
+                                                       const Tc* __restrict__ Lred) {
   constexpr int NC = ncoef_c(P);
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long p = t >> 3;  // box of the parent level == parent block of the child level
@@ -47,19 +48,25 @@ __global__ void __launch_bounds__(kThreads) l2l_kernel(Level par, const Tp* __re
     for (int k = 0; k < NC; ++k) L[k] = Tp(0);
   }
   Tc* dst = Lc + p * 8 * NC + c;
-  bool rebuild = false;
-  if constexpr (sizeof(Tc) == 4) rebuild = accumulate && harm;  // harmonic M2L levels are FP32
-  if (rebuild) {
-    Tc Lm[NC];
+  if (accumulate && harm) {
+    // The M2L wrote only its c <= 1 locals (in the full rows, tensor cores, or
+    // in compact rows [parent][reduced coef][child], CUDA cores).  The
+    // parent's shifted locals are harmonic too (an exact re-expansion of a
+    // harmonic polynomial), so the sum is: add the c <= 1 values, then rebuild
+    // the c >= 2 components of the sum from the Laplace identity, in place.
+    constexpr int NR = nred_c(P);
+    const Tc* red = Lred ? Lred + p * 8 * NR + c : nullptr;
 #pragma unroll
     for (int n = 0; n <= P; ++n)
 #pragma unroll
       for (int s = 0; s <= n; ++s)
 #pragma unroll
-        for (int cc = 0; cc <= 1 && cc <= s; ++cc) Lm[cidx(n - s, s - cc, cc)] = dst[cidx(n - s, s - cc, cc) * 8];
-    harmonic_expand<P, Tc>(Lm);
+        for (int cc = 0; cc <= 1 && cc <= s; ++cc)
+          L[cidx(n - s, s - cc, cc)] +=
+              Tp(red ? red[ridx(n - s, s - cc, cc) * 8] : dst[cidx(n - s, s - cc, cc) * 8]);
+    harmonic_expand<P, Tp>(L);
 #pragma unroll
-    for (int k = 0; k < NC; ++k) dst[k * 8] = Tc(Lm[k] + Tc(L[k]));
+    for (int k = 0; k < NC; ++k) dst[k * 8] = Tc(L[k]);
   } else {
 #pragma unroll
     for (int k = 0; k < NC; ++k) dst[k * 8] = accumulate ? Tc(dst[k * 8] + Tc(L[k])) : Tc(L[k]);
@@ -70,20 +77,20 @@ __global__ void __launch_bounds__(kThreads) l2l_kernel(Level par, const Tp* __re
 
 template <typename Tp, typename Tc>
 cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, const Level& child, Tc* Lc, int accumulate,
-                       int harm, cudaStream_t s) {
+                       int harm, const Tc* Lred, cudaStream_t s) {
   const long long threads = par.nbox * 8;
   if (threads == 0) return cudaSuccess;
   const int bs = small_grid_block(threads);
   FMM_ORDER_SWITCH(t.p, (l2l_kernel<PP, Tp, Tc><<<(unsigned)((threads + bs - 1) / bs), bs, 0, s>>>(par, Lp, child, Lc,
-                                                                                          accumulate, harm)));
+                                                                                          accumulate, harm, Lred)));
   return cudaGetLastError();
 }
 
 template cudaError_t launch_l2l<float, float>(const TreeTables&, const Level&, const float*, const Level&, float*, int,
-                                              int, cudaStream_t);
+                                              int, const float*, cudaStream_t);
 template cudaError_t launch_l2l<double, double>(const TreeTables&, const Level&, const double*, const Level&,
-                                                double*, int, int, cudaStream_t);
+                                                double*, int, int, const double*, cudaStream_t);
 template cudaError_t launch_l2l<double, float>(const TreeTables&, const Level&, const double*, const Level&, float*,
-                                               int, int, cudaStream_t);
+                                               int, int, const float*, cudaStream_t);
 
 }  // namespace fmmgb

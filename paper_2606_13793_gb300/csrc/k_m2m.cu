@@ -16,7 +16,7 @@ using namespace tree;
 template <int P, typename Tc, typename Tp>
 __global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(Tp) == 4) ? 2 : 1) m2m_kernel(Level child, const Tc* __restrict__ Mc, Level par,
                                                        Tp* __restrict__ Mp, __nv_bfloat16* __restrict__ Mhi,
-                                                       __nv_bfloat16* __restrict__ Mlo, int harm) {
+                                                       __nv_bfloat16* __restrict__ Mlo, int harm, Tp* __restrict__ Mfold) {
   constexpr int NC = ncoef_c(P);
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long p = t >> 3;
@@ -49,8 +49,7 @@ __global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(Tp) == 4) ? 2 : 1)
   const long long gp = ((long long)(pz >> 1) * par.np[1] + (py >> 1)) * par.np[0] + (px >> 1);
   const int cp = (px & 1) | ((py & 1) << 1) | ((pz & 1) << 2);
   Tp* dst = Mp + gp * 8 * NC + cp;
-  bool fold = false;
-  if constexpr (sizeof(Tp) == 4) fold = Mhi && harm;  // planes exist for FP32 levels only
+  const bool fold = harm && (Mhi || Mfold);
   if (!fold) {
     // sibling lanes share the writes: lane c stores coefficients c, c+8, ...
 #pragma unroll
@@ -63,9 +62,9 @@ __global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(Tp) == 4) ? 2 : 1)
     }
     return;
   }
-  // harmonic planes: every lane scales and folds the whole expansion, then
-  // stores its share of the FP32 row and of the (p+1)^2 folded components
-  // ([parent][reduced coef][child])
+  // harmonic rows: every lane scales and folds the whole expansion, then
+  // stores its share of the full row and of the (p+1)^2 folded components
+  // ([parent][reduced coef][child]) as bf16 planes and / or in the level's type
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
     const int n = (k >= 1) + (k >= 4) + (k >= 10) + (k >= 20) + (k >= 35) + (k >= 56) + (k >= 84) + (k >= 120);
@@ -81,7 +80,11 @@ __global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(Tp) == 4) ? 2 : 1)
     for (int s = 0; s <= n; ++s)
 #pragma unroll
       for (int cc = 0; cc <= 1 && cc <= s; ++cc) {
-        if ((r & 7) == c) store_split(Mhi, Mlo, (size_t)(gp * 8 * NR + cp + r * 8), M[cidx(n - s, s - cc, cc)]);
+        if ((r & 7) == c) {
+          const size_t o = (size_t)(gp * 8 * NR + cp + r * 8);
+          if (Mhi) store_split(Mhi, Mlo, o, M[cidx(n - s, s - cc, cc)]);
+          if (Mfold) Mfold[o] = M[cidx(n - s, s - cc, cc)];
+        }
         ++r;
       }
 }
@@ -90,21 +93,21 @@ __global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(Tp) == 4) ? 2 : 1)
 
 template <typename Tc, typename Tp>
 cudaError_t launch_m2m(const TreeTables& t, const Level& child, const Tc* Mc, const Level& par, Tp* Mp, void* Mhi,
-                       void* Mlo, int harm, cudaStream_t s) {
+                       void* Mlo, int harm, Tp* Mfold, cudaStream_t s) {
   const long long threads = child.npar * 8;
   if (threads == 0) return cudaSuccess;
   const int bs = small_grid_block(threads);
   FMM_ORDER_SWITCH(t.p, (m2m_kernel<PP, Tc, Tp><<<(unsigned)((threads + bs - 1) / bs), bs, 0, s>>>(
                             child, Mc, par, Mp, static_cast<__nv_bfloat16*>(Mhi), static_cast<__nv_bfloat16*>(Mlo),
-                            harm)));
+                            harm, Mfold)));
   return cudaGetLastError();
 }
 
 template cudaError_t launch_m2m<float, float>(const TreeTables&, const Level&, const float*, const Level&, float*,
-                                              void*, void*, int, cudaStream_t);
+                                              void*, void*, int, float*, cudaStream_t);
 template cudaError_t launch_m2m<double, double>(const TreeTables&, const Level&, const double*, const Level&,
-                                                double*, void*, void*, int, cudaStream_t);
+                                                double*, void*, void*, int, double*, cudaStream_t);
 template cudaError_t launch_m2m<float, double>(const TreeTables&, const Level&, const float*, const Level&, double*,
-                                               void*, void*, int, cudaStream_t);
+                                               void*, void*, int, double*, cudaStream_t);
 
 }  // namespace fmmgb

@@ -151,7 +151,6 @@ __device__ __forceinline__ void p2m_body(const Box& B, const T* __restrict__ rho
         dst[cidx(a, bb, cc) * 8] = acc[q];
         ++q;
       }
-  if constexpr (sizeof(T) == 4)  // planes exist for FP32 leaf levels only
   if (Mr) {
     // harmonic planes: this thread's parity class folds onto c = h (the fold
     // keeps the parity of c), staged as [parent][reduced coef][child]
@@ -188,14 +187,14 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho
                                                        __nv_bfloat16* __restrict__ Mlo, T* __restrict__ rho_box,
                                                        __nv_bfloat16* __restrict__ rhi,
                                                        __nv_bfloat16* __restrict__ rlo, int* __restrict__ flag,
-                                                       int harm) {
+                                                       int harm, T* __restrict__ Mfold) {
   constexpr int NC = ncoef_c(P);
   constexpr int ROW = 8 * NC;     // values per parent row
   constexpr int ROWP = ROW + 8;   // staged row pitch
   constexpr int ROWR = 8 * nred_c(P);  // values per parent row of the harmonic planes
   extern __shared__ __align__(16) unsigned char p2m_smem[];
   T* Ms = reinterpret_cast<T*>(p2m_smem);
-  T* Mr = (harm && Mhi) ? Ms + kP2mParents * ROWP : nullptr;
+  T* Mr = (harm && (Mhi || Mfold)) ? Ms + kP2mParents * ROWP : nullptr;
   const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
   const long long w = t >> 5;
   const Box B = box_of(leaf, (w >> 1) * 32 + (t & 31));
@@ -220,6 +219,10 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho
   } else {
     for (int i = threadIdx.x; i < count; i += kThreads) Mleaf[g0 + i] = Ms[(i / ROW) * ROWP + i % ROW];
   }
+  if (Mfold) {  // the folded multipoles in the level's type (CUDA-core harmonic M2L)
+    const int pc = (int)np * ROWR;
+    for (int i = threadIdx.x; i < pc; i += kThreads) Mfold[p0 * ROWR + i] = Mr[(i / ROWR) * (ROWR + 8) + i % ROWR];
+  }
   if (Mhi) {  // 8 values -> 16 bytes of hi and 16 bytes of lo
     const int rl = Mr ? ROWR : ROW, rp = Mr ? ROWR + 8 : ROWP;
     const T* src = Mr ? Mr : Ms;
@@ -243,11 +246,14 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho
 template <int P, typename T>
 cudaError_t p2m_launch(unsigned blocks, cudaStream_t s, const T* rho, int nx, int ny, int b, Level leaf, T* Mleaf,
                 __nv_bfloat16* Mhi, __nv_bfloat16* Mlo, T* rho_box, __nv_bfloat16* rhi, __nv_bfloat16* rlo, int* flag,
-                int harm) {
+                int harm, T* Mfold) {
   constexpr size_t full = (size_t)kP2mParents * (8 * ncoef_c(P) + 8) * sizeof(T);
-  // staged harmonic rows: FP32 leaf levels only (the planes feed the tensor cores)
-  constexpr size_t red = sizeof(T) == 4 ? (size_t)kP2mParents * (8 * nred_c(P) + 8) * sizeof(T) : 0;
-  const size_t smem = full + ((harm && Mhi) ? red : 0);
+  // staged harmonic rows, where they fit beside the full ones (the plan folds
+  // nothing at FP64 order 8, which would not)
+  constexpr size_t red0 = (size_t)kP2mParents * (8 * nred_c(P) + 8) * sizeof(T);
+  constexpr size_t red = full + red0 <= 227 * 1024 ? red0 : 0;
+  if (harm && (Mhi || Mfold) && red == 0) return cudaErrorInvalidValue;
+  const size_t smem = full + ((harm && (Mhi || Mfold)) ? red : 0);
   static bool attr = false;
   if (!attr && full + red > 48 * 1024) {
     const cudaError_t e =
@@ -256,7 +262,7 @@ cudaError_t p2m_launch(unsigned blocks, cudaStream_t s, const T* rho, int nx, in
     attr = true;
   }
   p2m_kernel<P, T><<<blocks, kThreads, smem, s>>>(rho, nx, ny, b, leaf, Mleaf, Mhi, Mlo, rho_box, rhi, rlo, flag,
-                                                  harm);
+                                                  harm, Mfold);
   return cudaGetLastError();
 }
 
@@ -264,20 +270,21 @@ cudaError_t p2m_launch(unsigned blocks, cudaStream_t s, const T* rho, int nx, in
 
 template <typename T>
 cudaError_t launch_p2m(const TreeTables& t, const T* rho, const int dims[3], const Level& leaf, T* Mleaf, T* rho_box,
-                       void* Mhi, void* Mlo, void* rho_hi, void* rho_lo, int* flag, int harm, cudaStream_t s) {
+                       void* Mhi, void* Mlo, void* rho_hi, void* rho_lo, int* flag, int harm, T* Mfold,
+                       cudaStream_t s) {
   const long long threads = leaf.npar * 16;  // two threads per box
   if (threads == 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   FMM_ORDER_SWITCH(t.p, (e = p2m_launch<PP, T>(grid_threads(threads), s,
                             rho, dims[0], dims[1], t.b, leaf, Mleaf, static_cast<__nv_bfloat16*>(Mhi),
                             static_cast<__nv_bfloat16*>(Mlo), rho_box, static_cast<__nv_bfloat16*>(rho_hi),
-                            static_cast<__nv_bfloat16*>(rho_lo), flag, harm)));
+                            static_cast<__nv_bfloat16*>(rho_lo), flag, harm, Mfold)));
   return e;
 }
 
 template cudaError_t launch_p2m<float>(const TreeTables&, const float*, const int*, const Level&, float*, float*,
-                                       void*, void*, void*, void*, int*, int, cudaStream_t);
+                                       void*, void*, void*, void*, int*, int, float*, cudaStream_t);
 template cudaError_t launch_p2m<double>(const TreeTables&, const double*, const int*, const Level&, double*, double*,
-                                        void*, void*, void*, void*, int*, int, cudaStream_t);
+                                        void*, void*, void*, void*, int*, int, double*, cudaStream_t);
 
 }  // namespace fmmgb

@@ -232,3 +232,25 @@ def test_bad_arguments_raise():
     plan.close()
     with pytest.raises(fmm.FMMError):
         fmm.FMMPlan((30, 32, 32), 4, 4, "fp32")
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+@pytest.mark.parametrize("p", [4, 6, 8])
+def test_cuda_core_harmonic_compression(orc, prec, tol, p):
+    """The CUDA-core M2L on the (p+1)^2 harmonic components (folded multipoles
+    in, the c <= 1 locals out, the rest rebuilt before L2L) and on every
+    Cartesian component, both against the oracle (FP64 at order 8 keeps the
+    Cartesian form: P2M could not stage the folded rows)."""
+    shape = (48, 40, 56)
+    rho = inputs.lognormal(shape, seed=p).astype(np.float64)
+    ref = orc.fmm(rho, 4, p)["phi"]
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    for harmonic in (True, False):
+        plan = fmm.FMMPlan(shape, p, 4, prec, accel=False, harmonic=harmonic)
+        phi = plan.solve(torch.from_numpy(rho).cuda().to(dt))
+        torch.cuda.synchronize()
+        plan.check()
+        plan.close()
+        err = rel_l2(phi.double().cpu().numpy(), ref)
+        print(f"{prec} p={p} harmonic={harmonic}: {err:.2e}")
+        assert err <= tol
