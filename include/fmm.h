@@ -94,10 +94,10 @@ typedef struct {
                          ~6x the leaf-level work).  With 1, accel must not be 2
                          and fmm_solve_adjoint returns FMM_ERR_UNSUPPORTED
                          (the truncated M2P operator is not symmetric)          */
-  int m2l_cartesian;  /* 0 (default): the M2L (bf16x3 tensor cores, and the
-                         CUDA cores of FMM_FP32 / FMM_FP64; TF32 and the FP64
-                         levels of the mixed precisions stay Cartesian) and the
-                         tensor-core M2P contract the (p+1)^2 harmonic components
+  int m2l_cartesian;  /* 0 (default): the M2L (tensor cores, and the CUDA
+                         cores of FMM_FP32 / FMM_FP64; the FP64 levels of the
+                         mixed precisions stay Cartesian) and the tensor-core
+                         M2P contract the (p+1)^2 harmonic components
                          (multipoles folded by the Laplace identity of the
                          derivatives of 1/r, which keeps the total order; the
                          remaining locals rebuilt from the same identity before

@@ -172,7 +172,7 @@ struct fmm_plan_s {
   int near_ntiles = 0;
   // tensor-core M2L and near field
   int tc_kind = -1;
-  bool harm = false;  // harmonic compression of the bf16x3 tensor-core M2L/M2P (planes of nr components)
+  bool harm = false;  // harmonic compression of the tensor-core M2L/M2P (activation rows of nr components)
   bool harm_cc = false;  // harmonic compression of the CUDA-core M2L (Level::fold_off / lred_off)
   int nr = 0;         // (p + 1)^2
   int plane_nc() const { return harm ? nr : nc; }
@@ -1027,8 +1027,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
   const bool tcp = tc_precision(o.precision);
   if (tcp) P->tc_kind = o.precision == FMM_M2L_BF16X3 ? TC_BF16X3 : TC_TF32;
   P->nr = (order + 1) * (order + 1);
-  P->harm = tcp && P->tc_kind == TC_BF16X3 && !o.m2l_cartesian && order >= 2 &&
-            P->nr <= kTcMaxColMap;
+  P->harm = tcp && !o.m2l_cartesian && order >= 2 && P->nr <= kTcMaxColMap;
   {
     // CUDA-core precisions only: in the mixed ones the CUDA-core (FP64) levels
     // run beside the tensor-core levels and, compressed, their denser DFMA
@@ -1066,6 +1065,10 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
       off = align(off + red);
       lv.lred_off = off;
       off = align(off + red);
+    }
+    if (P->harm && lv.tc && P->tc_kind == TC_TF32) {  // TF32 reads FP32 rows: the folded ones
+      lv.fold_off = off;
+      off = align(off + (size_t)lv.npar * 8 * P->nr * 4);
     }
     if (lv.tc && P->tc_kind == TC_BF16X3) {
       const size_t plane = (size_t)lv.npar * 8 * P->plane_nc() * 2;
@@ -1208,7 +1211,8 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
           if (e == cudaSuccess)
             e = make_row_map(P->map_lo[l], P->arena + lv.lo_off, 8 * P->plane_nc(), 2, lv.np, 64);
         } else {
-          e = make_row_map(P->map_hi[l], P->arena + lv.m_off, 8 * P->nc, 4, lv.np, 32);
+          e = lv.fold_off ? make_row_map(P->map_hi[l], P->arena + lv.fold_off, 8 * P->nr, 4, lv.np, 32)
+                          : make_row_map(P->map_hi[l], P->arena + lv.m_off, 8 * P->nc, 4, lv.np, 32);
           if (e == cudaSuccess) std::memcpy(P->map_lo[l], P->map_hi[l], 128);
         }
         if (e != cudaSuccess) return cleanup(fail(FMM_ERR_CUDA, "tensor map encoding failed for level %d", l));
@@ -1482,7 +1486,7 @@ fmm_status do_m2m(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s) {
 // rest first.  l == 2 (no parent far field) with a harmonic M2L: the rebuild
 // alone (no parent locals).
 bool harmonic_m2l_level(fmm_plan_t P, int l) {
-  return ((P->harm && P->lev[l].tc) || P->lev[l].fold_off) && !(l == P->L && P->m2p);
+  return ((P->harm && P->lev[l].tc) || P->lev[l].lred_off) && !(l == P->L && P->m2p);
 }
 
 fmm_status do_l2l(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s, int accumulate) {
