@@ -109,10 +109,11 @@ typedef struct {
                          order-1: multipole components above mult_order take
                          no part in M2L / M2P (locals stay to `order`): the
                          paper keeps multipoles to 2 and locals to 3 (Sec. 2.1,
-                         2.3), i.e. order 3, mult_order 2.  Not symmetric, so
-                         fmm_solve_adjoint returns FMM_ERR_UNSUPPORTED; start
-                         from fmm_default_opts (a zeroed struct means
-                         monopoles only)                                      */
+                         2.3), i.e. order 3, mult_order 2.  Not symmetric: its
+                         transpose swaps the two limits, so such a plan also
+                         holds M2L weights with locals to mult_order, which
+                         fmm_solve_adjoint runs.  Start from fmm_default_opts
+                         (a zeroed struct means monopoles only)               */
   int reserved[2];    /* must be zero */
 } fmm_opts;
 

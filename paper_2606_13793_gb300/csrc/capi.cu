@@ -54,13 +54,14 @@ fmm_status fail(fmm_status st, const char* fmt, ...) {
 struct MultiIndex {
   int p = 0, nc = 0;
   int mo = 0;  // multipole order limit (components above it take no part in M2L / M2P); p by default
+  int lo = 0;  // local order limit of the M2L (p by default; mo of the forward in its transpose)
   std::vector<int> a, b, c;  // components, canonical order
   int index(int x, int y, int z) const {
     const int n = x + y + z;
     return n * (n + 1) * (n + 2) / 6 + (n - x) * (n - x + 1) / 2 + (n - x - y);
   }
   void init(int order) {
-    p = mo = order;
+    p = mo = lo = order;
     a.clear(), b.clear(), c.clear();
     for (int n = 0; n <= p; ++n)
       for (int x = n; x >= 0; --x)
@@ -177,6 +178,14 @@ struct fmm_plan_s {
   int nr = 0;         // (p + 1)^2
   int plane_nc() const { return harm ? nr : nc; }
   TcLaunch tc{};
+  // mult_order < order: the M2L with the two limits swapped (multipoles to p,
+  // locals to mult_order), which the adjoint solve runs (transposed = true)
+  bool asym = false, transposed = false;
+  void* d_w_m2l_f32_t = nullptr;
+  void* d_w_m2l_f64_t = nullptr;
+  int* d_m2l_tile_k_t = nullptr;
+  long long* d_m2l_tile_w_t = nullptr;
+  TcLaunch tc_t{};
   bool near_tc = false;
   std::vector<TcLaunch> tcn;  // near field: kTcMaxPasses passes per launch
   alignas(64) unsigned char map_near_hi[128];
@@ -363,7 +372,7 @@ double m2l_entry(const MultiIndex& mi, const TaylorTable& tt, int d, int k, int 
   const int be = n / 8, ct = n % 8, al = k / 8, cs = k % 8;
   if (be >= nc || al >= nc) return 0.0;
   const int ob = level_of_order(mi, be), oa = level_of_order(mi, al);
-  if (oa + ob > p || oa > mi.mo) return 0.0;
+  if (oa + ob > p || oa > mi.mo || ob > mi.lo) return 0.0;
   const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
   int u[3];
   for (int q = 0; q < 3; ++q) u[q] = ((ct >> q) & 1) - ((cs >> q) & 1) - 2 * D[q];
@@ -1184,6 +1193,31 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     P->m2l_ntiles = (int)tk.size();
     P->h_m2l_tile_k = tk;
     if ((st = P->upload(tk, &P->d_m2l_tile_k, s)) || (st = P->upload(tw, &P->d_m2l_tile_w, s))) return cleanup(st);
+    MultiIndex mt = P->mi;  // the transpose of a mult_order < order operator swaps the limits
+    mt.mo = P->p;
+    mt.lo = P->mi.mo;
+    P->asym = P->mi.mo < P->p && P->L >= 2;
+    if (P->asym && (any64 || any32)) {
+      std::vector<int> tk2;
+      std::vector<long long> tw2;
+      if (any64) {
+        std::vector<double> W;
+        m2l_weights<double>(mt, tt, W, tk2, tw2, true, P->harm_cc);
+        double* d = nullptr;
+        if ((st = P->upload(W, &d, s))) return cleanup(st);
+        P->d_w_m2l_f64_t = d;
+      }
+      if (any32) {
+        std::vector<float> W;
+        m2l_weights<float>(mt, tt, W, tk2, tw2, true, P->harm_cc);
+        float* d = nullptr;
+        if ((st = P->upload(W, &d, s))) return cleanup(st);
+        P->d_w_m2l_f32_t = d;
+      }
+      if ((int)tk2.size() != P->m2l_ntiles) return cleanup(fail(FMM_ERR_CUDA, "transposed M2L tiles differ"));
+      if ((st = P->upload(tk2, &P->d_m2l_tile_k_t, s)) || (st = P->upload(tw2, &P->d_m2l_tile_w_t, s)))
+        return cleanup(st);
+    }
     if (anytc) {
       TcHost H;
       if (!build_tc(P->mi, tt, P->tc_kind, H, P->harm))
@@ -1202,6 +1236,18 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
         for (size_t r = 0; r < red.size(); ++r) P->tc.col_map[r] = (int16_t)red[r];
       }
       P->tc.err = nullptr;  // set below, after the flag exists
+      if (P->asym) {
+        TcHost Ht;
+        if (!build_tc(mt, tt, P->tc_kind, Ht, P->harm))
+          return cleanup(fail(FMM_ERR_UNSUPPORTED, "order too high for the transposed tensor-core schedule"));
+        unsigned char* dwt = nullptr;
+        if ((st = P->upload(Ht.W, &dwt, s))) return cleanup(st);
+        P->tc_t = P->tc;  // same maps, columns and kind; its own passes and weights
+        P->tc_t.W = dwt;
+        P->tc_t.npass = Ht.npass;
+        P->tc_t.a_stages = Ht.a_stages;
+        for (int i = 0; i < Ht.npass; ++i) P->tc_t.pass[i] = Ht.pass[i];
+      }
       for (int l = 2; l <= P->L; ++l) {
         const Level& lv = P->lev[l];
         if (!lv.tc) continue;
@@ -1342,6 +1388,8 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
   }
   P->tc.err = P->d_flag;
   P->tc.accumulate = 0;
+  P->tc_t.err = P->d_flag;
+  P->tc_t.accumulate = 0;
   P->tcm.err = P->d_flag;
   for (int l = 2; l <= P->L; ++l)
     if (!P->lev[l].tc) zrun_default(m2l_gemm(P, l), P->h_m2l_tile_k, &P->m2l_choice[l], P->lev[l].f64);
@@ -1522,9 +1570,10 @@ NbrGemm m2l_gemm(fmm_plan_t P, int l) {
   g.A = lv.fold_off ? static_cast<void*>(P->arena + lv.fold_off) : P->M(l);
   g.row_len = 8 * nk;
   for (int q = 0; q < 3; ++q) g.grid[q] = lv.np[q];
-  g.W = lv.f64 ? P->d_w_m2l_f64 : P->d_w_m2l_f32;
-  g.tile_k = P->d_m2l_tile_k;
-  g.tile_w = P->d_m2l_tile_w;
+  const bool tr = P->transposed && P->asym;
+  g.W = lv.f64 ? (tr ? P->d_w_m2l_f64_t : P->d_w_m2l_f64) : (tr ? P->d_w_m2l_f32_t : P->d_w_m2l_f32);
+  g.tile_k = tr ? P->d_m2l_tile_k_t : P->d_m2l_tile_k;
+  g.tile_w = tr ? P->d_m2l_tile_w_t : P->d_m2l_tile_w;
   g.C = lv.lred_off ? static_cast<void*>(P->arena + lv.lred_off) : P->Lx(l);
   g.n_cols = 8 * nk;
   g.ntiles = P->m2l_ntiles;
@@ -1604,7 +1653,7 @@ fmm_status do_p2l(fmm_plan_t P, cudaStream_t s) {
 fmm_status do_m2l(fmm_plan_t P, int l, cudaStream_t s) {
   const Level& lv = P->lev[l];
   if (lv.tc) {
-    TcLaunch L = P->tc;
+    TcLaunch L = (P->transposed && P->asym) ? P->tc_t : P->tc;
     L.C = static_cast<float*>(P->Lx(l));
     for (int q = 0; q < 3; ++q) L.grid[q] = lv.np[q];
     CUDA_TRY(launch_m2l_tc(L, P->map_hi[l], P->map_lo[l], s));
@@ -1752,8 +1801,6 @@ fmm_status fmm_solve(fmm_plan_t P, const void* rho, void* phi, void* accel, void
 fmm_status fmm_solve_adjoint(fmm_plan_t P, const void* grad_phi, const void* grad_accel, void* grad_rho, void* stream) {
   if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
   if (!grad_rho || (!grad_phi && !grad_accel)) return fail(FMM_ERR_ARG, "grad_rho and one gradient must be non-NULL");
-  if (P->mi.mo < P->p)
-    return fail(FMM_ERR_UNSUPPORTED, "no adjoint with mult_order < order (the transpose swaps the two orders)");
   if (grad_accel && P->near_comps == 4)
     return fail(FMM_ERR_UNSUPPORTED, "the adjoint of the analytic acceleration is not built (use accel = 1)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1771,9 +1818,14 @@ fmm_status fmm_solve_adjoint(fmm_plan_t P, const void* grad_phi, const void* gra
                                             static_cast<float*>(w), s));
     }
   }
-  if (P->f64_data())
-    return run_solve<double>(P, static_cast<const double*>(w), static_cast<double*>(grad_rho), nullptr, s, true);
-  return run_solve<float>(P, static_cast<const float*>(w), static_cast<float*>(grad_rho), nullptr, s, true);
+  // mult_order < order: the transpose runs the M2L with the orders swapped
+  P->transposed = true;
+  const fmm_status r =
+      P->f64_data()
+          ? run_solve<double>(P, static_cast<const double*>(w), static_cast<double*>(grad_rho), nullptr, s, true)
+          : run_solve<float>(P, static_cast<const float*>(w), static_cast<float*>(grad_rho), nullptr, s, true);
+  P->transposed = false;
+  return r;
 }
 
 fmm_status fmm_solve_host(fmm_plan_t P, const void* rho_host, void* phi_host, void* accel_host, void* stream) {
