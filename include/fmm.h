@@ -91,9 +91,11 @@ typedef struct {
   int final_stage;    /* 0: M2L + L2P at the leaf level too; 1: the paper's own
                          final stage (Sec. 4): the leaf interaction list is
                          evaluated by M2P at the cell centres (more accurate,
-                         ~6x the leaf-level work).  With 1, accel must not be 2
-                         and fmm_solve_adjoint returns FMM_ERR_UNSUPPORTED
-                         (the truncated M2P operator is not symmetric)          */
+                         ~6x the leaf-level work).  With 1, accel must not be 2.
+                         The truncated M2P operator is not symmetric: its
+                         transpose (P2L, the leaf cells' own sources expanded
+                         about the listed boxes' centres) is what
+                         fmm_solve_adjoint runs at the leaf level           */
   int m2l_cartesian;  /* 0 (default): the M2L (tensor cores, and the CUDA
                          cores of FMM_FP32 / FMM_FP64; the FP64 levels of the
                          mixed precisions stay Cartesian) and the tensor-core
@@ -159,7 +161,17 @@ fmm_status fmm_solve(fmm_plan_t plan, const void* rho, void* phi, void* accel, v
  *   grad_rho   : device [nz][ny][nx] (written): A^T (grad_phi - FD^T grad_accel/dx) G dx^2.
  * With |alpha|+|beta| <= order the FMM operator A is symmetric (Green's
  * function symmetry, Sec. 2.3), so A^T is the same chain of kernels applied to
- * the adjoint source; the stencil transpose FD^T is its own kernel.
+ * the adjoint source; the stencil transpose FD^T is its own kernel.  The two
+ * truncations that break the symmetry run their transposes: final_stage = 1
+ * replaces the leaf M2P by P2L, and mult_order < order runs the M2L with the
+ * multipole and local limits swapped.  Errors: FMM_ERR_ARG,
+ * FMM_ERR_UNSUPPORTED (grad_accel with accel = 2), FMM_ERR_CUDA.
+ *
+ * A plan runs one call at a time: fmm_solve, fmm_solve_adjoint,
+ * fmm_solve_host and fmm_plan_autotune share the plan's workspace arena (and
+ * the adjoint switches the plan's M2L weights for its duration), so calls on
+ * one plan are made from one host thread at a time and ordered on one stream.
+ * Separate plans are independent.
  */
 fmm_status fmm_solve_adjoint(fmm_plan_t plan, const void* grad_phi, const void* grad_accel, void* grad_rho,
                              void* stream);

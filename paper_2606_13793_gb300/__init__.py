@@ -160,7 +160,11 @@ def _stream_handle(stream=None):
 
 
 class FMMPlan:
-    """One solver for a fixed grid shape, order, leaf size and precision."""
+    """One solver for a fixed grid shape, order, leaf size and precision.
+
+    A plan runs one call at a time: its solves, adjoints, host solves and
+    autotuning share one device workspace, so use a plan from one thread and
+    order its calls on one stream (separate plans are independent)."""
 
     def __init__(self, shape, order: int = 6, leaf: int = 4, precision: str = "fp32", dx: float = 1.0,
                  G: float = 1.0, n_fp64_levels: int = 3, accel=True, final_stage: str = "m2l", harmonic=True,
@@ -185,8 +189,10 @@ class FMMPlan:
         opts.accel = 2 if accel == "analytic" else (1 if accel else 0)
         # final_stage: "m2l" (M2L + L2P at the leaf level) or "m2p" (the
         # paper's final stage: M2P at the cell centres)
+        if final_stage not in ("m2l", "m2p"):
+            raise ValueError('final_stage must be "m2l" or "m2p"')
         opts.final_stage = 1 if final_stage == "m2p" else 0
-        # harmonic: bf16x3 tensor-core M2L/M2P on the (p+1)^2 harmonic
+        # harmonic: M2L (and tensor-core M2P) on the (p+1)^2 harmonic
         # components (False: every Cartesian component)
         opts.m2l_cartesian = 0 if harmonic else 1
         # mult_order: multipoles kept to this order (None: the order itself;

@@ -82,6 +82,14 @@ def test_argument_validation_without_gpu(lib):
     assert lib.fmm_plan_destroy(None) == 0
 
 
+def test_binding_rejects_unknown_options(lib):
+    # checked in the binding, before any device call
+    with pytest.raises(ValueError, match="final_stage"):
+        fmm.FMMPlan((8, 8, 8), 2, 4, final_stage="p2p")
+    with pytest.raises(ValueError, match="precision"):
+        fmm.FMMPlan((8, 8, 8), 2, 4, precision="fp16")
+
+
 def test_default_options(lib):
     opts = fmm._Opts()
     lib.fmm_default_opts(ctypes.byref(opts))
