@@ -58,6 +58,9 @@ def parse():
                     help="bf16x3: tensor-core M2L on every Cartesian component instead of the (p+1)^2 harmonic ones")
     ap.add_argument("--final-stage", default="m2l", choices=["m2l", "m2p"],
                     help="leaf level by M2L + L2P (m2l) or by the interaction list evaluated at the cells (m2p)")
+    ap.add_argument("--fp64-levels", type=int, default=3,
+                    help="tensor-core precisions: M2L levels 2 .. 1+N run in FP64 on the CUDA cores (default 3, "
+                         "the library's default)")
     return ap.parse_args()
 
 
@@ -327,7 +330,8 @@ def main():
     rho = torch.from_numpy(rho_np).cuda()
     plan = fmm.FMMPlan((n, n, n), p, b, args.precision, dx=dx,
                        accel="analytic" if args.accel == "analytic" else True, final_stage=args.final_stage,
-                       harmonic=not args.m2l_cartesian)
+                       harmonic=not args.m2l_cartesian, n_fp64_levels=args.fp64_levels)
+    tc_prec = args.precision in ("bf16x3", "tf32")
     harmonic = args.precision == "bf16x3" and not args.m2l_cartesian  # tensor-core levels
     harmonic_cc = (not args.m2l_cartesian and args.order >= 2         # CUDA-core levels (FP32 / FP64 plans)
                    and args.precision in ("fp32", "fp64"))
@@ -461,7 +465,8 @@ def main():
     # overstates their share); else the largest stage.
     dom = "m2l_tc" if "m2l_tc" in per_kernel else max(per_kernel, key=lambda k: per_kernel[k]["ms_per_step"])
     workload = f"{n}^3 p={p} leaf {b} {args.precision}" + (" m2p" if args.final_stage == "m2p" else "") + \
-        (" harmonic" if harmonic else "")
+        (" harmonic" if harmonic else "") + \
+        (f" fp64 levels {args.fp64_levels}" if tc_prec and args.fp64_levels != 3 else "")
     traffic = profiled_traffic(dom + "/" + args.precision, workload)
     d = per_kernel[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": "TFLOP/s",
@@ -491,6 +496,7 @@ def main():
                                  f"rho ({n ** 3 * 4 / 2 ** 20:.0f} MiB) fits in L2: not a bandwidth-valid size",
                            "parallelism": f"replicas x{world}", "cuda_core_variants": tuning, "accel": args.accel,
                            "final_stage": args.final_stage,
+                           **({"fp64_m2l_levels": f"2..{1 + args.fp64_levels}"} if tc_prec else {}),
                            "m2l_components": "harmonic (p+1)^2" if (harmonic or harmonic_cc) else "cartesian nc(p)",
                            "autotuned": not args.no_autotune, **compare},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
