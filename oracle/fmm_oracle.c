@@ -196,7 +196,11 @@ static void or_m2m(const or_index* ix, const double* Mc, const double d[3], doub
       const int* b = ix->mi[kb];
       if (b[0] > a[0] || b[1] > a[1] || b[2] > a[2]) continue;
       double w = 1.0;
+#if ORACLE_MUTANT == 10 /* planted mistake: binomial coefficients dropped */
+      for (int q = 0; q < 3; ++q) w *= or_ipow(d[q], a[q] - b[q]);
+#else
       for (int q = 0; q < 3; ++q) w *= or_binom(a[q], b[q]) * or_ipow(d[q], a[q] - b[q]);
+#endif
       s += w * Mc[kb];
     }
     Mp[ka] += s;
@@ -286,7 +290,11 @@ static double or_l2p(const or_index* ix, const double* L, const double e[3]) {
   for (int k = 0; k < ix->nc; ++k) {
     const int* b = ix->mi[k];
     double w = 1.0;
+#if ORACLE_MUTANT == 11 /* planted mistake: the 1/beta! factor dropped */
+    for (int q = 0; q < 3; ++q) w *= or_ipow(e[q], b[q]);
+#else
     for (int q = 0; q < 3; ++q) w *= or_ipow(e[q], b[q]) / or_fact(b[q]);
+#endif
     s += w * L[k];
   }
   return s;
@@ -490,7 +498,11 @@ static void or_p2m_region(const or_index* ix, const double* rho, const int N[3],
         if (x < 0 || x >= N[0]) continue;
         double m = rho[((long)z * N[1] + y) * N[0] + x];
         if (m == 0.0) continue;
+#if ORACLE_MUTANT == 9 /* planted mistake: cells placed at their lower corners */
+        double e[3] = {x - c[0], y - c[1], z - c[2]};
+#else
         double e[3] = {x + 0.5 - c[0], y + 0.5 - c[1], z + 0.5 - c[2]};
+#endif
         for (int k = 0; k < ix->nc; ++k) {
           const int* a = ix->mi[k];
           M[k] += m * or_ipow(e[0], a[0]) * or_ipow(e[1], a[1]) * or_ipow(e[2], a[2]);
@@ -723,7 +735,11 @@ static double or_fd_deriv(const double* f, long stride, int i, int n) {
 #define F(q) f[(long)(q) * stride]
   if (n == 1) return 0.0;
   if (n == 2) return F(1) - F(0);
+#if ORACLE_MUTANT == 12 /* planted mistake: outer weights of the 5-point stencil with the wrong sign */
+  if (i >= 2 && i <= n - 3) return (F(i + 2) + 8.0 * F(i + 1) - 8.0 * F(i - 1) - F(i - 2)) / 12.0;
+#else
   if (i >= 2 && i <= n - 3) return (-F(i + 2) + 8.0 * F(i + 1) - 8.0 * F(i - 1) + F(i - 2)) / 12.0;
+#endif
   if (i >= 1 && i <= n - 2) return (F(i + 1) - F(i - 1)) / 2.0;
   if (i == 0) return (-3.0 * F(0) + 4.0 * F(1) - F(2)) / 2.0;
   return (3.0 * F(n - 1) - 4.0 * F(n - 2) + F(n - 3)) / 2.0;
@@ -767,7 +783,11 @@ static void or_fd_scatter(double* out, long stride, int i, int n, double w) {
   } else if (i == 0) {
     O(0) += -3.0 * w / 2.0;
     O(1) += 4.0 * w / 2.0;
+#if ORACLE_MUTANT == 13 /* planted mistake: one-sided edge weight scattered with the wrong sign */
+    O(2) += w / 2.0;
+#else
     O(2) += -w / 2.0;
+#endif
   } else {
     O(n - 1) += 3.0 * w / 2.0;
     O(n - 2) += -4.0 * w / 2.0;
@@ -989,7 +1009,11 @@ int oracle_adjoint(const double* gphi, const double* gaccel, int nx, int ny, int
     for (int k = 0; k < nc; ++k) {
       const int* be = ix->mi[k];
       double t = 1.0;
+#if ORACLE_MUTANT == 14 /* planted mistake: L2P^T without the 1/beta! factor */
+      for (int q = 0; q < 3; ++q) t *= or_ipow(e[q], be[q]);
+#else
       for (int q = 0; q < 3; ++q) t *= or_ipow(e[q], be[q]) / or_fact(be[q]);
+#endif
       La[k] += w[c] * t;
     }
   }

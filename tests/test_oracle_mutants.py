@@ -20,9 +20,22 @@ MUTANTS = {
     6: "near-field pair force pointing away from the mass",
     7: "final-stage M2P without the (-1)^|alpha| factor",
     8: "multipole and local order limits applied to the wrong sides",
+    9: "P2M with the cells at their lower corners instead of their centres",
+    10: "M2M without the binomial coefficients",
+    11: "L2P without the 1/beta! factor",
+    12: "5-point stencil with its outer weights' signs flipped",
+    13: "stencil transpose with a one-sided edge weight of the wrong sign",
+    14: "adjoint chain's L2P^T without the 1/beta! factor",
 }
 
+# Cheap single-operator pins first: a mutant's battery stops at the first pin
+# that fails.
 PINS = [
+    ops.test_p2m_closed_forms,
+    ops.test_m2m_equals_direct_p2m_about_parent,
+    ops.test_l2p_closed_form,
+    ops.test_fd_stencils_exact_on_polynomials,
+    ops.test_fd_adjoint_is_transpose,
     ops.test_m2l_converges_geometrically,
     ops.test_l2l_then_l2p_is_exact,
     solve.test_converges_to_direct_sum_in_p,
@@ -33,16 +46,19 @@ PINS = [
     m2p.test_m2p_converges_and_beats_m2l_l2p,
     orders.test_monopole_only_far_field_ignores_mass_moved_inside_boxes,
     orders.test_order_zero_locals_give_a_constant_far_field_per_box,
+    solve.test_adjoint_chain_is_transpose,
 ]
 
 
-def _failures(orc):
+def _failures(orc, first=False):
     failed = []
     for pin in PINS:
         try:
             pin(orc)
         except AssertionError:
             failed.append(getattr(pin, "__name__", "lambda"))
+            if first:
+                break
     return failed
 
 
@@ -54,5 +70,6 @@ def test_battery_passes_on_the_oracle(orc):
 def test_pins_catch_planted_mistake(tmp_path, k):
     path = oracle.build(str(tmp_path / f"liboracle_mutant{k}.so"), mutant=k, force=True)
     mutant = oracle.Oracle(oracle.load(path))
-    failed = _failures(mutant)
+    failed = _failures(mutant, first=True)
+    print(f"mutant {k} ({MUTANTS[k]}): caught by {failed[0] if failed else 'nothing'}")
     assert failed, f"no pin caught mutant {k}: {MUTANTS[k]}"
