@@ -312,7 +312,11 @@ static void or_l2p_grad(const or_index* ix, const double* L, const double e[3], 
       double w = 1.0;
       for (int r = 0; r < 3; ++r) {
         const int pw = b[r] - (r == q);
+#if ORACLE_MUTANT == 15 /* planted mistake: the undifferentiated factorials kept */
+        w *= or_ipow(e[r], pw) / or_fact(b[r]);
+#else
         w *= or_ipow(e[r], pw) / or_fact(pw);
+#endif
       }
       g[q] += w * L[k];
     }
@@ -660,6 +664,9 @@ static double or_near_cell(const or_hier* H, const double* rho, int x, int y, in
       if (qj < 0 || qj >= lf->n[1]) continue;
       for (int qi = bi - 1; qi <= bi + 1; ++qi) {
         if (qi < 0 || qi >= lf->n[0]) continue;
+#if ORACLE_MUTANT == 16 /* planted mistake: only the 6 face neighbours (edge and corner boxes dropped) */
+        if (abs(qi - bi) + abs(qj - bj) + abs(qk - bk) > 1) continue;
+#endif
         for (int sz = qk * b; sz < qk * b + b; ++sz)
           for (int sy = qj * b; sy < qj * b + b; ++sy)
             for (int sx = qi * b; sx < qi * b + b; ++sx) {

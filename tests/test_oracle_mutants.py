@@ -26,6 +26,8 @@ MUTANTS = {
     12: "5-point stencil with its outer weights' signs flipped",
     13: "stencil transpose with a one-sided edge weight of the wrong sign",
     14: "adjoint chain's L2P^T without the 1/beta! factor",
+    15: "gradient of L2P with the undifferentiated factorials",
+    16: "near field over the face neighbours only (edge and corner boxes dropped)",
 }
 
 # Cheap single-operator pins first: a mutant's battery stops at the first pin
