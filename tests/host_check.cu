@@ -1,4 +1,13 @@
-// Host-side check of the tensor-core schedules (no GPU needed).
+// Host-side checks of the plan's tables and tensor-core schedules (no GPU
+// needed).  capi.cu, the library's host code, is compiled into this program.
+//
+//   host_check            the tensor-core schedules (below)
+//   host_check plant      planted schedule corruptions, each must be caught
+//   host_check tables DIR writes the plan's M2L, M2P and near-field weight
+//                         tables (FP64, raw) into DIR for comparison with the
+//                         oracle's operators
+//   host_check harmonic   harmonic compression against the Cartesian
+//                         contraction, orders 2..8 (exact up to rounding)
 //
 // The library's plan packs every tensor-core contraction (M2L per level,
 // final-stage M2P, the near field) into passes of MMA spans, per-issuer
@@ -28,6 +37,7 @@
 // accumulator opened late, a ring smaller than a span) and exits 0 only if
 // every corruption is caught.
 #include "capi.cu"
+#include "tree_common.cuh"
 
 #include <cstdio>
 #include <random>
@@ -321,10 +331,142 @@ int planted_mistakes() {
   return missed;
 }
 
+// ---------------------------------------------------------------- tables --
+
+bool write_table(const std::string& path, const std::vector<double>& v) {
+  FILE* f = std::fopen(path.c_str(), "wb");
+  if (!f) return false;
+  const bool ok = std::fwrite(v.data(), sizeof(double), v.size(), f) == v.size();
+  return std::fclose(f) == 0 && ok;
+}
+
+// M2L weights [27][8 nc][8 nc] (neighbour parent, alpha*8 + source child,
+// beta*8 + target child) with multipole / local limits mo, lo.
+bool dump_m2l(const std::string& dir, int p, int mo, int lo) {
+  MultiIndex mi;
+  mi.init(p);
+  mi.mo = mo, mi.lo = lo;
+  TaylorTable tt;
+  tt.build(mi);
+  const int K = 8 * mi.nc;
+  std::vector<double> W((size_t)27 * K * K);
+  for (int d = 0; d < 27; ++d)
+    for (int k = 0; k < K; ++k)
+      for (int n = 0; n < K; ++n) W[((size_t)d * K + k) * K + n] = m2l_entry(mi, tt, d, k, n);
+  char name[64];
+  std::snprintf(name, sizeof name, "/m2l_p%d_mo%d_lo%d.bin", p, mo, lo);
+  return write_table(dir + name, W);
+}
+
+// Final-stage M2P weights [27][8 nc][8 b^3] (neighbour parent, alpha*8 +
+// source child, target child * b^3 + cell).
+bool dump_m2p(const std::string& dir, int p, int b) {
+  MultiIndex mi;
+  mi.init(p);
+  M2pTable tab;
+  tab.build(mi, b);
+  const int K = 8 * mi.nc, N = 8 * b * b * b;
+  std::vector<double> W((size_t)27 * K * N);
+  for (int d = 0; d < 27; ++d)
+    for (int k = 0; k < K; ++k)
+      for (int n = 0; n < N; ++n) W[((size_t)d * K + k) * N + n] = m2p_entry(mi, tab, d, k, n);
+  char name[64];
+  std::snprintf(name, sizeof name, "/m2p_p%d_b%d.bin", p, b);
+  return write_table(dir + name, W);
+}
+
+// Near-field weights [27][b^3][4 b^3] (neighbour box, source cell,
+// component * b^3 + target cell; components: g, then the three force columns).
+bool dump_near(const std::string& dir, int b) {
+  const int b3 = b * b * b;
+  std::vector<double> W((size_t)27 * b3 * 4 * b3);
+  for (int d = 0; d < 27; ++d) {
+    const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+    for (int k = 0; k < b3; ++k)
+      for (int n = 0; n < 4 * b3; ++n) W[((size_t)d * b3 + k) * 4 * b3 + n] = near_entry(b, D, k, n);
+  }
+  char name[64];
+  std::snprintf(name, sizeof name, "/near_b%d.bin", b);
+  return write_table(dir + name, W);
+}
+
+// ------------------------------------------------------------- harmonic --
+
+// For random multipoles of one source child, the compressed contraction
+// (fold the multipoles, contract the (p+1)^2 components with the reduced
+// weights, rebuild the locals with c >= 2) must equal the Cartesian one, for
+// every neighbour parent and child pair.  The same for M2P (fold only).
+template <int P>
+double harmonic_error() {
+  constexpr int NC = fmmgb::tree::ncoef_c(P);
+  MultiIndex mi;
+  mi.init(P);
+  TaylorTable tt;
+  tt.build(mi);
+  M2pTable tab;
+  tab.build(mi, 2);
+  const std::vector<int> red = harmonic_components(mi);
+  std::mt19937 rng(100 + P);
+  std::uniform_real_distribution<double> U(-1, 1);
+  double err = 0;
+  for (int d = 0; d < 27; ++d)
+    for (int cs = 0; cs < 8; ++cs) {
+      double M[NC], Mf[NC];
+      for (int k = 0; k < NC; ++k) Mf[k] = M[k] = U(rng);
+      fmmgb::tree::harmonic_fold<P, double>(Mf);
+      for (int ct = 0; ct < 8; ++ct) {
+        double Lc[NC] = {}, Lh[NC] = {}, scale = 0;
+        for (int n = 0; n < NC; ++n)
+          for (int k = 0; k < NC; ++k) {
+            const double w = m2l_entry(mi, tt, d, k * 8 + cs, n * 8 + ct);
+            Lc[n] += w * M[k];
+            scale += std::fabs(w * M[k]);
+          }
+        for (int rn : red)
+          for (int rk : red) Lh[rn] += m2l_entry(mi, tt, d, rk * 8 + cs, rn * 8 + ct) * Mf[rk];
+        fmmgb::tree::harmonic_expand<P, double>(Lh);
+        for (int n = 0; n < NC; ++n) err = std::max(err, std::fabs(Lh[n] - Lc[n]) / std::max(scale, 1e-300));
+        for (int cell = 0; cell < 8; ++cell) {
+          const int col = ct * 8 + cell;
+          double pc = 0, ph = 0, s2 = 0;
+          for (int k = 0; k < NC; ++k) {
+            const double w = m2p_entry(mi, tab, d, k * 8 + cs, col);
+            pc += w * M[k];
+            s2 += std::fabs(w * M[k]);
+          }
+          for (int rk : red) ph += m2p_entry(mi, tab, d, rk * 8 + cs, col) * Mf[rk];
+          err = std::max(err, std::fabs(ph - pc) / std::max(s2, 1e-300));
+        }
+      }
+    }
+  return err;
+}
+
+int harmonic_check() {
+  const double errs[7] = {harmonic_error<2>(), harmonic_error<3>(), harmonic_error<4>(), harmonic_error<5>(),
+                          harmonic_error<6>(), harmonic_error<7>(), harmonic_error<8>()};
+  int bad = 0;
+  for (int p = 2; p <= 8; ++p) {
+    std::printf("harmonic p=%d: max |compressed - Cartesian| / sum|terms| = %.2e\n", p, errs[p - 2]);
+    bad += !(errs[p - 2] <= 1e-12);
+  }
+  return bad;
+}
+
 }  // namespace
 
 int main(int argc, char** argv) {
-  if (argc > 1 && std::string(argv[1]) == "plant") return planted_mistakes() ? 1 : 0;
+  const std::string mode = argc > 1 ? argv[1] : "";
+  if (mode == "plant") return planted_mistakes() ? 1 : 0;
+  if (mode == "harmonic") return harmonic_check() ? 1 : 0;
+  if (mode == "tables") {
+    if (argc < 3) return 2;
+    const std::string dir = argv[2];
+    const bool ok = dump_m2l(dir, 3, 3, 3) && dump_m2l(dir, 4, 4, 4) && dump_m2l(dir, 4, 3, 4) &&
+                    dump_m2l(dir, 4, 4, 3) && dump_m2p(dir, 3, 2) && dump_m2p(dir, 4, 4) && dump_near(dir, 2) &&
+                    dump_near(dir, 4);
+    return ok ? 0 : 1;
+  }
   bool ok = true;
   for (int kind : {TC_BF16X3, TC_TF32})
     for (int p : {2, 4, 6, 8})

@@ -1,0 +1,173 @@
+"""The plan's host-side tables and tensor-core schedules, checked without a GPU.
+
+tests/host_check.cu compiles the library's host code (capi.cu) and:
+
+* checks every tensor-core schedule (M2L at orders 2-8, Cartesian and
+  harmonic, bf16x3 and TF32, multipoles or locals below the order; final-stage
+  M2P; near field): TMEM and shared-memory budgets, issuer ownership of the
+  accumulators, the weight-ring producer's replay (no stall, no overlap), and
+  the MMAs emulated from the packed, swizzled weight tiles against the direct
+  contraction with the plan's weight function; five corruptions planted in a
+  built schedule must each be caught;
+* writes the plan's unit-box weight tables (S0 of the path: M2L per neighbour
+  parent and child pair, final-stage M2P per cell, near-field kernel), which
+  are compared here with the oracle's own operators (Sec. 2.3, eq. M2L; the
+  final stage of Sec. 4; eq. direct);
+* checks the harmonic compression (fold the multipoles, contract the (p+1)^2
+  components, rebuild the locals) against the Cartesian contraction, p = 2..8.
+"""
+import itertools
+import math
+import os
+import shutil
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+from paper_2606_13793_gb300 import _build  # noqa: E402
+
+SRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "host_check.cu")
+
+
+@pytest.fixture(scope="module")
+def host_check(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    # the kernels' objects resolve the launch functions capi.cu references
+    objs = [os.path.join(_build.BUILD_DIR, os.path.splitext(s)[0] + ".o") for s in _build.SOURCES if s != "capi.cu"]
+    _build.build(force=not all(os.path.exists(o) for o in objs))
+    exe = str(tmp_path_factory.mktemp("host_check") / "host_check")
+    cmd = [nvcc, *_build.ARCH, "-O1", "-std=c++17", "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"),
+           "-I", _build.CSRC, SRC, *objs, "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    return exe
+
+
+def _run(exe, *args):
+    r = subprocess.run([exe, *args], capture_output=True, text=True, timeout=600)
+    print(r.stdout)
+    return r
+
+
+def test_tensor_core_schedules(host_check):
+    r = _run(host_check)
+    assert r.returncode == 0, r.stdout + r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 54 and all("uncovered 0" in ln for ln in lines)
+
+
+def test_planted_schedule_corruptions_are_caught(host_check):
+    r = _run(host_check, "plant")
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.count("FAILED") == 5
+
+
+def test_harmonic_compression_is_exact(host_check):
+    r = _run(host_check, "harmonic")
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.count("harmonic p=") == 7
+
+
+@pytest.fixture(scope="module")
+def tables(host_check, tmp_path_factory):
+    d = tmp_path_factory.mktemp("tables")
+    r = _run(host_check, "tables", str(d))
+    assert r.returncode == 0, r.stdout + r.stderr
+    return d
+
+
+def _offsets(d):
+    return (d % 3 - 1, (d // 3) % 3 - 1, d // 9 - 1)
+
+
+def _child_offset(ct, cs, D):
+    """c_target - c_source in child boxes: target child ct of the parent at the
+    origin, source child cs of the neighbour parent D."""
+    return np.array([((ct >> q) & 1) - ((cs >> q) & 1) - 2 * D[q] for q in range(3)], dtype=float)
+
+
+def _factorials(idx):
+    return np.array([math.prod(math.factorial(int(v)) for v in row) for row in idx], dtype=float)
+
+
+@pytest.mark.parametrize("p,mo,lo", [(3, 3, 3), (4, 4, 4), (4, 3, 4), (4, 4, 3)])
+def test_m2l_table_equals_the_oracle_operator(orc, tables, p, mo, lo):
+    """Unit-box weights: with child boxes of side 1 the scaled multipoles and
+    locals are M and L / beta!, so W[alpha, beta] = L_beta(e_alpha) / beta!
+    from the oracle's M2L at R = c_target - c_source, zero for near pairs and
+    past the multipole / local limits."""
+    nc = orc.ncoef(p)
+    K = 8 * nc
+    W = np.fromfile(tables / f"m2l_p{p}_mo{mo}_lo{lo}.bin").reshape(27, K, K)
+    idx = orc.index(p)
+    order = idx.sum(1)
+    bfact = _factorials(idx)
+    limit = (order[:, None] <= mo) & (order[None, :] <= lo)
+    cache = {}
+    worst = 0.0
+    for d in range(27):
+        D = _offsets(d)
+        for cs, ct in itertools.product(range(8), range(8)):
+            got = W[d, cs::8, ct::8]  # [alpha, beta]
+            u = _child_offset(ct, cs, D)
+            if np.abs(u).max() < 2:
+                assert not got.any()
+                continue
+            key = tuple(u)
+            if key not in cache:
+                A = np.stack([orc.m2l(np.eye(nc)[a], u, p) for a in range(nc)])  # [alpha, beta]
+                cache[key] = A / bfact[None, :]
+            ref = np.where(limit, cache[key], 0.0)
+            np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-13 * np.abs(ref).max())
+            worst = max(worst, float(np.abs(got - ref).max() / np.abs(ref).max()))
+    print(f"M2L p={p} mo={mo} lo={lo}: max |plan - oracle| / max |W| = {worst:.1e}")
+
+
+@pytest.mark.parametrize("p,b", [(3, 2), (4, 4)])
+def test_m2p_table_equals_the_oracle_derivatives(orc, tables, p, b):
+    """Final-stage M2P (Sec. 4) in leaf-box units: the potential at a cell of
+    target child ct from a unit multipole alpha of source child cs is
+    (-1)^|alpha| / alpha! D_alpha(R), D = the oracle's derivative tensor of
+    -1/r, R = the child offset plus the cell's offset from its box centre."""
+    nc = orc.ncoef(p)
+    b3 = b ** 3
+    W = np.fromfile(tables / f"m2p_p{p}_b{b}.bin").reshape(27, 8 * nc, 8 * b3)
+    idx = orc.index(p)
+    sign_fact = np.where(idx.sum(1) % 2, -1.0, 1.0) / _factorials(idx)
+    for d in range(27):
+        D = _offsets(d)
+        for cs, ct in itertools.product(range(8), range(8)):
+            got = W[d, cs::8, ct * b3:(ct + 1) * b3]  # [alpha, cell]
+            u = _child_offset(ct, cs, D)
+            if np.abs(u).max() < 2:
+                assert not got.any()
+                continue
+            for cell in range(b3):
+                e = np.array([cell % b, (cell // b) % b, cell // (b * b)], dtype=float)
+                ref = sign_fact * orc.dtensor(u + (e + 0.5) / b - 0.5, p)
+                np.testing.assert_allclose(got[:, cell], ref, rtol=1e-11, atol=1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("b", [2, 4])
+def test_near_table_equals_the_kernel(tables, b):
+    """Near field (eq. direct), cell units: g(r) = -1/|r| with g(0) = -1, and
+    the force columns dg/dx_q = r_q / |r|^3 (zero at r = 0), r = target -
+    source over the 27 neighbour boxes."""
+    b3 = b ** 3
+    W = np.fromfile(tables / f"near_b{b}.bin").reshape(27, b3, 4 * b3)
+    cells = np.array([(c % b, (c // b) % b, c // (b * b)) for c in range(b3)], dtype=float)
+    for d in range(27):
+        r = cells[None, :, :] - cells[:, None, :] - b * np.array(_offsets(d), dtype=float)  # [source, target, 3]
+        rn = np.linalg.norm(r, axis=2)
+        g = np.where(rn == 0, -1.0, -1.0 / np.where(rn == 0, 1.0, rn))
+        np.testing.assert_allclose(W[d, :, :b3], g, rtol=1e-15)
+        for q in range(3):
+            f = np.where(rn == 0, 0.0, r[:, :, q] / np.where(rn == 0, 1.0, rn) ** 3)
+            np.testing.assert_allclose(W[d, :, (q + 1) * b3:(q + 2) * b3], f, rtol=1e-14, atol=1e-16)
