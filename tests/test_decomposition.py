@@ -179,7 +179,7 @@ def _run(world, shape=(24, 20, 40), b=4, p=4, m2l_halo=None):
     import oracle
 
     oracle.load()  # built once here, before the ranks load it
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:  # no fork of a threaded process
         out = mgr.dict()
         mp.spawn(_slab_solve, args=(world, _free_port(), shape, b, p, m2l_halo, out), nprocs=world, join=True)
         return out["result"]

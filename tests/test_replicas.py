@@ -37,7 +37,7 @@ def _rank(rank, world, port, out):
 
 def test_replica_timing_takes_the_slowest_rank():
     world, port = 2, _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:  # no fork of a threaded process
         out = mgr.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
