@@ -86,6 +86,7 @@ def _bind(lib):
         "oracle_direct": (I, [DP, I, I, I, D, D, DP, I]),
         "oracle_fmm_sample": (I, [DP, I, I, I, I, I, D, D, L, LP, DP, DP, I]),
         "oracle_adjoint": (I, [DP, DP, I, I, I, I, I, D, D, DP, I]),
+        "oracle_adjoint_analytic": (I, [DP, DP, I, I, I, I, I, D, D, DP, I]),
         "oracle_fmm_accel": (I, [DP, I, I, I, I, I, D, D, DP, I]),
         "oracle_direct_accel": (I, [DP, I, I, I, D, D, DP, I]),
         "oracle_fmm_sample_accel": (I, [DP, I, I, I, I, I, D, D, L, LP, DP, I]),
@@ -303,13 +304,15 @@ class Oracle:
             raise ValueError("oracle_fmm_sample rejected its arguments")
         return (phi, acc) if accel else phi
 
-    def adjoint(self, gphi, gaccel, b, p, dx=1.0, G=1.0, threads: int = 0) -> np.ndarray:
+    def adjoint(self, gphi, gaccel, b, p, dx=1.0, G=1.0, threads: int = 0, analytic: bool = False) -> np.ndarray:
+        """grad_rho of <gphi, phi> + <gaccel, accel>: accel by the 5-point
+        stencil of phi, or (analytic=True) the force of fmm_accel."""
         gphi = _f64(gphi)
         nz, ny, nx = gphi.shape
         ga = _f64(gaccel) if gaccel is not None else None
         out = np.zeros_like(gphi)
-        rc = self.lib.oracle_adjoint(_dp(gphi), _dp(ga) if ga is not None else _c_double_p(),
-                                     nx, ny, nz, b, p, dx, G, _dp(out), threads)
+        fn = self.lib.oracle_adjoint_analytic if analytic else self.lib.oracle_adjoint
+        rc = fn(_dp(gphi), _dp(ga) if ga is not None else _c_double_p(), nx, ny, nz, b, p, dx, G, _dp(out), threads)
         if rc != 0:
             raise ValueError("oracle_adjoint rejected its arguments")
         return out

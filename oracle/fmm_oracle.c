@@ -985,8 +985,15 @@ int oracle_fmm_sample(const double* rho, int nx, int ny, int nz, int b, int p, d
 /*             w = grad_phi + FD^T(-(1/dx) grad_accel)                       */
 /* ------------------------------------------------------------------------ */
 
-int oracle_adjoint(const double* gphi, const double* gaccel, int nx, int ny, int nz, int b, int p, double dx,
-                   double G, double* grho, int nthreads) {
+/* analytic = 0: the force is the 5-point stencil of phi, so grad_accel joins
+ * the source w through FD^T.  analytic = 1: the force is the analytic one of
+ * oracle_fmm_accel, accel = -G dx (grad far + grad near); with v = -grad_accel
+ * / dx (the factor relative to the potential's G dx^2) its transpose adds
+ * grad-L2P^T v to the leaf Lam (sum_q v_q e^(beta - e_q) / (beta - e_q)!)
+ * and, per source cell c, sum over the targets t whose near region holds c of
+ * v(t) . grad g(x_t - x_c). */
+static int or_adjoint(const double* gphi, const double* gaccel, int analytic, int nx, int ny, int nz, int b, int p,
+                      double dx, double G, double* grho, int nthreads) {
   or_hier H;
   if (or_hier_init(&H, nx, ny, nz, b, p)) return -1;
   or_set_threads(nthreads);
@@ -997,7 +1004,12 @@ int oracle_adjoint(const double* gphi, const double* gaccel, int nx, int ny, int
   const double scale = G * dx * dx;
   double* w = (double*)malloc(sizeof(double) * n);
   memcpy(w, gphi, sizeof(double) * n);
-  if (gaccel) oracle_fd_accel_adjoint(gaccel, nx, ny, nz, dx, w);
+  double* v = NULL; /* analytic: v[3][n] = -grad_accel / dx */
+  if (gaccel && !analytic) oracle_fd_accel_adjoint(gaccel, nx, ny, nz, dx, w);
+  if (gaccel && analytic) {
+    v = (double*)malloc(sizeof(double) * 3 * n);
+    for (long c = 0; c < 3 * n; ++c) v[c] = -gaccel[c] / dx;
+  }
   /* L2P^T: Lam_beta(B) = sum_{i in B} w_i e_i^beta / beta! */
   double** Lam = (double**)calloc(H.L + 1, sizeof(double*));
   double** Mu = (double**)calloc(H.L + 1, sizeof(double*));
@@ -1022,6 +1034,23 @@ int oracle_adjoint(const double* gphi, const double* gaccel, int nx, int ny, int
       for (int q = 0; q < 3; ++q) t *= or_ipow(e[q], be[q]) / or_fact(be[q]);
 #endif
       La[k] += w[c] * t;
+    }
+    if (v) {
+      for (int k = 0; k < nc; ++k) {
+        /* grad-L2P^T: d/de_q (e^beta / beta!) = e^(beta - e_q) / (beta - e_q)! */
+        const int* be = ix->mi[k];
+        double s = 0.0;
+        for (int q = 0; q < 3; ++q) {
+          if (be[q] == 0) continue;
+          double t = 1.0;
+          for (int r = 0; r < 3; ++r) {
+            const int pw = be[r] - (r == q);
+            t *= or_ipow(e[r], pw) / or_fact(pw);
+          }
+          s += v[q * n + c] * t;
+        }
+        La[k] += s;
+      }
     }
   }
   /* walk levels fine -> coarse: at level l, M2L^T scatters Lam(T) into
@@ -1130,8 +1159,19 @@ int oracle_adjoint(const double* gphi, const double* gaccel, int nx, int ny, int
           if (qi < 0 || qi >= lf->n[0]) continue;
           for (int tz = qk * b; tz < qk * b + b; ++tz)
             for (int ty = qj * b; ty < qj * b + b; ++ty)
-              for (int tx = qi * b; tx < qi * b + b; ++tx)
-                nearv += w[((long)tz * ny + ty) * nx + tx] * or_g((double)(tx - x), (double)(ty - y), (double)(tz - z));
+              for (int tx = qi * b; tx < qi * b + b; ++tx) {
+                const long t = ((long)tz * ny + ty) * nx + tx;
+                nearv += w[t] * or_g((double)(tx - x), (double)(ty - y), (double)(tz - z));
+                if (v) {
+                  double gg[3];
+#if ORACLE_MUTANT == 17 /* planted mistake: transposed pair force taken from source to target */
+                  or_grad_g((double)(x - tx), (double)(y - ty), (double)(z - tz), gg);
+#else
+                  or_grad_g((double)(tx - x), (double)(ty - y), (double)(tz - z), gg);
+#endif
+                  nearv += v[t] * gg[0] + v[n + t] * gg[1] + v[2 * n + t] * gg[2];
+                }
+              }
         }
       }
     }
@@ -1140,8 +1180,21 @@ int oracle_adjoint(const double* gphi, const double* gaccel, int nx, int ny, int
   or_free_levels(&H, Lam);
   or_free_levels(&H, Mu);
   free(w);
+  free(v);
   free(ix);
   return 0;
+}
+
+int oracle_adjoint(const double* gphi, const double* gaccel, int nx, int ny, int nz, int b, int p, double dx,
+                   double G, double* grho, int nthreads) {
+  return or_adjoint(gphi, gaccel, 0, nx, ny, nz, b, p, dx, G, grho, nthreads);
+}
+
+/* Transpose of (phi, analytic accel): grad_rho from grad_phi and the
+ * gradient with respect to oracle_fmm_accel's force. */
+int oracle_adjoint_analytic(const double* gphi, const double* gaccel, int nx, int ny, int nz, int b, int p, double dx,
+                            double G, double* grho, int nthreads) {
+  return or_adjoint(gphi, gaccel, 1, nx, ny, nz, b, p, dx, G, grho, nthreads);
 }
 
 /* ------------------------------------------------------------------------ */

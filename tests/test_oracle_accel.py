@@ -76,3 +76,25 @@ def test_accel_matches_fd_gradient_of_phi_in_the_interior(orc):
     an = orc.fmm_accel(rho, 4, 8)
     inner = (slice(None), slice(4, -4), slice(4, -4), slice(4, -4))
     assert rel(fd[inner], an[inner]) < 1e-2
+
+
+def test_adjoint_of_the_analytic_force_is_its_transpose(orc):
+    """<gphi, phi(rho)> + <ga, accel(rho)> = <A^T (gphi, ga), rho> with accel
+    the analytic force of fmm_accel: the explicit transpose chain (grad-L2P^T
+    into the leaf locals, the shared M2L / L2L / M2M transposes, P2M^T, and
+    the near pair forces transposed) against the forward solves."""
+    rng = np.random.default_rng(12)
+    shape, b, p, dx, G = (16, 24, 20), 4, 4, 0.3, 1.7
+    rho = rng.standard_normal(shape[::-1])
+    gphi = rng.standard_normal(shape[::-1])
+    ga = rng.standard_normal((3,) + shape[::-1])
+    phi = orc.fmm(rho, b, p, dx=dx, G=G)["phi"]
+    acc = orc.fmm_accel(rho, b, p, dx=dx, G=G)
+    lhs = np.vdot(gphi, phi) + np.vdot(ga, acc)
+    at = orc.adjoint(gphi, ga, b, p, dx=dx, G=G, analytic=True)
+    assert lhs == pytest.approx(np.vdot(at, rho), rel=1e-11)
+    # the force part alone, and the potential part equal to the stencil adjoint's
+    at_f = orc.adjoint(np.zeros_like(gphi), ga, b, p, dx=dx, G=G, analytic=True)
+    assert np.vdot(ga, acc) == pytest.approx(np.vdot(at_f, rho), rel=1e-11)
+    np.testing.assert_array_equal(orc.adjoint(gphi, None, b, p, dx=dx, G=G, analytic=True),
+                                  orc.adjoint(gphi, None, b, p, dx=dx, G=G))

@@ -28,6 +28,7 @@ MUTANTS = {
     14: "adjoint chain's L2P^T without the 1/beta! factor",
     15: "gradient of L2P with the undifferentiated factorials",
     16: "near field over the face neighbours only (edge and corner boxes dropped)",
+    17: "analytic force's adjoint with the transposed pair force reversed",
 }
 
 # Cheap single-operator pins first: a mutant's battery stops at the first pin
@@ -49,6 +50,7 @@ PINS = [
     orders.test_monopole_only_far_field_ignores_mass_moved_inside_boxes,
     orders.test_order_zero_locals_give_a_constant_far_field_per_box,
     solve.test_adjoint_chain_is_transpose,
+    accel.test_adjoint_of_the_analytic_force_is_its_transpose,
 ]
 
 
