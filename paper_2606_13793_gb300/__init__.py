@@ -324,9 +324,16 @@ class FMMPlan:
         return int(self.lib.fmm_solve_launches(self._h, 1 if accel else 0))
 
     def close(self):
+        """Frees the plan's device memory; later calls on it raise."""
         if getattr(self, "_h", None) is not None and self._h.value:
             self.lib.fmm_plan_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def __del__(self):
         try:
@@ -368,6 +375,12 @@ class BatchSolver:
         if getattr(self, "_h", None) is not None and self._h.value:
             self.lib.fmm_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def __del__(self):
         try:
