@@ -41,9 +41,11 @@ def acc_tol(n, prec):
     return base * max(1.0, n / 256.0)
 
 
-def solve(rho32, b, p, prec, dx=1.0, n_fp64_levels=3):
+def solve(rho32, b, p, prec, dx=1.0, n_fp64_levels=3, autotune=False):
     nz, ny, nx = rho32.shape
     plan = fmm.FMMPlan((nx, ny, nz), p, b, prec, dx=dx, n_fp64_levels=n_fp64_levels)
+    if autotune:
+        plan.autotune()
     phi, acc = plan.solve(torch.from_numpy(np.ascontiguousarray(rho32)).cuda(), accel=True)
     torch.cuda.synchronize()
     plan.check()
@@ -109,10 +111,11 @@ def test_tc_level_locals_match_oracle(orc):
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
 def test_tc_full_size_sampled(orc, prec):
-    """512^3, p=6, leaf 4, lognormal: the benchmark configuration, sampled."""
+    """512^3, p=6, leaf 4, lognormal: the benchmark configuration (autotuned
+    like the benchmark's plan), sampled."""
     n = 512
     rho32 = inputs.lognormal(n, seed=2606)
-    phi, acc = solve(rho32, 4, 6, prec, dx=1.0 / n)
+    phi, acc = solve(rho32, 4, 6, prec, dx=1.0 / n, autotune=True)
     rng = np.random.default_rng(7)
     cells = rng.integers(0, n ** 3, 40)
     cells[:4] = [0, n ** 3 - 1, n // 2 * (n * n + n + 1), (n // 2) * n * n + 5 * n + 9]
