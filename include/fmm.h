@@ -272,7 +272,12 @@ fmm_status fmm_plan_set_tuning(fmm_plan_t plan, int level, int shape, int dsplit
  *                       grids execute concurrently -- and launches it; later
  *                       calls with the same buffers only launch the graph
  *                       (new buffers: a new capture).  Asynchronous on `stream`.
- *   fmm_batch_destroy : frees the graph and the batch's streams/events.
+ *   fmm_batch_destroy : frees the graph and the batch's streams/events
+ *                       (NULL: no-op).
+ * Errors: FMM_ERR_ARG (NULL batch, plan or buffer array, a NULL rho[i] /
+ * phi[i], count < 1), FMM_ERR_ALLOC (host memory), FMM_ERR_CUDA (stream,
+ * event, capture, instantiation or launch failure; the solve errors of
+ * fmm_solve pass through from the first, uncaptured run).
  * The batch is the multi-field form of the solve; the paper solves one field
  * per call (this is the data-parallel batch of many problems).
  */
@@ -285,7 +290,8 @@ fmm_status fmm_batch_destroy(fmm_batch_t batch);
 int fmm_batch_launches(fmm_batch_t batch, int with_accel);
 
 /* fmm_check -- synchronises the plan's last stream and reports device-side
- * flags (FMM_ERR_NONFINITE, FMM_ERR_TIMEOUT), clearing them. */
+ * flags (FMM_ERR_NONFINITE, FMM_ERR_TIMEOUT), clearing them.  FMM_ERR_ARG for
+ * a NULL plan, FMM_ERR_CUDA for an error the synchronisation returns. */
 fmm_status fmm_check(fmm_plan_t plan);
 
 /* Bytes of device memory the plan holds (tables + workspace arena). */
@@ -302,7 +308,8 @@ int fmm_solve_launches(fmm_plan_t plan, int with_accel);
  *   fmm_timing_read   : synchronises, then writes for each stage i < nstages
  *                       the summed milliseconds ms[i] and launch count
  *                       launches[i] since the last enable/read, and clears them.
- * Stages (index: name): see fmm_timing_stage_name().
+ * Stages (index: name): see fmm_timing_stage_name().  Errors: FMM_ERR_ARG
+ * (NULL plan or arrays), FMM_ERR_CUDA (event creation or timing failure).
  */
 fmm_status fmm_timing_enable(fmm_plan_t plan, int enable);
 fmm_status fmm_timing_read(fmm_plan_t plan, double* ms, int* launches, int nstages);
@@ -321,7 +328,9 @@ const char* fmm_last_error(void);
  * order, then a descending, then b descending), as double, in cell units
  * about each box centre (M_alpha = sum m (x-c)^alpha, L_beta as in eq. M2L).
  *   what: 0 = multipoles M, 1 = local expansions L.  level: 2..L.
- * Synchronises the device.  For tests that localise a mismatch.
+ * Synchronises the device.  For tests that localise a mismatch.  Errors:
+ * FMM_ERR_ARG (NULL plan, `what` not 0 or 1, a level that is not stored, a
+ * host buffer shorter than nbox * ncoef), FMM_ERR_CUDA (copy failure).
  */
 fmm_status fmm_debug_level(fmm_plan_t plan, int what, int level, double* host_out, size_t host_count);
 
