@@ -1833,18 +1833,20 @@ fmm_status fmm_solve_host(fmm_plan_t P, const void* rho_host, void* phi_host, vo
   if (!rho_host || !phi_host) return fail(FMM_ERR_ARG, "rho and phi must be non-NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)P->ncell() * P->esize();
-  if (!P->d_io_rho) {
-    if (cudaMalloc(&P->d_io_rho, bytes) != cudaSuccess || cudaMalloc(&P->d_io_phi, bytes) != cudaSuccess) {
+  // staging buffers, allocated once each (a failed allocation leaves the
+  // others in place and is retried by the next call)
+  auto stage = [](void** buf, size_t n) {
+    if (*buf) return true;
+    void* q = nullptr;
+    if (cudaMalloc(&q, n) != cudaSuccess) {
       cudaGetLastError();
-      return fail(FMM_ERR_ALLOC, "staging allocation failed");
+      return false;
     }
-  }
-  if (accel_host && !P->d_io_acc) {
-    if (cudaMalloc(&P->d_io_acc, 3 * bytes) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(FMM_ERR_ALLOC, "staging allocation failed");
-    }
-  }
+    *buf = q;
+    return true;
+  };
+  if (!stage(&P->d_io_rho, bytes) || !stage(&P->d_io_phi, bytes) || (accel_host && !stage(&P->d_io_acc, 3 * bytes)))
+    return fail(FMM_ERR_ALLOC, "staging allocation failed");
   CUDA_TRY(cudaMemcpyAsync(P->d_io_rho, rho_host, bytes, cudaMemcpyHostToDevice, s));
   fmm_status st = fmm_solve(P, P->d_io_rho, P->d_io_phi, accel_host ? P->d_io_acc : nullptr, stream);
   if (st != FMM_OK) return st;
