@@ -1902,9 +1902,19 @@ int fmm_solve_launches(fmm_plan_t P, int with_accel) {
 
 fmm_status fmm_timing_enable(fmm_plan_t P, int enable) {
   if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
-  if (enable && P->ev_pool.empty()) {
-    P->ev_pool.resize(kEventPool);
-    for (auto& e : P->ev_pool) CUDA_TRY(cudaEventCreate(&e));
+  if (enable && P->ev_pool.empty()) {  // the whole pool or none of it
+    std::vector<cudaEvent_t> pool;
+    pool.reserve(kEventPool);
+    for (int i = 0; i < kEventPool; ++i) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        for (cudaEvent_t f : pool) cudaEventDestroy(f);
+        return fail(FMM_ERR_CUDA, "timing event creation failed");
+      }
+      pool.push_back(e);
+    }
+    P->ev_pool = std::move(pool);
   }
   CUDA_TRY(cudaDeviceSynchronize());
   P->recs.clear();
