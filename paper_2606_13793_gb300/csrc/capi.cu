@@ -1863,7 +1863,9 @@ fmm_status fmm_check(fmm_plan_t P) {
   CUDA_TRY(cudaMemcpy(&flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     CUDA_TRY(cudaMemset(P->d_flag, 0, sizeof(int)));
-    if (flag & 1) return fail(FMM_ERR_NONFINITE, "the density held a NaN or Inf");
+    if (flag & 1)
+      return fail(FMM_ERR_NONFINITE, "the density held a NaN or Inf%s",
+                  (flag & 2) ? " (and a device wait reached its time limit)" : "");
     return fail(FMM_ERR_TIMEOUT, "a device wait reached its time limit (wait sites 0x%x)", (flag >> 8) & 0xff);
   }
   return FMM_OK;
