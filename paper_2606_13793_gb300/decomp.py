@@ -129,6 +129,23 @@ class SlabDecomposition:
         multiply by the leaf size for cells)."""
         return self._halo_transfers(self.L, self.NEAR_HALO if width is None else width)
 
+    def received_bytes(self, rank: int, ncoef: int, elem_bytes: int = 4, density_bytes: int = 4):
+        """Bytes `rank` receives in one solve, by exchange: the density halo
+        (cells of density_bytes), the multipole halos of each distributed level
+        (ncoef coefficients of elem_bytes per box) and the all-gather of the
+        split level (every box it does not own)."""
+        nx, ny, _ = self.shape
+        out = {"density": sum((t.hi - t.lo) * self.leaf * nx * ny * density_bytes
+                              for t in self.density_halos() if t.dst == rank)}
+        for l in range(self.L, self.split, -1):
+            ex, ey, _ = self.ext[l]
+            out[f"multipoles level {l}"] = sum((t.hi - t.lo) * ex * ey * ncoef * elem_bytes
+                                               for t in self.multipole_halos(l) if t.dst == rank)
+        ex, ey, ez = self.ext[self.split]
+        lo, hi = self.owned(rank, self.split)
+        out[f"allgather level {self.split}"] = (ez - (hi - lo)) * ex * ey * ncoef * elem_bytes
+        return out
+
     def exchanges(self):
         """Every exchange of one solve, in order: density halos, multipole
         halos of each distributed level (finest first), then the all-gather of

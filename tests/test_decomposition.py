@@ -212,6 +212,24 @@ def test_plan_geometry():
         (0, 1): (0, 2), (2, 1): (4, 5)}
 
 
+def test_received_bytes_count_the_halo_boxes():
+    D = decomp.SlabDecomposition((24, 20, 40), 4, 3)  # leaf boxes 6 x 5 x 10, split level 2
+    nc = 35
+    for r in range(3):
+        got = D.received_bytes(r, nc, elem_bytes=8, density_bytes=8)
+        lo, hi = D.cells(r)
+        # density: the cells within one leaf box (4 cells) of the slab, along z
+        cells = len([z for z in range(40) if (lo - 4 <= z < lo) or (hi <= z < hi + 4)])
+        assert got["density"] == cells * 24 * 20 * 8
+        for l in (4, 3):
+            blo, bhi = D.owned(r, l)
+            nz = D.ext[l][2]
+            boxes = len([z for z in range(nz) if (blo - 2 <= z < blo) or (bhi <= z < bhi + 2)])
+            assert got[f"multipoles level {l}"] == boxes * D.ext[l][0] * D.ext[l][1] * nc * 8
+        slo, shi = D.owned(r, 2)
+        assert got["allgather level 2"] == (D.ext[2][2] - (shi - slo)) * D.ext[2][0] * D.ext[2][1] * nc * 8
+
+
 @pytest.mark.parametrize("world", [2, 3, 4])
 def test_slab_solve_equals_single_domain(world):
     finite, err, split, L = _run(world)
