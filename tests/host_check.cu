@@ -19,7 +19,7 @@
 //    1 KB multiples within the shared-memory budget;
 //  * ownership: per chunk the issuers' span ranges are contiguous, every
 //    accumulator column belongs to one issuer, and an accumulator opens (its
-//    first MMA overwrites) in one chunk only;
+//    first MMA overwrites) in one chunk only, by one span;
 //  * the weight rings: replayed in the producer's order (tile, neighbour
 //    column (dx, dz), chunk, dy, span) over two tiles, with the consumer
 //    releasing spans only when the producer must wait, no span is larger than
@@ -34,8 +34,8 @@
 // Exit status 0 when every schedule passes; each case prints one line.
 // With the argument "plant", it corrupts built schedules instead (a zeroed
 // weight tile, a tile row read unswizzled, two issuers on one accumulator, an
-// accumulator opened late, a ring smaller than a span) and exits 0 only if
-// every corruption is caught.
+// accumulator opened late, an accumulator opened by two spans, a ring smaller
+// than a span) and exits 0 only if every corruption is caught.
 #include "capi.cu"
 #include "tree_common.cuh"
 
@@ -144,6 +144,13 @@ bool check(const char* name, int kind, const TcHost& H, int ncol, int klen, cons
     std::vector<int> owner(512, -1), opened(512, -1);
     for (int j = 0; j < P.nchunks; ++j) {
       if (P.span_idx[j][kTcIssuers] != P.span_idx[j + 1][0]) return fail(name, "span ranges not contiguous", ps);
+      // in the chunk where an accumulator opens, one span only may write it
+      // (every span of that chunk's first step overwrites)
+      std::vector<int> openers(512, 0);
+      for (int si = P.span_idx[j][0]; si < P.span_idx[j][kTcIssuers]; ++si)
+        if (P.span[si].first == j)
+          for (int r = 0; r < P.span[si].n; ++r)
+            if (++openers[P.span[si].tmem_col + r] > 1) return fail(name, "accumulator opened by two spans", ps);
       for (int q = 0; q < kTcIssuers; ++q) {
         if (P.span_idx[j][q] > P.span_idx[j][q + 1]) return fail(name, "span range reversed", ps);
         for (int si = P.span_idx[j][q]; si < P.span_idx[j][q + 1]; ++si) {
@@ -323,6 +330,23 @@ int planted_mistakes() {
     if (P.nchunks < 2) return false;
     P.span[P.span_idx[0][0]].first = 1;
     return true;
+  });
+  plant("accumulator opened by two spans", [](TcHost& H) {  // two openers of one issuer in one chunk
+    TcPass& P = H.pass[0];
+    for (int j = 0; j < P.nchunks; ++j)
+      for (int q = 0; q < kTcIssuers; ++q) {
+        int a = -1;
+        for (int si = P.span_idx[j][q]; si < P.span_idx[j][q + 1]; ++si) {
+          if (P.span[si].first != j) continue;
+          if (a < 0) {
+            a = si;
+          } else {
+            P.span[si].tmem_col = P.span[a].tmem_col;
+            return true;
+          }
+        }
+      }
+    return false;
   });
   plant("weight ring smaller than a span", [](TcHost& H) {
     H.pass[0].ring_bytes[0] = 1024;

@@ -7,7 +7,7 @@ tests/host_check.cu compiles the library's host code (capi.cu) and:
   M2P; near field): TMEM and shared-memory budgets, issuer ownership of the
   accumulators, the weight-ring producer's replay (no stall, no overlap), and
   the MMAs emulated from the packed, swizzled weight tiles against the direct
-  contraction with the plan's weight function; five corruptions planted in a
+  contraction with the plan's weight function; six corruptions planted in a
   built schedule must each be caught;
 * writes the plan's unit-box weight tables (S0 of the path: M2L per neighbour
   parent and child pair, final-stage M2P per cell, near-field kernel), which
@@ -66,7 +66,7 @@ def test_tensor_core_schedules(host_check):
 def test_planted_schedule_corruptions_are_caught(host_check):
     r = _run(host_check, "plant")
     assert r.returncode == 0, r.stdout + r.stderr
-    assert r.stdout.count("FAILED") == 5
+    assert r.stdout.count("FAILED") == 6
 
 
 def test_harmonic_compression_is_exact(host_check):
