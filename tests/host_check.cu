@@ -18,8 +18,9 @@
 //  * resources: a pass uses at most 512 TMEM columns, the weight rings are
 //    1 KB multiples within the shared-memory budget;
 //  * ownership: per chunk the issuers' span ranges are contiguous, every
-//    accumulator column belongs to one issuer, and an accumulator opens (its
-//    first MMA overwrites) in one chunk only, by one span;
+//    accumulator column belongs to one issuer, an accumulator opens (its
+//    first MMA overwrites) in one chunk only, by one span, and the epilogue
+//    stores each output column from one group of one pass;
 //  * the weight rings: replayed in the producer's order (tile, neighbour
 //    column (dx, dz), chunk, dy, span) over two tiles, with the consumer
 //    releasing spans only when the producer must wait, no span is larger than
@@ -129,11 +130,19 @@ bool check(const char* name, int kind, const TcHost& H, int ncol, int klen, cons
         ref[n] += t;
         sabs[n] += std::fabs(t);
       }
-  std::vector<int> covered(ncol, 0);
+  std::vector<int> covered(ncol, 0), writer(ncol, -1);
   int spans = 0;
   for (int ps = 0; ps < H.npass; ++ps) {
     const TcPass& P = H.pass[ps];
     spans += P.span_idx[P.nchunks][0];
+    // the epilogue stores each output column once: one group of one pass
+    for (int g = 0; g < P.ng; ++g)
+      for (int c = 0; c < P.out_ncols[g]; ++c) {
+        const int n = P.out_col0[g] + c;
+        if (n < 0 || n >= ncol) return fail(name, "output column out of range", ps);
+        if (writer[n] >= 0) return fail(name, "output column stored by two groups", ps);
+        writer[n] = ps * 64 + g;
+      }
     if (P.tmem_cols > 512) return fail(name, "more than 512 TMEM columns", ps);
     long ring_sum = 0;
     for (int q = 0; q < kTcIssuers; ++q) {
