@@ -92,7 +92,7 @@ __device__ __forceinline__ void store_split(__nv_bfloat16* hi, __nv_bfloat16* lo
 // In-place upward (multipole) shift along axis Q by d:
 //   M'_{..a..} = sum_{a' <= a} C(a, a') d^(a - a') M_{..a'..}
 template <int P, int Q, typename T>
-__device__ __forceinline__ void shift_up(T (&M)[ncoef_c(P)], const T (&dp)[P + 1]) {
+__host__ __device__ __forceinline__ void shift_up(T (&M)[ncoef_c(P)], const T (&dp)[P + 1]) {
 #pragma unroll
   for (int u = 0; u <= P; ++u)
 #pragma unroll
@@ -112,7 +112,7 @@ __device__ __forceinline__ void shift_up(T (&M)[ncoef_c(P)], const T (&dp)[P + 1
 // In-place downward (local) shift along axis Q by d:
 //   L'_{..a..} = sum_{a' >= a} C(a', a) d^(a' - a) L_{..a'..}
 template <int P, int Q, typename T>
-__device__ __forceinline__ void shift_down(T (&L)[ncoef_c(P)], const T (&dp)[P + 1]) {
+__host__ __device__ __forceinline__ void shift_down(T (&L)[ncoef_c(P)], const T (&dp)[P + 1]) {
 #pragma unroll
   for (int u = 0; u <= P; ++u)
 #pragma unroll
@@ -130,7 +130,7 @@ __device__ __forceinline__ void shift_down(T (&L)[ncoef_c(P)], const T (&dp)[P +
 }
 
 template <int P, typename T>
-__device__ __forceinline__ void powers(T x, T (&dp)[P + 1]) {
+__host__ __device__ __forceinline__ void powers(T x, T (&dp)[P + 1]) {
   dp[0] = T(1);
 #pragma unroll
   for (int k = 1; k <= P; ++k) dp[k] = dp[k - 1] * x;
@@ -138,7 +138,7 @@ __device__ __forceinline__ void powers(T x, T (&dp)[P + 1]) {
 
 // Child c of a parent box sits at +-1/2 child box along each axis.
 template <typename T>
-__device__ __forceinline__ T half_offset(int c, int q) {
+__host__ __device__ __forceinline__ T half_offset(int c, int q) {
   return ((c >> q) & 1) ? T(0.5) : T(-0.5);
 }
 

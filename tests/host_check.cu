@@ -4,8 +4,9 @@
 //   host_check            the tensor-core schedules (below)
 //   host_check plant      planted schedule corruptions, each must be caught
 //   host_check tables DIR writes the plan's M2L, M2P and near-field weight
-//                         tables (FP64, raw) into DIR for comparison with the
-//                         oracle's operators
+//                         tables and the kernels' M2M / L2L shifts of random
+//                         expansions (FP64, raw) into DIR for comparison with
+//                         the oracle's operators
 //   host_check harmonic   harmonic compression against the Cartesian
 //                         contraction, orders 2..8 (exact up to rounding)
 //
@@ -423,6 +424,45 @@ bool dump_near(const std::string& dir, int b) {
   return write_table(dir + name, W);
 }
 
+// ---------------------------------------------------------------- shifts --
+
+// The kernels' separable shifts (M2M: shift_up, L2L: shift_down along x, y,
+// z in turn) for random expansions and displacements; each case is written as
+// [input (nc), d (3), output (nc)] for comparison with the oracle's M2M / L2L.
+template <int P>
+bool dump_shifts(const std::string& dir) {
+  constexpr int NC = fmmgb::tree::ncoef_c(P);
+  std::mt19937 rng(300 + P);
+  std::uniform_real_distribution<double> U(-1, 1);
+  std::vector<double> up, down;
+  for (int rep = 0; rep < 6; ++rep) {
+    double M[NC], L[NC], d[3], dp[P + 1];
+    for (int k = 0; k < NC; ++k) M[k] = U(rng), L[k] = U(rng);
+    for (double& x : d) x = U(rng);
+    if (rep == 0) d[0] = fmmgb::tree::half_offset<double>(5, 0), d[1] = fmmgb::tree::half_offset<double>(5, 1),
+                  d[2] = fmmgb::tree::half_offset<double>(5, 2);  // a child offset, as the kernels use
+    up.insert(up.end(), M, M + NC);
+    up.insert(up.end(), d, d + 3);
+    down.insert(down.end(), L, L + NC);
+    down.insert(down.end(), d, d + 3);
+    fmmgb::tree::powers<P, double>(d[0], dp);
+    fmmgb::tree::shift_up<P, 0, double>(M, dp);
+    fmmgb::tree::shift_down<P, 0, double>(L, dp);
+    fmmgb::tree::powers<P, double>(d[1], dp);
+    fmmgb::tree::shift_up<P, 1, double>(M, dp);
+    fmmgb::tree::shift_down<P, 1, double>(L, dp);
+    fmmgb::tree::powers<P, double>(d[2], dp);
+    fmmgb::tree::shift_up<P, 2, double>(M, dp);
+    fmmgb::tree::shift_down<P, 2, double>(L, dp);
+    up.insert(up.end(), M, M + NC);
+    down.insert(down.end(), L, L + NC);
+  }
+  char a[64], b[64];
+  std::snprintf(a, sizeof a, "/shift_up_p%d.bin", P);
+  std::snprintf(b, sizeof b, "/shift_down_p%d.bin", P);
+  return write_table(dir + a, up) && write_table(dir + b, down);
+}
+
 // ------------------------------------------------------------- harmonic --
 
 // For random multipoles of one source child, the compressed contraction
@@ -497,7 +537,7 @@ int main(int argc, char** argv) {
     const std::string dir = argv[2];
     const bool ok = dump_m2l(dir, 3, 3, 3) && dump_m2l(dir, 4, 4, 4) && dump_m2l(dir, 4, 3, 4) &&
                     dump_m2l(dir, 4, 4, 3) && dump_m2p(dir, 3, 2) && dump_m2p(dir, 4, 4) && dump_near(dir, 2) &&
-                    dump_near(dir, 4);
+                    dump_near(dir, 4) && dump_shifts<3>(dir) && dump_shifts<6>(dir) && dump_shifts<8>(dir);
     return ok ? 0 : 1;
   }
   bool ok = true;

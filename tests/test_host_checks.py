@@ -14,7 +14,9 @@ tests/host_check.cu compiles the library's host code (capi.cu) and:
   are compared here with the oracle's own operators (Sec. 2.3, eq. M2L; the
   final stage of Sec. 4; eq. direct);
 * checks the harmonic compression (fold the multipoles, contract the (p+1)^2
-  components, rebuild the locals) against the Cartesian contraction, p = 2..8.
+  components, rebuild the locals) against the Cartesian contraction, p = 2..8;
+* runs the kernels' separable M2M / L2L shift helpers on the host, compared
+  here with the oracle's M2M (eq. M2M_general) and L2L (eq. L2L).
 """
 import itertools
 import math
@@ -171,3 +173,24 @@ def test_near_table_equals_the_kernel(tables, b):
         for q in range(3):
             f = np.where(rn == 0, 0.0, r[:, :, q] / np.where(rn == 0, 1.0, rn) ** 3)
             np.testing.assert_allclose(W[d, :, (q + 1) * b3:(q + 2) * b3], f, rtol=1e-14, atol=1e-16)
+
+
+@pytest.mark.parametrize("p", [3, 6, 8])
+def test_kernel_shifts_equal_the_oracle_m2m_and_l2l(orc, tables, p):
+    """The kernels' separable shifts along x, y, z in turn (M2M and L2L are
+    built from them) against the oracle's eq. M2M_general and eq. L2L: with
+    unit box size the scaled multipoles are M and the scaled locals L / beta!,
+    so shift_up(M, d) = M2M(M, d) and shift_down(L / beta!, a) = L2L(L, a) /
+    beta!.  The first case is a child offset (+-1/2), as the kernels use."""
+    nc = orc.ncoef(p)
+    bfact = _factorials(orc.index(p))
+    up = np.fromfile(tables / f"shift_up_p{p}.bin").reshape(-1, 2 * nc + 3)
+    down = np.fromfile(tables / f"shift_down_p{p}.bin").reshape(-1, 2 * nc + 3)
+    for row in up:
+        M, d, got = row[:nc], row[nc:nc + 3], row[nc + 3:]
+        ref = orc.m2m(M, d, p)
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-13 * np.abs(ref).max())
+    for row in down:
+        Lt, a, got = row[:nc], row[nc:nc + 3], row[nc + 3:]
+        ref = orc.l2l(Lt * bfact, a, p) / bfact
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-13 * np.abs(ref).max())
