@@ -9,6 +9,8 @@
 //                         the oracle's operators
 //   host_check harmonic   harmonic compression against the Cartesian
 //                         contraction, orders 2..8 (exact up to rounding)
+//   host_check cuda-core  the CUDA-core M2L weight tiles (prefix-cut
+//                         reductions) against the full contraction
 //
 // The library's plan packs every tensor-core contraction (M2L per level,
 // final-stage M2P, the near field) into passes of MMA spans, per-issuer
@@ -463,6 +465,66 @@ bool dump_shifts(const std::string& dir) {
   return write_table(dir + a, up) && write_table(dir + b, down);
 }
 
+// ------------------------------------------------------ CUDA-core tiles --
+
+// The CUDA-core M2L weight tiles (32 output columns each, reduction cut to
+// the prefix the tile's lowest order needs): the contraction read from the
+// tiles as the kernels read it must equal the full contraction with the
+// weight function, i.e. no non-zero weight lies past a tile's prefix.
+bool cc_tiles_case(int p, int mo, int lo, bool harm) {
+  MultiIndex mi;
+  mi.init(p);
+  if (mo >= 0) mi.mo = mo;
+  if (lo >= 0) mi.lo = lo;
+  TaylorTable tt;
+  tt.build(mi);
+  std::vector<double> W;
+  std::vector<int> tk;
+  std::vector<long long> tw;
+  m2l_weights<double>(mi, tt, W, tk, tw, true, harm);
+  const std::vector<int> red = harmonic_components(mi);
+  const int nk = harm ? (int)red.size() : mi.nc, K = 8 * nk, ncol = 8 * nk;
+  std::mt19937 rng(500 + p);
+  std::uniform_real_distribution<double> U(-1, 1);
+  std::vector<std::vector<double>> A(27, std::vector<double>(K));
+  for (auto& r : A)
+    for (double& a : r) a = U(rng);
+  double err = 0;
+  long long kept = 0, full = 0;
+  for (int n = 0; n < ncol; ++n) {
+    const int t = n / kNTile, j = n % kNTile;
+    double got = 0, ref = 0, sabs = 0;
+    for (int d = 0; d < 27; ++d) {
+      const double* blk = W.data() + tw[t] + (long long)d * tk[t] * kNTile;
+      for (int k = 0; k < tk[t]; ++k) got += A[d][k] * blk[(long long)k * kNTile + j];
+      for (int k = 0; k < K; ++k) {
+        const double w = harm ? m2l_entry(mi, tt, d, red[k / 8] * 8 + k % 8, red[n / 8] * 8 + n % 8)
+                              : m2l_entry(mi, tt, d, k, n);
+        ref += A[d][k] * w;
+        sabs += std::fabs(A[d][k] * w);
+      }
+      kept += tk[t];
+      full += K;
+    }
+    if (sabs > 0) err = std::max(err, std::fabs(got - ref) / sabs);
+  }
+  std::printf("cuda-core tiles p=%d mo=%d lo=%d%s: reduction kept %.0f%%, err/sum|terms| %.1e\n", p, mi.mo, mi.lo,
+              harm ? " harmonic" : "", 100.0 * kept / full, err);
+  return err <= 1e-13;
+}
+
+int cc_tiles_check() {
+  int bad = 0;
+  for (int p = 2; p <= 8; ++p)
+    for (bool harm : {false, true}) bad += !cc_tiles_case(p, -1, -1, harm);
+  for (bool harm : {false, true}) {
+    bad += !cc_tiles_case(3, 2, -1, harm);  // the paper's orders
+    bad += !cc_tiles_case(3, -1, 2, harm);  // and their transpose
+    bad += !cc_tiles_case(6, 4, -1, harm);
+  }
+  return bad;
+}
+
 // ------------------------------------------------------------- harmonic --
 
 // For random multipoles of one source child, the compressed contraction
@@ -532,6 +594,7 @@ int main(int argc, char** argv) {
   const std::string mode = argc > 1 ? argv[1] : "";
   if (mode == "plant") return planted_mistakes() ? 1 : 0;
   if (mode == "harmonic") return harmonic_check() ? 1 : 0;
+  if (mode == "cuda-core") return cc_tiles_check() ? 1 : 0;
   if (mode == "tables") {
     if (argc < 3) return 2;
     const std::string dir = argv[2];

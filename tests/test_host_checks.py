@@ -15,6 +15,8 @@ tests/host_check.cu compiles the library's host code (capi.cu) and:
   final stage of Sec. 4; eq. direct);
 * checks the harmonic compression (fold the multipoles, contract the (p+1)^2
   components, rebuild the locals) against the Cartesian contraction, p = 2..8;
+* reads the CUDA-core M2L weight tiles (reductions cut to a prefix per tile)
+  as the kernels do and checks they give the full contraction;
 * runs the kernels' separable M2M / L2L shift helpers on the host, compared
   here with the oracle's M2M (eq. M2M_general) and L2L (eq. L2L).
 """
@@ -75,6 +77,15 @@ def test_harmonic_compression_is_exact(host_check):
     r = _run(host_check, "harmonic")
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.count("harmonic p=") == 7
+
+
+def test_cuda_core_weight_tiles_hold_every_weight(host_check):
+    """The CUDA-core M2L tiles cut each 32-column tile's reduction to the
+    prefix its lowest order needs; read as the kernels read them they give
+    the full contraction exactly (orders 2-8, both forms, reduced orders)."""
+    r = _run(host_check, "cuda-core")
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.count("cuda-core tiles") == 20
 
 
 @pytest.fixture(scope="module")
