@@ -4,10 +4,11 @@
 // interaction list of Sec. 2.2) the same translation-invariant contraction,
 //   L[P][n] += sum_{d in 27 neighbours} sum_{k < K(n)} M[P + d][k] * W_d[k][n],
 // with P a parent box, k = (alpha, source child) and n = (beta, target child).
-// One CTA computes 128 parents (an 8x4x4 block) for one "pass" of output
+// One CTA computes 128 parents (an 8x16x1 block) for one "pass" of output
 // columns:
 //   * A (M = 128 rows): the neighbour-shifted parent rows, one 128-byte chunk
-//     of the reduction at a time, loaded by TMA from a 4-D tensor map; rows
+//     of the reduction at a time, loaded by TMA from a 4-D tensor map as an
+//     8x18x1 box whose one-row y halo serves the three dy neighbours; rows
 //     past the domain are zero-filled by TMA, which is the isolated boundary.
 //   * B: a weight tile per (neighbour, chunk, column group), stored
 //     pre-swizzled (128-byte swizzle) so one bulk copy lands it ready for the
