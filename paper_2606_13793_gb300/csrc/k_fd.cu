@@ -1,8 +1,12 @@
 // Force by finite differences (App. C): a = -grad(phi) with the 4th-order
 // 5-point central stencil, 2nd-order central one cell from an edge and
 // 2nd-order one-sided at an edge; and the transpose of that map for the
-// adjoint solve.  HBM-bound: one thread per cell, x fastest, so every
-// stencil read along x is coalesced and the y/z reads hit L2.
+// adjoint solve.  HBM-bound.  The force kernels walk z through tiles of the
+// x-y plane (z neighbours in registers, x-y neighbours from a shared-memory
+// tile with a 2-cell halo): fd_accel_vec4_kernel for FP32 rows with 16-byte
+// alignment (four x-cells a thread), fd_accel_tiled_kernel otherwise, and a
+// plain one-thread-per-cell kernel for grids past the launch limits.  The
+// adjoint source kernel is one thread per cell, x fastest.
 #include "fmm_internal.h"
 
 namespace fmmgb {
