@@ -577,7 +577,50 @@ double harmonic_error() {
   return err;
 }
 
+// The L2L kernel adds the M2L's c <= 1 locals to the parent's shifted
+// locals and rebuilds the c >= 2 components of the sum in place.  That needs
+// the shifted parent locals to be harmonic themselves: a harmonic local
+// expansion (c >= 2 rebuilt from c <= 1) shifted by shift_down along x, y, z
+// must equal the rebuild of its own c <= 1 part.
+template <int P>
+double harmonic_shift_error() {
+  constexpr int NC = fmmgb::tree::ncoef_c(P);
+  MultiIndex mi;
+  mi.init(P);
+  const std::vector<int> red = harmonic_components(mi);
+  std::mt19937 rng(700 + P);
+  std::uniform_real_distribution<double> U(-1, 1);
+  double err = 0;
+  for (int rep = 0; rep < 16; ++rep) {
+    double L[NC] = {}, R[NC], dp[P + 1];
+    for (int k : red) L[k] = U(rng);
+    fmmgb::tree::harmonic_expand<P, double>(L);
+    for (int q = 0; q < 3; ++q) {
+      fmmgb::tree::powers<P, double>(fmmgb::tree::half_offset<double>(rep & 7, q), dp);
+      if (q == 0) fmmgb::tree::shift_down<P, 0, double>(L, dp);
+      if (q == 1) fmmgb::tree::shift_down<P, 1, double>(L, dp);
+      if (q == 2) fmmgb::tree::shift_down<P, 2, double>(L, dp);
+    }
+    for (int k = 0; k < NC; ++k) R[k] = 0;
+    for (int k : red) R[k] = L[k];
+    fmmgb::tree::harmonic_expand<P, double>(R);
+    double scale = 0;
+    for (int k = 0; k < NC; ++k) scale = std::max(scale, std::fabs(L[k]));
+    for (int k = 0; k < NC; ++k) err = std::max(err, std::fabs(R[k] - L[k]) / scale);
+  }
+  return err;
+}
+
 int harmonic_check() {
+  const double shift_errs[7] = {harmonic_shift_error<2>(), harmonic_shift_error<3>(), harmonic_shift_error<4>(),
+                                harmonic_shift_error<5>(), harmonic_shift_error<6>(), harmonic_shift_error<7>(),
+                                harmonic_shift_error<8>()};
+  int bad_shift = 0;
+  for (int p = 2; p <= 8; ++p) {
+    std::printf("harmonic locals stay harmonic under L2L, p=%d: %.2e\n", p, shift_errs[p - 2]);
+    bad_shift += !(shift_errs[p - 2] <= 1e-13);
+  }
+  if (bad_shift) return bad_shift;
   const double errs[7] = {harmonic_error<2>(), harmonic_error<3>(), harmonic_error<4>(), harmonic_error<5>(),
                           harmonic_error<6>(), harmonic_error<7>(), harmonic_error<8>()};
   int bad = 0;

@@ -14,7 +14,9 @@ tests/host_check.cu compiles the library's host code (capi.cu) and:
   are compared here with the oracle's own operators (Sec. 2.3, eq. M2L; the
   final stage of Sec. 4; eq. direct);
 * checks the harmonic compression (fold the multipoles, contract the (p+1)^2
-  components, rebuild the locals) against the Cartesian contraction, p = 2..8;
+  components, rebuild the locals) against the Cartesian contraction, and that
+  harmonic locals stay harmonic under the kernels' L2L shift (which the
+  in-place rebuild after L2L relies on), p = 2..8;
 * reads the CUDA-core M2L weight tiles (reductions cut to a prefix per tile)
   as the kernels do and checks they give the full contraction;
 * runs the kernels' separable M2M / L2L shift helpers on the host, compared
@@ -77,6 +79,8 @@ def test_harmonic_compression_is_exact(host_check):
     r = _run(host_check, "harmonic")
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.count("harmonic p=") == 7
+    # the in-place rebuild after L2L: shifted harmonic locals stay harmonic
+    assert r.stdout.count("stay harmonic under L2L") == 7
 
 
 def test_cuda_core_weight_tiles_hold_every_weight(host_check):
