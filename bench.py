@@ -478,7 +478,7 @@ def main():
     # ---- CPU oracle baseline (rank 0, bounded sample) ----
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
-        n_s = 128 if n >= 128 else n
+        n_s = 256 if n >= 256 else n  # a bounded sample: 16.8 M cells, tens of seconds of host work
         dt, thr = run_oracle_sample(n_s, p, b)
         cpu = {"value": n_s ** 3 / dt / 1e6, "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": f"one full FP64 oracle solve of a {n_s}^3 grid of the same lognormal recipe (p={p}, "
