@@ -260,7 +260,7 @@ def run_oracle_sample(n, order, leaf, seed=2606):
 def reference_arm(args, rank):
     if rank != 0:
         return
-    n_s = 64
+    n_s = min(args.n, 128)  # per step: 2.1 M cells, a few seconds of host work
     for _ in range(args.warmup):
         run_oracle_sample(n_s, args.order, args.leaf)
     total = 0.0
