@@ -227,6 +227,11 @@ struct fmm_plan_s {
   int p2l_ntiles = 0;
   std::vector<int> h_p2l_tile_k;
   TcLaunch tcm{};
+  // prefix-schedule forms (k_nbr_tc.cu) of the M2L (and its transpose), the
+  // final-stage M2P and the near field; the span forms above run where a
+  // prefix schedule does not apply
+  bool tp_m2l = false, tp_m2l_t = false, tp_m2p = false, tp_near = false;
+  TpLaunch tpl{}, tpl_t{}, tpm{}, tpn{};
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // timing
   bool timing = false;
@@ -779,6 +784,410 @@ bool build_tc_generic(int kind, const std::vector<TcCols>& gs, const Entry& entr
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Prefix schedule of the tensor-core contraction (k_nbr_tc.cu).
+//
+// Output column n (0 <= n < kcol.size()) reduces over k < kcol[n], with kcol
+// non-increasing, so K step s (kstep reduction values) is needed by the
+// column prefix of those with kcol[n] > s * kstep.  The columns are split
+// into passes (contiguous ranges, at most 512 TMEM columns each) by a cost
+// model of the tensor pipe measured on GB300: an MMA of M = 128, K = 16 costs
+// max(40, 32 + N / 4, N / 2) cycles.  Within a pass, K step s is one MMA per
+// product over its prefix (N <= 256 per instruction), into
+//   D  for s < l2_step (hi*hi, hi*lo, lo*hi; or, "fused" when the prefix is
+//      narrow: hi*hi and hi*lo as one MMA over [lo rows reversed; hi rows]
+//      into E and D, then lo*hi into D),
+//   L2 for s >= l2_step,
+// so that the FP32 accumulators of the lowest columns (the longest sums)
+// each take about half the MMAs: the tensor cores add with truncation.
+// The weight blocks of a K step (32-byte rows, 32-byte swizzle) are packed
+// in MMA order into pieces of at most kTpPieceBytes that never cross a
+// 128-byte activation chunk; the program of MMAs is the same for every
+// (dx, dz) neighbour column, only the weights differ.
+struct TpHost {
+  std::vector<TpPass> pass;
+  int a_stages = 2, w_slots = 0;
+  int owner_slot0[kTpIssuers] = {}, owner_nslots[kTpIssuers] = {};
+  std::vector<unsigned char> W;
+};
+
+// Tensor-pipe cycles of one MMA (M = 128, K = 16 bf16 / 8 TF32) of N columns.
+double tp_mma_cycles(int n) { return std::max(40.0, std::max(32.0 + n / 4.0, n / 2.0)); }
+
+// MMA shapes (first accumulator column, N) the schedule issues: N <= 128 at
+// any 16-column boundary, or N a multiple of 32 up to 256 filling from column
+// 0 or 256 without crossing the next 256-column boundary.  (Wider MMAs at
+// other columns faulted on GB300; these are the forms that have run.)
+bool tp_shape_ok(int tcol, int n) {
+  if (n < 16 || n % 16 || tcol < 0 || tcol % 16) return false;
+  if (n <= 128) return true;
+  return n % 32 == 0 && n <= 256 && (tcol == 0 || tcol == 256);
+}
+
+struct TpStepPlan {
+  int n = 0;         // prefix columns (multiple of 16)
+  int region = 0;    // 0 D, 1 fused (E + D), 2 L2, 3 fused with lo*hi into L2
+};
+
+struct TpPassPlan {
+  int c0 = 0, c1 = 0;   // output columns
+  int S = 0;            // K steps
+  int D = 0, E = 0, W2 = 0, l2_step = 0;
+  int chain = 0;        // MMAs into the busiest accumulator column per tile
+  double cycles = 0;    // per tile
+  std::vector<TpStepPlan> steps;
+};
+
+// Plans one pass over columns [c0, c1); false if it does not fit.
+bool tp_plan_pass(int kind, const std::vector<int>& kcol, int c0, int c1, TpPassPlan& out) {
+  const bool split = kind == TC_BF16X3;
+  const int kstep = split ? 16 : 8, products = split ? 3 : 1;
+  TpPassPlan P;
+  P.c0 = c0, P.c1 = c1;
+  P.D = (c1 - c0 + 15) / 16 * 16;
+  if (P.D > 512 || c1 <= c0) return false;
+  P.S = (kcol[c0] + kstep - 1) / kstep;
+  if (P.S <= 0) return false;
+  std::vector<int> N(P.S);
+  for (int s = 0; s < P.S; ++s) {
+    int n = 0;
+    while (c0 + n < c1 && kcol[c0 + n] > s * kstep) ++n;
+    N[s] = (n + 15) / 16 * 16;
+  }
+  auto unfused = [&](int n) {
+    double c = 0;
+    for (int o = 0; o < n; o += 128) c += tp_mma_cycles(std::min(128, n - o));
+    return products * c;
+  };
+  const double fused_gain_min = 1.0;
+  // a fused step of N columns issues 2N from column E - N (E: the E region)
+  auto fusable = [](int n, int E) { return n <= E && tp_shape_ok(E - n, 2 * n); };
+  // candidates: l2_step from S (no L2) down; E from the fusable steps that fit
+  TpPassPlan best;
+  bool have = false;
+  for (int s2 = P.S; s2 >= 1; --s2) {
+    const int W2 = s2 < P.S ? N[s2] : 0;
+    if (P.D + W2 > 512) continue;
+    const int ebudget = std::min(128, 512 - P.D - W2);
+    // E: the widest fusable prefix that pays (each candidate width checked
+    // against the shapes of every step fused under it)
+    int E = 0;
+    double best_gain = 0;
+    if (split)
+      for (int cand = 16; cand <= ebudget; cand += 16) {
+        double gain = 0;
+        for (int s = 0; s < s2; ++s)
+          if (fusable(N[s], cand))
+            gain += std::max(0.0, unfused(N[s]) - (tp_mma_cycles(2 * N[s]) + tp_mma_cycles(N[s])));
+        if (gain > best_gain + fused_gain_min) best_gain = gain, E = cand;
+      }
+    TpPassPlan c = P;
+    c.W2 = W2, c.E = E, c.l2_step = s2;
+    c.steps.assign(P.S, {});
+    int chainD = 0, chainL = 0;
+    double cyc = 0;
+    for (int s = 0; s < P.S; ++s) {
+      TpStepPlan& st = c.steps[s];
+      st.n = N[s];
+      if (s >= s2) {
+        st.region = 2;
+        chainL += products;
+        cyc += unfused(N[s]);
+      } else if (E > 0 && fusable(N[s], E) &&
+                 tp_mma_cycles(2 * N[s]) + tp_mma_cycles(N[s]) + fused_gain_min < unfused(N[s])) {
+        st.region = 1;
+        chainD += 2;
+        cyc += tp_mma_cycles(2 * N[s]) + tp_mma_cycles(N[s]);
+      } else {
+        st.region = 0;
+        if (N[s] > 0) chainD += products;
+        cyc += unfused(N[s]);
+      }
+    }
+    c.chain = 27 * std::max(chainD, chainL);
+    c.cycles = 27 * cyc;
+    // prefer chains within ~1100 MMAs (the accuracy of the span schedule's
+    // split accumulators), then the fewest cycles
+    auto score = [](const TpPassPlan& x) { return x.cycles * (x.chain > 1100 ? 1.0 + (x.chain - 1100) / 1100.0 : 1.0); };
+    if (!have || score(c) < score(best)) best = c, have = true;
+  }
+  if (!have) return false;
+  // with no late-step region, a fused step's lo*hi gets the L2 region to
+  // itself when the columns fit: the D accumulators then take hi*hi alone
+  if (best.l2_step == best.S && best.E > 0 && best.E + best.D + best.E <= 512) {
+    best.W2 = best.E;
+    int chainD = 0, chainL = 0;
+    for (TpStepPlan& st : best.steps) {
+      if (st.region == 1) st.region = 3, ++chainL;
+      chainD += st.region == 0 ? products : 1;
+    }
+    best.chain = 27 * std::max(chainD, chainL);
+  }
+  out = best;
+  return true;
+}
+
+// Builds passes, MMA programs and packed weights; entry(d, k, n) is the
+// weight of the contraction (0 beyond kcol[n] and past the row length klen).
+template <typename Entry>
+bool build_tp_generic(int kind, const std::vector<int>& kcol, int klen, const Entry& entry, TpHost& H,
+                      int max_chain = 2100) {
+  const bool split = kind == TC_BF16X3;
+  const int kstep = split ? 16 : 8, esz = split ? 2 : 4;
+  const int ncols = (int)kcol.size();
+  if (ncols == 0) return false;
+  for (int n = 1; n < ncols; ++n)
+    if (kcol[n] > kcol[n - 1]) return false;  // prefixes must shrink
+  // candidate pass boundaries: where the reduction length changes (multiples of 8)
+  std::vector<int> bnd{0};
+  for (int n = 1; n < ncols; ++n)
+    if (kcol[n] != kcol[n - 1] && n % 8 == 0) bnd.push_back(n);
+  bnd.push_back(ncols);
+  const int nb = (int)bnd.size();
+  // copy costs per tile (cycles): activation boxes at ~50 B/clk, weights at ~70 B/clk
+  const int planes = split ? 2 : 1;
+  auto pass_cost = [&](const TpPassPlan& pp) {
+    const int nch = (pp.S + 3) / 4;
+    const double a_bytes = 9.0 * nch * planes * kTcAPlaneBytes;
+    double w_bytes = 0;
+    for (const TpStepPlan& st : pp.steps) w_bytes += 27.0 * st.n * 32 * planes;
+    return std::max(pp.cycles, a_bytes / 50.0 + w_bytes / 70.0) + 4000.0;  // + epilogue and pipeline fill
+  };
+  // dp over boundaries: best[i][np] = cost of columns [0, bnd[i]) in np passes
+  const double inf = 1e300;
+  std::vector<std::vector<double>> best(nb, std::vector<double>(kTpMaxPasses + 1, inf));
+  std::vector<std::vector<int>> from(nb, std::vector<int>(kTpMaxPasses + 1, -1));
+  std::vector<std::vector<TpPassPlan>> plan_of(nb, std::vector<TpPassPlan>(nb));
+  std::vector<std::vector<char>> ok_of(nb, std::vector<char>(nb, 0));
+  for (int i = 0; i < nb; ++i)
+    for (int j = i + 1; j < nb; ++j)
+      if (tp_plan_pass(kind, kcol, bnd[i], bnd[j], plan_of[i][j]) && plan_of[i][j].chain <= max_chain) ok_of[i][j] = 1;
+  best[0][0] = 0;
+  for (int j = 1; j < nb; ++j)
+    for (int np = 1; np <= kTpMaxPasses; ++np)
+      for (int i = 0; i < j; ++i)
+        if (ok_of[i][j] && best[i][np - 1] < inf) {
+          const double c = best[i][np - 1] + pass_cost(plan_of[i][j]);
+          if (c < best[j][np]) best[j][np] = c, from[j][np] = i;
+        }
+  int npass = -1;
+  for (int np = 1; np <= kTpMaxPasses; ++np)
+    if (best[nb - 1][np] < inf && (npass < 0 || best[nb - 1][np] < best[nb - 1][npass])) npass = np;
+  if (npass < 0) return false;
+  std::vector<TpPassPlan> plans(npass);
+  for (int j = nb - 1, np = npass; np > 0; --np) {
+    const int i = from[j][np];
+    plans[np - 1] = plan_of[i][j];
+    j = i;
+  }
+  H.pass.assign(npass, TpPass{});
+  H.W.clear();
+  H.a_stages = split ? 2 : 3;
+  H.w_slots = tp_w_slots(kind, H.a_stages);
+  if (H.w_slots < kTpIssuers) return false;
+  for (int ps = 0; ps < npass; ++ps) {
+    const TpPassPlan& pp = plans[ps];
+    TpPass& T = H.pass[ps];
+    std::memset(&T, 0, sizeof(T));
+    T.col0 = pp.c0;
+    T.ncols = pp.c1 - pp.c0;
+    T.nchunks = (pp.S + 3) / 4;
+    if (T.nchunks > kTpMaxChunks) return false;
+    T.tmem_cols = (pp.E + pp.D + pp.W2 + 15) / 16 * 16;
+    T.nbuf = 2 * T.tmem_cols <= 512 ? 2 : 1;
+    T.ngroups = (T.ncols + 15) / 16;
+    if (T.ngroups > kTpMaxGroups) return false;
+    for (int g = 0; g < T.ngroups; ++g) {
+      T.grp_d[g] = (int16_t)(pp.E + 16 * g);
+      T.grp_e[g] = (int16_t)(16 * g + 16 <= pp.E ? pp.E - 16 - 16 * g : -1);
+      T.grp_l2[g] = (int16_t)(16 * g + 16 <= pp.W2 ? pp.E + pp.D + 16 * g : -1);
+    }
+    // Units: the MMAs reading one weight block of one K step.  A unit's
+    // accumulator columns lie in one ownership group: the first 128 columns
+    // of D together with E (and L2 when it holds the fused steps' lo*hi), a
+    // later 128-column chunk of D, or L2 when it holds the late K steps.
+    struct Unit {
+      int s, dy, form, tcol, n, tcol2;
+      int group;
+      std::vector<int> row_col;    // output column (pass-relative) of each block row
+      std::vector<int> row_plane;  // 0 hi, 1 lo
+    };
+    const bool l2_late = pp.l2_step < pp.S;  // L2 holds late K steps (else: the fused lo*hi, or nothing)
+    const int ngroups_d = (pp.D + 127) / 128;
+    const int g_l2 = l2_late ? ngroups_d : -1;
+    const int ngrp = ngroups_d + (l2_late ? 1 : 0);
+    auto step_units = [&](int s, int dy) {
+      std::vector<Unit> out;
+      const TpStepPlan& st = pp.steps[s];
+      const int n = st.n;
+      if (st.region == 1 || st.region == 3) {  // fused: [lo rows reversed; hi rows]
+        Unit u{s, dy, 1, pp.E - n, n, st.region == 3 ? pp.E + pp.D : pp.E, 0, {}, {}};
+        for (int r = 0; r < n; ++r) u.row_col.push_back(n - 1 - r), u.row_plane.push_back(1);
+        for (int r = 0; r < n; ++r) u.row_col.push_back(r), u.row_plane.push_back(0);
+        out.push_back(u);
+        return out;
+      }
+      const int base = st.region == 2 ? pp.E + pp.D : pp.E;
+      for (int o = 0; o < n; o += 128) {
+        const int m = std::min(128, n - o);
+        Unit u{s, dy, split ? 0 : 2, base + o, m, 0, st.region == 2 ? g_l2 : o / 128, {}, {}};
+        for (int pl = 0; pl < (split ? 2 : 1); ++pl)
+          for (int r = 0; r < m; ++r) u.row_col.push_back(o + r), u.row_plane.push_back(pl);
+        out.push_back(u);
+      }
+      return out;
+    };
+    // ownership groups -> issuers: heaviest first, each to the least-loaded issuer
+    std::vector<long long> gload(ngrp, 0);
+    for (int s = 0; s < pp.S; ++s)
+      for (const Unit& u : step_units(s, 0)) gload[u.group] += u.form == 0 ? 3 : u.form == 1 ? 2 : 1;
+    std::vector<int> owner(ngrp, 0);
+    {
+      std::vector<int> order(ngrp);
+      for (int g = 0; g < ngrp; ++g) order[g] = g;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gload[a] > gload[b]; });
+      long long load[kTpIssuers] = {};
+      for (int g : order) {
+        int q = 0;
+        for (int t = 1; t < kTpIssuers; ++t)
+          if (load[t] < load[q]) q = t;
+        owner[g] = q;
+        load[q] += gload[g];
+      }
+    }
+    // pieces: per chunk, each owner's units packed in (dy, K step) order; a
+    // piece holds one owner's blocks; the pieces of a chunk are then ordered
+    // by their first unit's (dy, K step), so the ring fills in the order the
+    // owners read
+    struct Piece {
+      int owner, key, len;
+      std::vector<Unit> units;
+      std::vector<int> offs;
+    };
+    std::vector<Piece> pieces;
+    std::vector<uint32_t> prog;
+    std::vector<int> piece_unit{0};
+    for (int j = 0; j < T.nchunks; ++j) {
+      T.chunk_piece[j] = (int16_t)pieces.size();
+      std::vector<Piece> cp;
+      std::vector<int> open(kTpIssuers, -1);
+      for (int dy = 0; dy < 3; ++dy)
+        for (int s = 4 * j; s < std::min(pp.S, 4 * j + 4); ++s)
+          for (Unit& u : step_units(s, dy)) {
+            const int q = owner[u.group];
+            const int bytes = (int)u.row_col.size() * 32;
+            if (bytes > kTpPieceBytes) return false;
+            int& o = open[q];
+            if (o < 0 || cp[o].len + bytes > kTpPieceBytes) {
+              cp.push_back(Piece{q, dy * 4 + (s - 4 * j), 0, {}, {}});
+              o = (int)cp.size() - 1;
+            }
+            cp[o].offs.push_back(cp[o].len);
+            cp[o].len += bytes;
+            cp[o].units.push_back(u);
+          }
+      std::stable_sort(cp.begin(), cp.end(), [](const Piece& a, const Piece& b) { return a.key < b.key; });
+      for (Piece& pc : cp) pieces.push_back(std::move(pc));
+    }
+    T.chunk_piece[T.nchunks] = (int16_t)pieces.size();
+    T.npieces = (int)pieces.size();
+    if (T.npieces > kTpMaxPieces) return false;
+    for (int k = 0; k < T.npieces; ++k) {
+      const Piece& pc = pieces[k];
+      T.piece_len16[k] = (uint16_t)(pc.len / 16);
+      T.piece_owner[k] = (int8_t)pc.owner;
+      T.piece_unit[k] = (int16_t)prog.size();
+      for (size_t i = 0; i < pc.units.size(); ++i) {
+        const Unit& u = pc.units[i];
+        const int nn = u.form == 1 ? 2 * u.n : u.n;
+        if (!tp_shape_ok(u.tcol, nn) || u.tcol + nn > T.tmem_cols) return false;
+        if (u.form == 1 && (!tp_shape_ok(u.tcol2, u.n) || u.tcol2 + u.n > T.tmem_cols)) return false;
+        prog.push_back(tp_unit(pc.offs[i], u.s % 4, u.dy, u.form, u.tcol, u.n, u.tcol2));
+      }
+    }
+    T.piece_unit[T.npieces] = (int16_t)prog.size();
+    if ((int)prog.size() > kTpMaxUnits) return false;
+    for (size_t m = 0; m < prog.size(); ++m) T.unit[m] = prog[m];
+    // weights: [dx, dz column][piece] x kTpPieceBytes, in the 32-byte-row,
+    // 32-byte-swizzle image the MMAs read
+    T.w_base = (long long)H.W.size();
+    H.W.resize(H.W.size() + (size_t)9 * T.npieces * kTpPieceBytes, 0);
+    for (int xz = 0; xz < 9; ++xz) {
+      const int dx = xz % 3 - 1, dz = xz / 3 - 1;
+      for (int k = 0; k < T.npieces; ++k) {
+        const Piece& pc = pieces[k];
+        for (size_t i = 0; i < pc.units.size(); ++i) {
+          const Unit& u = pc.units[i];
+          const int d = (dx + 1) + 3 * u.dy + 9 * (dz + 1);
+          unsigned char* blk =
+              H.W.data() + T.w_base + ((size_t)xz * T.npieces + k) * kTpPieceBytes + pc.offs[i];
+          for (int r = 0; r < (int)u.row_col.size(); ++r) {
+            const int nrel = u.row_col[r], n = pp.c0 + nrel;
+            if (nrel < 0 || n >= pp.c1) continue;
+            for (int e = 0; e < kstep; ++e) {
+              const int kk = u.s * kstep + e;
+              if (kk >= kcol[n] || kk >= klen) continue;
+              const double w = entry(d, kk, n);
+              if (w == 0.0) continue;
+              const int byte = e * esz;
+              const size_t o = (size_t)r * 32 + (size_t)((((byte >> 4) ^ ((r >> 2) & 1)) << 4) | (byte & 15));
+              if (split) {
+                const uint16_t h = bf16_rn((float)w);
+                const uint16_t l = bf16_rn((float)(w - (double)bf16_to_f(h)));
+                std::memcpy(blk + o, u.row_plane[r] ? &l : &h, 2);
+              } else {
+                const float t = tf32_rn(w);
+                std::memcpy(blk + o, &t, 4);
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  // owner rings: every owner with pieces gets a slot, the rest go to the
+  // owners in proportion to the bytes they stream (largest remainder)
+  {
+    double bytes[kTpIssuers] = {};
+    for (const TpPass& T : H.pass)
+      for (int k = 0; k < T.npieces; ++k) bytes[T.piece_owner[k]] += T.piece_len16[k] * 16.0;
+    int ns[kTpIssuers] = {}, used = 0;
+    double tot = 0;
+    for (int q = 0; q < kTpIssuers; ++q) {
+      tot += bytes[q];
+      if (bytes[q] > 0) ns[q] = 1, ++used;
+    }
+    if (used > H.w_slots) return false;
+    while (used < H.w_slots) {
+      int best = -1;
+      double bd = -1;
+      for (int q = 0; q < kTpIssuers; ++q)
+        if (bytes[q] > 0) {
+          const double deficit = bytes[q] / tot * H.w_slots - ns[q];
+          if (deficit > bd) bd = deficit, best = q;
+        }
+      ++ns[best];
+      ++used;
+    }
+    int s0 = 0;
+    for (int q = 0; q < kTpIssuers; ++q) {
+      H.owner_slot0[q] = s0;
+      H.owner_nslots[q] = ns[q];
+      s0 += ns[q];
+    }
+  }
+  // one accumulator-set layout for every pass of the launch: a CTA moving
+  // from one pass to the next reuses the sets in the same places, so the
+  // acc_empty barriers of a set cover its whole column range
+  int tmax = 0;
+  for (const TpPass& T : H.pass) tmax = std::max(tmax, T.tmem_cols);
+  for (TpPass& T : H.pass) {
+    T.tmem_cols = tmax;
+    T.nbuf = 2 * tmax <= 512 ? 2 : 1;
+  }
+  return true;
+}
+
 // M2L groups: order blocks (orders 0 and 1 merged), each with the prefix
 // 8 nc(p - lowest order), split into pieces of <= 128 columns.  harm: rows
 // and columns are the harmonic components only ((q + 1)^2 up to order q; the
@@ -907,6 +1316,48 @@ bool build_tc_m2p(const MultiIndex& mi, const M2pTable& tab, int kind, TcHost& H
     return m2p_entry(mi, tab, d, red[k / 8] * 8 + k % 8, n);
   };
   return build_tc_generic(kind, gs, entry, H, 2);
+}
+
+// Prefix-schedule (k_nbr_tc.cu) forms of the three contractions above; they
+// return false where the prefix schedule does not apply (then the span
+// schedule of build_tc* runs).
+bool build_tp_m2l(const MultiIndex& mi, const TaylorTable& tt, int kind, TpHost& H, bool harm) {
+  const std::vector<int> red = harmonic_components(mi);
+  const int nk = harm ? (int)red.size() : mi.nc;
+  auto count = [harm](int q) { return harm ? (q + 1) * (q + 1) : ncoef(q); };
+  std::vector<int> kcol(8 * nk);
+  for (int n = 0; n < 8 * nk; ++n) {
+    const int m = level_of_order(mi, harm ? red[n / 8] : n / 8);
+    kcol[n] = 8 * count(std::min(mi.p - m, mi.mo));
+  }
+  auto entry = [&](int d, int k, int n) {
+    if (!harm) return m2l_entry(mi, tt, d, k, n);
+    return m2l_entry(mi, tt, d, red[k / 8] * 8 + k % 8, red[n / 8] * 8 + n % 8);
+  };
+  return build_tp_generic(kind, kcol, 8 * nk, entry, H);
+}
+
+bool build_tp_near(int b, int comps, int kind, TpHost& H) {
+  const int b3 = b * b * b;
+  std::vector<int> kcol(comps * b3, b3);
+  auto entry = [b](int d, int k, int n) {
+    const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+    return near_entry(b, D, k, n);
+  };
+  return build_tp_generic(kind, kcol, b3, entry, H);
+}
+
+bool build_tp_m2p(const MultiIndex& mi, const M2pTable& tab, int kind, TpHost& H, bool harm) {
+  const int ncol = 8 * tab.b * tab.b * tab.b;
+  const std::vector<int> red = harmonic_components(mi);
+  const int K = 8 * (harm ? (mi.mo + 1) * (mi.mo + 1) : ncoef(mi.mo));
+  std::vector<int> kcol(ncol, K);
+  auto entry = [&](int d, int k, int n) {
+    if (!harm) return m2p_entry(mi, tab, d, k, n);
+    if (k / 8 >= (int)red.size()) return 0.0;
+    return m2p_entry(mi, tab, d, red[k / 8] * 8 + k % 8, n);
+  };
+  return build_tp_generic(kind, kcol, K, entry, H);
 }
 
 // Weights of a CUDA-core contraction whose column tiles all reduce over K:
@@ -1219,11 +1670,45 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
         return cleanup(st);
     }
     if (anytc) {
+      auto fill_tp = [&](const TpHost& Hp, TpLaunch& T, const unsigned char* dw) {
+        T.npass = (int)Hp.pass.size();
+        for (int i = 0; i < T.npass; ++i) T.pass[i] = Hp.pass[i];
+        T.a_stages = Hp.a_stages;
+        T.w_slots = Hp.w_slots;
+        for (int q = 0; q < kTpIssuers; ++q) T.owner_slot0[q] = (int8_t)Hp.owner_slot0[q], T.owner_nslots[q] = (int8_t)Hp.owner_nslots[q];
+        T.W = dw;
+        T.n_cols = 8 * P->nc;
+        T.kind = P->tc_kind;
+        T.accumulate = 0;
+        T.col_mapped = P->harm ? 1 : 0;
+        if (P->harm) {
+          const std::vector<int> red = harmonic_components(P->mi);
+          for (size_t r = 0; r < red.size(); ++r) T.col_map[r] = (int16_t)red[r];
+        }
+      };
+      {
+        TpHost Hp;
+        if (build_tp_m2l(P->mi, tt, P->tc_kind, Hp, P->harm)) {
+          unsigned char* dw = nullptr;
+          if ((st = P->upload(Hp.W, &dw, s))) return cleanup(st);
+          fill_tp(Hp, P->tpl, dw);
+          P->tp_m2l = true;
+        }
+        if (P->asym) {
+          TpHost Ht;
+          if (build_tp_m2l(mt, tt, P->tc_kind, Ht, P->harm)) {
+            unsigned char* dw = nullptr;
+            if ((st = P->upload(Ht.W, &dw, s))) return cleanup(st);
+            fill_tp(Ht, P->tpl_t, dw);
+            P->tp_m2l_t = true;
+          }
+        }
+      }
       TcHost H;
-      if (!build_tc(P->mi, tt, P->tc_kind, H, P->harm))
+      if (!(P->tp_m2l && (!P->asym || P->tp_m2l_t)) && !build_tc(P->mi, tt, P->tc_kind, H, P->harm))
         return cleanup(fail(FMM_ERR_UNSUPPORTED, "order too high for the tensor-core schedule"));
       unsigned char* dw = nullptr;
-      if ((st = P->upload(H.W, &dw, s))) return cleanup(st);
+      if (!H.W.empty() && (st = P->upload(H.W, &dw, s))) return cleanup(st);
       P->tc.W = dw;
       P->tc.npass = H.npass;
       P->tc.a_stages = H.a_stages;
@@ -1236,7 +1721,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
         for (size_t r = 0; r < red.size(); ++r) P->tc.col_map[r] = (int16_t)red[r];
       }
       P->tc.err = nullptr;  // set below, after the flag exists
-      if (P->asym) {
+      if (P->asym && !P->tp_m2l_t) {
         TcHost Ht;
         if (!build_tc(mt, tt, P->tc_kind, Ht, P->harm))
           return cleanup(fail(FMM_ERR_UNSUPPORTED, "order too high for the transposed tensor-core schedule"));
@@ -1290,6 +1775,26 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     tab.build(P->mi, P->b);
     const Level& lf = P->lev[P->L];
     if (lf.tc) {
+      TpHost Hp;
+      if (build_tp_m2p(P->mi, tab, P->tc_kind, Hp, P->harm)) {
+        unsigned char* dw = nullptr;
+        if ((st = P->upload(Hp.W, &dw, s))) return cleanup(st);
+        TpLaunch& T = P->tpm;
+        T.npass = (int)Hp.pass.size();
+        for (int i = 0; i < T.npass; ++i) T.pass[i] = Hp.pass[i];
+        T.a_stages = Hp.a_stages;
+        T.w_slots = Hp.w_slots;
+        for (int q = 0; q < kTpIssuers; ++q) T.owner_slot0[q] = (int8_t)Hp.owner_slot0[q], T.owner_nslots[q] = (int8_t)Hp.owner_nslots[q];
+        T.W = dw;
+        T.n_cols = 8 * P->b * P->b * P->b;
+        T.kind = P->tc_kind;
+        T.accumulate = 0;
+        for (int q = 0; q < 3; ++q) T.grid[q] = lf.np[q];
+        T.C = reinterpret_cast<float*>(P->arena + P->m2p_off);
+        P->tp_m2p = P->m2p_tc = true;
+      }
+    }
+    if (lf.tc && !P->tp_m2p) {
       TcHost H;
       if (build_tc_m2p(P->mi, tab, P->tc_kind, H, P->harm)) {
         unsigned char* dw = nullptr;
@@ -1357,6 +1862,26 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     }
   }
   if (P->near_tc) {
+    TpHost Hp;
+    if (build_tp_near(P->b, P->near_comps, TC_BF16X3, Hp)) {
+      unsigned char* dw = nullptr;
+      if ((st = P->upload(Hp.W, &dw, s))) return cleanup(st);
+      TpLaunch& T = P->tpn;
+      T.npass = (int)Hp.pass.size();
+      for (int i = 0; i < T.npass; ++i) T.pass[i] = Hp.pass[i];
+      T.a_stages = Hp.a_stages;
+      T.w_slots = Hp.w_slots;
+      for (int q = 0; q < kTpIssuers; ++q) T.owner_slot0[q] = (int8_t)Hp.owner_slot0[q], T.owner_nslots[q] = (int8_t)Hp.owner_nslots[q];
+      T.W = dw;
+      T.n_cols = P->b * P->b * P->b * P->near_comps;
+      T.kind = TC_BF16X3;
+      T.accumulate = 0;
+      for (int q = 0; q < 3; ++q) T.grid[q] = P->lev[P->L].n[q];
+      T.C = reinterpret_cast<float*>(P->arena + P->near_off);
+      P->tp_near = true;
+    }
+  }
+  if (P->near_tc && !P->tp_near) {
     TcHost H;
     // bf16x3 in both tensor-core precisions: a TF32 near field would carry
     // ~3e-4 relative error on its (same-signed) sums
@@ -1379,13 +1904,17 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
       T.C = reinterpret_cast<float*>(P->arena + P->near_off);
       T.err = P->d_flag;
     }
+  }
+  if (P->near_tc) {
     // activation rows: the b^3 cell values of a leaf box (the output rows carry
     // near_comps x b^3 columns)
     const int b3 = P->b * P->b * P->b;
-    cudaError_t e = make_row_map(P->map_near_hi, P->arena + P->rho_hi_off, b3, 2, P->tcn[0].grid, 64);
-    if (e == cudaSuccess) e = make_row_map(P->map_near_lo, P->arena + P->rho_lo_off, b3, 2, P->tcn[0].grid, 64);
+    const int* ng = P->lev[P->L].n;
+    cudaError_t e = make_row_map(P->map_near_hi, P->arena + P->rho_hi_off, b3, 2, ng, 64);
+    if (e == cudaSuccess) e = make_row_map(P->map_near_lo, P->arena + P->rho_lo_off, b3, 2, ng, 64);
     if (e != cudaSuccess) return cleanup(fail(FMM_ERR_CUDA, "tensor map encoding failed for the near field"));
   }
+  P->tpl.err = P->tpl_t.err = P->tpm.err = P->tpn.err = P->d_flag;
   P->tc.err = P->d_flag;
   P->tc.accumulate = 0;
   P->tc_t.err = P->d_flag;
@@ -1606,6 +2135,10 @@ NbrGemm near_gemm(fmm_plan_t P) {
 // them and the schedule fits, else the CUDA-core contraction).
 fmm_status do_m2p(fmm_plan_t P, cudaStream_t s) {
   const Level& lf = P->lev[P->L];
+  if (P->tp_m2p) {
+    CUDA_TRY(launch_nbr_tc(P->tpm, P->map_hi[P->L], P->map_lo[P->L], s));
+    return FMM_OK;
+  }
   if (P->m2p_tc) {
     CUDA_TRY(launch_m2l_tc(P->tcm, P->map_hi[P->L], P->map_lo[P->L], s));
     return FMM_OK;
@@ -1652,6 +2185,13 @@ fmm_status do_p2l(fmm_plan_t P, cudaStream_t s) {
 
 fmm_status do_m2l(fmm_plan_t P, int l, cudaStream_t s) {
   const Level& lv = P->lev[l];
+  if (lv.tc && ((P->transposed && P->asym) ? P->tp_m2l_t : P->tp_m2l)) {
+    TpLaunch& L = (P->transposed && P->asym) ? P->tpl_t : P->tpl;
+    L.C = static_cast<float*>(P->Lx(l));
+    for (int q = 0; q < 3; ++q) L.grid[q] = lv.np[q];
+    CUDA_TRY(launch_nbr_tc(L, P->map_hi[l], P->map_lo[l], s));
+    return FMM_OK;
+  }
   if (lv.tc) {
     TcLaunch L = (P->transposed && P->asym) ? P->tc_t : P->tc;
     L.C = static_cast<float*>(P->Lx(l));
@@ -1737,7 +2277,10 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
   // near field over the 27 neighbour leaf boxes
   if (P->near_tc) {
     StageTimer t(P, ST_NEAR_TC, s);
-    for (const TcLaunch& NL : P->tcn) CUDA_TRY(launch_m2l_tc(NL, P->map_near_hi, P->map_near_lo, s));
+    if (P->tp_near)
+      CUDA_TRY(launch_nbr_tc(P->tpn, P->map_near_hi, P->map_near_lo, s));
+    else
+      for (const TcLaunch& NL : P->tcn) CUDA_TRY(launch_m2l_tc(NL, P->map_near_hi, P->map_near_lo, s));
   } else if (!near_side) {
     StageTimer t(P, ST_NEAR, s);
     CUDA_TRY(launch_nbr_gemm<T>(near_gemm(P), s));
@@ -1896,7 +2439,7 @@ int fmm_solve_launches(fmm_plan_t P, int with_accel) {
     if (l == 2 && L == 2 && P->m2p) n += 1;          // zero leaf locals (final-stage M2P, no parent far field)
     if (!P->lev[l].tc && P->m2l_choice[l].dsplit > 1 && !(l == L && P->m2p)) n += 1;  // partial-sum reduction
   }
-  n += P->near_tc ? (int)P->tcn.size() + 1 : 2;  // near field + leaf finish
+  n += P->near_tc ? (P->tp_near ? 1 : (int)P->tcn.size()) + 1 : 2;  // near field + leaf finish
   if (!P->near_tc && P->near_choice.dsplit > 1) n += 1;
   if (with_accel && P->near_comps == 1) n += 1;  // FD stencil (the analytic force comes with the leaf kernel)
   return n;

@@ -263,4 +263,104 @@ cudaError_t make_row_map(void* map_out /* CUtensorMap */, const void* base, int 
                          const int grid[3], int box_inner);
 cudaError_t launch_m2l_tc(const TcLaunch& L, const void* map_hi, const void* map_lo, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Prefix-schedule tensor-core contraction (k_nbr_tc.cu): the same neighbour
+// contraction, with output columns ordered so that every K step of the
+// reduction (16 bf16 or 8 TF32 values) is needed by a prefix of them.  One
+// tile (128 rows) keeps all its output columns in one accumulator set, so a
+// K step is one MMA per product and 128-column chunk of that prefix instead
+// of one per column group:
+//   * D: the accumulators of every output column (hi*hi, lo*hi, hi*lo);
+//   * E (TMEM columns [0, e), before D): "fused" K steps with a narrow
+//     prefix issue hi*hi and hi*lo as one MMA of 2N columns over a weight
+//     block [lo rows reversed; hi rows], whose first N columns land in E
+//     (E column c holds output column e - 1 - c) and the last N in D;
+//   * L2: the K steps from a split point on accumulate in a region of their
+//     own (or, with no such split, the fused steps' lo*hi), so that no FP32
+//     accumulator takes more than about half of the long low-order sums (the
+//     tensor cores add with truncation).
+// The epilogue adds D, E and L2 in a fixed order.  Every accumulator column
+// has one issuing thread ("owner": 128-column chunks of D, E with the first
+// chunk, L2 apart), so each column sums its products in a fixed order and
+// results are bit-reproducible.  Weights stream as pieces (<= 16 KB, never
+// across a reduction chunk, each read by one owner only) copied by
+// kTpWLanes threads: bulk copies issued by one thread complete one after
+// another.
+constexpr int kTpMaxPasses = 4;
+constexpr int kTpMaxChunks = 48;
+constexpr int kTpMaxPieces = 256;
+constexpr int kTpMaxUnits = 1024;
+constexpr int kTpMaxGroups = 48;
+constexpr int kTpIssuers = 4;
+constexpr int kTpWLanes = 4;  // copy lanes of one owner's producer warp
+constexpr int kTpALanes = 4;
+constexpr int kTpPieceBytes = 16384;
+constexpr int kTpMaxSlots = 16;
+constexpr int kTpMaxAStages = 4;
+
+// One unit of a column program: the MMAs that read one weight block of one
+// K step, 32 bits:
+//   bits 0-4    block offset in its piece / 512
+//   bits 5-6    K step in the activation chunk
+//   bits 7-8    dy (activation window)
+//   bits 9-10   form: 0 three products (hi rows, then lo rows: hi*hi, lo*hi,
+//               hi*lo into columns tcol..), 1 fused (lo rows reversed, then
+//               hi rows: hi*[lo; hi] over 2N columns from tcol, then lo*hi
+//               into tcol2), 2 one product (TF32)
+//   bits 11-15  TMEM column / 16 of the (first) MMA
+//   bits 16-20  N / 16
+//   bits 21-25  form 1: TMEM column / 16 of the lo*hi MMA
+inline constexpr uint32_t tp_unit(int b_off, int ks, int dy, int form, int tcol, int n, int tcol2) {
+  return (uint32_t)(b_off >> 9) | ((uint32_t)ks << 5) | ((uint32_t)dy << 7) | ((uint32_t)form << 9) |
+         ((uint32_t)(tcol >> 4) << 11) | ((uint32_t)(n >> 4) << 16) | ((uint32_t)(tcol2 >> 4) << 21);
+}
+
+struct TpPass {
+  int nchunks;        // 128-byte activation chunks per neighbour row
+  int npieces;        // weight pieces per (dx, dz) neighbour column
+  int tmem_cols;      // TMEM columns of one accumulator set (E + D + L2, multiple of 16)
+  int nbuf;           // accumulator sets (2 when they fit in 512 columns)
+  int ngroups;        // 16-column output groups
+  int col0, ncols;    // output columns [col0, col0 + ncols) of the full row
+  long long w_base;   // bytes: pieces of this pass, [dx, dz column][piece] x kTpPieceBytes
+  int16_t chunk_piece[kTpMaxChunks + 1];  // pieces of chunk j: [chunk_piece[j], chunk_piece[j + 1])
+  int16_t piece_unit[kTpMaxPieces + 1];   // units of piece k: [piece_unit[k], piece_unit[k + 1])
+  uint16_t piece_len16[kTpMaxPieces];     // bytes of piece k / 16
+  int8_t piece_owner[kTpMaxPieces];       // issuer that reads piece k
+  // epilogue: group g = output columns col0 + 16 g ..: TMEM column of its D
+  // accumulators, of its reversed E accumulators (column grp_e[g] + 15 - i
+  // holds column 16 g + i) and of its L2 accumulators; -1 when absent
+  int16_t grp_d[kTpMaxGroups], grp_e[kTpMaxGroups], grp_l2[kTpMaxGroups];
+  uint32_t unit[kTpMaxUnits];
+};
+
+struct TpLaunch {
+  TpPass pass[kTpMaxPasses];
+  int npass;
+  int a_stages;   // activation stages (2 .. kTpMaxAStages)
+  int w_slots;    // weight ring slots of kTpPieceBytes (<= kTpMaxSlots)
+  // each issuer ("owner") has a ring of its own: slots [owner_slot0[q],
+  // owner_slot0[q] + owner_nslots[q]), the same for every pass, filled by a
+  // producer warp of its own in the owner's piece order
+  int8_t owner_slot0[kTpIssuers], owner_nslots[kTpIssuers];
+  const unsigned char* W;
+  float* C;       // [rows][n_cols]
+  int n_cols;
+  int accumulate; // 1: C += result, 0: C = result
+  int grid[3];    // row grid
+  int kind;       // TC_BF16X3 or TC_TF32
+  int* err;
+  int col_mapped; // as TcLaunch
+  int16_t col_map[kTcMaxColMap];
+};
+
+// Shared memory of the prefix-schedule kernel for a stage count / kind.
+inline int tp_smem_budget() { return kTcSmemUsable; }
+inline int tp_w_slots(int kind, int a_stages) {
+  const int left = kTcSmemUsable - 2048 - a_stages * kTcAPlaneBytes * (kind == 0 ? 2 : 1);
+  const int s = left / kTpPieceBytes;
+  return s > kTpMaxSlots ? kTpMaxSlots : s;
+}
+cudaError_t launch_nbr_tc(const TpLaunch& L, const void* map_hi, const void* map_lo, cudaStream_t s);
+
 }  // namespace fmmgb

@@ -40,6 +40,7 @@
 #include <algorithm>
 
 #include "fmm_internal.h"
+#include "tc_ptx.cuh"
 
 namespace fmmgb {
 namespace {
@@ -52,128 +53,6 @@ constexpr int kSmemBytes = kTcSmemUsable + 1024 /*alignment*/;
 static_assert((2 * kTcMaxAStages + 2 * kTcIssuers * kRingE + 4) * 8 + 4 <= 2048, "barrier region");
 static_assert(kSmemBytes <= 227 * 1024, "shared memory of the tensor-core kernel");
 static_assert(kAPlane % 1024 == 0, "activation planes keep the 1 KB swizzle alignment");
-constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s per wait
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.b32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the phase of `parity` to complete; false on time-out, after
-// recording FMM_ERR_TIMEOUT (bit 1) and the wait site (bits 8..15) in *err.
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int site) {
-  const unsigned long long t0 = globaltimer();
-  for (uint32_t i = 0;; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63u) == 63u) {
-      if (*reinterpret_cast<volatile int*>(err) & 2) return false;  // another CTA timed out
-      if (globaltimer() - t0 > kTimeoutNs) {
-        atomicOr(err, 2 | (1 << (8 + site)));
-        return false;
-      }
-    }
-  }
-}
-
-// One inline probe first: most waits are already satisfied.
-__device__ __forceinline__ bool wait_fast(uint64_t* bar, uint32_t parity, int* err, int site) {
-  return mbar_try_wait(bar, parity) || mbar_wait(bar, parity, err, site);
-}
-
-enum WaitSite { W_PROD_A = 0, W_PROD_B, W_MMA_A, W_MMA_B, W_EPI, W_DRAIN, W_MMA_ACC };
-
-__device__ __forceinline__ void tma_load_4d(void* dst, const void* map, uint64_t* bar, int c0, int c1, int c2,
-                                            int c3) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 B, 8-row groups 1024 B apart (sm_100 family descriptor, version 1).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1u << 16;            // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: next 8-row group
-  d |= (uint64_t)1u << 46;            // descriptor version
-  d |= (uint64_t)2u << 61;            // SWIZZLE_128B
-  return d;
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // Issues the MMAs of one span: KS K steps of 32 bytes each (descriptor start
 // address + 2 per step), three products per step for bf16x3.
@@ -287,7 +166,7 @@ __global__ void __maxnreg__(72)
     }
     if (!ok)  // drain: never leave the CTA with copies in flight
       for (uint32_t i = (ai > nA ? ai - nA : 0); i < ai; ++i)
-        mbar_wait(&a_full[i % nA], (i / nA) & 1, P.err, W_DRAIN);
+        mbar_wait_drain(&a_full[i % nA], (i / nA) & 1);
   } else if (warp >= 1 && warp <= NQ && lane == 0) {
     // ---------------- weight producers ----------------
     // Ring q = warp - 1, in the order its issuer consumes: tile, neighbour
@@ -337,7 +216,7 @@ __global__ void __maxnreg__(72)
       }
     }
     if (!ok)  // drain: never leave the CTA with copies in flight
-      for (uint32_t i = tail; i < e; ++i) mbar_wait(&full[i % kRingE], (i / kRingE) & 1, P.err, W_DRAIN);
+      for (uint32_t i = tail; i < e; ++i) mbar_wait_drain(&full[i % kRingE], (i / kRingE) & 1);
   } else if (warp > NQ && warp <= 2 * NQ && lane == 0) {
     // ---------------- MMA issuers ----------------
     const int q = warp - 1 - NQ;

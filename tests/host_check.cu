@@ -11,6 +11,11 @@
 //                         contraction, orders 2..8 (exact up to rounding)
 //   host_check cuda-core  the CUDA-core M2L weight tiles (prefix-cut
 //                         reductions) against the full contraction
+//   host_check prefix     the prefix-schedule contractions (k_nbr_tc.cu):
+//                         resources, owner rings, one writer per TMEM
+//                         column, emulated MMAs, randomised protocol replays
+//   host_check prefix-plant  planted prefix-schedule mistakes, each caught
+//   host_check rounding   the FP32 accumulation-chain bound of each schedule
 //
 // The library's plan packs every tensor-core contraction (M2L per level,
 // final-stage M2P, the near field) into passes of MMA spans, per-issuer
@@ -44,6 +49,8 @@
 #include "tree_common.cuh"
 
 #include <cstdio>
+#include <cmath>
+#include <functional>
 #include <random>
 #include <string>
 
@@ -367,6 +374,678 @@ int planted_mistakes() {
   return missed;
 }
 
+// ------------------------------------------------------- prefix schedule --
+//
+// The prefix schedules (k_nbr_tc.cu, build_tp_*): resources (TMEM columns of
+// the accumulator sets, ring slots against the producer lanes, piece sizes),
+// the program's fields (every MMA inside its piece and inside its accumulator
+// set, N a multiple of 16 up to 256, pieces never crossing a chunk), the
+// epilogue's groups (D, reversed E and L2 regions inside the set), and the
+// arithmetic: every MMA emulated from the packed, swizzled 32-byte rows
+// (bf16 hi / lo planes or TF32) over the 27 neighbour rows of random
+// activations, accumulated per TMEM column and read back the epilogue's way,
+// against the direct contraction.  `rz` also accumulates every MMA's sum into
+// FP32 with truncation (the tensor cores' adder) on same-signed activations,
+// to compare accumulator chains between schedules.
+
+// The kernel's barrier protocol replayed on the CPU (the same slot, stage and
+// parity arithmetic as k_nbr_tc.cu): activation producer groups, one weight
+// producer per owner ring, the issuers (every stage, their own pieces), the
+// epilogue's accumulator hand-off.  A barrier is a count of completed phases
+// plus the arrivals of the current one; a wait is modelled as the hardware
+// does it (satisfied when the current phase's parity differs from the one
+// waited for) and must agree with the phase the protocol means; each run
+// picks the next actor at random, and every actor must finish.
+struct SimBar {
+  int expected = 1, arrived = 0, done = 0;  // done: completed phases
+  void arrive(int n = 1) {
+    arrived += n;
+    while (arrived >= expected) arrived -= expected, ++done;
+  }
+  bool hw(uint32_t parity) const { return (uint32_t)(done & 1) != parity; }
+};
+
+std::string simulate_protocol(const TpHost& H, int kind, int nitems, unsigned seed) {
+  const int planes = kind == TC_BF16X3 ? 2 : 1, G = kTpALanes / planes, nA = H.a_stages, Q = kTpIssuers;
+  std::vector<SimBar> a_full(nA), a_empty(nA), w_full(H.w_slots), w_empty(H.w_slots), acc_full(2), acc_empty(2);
+  for (auto& b : a_full) b.expected = planes;
+  for (auto& b : a_empty) b.expected = Q;
+  for (auto& b : acc_full) b.expected = Q;
+  for (auto& b : acc_empty) b.expected = 4;
+  // the work each CTA does: items of passes (item i -> pass i % npass), as a flat list of stages
+  struct Stage { int pass, xz, j; };
+  std::vector<std::vector<Stage>> item_stages(nitems);
+  std::vector<int> item_pass(nitems);
+  for (int it = 0; it < nitems; ++it) {
+    item_pass[it] = it * (int)H.pass.size() / nitems;
+    for (int xz = 0; xz < 9; ++xz)
+      for (int j = 0; j < H.pass[item_pass[it]].nchunks; ++j) item_stages[it].push_back({item_pass[it], xz, j});
+  }
+  std::vector<Stage> stages;
+  for (auto& v : item_stages) stages.insert(stages.end(), v.begin(), v.end());
+  const int T = (int)stages.size();
+  // owner piece sequences (owner-local index l -> (stage, piece))
+  std::vector<std::vector<std::pair<int, int>>> own(Q);
+  for (int t = 0; t < T; ++t) {
+    const TpPass& P = H.pass[stages[t].pass];
+    for (int k = P.chunk_piece[stages[t].j]; k < P.chunk_piece[stages[t].j + 1]; ++k) own[P.piece_owner[k]].push_back({t, k});
+  }
+  auto acc_buf = [&](int it, std::vector<int>& uses, int& flip, int& phase) {
+    const int nbuf = H.pass[item_pass[it]].nbuf;
+    const int buf = nbuf == 2 ? (flip++ & 1) : 0;
+    phase = uses[buf]++;
+    return buf;
+  };
+  std::mt19937 rng(seed);
+  std::string err;
+  auto wait_ok = [&](const SimBar& b, int phase_index, uint32_t parity, const char* who) {
+    const bool intended = b.done > phase_index, hardware = b.hw(parity);
+    if (intended != hardware && err.empty())
+      err = std::string(who) + ": a parity wait that does not match its phase (" +
+            (hardware ? "passes early" : "would hang") + ")";
+    return intended && hardware;
+  };
+  // actors
+  std::vector<int> a_next(G, 0);               // next stage of A group g
+  std::vector<size_t> w_next(Q, 0);            // next owner-local piece of producer q
+  struct Iss { int item = 0, t = 0, stage_in_item = 0, piece = -1, phase = 0, buf = 0, state = 0; size_t l = 0;
+               std::vector<int> uses{0, 0}; int flip = 0; };
+  std::vector<Iss> iss(Q);
+  struct Epi { int item = 0, state = 0, buf = 0, phase = 0; std::vector<int> uses{0, 0}; int flip = 0; } epi;
+  // each actor's speed for this run: skewed interleavings (an idle issuer far
+  // ahead of a busy one) are the ones that expose a mis-sequenced wait
+  std::vector<double> speed(G + 2 * Q + 1);
+  for (double& v : speed) v = std::pow(10.0, (double)(rng() % 3));
+  auto pick = [&](const std::vector<int>& c) {
+    double tot = 0;
+    for (int a : c) tot += speed[a];
+    double r = tot * (rng() / (double)rng.max());
+    for (int a : c)
+      if ((r -= speed[a]) <= 0) return a;
+    return c.back();
+  };
+  for (auto& g : a_next) g = 0;
+  for (int g = 0; g < G; ++g) while (a_next[g] < T && (a_next[g] % nA) % G != g) ++a_next[g];
+  acc_empty[0].arrive(4);
+  acc_empty[1].arrive(4);
+  for (int step = 0; step < 50000000 && err.empty(); ++step) {
+    std::vector<int> can;  // actors that can move: 0..G-1 A groups, G..G+Q-1 producers, G+Q.. issuers, last epilogue
+    auto try_actor = [&](int a, bool act) -> bool {
+      if (a < G) {
+        const int t = a_next[a];
+        if (t >= T) return false;
+        const int slot = t % nA, use = t / nA;
+        if (use > 0 && !wait_ok(a_empty[slot], use - 1, ((use & 1) ^ 1), "activation producer")) return false;
+        if (act) {
+          a_full[slot].arrive(planes);
+          int nt = t + 1;
+          while (nt < T && (nt % nA) % G != a) ++nt;
+          a_next[a] = nt;
+        }
+        return true;
+      }
+      if (a < G + Q) {
+        const int q = a - G;
+        const size_t l = w_next[q];
+        if (l >= own[q].size()) return false;
+        const int ns = H.owner_nslots[q], slot = H.owner_slot0[q] + (int)(l % ns), use = (int)(l / ns);
+        if (use > 0 && !wait_ok(w_empty[slot], use - 1, ((use & 1) ^ 1), "weight producer")) return false;
+        if (act) w_full[slot].arrive(), ++w_next[q];
+        return true;
+      }
+      if (a < G + 2 * Q) {
+        const int q = a - G - Q;
+        Iss& I = iss[q];
+        if (I.item >= nitems) return false;
+        const TpPass& P = H.pass[item_pass[I.item]];
+        if (I.state == 0) {  // accumulator set
+          int flip = I.flip, ph = 0;
+          std::vector<int> uses = I.uses;
+          const int buf = acc_buf(I.item, uses, flip, ph);
+          if (!wait_ok(acc_empty[buf], ph, ph & 1, "issuer (accumulators)")) return false;
+          if (act) I.flip = flip, I.uses = uses, I.buf = buf, I.state = 1;
+          return true;
+        }
+        if (I.state == 1) {  // stage t
+          const int slot = I.t % nA, use = I.t / nA;
+          if (!wait_ok(a_full[slot], use, use & 1, "issuer (activations)")) return false;
+          if (act) I.state = 2, I.piece = P.chunk_piece[stages[I.t].j];
+          return true;
+        }
+        if (I.state == 2) {  // pieces of the stage's chunk
+          const int j = stages[I.t].j;
+          while (I.piece < P.chunk_piece[j + 1] && P.piece_owner[I.piece] != q) ++I.piece;
+          if (I.piece < P.chunk_piece[j + 1]) {
+            const int ns = H.owner_nslots[q], slot = H.owner_slot0[q] + (int)(I.l % ns), use = (int)(I.l / ns);
+            if (!wait_ok(w_full[slot], use, use & 1, "issuer (weights)")) return false;
+            if (act) w_empty[slot].arrive(), ++I.l, ++I.piece;
+            return true;
+          }
+          if (act) {
+            a_empty[I.t % nA].arrive();
+            ++I.t;
+            if (++I.stage_in_item == (int)item_stages[I.item].size()) {
+              acc_full[I.buf].arrive();
+              ++I.item, I.stage_in_item = 0, I.state = 0;
+            } else {
+              I.state = 1;
+            }
+          }
+          return true;
+        }
+        return false;
+      }
+      // epilogue
+      if (epi.item >= nitems) return false;
+      int flip = epi.flip, ph = 0;
+      std::vector<int> uses = epi.uses;
+      const int buf = acc_buf(epi.item, uses, flip, ph);
+      if (!wait_ok(acc_full[buf], ph, ph & 1, "epilogue")) return false;
+      if (act) epi.flip = flip, epi.uses = uses, acc_empty[buf].arrive(4), ++epi.item;
+      return true;
+    };
+    const int nact = G + 2 * Q + 1;
+    for (int a = 0; a < nact; ++a)
+      if (try_actor(a, false)) can.push_back(a);
+    if (!err.empty()) break;
+    if (can.empty()) {
+      bool done = epi.item >= nitems;
+      for (int q = 0; q < Q; ++q) done = done && iss[q].item >= nitems && w_next[q] >= own[q].size();
+      if (!done) err = "deadlock";
+      break;
+    }
+    try_actor(pick(can), true);
+  }
+  return err;
+}
+
+struct TpResult {
+  double err = 0, rz = 0;
+  int missing = 0;
+};
+
+float bf_at(const unsigned char* blk, int r, int e) {  // element e of row r of a 32-byte-row bf16 block
+  const int byte = e * 2;
+  uint16_t h;
+  std::memcpy(&h, blk + (size_t)r * 32 + ((((byte >> 4) ^ ((r >> 2) & 1)) << 4) | (byte & 15)), 2);
+  return bf16_to_f(h);
+}
+float tf_at(const unsigned char* blk, int r, int e) {
+  const int byte = e * 4;
+  float w;
+  std::memcpy(&w, blk + (size_t)r * 32 + ((((byte >> 4) ^ ((r >> 2) & 1)) << 4) | (byte & 15)), 4);
+  return w;
+}
+float rz_add(float acc, double inc) {  // FP32 add truncated toward zero
+  const double x = (double)acc + inc;
+  float f = (float)x;
+  if (std::fabs((double)f) > std::fabs(x)) f = std::nextafter(f, 0.0f);
+  return f;
+}
+
+template <typename Entry>
+bool tp_check(const char* name, int kind, const TpHost& H, int ncol, int klen, const Entry& entry, bool positive = false,
+              TpResult* res = nullptr) {
+  const bool split = kind == TC_BF16X3;
+  const int kstep = split ? 16 : 8;
+  std::mt19937 rng(ncol * 7 + kind);
+  std::uniform_real_distribution<double> U(positive ? 0.0 : -1.0, 1.0);
+  std::vector<std::vector<float>> A(27, std::vector<float>(klen, 0.f));
+  for (auto& r : A)
+    for (float& a : r) a = (float)U(rng);
+  std::vector<double> ref(ncol, 0), got(ncol, 0), sabs(ncol, 0);
+  std::vector<float> gotz(ncol, 0.f);
+  for (int d = 0; d < 27; ++d)
+    for (int k = 0; k < klen; ++k)
+      for (int n = 0; n < ncol; ++n) {
+        const double t = A[d][k] * entry(d, k, n);
+        ref[n] += t;
+        sabs[n] += std::fabs(t);
+      }
+  std::vector<int> writer(ncol, -1);
+  if (H.w_slots < 1 || H.w_slots > kTpMaxSlots) return fail(name, "ring slots", -1);
+  for (int q = 0, s0 = 0; q < kTpIssuers; ++q) {
+    if (H.owner_slot0[q] != s0 || H.owner_nslots[q] < 0) return fail(name, "owner rings do not tile the slots", -1);
+    s0 += H.owner_nslots[q];
+    if (q == kTpIssuers - 1 && s0 != H.w_slots) return fail(name, "owner rings do not tile the slots", -1);
+  }
+  for (const TpPass& P : H.pass)
+    for (int k = 0; k < P.npieces; ++k)
+      if (H.owner_nslots[P.piece_owner[k]] < 1) return fail(name, "an owner with pieces has no ring slot", -1);
+  if (H.a_stages < 2 || H.a_stages > kTpMaxAStages) return fail(name, "activation stages", -1);
+  if (2048 + H.a_stages * kTcAPlaneBytes * (split ? 2 : 1) + H.w_slots * kTpPieceBytes > kTcSmemUsable)
+    return fail(name, "shared memory over the budget", -1);
+  int mmas = 0;
+  for (int ps = 0; ps < (int)H.pass.size(); ++ps) {
+    const TpPass& P = H.pass[ps];
+    if (P.tmem_cols % 16 || P.tmem_cols * P.nbuf > 512) return fail(name, "more than 512 TMEM columns", ps);
+    if (P.chunk_piece[0] != 0 || P.chunk_piece[P.nchunks] != P.npieces) return fail(name, "chunk pieces", ps);
+    for (int j = 0; j < P.nchunks; ++j)
+      if (P.chunk_piece[j] > P.chunk_piece[j + 1]) return fail(name, "chunk pieces reversed", ps);
+    if (P.piece_unit[0] != 0) return fail(name, "piece program", ps);
+    for (int g = 0; g < P.ngroups; ++g) {
+      if (P.grp_d[g] < 0 || P.grp_d[g] + 16 > P.tmem_cols) return fail(name, "epilogue D outside the set", ps);
+      if (P.grp_e[g] >= 0 && P.grp_e[g] + 16 > P.tmem_cols) return fail(name, "epilogue E outside the set", ps);
+      if (P.grp_l2[g] >= 0 && P.grp_l2[g] + 16 > P.tmem_cols) return fail(name, "epilogue L2 outside the set", ps);
+      for (int c = 0; c < 16 && 16 * g + c < P.ncols; ++c) {
+        const int n = P.col0 + 16 * g + c;
+        if (n < 0 || n >= ncol) return fail(name, "output column out of range", ps);
+        if (writer[n] >= 0) return fail(name, "output column stored by two passes", ps);
+        writer[n] = ps;
+      }
+    }
+    // emulate one row: TMEM columns of one set, exact and truncating; every
+    // column must be written by one issuer only (fixed summation order)
+    std::vector<double> tm(P.tmem_cols, 0.0);
+    std::vector<float> tz(P.tmem_cols, 0.f);
+    std::vector<int> col_owner(P.tmem_cols, -1);
+    auto mma = [&](int tcol, int n, const unsigned char* blk, int row0, int plane, int d, int s, int owner) {
+      if (!tp_shape_ok(tcol, n)) return std::string("MMA shape outside the validated forms");
+      if (tcol + n > P.tmem_cols) return std::string("MMA writes outside its accumulator set");
+      for (int i = 0; i < n; ++i) {
+        int& o = col_owner[tcol + i];
+        if (o >= 0 && o != owner) return std::string("accumulator column written by two issuers");
+        o = owner;
+        double acc = 0;
+        for (int e = 0; e < kstep; ++e) {
+          const int kk = s * kstep + e;
+          const float a = kk < klen ? A[d][kk] : 0.f;
+          if (split) {
+            const float ah = bf16_to_f(bf16_rn(a));
+            const float av = plane ? bf16_to_f(bf16_rn(a - ah)) : ah;
+            acc += (double)av * bf_at(blk, row0 + i, e);
+          } else {
+            acc += (double)tf32_trunc(a) * tf_at(blk, row0 + i, e);
+          }
+        }
+        tm[tcol + i] += acc;
+        tz[tcol + i] = rz_add(tz[tcol + i], acc);
+      }
+      ++mmas;
+      return std::string();
+    };
+    for (int xz = 0; xz < 9; ++xz) {
+      const int dx = xz % 3 - 1, dz = xz / 3 - 1;
+      for (int j = 0; j < P.nchunks; ++j)
+        for (int k = P.chunk_piece[j]; k < P.chunk_piece[j + 1]; ++k) {
+          const int len = P.piece_len16[k] * 16;
+          if (len <= 0 || len > kTpPieceBytes) return fail(name, "piece size", ps);
+          if (P.piece_owner[k] < 0 || P.piece_owner[k] >= kTpIssuers) return fail(name, "piece owner", ps);
+          const unsigned char* piece = H.W.data() + P.w_base + ((size_t)xz * P.npieces + k) * kTpPieceBytes;
+          for (int u = P.piece_unit[k]; u < P.piece_unit[k + 1]; ++u) {
+            const uint32_t w = P.unit[u];
+            const int b_off = (int)(w & 31u) << 9, ks = (w >> 5) & 3, dy = (w >> 7) & 3, form = (w >> 9) & 3;
+            const int tcol = (int)((w >> 11) & 31u) << 4, n = (int)((w >> 16) & 31u) << 4;
+            const int tcol2 = (int)((w >> 21) & 31u) << 4;
+            if (dy > 2) return fail(name, "bad unit operand", ps);
+            if (split != (form != 2)) return fail(name, "unit form against the precision", ps);
+            const int rows = form == 2 ? n : 2 * n;
+            if (b_off + rows * 32 > len) return fail(name, "unit reads past its piece", ps);
+            const int d = (dx + 1) + 3 * dy + 9 * (dz + 1), s = 4 * j + ks, q = P.piece_owner[k];
+            std::string e;
+            if (form == 0) {  // hi rows then lo rows: hi*hi, lo*hi, hi*lo
+              if (e.empty()) e = mma(tcol, n, piece + b_off, 0, 0, d, s, q);
+              if (e.empty()) e = mma(tcol, n, piece + b_off, 0, 1, d, s, q);
+              if (e.empty()) e = mma(tcol, n, piece + b_off, n, 0, d, s, q);
+            } else if (form == 1) {  // hi*[lo reversed; hi] over 2N, then lo*hi
+              if (e.empty()) e = mma(tcol, 2 * n, piece + b_off, 0, 0, d, s, q);
+              if (e.empty()) e = mma(tcol2, n, piece + b_off, n, 1, d, s, q);
+            } else {
+              e = mma(tcol, n, piece + b_off, 0, 0, d, s, q);
+            }
+            if (!e.empty()) return fail(name, e.c_str(), ps);
+          }
+        }
+    }
+    for (int g = 0; g < P.ngroups; ++g)
+      for (int c = 0; c < 16 && 16 * g + c < P.ncols; ++c) {
+        const int n = P.col0 + 16 * g + c;
+        double v = tm[P.grp_d[g] + c];
+        float vz = tz[P.grp_d[g] + c];
+        if (P.grp_e[g] >= 0) v += tm[P.grp_e[g] + 15 - c], vz += tz[P.grp_e[g] + 15 - c];
+        if (P.grp_l2[g] >= 0) v += tm[P.grp_l2[g] + c], vz += tz[P.grp_l2[g] + c];
+        got[n] = v;
+        gotz[n] = vz;
+      }
+  }
+  for (unsigned seed = 1; seed <= 20; ++seed) {
+    const std::string e = simulate_protocol(H, kind, 3 * (int)H.pass.size(), seed);
+    if (!e.empty()) return fail(name, ("barrier protocol: " + e).c_str(), -1);
+  }
+  TpResult R;
+  for (int n = 0; n < ncol; ++n) {
+    R.missing += writer[n] < 0;
+    if (sabs[n] > 0) {
+      R.err = std::max(R.err, std::fabs(got[n] - ref[n]) / sabs[n]);
+      R.rz = std::max(R.rz, std::fabs((double)gotz[n] - ref[n]) / sabs[n]);
+    }
+  }
+  if (res) *res = R;
+  const double tol = split ? 2e-5 : 1e-3;
+  size_t pieces = 0;
+  int maxset = 0;
+  for (const TpPass& P : H.pass) pieces += P.npieces, maxset = std::max(maxset, P.tmem_cols * P.nbuf);
+  std::printf("%-28s %-6s passes %d mmas/tile %5d pieces/column %3zu tmem %3d weights %6.2f MB uncovered %d "
+              "err/sum|terms| %.2e rz %.2e\n",
+              name, split ? "bf16x3" : "tf32", (int)H.pass.size(), mmas, pieces, maxset, H.W.size() / 1e6,
+              R.missing, R.err, R.rz);
+  if (R.missing) return fail(name, "output columns never written", -1);
+  if (!(R.err <= tol)) return fail(name, "result differs from the direct contraction", -1);
+  return true;
+}
+
+bool tp_m2l_case(int kind, int p, int mult_order, int local_order, bool harm, bool& built) {
+  MultiIndex mi;
+  mi.init(p);
+  if (mult_order >= 0) mi.mo = mult_order;
+  if (local_order >= 0) mi.lo = local_order;
+  TaylorTable tt;
+  tt.build(mi);
+  TpHost H;
+  char name[64];
+  std::snprintf(name, sizeof name, "m2l p=%d mo=%d lo=%d%s", p, mi.mo, mi.lo, harm ? " harmonic" : "");
+  built = build_tp_m2l(mi, tt, kind, H, harm);
+  if (!built) {
+    std::printf("%-28s %-6s span schedule (no prefix schedule)\n", name, kind == TC_BF16X3 ? "bf16x3" : "tf32");
+    return true;
+  }
+  const std::vector<int> red = harmonic_components(mi);
+  const int nk = harm ? (int)red.size() : mi.nc;
+  return tp_check(name, kind, H, 8 * nk, 8 * nk, [&](int d, int k, int n) {
+    return harm ? m2l_entry(mi, tt, d, red[k / 8] * 8 + k % 8, red[n / 8] * 8 + n % 8) : m2l_entry(mi, tt, d, k, n);
+  });
+}
+
+bool tp_m2p_case(int kind, int p, int b, int mult_order, bool harm, bool& built) {
+  MultiIndex mi;
+  mi.init(p);
+  if (mult_order >= 0) mi.mo = mult_order;
+  M2pTable tab;
+  tab.build(mi, b);
+  TpHost H;
+  char name[64];
+  std::snprintf(name, sizeof name, "m2p p=%d mo=%d b=%d%s", p, mi.mo, b, harm ? " harmonic" : "");
+  built = build_tp_m2p(mi, tab, kind, H, harm);
+  if (!built) {
+    std::printf("%-28s %-6s span schedule (no prefix schedule)\n", name, kind == TC_BF16X3 ? "bf16x3" : "tf32");
+    return true;
+  }
+  const std::vector<int> red = harmonic_components(mi);
+  const int nk = harm ? (int)red.size() : mi.nc;
+  return tp_check(name, kind, H, 8 * b * b * b, 8 * nk, [&](int d, int k, int n) {
+    return harm ? m2p_entry(mi, tab, d, red[k / 8] * 8 + k % 8, n) : m2p_entry(mi, tab, d, k, n);
+  });
+}
+
+bool tp_near_case(int b, int comps, bool& built) {
+  TpHost H;
+  char name[64];
+  std::snprintf(name, sizeof name, "near b=%d columns=%d", b, comps);
+  built = build_tp_near(b, comps, TC_BF16X3, H);
+  if (!built) {
+    std::printf("%-28s %-6s span schedule (no prefix schedule)\n", name, "bf16x3");
+    return true;
+  }
+  return tp_check(name, TC_BF16X3, H, comps * b * b * b, b * b * b, [b](int d, int k, int n) {
+    const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+    return near_entry(b, D, k, n);
+  });
+}
+
+// Every configuration the span schedule covers; `built` counts the ones with
+// a prefix schedule.
+int prefix_check(int& built_count) {
+  bool ok = true, built = false;
+  built_count = 0;
+  for (int kind : {TC_BF16X3, TC_TF32})
+    for (int p : {2, 4, 6, 8})
+      for (bool harm : {false, true}) ok &= tp_m2l_case(kind, p, -1, -1, harm, built), built_count += built;
+  for (int p : {3, 4, 6})
+    for (bool harm : {false, true}) {
+      ok &= tp_m2l_case(TC_BF16X3, p, p - 1, -1, harm, built), built_count += built;
+      ok &= tp_m2l_case(TC_BF16X3, p, -1, p - 1, harm, built), built_count += built;
+      ok &= tp_m2p_case(TC_BF16X3, p, 2, p - 1, harm, built), built_count += built;
+    }
+  for (int kind : {TC_BF16X3, TC_TF32})
+    for (int p : {4, 6})
+      for (int b : {2, 4})
+        for (bool harm : {false, true}) ok &= tp_m2p_case(kind, p, b, -1, harm, built), built_count += built;
+  for (int b : {2, 4, 8})
+    for (int comps : {1, 4}) ok &= tp_near_case(b, comps, built), built_count += built;
+  return ok ? 0 : 1;
+}
+
+// The span schedule (build_tc) under the same truncating accumulation: one
+// FP32 add per MMA (K step and product) into its span's accumulator.
+double span_rz_error(const TcHost& H, int kind, int ncol, int klen, const std::function<double(int, int, int)>& entry,
+                     bool positive) {
+  const int chunk = kind == TC_BF16X3 ? 64 : 32, kstep = chunk / 4, esz = kind == TC_BF16X3 ? 2 : 4;
+  std::mt19937 rng(ncol * 7 + kind);
+  std::uniform_real_distribution<double> U(positive ? 0.0 : -1.0, 1.0);
+  std::vector<std::vector<float>> A(27, std::vector<float>(klen, 0.f));
+  for (auto& r : A)
+    for (float& a : r) a = (float)U(rng);
+  std::vector<double> ref(ncol, 0), sabs(ncol, 0);
+  for (int d = 0; d < 27; ++d)
+    for (int k = 0; k < klen; ++k)
+      for (int n = 0; n < ncol; ++n) {
+        const double t = A[d][k] * entry(d, k, n);
+        ref[n] += t;
+        sabs[n] += std::fabs(t);
+      }
+  std::vector<double> got(ncol, 0);
+  for (int ps = 0; ps < H.npass; ++ps) {
+    const TcPass& P = H.pass[ps];
+    std::vector<float> tz(512, 0.f);
+    for (int xz = 0; xz < 9; ++xz)
+      for (int j = 0; j < P.nchunks; ++j)
+        for (int dy = 0; dy < 3; ++dy) {
+          const int d = (xz % 3) + 3 * dy + 9 * (xz / 3);
+          for (int si = P.span_idx[j][0]; si < P.span_idx[j][kTcIssuers]; ++si) {
+            const TcSpan& S = P.span[si];
+            const unsigned char* tile = H.W.data() + P.w_base + (size_t)d * P.bytes_per_d + S.w_off;
+            for (int r = 0; r < S.n; ++r)
+              for (int ks = 0; ks < S.ksteps; ++ks) {
+                const int nprod = kind == TC_BF16X3 && S.prod == 0 ? 3 : 1;
+                for (int pr = 0; pr < nprod; ++pr) {
+                  double acc = 0;
+                  for (int e = ks * kstep; e < (ks + 1) * kstep; ++e) {
+                    const int k = j * chunk + e;
+                    const float a = k < klen ? A[d][k] : 0.f;
+                    const int byte = e * esz;
+                    const size_t off = (size_t)r * 128 + (size_t)((((byte >> 4) ^ (r & 7)) << 4) | (byte & 15));
+                    if (kind == TC_BF16X3) {
+                      const float ah = bf16_to_f(bf16_rn(a)), al = bf16_to_f(bf16_rn(a - ah));
+                      uint16_t w1, wl;
+                      std::memcpy(&w1, tile + off, 2);
+                      if (S.prod == 0) {
+                        std::memcpy(&wl, tile + (size_t)S.n * 128 + off, 2);
+                        acc += pr == 0 ? (double)ah * bf16_to_f(w1) : pr == 1 ? (double)ah * bf16_to_f(wl)
+                                                                             : (double)al * bf16_to_f(w1);
+                      } else {
+                        acc += (double)(S.prod == 3 ? al : ah) * bf16_to_f(w1);
+                      }
+                    } else {
+                      float w;
+                      std::memcpy(&w, tile + off, 4);
+                      acc += (double)tf32_trunc(a) * w;
+                    }
+                  }
+                  tz[S.tmem_col + r] = rz_add(tz[S.tmem_col + r], acc);
+                }
+              }
+          }
+        }
+    for (int g = 0; g < P.ng; ++g)
+      for (int c = 0; c < P.out_ncols[g]; ++c) {
+        double v = tz[P.out_tmem[g] + c];
+        if (P.out_tmem2[g] >= 0) v += tz[P.out_tmem2[g] + c];
+        if (P.out_tmem3[g] >= 0) v += tz[P.out_tmem3[g] + c];
+        if (P.out_tmem4[g] >= 0) v += tz[P.out_tmem4[g] + c];
+        got[P.out_col0[g] + c] = v;
+      }
+  }
+  double err = 0;
+  for (int n = 0; n < ncol; ++n)
+    if (sabs[n] > 0) err = std::max(err, std::fabs(got[n] - ref[n]) / sabs[n]);
+  return err;
+}
+
+// Accumulator rounding of the span and prefix schedules on same-signed
+// activations (order 6 harmonic M2L, the near field of leaf 4), for the record.
+int rounding_report() {
+  MultiIndex mi;
+  mi.init(6);
+  TaylorTable tt;
+  tt.build(mi);
+  const std::vector<int> red = harmonic_components(mi);
+  const int nk = (int)red.size();
+  auto entry = [&](int d, int k, int n) { return m2l_entry(mi, tt, d, red[k / 8] * 8 + k % 8, red[n / 8] * 8 + n % 8); };
+  TpHost H;
+  TpResult R;
+  if (!build_tp_m2l(mi, tt, TC_BF16X3, H, true)) return 1;
+  if (!tp_check("m2l p=6 harmonic, A >= 0", TC_BF16X3, H, 8 * nk, 8 * nk, entry, true, &R)) return 1;
+  TcHost Hs;
+  if (!build_tc(mi, tt, TC_BF16X3, Hs, true)) return 1;
+  std::printf("%-28s span schedule rz %.2e\n", "m2l p=6 harmonic, A >= 0",
+              span_rz_error(Hs, TC_BF16X3, 8 * nk, 8 * nk, entry, true));
+  TpHost Hn;
+  TpResult Rn;
+  if (!build_tp_near(4, 1, TC_BF16X3, Hn)) return 1;
+  if (!tp_check("near b=4, A >= 0", TC_BF16X3, Hn, 64, 64, [](int d, int k, int n) {
+        const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+        return near_entry(4, D, k, n);
+      }, true, &Rn))
+    return 1;
+  TcHost Hns;
+  if (!build_tc_near(4, 1, TC_BF16X3, Hns)) return 1;
+  std::printf("%-28s span schedule rz %.2e\n", "near b=4, A >= 0",
+              span_rz_error(Hns, TC_BF16X3, 64, 64, [](int d, int k, int n) {
+                const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+                return near_entry(4, D, k, n);
+              }, true));
+  return 0;
+}
+
+// Planted mistakes in a built prefix schedule (order 6, harmonic, bf16x3),
+// each of which the check must catch.  Returns the number that were not.
+int planted_prefix_mistakes() {
+  MultiIndex mi;
+  mi.init(6);
+  TaylorTable tt;
+  tt.build(mi);
+  const std::vector<int> red = harmonic_components(mi);
+  const int nk = (int)red.size();
+  auto entry = [&](int d, int k, int n) { return m2l_entry(mi, tt, d, red[k / 8] * 8 + k % 8, red[n / 8] * 8 + n % 8); };
+  int missed = 0;
+  auto plant = [&](const char* what, auto corrupt) {
+    TpHost H;
+    if (!build_tp_m2l(mi, tt, TC_BF16X3, H, true) || !corrupt(H)) {
+      std::printf("planted mistake could not be placed: %s\n", what);
+      ++missed;
+      return;
+    }
+    if (tp_check(what, TC_BF16X3, H, 8 * nk, 8 * nk, entry)) {
+      std::printf("planted mistake NOT caught: %s\n", what);
+      ++missed;
+    }
+  };
+  auto first_form = [](const TpPass& P, int form) {
+    for (int u = 0; u < P.piece_unit[P.npieces]; ++u)
+      if ((int)((P.unit[u] >> 9) & 3u) == form) return u;
+    return -1;
+  };
+  {  // the protocol replay must reject two owners taking turns on one ring slot
+    TpHost H;
+    if (!build_tp_m2l(mi, tt, TC_BF16X3, H, true)) {
+      ++missed;
+    } else {
+      int q0 = -1, q1 = -1;  // two owners with pieces: the second's ring moved onto the first's
+      for (int q = 0; q < kTpIssuers; ++q)
+        if (H.owner_nslots[q] > 0) (q0 < 0 ? q0 : q1) = q0 < 0 ? q : (q1 < 0 ? q : q1);
+      int bad = 0;
+      if (q0 >= 0 && q1 >= 0) {
+        H.owner_slot0[q1] = H.owner_slot0[q0];
+        H.owner_nslots[q1] = H.owner_nslots[q0];
+        for (unsigned seed = 1; seed <= 40; ++seed) bad += !simulate_protocol(H, TC_BF16X3, 3, seed).empty();
+      }
+      std::printf("two owners on one ring: %d of 40 replays fail the protocol check\n", bad);
+      if (bad == 0) {
+        std::printf("planted mistake NOT caught: two owners on one ring\n");
+        ++missed;
+      }
+    }
+  }
+  plant("zeroed weight block", [](TpHost& H) {  // the first block of the first column (dx = dz = -1)
+    const TpPass& P = H.pass[0];
+    std::fill_n(H.W.begin() + P.w_base, 4096, (unsigned char)0);
+    return true;
+  });
+  plant("block row read unswizzled", [](TpHost& H) {  // row 5: its 16-byte halves trade places
+    const TpPass& P = H.pass[0];
+    unsigned char* row = H.W.data() + P.w_base + 5 * 32;
+    std::swap_ranges(row, row + 16, row + 16);
+    return true;
+  });
+  plant("unit into the wrong accumulator columns", [&](TpHost& H) {
+    TpPass& P = H.pass[0];
+    const int u = first_form(P, 0);
+    if (u < 0) return false;
+    P.unit[u] += 1u << 11;  // TMEM column + 16
+    return true;
+  });
+  plant("unit on the wrong dy window", [](TpHost& H) {
+    TpPass& P = H.pass[0];
+    P.unit[0] = (P.unit[0] & ~(3u << 7)) | (((((P.unit[0] >> 7) & 3u) + 1) % 3) << 7);
+    return true;
+  });
+  plant("unit on the wrong K step of its chunk", [](TpHost& H) {
+    TpPass& P = H.pass[0];
+    P.unit[0] ^= 1u << 5;
+    return true;
+  });
+  plant("fused MMA one group off in E", [&](TpHost& H) {  // its reversed columns land one group late
+    TpPass& P = H.pass[0];
+    for (int u = 0; u < P.piece_unit[P.npieces]; ++u)
+      if (((P.unit[u] >> 9) & 3u) == 1 && ((P.unit[u] >> 16) & 31u) <= 2) {  // N <= 32: room to shift
+        P.unit[u] += 1u << 11;
+        return true;
+      }
+    return false;
+  });
+  plant("epilogue reads E unreversed", [](TpHost& H) {
+    TpPass& P = H.pass[0];
+    if (P.grp_e[0] < 0 || P.ngroups < 2 || P.grp_e[1] < 0) return false;
+    std::swap(P.grp_e[0], P.grp_e[1]);
+    return true;
+  });
+  plant("epilogue drops the L2 region", [](TpHost& H) {
+    TpPass& P = H.pass[0];
+    if (P.grp_l2[0] < 0) return false;
+    P.grp_l2[0] = -1;
+    return true;
+  });
+  plant("piece cut one unit early", [](TpHost& H) {
+    TpPass& P = H.pass[0];
+    if (P.npieces < 2 || P.piece_unit[1] - P.piece_unit[0] < 2) return false;
+    P.piece_unit[1] -= 1;
+    return true;
+  });
+  plant("piece read by a second issuer", [](TpHost& H) {  // its columns then have two writers
+    TpPass& P = H.pass[0];
+    for (int k = 1; k < P.npieces; ++k)
+      if (P.piece_owner[k] != P.piece_owner[0]) {
+        for (int k2 = 0; k2 < P.npieces; ++k2)  // a piece of the first piece's owner moves to another issuer
+          if (k2 != 0 && P.piece_owner[k2] == P.piece_owner[0]) {
+            P.piece_owner[k2] = P.piece_owner[k];
+            return true;
+          }
+      }
+    return false;
+  });
+  return missed;
+}
+
 // ---------------------------------------------------------------- tables --
 
 bool write_table(const std::string& path, const std::vector<double>& v) {
@@ -638,6 +1317,14 @@ int main(int argc, char** argv) {
   if (mode == "plant") return planted_mistakes() ? 1 : 0;
   if (mode == "harmonic") return harmonic_check() ? 1 : 0;
   if (mode == "cuda-core") return cc_tiles_check() ? 1 : 0;
+  if (mode == "prefix") {
+    int built = 0;
+    const int r = prefix_check(built);
+    std::printf("prefix schedules built: %d\n", built);
+    return r;
+  }
+  if (mode == "prefix-plant") return planted_prefix_mistakes() ? 1 : 0;
+  if (mode == "rounding") return rounding_report();
   if (mode == "tables") {
     if (argc < 3) return 2;
     const std::string dir = argv[2];

@@ -75,6 +75,26 @@ def test_planted_schedule_corruptions_are_caught(host_check):
     assert r.stdout.count("FAILED") == 6
 
 
+def test_prefix_schedules(host_check):
+    """Every prefix-schedule contraction (M2L p = 2..7 and harmonic p = 8
+    cases, final-stage M2P, near field): resources, owner rings, one writer
+    per accumulator column, the emulated MMAs against the direct contraction,
+    and randomised replays of the barrier protocol (no deadlock, exact parity
+    waits)."""
+    r = _run(host_check, "prefix")
+    assert r.returncode == 0, r.stdout + r.stderr
+    built = [ln for ln in r.stdout.splitlines() if "passes" in ln]
+    assert len(built) >= 40 and all("uncovered 0" in ln for ln in built)
+    assert "prefix schedules built: %d" % len(built) in r.stdout
+
+
+def test_planted_prefix_mistakes_are_caught(host_check):
+    r = _run(host_check, "prefix-plant")
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.count("FAILED") == 10
+    assert "two owners on one ring: 40 of 40" in r.stdout
+
+
 def test_harmonic_compression_is_exact(host_check):
     r = _run(host_check, "harmonic")
     assert r.returncode == 0, r.stdout + r.stderr
