@@ -204,17 +204,23 @@ fmm_status fmm_solve_host(fmm_plan_t plan, const void* rho_host, void* phi_host,
  * compiled into this library.  Every device on which the library is loaded
  * holds that array until the process exits.  A solve fits when its tables
  * plus its arena fit the array: at leaf 4 that is up to 64^3 cells for
- * orders <= 6 (larger grids or orders return FMM_ERR_ARG with the byte count
- * in fmm_last_error(), before any device work).
+ * orders <= 6.  Orders above 6 and grid extents above 4096 return
+ * FMM_ERR_ARG before any device work; a grid whose tables and arena do not
+ * fit returns FMM_ERR_ARG (the byte count in fmm_last_error()) while the
+ * array is being laid out, after some of its clearing and table copies may
+ * already be queued on `stream` -- the array's tables are then marked stale
+ * and rebuilt by the next call, but a call still running on another stream
+ * would read them being overwritten (see the note on overlapping calls).
  *
  *   grid, order, leaf : as fmm_plan (order <= 6).
  *   rho, phi, accel   : device float arrays as fmm_solve (accel may be NULL),
  *                       16-byte aligned, owned by the caller.
  *   stream            : cudaStream_t for every copy and kernel of the call.
  *
- * Set-up: the first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  The call keeps the array's tables from the
+ * Set-up: every call looks up the array's device address
+ * (cudaGetSymbolAddress, with the device current; no allocation) and
+ * rebuilds the tables when the address changed (after a device reset); make
+ * the first call on a device before any stream capture.  The call keeps the array's tables from the
  * previous call when order, leaf and grid are unchanged (otherwise it
  * rebuilds them on the host and copies them in), and clears every part of
  * the array that must start at zero.  All calls share one array: calls whose
@@ -256,6 +262,30 @@ fmm_status fmm_solve_static(const fmm_grid* grid, int order, int leaf, const voi
  * The paper has no counterpart (its M2L runs on CPU cores).
  */
 fmm_status fmm_plan_autotune(fmm_plan_t plan, void* stream);
+
+/*
+ * Tensor-core schedules.  Each tensor-core contraction -- `what` 0: the M2L
+ * of the tensor-core levels (Sec. 2.3, eq. M2L), 1: the near field (Sec. 2.3,
+ * the direct cell-cell part), 2: the final-stage M2P (Sec. 4) -- has up to two
+ * schedules with the same arithmetic: the span schedule (k_m2l_tc.cu: column
+ * groups of one order range, one MMA per group and K step) and the prefix
+ * schedule (k_nbr_tc.cu: all columns of a pass in one accumulator set, one
+ * wide MMA per K step over the prefix of columns it feeds).  Where both
+ * exist, a plan starts with the one measured faster on GB300 at 512^3 (M2L
+ * and M2P: prefix; near field: span) and fmm_plan_autotune times both.
+ *   fmm_plan_tc_schedule     : *available = bit 0 span, bit 1 prefix;
+ *                              *prefix = 1 prefix, 0 span, -1 neither (the
+ *                              contraction is not on the tensor cores).
+ *                              Either pointer may be NULL.
+ *   fmm_plan_set_tc_schedule : selects one; FMM_ERR_ARG if that schedule does
+ *                              not exist for the contraction (or, for the M2L
+ *                              of a plan with mult_order < order, for its
+ *                              transposed form).
+ * Both schedules give the same sums up to the order of the FP32 additions.
+ * The paper has no counterpart.
+ */
+fmm_status fmm_plan_tc_schedule(fmm_plan_t plan, int what, int* prefix, int* available);
+fmm_status fmm_plan_set_tc_schedule(fmm_plan_t plan, int what, int prefix);
 fmm_status fmm_plan_tuning(fmm_plan_t plan, int level, int* shape, int* dsplit);
 fmm_status fmm_plan_set_tuning(fmm_plan_t plan, int level, int shape, int dsplit);
 

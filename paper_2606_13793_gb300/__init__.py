@@ -51,6 +51,8 @@ EXPORTS = [
     "fmm_plan_autotune",
     "fmm_plan_tuning",
     "fmm_plan_set_tuning",
+    "fmm_plan_tc_schedule",
+    "fmm_plan_set_tc_schedule",
     "fmm_batch_solve",
     "fmm_batch_destroy",
     "fmm_batch_launches",
@@ -120,6 +122,10 @@ def load(path: str | None = None):
         lib.fmm_plan_tuning.restype = i
         lib.fmm_plan_set_tuning.argtypes = [vp, i, i, i]
         lib.fmm_plan_set_tuning.restype = i
+        lib.fmm_plan_tc_schedule.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+        lib.fmm_plan_tc_schedule.restype = i
+        lib.fmm_plan_set_tc_schedule.argtypes = [vp, i, i]
+        lib.fmm_plan_set_tc_schedule.restype = i
         lib.fmm_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
         lib.fmm_batch_create.restype = i
         lib.fmm_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
@@ -308,7 +314,8 @@ class FMMPlan:
         return int(self.lib.fmm_workspace_bytes(self._h))
 
     def autotune(self, stream=None):
-        """Time the CUDA-core contraction variants and keep the fastest."""
+        """Time the CUDA-core contraction variants and the two tensor-core
+        schedules of each tensor-core contraction; keep the fastest."""
         _check(self.lib, self.lib.fmm_plan_autotune(self._h, _stream_handle(stream)))
 
     def tuning(self, level: int):
@@ -319,6 +326,23 @@ class FMMPlan:
 
     def set_tuning(self, level: int, shape: int, dsplit: int):
         _check(self.lib, self.lib.fmm_plan_set_tuning(self._h, int(level), int(shape), int(dsplit)))
+
+    TC_SCHEDULE = {"m2l": 0, "near": 1, "m2p": 2}
+
+    def tc_schedule(self, what: str):
+        """("prefix" | "span" | None, set of available schedules) of the
+        tensor-core contraction `what` ("m2l", "near" or "m2p")."""
+        pre, avail = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib, self.lib.fmm_plan_tc_schedule(self._h, self.TC_SCHEDULE[what], ctypes.byref(pre),
+                                                        ctypes.byref(avail)))
+        names = {n for bit, n in ((1, "span"), (2, "prefix")) if avail.value & bit}
+        return ({1: "prefix", 0: "span"}.get(pre.value), names)
+
+    def set_tc_schedule(self, what: str, schedule: str):
+        if schedule not in ("prefix", "span"):
+            raise ValueError("schedule is 'prefix' or 'span'")
+        _check(self.lib, self.lib.fmm_plan_set_tc_schedule(self._h, self.TC_SCHEDULE[what],
+                                                            1 if schedule == "prefix" else 0))
 
     def launches(self, accel: bool = True) -> int:
         return int(self.lib.fmm_solve_launches(self._h, 1 if accel else 0))
@@ -404,12 +428,25 @@ def solve_static(rho, order: int = 6, leaf: int = 4, dx: float = 1.0, G: float =
         raise TypeError("rho must be a 3-D float32 CUDA tensor [nz][ny][nx]")
     if not rho.is_contiguous():
         raise ValueError("rho must be contiguous")
+    if rho.device.index is not None and rho.device.index != torch.cuda.current_device():
+        raise ValueError("rho is on %s but the current device is cuda:%d: the library works on the current device"
+                         % (rho.device, torch.cuda.current_device()))
     nz, ny, nx = rho.shape
-    phi = phi_out if phi_out is not None else torch.empty_like(rho)
+
+    def _out(t, name, shape):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or t.device != rho.device:
+            raise TypeError("%s must be a float32 tensor on %s" % (name, rho.device))
+        if tuple(t.shape) != shape:
+            raise ValueError("%s must have shape %s, not %s" % (name, shape, tuple(t.shape)))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        return t
+
+    phi = _out(phi_out, "phi_out", (nz, ny, nx)) if phi_out is not None else torch.empty_like(rho)
     acc = None
     if accel:
-        acc = accel_out if accel_out is not None else torch.empty((3, nz, ny, nx), dtype=torch.float32,
-                                                                  device=rho.device)
+        acc = (_out(accel_out, "accel_out", (3, nz, ny, nx)) if accel_out is not None else
+               torch.empty((3, nz, ny, nx), dtype=torch.float32, device=rho.device))
     grid = _Grid(nx, ny, nz, float(dx), float(G))
     _check(lib, lib.fmm_solve_static(ctypes.byref(grid), int(order), int(leaf), ctypes.c_void_p(rho.data_ptr()),
                                      ctypes.c_void_p(phi.data_ptr()),

@@ -229,8 +229,12 @@ struct fmm_plan_s {
   TcLaunch tcm{};
   // prefix-schedule forms (k_nbr_tc.cu) of the M2L (and its transpose), the
   // final-stage M2P and the near field; the span forms above run where a
-  // prefix schedule does not apply
+  // prefix schedule does not apply.  Where both exist, use_tp[] picks one
+  // (TcSched: M2L, near field, M2P): defaults from measurement, then
+  // fmm_plan_autotune times both.
   bool tp_m2l = false, tp_m2l_t = false, tp_m2p = false, tp_near = false;
+  bool span_m2l = false, span_m2l_t = false, span_near = false, span_m2p = false;
+  bool use_tp[3] = {true, false, true};
   TpLaunch tpl{}, tpl_t{}, tpm{}, tpn{};
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // timing
@@ -1705,7 +1709,9 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
         }
       }
       TcHost H;
-      if (!(P->tp_m2l && (!P->asym || P->tp_m2l_t)) && !build_tc(P->mi, tt, P->tc_kind, H, P->harm))
+      P->span_m2l = build_tc(P->mi, tt, P->tc_kind, H, P->harm);
+      if (!P->span_m2l) H = TcHost{};
+      if (!P->span_m2l && !(P->tp_m2l && (!P->asym || P->tp_m2l_t)))
         return cleanup(fail(FMM_ERR_UNSUPPORTED, "order too high for the tensor-core schedule"));
       unsigned char* dw = nullptr;
       if (!H.W.empty() && (st = P->upload(H.W, &dw, s))) return cleanup(st);
@@ -1721,10 +1727,13 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
         for (size_t r = 0; r < red.size(); ++r) P->tc.col_map[r] = (int16_t)red[r];
       }
       P->tc.err = nullptr;  // set below, after the flag exists
-      if (P->asym && !P->tp_m2l_t) {
-        TcHost Ht;
-        if (!build_tc(mt, tt, P->tc_kind, Ht, P->harm))
+      TcHost Ht;
+      if (P->asym) {
+        P->span_m2l_t = build_tc(mt, tt, P->tc_kind, Ht, P->harm);
+        if (!P->span_m2l_t && !P->tp_m2l_t)
           return cleanup(fail(FMM_ERR_UNSUPPORTED, "order too high for the transposed tensor-core schedule"));
+      }
+      if (P->asym && P->span_m2l_t) {
         unsigned char* dwt = nullptr;
         if ((st = P->upload(Ht.W, &dwt, s))) return cleanup(st);
         P->tc_t = P->tc;  // same maps, columns and kind; its own passes and weights
@@ -1794,7 +1803,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
         P->tp_m2p = P->m2p_tc = true;
       }
     }
-    if (lf.tc && !P->tp_m2p) {
+    if (lf.tc) {
       TcHost H;
       if (build_tc_m2p(P->mi, tab, P->tc_kind, H, P->harm)) {
         unsigned char* dw = nullptr;
@@ -1809,7 +1818,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
         T.accumulate = 0;
         for (int q = 0; q < 3; ++q) T.grid[q] = lf.np[q];
         T.C = reinterpret_cast<float*>(P->arena + P->m2p_off);
-        P->m2p_tc = true;
+        P->m2p_tc = P->span_m2p = true;
       }
     }
     if (!P->m2p_tc) {
@@ -1881,28 +1890,30 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
       P->tp_near = true;
     }
   }
-  if (P->near_tc && !P->tp_near) {
+  if (P->near_tc) {
     TcHost H;
     // bf16x3 in both tensor-core precisions: a TF32 near field would carry
     // ~3e-4 relative error on its (same-signed) sums
-    if (!build_tc_near(P->b, P->near_comps, TC_BF16X3, H))
-      return cleanup(fail(FMM_ERR_UNSUPPORTED, "near-field schedule failed"));
-    unsigned char* dw = nullptr;
-    if ((st = P->upload(H.W, &dw, s))) return cleanup(st);
-    // every launch writes its own columns of the same rows
-    P->tcn.assign((H.npass + kTcMaxPasses - 1) / kTcMaxPasses, TcLaunch{});
-    for (size_t li = 0; li < P->tcn.size(); ++li) {
-      TcLaunch& T = P->tcn[li];
-      T.W = dw;
-      T.npass = std::min(kTcMaxPasses, H.npass - (int)li * kTcMaxPasses);
-      T.a_stages = H.a_stages;
-      for (int i = 0; i < T.npass; ++i) T.pass[i] = H.pass[li * kTcMaxPasses + i];
-      T.n_cols = P->b * P->b * P->b * P->near_comps;
-      T.kind = TC_BF16X3;
-      T.accumulate = 0;
-      for (int q = 0; q < 3; ++q) T.grid[q] = P->lev[P->L].n[q];
-      T.C = reinterpret_cast<float*>(P->arena + P->near_off);
-      T.err = P->d_flag;
+    P->span_near = build_tc_near(P->b, P->near_comps, TC_BF16X3, H);
+    if (!P->span_near && !P->tp_near) return cleanup(fail(FMM_ERR_UNSUPPORTED, "near-field schedule failed"));
+    if (P->span_near) {
+      unsigned char* dw = nullptr;
+      if ((st = P->upload(H.W, &dw, s))) return cleanup(st);
+      // every launch writes its own columns of the same rows
+      P->tcn.assign((H.npass + kTcMaxPasses - 1) / kTcMaxPasses, TcLaunch{});
+      for (size_t li = 0; li < P->tcn.size(); ++li) {
+        TcLaunch& T = P->tcn[li];
+        T.W = dw;
+        T.npass = std::min(kTcMaxPasses, H.npass - (int)li * kTcMaxPasses);
+        T.a_stages = H.a_stages;
+        for (int i = 0; i < T.npass; ++i) T.pass[i] = H.pass[li * kTcMaxPasses + i];
+        T.n_cols = P->b * P->b * P->b * P->near_comps;
+        T.kind = TC_BF16X3;
+        T.accumulate = 0;
+        for (int q = 0; q < 3; ++q) T.grid[q] = P->lev[P->L].n[q];
+        T.C = reinterpret_cast<float*>(P->arena + P->near_off);
+        T.err = P->d_flag;
+      }
     }
   }
   if (P->near_tc) {
@@ -2131,11 +2142,22 @@ NbrGemm near_gemm(fmm_plan_t P) {
   return g;
 }
 
+// Which tensor-core schedule a contraction runs: the prefix form when it is
+// the only one, or when both exist and it is selected.
+enum TcSched { TS_M2L = 0, TS_NEAR = 1, TS_M2P = 2 };
+bool tc_prefix(fmm_plan_t P, int what) {
+  const bool tp = what == TS_M2L ? ((P->transposed && P->asym) ? P->tp_m2l_t : P->tp_m2l)
+                                 : what == TS_NEAR ? P->tp_near : P->tp_m2p;
+  const bool span = what == TS_M2L ? ((P->transposed && P->asym) ? P->span_m2l_t : P->span_m2l)
+                                   : what == TS_NEAR ? P->span_near : P->span_m2p;
+  return tp && (P->use_tp[what] || !span);
+}
+
 // Final-stage M2P of the leaf level (tensor cores when the leaf level is on
 // them and the schedule fits, else the CUDA-core contraction).
 fmm_status do_m2p(fmm_plan_t P, cudaStream_t s) {
   const Level& lf = P->lev[P->L];
-  if (P->tp_m2p) {
+  if (tc_prefix(P, TS_M2P)) {
     CUDA_TRY(launch_nbr_tc(P->tpm, P->map_hi[P->L], P->map_lo[P->L], s));
     return FMM_OK;
   }
@@ -2185,7 +2207,7 @@ fmm_status do_p2l(fmm_plan_t P, cudaStream_t s) {
 
 fmm_status do_m2l(fmm_plan_t P, int l, cudaStream_t s) {
   const Level& lv = P->lev[l];
-  if (lv.tc && ((P->transposed && P->asym) ? P->tp_m2l_t : P->tp_m2l)) {
+  if (lv.tc && tc_prefix(P, TS_M2L)) {
     TpLaunch& L = (P->transposed && P->asym) ? P->tpl_t : P->tpl;
     L.C = static_cast<float*>(P->Lx(l));
     for (int q = 0; q < 3; ++q) L.grid[q] = lv.np[q];
@@ -2277,7 +2299,7 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
   // near field over the 27 neighbour leaf boxes
   if (P->near_tc) {
     StageTimer t(P, ST_NEAR_TC, s);
-    if (P->tp_near)
+    if (tc_prefix(P, TS_NEAR))
       CUDA_TRY(launch_nbr_tc(P->tpn, P->map_near_hi, P->map_near_lo, s));
     else
       for (const TcLaunch& NL : P->tcn) CUDA_TRY(launch_m2l_tc(NL, P->map_near_hi, P->map_near_lo, s));
@@ -2439,7 +2461,7 @@ int fmm_solve_launches(fmm_plan_t P, int with_accel) {
     if (l == 2 && L == 2 && P->m2p) n += 1;          // zero leaf locals (final-stage M2P, no parent far field)
     if (!P->lev[l].tc && P->m2l_choice[l].dsplit > 1 && !(l == L && P->m2p)) n += 1;  // partial-sum reduction
   }
-  n += P->near_tc ? (P->tp_near ? 1 : (int)P->tcn.size()) + 1 : 2;  // near field + leaf finish
+  n += P->near_tc ? (tc_prefix(P, TS_NEAR) ? 1 : (int)P->tcn.size()) + 1 : 2;  // near field + leaf finish
   if (!P->near_tc && P->near_choice.dsplit > 1) n += 1;
   if (with_accel && P->near_comps == 1) n += 1;  // FD stencil (the analytic force comes with the leaf kernel)
   return n;
@@ -2533,8 +2555,10 @@ constexpr int kStaticMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_static_workspace[kStaticWorkspaceBytes];
 
-// Per device: the array's device address (looked up once, with the device
-// current) and the (order, leaf, nx, ny, nz) whose tables the array holds.
+// Per device: the array's device address (looked up on every call, with the
+// device current: a device reset gives the array a new address, whose
+// contents are then not the tables of the last call) and the (order, leaf,
+// nx, ny, nz) whose tables the array holds.
 struct StaticSlot {
   unsigned char* ptr = nullptr;
   int key[5] = {-1, -1, -1, -1, -1};
@@ -2569,12 +2593,15 @@ extern "C" fmm_status fmm_solve_static(const fmm_grid* grid, int order, int leaf
 
   std::lock_guard<std::mutex> lock(g_static_mutex);
   StaticSlot& slot = g_static_slots[dev];
-  if (!slot.ptr) {
+  {
     void* addr = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&addr, g_static_workspace);
     if (e != cudaSuccess || !addr)
       return fail(FMM_ERR_CUDA, "cudaGetSymbolAddress of the static workspace failed: %s", cudaGetErrorString(e));
-    slot.ptr = static_cast<unsigned char*>(addr);
+    if (static_cast<unsigned char*>(addr) != slot.ptr) {  // first call, or a new context: no tables held
+      slot.ptr = static_cast<unsigned char*>(addr);
+      for (int& k : slot.key) k = -1;
+    }
   }
   std::unique_ptr<fmm_plan_s> P(new (std::nothrow) fmm_plan_s());
   if (!P) return fail(FMM_ERR_ALLOC, "host allocation failed");
@@ -2744,6 +2771,7 @@ namespace {
 using SimtChoice = fmm_plan_s::SimtChoice;
 std::mutex g_tune_mu;
 std::map<std::string, SimtChoice> g_tune_cache;
+std::map<std::string, bool> g_tc_tune_cache;  // tensor-core schedule: prefix (true) or span
 
 bool choice_valid(fmm_plan_t P, NbrGemm g, const std::vector<int>& tk, size_t es, SimtChoice c) {
   // FP64 levels of a tensor-core plan keep the small-footprint tile that can
@@ -2809,6 +2837,67 @@ fmm_status tune_one(fmm_plan_t P, NbrGemm g, const std::vector<int>& tk, const c
   return FMM_OK;
 }
 
+// Times the two tensor-core schedules of a contraction (3 launches after a
+// warm-up each) and keeps the faster; cached per process like tune_one.
+fmm_status tune_tc(fmm_plan_t P, int what, cudaStream_t s) {
+  const bool tp = what == TS_M2L ? P->tp_m2l : what == TS_NEAR ? P->tp_near : P->tp_m2p;
+  const bool span = what == TS_M2L ? P->span_m2l : what == TS_NEAR ? P->span_near : P->span_m2p;
+  if (!tp || !span) return FMM_OK;
+  int level = P->L;  // M2L: the finest tensor-core level (the M2P's level excluded)
+  if (what == TS_M2L) {
+    level = -1;
+    for (int l = 2; l <= P->L; ++l)
+      if (P->lev[l].tc && !(l == P->L && P->m2p)) level = l;
+    if (level < 0) return FMM_OK;
+  }
+  const int* g = what == TS_NEAR ? P->lev[P->L].n : P->lev[level].np;
+  char key[160];
+  std::snprintf(key, sizeof key, "tc%d/%d,%d,%d/%d/%d/%d/%d/%d", what, g[0], g[1], g[2], P->p, P->b, P->tc_kind,
+                P->harm ? 1 : 0, P->near_comps);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tc_tune_cache.find(key);
+    if (it != g_tc_tune_cache.end()) {
+      P->use_tp[what] = it->second;
+      return FMM_OK;
+    }
+  }
+  auto launch = [&]() -> fmm_status {
+    if (what == TS_M2L) return do_m2l(P, level, s);
+    if (what == TS_M2P) return do_m2p(P, s);
+    if (tc_prefix(P, TS_NEAR)) {
+      CUDA_TRY(launch_nbr_tc(P->tpn, P->map_near_hi, P->map_near_lo, s));
+    } else {
+      for (const TcLaunch& NL : P->tcn) CUDA_TRY(launch_m2l_tc(NL, P->map_near_hi, P->map_near_lo, s));
+    }
+    return FMM_OK;
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(FMM_ERR_CUDA, "event creation failed");
+  }
+  float ms[2] = {0.f, 0.f};
+  fmm_status st = FMM_OK;
+  for (int prefix = 0; prefix < 2 && st == FMM_OK; ++prefix) {
+    P->use_tp[what] = prefix != 0;
+    if ((st = launch())) break;  // warm-up
+    if (cudaEventRecord(e0, s) != cudaSuccess) st = fail(FMM_ERR_CUDA, "event record failed");
+    for (int r = 0; r < 3 && st == FMM_OK; ++r) st = launch();
+    if (st == FMM_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms[prefix], e0, e1) != cudaSuccess))
+      st = fail(FMM_ERR_CUDA, "tensor-core schedule timing failed");
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != FMM_OK) return st;
+  P->use_tp[what] = ms[1] < ms[0];
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tc_tune_cache[key] = P->use_tp[what];
+  return FMM_OK;
+}
+
 }  // namespace
 
 extern "C" fmm_status fmm_plan_autotune(fmm_plan_t P, void* stream) {
@@ -2830,7 +2919,32 @@ extern "C" fmm_status fmm_plan_autotune(fmm_plan_t P, void* stream) {
                        : tune_one<float>(P, g, P->h_near_tile_k, "near", 3, s, &P->near_choice);
     if (st) return st;
   }
+  for (int what = 0; what < 3; ++what)
+    if ((st = tune_tc(P, what, s))) return st;
   CUDA_TRY(cudaStreamSynchronize(s));
+  return FMM_OK;
+}
+
+extern "C" fmm_status fmm_plan_tc_schedule(fmm_plan_t P, int what, int* prefix, int* available) {
+  g_last_error.clear();
+  if (!P || what < 0 || what > 2) return fail(FMM_ERR_ARG, "plan is NULL or `what` is not 0, 1 or 2");
+  const bool tp = what == TS_M2L ? P->tp_m2l : what == TS_NEAR ? P->tp_near : P->tp_m2p;
+  const bool span = what == TS_M2L ? P->span_m2l : what == TS_NEAR ? P->span_near : P->span_m2p;
+  if (available) *available = (span ? 1 : 0) | (tp ? 2 : 0);
+  if (prefix) *prefix = (tp || span) ? (tc_prefix(P, what) ? 1 : 0) : -1;
+  return FMM_OK;
+}
+
+extern "C" fmm_status fmm_plan_set_tc_schedule(fmm_plan_t P, int what, int prefix) {
+  g_last_error.clear();
+  if (!P || what < 0 || what > 2) return fail(FMM_ERR_ARG, "plan is NULL or `what` is not 0, 1 or 2");
+  const bool tp = what == TS_M2L ? P->tp_m2l : what == TS_NEAR ? P->tp_near : P->tp_m2p;
+  const bool span = what == TS_M2L ? P->span_m2l : what == TS_NEAR ? P->span_near : P->span_m2p;
+  if (prefix ? !tp : !span) return fail(FMM_ERR_ARG, "the %s schedule of that contraction does not exist in this plan",
+                                        prefix ? "prefix" : "span");
+  if (what == TS_M2L && P->asym && !(prefix ? P->tp_m2l_t : P->span_m2l_t))
+    return fail(FMM_ERR_ARG, "the transposed M2L has no %s schedule", prefix ? "prefix" : "span");
+  P->use_tp[what] = prefix != 0;
   return FMM_OK;
 }
 

@@ -189,3 +189,75 @@ def test_tc_harmonic_final_stage_m2p(orc):
     c = _solve_opts(rho, 4, 6, "bf16x3", final_stage="m2p", harmonic=False)
     print(f"m2p harmonic {rel_l2(h, ref):.2e} cartesian {rel_l2(c, ref):.2e}")
     assert rel_l2(h, ref) <= TOL["bf16x3"] and rel_l2(c, ref) <= TOL["bf16x3"]
+
+
+def _solve_with(rho32, p, prec, schedules, final_stage="m2l"):
+    """Solves with every tensor-core contraction on the given schedule
+    ("prefix" / "span") where that schedule exists; returns phi, acc and the
+    schedules that ran."""
+    nz, ny, nx = rho32.shape
+    plan = fmm.FMMPlan((nx, ny, nz), p, 4, prec, final_stage=final_stage)
+    ran = {}
+    for what in ("m2l", "near", "m2p"):
+        cur, avail = plan.tc_schedule(what)
+        if cur is None:
+            continue
+        want = schedules.get(what, cur)
+        if want in avail:
+            plan.set_tc_schedule(what, want)
+        ran[what] = plan.tc_schedule(what)[0]
+    rho = torch.from_numpy(np.ascontiguousarray(rho32)).cuda()
+    phi, acc = plan.solve(rho, accel=True)
+    phi2, _ = plan.solve(rho, accel=True)
+    torch.cuda.synchronize()
+    plan.check()
+    assert torch.equal(phi, phi2), "a schedule gave two different answers"
+    out = phi.double().cpu().numpy(), acc.double().cpu().numpy()
+    plan.close()
+    return out[0], out[1], ran
+
+
+@pytest.mark.parametrize("case", [("bf16x3", 6, "m2l"), ("bf16x3", 8, "m2l"), ("tf32", 6, "m2l"),
+                                  ("bf16x3", 6, "m2p"), ("bf16x3", 4, "m2l")])
+def test_tc_both_schedules_match_oracle(orc, case):
+    """Span and prefix schedules of the M2L, the near field and the
+    final-stage M2P each reach the oracle within the precision's bound, give
+    the same result twice, and agree with each other to FP32 summation-order
+    differences."""
+    prec, p, final_stage = case
+    rho = inputs.lognormal(64, seed=77 + p).astype(np.float64)
+    if final_stage == "m2l":
+        ref = orc.fmm(rho, 4, p, accel=True)
+        ref_phi = ref["phi"]
+    else:
+        ref_phi = orc.fmm_m2p(rho, 4, p)
+    res = {}
+    for sched in ("span", "prefix"):
+        phi, acc, ran = _solve_with(rho.astype(np.float32), p, prec, {w: sched for w in ("m2l", "near", "m2p")},
+                                    final_stage)
+        err = rel_l2(phi, ref_phi)
+        print(f"{prec} p={p} {final_stage} {sched}: ran {ran}, phi rel err {err:.3e}")
+        assert err <= TOL[prec]
+        if final_stage == "m2l":
+            assert rel_l2(acc, ref["accel"]) <= acc_tol(64, prec)
+        res[sched] = (phi, ran)
+    if res["span"][1] != res["prefix"][1]:  # both forms ran somewhere: they agree closely
+        assert rel_l2(res["span"][0], res["prefix"][0]) <= (2e-6 if prec == "bf16x3" else 2e-4)
+
+
+def test_tc_schedule_selection_api():
+    plan = fmm.FMMPlan((64, 64, 64), 6, 4, "bf16x3")
+    cur, avail = plan.tc_schedule("near")
+    assert cur == "span" and avail == {"span", "prefix"}
+    cur, avail = plan.tc_schedule("m2l")
+    assert cur == "prefix" and "prefix" in avail
+    assert plan.tc_schedule("m2p")[0] is None  # final stage is M2L here
+    plan.set_tc_schedule("near", "prefix")
+    assert plan.tc_schedule("near")[0] == "prefix"
+    with pytest.raises(fmm.FMMError):
+        plan.set_tc_schedule("m2p", "span")
+    plan.close()
+    plan8 = fmm.FMMPlan((64, 64, 64), 8, 4, "bf16x3")  # Cartesian p = 8 M2L: the span schedule only
+    cur, avail = plan8.tc_schedule("m2l")
+    assert cur in avail
+    plan8.close()

@@ -7,8 +7,11 @@ static device array as its workspace.
 Checked through the C ABI against the planned FP32 solve (fmm_solve), on two
 calls in a row -- the second reuses the tables the first left in the static
 array -- within the FP32 tolerance of the parity tests (1e-5 relative L2 on
-phi, 1e-4 on accel).  This file is collected last on purpose, and it passes
-alone in a fresh process as well as after the other tests.
+phi, 1e-4 on accel), and against the FP64 oracle; free device memory is
+unchanged across repeated calls (same and changed shapes); output tensors of
+the wrong shape, type, layout or device are rejected before the call.  This
+file is collected last on purpose, and it passes alone in a fresh process as
+well as after the other tests.
 """
 import numpy as np
 import pytest
@@ -28,7 +31,7 @@ def built():
 
 
 def rel_l2(a, b):
-    a, b = a.double(), b.double()
+    a, b = a.double().cpu(), b.double().cpu()
     return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
 
 
@@ -73,3 +76,46 @@ def test_static_solve_rejects_too_large():
     assert e.value.status == 1 and "static" in str(e.value)
     with pytest.raises(fmm.FMMError):
         fmm.solve_static(torch.zeros(32, 32, 32, device="cuda"), 7, 4)
+
+
+def test_static_solve_matches_oracle(orc):
+    n, order, leaf = 32, 6, 4
+    rho = inputs.lognormal(n, seed=41)
+    ref = orc.fmm(rho.astype(np.float64), leaf, order, accel=True)
+    phi, acc = fmm.solve_static(torch.from_numpy(rho).cuda(), order, leaf, accel=True)
+    torch.cuda.synchronize()
+    assert rel_l2(phi, torch.from_numpy(ref["phi"])) <= 1e-5
+    assert rel_l2(acc, torch.from_numpy(ref["accel"])) <= 1e-4
+
+
+def test_static_solve_allocates_no_device_memory():
+    """Free device memory (cudaMemGetInfo: every allocator of the process,
+    not only torch's) stays the same over repeated calls with caller-owned
+    outputs, for an unchanged shape and for changed shapes."""
+    shapes = [(32, 32, 32), (32, 32, 32), (24, 40, 32), (32, 32, 32)]
+    bufs = []
+    for nz, ny, nx in shapes:
+        rho = torch.from_numpy(inputs.plummer((nx, ny, nz), seed=9)).cuda()
+        bufs.append((rho, torch.empty_like(rho), torch.empty((3, nz, ny, nx), device="cuda")))
+    fmm.solve_static(bufs[0][0], 4, 4, accel=True, phi_out=bufs[0][1], accel_out=bufs[0][2])  # warm-up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        for rho, phi, acc in bufs:
+            fmm.solve_static(rho, 4, 4, accel=True, phi_out=phi, accel_out=acc)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
+def test_static_solve_rejects_bad_outputs():
+    rho = torch.zeros(32, 32, 32, device="cuda")
+    with pytest.raises(ValueError):
+        fmm.solve_static(rho, 4, 4, phi_out=torch.empty(32, 32, 16, device="cuda"))
+    with pytest.raises(ValueError):
+        fmm.solve_static(rho, 4, 4, accel=True, accel_out=torch.empty(3, 32, 32, 31, device="cuda"))
+    with pytest.raises(TypeError):
+        fmm.solve_static(rho, 4, 4, phi_out=torch.empty(32, 32, 32, device="cuda", dtype=torch.float64))
+    with pytest.raises(TypeError):
+        fmm.solve_static(rho, 4, 4, phi_out=torch.empty(32, 32, 32))  # host memory
+    with pytest.raises(ValueError):
+        fmm.solve_static(rho, 4, 4, phi_out=torch.empty(32, 32, 64, device="cuda")[:, :, ::2])
