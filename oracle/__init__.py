@@ -25,6 +25,12 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
 * ``fmm_sample``   pinned: equals ``fmm`` at the sampled cells.
 * ``adjoint``      pinned: <u, A v> = <A^T u, v> against ``fmm``.
 * ``fd_accel``     pinned: exact on polynomials of the stencils' degree.
+* ``m2p_eval``     pinned: its gradient equals the central difference of its
+                   potential (an analytic derivative of the same truncated sum).
+* ``fmm_accel`` (final_stage "m2p")  pinned: converges to ``direct_accel`` in
+                   p; the point-mass closed form; equals the pair-force sum
+                   when every box is near; agrees with the stencil gradient of
+                   ``fmm_m2p``'s potential in the interior.
 """
 from __future__ import annotations
 
@@ -92,6 +98,8 @@ def _bind(lib):
         "oracle_fmm_sample_accel": (I, [DP, I, I, I, I, I, D, D, L, LP, DP, I]),
         "oracle_fmm_m2p": (I, [DP, I, I, I, I, I, D, D, DP, I]),
         "oracle_fmm_orders": (I, [DP, I, I, I, I, I, I, I, I, D, D, DP, I]),
+        "oracle_m2p_eval": (I, [DP, I, DP, DP, DP]),
+        "oracle_fmm_accel_ex": (I, [DP, I, I, I, I, I, I, D, D, DP, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -238,15 +246,34 @@ class Oracle:
         self.lib.oracle_direct(_dp(rho), nx, ny, nz, dx, G, _dp(phi), threads)
         return phi
 
-    def fmm_accel(self, rho, b: int, p: int, dx: float = 1.0, G: float = 1.0, threads: int = 0) -> np.ndarray:
+    def fmm_accel(self, rho, b: int, p: int, dx: float = 1.0, G: float = 1.0, threads: int = 0,
+                  final_stage: str = "m2l") -> np.ndarray:
         """Analytic acceleration [3][nz][ny][nx]: gradient of the leaf local
-        expansions plus the near-field pair forces."""
+        expansions plus the near-field pair forces; final_stage "m2p" takes
+        the leaf interaction list's M2P gradients at the cell centres instead
+        of the leaf M2L (the leaf locals are then the parent's alone)."""
         rho = _f64(rho)
         nz, ny, nx = rho.shape
         acc = np.zeros((3,) + rho.shape)
-        if self.lib.oracle_fmm_accel(_dp(rho), nx, ny, nz, b, p, dx, G, _dp(acc), threads) != 0:
+        if final_stage == "m2l":
+            rc = self.lib.oracle_fmm_accel(_dp(rho), nx, ny, nz, b, p, dx, G, _dp(acc), threads)
+        else:
+            rc = self.lib.oracle_fmm_accel_ex(_dp(rho), nx, ny, nz, b, p, {"m2l": 0, "m2p": 1}[final_stage], dx, G,
+                                              _dp(acc), threads)
+        if rc != 0:
             raise ValueError("oracle_fmm_accel rejected its arguments")
         return acc
+
+    def m2p_eval(self, M, R, p: int):
+        """(phi, grad) of one multipole set M (ncoef(p) coefficients, the
+        index order of `index`) evaluated by M2P at the point R."""
+        M = np.ascontiguousarray(M, dtype=np.float64)
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        phi = np.zeros(1)
+        g = np.zeros(3)
+        if self.lib.oracle_m2p_eval(_dp(M), p, _dp(R), _dp(phi), _dp(g)) != 0:
+            raise ValueError("oracle_m2p_eval rejected its arguments")
+        return float(phi[0]), g
 
     def fmm_m2p(self, rho, b: int, p: int, dx: float = 1.0, G: float = 1.0, threads: int = 0) -> np.ndarray:
         """Potential with the paper's final stage: M2P at the cell centres for the

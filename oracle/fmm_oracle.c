@@ -1197,6 +1197,91 @@ int oracle_adjoint_analytic(const double* gphi, const double* gaccel, int nx, in
   return or_adjoint(gphi, gaccel, 1, nx, ny, nz, b, p, dx, G, grho, nthreads);
 }
 
+/* Gradient of the M2P evaluation of Sec. 4's final stage with respect to the
+ * target point.  d/dx_q D_alpha(x - c) = D_{alpha + e_q}(x - c), so
+ *   d phi / dx_q = sum_alpha (-1)^|alpha| / alpha! D_{alpha + e_q}(R) M_alpha,
+ * which takes the derivative tensor one order above the multipoles'; ix1 is
+ * the index of order ix->p + 1 (its first ix->nc entries are ix's). */
+static void or_m2p_grad(const or_index* ix, const or_index* ix1, const double* M, const double R[3], double g[3]) {
+  double D[1000];
+  or_dtensor_ix(ix1, R, ix1->p, D);
+  g[0] = g[1] = g[2] = 0.0;
+  for (int ka = 0; ka < ix->nc; ++ka) {
+    const int* a = ix->mi[ka];
+    const int na = a[0] + a[1] + a[2];
+    if (na > ix->mo) continue;
+    const double w = ((na & 1) ? -1.0 : 1.0) / (or_fact(a[0]) * or_fact(a[1]) * or_fact(a[2])) * M[ka];
+    for (int q = 0; q < 3; ++q)
+#if ORACLE_MUTANT == 18 /* planted mistake: the gradient reads D_alpha instead of D_{alpha + e_q} */
+      g[q] += w * D[ix1->lut[a[0]][a[1]][a[2]]];
+#else
+      g[q] += w * D[ix1->lut[a[0] + (q == 0)][a[1] + (q == 1)][a[2] + (q == 2)]];
+#endif
+  }
+}
+
+/* M2P of one multipole set at one point, with its gradient (test hook for
+ * the pins of or_m2p_grad). */
+int oracle_m2p_eval(const double* M, int p, const double* R, double* phi, double* grad) {
+  if (p < 0 || p + 1 > OR_MAXP) return -1;
+  or_index* ix = (or_index*)malloc(sizeof(or_index));
+  or_index* ix1 = (or_index*)malloc(sizeof(or_index));
+  or_index_init(ix, p);
+  or_index_init(ix1, p + 1);
+  *phi = or_m2p(ix, M, R);
+  or_m2p_grad(ix, ix1, M, R, grad);
+  free(ix);
+  free(ix1);
+  return 0;
+}
+
+/* Analytic acceleration with either final stage (final_stage 0: the leaf
+ * M2L and L2P, as oracle_fmm_accel; 1: the leaf locals are the parent's
+ * shifted locals alone and the leaf interaction list is evaluated by M2P at
+ * the cell centre, Sec. 4):
+ *   accel = -G dx ( grad L2P(L_leaf) [+ sum_{S in IL} grad M2P(M_S)]
+ *                   + sum_near m (x - y) / |x - y|^3 ). */
+int oracle_fmm_accel_ex(const double* rho, int nx, int ny, int nz, int b, int p, int final_stage, double dx, double G,
+                        double* accel, int nthreads) {
+  or_hier H;
+  if (or_hier_init(&H, nx, ny, nz, b, p)) return -1;
+  if (final_stage < 0 || final_stage > 1 || p + 1 > OR_MAXP) return -1;
+  or_set_threads(nthreads);
+  or_index* ix = (or_index*)malloc(sizeof(or_index));
+  or_index* ix1 = (or_index*)malloc(sizeof(or_index));
+  or_index_init(ix, p);
+  or_index_init(ix1, p + 1);
+  double** M = or_upward(&H, ix, rho);
+  double** L = or_downward_ex(&H, ix, M, final_stage ? 0 : 1);
+  const long n = (long)nx * ny * nz;
+  const double scale = -G * dx;
+  const or_level* lf = &H.lev[H.L];
+#pragma omp parallel for schedule(dynamic, 64)
+  for (long c = 0; c < n; ++c) {
+    int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long)nx * ny));
+    double gf[3], gn[3];
+    or_far_grad(&H, ix, L, x, y, z, gf);
+    if (final_stage && H.L >= 2) {
+      int il[216][3];
+      const int m = or_ilist(&H, H.L, x / b, y / b, z / b, il);
+      for (int q = 0; q < m; ++q) {
+        double cs[3], g[3];
+        or_bcentre(lf, il[q][0], il[q][1], il[q][2], cs);
+        const double R[3] = {x + 0.5 - cs[0], y + 0.5 - cs[1], z + 0.5 - cs[2]};
+        or_m2p_grad(ix, ix1, M[H.L] + or_bidx(lf, il[q][0], il[q][1], il[q][2]) * ix->nc, R, g);
+        for (int r = 0; r < 3; ++r) gf[r] += g[r];
+      }
+    }
+    or_near_grad(&H, rho, x, y, z, gn);
+    for (int q = 0; q < 3; ++q) accel[q * n + c] = scale * (gf[q] + gn[q]);
+  }
+  or_free_levels(&H, M);
+  or_free_levels(&H, L);
+  free(ix);
+  free(ix1);
+  return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Analytic acceleration (the force read off the expansions and the near    */
 /* pair forces, instead of the stencil of App. C):                          */

@@ -29,6 +29,7 @@ MUTANTS = {
     15: "gradient of L2P with the undifferentiated factorials",
     16: "near field over the face neighbours only (edge and corner boxes dropped)",
     17: "analytic force's adjoint with the transposed pair force reversed",
+    18: "M2P gradient reading D_alpha instead of D_{alpha + e_q}",
 }
 
 # Cheap single-operator pins first: a mutant's battery stops at the first pin
@@ -51,6 +52,7 @@ PINS = [
     orders.test_order_zero_locals_give_a_constant_far_field_per_box,
     solve.test_adjoint_chain_is_transpose,
     accel.test_adjoint_of_the_analytic_force_is_its_transpose,
+    accel.test_m2p_gradient_is_the_derivative_of_m2p,
 ]
 
 
