@@ -58,6 +58,8 @@ def parse():
                     help="bf16x3: tensor-core M2L on every Cartesian component instead of the (p+1)^2 harmonic ones")
     ap.add_argument("--final-stage", default="m2l", choices=["m2l", "m2p"],
                     help="leaf level by M2L + L2P (m2l) or by the interaction list evaluated at the cells (m2p)")
+    ap.add_argument("--coarse", default="fp64", choices=["fp64", "fp32"],
+                    help="precision of the coarse M2L levels of the mixed precisions (CUDA cores)")
     ap.add_argument("--fp64-levels", type=int, default=3,
                     help="tensor-core precisions: M2L levels 2 .. 1+N run in FP64 on the CUDA cores (default 3, "
                          "the library's default)")
@@ -257,6 +259,49 @@ def run_oracle_sample(n, order, leaf, seed=2606):
     return time.perf_counter() - t0, orc.max_threads()
 
 
+def oracle_cells(n, extra=128, seed=7):
+    """A fixed set of flat cell indices for the per-run error against the
+    oracle: x-rows of 64 cells on both sides of the planes where the leaf
+    level's tensor-core tiles meet (y and z tile boundaries) and along two
+    domain edges (zero-filled activation boxes), the eight corners, the six
+    face centres, and `extra` uniformly random cells."""
+    import numpy as np
+
+    q = max(n // 4, 1)
+    rows = [(q - 1, n // 2 - 1), (q, n // 2), (0, 0), (n - 1, n - 1)]
+    x = np.arange(min(64, n)) * max(n // 64, 1)
+    parts = [z * n * n + y * n + x for y, z in rows]
+    h = n // 2
+    parts.append(np.array([z * n * n + y * n + xx for z in (0, n - 1) for y in (0, n - 1) for xx in (0, n - 1)] +
+                          [h * n * n + h * n, h * n * n + h * n + n - 1, h * n * n + h, h * n * n + (n - 1) * n + h,
+                           h * n + h, (n - 1) * n * n + h * n + h]))
+    parts.append(np.random.default_rng(seed).integers(0, n ** 3, extra))
+    return np.unique(np.concatenate(parts).astype(np.int64))
+
+
+def oracle_error(phi, n, order, leaf, final_stage, seed=2606):
+    """Relative L2 and max-abs error of phi (a CUDA tensor, [n][n][n]) at
+    oracle_cells against the FP64 oracle's sampled solve of the same field."""
+    import numpy as np
+    import torch
+
+    from oracle import Oracle
+    from paper_2606_13793_gb300 import inputs
+
+    if final_stage == "m2p":  # the oracle samples the leaf-M2L final stage only
+        return None
+    orc = Oracle()
+    cells = oracle_cells(n)
+    rho = inputs.lognormal(n, seed=seed).astype(np.float64)
+    t0 = time.perf_counter()
+    ref = orc.fmm_sample(rho, leaf, order, cells, dx=1.0 / n, threads=cpu_cores())
+    dt = time.perf_counter() - t0
+    got = phi.reshape(-1)[torch.from_numpy(cells).to(phi.device)].double().cpu().numpy()
+    return {"rel_err_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "max_abs_rel_vs_oracle": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
+            "oracle_cells": int(cells.size), "oracle_sample_s": round(dt, 1)}
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return
@@ -330,11 +375,13 @@ def main():
     rho = torch.from_numpy(rho_np).cuda()
     plan = fmm.FMMPlan((n, n, n), p, b, args.precision, dx=dx,
                        accel="analytic" if args.accel == "analytic" else True, final_stage=args.final_stage,
-                       harmonic=not args.m2l_cartesian, n_fp64_levels=args.fp64_levels)
+                       harmonic=not args.m2l_cartesian, n_fp64_levels=args.fp64_levels,
+                       coarse=args.coarse)
     tc_prec = args.precision in ("bf16x3", "tf32")
     harmonic = args.precision == "bf16x3" and not args.m2l_cartesian  # tensor-core levels
-    harmonic_cc = (not args.m2l_cartesian and args.order >= 2         # CUDA-core levels (FP32 / FP64 plans)
-                   and args.precision in ("fp32", "fp64"))
+    harmonic_cc = (not args.m2l_cartesian and args.order >= 2         # CUDA-core levels (FP32 / FP64 plans,
+                   and (args.precision in ("fp32", "fp64")            # FP32 coarse levels of the mixed ones)
+                        or (tc_prec and args.coarse == "fp32")))
     if not args.no_autotune:
         plan.autotune()
     tuning = {str(l): list(plan.tuning(l)) for l in range(2, plan.leaf_level + 1) if plan.level_kind(l) != "tensor"}
@@ -400,6 +447,10 @@ def main():
 
     # ---- accuracy of this mode against the FP64 solve of the same field ----
     compare = {}
+    if not args.no_cpu and rank == 0 and world == 1:  # the oracle at a fixed cell set (outside the timed region)
+        oe = oracle_error(phi, n, p, b, args.final_stage)
+        if oe:
+            compare.update(oe)
     if not args.no_compare and rank == 0:
         phi_mode = phi.double().clone()
         p64 = fmm.FMMPlan((n, n, n), p, b, "fp64", dx=dx, final_stage=args.final_stage)
@@ -466,7 +517,8 @@ def main():
     dom = "m2l_tc" if "m2l_tc" in per_kernel else max(per_kernel, key=lambda k: per_kernel[k]["ms_per_step"])
     workload = f"{n}^3 p={p} leaf {b} {args.precision}" + (" m2p" if args.final_stage == "m2p" else "") + \
         (" harmonic" if harmonic else "") + \
-        (f" fp64 levels {args.fp64_levels}" if tc_prec and args.fp64_levels != 3 else "")
+        (f" fp64 levels {args.fp64_levels}" if tc_prec and args.fp64_levels != 3 else "") + \
+        (" coarse fp32" if tc_prec and args.coarse == "fp32" else "")
     traffic = profiled_traffic(dom + "/" + args.precision, workload)
     d = per_kernel[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": "TFLOP/s",
@@ -496,7 +548,7 @@ def main():
                                  f"rho ({n ** 3 * 4 / 2 ** 20:.0f} MiB) fits in L2: not a bandwidth-valid size",
                            "parallelism": f"replicas x{world}", "cuda_core_variants": tuning, "accel": args.accel,
                            "final_stage": args.final_stage,
-                           **({"fp64_m2l_levels": f"2..{1 + args.fp64_levels}"} if tc_prec else {}),
+                           **({"coarse_m2l_levels": f"2..{1 + args.fp64_levels} {args.coarse} (CUDA cores)"} if tc_prec else {}),
                            "m2l_components": "harmonic (p+1)^2" if (harmonic or harmonic_cc) else "cartesian nc(p)",
                            "autotuned": not args.no_autotune, **compare},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

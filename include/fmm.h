@@ -84,14 +84,14 @@ typedef struct {
                          5-point stencil (App. C); 2: analytic accel, the
                          gradient of the leaf local expansions plus the
                          near-field pair forces m (x - y)/|x - y|^3 between
-                         distinct cells (no self force).  With 2, the near
-                         field computes four columns per cell and
-                         fmm_solve_adjoint rejects grad_accel
-                         (FMM_ERR_UNSUPPORTED)                                  */
+                         distinct cells (no self force); with final_stage 1
+                         also the gradient of the leaf interaction list's M2P
+                         at the cell centres.  With 2, the near field (and
+                         the M2P) computes four columns per cell           */
   int final_stage;    /* 0: M2L + L2P at the leaf level too; 1: the paper's own
                          final stage (Sec. 4): the leaf interaction list is
                          evaluated by M2P at the cell centres (more accurate,
-                         ~6x the leaf-level work).  With 1, accel must not be 2.
+                         ~6x the leaf-level work).
                          The truncated M2P operator is not symmetric: its
                          transpose (P2L, the leaf cells' own sources expanded
                          about the listed boxes' centres) is what
@@ -116,7 +116,13 @@ typedef struct {
                          holds M2L weights with locals to mult_order, which
                          fmm_solve_adjoint runs.  Start from fmm_default_opts
                          (a zeroed struct means monopoles only)               */
-  int reserved[2];    /* must be zero */
+  int coarse_fp32;    /* mixed precisions: 0 (default) the coarse M2L levels
+                         (n_fp64_levels of them) in FP64; 1: in FP32 on the
+                         CUDA cores, harmonic components -- they are kept off
+                         the tensor cores for accuracy (the coarse levels carry
+                         the bulk of phi, where the split products' error
+                         counts most), which FP32 already gives            */
+  int reserved[1];    /* must be zero */
 } fmm_opts;
 
 /* Default options: FMM_FP32, n_fp64_levels = 3, accel = 1, mult_order = -1. */
@@ -158,14 +164,20 @@ fmm_status fmm_solve(fmm_plan_t plan, const void* rho, void* phi, void* accel, v
  * fmm_solve_adjoint -- gradient of a loss with respect to rho.
  *   grad_phi   : device [nz][ny][nx], dLoss/dphi (read only).
  *   grad_accel : device [3][nz][ny][nx] dLoss/daccel, or NULL.
- *   grad_rho   : device [nz][ny][nx] (written): A^T (grad_phi - FD^T grad_accel/dx) G dx^2.
+ *   grad_rho   : device [nz][ny][nx] (written): A^T (grad_phi - FD^T grad_accel/dx) G dx^2
+ *                with the stencil force (accel = 1); with the analytic force
+ *                (accel = 2) the transpose of (phi, accel) applied to
+ *                (grad_phi, grad_accel).
  * With |alpha|+|beta| <= order the FMM operator A is symmetric (Green's
  * function symmetry, Sec. 2.3), so A^T is the same chain of kernels applied to
- * the adjoint source; the stencil transpose FD^T is its own kernel.  The two
- * truncations that break the symmetry run their transposes: final_stage = 1
- * replaces the leaf M2P by P2L, and mult_order < order runs the M2L with the
- * multipole and local limits swapped.  Errors: FMM_ERR_ARG,
- * FMM_ERR_UNSUPPORTED (grad_accel with accel = 2), FMM_ERR_CUDA.
+ * the adjoint source; the stencil transpose FD^T is its own kernel.  The
+ * analytic force's transpose enters the same chain: its L2P gradient
+ * transposed is a dipole source in the P2M (and, with final_stage = 1, the
+ * force columns of the P2L), its near pair forces transposed join the near
+ * field's contraction (four input columns per cell, on the CUDA cores).  The
+ * two truncations that break the symmetry run their transposes: final_stage =
+ * 1 replaces the leaf M2P by P2L, and mult_order < order runs the M2L with the
+ * multipole and local limits swapped.  Errors: FMM_ERR_ARG, FMM_ERR_CUDA.
  *
  * A plan runs one call at a time: fmm_solve, fmm_solve_adjoint,
  * fmm_solve_host and fmm_plan_autotune share the plan's workspace arena (and
@@ -285,6 +297,18 @@ fmm_status fmm_plan_autotune(fmm_plan_t plan, void* stream);
  * The paper has no counterpart.
  */
 fmm_status fmm_plan_tc_schedule(fmm_plan_t plan, int what, int* prefix, int* available);
+
+/*
+ * fmm_plan_debug_timeout -- test hook for the bounded device waits.  The
+ * next solve's first prefix-schedule M2L launch leaves the first activation
+ * stage of every CTA unloaded: no copy or MMA is issued for it, so the
+ * issuers' wait on it reaches its time limit (2 s) with nothing in flight,
+ * the CTAs give up (each lets its own copies land and frees its tensor
+ * memory) and fmm_check then returns FMM_ERR_TIMEOUT naming the wait sites.
+ * That solve's output is invalid; the plan stays usable and the next solve is
+ * an ordinary one.  FMM_ERR_ARG if no M2L level runs the prefix schedule.
+ */
+fmm_status fmm_plan_debug_timeout(fmm_plan_t plan);
 fmm_status fmm_plan_set_tc_schedule(fmm_plan_t plan, int what, int prefix);
 fmm_status fmm_plan_tuning(fmm_plan_t plan, int level, int* shape, int* dsplit);
 fmm_status fmm_plan_set_tuning(fmm_plan_t plan, int level, int shape, int dsplit);

@@ -53,6 +53,7 @@ EXPORTS = [
     "fmm_plan_set_tuning",
     "fmm_plan_tc_schedule",
     "fmm_plan_set_tc_schedule",
+    "fmm_plan_debug_timeout",
     "fmm_batch_solve",
     "fmm_batch_destroy",
     "fmm_batch_launches",
@@ -73,7 +74,7 @@ class _Grid(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_fp64_levels", ctypes.c_int), ("accel", ctypes.c_int),
                 ("final_stage", ctypes.c_int), ("m2l_cartesian", ctypes.c_int), ("mult_order", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("coarse_fp32", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 _lib = None
@@ -126,6 +127,8 @@ def load(path: str | None = None):
         lib.fmm_plan_tc_schedule.restype = i
         lib.fmm_plan_set_tc_schedule.argtypes = [vp, i, i]
         lib.fmm_plan_set_tc_schedule.restype = i
+        lib.fmm_plan_debug_timeout.argtypes = [vp]
+        lib.fmm_plan_debug_timeout.restype = i
         lib.fmm_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
         lib.fmm_batch_create.restype = i
         lib.fmm_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
@@ -174,7 +177,7 @@ class FMMPlan:
 
     def __init__(self, shape, order: int = 6, leaf: int = 4, precision: str = "fp32", dx: float = 1.0,
                  G: float = 1.0, n_fp64_levels: int = 3, accel=True, final_stage: str = "m2l", harmonic=True,
-                 mult_order=None, stream=None):
+                 mult_order=None, stream=None, coarse: str = "fp64"):
         import torch
 
         self.lib = load()
@@ -190,6 +193,10 @@ class FMMPlan:
         self.lib.fmm_default_opts(ctypes.byref(opts))
         opts.precision = PRECISION[precision]
         opts.n_fp64_levels = int(n_fp64_levels)
+        # coarse: the precision of those coarse M2L levels in the mixed precisions
+        if coarse not in ("fp64", "fp32"):
+            raise ValueError("coarse must be 'fp64' or 'fp32'")
+        opts.coarse_fp32 = 1 if coarse == "fp32" else 0
         # accel: False (none), True (5-point stencil of phi), "analytic" (gradient
         # of the expansions plus near-field pair forces)
         opts.accel = 2 if accel == "analytic" else (1 if accel else 0)
@@ -343,6 +350,11 @@ class FMMPlan:
             raise ValueError("schedule is 'prefix' or 'span'")
         _check(self.lib, self.lib.fmm_plan_set_tc_schedule(self._h, self.TC_SCHEDULE[what],
                                                             1 if schedule == "prefix" else 0))
+
+    def debug_timeout(self):
+        """Test hook: the next solve's first prefix-schedule M2L launch lets
+        its bounded waits run out (fmm_plan_debug_timeout)."""
+        _check(self.lib, self.lib.fmm_plan_debug_timeout(self._h))
 
     def launches(self, accel: bool = True) -> int:
         return int(self.lib.fmm_solve_launches(self._h, 1 if accel else 0))

@@ -213,7 +213,18 @@ struct fmm_plan_s {
   int near_comps = 1;  // near-field columns per cell: potential, + 3 force components (analytic accel)
   // final-stage M2P (the paper's own final stage): leaf interaction list at the cell centres
   bool m2p = false, m2p_tc = false;
-  size_t m2p_off = 0;  // [leaf parent][child][b^3] potentials (scaled, x 1/b in the leaf kernel)
+  size_t m2p_off = 0;  // [leaf parent][child][m2p_comps][b^3] potentials (scaled, x 1/b in the leaf kernel)
+  int m2p_comps = 1;   // 4 with the analytic force: the potential and its three derivatives
+  // transpose of the analytic force (fmm_solve_adjoint with grad_accel and
+  // accel = 2): dipole P2M sources [3][cells] and the near field's transpose
+  // over [w, -g/dx] x b^3 per box (CUDA cores), into one potential column
+  size_t adj_dip_off = 0;
+  void* d_w_near_adj = nullptr;
+  int* d_near_adj_tile_k = nullptr;
+  long long* d_near_adj_tile_w = nullptr;
+  int near_adj_ntiles = 0;
+  std::vector<int> h_near_adj_tile_k;
+  const void* adj_g = nullptr;  // during an adjoint solve: the force's adjoint input [3][cells]
   void* d_w_m2p = nullptr;
   int* d_m2p_tile_k = nullptr;
   long long* d_m2p_tile_w = nullptr;
@@ -235,6 +246,7 @@ struct fmm_plan_s {
   bool tp_m2l = false, tp_m2l_t = false, tp_m2p = false, tp_near = false;
   bool span_m2l = false, span_m2l_t = false, span_near = false, span_m2p = false;
   bool use_tp[3] = {true, false, true};
+  bool inject_timeout = false;  // test hook (fmm_plan_debug_timeout): the next prefix launch starves its first stage
   TpLaunch tpl{}, tpl_t{}, tpm{}, tpn{};
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // timing
@@ -1291,23 +1303,33 @@ struct M2pTable {
   }
 };
 
-double m2p_entry(const MultiIndex& mi, const M2pTable& tab, int d, int k, int n) {
+// comps = 1: columns n = target child * b^3 + cell, the potential.  comps = 4
+// (the analytic force, App. C): n = child * 4 b^3 + comp * b^3 + cell, comp 0
+// the potential and comp 1 + q its derivative in the target's x_q (box
+// units): d/du_q D_a(u) = D_{a + e_q}(u), and with T the Taylor coefficients
+// of 1/r, D_a / a! = -T_a, so the weight is (-1)^|a| (-(a_q + 1) T_{a+e_q});
+// tab then holds the coefficients to order p + 1.
+double m2p_entry(const MultiIndex& mi, const M2pTable& tab, int d, int k, int n, int comps = 1) {
   const int b3 = tab.b * tab.b * tab.b;
-  const int al = k / 8, cs = k % 8, ct = n / b3, cell = n % b3;
+  const int al = k / 8, cs = k % 8, ct = n / (comps * b3), comp = (n / b3) % comps, cell = n % b3;
   if (al >= mi.nc || ct >= 8 || level_of_order(mi, al) > mi.mo) return 0.0;
   const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
   int u[3];
   for (int q = 0; q < 3; ++q) u[q] = ((ct >> q) & 1) - ((cs >> q) & 1) - 2 * D[q];
   if (std::max(std::abs(u[0]), std::max(std::abs(u[1]), std::abs(u[2]))) < 2) return 0.0;
   const std::vector<double>& tb = tab.t[(size_t)((u[2] + 3) * 49 + (u[1] + 3) * 7 + (u[0] + 3)) * b3 + cell];
-  return (((mi.a[al] + mi.b[al] + mi.c[al]) & 1) ? -1.0 : 1.0) * (-tb[al]);
+  const double sgn = ((mi.a[al] + mi.b[al] + mi.c[al]) & 1) ? -1.0 : 1.0;
+  if (comp == 0) return sgn * (-tb[al]);
+  int e[3] = {mi.a[al], mi.b[al], mi.c[al]};
+  const int aq = e[comp - 1]++;
+  return sgn * (-(aq + 1) * tb[mi.index(e[0], e[1], e[2])]);
 }
 
 // Tensor-core schedule of the M2P contraction: every output column needs the
 // whole reduction (no truncation prefix), so groups of up to 128 columns
 // share one K = 8 nc; one pass for b <= 4.
-bool build_tc_m2p(const MultiIndex& mi, const M2pTable& tab, int kind, TcHost& H, bool harm) {
-  const int ncol = 8 * tab.b * tab.b * tab.b;
+bool build_tc_m2p(const MultiIndex& mi, const M2pTable& tab, int kind, TcHost& H, bool harm, int comps = 1) {
+  const int ncol = 8 * comps * tab.b * tab.b * tab.b;
   const std::vector<int> red = harmonic_components(mi);
   const int K = 8 * (harm ? (mi.mo + 1) * (mi.mo + 1) : ncoef(mi.mo));
   std::vector<TcCols> gs;
@@ -1315,9 +1337,9 @@ bool build_tc_m2p(const MultiIndex& mi, const M2pTable& tab, int kind, TcHost& H
   // with harmonic planes the reduction runs over the folded components (the
   // M2P weights, derivatives of 1/r in alpha, fold the same way)
   auto entry = [&](int d, int k, int n) {
-    if (!harm) return m2p_entry(mi, tab, d, k, n);
+    if (!harm) return m2p_entry(mi, tab, d, k, n, comps);
     if (k / 8 >= (int)red.size()) return 0.0;
-    return m2p_entry(mi, tab, d, red[k / 8] * 8 + k % 8, n);
+    return m2p_entry(mi, tab, d, red[k / 8] * 8 + k % 8, n, comps);
   };
   return build_tc_generic(kind, gs, entry, H, 2);
 }
@@ -1351,15 +1373,15 @@ bool build_tp_near(int b, int comps, int kind, TpHost& H) {
   return build_tp_generic(kind, kcol, b3, entry, H);
 }
 
-bool build_tp_m2p(const MultiIndex& mi, const M2pTable& tab, int kind, TpHost& H, bool harm) {
-  const int ncol = 8 * tab.b * tab.b * tab.b;
+bool build_tp_m2p(const MultiIndex& mi, const M2pTable& tab, int kind, TpHost& H, bool harm, int comps = 1) {
+  const int ncol = 8 * comps * tab.b * tab.b * tab.b;
   const std::vector<int> red = harmonic_components(mi);
   const int K = 8 * (harm ? (mi.mo + 1) * (mi.mo + 1) : ncoef(mi.mo));
   std::vector<int> kcol(ncol, K);
   auto entry = [&](int d, int k, int n) {
-    if (!harm) return m2p_entry(mi, tab, d, k, n);
+    if (!harm) return m2p_entry(mi, tab, d, k, n, comps);
     if (k / 8 >= (int)red.size()) return 0.0;
-    return m2p_entry(mi, tab, d, red[k / 8] * 8 + k % 8, n);
+    return m2p_entry(mi, tab, d, red[k / 8] * 8 + k % 8, n, comps);
   };
   return build_tp_generic(kind, kcol, K, entry, H);
 }
@@ -1499,14 +1521,14 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     // stages a box row's full and folded components in shared memory.
     const size_t esz = o.precision == FMM_FP64 ? 8 : 4;
     const size_t stage = (size_t)16 * (8 * P->nc + 8 + 8 * P->nr + 8) * esz;
-    P->harm_cc = !tcp && !o.m2l_cartesian && order >= 2 && stage <= 227 * 1024;
+    P->harm_cc = (!tcp || o.coarse_fp32) && !o.m2l_cartesian && order >= 2 && stage <= 227 * 1024;
   }
   for (int l = 0; l <= P->L; ++l) {
     Level& lv = P->lev[l];
     lv.f64 = P->f64_data() ? 1 : 0;
     lv.tc = 0;
     if (tcp && l >= 2) {
-      if (l <= 1 + o.n_fp64_levels && l < P->L) lv.f64 = 1;
+      if (l <= 1 + o.n_fp64_levels && l < P->L) lv.f64 = o.coarse_fp32 ? 0 : 1;
       else lv.tc = order >= 2 ? 1 : 0;
     }
   }
@@ -1548,11 +1570,16 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
   P->near_off = off;
   off = align(off + cells_bytes * (size_t)P->near_comps);
   if (P->m2p) {  // every cell of every leaf parent block, phantom children included
+    P->m2p_comps = o.accel == 2 ? 4 : 1;
     P->m2p_off = off;
-    off = align(off + (size_t)P->lev[P->L].npar * 8 * (size_t)(P->b * P->b * P->b) * P->esize());
+    off = align(off + (size_t)P->lev[P->L].npar * 8 * (size_t)(P->b * P->b * P->b) * P->m2p_comps * P->esize());
   }
   P->work_off = off;
   off = align(off + cells_bytes);
+  if (P->near_comps == 4) {
+    P->adj_dip_off = off;
+    off = align(off + 3 * cells_bytes);
+  }
   P->near_tc = tcp && (leaf == 4 || leaf == 8);
   if (P->near_tc) {  // the near field always runs bf16x3 (hi/lo density planes)
     P->rho_hi_off = off;
@@ -1779,13 +1806,50 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     P->h_near_tile_k = tk;
     if ((st = P->upload(tk, &P->d_near_tile_k, s)) || (st = P->upload(tw, &P->d_near_tile_w, s))) return cleanup(st);
   }
+  if (P->near_comps == 4) {
+    // the near field (potential and pair forces) transposed: row box = source
+    // box, reduction k = (input column, cell of neighbour box d), output the
+    // source cell's potential column.  Column 0: the symmetric kernel; column
+    // 1 + q: the forward force at the neighbour's cell (the target) from this
+    // cell, near_entry with the opposite box offset.
+    const int b = P->b, b3 = b * b * b;
+    auto entry = [b, b3](int d, int k, int n) {
+      const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1}, Dm[3] = {-D[0], -D[1], -D[2]};
+      const int comp = k / b3, cell = k % b3;
+      return comp == 0 ? near_entry(b, D, cell, n) : near_entry(b, Dm, n, comp * b3 + cell);
+    };
+    std::vector<int> tk;
+    std::vector<long long> tw;
+    if (P->f64_data()) {
+      std::vector<double> W;
+      full_weights<double>(b3, 4 * b3, entry, W, tk, tw, !P->static_keep_tables);
+      double* d = nullptr;
+      if ((st = P->upload(W, &d, s))) return cleanup(st);
+      P->d_w_near_adj = d;
+    } else {
+      std::vector<float> W;
+      full_weights<float>(b3, 4 * b3, entry, W, tk, tw, !P->static_keep_tables);
+      float* d = nullptr;
+      if ((st = P->upload(W, &d, s))) return cleanup(st);
+      P->d_w_near_adj = d;
+    }
+    P->near_adj_ntiles = (int)tk.size();
+    P->h_near_adj_tile_k = tk;
+    if ((st = P->upload(tk, &P->d_near_adj_tile_k, s)) || (st = P->upload(tw, &P->d_near_adj_tile_w, s)))
+      return cleanup(st);
+  }
   if (P->m2p) {
-    M2pTable tab;
-    tab.build(P->mi, P->b);
+    const int mc = P->m2p_comps;
+    M2pTable tab;  // Taylor coefficients to order p + 1 when the force needs the derivatives
+    {
+      MultiIndex mt1;
+      mt1.init(P->mi.p + (mc > 1 ? 1 : 0));
+      tab.build(mt1, P->b);
+    }
     const Level& lf = P->lev[P->L];
     if (lf.tc) {
       TpHost Hp;
-      if (build_tp_m2p(P->mi, tab, P->tc_kind, Hp, P->harm)) {
+      if (build_tp_m2p(P->mi, tab, P->tc_kind, Hp, P->harm, mc)) {
         unsigned char* dw = nullptr;
         if ((st = P->upload(Hp.W, &dw, s))) return cleanup(st);
         TpLaunch& T = P->tpm;
@@ -1795,7 +1859,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
         T.w_slots = Hp.w_slots;
         for (int q = 0; q < kTpIssuers; ++q) T.owner_slot0[q] = (int8_t)Hp.owner_slot0[q], T.owner_nslots[q] = (int8_t)Hp.owner_nslots[q];
         T.W = dw;
-        T.n_cols = 8 * P->b * P->b * P->b;
+        T.n_cols = 8 * mc * P->b * P->b * P->b;
         T.kind = P->tc_kind;
         T.accumulate = 0;
         for (int q = 0; q < 3; ++q) T.grid[q] = lf.np[q];
@@ -1805,7 +1869,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
     }
     if (lf.tc) {
       TcHost H;
-      if (build_tc_m2p(P->mi, tab, P->tc_kind, H, P->harm)) {
+      if (build_tc_m2p(P->mi, tab, P->tc_kind, H, P->harm, mc) && H.npass <= kTcMaxPasses) {
         unsigned char* dw = nullptr;
         if ((st = P->upload(H.W, &dw, s))) return cleanup(st);
         TcLaunch& T = P->tcm;
@@ -1813,7 +1877,7 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
         T.npass = H.npass;
         T.a_stages = H.a_stages;
         for (int i = 0; i < H.npass; ++i) T.pass[i] = H.pass[i];
-        T.n_cols = 8 * P->b * P->b * P->b;
+        T.n_cols = 8 * mc * P->b * P->b * P->b;
         T.kind = P->tc_kind;
         T.accumulate = 0;
         for (int q = 0; q < 3; ++q) T.grid[q] = lf.np[q];
@@ -1822,8 +1886,8 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
       }
     }
     if (!P->m2p_tc) {
-      const int ncol = 8 * P->b * P->b * P->b;
-      auto entry = [&](int d, int k, int n) { return m2p_entry(P->mi, tab, d, k, n); };
+      const int ncol = 8 * mc * P->b * P->b * P->b;
+      auto entry = [&](int d, int k, int n) { return m2p_entry(P->mi, tab, d, k, n, mc); };
       std::vector<int> tk;
       std::vector<long long> tw;
       if (lf.f64) {
@@ -1848,8 +1912,8 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
       // the cells (target child, cell) of neighbour d, the columns are the
       // source's (alpha, child) locals; W'_d[k][n] = W_{-d}[n][k] (26 - d is
       // the opposite neighbour)
-      const int K = 8 * P->b * P->b * P->b;
-      auto entry = [&](int d, int k, int n) { return m2p_entry(P->mi, tab, 26 - d, n, k); };
+      const int K = 8 * mc * P->b * P->b * P->b;
+      auto entry = [&](int d, int k, int n) { return m2p_entry(P->mi, tab, 26 - d, n, k, mc); };
       std::vector<int> tk;
       std::vector<long long> tw;
       if (lf.f64) {
@@ -1990,10 +2054,9 @@ fmm_status fmm_plan(const fmm_grid* grid, int order, int leaf, const fmm_opts* o
   if (o.n_fp64_levels < 0 || o.n_fp64_levels > kMaxLevels) return fail(FMM_ERR_ARG, "bad n_fp64_levels");
   if (o.accel < 0 || o.accel > 2) return fail(FMM_ERR_ARG, "accel %d not in {0, 1, 2}", o.accel);
   if (o.final_stage < 0 || o.final_stage > 1) return fail(FMM_ERR_ARG, "final_stage %d not in {0, 1}", o.final_stage);
-  if (o.final_stage == 1 && o.accel == 2)
-    return fail(FMM_ERR_UNSUPPORTED, "the analytic acceleration is built for final_stage = 0 only");
   if (o.m2l_cartesian < 0 || o.m2l_cartesian > 1) return fail(FMM_ERR_ARG, "m2l_cartesian %d not in {0, 1}", o.m2l_cartesian);
   if (o.mult_order < -1) return fail(FMM_ERR_ARG, "mult_order %d below -1", o.mult_order);
+  if (o.coarse_fp32 < 0 || o.coarse_fp32 > 1) return fail(FMM_ERR_ARG, "coarse_fp32 %d not in {0, 1}", o.coarse_fp32);
   for (int r : o.reserved)
     if (r != 0) return fail(FMM_ERR_ARG, "reserved option fields must be zero");
   int dev = 0;
@@ -2173,7 +2236,7 @@ fmm_status do_m2p(fmm_plan_t P, cudaStream_t s) {
   g.tile_k = P->d_m2p_tile_k;
   g.tile_w = P->d_m2p_tile_w;
   g.C = P->arena + P->m2p_off;
-  g.n_cols = 8 * P->b * P->b * P->b;
+  g.n_cols = 8 * P->m2p_comps * P->b * P->b * P->b;
   g.ntiles = P->m2p_ntiles;
   g.accumulate = 0;
   g.dsplit = 1;
@@ -2189,7 +2252,7 @@ fmm_status do_p2l(fmm_plan_t P, cudaStream_t s) {
   const Level& lf = P->lev[P->L];
   NbrGemm g;
   g.A = P->arena + P->m2p_off;
-  g.row_len = 8 * P->b * P->b * P->b;
+  g.row_len = 8 * P->m2p_comps * P->b * P->b * P->b;
   for (int q = 0; q < 3; ++q) g.grid[q] = lf.np[q];
   g.W = P->d_w_p2l;
   g.tile_k = P->d_p2l_tile_k;
@@ -2211,7 +2274,11 @@ fmm_status do_m2l(fmm_plan_t P, int l, cudaStream_t s) {
     TpLaunch& L = (P->transposed && P->asym) ? P->tpl_t : P->tpl;
     L.C = static_cast<float*>(P->Lx(l));
     for (int q = 0; q < 3; ++q) L.grid[q] = lv.np[q];
-    CUDA_TRY(launch_nbr_tc(L, P->map_hi[l], P->map_lo[l], s));
+    L.skip_first_a = P->inject_timeout ? 1 : 0;
+    P->inject_timeout = false;
+    const cudaError_t e = launch_nbr_tc(L, P->map_hi[l], P->map_lo[l], s);
+    L.skip_first_a = 0;
+    CUDA_TRY(e);
     return FMM_OK;
   }
   if (lv.tc) {
@@ -2237,20 +2304,35 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
   T* rho_box = reinterpret_cast<T*>(P->arena + P->rho_box_off);
   T* near_box = reinterpret_cast<T*>(P->arena + P->near_off);
   fmm_status st;
+  // The transpose of the analytic force (adjoint solve with its input g):
+  // with v = -g / (dx b) its far part is dipole sources in the P2M (and the
+  // P2L's three force columns); its near part and the potential's are one
+  // contraction over [w, -g/dx] per box, whose single output column replaces
+  // the near field (the leaf finish scales both by G dx^2, as -G dx / b^2 /
+  // (G dx^2 / b) = -1 / (dx b) and -G dx / (G dx^2) = -1/dx make them the
+  // force's transpose).
+  const T* adj_g = adjoint ? static_cast<const T*>(P->adj_g) : nullptr;
+  T* adj_dip = adj_g ? reinterpret_cast<T*>(P->arena + P->adj_dip_off) : nullptr;
+  if (adj_g) CUDA_TRY(launch_scaled_copy<T>(adj_g, 3 * P->ncell(), -1.0 / (P->dx * P->b), adj_dip, s));
   // upward pass
   {
     StageTimer t(P, ST_P2M, s);
     const Level& lf = P->lev[L];
     const bool mplanes = lf.tc && P->tc_kind == TC_BF16X3;
-    CUDA_TRY(launch_p2m<T>(tt, rho, P->dims, lf, static_cast<T*>(P->M(L)), P->near_tc ? nullptr : rho_box,
+    const bool near_rows = !adj_g;  // the near field's own inputs (not read by the transposed force's)
+    CUDA_TRY(launch_p2m<T>(tt, rho, P->dims, lf, static_cast<T*>(P->M(L)),
+                           (P->near_tc || !near_rows) ? nullptr : rho_box,
                            mplanes ? P->arena + lf.hi_off : nullptr, mplanes ? P->arena + lf.lo_off : nullptr,
-                           P->near_tc ? P->arena + P->rho_hi_off : nullptr,
-                           P->near_tc ? P->arena + P->rho_lo_off : nullptr, P->d_flag,
+                           (P->near_tc && near_rows) ? P->arena + P->rho_hi_off : nullptr,
+                           (P->near_tc && near_rows) ? P->arena + P->rho_lo_off : nullptr, P->d_flag,
                            ((mplanes && P->harm) || lf.fold_off) ? 1 : 0,
-                           lf.fold_off ? reinterpret_cast<T*>(P->arena + lf.fold_off) : nullptr, s));
+                           lf.fold_off ? reinterpret_cast<T*>(P->arena + lf.fold_off) : nullptr, s, adj_dip));
   }
   const bool p2l = adjoint && P->m2p;  // leaf level by the transpose of M2P
-  if (p2l)
+  if (p2l && P->m2p_comps == 4)  // [w, v] per box, the force columns zero without g
+    CUDA_TRY(launch_cells_to_boxes4<T>(rho, adj_g, -1.0 / (P->dx * P->b), P->dims, P->lev[L], P->b, 1,
+                                       reinterpret_cast<T*>(P->arena + P->m2p_off), s));
+  else if (p2l)
     CUDA_TRY(launch_cells_to_parent_blocks<T>(rho, P->dims, P->lev[L], P->b,
                                               reinterpret_cast<T*>(P->arena + P->m2p_off), s));
   for (int l = L; l >= 3; --l) {
@@ -2270,7 +2352,7 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
   }
   bool any_simt = false;
   for (int l = 2; l <= L; ++l) any_simt |= !P->lev[l].tc;
-  const bool near_side = !P->near_tc && P->near_choice.dsplit > 1;
+  const bool near_side = !P->near_tc && P->near_choice.dsplit > 1 && !adj_g;
   const bool fork = P->side && (any_simt || near_side);
   cudaStream_t sf = fork ? P->side : s;
   if (fork) {
@@ -2297,7 +2379,25 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
     if ((st = (l == L && P->m2p) ? do_m2p(P, s) : do_m2l(P, l, s))) return st;
   }
   // near field over the 27 neighbour leaf boxes
-  if (P->near_tc) {
+  if (adj_g) {  // the transposed near field of the potential and the force, one output column
+    StageTimer t(P, ST_NEAR, s);
+    CUDA_TRY(launch_cells_to_boxes4<T>(rho, adj_g, -1.0 / P->dx, P->dims, P->lev[L], P->b, 0, near_box, s));
+    NbrGemm g;
+    g.A = near_box;
+    g.row_len = 4 * P->b * P->b * P->b;
+    for (int q = 0; q < 3; ++q) g.grid[q] = P->lev[L].n[q];
+    g.W = P->d_w_near_adj;
+    g.tile_k = P->d_near_adj_tile_k;
+    g.tile_w = P->d_near_adj_tile_w;
+    g.C = rho_box;
+    g.n_cols = P->b * P->b * P->b;
+    g.ntiles = P->near_adj_ntiles;
+    g.accumulate = 0;
+    g.dsplit = 1;
+    g.partial = nullptr;
+    g.shape = zrun_eligible(g, P->h_near_adj_tile_k.data(), P->near_adj_ntiles) ? 1 : 0;
+    CUDA_TRY(launch_nbr_gemm<T>(g, s));
+  } else if (P->near_tc) {
     StageTimer t(P, ST_NEAR_TC, s);
     if (tc_prefix(P, TS_NEAR))
       CUDA_TRY(launch_nbr_tc(P->tpn, P->map_near_hi, P->map_near_lo, s));
@@ -2324,14 +2424,15 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
   }
   if (accel && P->near_comps == 4) {  // analytic acceleration, read off the expansions
     StageTimer t(P, ST_LEAF, s);
-    CUDA_TRY(launch_leaf_finish_grad<T>(tt, P->lev[L], static_cast<const T*>(P->Lx(L)), near_box, P->dims,
-                                        P->G * P->dx * P->dx, -P->G * P->dx, phi, accel, s));
+    CUDA_TRY(launch_leaf_finish_grad<T>(tt, P->lev[L], static_cast<const T*>(P->Lx(L)), near_box,
+                                        (P->m2p && !p2l) ? reinterpret_cast<const T*>(P->arena + P->m2p_off) : nullptr,
+                                        P->dims, P->G * P->dx * P->dx, -P->G * P->dx, phi, accel, s));
     return FMM_OK;
   }
   {
     StageTimer t(P, ST_LEAF, s);
-    CUDA_TRY(launch_leaf_finish<T>(tt, P->lev[L], static_cast<const T*>(P->Lx(L)), near_box,
-                                   P->b * P->b * P->b * P->near_comps,
+    CUDA_TRY(launch_leaf_finish<T>(tt, P->lev[L], static_cast<const T*>(P->Lx(L)), adj_g ? rho_box : near_box,
+                                   P->b * P->b * P->b * (adj_g ? 1 : P->near_comps),
                                    (P->m2p && !p2l) ? reinterpret_cast<const T*>(P->arena + P->m2p_off) : nullptr,
                                    P->dims,
                                    P->G * P->dx * P->dx, phi, s));
@@ -2366,30 +2467,33 @@ fmm_status fmm_solve(fmm_plan_t P, const void* rho, void* phi, void* accel, void
 fmm_status fmm_solve_adjoint(fmm_plan_t P, const void* grad_phi, const void* grad_accel, void* grad_rho, void* stream) {
   if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
   if (!grad_rho || (!grad_phi && !grad_accel)) return fail(FMM_ERR_ARG, "grad_rho and one gradient must be non-NULL");
-  if (grad_accel && P->near_comps == 4)
-    return fail(FMM_ERR_UNSUPPORTED, "the adjoint of the analytic acceleration is not built (use accel = 1)");
+  if (grad_accel && !aligned16(grad_accel)) return fail(FMM_ERR_ARG, "device pointers must be 16-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   P->last_stream = s;
   void* w = P->arena + P->work_off;
+  // the analytic force's transpose runs inside the solve (run_solve); the
+  // stencil force's joins the source w through FD^T here
+  const bool analytic = grad_accel && P->near_comps == 4;
+  const void* fd_g = analytic ? nullptr : grad_accel;
   {
     StageTimer st(P, ST_ADJ_SRC, s);
     if (P->f64_data()) {
-      CUDA_TRY(launch_adjoint_source<double>(static_cast<const double*>(grad_phi),
-                                             static_cast<const double*>(grad_accel), P->dims, 1.0 / P->dx,
-                                             static_cast<double*>(w), s));
+      CUDA_TRY(launch_adjoint_source<double>(static_cast<const double*>(grad_phi), static_cast<const double*>(fd_g),
+                                             P->dims, 1.0 / P->dx, static_cast<double*>(w), s));
     } else {
-      CUDA_TRY(launch_adjoint_source<float>(static_cast<const float*>(grad_phi),
-                                            static_cast<const float*>(grad_accel), P->dims, 1.0 / P->dx,
-                                            static_cast<float*>(w), s));
+      CUDA_TRY(launch_adjoint_source<float>(static_cast<const float*>(grad_phi), static_cast<const float*>(fd_g),
+                                            P->dims, 1.0 / P->dx, static_cast<float*>(w), s));
     }
   }
   // mult_order < order: the transpose runs the M2L with the orders swapped
   P->transposed = true;
+  P->adj_g = analytic ? grad_accel : nullptr;
   const fmm_status r =
       P->f64_data()
           ? run_solve<double>(P, static_cast<const double*>(w), static_cast<double*>(grad_rho), nullptr, s, true)
           : run_solve<float>(P, static_cast<const float*>(w), static_cast<float*>(grad_rho), nullptr, s, true);
   P->transposed = false;
+  P->adj_g = nullptr;
   return r;
 }
 
@@ -2932,6 +3036,16 @@ extern "C" fmm_status fmm_plan_tc_schedule(fmm_plan_t P, int what, int* prefix, 
   const bool span = what == TS_M2L ? P->span_m2l : what == TS_NEAR ? P->span_near : P->span_m2p;
   if (available) *available = (span ? 1 : 0) | (tp ? 2 : 0);
   if (prefix) *prefix = (tp || span) ? (tc_prefix(P, what) ? 1 : 0) : -1;
+  return FMM_OK;
+}
+
+extern "C" fmm_status fmm_plan_debug_timeout(fmm_plan_t P) {
+  g_last_error.clear();
+  if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
+  bool any = false;
+  for (int l = 2; l <= P->L; ++l) any = any || (P->lev[l].tc && !(l == P->L && P->m2p));
+  if (!any || !tc_prefix(P, TS_M2L)) return fail(FMM_ERR_ARG, "no M2L level of this plan runs the prefix schedule");
+  P->inject_timeout = true;
   return FMM_OK;
 }
 

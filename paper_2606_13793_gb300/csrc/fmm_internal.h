@@ -114,9 +114,11 @@ struct TreeTables {
 template <typename T>
 // Mfold (nullable, with harm): the folded components in the level's type,
 // rows of 8 (p+1)^2 values (the CUDA-core harmonic M2L reads them).
+// dip (nullable): dipole sources [3][cells], weights v_q adding v_q d/de_q (e^alpha)
+// (box units) per cell -- the transpose of the analytic force's L2P gradient.
 cudaError_t launch_p2m(const TreeTables& t, const T* rho, const int dims[3], const Level& leaf, T* Mleaf, T* rho_box,
                        void* Mhi, void* Mlo, void* rho_hi, void* rho_lo, int* flag, int harm, T* Mfold,
-                       cudaStream_t s);
+                       cudaStream_t s, const T* dip = nullptr);
 // M2M into the parent level; Mhi/Mlo (bf16 planes of the parent, harmonic
 // components when harm = 1) when non-NULL.
 template <typename Tc, typename Tp>
@@ -132,11 +134,19 @@ cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, cons
                        int harm, const Tc* Lred, cudaStream_t s);
 template <typename T>
 cudaError_t launch_zero(T* p, size_t count, cudaStream_t s);
+// dst = sc * src (count values)
+template <typename T>
+cudaError_t launch_scaled_copy(const T* src, size_t count, double sc, T* dst, cudaStream_t s);
 // Copy of a cell grid in the leaf level's parent-blocked box order
 // [parent][child][b^3] (phantom boxes zero).
 template <typename T>
 cudaError_t launch_cells_to_parent_blocks(const T* src, const int dims[3], const Level& leaf, int b, T* dst,
                                           cudaStream_t s);
+// [w, sc g_x, sc g_y, sc g_z] x b^3 per leaf box (g nullable: zeros), boxes in
+// grid order (parent_blocked = 0) or [parent][child] order (1).
+template <typename T>
+cudaError_t launch_cells_to_boxes4(const T* w, const T* g, double sc, const int dims[3], const Level& leaf, int b,
+                                   int parent_blocked, T* dst, cudaStream_t s);
 // near_box rows hold near_stride values per leaf box, the potential sums first.
 template <typename T>
 // m2p (nullable): final-stage M2P potentials, parent-blocked [parent][child][b^3], in the
@@ -144,10 +154,13 @@ template <typename T>
 cudaError_t launch_leaf_finish(const TreeTables& t, const Level& leaf, const T* Lleaf, const T* near_box,
                                int near_stride, const T* m2p, const int dims[3], double scale, T* phi, cudaStream_t s);
 // With the analytic acceleration: near_box rows are [potential, d/dx, d/dy,
-// d/dz] x b^3; accel = ascale (far gradient + near gradient).
+// d/dz] x b^3; accel = ascale (far gradient + near gradient).  m2p (nullable):
+// the final-stage M2P's [parent][child][potential, d/dx, d/dy, d/dz][b^3],
+// box units like the local expansion's terms.
 template <typename T>
 cudaError_t launch_leaf_finish_grad(const TreeTables& t, const Level& leaf, const T* Lleaf, const T* near_box,
-                                    const int dims[3], double scale, double ascale, T* phi, T* accel, cudaStream_t s);
+                                    const T* m2p, const int dims[3], double scale, double ascale, T* phi, T* accel,
+                                    cudaStream_t s);
 template <typename T>
 cudaError_t launch_fd_accel(const T* phi, const int dims[3], double inv_dx, T* accel, cudaStream_t s);
 template <typename T>
@@ -351,6 +364,7 @@ struct TpLaunch {
   int kind;       // TC_BF16X3 or TC_TF32
   int* err;
   int col_mapped; // as TcLaunch
+  int skip_first_a; // test hook: every CTA leaves its first activation stage unloaded (its waits time out)
   int16_t col_map[kTcMaxColMap];
 };
 

@@ -116,7 +116,8 @@ __global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(T) == 4) ? 2 : 1)
 //   accel_q = -G dx [ h^-2 sum_beta Lt_beta d/dxi_q ((x - c)/h)^beta + near_q ]
 template <int P, typename T>
 __global__ void __launch_bounds__(kThreads) leaf_finish_grad_kernel(Level leaf, const T* __restrict__ Lleaf,
-                                                                    const T* __restrict__ near_box, int nx, int ny,
+                                                                    const T* __restrict__ near_box,
+                                                                    const T* __restrict__ m2p, int nx, int ny,
                                                                     int nz, int b, T scale, T ascale,
                                                                     T* __restrict__ phi, T* __restrict__ accel) {
   constexpr int NC = ncoef_c(P);
@@ -133,6 +134,9 @@ __global__ void __launch_bounds__(kThreads) leaf_finish_grad_kernel(Level leaf, 
   const long long box = ((long long)B.z * leaf.n[1] + B.y) * leaf.n[0] + B.x;
   const int b3 = b * b * b;
   const T* nb = near_box + box * 4 * b3;
+  // final-stage M2P: the leaf interaction list's potential and its gradient
+  // at the cell centres, in box units like the local expansion's ([comp][b^3])
+  const T* mp = m2p ? m2p + (B.par * 8 + B.c) * (long long)(4 * b3) : nullptr;
   for (int k = 0; k < b; ++k) {
     const T zk = (T(k) + T(0.5)) * inv_b - T(0.5);
     T zpow[P + 1], dzpow[P + 1];
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) leaf_finish_grad_kernel(Level leaf, 
         u2[(a + bb) * (a + bb + 1) / 2 + bb] = s;
         u2z[(a + bb) * (a + bb + 1) / 2 + bb] = sz;
       }
-    if (sizeof(T) == 4 && b == 4) {
+    if (sizeof(T) == 4 && b == 4 && !mp) {
       // 16-byte loads of the four near columns and 16-byte stores of the
       // potential and the three force rows; the plane unrolled so the loads
       // of one row issue ahead of the previous row's arithmetic
@@ -245,6 +249,12 @@ __global__ void __launch_bounds__(kThreads) leaf_finish_grad_kernel(Level leaf, 
           sy = fma(sy, xi, u1y[a]);
           sz = fma(sz, xi, u1z[a]);
         }
+        if (mp) {
+          s += mp[e0 + i];
+          sx += mp[b3 + e0 + i];
+          sy += mp[2 * b3 + e0 + i];
+          sz += mp[3 * b3 + e0 + i];
+        }
         phi[row + i] = scale * fma(s, inv_b, nb[e0 + i]);
         const T ib2 = inv_b * inv_b;
         accel[row + i] = ascale * fma(sx, ib2, nb[b3 + e0 + i]);
@@ -259,18 +269,22 @@ __global__ void __launch_bounds__(kThreads) leaf_finish_grad_kernel(Level leaf, 
 
 template <typename T>
 cudaError_t launch_leaf_finish_grad(const TreeTables& t, const Level& leaf, const T* Lleaf, const T* near_box,
-                                    const int dims[3], double scale, double ascale, T* phi, T* accel, cudaStream_t s) {
+                                    const T* m2p, const int dims[3], double scale, double ascale, T* phi, T* accel,
+                                    cudaStream_t s) {
   const long long threads = leaf.npar * 8;
   if (threads == 0) return cudaSuccess;
   FMM_ORDER_SWITCH(t.p, (leaf_finish_grad_kernel<PP, T><<<grid_threads(threads), kThreads, 0, s>>>(
-                            leaf, Lleaf, near_box, dims[0], dims[1], dims[2], t.b, (T)scale, (T)ascale, phi, accel)));
+                            leaf, Lleaf, near_box, m2p, dims[0], dims[1], dims[2], t.b, (T)scale, (T)ascale, phi,
+                            accel)));
   return cudaGetLastError();
 }
 
 template cudaError_t launch_leaf_finish_grad<float>(const TreeTables&, const Level&, const float*, const float*,
-                                                    const int*, double, double, float*, float*, cudaStream_t);
+                                                    const float*, const int*, double, double, float*, float*,
+                                                    cudaStream_t);
 template cudaError_t launch_leaf_finish_grad<double>(const TreeTables&, const Level&, const double*, const double*,
-                                                     const int*, double, double, double*, double*, cudaStream_t);
+                                                     const double*, const int*, double, double, double*, double*,
+                                                     cudaStream_t);
 
 template <typename T>
 cudaError_t launch_leaf_finish(const TreeTables& t, const Level& leaf, const T* Lleaf, const T* near_box,
@@ -317,5 +331,54 @@ template cudaError_t launch_cells_to_parent_blocks<float>(const float*, const in
                                                           cudaStream_t);
 template cudaError_t launch_cells_to_parent_blocks<double>(const double*, const int*, const Level&, int, double*,
                                                            cudaStream_t);
+
+// The four input columns of the analytic force's transposed near field and
+// final-stage P2L, per leaf box: [w, sc g_x, sc g_y, sc g_z] x b^3 (g, the
+// force's adjoint input [3][cells], may be NULL: zeros).  parent_blocked = 0:
+// boxes in grid order (the near-field rows); 1: [parent][child] order, phantom
+// children zero (the P2L rows).
+template <typename T>
+__global__ void cells_to_boxes4_kernel(const T* __restrict__ w, const T* __restrict__ g, T sc, int nx, int ny, int nz,
+                                       Level leaf, int b, int parent_blocked, T* __restrict__ dst) {
+  const long long b3 = (long long)b * b * b;
+  const long long nbox = parent_blocked ? leaf.npar * 8 : (long long)leaf.n[0] * leaf.n[1] * leaf.n[2];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbox * b3) return;
+  const long long bi = i / b3;
+  const int cell = (int)(i % b3);
+  int bx, by, bz;
+  bool real = true;
+  if (parent_blocked) {
+    const Box B = box_of(leaf, bi);
+    bx = B.x, by = B.y, bz = B.z, real = B.real;
+  } else {
+    bx = (int)(bi % leaf.n[0]), by = (int)((bi / leaf.n[0]) % leaf.n[1]), bz = (int)(bi / ((long long)leaf.n[0] * leaf.n[1]));
+  }
+  T v[4] = {T(0), T(0), T(0), T(0)};
+  if (real) {
+    const int x = bx * b + cell % b, y = by * b + (cell / b) % b, z = bz * b + cell / (b * b);
+    const long long c = ((long long)z * ny + y) * nx + x, n = (long long)nx * ny * nz;
+    v[0] = w[c];
+    if (g)
+      for (int q = 0; q < 3; ++q) v[1 + q] = sc * g[q * n + c];
+  }
+  T* o = dst + bi * 4 * b3 + cell;
+  for (int q = 0; q < 4; ++q) o[q * b3] = v[q];
+}
+
+template <typename T>
+cudaError_t launch_cells_to_boxes4(const T* w, const T* g, double sc, const int dims[3], const Level& leaf, int b,
+                                   int parent_blocked, T* dst, cudaStream_t s) {
+  const long long nbox = parent_blocked ? leaf.npar * 8 : (long long)leaf.n[0] * leaf.n[1] * leaf.n[2];
+  const long long n = nbox * b * b * b;
+  if (n == 0) return cudaSuccess;
+  cells_to_boxes4_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, g, (T)sc, dims[0], dims[1], dims[2], leaf,
+                                                                        b, parent_blocked, dst);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cells_to_boxes4<float>(const float*, const float*, double, const int*, const Level&, int,
+                                                   int, float*, cudaStream_t);
+template cudaError_t launch_cells_to_boxes4<double>(const double*, const double*, double, const int*, const Level&,
+                                                    int, int, double*, cudaStream_t);
 
 }  // namespace fmmgb

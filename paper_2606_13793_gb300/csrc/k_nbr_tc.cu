@@ -172,6 +172,7 @@ __global__ void __maxnreg__(96)
         for (int j = 0; ok && j < nch; ++j, ++t) {
           const uint32_t sa = t % nA;
           if (!active || (int)(sa % G) != my_g) continue;
+          if (P.skip_first_a && t == 0) continue;  // test hook: nothing is copied, nothing waits on a copy
           if (!(ok = wait_fast(&a_empty[sa], ((t / nA) & 1) ^ 1, P.err, W_PROD_A))) break;
           unsigned char* dst = a_ring + sa * kAStage + my_plane * kAPlane;
           mbar_expect_tx(&a_full[sa], kAPlane);
@@ -183,7 +184,7 @@ __global__ void __maxnreg__(96)
     }
     if (!ok && active)  // let this lane's copies land before the CTA exits
       for (uint32_t i = (done > nA ? done - nA : 0); i < done; ++i)
-        if ((int)((i % nA) % G) == my_g) mbar_wait_drain(&a_full[i % nA], (i / nA) & 1);
+        if ((int)((i % nA) % G) == my_g && !(P.skip_first_a && i == 0)) mbar_wait_drain(&a_full[i % nA], (i / nA) & 1);
   } else if (warp < kWarpI0) {
     // ---------------- weight producers: one warp per owner ----------------
     // Owner q's pieces, in its reading order, go round-robin through its own

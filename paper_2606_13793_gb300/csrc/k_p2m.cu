@@ -27,11 +27,15 @@ __host__ __device__ constexpr int ncoef_parity(int h) {
   return n;
 }
 
-template <int P, typename T, int h>
+// DIP: dipole sources as well (the transpose of the analytic force's far
+// part, the gradient of L2P): dip = [3][cells] weights v_q, each cell adding
+// v_q d/de_q (e^alpha) (box units) to the monomial moments of its density.
+template <int P, typename T, int h, bool DIP>
 __device__ __forceinline__ void p2m_body(const Box& B, const T* __restrict__ rho, int nx, int ny, int b,
                                          const Level& leaf, T* __restrict__ Ms, T* __restrict__ Mr,
                                          T* __restrict__ rho_box, __nv_bfloat16* __restrict__ rhi,
-                                         __nv_bfloat16* __restrict__ rlo, int* __restrict__ flag) {
+                                         __nv_bfloat16* __restrict__ rlo, int* __restrict__ flag,
+                                         const T* __restrict__ dip, long long ncell) {
   constexpr int NC = ncoef_c(P);
   constexpr int NH = ncoef_parity<P>(h);
   T acc[NH > 0 ? NH : 1];  // this thread's coefficients, in canonical order restricted to parity h of c
@@ -40,15 +44,26 @@ __device__ __forceinline__ void p2m_body(const Box& B, const T* __restrict__ rho
   bool bad = false;  // non-finite density (reported through the plan's flag)
   // One z-plane of the box: rows j = 0 .. b-1 of cells m[j][i] -> partial sums
   // t2[(a, bb)] = sum_j yj^bb sum_i m xi^a, then acc += t2 zk^c (this parity).
-  auto plane = [&](const T* mrow, int k, const T inv_b) {
-    T t2[(P + 1) * (P + 2) / 2];
+  // vrow (DIP): the plane's three dipole rows, [3][b * b]
+  auto plane = [&](const T* mrow, const T* vrow, int k, const T inv_b) {
+    constexpr int N2 = (P + 1) * (P + 2) / 2;
+    T t2[N2], t2z[DIP ? N2 : 1];
 #pragma unroll
-    for (int q = 0; q < (P + 1) * (P + 2) / 2; ++q) t2[q] = T(0);
+    for (int q = 0; q < N2; ++q) t2[q] = T(0);
+    if (DIP) {
+#pragma unroll
+      for (int q = 0; q < N2; ++q) t2z[q] = T(0);
+    }
     for (int j = 0; j < b; ++j) {
       const T yj = (T(j) + T(0.5)) * inv_b - T(0.5);
-      T t1[P + 1];
+      // t1: sum_i m xi^a (+ v_x a xi^(a-1)); t1y, t1z: sum_i v_y xi^a, v_z xi^a
+      T t1[P + 1], t1y[DIP ? P + 1 : 1], t1z[DIP ? P + 1 : 1];
 #pragma unroll
       for (int a = 0; a <= P; ++a) t1[a] = T(0);
+      if (DIP) {
+#pragma unroll
+        for (int a = 0; a <= P; ++a) t1y[a] = T(0), t1z[a] = T(0);
+      }
       for (int i = 0; i < b; ++i) {
         const T mi = mrow[j * b + i];
         bad |= !isfinite(mi);
@@ -59,13 +74,35 @@ __device__ __forceinline__ void p2m_body(const Box& B, const T* __restrict__ rho
           t1[a] += w;
           w *= xi;
         }
+        if (DIP) {
+          const T vx = vrow[j * b + i], vy = vrow[b * b + j * b + i], vz = vrow[2 * b * b + j * b + i];
+          T pw = vx, wy = vy, wz = vz;  // vx xi^(a-1), vy xi^a, vz xi^a
+#pragma unroll
+          for (int a = 0; a <= P; ++a) {
+            if (a >= 1) {
+              t1[a] = fma(T(a), pw, t1[a]);
+              pw *= xi;
+            }
+            t1y[a] += wy;
+            t1z[a] += wz;
+            wy *= xi;
+            wz *= xi;
+          }
+        }
       }
       T ypow[P + 1];
       powers<P, T>(yj, ypow);
 #pragma unroll
       for (int a = 0; a <= P; ++a)
 #pragma unroll
-        for (int bb = 0; a + bb <= P; ++bb) t2[(a + bb) * (a + bb + 1) / 2 + bb] += t1[a] * ypow[bb];
+        for (int bb = 0; a + bb <= P; ++bb) {
+          T v = t1[a] * ypow[bb];
+          if (DIP) {
+            if (bb >= 1) v = fma(t1y[a], T(bb) * ypow[bb - 1], v);
+            t2z[(a + bb) * (a + bb + 1) / 2 + bb] = fma(t1z[a], ypow[bb], t2z[(a + bb) * (a + bb + 1) / 2 + bb]);
+          }
+          t2[(a + bb) * (a + bb + 1) / 2 + bb] += v;
+        }
     }
     const T zk = (T(k) + T(0.5)) * inv_b - T(0.5);
     T zpow[P + 1];
@@ -80,6 +117,7 @@ __device__ __forceinline__ void p2m_body(const Box& B, const T* __restrict__ rho
           const int a = n - bc, bb = bc - cc;
           if ((cc & 1) != h) continue;
           acc[q] = fma(t2[(a + bb) * (a + bb + 1) / 2 + bb], zpow[cc], acc[q]);
+          if (DIP && cc >= 1) acc[q] = fma(t2z[(a + bb) * (a + bb + 1) / 2 + bb], T(cc) * zpow[cc - 1], acc[q]);
           ++q;
         }
   };
@@ -87,7 +125,7 @@ __device__ __forceinline__ void p2m_body(const Box& B, const T* __restrict__ rho
     const T inv_b = T(1) / T(b);
     const long long box = ((long long)B.z * leaf.n[1] + B.y) * leaf.n[0] + B.x;
     const int b3 = b * b * b;
-    if (sizeof(T) == 4 && b == 4) {
+    if (sizeof(T) == 4 && b == 4 && !DIP) {
       // two z-planes (8 rows of 16 bytes) in flight per thread before any use
       for (int k0 = 0; k0 < 4; k0 += 2) {
         float4 v[8];
@@ -113,25 +151,29 @@ __device__ __forceinline__ void p2m_body(const Box& B, const T* __restrict__ rho
             }
           }
         }
-        plane(reinterpret_cast<const T*>(&v[0]), k0, inv_b);
-        plane(reinterpret_cast<const T*>(&v[4]), k0 + 1, inv_b);
+        plane(reinterpret_cast<const T*>(&v[0]), nullptr, k0, inv_b);
+        plane(reinterpret_cast<const T*>(&v[4]), nullptr, k0 + 1, inv_b);
       }
     } else {
       for (int k = 0; k < b; ++k) {
         T mrow[64];  // b <= 8: one plane of b x b cells
+        T vrow[DIP ? 3 * 64 : 1];
         for (int j = 0; j < b; ++j) {
-          const T* row = rho + ((long long)(B.z * b + k) * ny + (B.y * b + j)) * nx + (long long)B.x * b;
+          const long long c0 = ((long long)(B.z * b + k) * ny + (B.y * b + j)) * nx + (long long)B.x * b;
+          const T* row = rho + c0;
           const long long e0 = box * b3 + (k * b + j) * b;
           for (int i = 0; i < b; ++i) {
             const T m = row[i];
             mrow[j * b + i] = m;
+            if (DIP)
+              for (int q = 0; q < 3; ++q) vrow[q * b * b + j * b + i] = dip[q * ncell + c0 + i];
             if (h == 0) {
               if (rho_box) rho_box[e0 + i] = m;
               if (rhi) store_split(rhi, rlo, (size_t)(e0 + i), m);
             }
           }
         }
-        plane(mrow, k, inv_b);
+        plane(mrow, DIP ? vrow : nullptr, k, inv_b);
       }
     }
   }
@@ -181,13 +223,14 @@ __device__ __forceinline__ void p2m_body(const Box& B, const T* __restrict__ rho
 // A block (256 threads, 128 boxes) covers kP2mParents whole parents, so its
 // output is one contiguous run of parent rows: staged in shared memory and
 // written with 16-byte stores (FP32 rows, and the bf16 hi/lo planes).
-template <int P, typename T>
+template <int P, typename T, bool DIP>
 __global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho, int nx, int ny, int b, Level leaf,
                                                        T* __restrict__ Mleaf, __nv_bfloat16* __restrict__ Mhi,
                                                        __nv_bfloat16* __restrict__ Mlo, T* __restrict__ rho_box,
                                                        __nv_bfloat16* __restrict__ rhi,
                                                        __nv_bfloat16* __restrict__ rlo, int* __restrict__ flag,
-                                                       int harm, T* __restrict__ Mfold) {
+                                                       int harm, T* __restrict__ Mfold, const T* __restrict__ dip,
+                                                       long long ncell) {
   constexpr int NC = ncoef_c(P);
   constexpr int ROW = 8 * NC;     // values per parent row
   constexpr int ROWP = ROW + 8;   // staged row pitch
@@ -200,9 +243,9 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho
   const Box B = box_of(leaf, (w >> 1) * 32 + (t & 31));
   if (B.par < leaf.npar) {
     if (w & 1)
-      p2m_body<P, T, 1>(B, rho, nx, ny, b, leaf, Ms, Mr, rho_box, rhi, rlo, flag);
+      p2m_body<P, T, 1, DIP>(B, rho, nx, ny, b, leaf, Ms, Mr, rho_box, rhi, rlo, flag, dip, ncell);
     else
-      p2m_body<P, T, 0>(B, rho, nx, ny, b, leaf, Ms, Mr, rho_box, rhi, rlo, flag);
+      p2m_body<P, T, 0, DIP>(B, rho, nx, ny, b, leaf, Ms, Mr, rho_box, rhi, rlo, flag, dip, ncell);
   }
   __syncthreads();
   const long long p0 = (long long)blockIdx.x * kP2mParents;
@@ -243,10 +286,27 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho
   }
 }
 
+template <int P, typename T, bool DIP>
+cudaError_t p2m_launch_dip(unsigned blocks, size_t smem, size_t attr_bytes, cudaStream_t s, const T* rho, int nx,
+                           int ny, int b, Level leaf, T* Mleaf, __nv_bfloat16* Mhi, __nv_bfloat16* Mlo, T* rho_box,
+                           __nv_bfloat16* rhi, __nv_bfloat16* rlo, int* flag, int harm, T* Mfold, const T* dip,
+                           long long ncell) {
+  static bool attr = false;
+  if (!attr && attr_bytes > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(p2m_kernel<P, T, DIP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)attr_bytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  p2m_kernel<P, T, DIP><<<blocks, kThreads, smem, s>>>(rho, nx, ny, b, leaf, Mleaf, Mhi, Mlo, rho_box, rhi, rlo, flag,
+                                                       harm, Mfold, dip, ncell);
+  return cudaGetLastError();
+}
+
 template <int P, typename T>
 cudaError_t p2m_launch(unsigned blocks, cudaStream_t s, const T* rho, int nx, int ny, int b, Level leaf, T* Mleaf,
                 __nv_bfloat16* Mhi, __nv_bfloat16* Mlo, T* rho_box, __nv_bfloat16* rhi, __nv_bfloat16* rlo, int* flag,
-                int harm, T* Mfold) {
+                int harm, T* Mfold, const T* dip, long long ncell) {
   constexpr size_t full = (size_t)kP2mParents * (8 * ncoef_c(P) + 8) * sizeof(T);
   // staged harmonic rows, where they fit beside the full ones (the plan folds
   // nothing at FP64 order 8, which would not)
@@ -254,16 +314,11 @@ cudaError_t p2m_launch(unsigned blocks, cudaStream_t s, const T* rho, int nx, in
   constexpr size_t red = full + red0 <= 227 * 1024 ? red0 : 0;
   if (harm && (Mhi || Mfold) && red == 0) return cudaErrorInvalidValue;
   const size_t smem = full + ((harm && (Mhi || Mfold)) ? red : 0);
-  static bool attr = false;
-  if (!attr && full + red > 48 * 1024) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(p2m_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(full + red));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  p2m_kernel<P, T><<<blocks, kThreads, smem, s>>>(rho, nx, ny, b, leaf, Mleaf, Mhi, Mlo, rho_box, rhi, rlo, flag,
-                                                  harm, Mfold);
-  return cudaGetLastError();
+  if (dip)
+    return p2m_launch_dip<P, T, true>(blocks, smem, full + red, s, rho, nx, ny, b, leaf, Mleaf, Mhi, Mlo, rho_box, rhi,
+                                      rlo, flag, harm, Mfold, dip, ncell);
+  return p2m_launch_dip<P, T, false>(blocks, smem, full + red, s, rho, nx, ny, b, leaf, Mleaf, Mhi, Mlo, rho_box, rhi,
+                                     rlo, flag, harm, Mfold, nullptr, ncell);
 }
 
 }  // namespace
@@ -271,20 +326,21 @@ cudaError_t p2m_launch(unsigned blocks, cudaStream_t s, const T* rho, int nx, in
 template <typename T>
 cudaError_t launch_p2m(const TreeTables& t, const T* rho, const int dims[3], const Level& leaf, T* Mleaf, T* rho_box,
                        void* Mhi, void* Mlo, void* rho_hi, void* rho_lo, int* flag, int harm, T* Mfold,
-                       cudaStream_t s) {
+                       cudaStream_t s, const T* dip) {
   const long long threads = leaf.npar * 16;  // two threads per box
   if (threads == 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   FMM_ORDER_SWITCH(t.p, (e = p2m_launch<PP, T>(grid_threads(threads), s,
                             rho, dims[0], dims[1], t.b, leaf, Mleaf, static_cast<__nv_bfloat16*>(Mhi),
                             static_cast<__nv_bfloat16*>(Mlo), rho_box, static_cast<__nv_bfloat16*>(rho_hi),
-                            static_cast<__nv_bfloat16*>(rho_lo), flag, harm, Mfold)));
+                            static_cast<__nv_bfloat16*>(rho_lo), flag, harm, Mfold, dip,
+                            (long long)dims[0] * dims[1] * dims[2])));
   return e;
 }
 
 template cudaError_t launch_p2m<float>(const TreeTables&, const float*, const int*, const Level&, float*, float*,
-                                       void*, void*, void*, void*, int*, int, float*, cudaStream_t);
+                                       void*, void*, void*, void*, int*, int, float*, cudaStream_t, const float*);
 template cudaError_t launch_p2m<double>(const TreeTables&, const double*, const int*, const Level&, double*, double*,
-                                        void*, void*, void*, void*, int*, int, double*, cudaStream_t);
+                                        void*, void*, void*, void*, int*, int, double*, cudaStream_t, const double*);
 
 }  // namespace fmmgb

@@ -43,7 +43,24 @@ __global__ void export_level_kernel(const T* __restrict__ src, Level lv, int wha
   }
 }
 
+template <typename T>
+__global__ void scaled_copy_kernel(const T* __restrict__ src, size_t count, T sc, T* __restrict__ dst) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = sc * src[i];
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_scaled_copy(const T* src, size_t count, double sc, T* dst, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  size_t blocks = (count + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  scaled_copy_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(src, count, (T)sc, dst);
+  return cudaGetLastError();
+}
+template cudaError_t launch_scaled_copy<float>(const float*, size_t, double, float*, cudaStream_t);
+template cudaError_t launch_scaled_copy<double>(const double*, size_t, double, double*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_zero(T* p, size_t count, cudaStream_t s) {

@@ -756,24 +756,26 @@ bool tp_m2l_case(int kind, int p, int mult_order, int local_order, bool harm, bo
   });
 }
 
-bool tp_m2p_case(int kind, int p, int b, int mult_order, bool harm, bool& built) {
-  MultiIndex mi;
+bool tp_m2p_case(int kind, int p, int b, int mult_order, bool harm, bool& built, int comps = 1) {
+  MultiIndex mi, mi1;
   mi.init(p);
+  mi1.init(p + 1);
   if (mult_order >= 0) mi.mo = mult_order;
   M2pTable tab;
-  tab.build(mi, b);
+  tab.build(comps > 1 ? mi1 : mi, b);
   TpHost H;
   char name[64];
-  std::snprintf(name, sizeof name, "m2p p=%d mo=%d b=%d%s", p, mi.mo, b, harm ? " harmonic" : "");
-  built = build_tp_m2p(mi, tab, kind, H, harm);
+  std::snprintf(name, sizeof name, "m2p p=%d mo=%d b=%d%s%s", p, mi.mo, b, harm ? " harmonic" : "",
+                comps > 1 ? " force" : "");
+  built = build_tp_m2p(mi, tab, kind, H, harm, comps);
   if (!built) {
     std::printf("%-28s %-6s span schedule (no prefix schedule)\n", name, kind == TC_BF16X3 ? "bf16x3" : "tf32");
     return true;
   }
   const std::vector<int> red = harmonic_components(mi);
   const int nk = harm ? (int)red.size() : mi.nc;
-  return tp_check(name, kind, H, 8 * b * b * b, 8 * nk, [&](int d, int k, int n) {
-    return harm ? m2p_entry(mi, tab, d, red[k / 8] * 8 + k % 8, n) : m2p_entry(mi, tab, d, k, n);
+  return tp_check(name, kind, H, 8 * comps * b * b * b, 8 * nk, [&](int d, int k, int n) {
+    return harm ? m2p_entry(mi, tab, d, red[k / 8] * 8 + k % 8, n, comps) : m2p_entry(mi, tab, d, k, n, comps);
   });
 }
 
@@ -812,6 +814,9 @@ int prefix_check(int& built_count) {
         for (bool harm : {false, true}) ok &= tp_m2p_case(kind, p, b, -1, harm, built), built_count += built;
   for (int b : {2, 4, 8})
     for (int comps : {1, 4}) ok &= tp_near_case(b, comps, built), built_count += built;
+  for (int kind : {TC_BF16X3, TC_TF32})  // the final-stage M2P with the force's gradient columns
+    for (int b : {2, 4})
+      for (bool harm : {false, true}) ok &= tp_m2p_case(kind, 6, b, -1, harm, built, 4), built_count += built;
   return ok ? 0 : 1;
 }
 
@@ -1090,6 +1095,25 @@ bool dump_m2p(const std::string& dir, int p, int b) {
   return write_table(dir + name, W);
 }
 
+// Final-stage M2P weights with the analytic force's three gradient columns
+// [27][8 nc][8 x 4 b^3] (neighbour parent, alpha * 8 + source child,
+// target child * 4 b^3 + component * b^3 + cell), Taylor table to order p + 1.
+bool dump_m2p_grad(const std::string& dir, int p, int b) {
+  MultiIndex mi, mi1;
+  mi.init(p);
+  mi1.init(p + 1);
+  M2pTable tab;
+  tab.build(mi1, b);
+  const int K = 8 * mi.nc, N = 8 * 4 * b * b * b;
+  std::vector<double> W((size_t)27 * K * N);
+  for (int d = 0; d < 27; ++d)
+    for (int k = 0; k < K; ++k)
+      for (int n = 0; n < N; ++n) W[((size_t)d * K + k) * N + n] = m2p_entry(mi, tab, d, k, n, 4);
+  char name[64];
+  std::snprintf(name, sizeof name, "/m2pg_p%d_b%d.bin", p, b);
+  return write_table(dir + name, W);
+}
+
 // Near-field weights [27][b^3][4 b^3] (neighbour box, source cell,
 // component * b^3 + target cell; components: g, then the three force columns).
 bool dump_near(const std::string& dir, int b) {
@@ -1329,7 +1353,7 @@ int main(int argc, char** argv) {
     if (argc < 3) return 2;
     const std::string dir = argv[2];
     const bool ok = dump_m2l(dir, 3, 3, 3) && dump_m2l(dir, 4, 4, 4) && dump_m2l(dir, 4, 3, 4) &&
-                    dump_m2l(dir, 4, 4, 3) && dump_m2p(dir, 3, 2) && dump_m2p(dir, 4, 4) && dump_near(dir, 2) &&
+                    dump_m2l(dir, 4, 4, 3) && dump_m2p(dir, 3, 2) && dump_m2p(dir, 4, 4) && dump_m2p_grad(dir, 3, 2) && dump_m2p_grad(dir, 4, 4) && dump_near(dir, 2) &&
                     dump_near(dir, 4) && dump_shifts<3>(dir) && dump_shifts<6>(dir) && dump_shifts<8>(dir);
     return ok ? 0 : 1;
   }

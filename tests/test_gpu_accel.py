@@ -1,6 +1,8 @@
 """Analytic acceleration (accel = "analytic": the gradient of the leaf local
-expansions plus the near-field pair forces) against the oracle's analytic
-force, at every precision, on tensor cores and CUDA cores.
+expansions plus the near-field pair forces; with the paper's final stage the
+gradient of the leaf interaction list's M2P at the cell centres too) against
+the oracle's analytic force, at every precision, on tensor cores and CUDA
+cores.
 
 Tolerances (relative L2 over all components): FP64 1e-10 (rounding order);
 FP32 1e-5 (no stencil here, so the force carries the potential's relative
@@ -32,9 +34,11 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
-def solve(rho, b, p, prec, dx=1.0, G=1.0):
+def solve(rho, b, p, prec, dx=1.0, G=1.0, final_stage="m2l", m2p_schedule=None):
     nz, ny, nx = rho.shape
-    plan = fmm.FMMPlan((nx, ny, nz), p, b, prec, dx=dx, G=G, accel="analytic")
+    plan = fmm.FMMPlan((nx, ny, nz), p, b, prec, dx=dx, G=G, accel="analytic", final_stage=final_stage)
+    if m2p_schedule is not None:
+        plan.set_tc_schedule("m2p", m2p_schedule)
     r = torch.from_numpy(np.ascontiguousarray(rho)).cuda().to(plan.dtype)
     phi, acc = plan.solve(r, accel=True)
     torch.cuda.synchronize()
@@ -83,10 +87,100 @@ def test_analytic_accel_full_size_sampled(orc):
     plan.close()
 
 
-def test_analytic_accel_adjoint_of_accel_is_rejected():
-    plan = fmm.FMMPlan((32, 32, 32), 4, 4, "fp32", accel="analytic")
-    g = torch.zeros(3, 32, 32, 32, device="cuda")
-    with pytest.raises(fmm.FMMError) as e:
-        plan.solve_adjoint(grad_accel=g)
-    assert e.value.status == 2
+def _adjoint(gphi, ga, b, p, prec, dx, G, final_stage="m2l"):
+    nz, ny, nx = (gphi if gphi is not None else ga[0]).shape
+    plan = fmm.FMMPlan((nx, ny, nz), p, b, prec, dx=dx, G=G, accel="analytic", final_stage=final_stage)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda().to(plan.dtype)  # noqa: E731
+    g = plan.solve_adjoint(grad_phi=t(gphi) if gphi is not None else None, grad_accel=t(ga) if ga is not None else None)
+    torch.cuda.synchronize()
+    plan.check()
+    out = g.double().cpu().numpy()
     plan.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+def test_adjoint_of_the_analytic_force_matches_oracle(orc, prec):
+    """grad_rho of <g_phi, phi> + <g_a, accel> with accel the analytic force:
+    the GPU's transposed pipeline (dipole P2M sources for the force's L2P
+    gradient, the near pair forces transposed into the same contraction as
+    the potential's) against the oracle's explicit transpose chain."""
+    rng = np.random.default_rng(31)
+    shape, b, p, dx, G = (48, 32, 40), 4, 6, 0.3, 1.7
+    gphi = rng.standard_normal(shape[::-1])
+    ga = rng.standard_normal((3,) + shape[::-1])
+    ref = orc.adjoint(gphi, ga, b, p, dx=dx, G=G, analytic=True)
+    got = _adjoint(gphi, ga, b, p, prec, dx, G)
+    err = rel(got, ref)
+    print(f"{prec}: adjoint of the analytic force, rel err {err:.2e}")
+    assert err <= {"fp64": 1e-10, "fp32": 1e-5, "bf16x3": 1e-5}[prec]
+    # the force part alone
+    ref_f = orc.adjoint(np.zeros(shape[::-1]), ga, b, p, dx=dx, G=G, analytic=True)
+    got_f = _adjoint(None, ga, b, p, prec, dx, G)
+    assert rel(got_f, ref_f) <= {"fp64": 1e-10, "fp32": 1e-5, "bf16x3": 1e-5}[prec]
+
+
+@pytest.mark.parametrize("leaf", [2, 8])
+def test_adjoint_of_the_analytic_force_other_leaf_sizes(orc, leaf):
+    rng = np.random.default_rng(leaf)
+    shape, p = (32, 24, 40), 4
+    gphi = rng.standard_normal(shape[::-1])
+    ga = rng.standard_normal((3,) + shape[::-1])
+    ref = orc.adjoint(gphi, ga, leaf, p, analytic=True)
+    assert rel(_adjoint(gphi, ga, leaf, p, "fp64", 1.0, 1.0), ref) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_adjoint_of_the_analytic_force_with_m2p_is_its_transpose(prec):
+    """Final stage M2P: <g_phi, phi(rho)> + <g_a, accel(rho)> equals
+    <adjoint(g_phi, g_a), rho>, the forward solves being the ones held to
+    the oracle in test_analytic_accel_m2p_*; FP64 to rounding, bf16x3 to the
+    split products' error."""
+    rng = np.random.default_rng(5)
+    shape, b, p, dx, G = (40, 32, 48), 4, 6, 0.4, 1.3
+    rho = rng.standard_normal(shape[::-1])
+    gphi = rng.standard_normal(shape[::-1])
+    ga = rng.standard_normal((3,) + shape[::-1])
+    phi, acc = solve(rho, b, p, prec, dx=dx, G=G, final_stage="m2p")
+    lhs = np.vdot(gphi, phi) + np.vdot(ga, acc)
+    at = _adjoint(gphi, ga, b, p, prec, dx, G, final_stage="m2p")
+    rhs = np.vdot(at, rho)
+    scale = np.abs(gphi).sum() * np.abs(phi).max() + np.abs(ga).sum() * np.abs(acc).max()
+    print(f"{prec} m2p: <g, A rho> {lhs:.12e}, <A^T g, rho> {rhs:.12e}")
+    assert abs(lhs - rhs) <= {"fp64": 1e-12, "bf16x3": 1e-6}[prec] * scale
+
+
+def _m2p_schedules(b, p, prec):
+    """The tensor-core M2P schedules a plan of this kind has (None: CUDA cores)."""
+    plan = fmm.FMMPlan((32, 32, 32), p, b, prec, accel="analytic", final_stage="m2p")
+    cur, avail = plan.tc_schedule("m2p")
+    plan.close()
+    return sorted(avail) if cur is not None else [None]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "tf32"])
+def test_analytic_accel_m2p_final_stage_matches_oracle(orc, prec):
+    """The paper's final stage (Sec. 4) with the analytic force: the leaf
+    interaction list's M2P gradients at the cell centres (derivative tensors
+    one order above the multipoles), on every M2P schedule the plan has."""
+    rho = inputs.lognormal((64, 48, 80), seed=13).astype(np.float64)
+    ref = orc.fmm_accel(rho, 4, 6, dx=0.5, G=2.0, final_stage="m2p")
+    ref_phi = orc.fmm_m2p(rho, 4, 6, dx=0.5, G=2.0)
+    tol = {"fp64": 1e-9, "fp32": 1e-5, "bf16x3": 1e-5, "tf32": 1e-3}[prec]
+    for sched in _m2p_schedules(4, 6, prec):
+        phi, acc = solve(rho, 4, 6, prec, dx=0.5, G=2.0, final_stage="m2p", m2p_schedule=sched)
+        err, perr = rel(acc, ref), rel(phi, ref_phi)
+        print(f"{prec} m2p ({sched}): analytic accel rel err {err:.2e}, phi {perr:.2e}")
+        assert err <= tol, sched
+        assert perr <= {"fp64": 1e-10, "fp32": 1e-5, "bf16x3": 1e-5, "tf32": 1e-3}[prec], sched
+
+
+@pytest.mark.parametrize("leaf", [2, 8])
+def test_analytic_accel_m2p_other_leaf_sizes(orc, leaf):
+    rho = inputs.gaussian_blobs((32, 48, 40), seed=6)
+    ref = orc.fmm_accel(rho, leaf, 4, final_stage="m2p")
+    for prec in ("fp64", "bf16x3"):
+        _, acc = solve(rho, leaf, 4, prec, final_stage="m2p")
+        err = rel(acc, ref)
+        print(f"leaf {leaf} {prec} m2p: analytic accel rel err {err:.2e}")
+        assert err <= {"fp64": 1e-9, "bf16x3": 1e-5}[prec], (leaf, prec)

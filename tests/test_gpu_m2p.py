@@ -64,9 +64,11 @@ def test_m2p_more_accurate_than_m2l_l2p(orc):
     assert rel(solve(rho, 4, 4, "fp64"), d) < rel(m2l, d)
 
 
-def test_m2p_rejects_analytic_accel():
-    with pytest.raises(fmm.FMMError):
-        fmm.FMMPlan((32, 32, 32), 4, 4, "fp32", final_stage="m2p", accel="analytic")
+def test_m2p_accepts_analytic_accel():
+    """The analytic force with the paper's final stage is built (its parity
+    with the oracle is in test_gpu_accel.py)."""
+    plan = fmm.FMMPlan((32, 32, 32), 4, 4, "fp32", final_stage="m2p", accel="analytic")
+    plan.close()
 
 
 @pytest.mark.parametrize("shape,b,p", [((24, 16, 20), 4, 4), ((16, 24, 32), 2, 3), ((32, 32, 32), 8, 4)])

@@ -192,6 +192,38 @@ def test_m2p_table_equals_the_oracle_derivatives(orc, tables, p, b):
                 np.testing.assert_allclose(got[:, cell], ref, rtol=1e-11, atol=1e-13 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("p,b", [(3, 2), (4, 4)])
+def test_m2p_gradient_table_equals_the_oracle_derivatives(orc, tables, p, b):
+    """The final-stage M2P's force columns (App. C, Sec. 4): the derivative of
+    the potential at a cell in the target's x_q, in leaf-box units, is
+    (-1)^|alpha| / alpha! D_{alpha + e_q}(R), D = the oracle's derivative
+    tensor of -1/r to order p + 1; column 0 of each child block is the
+    potential table itself."""
+    nc = orc.ncoef(p)
+    b3 = b ** 3
+    W = np.fromfile(tables / f"m2pg_p{p}_b{b}.bin").reshape(27, 8 * nc, 8, 4, b3)
+    W1 = np.fromfile(tables / f"m2p_p{p}_b{b}.bin").reshape(27, 8 * nc, 8, b3)
+    np.testing.assert_array_equal(W[:, :, :, 0, :], W1)
+    idx = orc.index(p)
+    idx1 = {tuple(a): i for i, a in enumerate(orc.index(p + 1))}
+    sign_fact = np.where(idx.sum(1) % 2, -1.0, 1.0) / _factorials(idx)
+    shifted = [np.array([idx1[tuple(a + e)] for a in idx]) for e in np.eye(3, dtype=int)]
+    for d in range(27):
+        D = _offsets(d)
+        for cs, ct in itertools.product(range(8), range(8)):
+            u = _child_offset(ct, cs, D)
+            got = W[d, cs::8, ct]  # [alpha, comp, cell]
+            if np.abs(u).max() < 2:
+                assert not got.any()
+                continue
+            for cell in range(b3):
+                e = np.array([cell % b, (cell // b) % b, cell // (b * b)], dtype=float)
+                Dt = orc.dtensor(u + (e + 0.5) / b - 0.5, p + 1)
+                for q in range(3):
+                    ref = sign_fact * Dt[shifted[q]]
+                    np.testing.assert_allclose(got[:, 1 + q, cell], ref, rtol=1e-11, atol=1e-13 * np.abs(ref).max())
+
+
 @pytest.mark.parametrize("b", [2, 4])
 def test_near_table_equals_the_kernel(tables, b):
     """Near field (eq. direct), cell units: g(r) = -1/|r| with g(0) = -1, and
