@@ -58,7 +58,7 @@ def parse():
                     help="bf16x3: tensor-core M2L on every Cartesian component instead of the (p+1)^2 harmonic ones")
     ap.add_argument("--final-stage", default="m2l", choices=["m2l", "m2p"],
                     help="leaf level by M2L + L2P (m2l) or by the interaction list evaluated at the cells (m2p)")
-    ap.add_argument("--coarse", default="fp64", choices=["fp64", "fp32"],
+    ap.add_argument("--coarse", default="fp32", choices=["fp64", "fp32"],
                     help="precision of the coarse M2L levels of the mixed precisions (CUDA cores)")
     ap.add_argument("--fp64-levels", type=int, default=3,
                     help="tensor-core precisions: M2L levels 2 .. 1+N run in FP64 on the CUDA cores (default 3, "
@@ -518,7 +518,7 @@ def main():
     workload = f"{n}^3 p={p} leaf {b} {args.precision}" + (" m2p" if args.final_stage == "m2p" else "") + \
         (" harmonic" if harmonic else "") + \
         (f" fp64 levels {args.fp64_levels}" if tc_prec and args.fp64_levels != 3 else "") + \
-        (" coarse fp32" if tc_prec and args.coarse == "fp32" else "")
+        (" coarse fp64" if tc_prec and args.coarse == "fp64" else "")
     traffic = profiled_traffic(dom + "/" + args.precision, workload)
     d = per_kernel[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": "TFLOP/s",

@@ -116,16 +116,22 @@ typedef struct {
                          holds M2L weights with locals to mult_order, which
                          fmm_solve_adjoint runs.  Start from fmm_default_opts
                          (a zeroed struct means monopoles only)               */
-  int coarse_fp32;    /* mixed precisions: 0 (default) the coarse M2L levels
-                         (n_fp64_levels of them) in FP64; 1: in FP32 on the
-                         CUDA cores, harmonic components -- they are kept off
-                         the tensor cores for accuracy (the coarse levels carry
-                         the bulk of phi, where the split products' error
-                         counts most), which FP32 already gives            */
+  int coarse_fp32;    /* mixed precisions: the coarse M2L levels (n_fp64_levels
+                         of them) are kept off the tensor cores for accuracy
+                         (they carry the bulk of phi, where the split
+                         products' error counts most); 1 (default): in FP32
+                         on the CUDA cores, harmonic components, which
+                         already gives that accuracy (512^3 p = 6 bf16x3:
+                         6.7e-7 against the oracle, 7.40 ms a step); 0: in
+                         FP64, Cartesian (6.2e-7, 7.98 ms: at 1.25 TFLOP/s the
+                         FP64 work runs beside the tensor-core levels and
+                         slows them; at p = 8 it sets the step, 22.7 against
+                         11.95 ms)                                           */
   int reserved[1];    /* must be zero */
 } fmm_opts;
 
-/* Default options: FMM_FP32, n_fp64_levels = 3, accel = 1, mult_order = -1. */
+/* Default options: FMM_FP32, n_fp64_levels = 3, accel = 1, mult_order = -1,
+ * coarse_fp32 = 1. */
 void fmm_default_opts(fmm_opts* opts);
 
 /*

@@ -177,7 +177,7 @@ class FMMPlan:
 
     def __init__(self, shape, order: int = 6, leaf: int = 4, precision: str = "fp32", dx: float = 1.0,
                  G: float = 1.0, n_fp64_levels: int = 3, accel=True, final_stage: str = "m2l", harmonic=True,
-                 mult_order=None, stream=None, coarse: str = "fp64"):
+                 mult_order=None, stream=None, coarse: str = "fp32"):
         import torch
 
         self.lib = load()

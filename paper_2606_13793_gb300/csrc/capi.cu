@@ -2016,6 +2016,7 @@ void fmm_default_opts(fmm_opts* o) {
   o->n_fp64_levels = 3;
   o->accel = 1;
   o->mult_order = -1;
+  o->coarse_fp32 = 1;
 }
 
 const char* fmm_last_error(void) { return g_last_error.c_str(); }

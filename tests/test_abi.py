@@ -95,7 +95,7 @@ def test_default_options(lib):
     lib.fmm_default_opts(ctypes.byref(opts))
     assert opts.precision == 1 and opts.n_fp64_levels == 3 and opts.accel == 1
     assert opts.final_stage == 0 and opts.m2l_cartesian == 0 and opts.mult_order == -1
-    assert opts.coarse_fp32 == 0 and list(opts.reserved) == [0]
+    assert opts.coarse_fp32 == 1 and list(opts.reserved) == [0]
 
 
 def test_binding_fails_loudly_without_library(tmp_path):

@@ -263,24 +263,23 @@ def test_tc_schedule_selection_api():
     plan8.close()
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
-def test_tc_fp32_coarse_levels(orc, prec):
-    """coarse="fp32": the coarse M2L levels (2 .. 4) of the mixed precisions in
-    FP32 on the CUDA cores (harmonic components) instead of FP64; the
-    tensor-core levels and every other step as before.  The FP32 error of a
-    coarse level (~1e-7 relative) is far below the split products', so phi
-    stays within the precision's bound."""
+@pytest.mark.parametrize("prec,coarse", [("bf16x3", "fp32"), ("tf32", "fp32"), ("bf16x3", "fp64")])
+def test_tc_coarse_levels(orc, prec, coarse):
+    """The coarse M2L levels (2 .. 4) of the mixed precisions off the tensor
+    cores: FP32 on the CUDA cores, harmonic components (the default), or FP64
+    Cartesian.  The FP32 error of a coarse level (~1e-7 relative) is far below
+    the split products', so phi stays within the precision's bound."""
     n = 128
     rho = inputs.lognormal(n, seed=8).astype(np.float64)
     ref = orc.fmm(rho, 4, 6, accel=True)
-    plan = fmm.FMMPlan((n, n, n), 6, 4, prec, coarse="fp32")
+    plan = fmm.FMMPlan((n, n, n), 6, 4, prec, coarse=coarse)
     kinds = {l: plan.level_kind(l) for l in range(2, plan.leaf_level + 1)}
-    assert [kinds[l] for l in (2, 3, 4)] == ["fp32"] * 3 and kinds[plan.leaf_level] == "tensor", kinds
+    assert [kinds[l] for l in (2, 3, 4)] == [coarse] * 3 and kinds[plan.leaf_level] == "tensor", kinds
     phi, acc = plan.solve(torch.from_numpy(rho.astype(np.float32)).cuda(), accel=True)
     torch.cuda.synchronize()
     plan.check()
     err = rel_l2(phi.double().cpu().numpy(), ref["phi"])
-    print(f"{prec} with FP32 coarse levels: phi rel err {err:.3e}")
+    print(f"{prec} with {coarse} coarse levels: phi rel err {err:.3e}")
     assert err <= TOL[prec]
     assert rel_l2(acc.double().cpu().numpy(), ref["accel"]) <= acc_tol(n, prec)
     plan.close()

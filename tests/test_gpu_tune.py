@@ -68,7 +68,7 @@ def test_variant_matches_oracle(case, prec, variant):
 
 
 def test_variant_rejected_where_it_does_not_apply():
-    plan = fmm.FMMPlan((64, 64, 64), 6, 4, "bf16x3")
+    plan = fmm.FMMPlan((64, 64, 64), 6, 4, "bf16x3", coarse="fp64")
     with pytest.raises(fmm.FMMError):
         plan.set_tuning(plan.leaf_level, 1, 1)  # a tensor-core level
     with pytest.raises(fmm.FMMError):
@@ -79,6 +79,12 @@ def test_variant_rejected_where_it_does_not_apply():
         plan.set_tuning(3, 4, 1)
     plan.set_tuning(3, 3, 27)
     assert plan.tuning(3) == (3, 27)
+    plan.close()
+    plan = fmm.FMMPlan((64, 64, 64), 6, 4, "bf16x3")  # FP32 coarse levels (default): z-run tiles apply
+    plan.set_tuning(3, 1, 1)
+    assert plan.tuning(3) == (1, 1)
+    with pytest.raises(fmm.FMMError):
+        plan.set_tuning(plan.leaf_level, 1, 1)
     plan.close()
 
 
