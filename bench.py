@@ -564,8 +564,10 @@ def main():
 
 def batch_main(args, fmm, inputs, torch, dist, rank, world):
     """Uneven batch: seeded sizes from {64, 96, 128, 192}^3, Plummer + 1% noise,
-    every field solved (phi and accel) by one graph launch per step.  Beside
-    it: the same fields solved one after another without the graph."""
+    every field solved (phi and accel) by one graph launch per step, whose
+    kernels each run one step kind over every field (the fused form).  Beside
+    it: the same fields solved one after another without the graph, and the
+    graph of per-field solves."""
     prec = args.precision if args.precision != DEFAULT_PRECISION else "fp32"
     p, b = args.order, args.leaf
     sizes = inputs.batch_sizes(args.batch, seed=2606 + rank)
@@ -605,6 +607,9 @@ def batch_main(args, fmm, inputs, torch, dist, rank, world):
         return float(t.item())
 
     seq_ms = timed(step_seq)
+    per_field = fmm.BatchSolver(plans, autotune=False, fused=False)
+    pf_ms = timed(lambda: per_field.solve(rhos, phis, accs))
+    per_field.close()
     with ClockSampler(gpu_index_for_smi(torch)) as clk:
         ms = timed(step)
     for q in plans:
@@ -642,7 +647,10 @@ def batch_main(args, fmm, inputs, torch, dist, rank, world):
                 "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32/f32", "bf16x3": "bf16x3/f32"}[prec],
                 "data": "synthetic",
                 "config": {"workload": f"batch of {args.batch} Plummer fields, sizes "
-                                       f"{{64,96,128,192}}^3 (seeded), p={p}, leaf {b}^3, one CUDA graph",
+                                       f"{{64,96,128,192}}^3 (seeded), p={p}, leaf {b}^3, one CUDA graph"
+                                       + (" of multi-field launches" if batch.fused == 1 else " of per-field solves"),
+                           "fused": batch.fused == 1,
+                           "per_field_graph_mcells_s": cells * args.steps * world / (pf_ms / 1e3) / 1e6,
                            "cells_per_step": cells, "size_counts": {str(s): sizes.count(s) for s in sorted(set(sizes))},
                            "precision": prec, "autotuned": not args.no_autotune,
                            "sequential_no_graph_mcells_s":

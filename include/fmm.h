@@ -326,14 +326,34 @@ fmm_status fmm_plan_set_tuning(fmm_plan_t plan, int level, int shape, int dsplit
  *   fmm_batch_solve   : solves every plan's density with one graph launch.
  *                       rho[i], phi[i] (and accel[i] if `accel` is non-NULL and
  *                       accel[i] is non-NULL) are plan i's device buffers as in
- *                       fmm_solve.  The first call with a given set of buffers
- *                       runs each solve once, then captures all of them into a
- *                       CUDA graph -- each plan on its own branch, so small
- *                       grids execute concurrently -- and launches it; later
- *                       calls with the same buffers only launch the graph
- *                       (new buffers: a new capture).  Asynchronous on `stream`.
- *   fmm_batch_destroy : frees the graph and the batch's streams/events
- *                       (NULL: no-op).
+ *                       fmm_solve.  Two forms, chosen per call:
+ *                       - fused: when every plan runs all its contractions on
+ *                         the CUDA cores (no tensor-core level, near field or
+ *                         final-stage M2P), the plans share the order and
+ *                         precision, every level holds the data's precision and
+ *                         a force, if asked for, is the FP32 stencil on rows of
+ *                         a multiple of 4 cells (all buffers 16-byte aligned,
+ *                         every accel[i] non-NULL), each step kind of Sec. 2.3
+ *                         is one kernel launch over every field: P2M, M2M per
+ *                         depth below the leaf level, the M2L levels and near
+ *                         fields of all fields together (one launch per
+ *                         contraction tile shape, without neighbour split),
+ *                         L2L per level, the leaf evaluation and the stencil;
+ *                       - otherwise one CUDA graph of the per-plan solves, each
+ *                         plan on its own branch.
+ *                       The first call with a given set of buffers runs the
+ *                       work once, then captures it into a CUDA graph and
+ *                       launches that; later calls with the same buffers only
+ *                       launch the graph (new buffers: a new capture, and for
+ *                       the fused form a new upload of its item table).
+ *                       Asynchronous on `stream`.
+ *   fmm_batch_set_fused : enable (default) or disable the fused form
+ *                       (disabled: always the graph of per-plan solves).
+ *   fmm_batch_is_fused : 1 if the batch's current graph is the fused form,
+ *                       0 if it is the per-plan one, -1 before the first solve
+ *                       (or for a NULL batch).
+ *   fmm_batch_destroy : frees the graph, the item table and the batch's
+ *                       streams/events (NULL: no-op).
  * Errors: FMM_ERR_ARG (NULL batch, plan or buffer array, a NULL rho[i] /
  * phi[i], count < 1), FMM_ERR_ALLOC (host memory), FMM_ERR_CUDA (stream,
  * event, capture, instantiation or launch failure; the solve errors of
@@ -346,7 +366,11 @@ fmm_status fmm_batch_create(const fmm_plan_t* plans, int count, fmm_batch_t* out
 fmm_status fmm_batch_solve(fmm_batch_t batch, const void* const* rho, void* const* phi, void* const* accel,
                            void* stream);
 fmm_status fmm_batch_destroy(fmm_batch_t batch);
-/* Kernel launches one fmm_batch_solve graph holds (sum over the plans). */
+fmm_status fmm_batch_set_fused(fmm_batch_t batch, int enable);
+int fmm_batch_is_fused(fmm_batch_t batch);
+/* Kernel launches one fmm_batch_solve graph holds: the fused form's step
+ * count when the plans qualify for it (and it is enabled), else the sum over
+ * the plans. */
 int fmm_batch_launches(fmm_batch_t batch, int with_accel);
 
 /* fmm_check -- synchronises the plan's last stream and reports device-side

@@ -57,6 +57,8 @@ EXPORTS = [
     "fmm_batch_solve",
     "fmm_batch_destroy",
     "fmm_batch_launches",
+    "fmm_batch_set_fused",
+    "fmm_batch_is_fused",
 ]
 
 
@@ -137,6 +139,10 @@ def load(path: str | None = None):
         lib.fmm_batch_destroy.restype = i
         lib.fmm_batch_launches.argtypes = [vp, i]
         lib.fmm_batch_launches.restype = i
+        lib.fmm_batch_set_fused.argtypes = [vp, i]
+        lib.fmm_batch_set_fused.restype = i
+        lib.fmm_batch_is_fused.argtypes = [vp]
+        lib.fmm_batch_is_fused.restype = i
         lib.fmm_solve_static.argtypes = [ctypes.POINTER(_Grid), i, i, vp, vp, vp, vp]
         lib.fmm_solve_static.restype = i
         lib.fmm_plan_level_kind.argtypes = [vp, i]
@@ -380,9 +386,11 @@ class FMMPlan:
 
 class BatchSolver:
     """Many independent solves (uneven grids) replayed as one CUDA graph
-    (fmm_batch_*).  The plans must outlive the solver."""
+    (fmm_batch_*): each step kind one launch over every field where the plans
+    allow it (fused=True), else the graph of per-plan solves.  The plans must
+    outlive the solver."""
 
-    def __init__(self, plans, autotune: bool = True):
+    def __init__(self, plans, autotune: bool = True, fused: bool = True):
         self.lib = load()
         self.plans = list(plans)
         if autotune:
@@ -392,6 +400,12 @@ class BatchSolver:
         h = ctypes.c_void_p()
         _check(self.lib, self.lib.fmm_batch_create(arr, len(self.plans), ctypes.byref(h)))
         self._h = h
+        _check(self.lib, self.lib.fmm_batch_set_fused(self._h, 1 if fused else 0))
+
+    @property
+    def fused(self) -> int:
+        """1: the current graph is the fused form, 0: per-plan solves, -1: no solve yet."""
+        return int(self.lib.fmm_batch_is_fused(self._h))
 
     def solve(self, rhos, phis, accels=None, stream=None):
         n = len(self.plans)

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -2734,6 +2735,17 @@ extern "C" fmm_status fmm_solve_static(const fmm_grid* grid, int order, int leaf
 
 // ---------------------------------------------------------------------------
 // Batched solves under one CUDA graph.
+// One launch of a fused batch: a multi-item kernel over the items whose
+// arguments and grids sit in the batch's device table.
+namespace {
+enum MultiKind { MK_P2M, MK_M2M, MK_GEMM, MK_L2L, MK_LEAF, MK_FD };
+struct MultiStep {
+  int kind = 0, shape = 0, n = 0, bs = 0, harm_rows = 0;
+  long long blocks = 0;
+  size_t args_off = 0, grids_off = 0;
+};
+}  // namespace
+
 struct fmm_batch_s {
   std::vector<fmm_plan_t> plans;
   std::vector<cudaStream_t> side;  // one capture branch per plan (reused round-robin)
@@ -2742,6 +2754,17 @@ struct fmm_batch_s {
   cudaGraphExec_t exec = nullptr;
   std::vector<const void*> key;    // buffers the graph was captured with
   bool with_accel = false;
+  // Fused form: each step kind one launch over every field (multi.cuh)
+  bool allow_fused = true;
+  int fused = -1;                  // the graph holds: -1 nothing yet, 0 per-field solves, 1 fused steps
+  std::vector<MultiStep> steps;
+  std::vector<unsigned char> h_tab;  // item arguments and grids, as uploaded
+  unsigned char* d_tab = nullptr;
+  size_t d_tab_cap = 0;
+  // the contraction launches of the fused form run side by side: streams
+  // and fork / join events
+  cudaStream_t fk[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -2750,6 +2773,312 @@ void batch_free_graph(fmm_batch_t B) {
   if (B->graph) cudaGraphDestroy(B->graph);
   B->exec = nullptr;
   B->graph = nullptr;
+}
+
+// Whether the plans of a batch run fused: CUDA-core plans (no tensor-core
+// level, near field or final-stage M2P) of one order whose levels all hold
+// the data's precision, with the stencil force where a force is asked for
+// (the FP32 stencil kernel; FP64 forces keep the per-field graph).
+bool batch_fusable_plans(fmm_batch_t B, bool with_accel) {
+  const fmm_plan_t P0 = B->plans[0];
+  for (fmm_plan_t P : B->plans) {
+    if (P->p != P0->p || P->f64_data() != P0->f64_data() || P->L < 2 || P->near_tc || P->m2p) return false;
+    for (int l = 2; l <= P->L; ++l)
+      if (P->lev[l].tc || P->lev[l].f64 != P->f64_data()) return false;
+    if (with_accel && (!P->opts.accel || P->near_comps != 1 || P->f64_data() || P->dims[0] % 4 != 0)) return false;
+  }
+  return true;
+}
+
+template <typename A>
+size_t tab_put(std::vector<unsigned char>& tab, const A* v, size_t n) {
+  const size_t off = (tab.size() + 15) & ~(size_t)15;
+  tab.resize(off + n * sizeof(A));
+  if (n) std::memcpy(tab.data() + off, v, n * sizeof(A));
+  return off;
+}
+
+// Appends one step of items (those with no blocks left out).
+template <typename A>
+void add_step(fmm_batch_t B, int kind, int shape, int bs, int harm_rows, const std::vector<A>& args,
+              const std::vector<std::array<unsigned, 3>>& grids) {
+  std::vector<A> a;
+  std::vector<MultiGrid> g;
+  long long start = 0;
+  for (size_t i = 0; i < args.size(); ++i) {
+    const long long nb = (long long)grids[i][0] * grids[i][1] * grids[i][2];
+    if (nb <= 0) continue;
+    a.push_back(args[i]);
+    MultiGrid m{};
+    m.gx = grids[i][0];
+    m.gy = grids[i][1];
+    m.gz = grids[i][2];
+    m.start = start;
+    g.push_back(m);
+    start += nb;
+  }
+  if (a.empty()) return;
+  MultiStep st;
+  st.kind = kind;
+  st.shape = shape;
+  st.bs = bs;
+  st.harm_rows = harm_rows;
+  st.n = (int)a.size();
+  st.blocks = start;
+  st.args_off = tab_put(B->h_tab, a.data(), a.size());
+  st.grids_off = tab_put(B->h_tab, g.data(), g.size());
+  B->steps.push_back(st);
+}
+
+// Tile shape of a contraction inside the fused batch, where the other
+// fields fill the GPU: the z-run tiles of the longer run (the fastest per
+// row); a grid of at most 4 x 4 x 4 rows
+// takes the 4 x 4 x 4 tile (a z-run tile of 8 x 4 x RZ rows would be mostly
+// padding; the column-per-lane form is far slower per row in FP32).
+int batch_shape(const NbrGemm& g, const std::vector<int>& tile_k) {
+  if (g.grid[0] <= 4 && g.grid[1] <= 4 && g.grid[2] <= 4) return 0;
+  if (!zrun_eligible(g, tile_k.data(), g.ntiles)) return g.shape;
+  // RZ = 8: in the batch it covers about twice the padded rows per unit
+  // time of RZ = 4, more than its extra padding (a third on 12^3-row grids)
+  return 1;
+}
+
+std::array<unsigned, 3> blocks_1d(long long threads, int bs) {
+  return {(unsigned)((threads + bs - 1) / bs), 1u, 1u};
+}
+
+// The fused schedule (Sec. 2.3's steps, each over every field): P2M; M2M by
+// depth below the leaf level; every field's M2L levels and near field
+// together, one launch per contraction shape; L2L by absolute level (the
+// level-2 harmonic rebuild first); the leaf evaluation; the stencil force.
+// Buffers may be NULL when only the step count is wanted.
+template <typename T>
+void build_fused(fmm_batch_t B, const void* const* rho, void* const* phi, void* const* accel, bool with_accel) {
+  B->steps.clear();
+  B->h_tab.clear();
+  const int n = (int)B->plans.size();
+  constexpr int bs = 256;  // block size of the tree kernels (M2M, L2L)
+  int maxL = 0;
+  for (fmm_plan_t P : B->plans) maxL = std::max(maxL, P->L);
+  {  // P2M (and the near field's box-major density)
+    std::vector<P2mArgs> a;
+    std::vector<std::array<unsigned, 3>> g;
+    int harm_rows = 0;
+    for (int i = 0; i < n; ++i) {
+      const fmm_plan_t P = B->plans[i];
+      const Level& lf = P->lev[P->L];
+      P2mArgs x{};
+      x.rho = rho ? rho[i] : nullptr;
+      x.nx = P->dims[0];
+      x.ny = P->dims[1];
+      x.b = P->b;
+      x.leaf = lf;
+      x.Mleaf = P->M(P->L);
+      x.rho_box = P->arena + P->rho_box_off;
+      x.flag = P->d_flag;
+      x.harm = lf.fold_off ? 1 : 0;
+      x.Mfold = lf.fold_off ? P->arena + lf.fold_off : nullptr;
+      x.ncell = P->ncell();
+      harm_rows |= x.harm;
+      a.push_back(x);
+      g.push_back(blocks_1d(lf.npar * 16, 256));
+    }
+    add_step(B, MK_P2M, 0, 256, harm_rows, a, g);
+  }
+  for (int k = 0; k + 3 <= maxL; ++k) {  // M2M: level L - k to L - k - 1 of every field deep enough
+    std::vector<M2mArgs> a;
+    std::vector<std::array<unsigned, 3>> g;
+    for (fmm_plan_t P : B->plans) {
+      const int l = P->L - k;
+      if (l < 3) continue;
+      const Level &c = P->lev[l], &q = P->lev[l - 1];
+      M2mArgs x{};
+      x.child = c;
+      x.Mc = P->M(l);
+      x.par = q;
+      x.Mp = P->M(l - 1);
+      x.harm = q.fold_off ? 1 : 0;
+      x.Mfold = q.fold_off ? P->arena + q.fold_off : nullptr;
+      a.push_back(x);
+      g.push_back(blocks_1d(c.npar * 8, bs));
+    }
+    add_step(B, MK_M2M, 0, bs, 0, a, g);
+  }
+  {  // M2L of every level and the near field: independent contractions
+    std::vector<NbrGemm> a[4];
+    std::vector<std::array<unsigned, 3>> g[4];
+    auto add = [&](NbrGemm x, const std::vector<int>& tile_k) {
+      x.dsplit = 1;  // the batch fills the GPU: no neighbour split, no partial sums
+      x.partial = nullptr;
+      x.max_blocks = 0;
+      x.shape = batch_shape(x, tile_k);
+      std::array<unsigned, 3> gr;
+      if (x.shape == 1 || x.shape == 2)
+        nbr_gemm_zrun_grid<T>(x, x.shape - 1, gr.data());
+      else
+        nbr_gemm_simt_col_grid<T>(x, gr.data());
+      a[x.shape].push_back(x);
+      g[x.shape].push_back(gr);
+    };
+    for (fmm_plan_t P : B->plans) {
+      for (int l = 2; l <= P->L; ++l) add(m2l_gemm(P, l), P->h_m2l_tile_k);
+      add(near_gemm(P), P->h_near_tile_k);
+    }
+    for (int sh = 0; sh < 4; ++sh) add_step(B, MK_GEMM, sh, 0, 0, a[sh], g[sh]);
+  }
+  for (int l = 2; l <= maxL; ++l) {  // L2L, coarse to fine
+    std::vector<L2lArgs> a;
+    std::vector<std::array<unsigned, 3>> g;
+    for (fmm_plan_t P : B->plans) {
+      if (l > P->L) continue;
+      const bool harm = harmonic_m2l_level(P, l);
+      if (l == 2 && !harm) continue;  // level-2 locals are its M2L alone
+      const Level &q = P->lev[l - 1], &c = P->lev[l];
+      L2lArgs x{};
+      x.par = q;
+      x.Lp = l == 2 ? nullptr : P->Lx(l - 1);
+      x.child = c;
+      x.Lc = P->Lx(l);
+      x.accumulate = 1;
+      x.harm = harm ? 1 : 0;
+      x.Lred = harm && c.lred_off ? P->arena + c.lred_off : nullptr;
+      a.push_back(x);
+      g.push_back(blocks_1d(q.nbox * 8, bs));
+    }
+    add_step(B, MK_L2L, 0, bs, 0, a, g);
+  }
+  {  // leaf evaluation: L2P plus the near field, scaled
+    std::vector<LeafArgs> a;
+    std::vector<std::array<unsigned, 3>> g;
+    for (int i = 0; i < n; ++i) {
+      const fmm_plan_t P = B->plans[i];
+      LeafArgs x{};
+      x.leaf = P->lev[P->L];
+      x.Lleaf = P->Lx(P->L);
+      x.near_box = P->arena + P->near_off;
+      x.near_stride = P->b * P->b * P->b * P->near_comps;
+      x.nx = P->dims[0];
+      x.ny = P->dims[1];
+      x.b = P->b;
+      x.scale = P->G * P->dx * P->dx;
+      x.phi = phi ? phi[i] : nullptr;
+      a.push_back(x);
+      g.push_back(blocks_1d(x.leaf.npar * 8, 256));
+    }
+    add_step(B, MK_LEAF, 0, 256, 0, a, g);
+  }
+  if (with_accel) {  // force by the 5-point stencil (App. C)
+    std::vector<FdArgs> a;
+    std::vector<std::array<unsigned, 3>> g;
+    for (int i = 0; i < n; ++i) {
+      const fmm_plan_t P = B->plans[i];
+      FdArgs x{};
+      x.phi = phi ? phi[i] : nullptr;
+      x.nx = P->dims[0];
+      x.ny = P->dims[1];
+      x.nz = P->dims[2];
+      x.inv_dx = 1.0 / P->dx;
+      x.accel = accel ? accel[i] : nullptr;
+      std::array<unsigned, 3> gr;
+      fd_multi_grid(P->dims, gr.data());
+      a.push_back(x);
+      g.push_back(gr);
+    }
+    add_step(B, MK_FD, 0, 0, 0, a, g);
+  }
+}
+
+// The steps in order, except that the contraction launches (independent of
+// one another) run side by side: the first on `s`, the others on the fork
+// streams, joined before the next step.  The first is the 4 x 4 x 4 tile
+// launch of the few-row grids: its blocks are long (a row's whole reduction
+// in one block) and few, so they start first and the z-run launches fill the
+// GPU around them instead of waiting for their tail.
+template <typename T>
+fmm_status run_fused(fmm_batch_t B, cudaStream_t s) {
+  const int p = B->plans[0]->p;
+  int ngemm = 0, nfork = 0;
+  for (const MultiStep& st : B->steps) ngemm += st.kind == MK_GEMM;
+  for (const MultiStep& st : B->steps) {
+    const void* a = B->d_tab + st.args_off;
+    const MultiGrid* g = reinterpret_cast<const MultiGrid*>(B->d_tab + st.grids_off);
+    cudaError_t e = cudaSuccess;
+    cudaStream_t ls = s;
+    if (st.kind == MK_GEMM && ngemm > 1) {
+      if (nfork == 0) CUDA_TRY(cudaEventRecord(B->fev[0], s));
+      if (nfork > 0) {  // the fork streams (at most three more contraction shapes)
+        ls = B->fk[nfork - 1];
+        CUDA_TRY(cudaStreamWaitEvent(ls, B->fev[0], 0));
+      }
+      ++nfork;
+    }
+    if (st.kind != MK_GEMM && nfork > 1) {  // join the fork streams
+      for (int k = 1; k < nfork; ++k) {
+        CUDA_TRY(cudaEventRecord(B->fev[k], B->fk[k - 1]));
+        CUDA_TRY(cudaStreamWaitEvent(s, B->fev[k], 0));
+      }
+      nfork = 0;
+      ngemm = 0;
+    }
+    switch (st.kind) {
+      case MK_P2M:
+        e = launch_p2m_multi<T>(p, static_cast<const P2mArgs*>(a), g, st.n, st.blocks, st.harm_rows, ls);
+        break;
+      case MK_M2M:
+        e = launch_m2m_multi<T, T>(p, static_cast<const M2mArgs*>(a), g, st.n, st.blocks, st.bs, ls);
+        break;
+      case MK_GEMM: {
+        const NbrGemm* gs = static_cast<const NbrGemm*>(a);
+        if (st.shape == 0)
+          e = launch_nbr_gemm_simt_multi<T>(gs, g, st.n, st.blocks, ls);
+        else if (st.shape == 3)
+          e = launch_nbr_gemm_col_multi<T>(gs, g, st.n, st.blocks, ls);
+        else
+          e = launch_nbr_gemm_zrun_multi<T>(st.shape - 1, gs, g, st.n, st.blocks, ls);
+        break;
+      }
+      case MK_L2L:
+        e = launch_l2l_multi<T, T>(p, static_cast<const L2lArgs*>(a), g, st.n, st.blocks, st.bs, ls);
+        break;
+      case MK_LEAF:
+        e = launch_leaf_finish_multi<T>(p, static_cast<const LeafArgs*>(a), g, st.n, st.blocks, ls);
+        break;
+      case MK_FD:
+        e = launch_fd_accel_multi(static_cast<const FdArgs*>(a), g, st.n, st.blocks, ls);
+        break;
+    }
+    CUDA_TRY(e);
+  }
+  return FMM_OK;
+}
+
+// Builds the fused schedule for these buffers and uploads its table.
+fmm_status prepare_fused(fmm_batch_t B, const void* const* rho, void* const* phi, void* const* accel) {
+  if (B->plans[0]->f64_data())
+    build_fused<double>(B, rho, phi, accel, accel != nullptr);
+  else
+    build_fused<float>(B, rho, phi, accel, accel != nullptr);
+  const size_t bytes = std::max<size_t>(B->h_tab.size(), 16);
+  // a graph launched on any stream may still read the previous table
+  CUDA_TRY(cudaDeviceSynchronize());
+  if (bytes > B->d_tab_cap) {
+    if (B->d_tab) cudaFree(B->d_tab);
+    B->d_tab = nullptr;
+    B->d_tab_cap = 0;
+    void* d = nullptr;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FMM_ERR_ALLOC, "cudaMalloc(%zu) of the batch table failed", bytes);
+    }
+    B->d_tab = static_cast<unsigned char*>(d);
+    B->d_tab_cap = bytes;
+  }
+  CUDA_TRY(cudaMemcpy(B->d_tab, B->h_tab.data(), B->h_tab.size(), cudaMemcpyHostToDevice));
+  return FMM_OK;
+}
+
+fmm_status run_fused_any(fmm_batch_t B, cudaStream_t s) {
+  return B->plans[0]->f64_data() ? run_fused<double>(B, s) : run_fused<float>(B, s);
 }
 }  // namespace
 
@@ -2776,6 +3105,16 @@ extern "C" fmm_status fmm_batch_create(const fmm_plan_t* plans, int count, fmm_b
       fmm_batch_destroy(B);
       return fail(FMM_ERR_CUDA, "event creation failed");
     }
+  for (auto& st : B->fk)
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      fmm_batch_destroy(B);
+      return fail(FMM_ERR_CUDA, "stream creation failed");
+    }
+  for (auto& e : B->fev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      fmm_batch_destroy(B);
+      return fail(FMM_ERR_CUDA, "event creation failed");
+    }
   *out = B;
   return FMM_OK;
 }
@@ -2796,6 +3135,38 @@ extern "C" fmm_status fmm_batch_solve(fmm_batch_t B, const void* const* rho, voi
   }
   if (!B->exec || key != B->key) {
     batch_free_graph(B);
+    B->fused = -1;
+    bool fuse = B->allow_fused && batch_fusable_plans(B, accel != nullptr);
+    for (int i = 0; i < n && fuse; ++i)
+      fuse = aligned16(rho[i]) && aligned16(phi[i]) && (!accel || (accel[i] && aligned16(accel[i])));
+    if (fuse) {
+      fmm_status st = prepare_fused(B, rho, phi, accel);
+      if (st != FMM_OK) return st;
+      // one eager pass: first-use set-up must not happen inside a capture
+      if ((st = run_fused_any(B, s)) != FMM_OK) return st;
+      CUDA_TRY(cudaStreamSynchronize(s));
+      cudaStream_t cap = B->side[0];
+      CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+      st = run_fused_any(B, cap);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(cap, &g);
+      if (st != FMM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (ec != cudaSuccess) return fail(FMM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ec));
+      B->graph = g;
+      if (cudaGraphInstantiate(&B->exec, g, 0) != cudaSuccess) {
+        batch_free_graph(B);
+        return fail(FMM_ERR_CUDA, "graph instantiation failed");
+      }
+      B->key = key;
+      B->with_accel = accel != nullptr;
+      B->fused = 1;
+      for (auto* P : B->plans) P->last_stream = s;
+      CUDA_TRY(cudaGraphLaunch(B->exec, s));
+      return FMM_OK;
+    }
     // one eager solve per plan: first-use set-up (kernel attributes, lazy
     // module loading) must not happen inside a capture
     for (int i = 0; i < n; ++i) {
@@ -2842,6 +3213,7 @@ extern "C" fmm_status fmm_batch_solve(fmm_batch_t B, const void* const* rho, voi
     }
     B->key = key;
     B->with_accel = accel != nullptr;
+    B->fused = 0;
   }
   for (auto* P : B->plans) P->last_stream = s;  // fmm_check waits on the graph's stream
   CUDA_TRY(cudaGraphLaunch(B->exec, s));
@@ -2851,9 +3223,17 @@ extern "C" fmm_status fmm_batch_solve(fmm_batch_t B, const void* const* rho, voi
 extern "C" fmm_status fmm_batch_destroy(fmm_batch_t B) {
   if (!B) return FMM_OK;
   batch_free_graph(B);
+  if (B->d_tab) {
+    cudaDeviceSynchronize();  // a launched graph may still read the table
+    cudaFree(B->d_tab);
+  }
   for (auto& st : B->side)
     if (st) cudaStreamDestroy(st);
   for (auto& e : B->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& st : B->fk)
+    if (st) cudaStreamDestroy(st);
+  for (auto& e : B->fev)
     if (e) cudaEventDestroy(e);
   delete B;
   return FMM_OK;
@@ -2861,10 +3241,38 @@ extern "C" fmm_status fmm_batch_destroy(fmm_batch_t B) {
 
 extern "C" int fmm_batch_launches(fmm_batch_t B, int with_accel) {
   if (!B) return -1;
+  if (B->allow_fused && batch_fusable_plans(B, with_accel != 0)) {
+    // the fused schedule's step count (the buffers do not change it); the
+    // table held for the current buffers is left as it is
+    std::vector<MultiStep> keep_steps;
+    std::vector<unsigned char> keep_tab;
+    keep_steps.swap(B->steps);
+    keep_tab.swap(B->h_tab);
+    if (B->plans[0]->f64_data())
+      build_fused<double>(B, nullptr, nullptr, nullptr, with_accel != 0);
+    else
+      build_fused<float>(B, nullptr, nullptr, nullptr, with_accel != 0);
+    const int count = (int)B->steps.size();
+    keep_steps.swap(B->steps);
+    keep_tab.swap(B->h_tab);
+    return count;
+  }
   int n = 0;
   for (auto* P : B->plans) n += fmm_solve_launches(P, with_accel);
   return n;
 }
+
+extern "C" fmm_status fmm_batch_set_fused(fmm_batch_t B, int enable) {
+  if (!B) return fail(FMM_ERR_ARG, "batch is NULL");
+  if ((enable != 0) != B->allow_fused) {
+    B->allow_fused = enable != 0;
+    batch_free_graph(B);
+    B->key.clear();
+  }
+  return FMM_OK;
+}
+
+extern "C" int fmm_batch_is_fused(fmm_batch_t B) { return B ? B->fused : -1; }
 
 // ---------------------------------------------------------------------------
 // Autotuner of the CUDA-core contractions (M2L levels off the tensor cores and

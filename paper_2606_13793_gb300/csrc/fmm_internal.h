@@ -59,6 +59,13 @@ struct Level {
   size_t fold_off, lred_off;
 };
 
+// One item of a multi-item launch (multi.cuh): its grid of blocks and the
+// first flat block of the launch that belongs to it.
+struct MultiGrid {
+  unsigned gx, gy, gz, pad;
+  long long start;
+};
+
 // Neighbour-contraction ("implicit GEMM") description for the SIMT kernel:
 //   C[row][n] (+)= sum_{d in 27 neighbours} sum_{k < K(tile(n))} A[row + d][k] * W_d[k][n]
 // rows live on a 3-D grid; a neighbour outside the grid contributes zero.
@@ -92,6 +99,23 @@ bool zrun_eligible(const NbrGemm& g, const int* tile_k_host, int ntiles);
 // Dispatch on g.shape.
 template <typename T>
 cudaError_t launch_nbr_gemm(const NbrGemm& g, cudaStream_t s);
+// Multi-item forms (multi.cuh) for items of one shape with dsplit 1 (no
+// partial sums): gs / grids are device arrays of n items; *_grid gives an
+// item's grid (shape 0 / 3: nbr_gemm_simt_col_grid, shapes 1 / 2:
+// nbr_gemm_zrun_grid with shape - 1).
+template <typename T>
+cudaError_t launch_nbr_gemm_simt_multi(const NbrGemm* gs, const MultiGrid* grids, int n, long long blocks,
+                                       cudaStream_t s);
+template <typename T>
+cudaError_t launch_nbr_gemm_col_multi(const NbrGemm* gs, const MultiGrid* grids, int n, long long blocks,
+                                      cudaStream_t s);
+template <typename T>
+cudaError_t launch_nbr_gemm_zrun_multi(int shape, const NbrGemm* gs, const MultiGrid* grids, int n, long long blocks,
+                                       cudaStream_t s);
+template <typename T>
+void nbr_gemm_simt_col_grid(const NbrGemm& g, unsigned out[3]);
+template <typename T>
+void nbr_gemm_zrun_grid(const NbrGemm& g, int shape, unsigned out[3]);
 // C (+)= sum over nparts partial arrays of count values, in part order.
 template <typename T>
 cudaError_t launch_reduce_partials(const T* part, int nparts, long long count, T* C, int accumulate, cudaStream_t s);
@@ -132,6 +156,81 @@ template <typename Tp, typename Tc>
 // of in the full rows
 cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, const Level& child, Tc* Lc, int accumulate,
                        int harm, const Tc* Lred, cudaStream_t s);
+// Multi-item forms (batched solves, multi.cuh): args and grids are device
+// arrays of n items sorted by first block; blocks = the launch's total, bs
+// the block size every item's grid was computed with.
+// P2M of one leaf level (launch_p2m's arguments; boxes of kThreads / 2 per
+// block: grid = ceil(npar * 16 / kThreads) blocks of kThreads).
+struct P2mArgs {
+  const void* rho;
+  int nx, ny, b;
+  Level leaf;
+  void* Mleaf;
+  void* Mhi;
+  void* Mlo;
+  void* rho_box;
+  void* rho_hi;
+  void* rho_lo;
+  int* flag;
+  int harm;
+  void* Mfold;
+  long long ncell;
+};
+// harm_rows: 1 when any item stages folded rows (harm with Mhi or Mfold)
+template <typename T>
+cudaError_t launch_p2m_multi(int p, const P2mArgs* args, const MultiGrid* grids, int n, long long blocks,
+                             int harm_rows, cudaStream_t s);
+// Leaf evaluation (launch_leaf_finish's arguments; one thread per leaf box:
+// grid = ceil(npar * 8 / kThreads) blocks of kThreads).
+struct LeafArgs {
+  Level leaf;
+  const void* Lleaf;
+  const void* near_box;
+  int near_stride;
+  const void* m2p;
+  int nx, ny, b;
+  double scale;
+  void* phi;
+};
+template <typename T>
+cudaError_t launch_leaf_finish_multi(int p, const LeafArgs* args, const MultiGrid* grids, int n, long long blocks,
+                                     cudaStream_t s);
+// The 5-point stencil of App. C on FP32 rows of a multiple of four cells,
+// 16-byte aligned; fd_multi_grid gives an item's grid (blocks of 32 x 8).
+struct FdArgs {
+  const void* phi;
+  int nx, ny, nz;
+  double inv_dx;
+  void* accel;
+};
+cudaError_t launch_fd_accel_multi(const FdArgs* args, const MultiGrid* grids, int n, long long blocks,
+                                  cudaStream_t s);
+void fd_multi_grid(const int dims[3], unsigned g[3]);
+struct M2mArgs {
+  Level child;
+  const void* Mc;
+  Level par;
+  void* Mp;
+  void* Mhi;
+  void* Mlo;
+  int harm;
+  void* Mfold;
+};
+template <typename Tc, typename Tp>
+cudaError_t launch_m2m_multi(int p, const M2mArgs* args, const MultiGrid* grids, int n, long long blocks, int bs,
+                             cudaStream_t s);
+struct L2lArgs {
+  Level par;
+  const void* Lp;
+  Level child;
+  void* Lc;
+  int accumulate;
+  int harm;
+  const void* Lred;
+};
+template <typename Tp, typename Tc>
+cudaError_t launch_l2l_multi(int p, const L2lArgs* args, const MultiGrid* grids, int n, long long blocks, int bs,
+                             cudaStream_t s);
 template <typename T>
 cudaError_t launch_zero(T* p, size_t count, cudaStream_t s);
 // dst = sc * src (count values)

@@ -8,6 +8,7 @@
 // plain one-thread-per-cell kernel for grids past the launch limits.  The
 // adjoint source kernel is one thread per cell, x fastest.
 #include "fmm_internal.h"
+#include "multi.cuh"
 
 namespace fmmgb {
 namespace {
@@ -121,16 +122,15 @@ __global__ void __launch_bounds__(kFdTX* kFdTY) fd_accel_tiled_kernel(const T* _
 // (float4, no corners: the stencil is a cross) and two cells left and right
 // of each tile row.
 constexpr int kFd4TX = 4 * kFdTX;  // cells per tile row
-__global__ void __launch_bounds__(kFdTX* kFdTY) fd_accel_vec4_kernel(const float* __restrict__ phi, int nx, int ny,
-                                                                     int nz, float inv_dx,
-                                                                     float* __restrict__ accel) {
+__device__ __forceinline__ void fd_accel_vec4_body(const float* __restrict__ phi, int nx, int ny, int nz,
+                                                  float inv_dx, float* __restrict__ accel, const VBlock& vb) {
   constexpr int HX = kFd4TX + 8, HY = kFdTY + 4, C0 = 4;  // tile row: halo at C0-2, C0-1 and C0+128, C0+129
   __shared__ __align__(16) float tile[2][HY][HX];
   const long long n = (long long)nx * ny * nz;
   const long long plane = (long long)nx * ny;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * kFdTX + tx;
-  const int x0 = blockIdx.x * kFd4TX, y0 = blockIdx.y * kFdTY, z0 = blockIdx.z * kFdZC;
+  const int x0 = vb.x * kFd4TX, y0 = vb.y * kFdTY, z0 = vb.z * kFdZC;
   const int x = x0 + 4 * tx, y = y0 + ty;
   const bool inside = x < nx && y < ny;  // nx % 4 == 0: all four cells
   const long long col = (long long)y * nx + x;
@@ -221,6 +221,24 @@ __global__ void __launch_bounds__(kFdTX* kFdTY) fd_accel_vec4_kernel(const float
       *reinterpret_cast<float4*>(accel + 2 * n + c) = make_float4(az[0], az[1], az[2], az[3]);
     }
   }
+}
+
+__global__ void __launch_bounds__(kFdTX* kFdTY, 3) fd_accel_vec4_kernel(const float* __restrict__ phi, int nx, int ny,
+                                                                     int nz, float inv_dx,
+                                                                     float* __restrict__ accel) {
+  fd_accel_vec4_body(phi, nx, ny, nz, inv_dx, accel, native_vblock());
+}
+
+// The stencils of many solves in one launch (batched solves; FP32 rows of a
+// multiple of four cells, 16-byte aligned).
+__global__ void __launch_bounds__(kFdTX* kFdTY, 3) fd_accel_vec4_multi_kernel(const FdArgs* __restrict__ a,
+                                                                           const MultiGrid* __restrict__ g, int n) {
+  __shared__ FdArgs x;  // the item's arguments, read by the body from shared memory
+  const int i = multi_item(g, n);
+  if (threadIdx.x == 0 && threadIdx.y == 0) x = a[i];
+  __syncthreads();
+  fd_accel_vec4_body(static_cast<const float*>(x.phi), x.nx, x.ny, x.nz, (float)x.inv_dx, static_cast<float*>(x.accel),
+                     multi_vblock(g[i]));
 }
 
 // Grid: x blocks over a row, y = row index, z = slice (32-bit indexing).
@@ -320,6 +338,19 @@ cudaError_t launch_fd_accel(const T* phi, const int dims[3], double inv_dx, T* a
             (unsigned)((dims[2] + kFdZC - 1) / kFdZC));
   fd_accel_tiled_kernel<T><<<grid, dim3(kFdTX, kFdTY), 0, s>>>(phi, dims[0], dims[1], dims[2], (T)inv_dx, accel);
   return cudaGetLastError();
+}
+
+cudaError_t launch_fd_accel_multi(const FdArgs* args, const MultiGrid* grids, int n, long long blocks,
+                                  cudaStream_t s) {
+  if (n == 0 || blocks == 0) return cudaSuccess;
+  fd_accel_vec4_multi_kernel<<<(unsigned)blocks, dim3(kFdTX, kFdTY), 0, s>>>(args, grids, n);
+  return cudaGetLastError();
+}
+
+void fd_multi_grid(const int dims[3], unsigned g[3]) {
+  g[0] = (unsigned)((dims[0] + kFd4TX - 1) / kFd4TX);
+  g[1] = (unsigned)((dims[1] + kFdTY - 1) / kFdTY);
+  g[2] = (unsigned)((dims[2] + kFdZC - 1) / kFdZC);
 }
 
 template <typename T>

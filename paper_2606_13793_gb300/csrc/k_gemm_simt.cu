@@ -21,6 +21,7 @@
 // then looping over items (a few persistent CTAs that share SMs with other
 // kernels instead of flooding them).
 #include "fmm_internal.h"
+#include "multi.cuh"
 
 namespace fmmgb {
 namespace {
@@ -34,7 +35,7 @@ template <typename T>
 constexpr int kChunkOf = sizeof(T) == 8 ? kKChunk / 2 : kKChunk;
 
 template <typename T>
-__global__ void __launch_bounds__(64) nbr_gemm_simt_kernel(NbrGemm g) {
+__device__ __forceinline__ void nbr_gemm_simt_body(const NbrGemm& g, const VBlock vb) {
   constexpr int KC = kChunkOf<T>;
   __shared__ T As[KC][kRows + kPad];
   __shared__ T Bs[KC][kNTile];
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(64) nbr_gemm_simt_kernel(NbrGemm g) {
   const int ntx = (g.grid[0] + 3) >> 2, nty = (g.grid[1] + 3) >> 2, ntz = (g.grid[2] + 3) >> 2;
   const long long tiles = (long long)ntx * nty * ntz;
   const long long items = tiles * g.ntiles * (g.dsplit > 1 ? 27 : 1);
-  for (long long w = blockIdx.x; w < items; w += gridDim.x) {
+  for (long long w = vb.x; w < items; w += vb.gx) {
     const int bt = (int)(w % tiles);
     const int tile = (int)((w / tiles) % g.ntiles);
     const int dgrp = (int)(w / (tiles * g.ntiles));
@@ -120,6 +121,21 @@ __global__ void __launch_bounds__(64) nbr_gemm_simt_kernel(NbrGemm g) {
   }  // work items
 }
 
+template <typename T>
+__global__ void __launch_bounds__(64) nbr_gemm_simt_kernel(NbrGemm g) {
+  nbr_gemm_simt_body<T>(g, native_vblock());
+}
+
+template <typename T>
+__global__ void __launch_bounds__(64) nbr_gemm_simt_multi_kernel(const NbrGemm* __restrict__ gs,
+                                                                 const MultiGrid* __restrict__ grids, int n) {
+  __shared__ NbrGemm g;  // the item's description, read by the body from shared memory
+  const int i = multi_item(grids, n);
+  if (threadIdx.x == 0) g = gs[i];
+  __syncthreads();
+  nbr_gemm_simt_body<T>(g, multi_vblock(grids[i]));
+}
+
 // Column-per-lane variant (shape 3), for the FP64 levels: every lane owns one
 // output column and R consecutive rows of its warp, so a block is 4 warps x
 // 32 columns x R rows with no shared memory.  The 64-bit FMA pipe of an SM is
@@ -131,12 +147,12 @@ __global__ void __launch_bounds__(64) nbr_gemm_simt_kernel(NbrGemm g) {
 constexpr int kColRows = 4;  // rows per warp
 
 template <typename T>
-__global__ void __launch_bounds__(128) nbr_gemm_col_kernel(NbrGemm g) {
+__device__ __forceinline__ void nbr_gemm_col_body(const NbrGemm& g, const VBlock vb) {
   constexpr int R = kColRows;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long rows = (long long)g.grid[0] * g.grid[1] * g.grid[2];
-  const int tile = blockIdx.y;
-  const int d0 = g.dsplit > 1 ? (int)blockIdx.z : 0;  // dsplit is 1 or 27 here
+  const int tile = vb.y;
+  const int d0 = g.dsplit > 1 ? (int)vb.z : 0;  // dsplit is 1 or 27 here
   const int d1 = g.dsplit > 1 ? d0 + 1 : 27;
   const int K = g.tile_k[tile];
   const T* W0 = static_cast<const T*>(g.W) + g.tile_w[tile] + lane;
@@ -145,7 +161,7 @@ __global__ void __launch_bounds__(128) nbr_gemm_col_kernel(NbrGemm g) {
   int rx[R], ry[R], rz[R];
 #pragma unroll
   for (int i = 0; i < R; ++i) {
-    row[i] = ((long long)blockIdx.x * 4 + warp) * R + i;
+    row[i] = ((long long)vb.x * 4 + warp) * R + i;
     const long long rr = row[i] < rows ? row[i] : 0;
     rx[i] = (int)(rr % g.grid[0]);
     ry[i] = (int)((rr / g.grid[0]) % g.grid[1]);
@@ -186,6 +202,21 @@ __global__ void __launch_bounds__(128) nbr_gemm_col_kernel(NbrGemm g) {
       *dst = g.accumulate ? (*dst + acc[i]) : acc[i];
     }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) nbr_gemm_col_kernel(NbrGemm g) {
+  nbr_gemm_col_body<T>(g, native_vblock());
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) nbr_gemm_col_multi_kernel(const NbrGemm* __restrict__ gs,
+                                                                 const MultiGrid* __restrict__ grids, int n) {
+  __shared__ NbrGemm g;  // the item's description, read by the body from shared memory
+  const int i = multi_item(grids, n);
+  if (threadIdx.x == 0) g = gs[i];
+  __syncthreads();
+  nbr_gemm_col_body<T>(g, multi_vblock(grids[i]));
 }
 
 // C (+)= sum over the neighbour-group partials, in group order.
@@ -244,6 +275,46 @@ cudaError_t launch_nbr_gemm_simt(const NbrGemm& g, cudaStream_t s) {
                                    g.accumulate, s);
 }
 
+// Multi-item forms: shapes 0 and 3 (z-run shapes in k_gemm_zrun.cu).
+template <typename T>
+cudaError_t launch_nbr_gemm_simt_multi(const NbrGemm* gs, const MultiGrid* grids, int n, long long blocks,
+                                       cudaStream_t s) {
+  if (n <= 0 || blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  nbr_gemm_simt_multi_kernel<T><<<(unsigned)blocks, 64, 0, s>>>(gs, grids, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_nbr_gemm_col_multi(const NbrGemm* gs, const MultiGrid* grids, int n, long long blocks,
+                                      cudaStream_t s) {
+  if (n <= 0 || blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  nbr_gemm_col_multi_kernel<T><<<(unsigned)blocks, 128, 0, s>>>(gs, grids, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+void nbr_gemm_simt_col_grid(const NbrGemm& g, unsigned out[3]) {
+  const unsigned nd = g.dsplit > 1 ? 27u : 1u;
+  if (g.shape == 3) {
+    const long long rows = (long long)g.grid[0] * g.grid[1] * g.grid[2];
+    out[0] = (unsigned)((rows + 4 * kColRows - 1) / (4 * kColRows));
+    out[1] = (unsigned)g.ntiles;
+    out[2] = nd;
+  } else {
+    const long long tiles = (long long)((g.grid[0] + 3) / 4) * ((g.grid[1] + 3) / 4) * ((g.grid[2] + 3) / 4);
+    out[0] = (unsigned)(tiles * g.ntiles * nd);
+    out[1] = out[2] = 1;
+  }
+}
+
+template cudaError_t launch_nbr_gemm_simt_multi<float>(const NbrGemm*, const MultiGrid*, int, long long, cudaStream_t);
+template cudaError_t launch_nbr_gemm_simt_multi<double>(const NbrGemm*, const MultiGrid*, int, long long, cudaStream_t);
+template cudaError_t launch_nbr_gemm_col_multi<float>(const NbrGemm*, const MultiGrid*, int, long long, cudaStream_t);
+template cudaError_t launch_nbr_gemm_col_multi<double>(const NbrGemm*, const MultiGrid*, int, long long, cudaStream_t);
+template void nbr_gemm_simt_col_grid<float>(const NbrGemm&, unsigned[3]);
+template void nbr_gemm_simt_col_grid<double>(const NbrGemm&, unsigned[3]);
 template cudaError_t launch_nbr_gemm_simt<float>(const NbrGemm&, cudaStream_t);
 template cudaError_t launch_nbr_gemm_simt<double>(const NbrGemm&, cudaStream_t);
 template cudaError_t launch_nbr_gemm<float>(const NbrGemm&, cudaStream_t);

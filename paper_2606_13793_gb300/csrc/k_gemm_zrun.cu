@@ -18,6 +18,7 @@
 //
 // A neighbour row outside the grid reads zero: the isolated boundary.
 #include "fmm_internal.h"
+#include "multi.cuh"
 
 namespace fmmgb {
 namespace {
@@ -55,7 +56,7 @@ constexpr size_t zrun_smem_bytes() {
 }
 
 template <typename T, int RZ>
-__global__ void __launch_bounds__(kZrThreads) nbr_gemm_zrun_kernel(NbrGemm g) {
+__device__ __forceinline__ void nbr_gemm_zrun_body(const NbrGemm& g, const VBlock vb) {
   using H = ZrHalo<RZ>;
   using V = typename Vec<T>::type;
   constexpr int VN = Vec<T>::n;
@@ -66,14 +67,14 @@ __global__ void __launch_bounds__(kZrThreads) nbr_gemm_zrun_kernel(NbrGemm g) {
   const int t = threadIdx.x;
   const int cg = t % kZrCG, xr = (t / kZrCG) % kZrBX, yr = t / 32;
   const int ntx = (g.grid[0] + kZrBX - 1) / kZrBX, nty = (g.grid[1] + kZrBY - 1) / kZrBY;
-  const int bt = blockIdx.x;
+  const int bt = vb.x;
   const int ox = (bt % ntx) * kZrBX, oy = ((bt / ntx) % nty) * kZrBY, oz = (bt / (ntx * nty)) * RZ;
-  const int tile = blockIdx.y;
+  const int tile = vb.y;
   const int K = g.tile_k[tile];
   const T* W0 = static_cast<const T*>(g.W) + g.tile_w[tile];
   const T* A = static_cast<const T*>(g.A);
   const int nxy = 9 / g.dsplit;  // (dx, dy) pairs of this CTA
-  const int xy0 = (g.dsplit > 1 ? (int)blockIdx.z : 0) * nxy;
+  const int xy0 = (g.dsplit > 1 ? (int)vb.z : 0) * nxy;
 
   T acc[RZ][kZrCT];
 #pragma unroll
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(kZrThreads) nbr_gemm_zrun_kernel(NbrGemm g) {
   const int x = ox + xr, y = oy + yr;
   if (x >= g.grid[0] || y >= g.grid[1]) return;
   const long long rows = (long long)g.grid[0] * g.grid[1] * g.grid[2];
-  T* Pz = g.dsplit > 1 ? static_cast<T*>(g.partial) + (long long)blockIdx.z * rows * g.n_cols : nullptr;
+  T* Pz = g.dsplit > 1 ? static_cast<T*>(g.partial) + (long long)vb.z * rows * g.n_cols : nullptr;
   T* C = static_cast<T*>(g.C);
 #pragma unroll
   for (int z = 0; z < RZ; ++z) {
@@ -156,6 +157,37 @@ __global__ void __launch_bounds__(kZrThreads) nbr_gemm_zrun_kernel(NbrGemm g) {
       dst[i] = v;
     }
   }
+}
+
+template <typename T, int RZ>
+__global__ void __launch_bounds__(kZrThreads) nbr_gemm_zrun_kernel(NbrGemm g) {
+  nbr_gemm_zrun_body<T, RZ>(g, native_vblock());
+}
+
+template <typename T, int RZ>
+__global__ void __launch_bounds__(kZrThreads) nbr_gemm_zrun_multi_kernel(const NbrGemm* __restrict__ gs,
+                                                                         const MultiGrid* __restrict__ grids, int n) {
+  __shared__ NbrGemm g;  // the item's description, read by the body from shared memory
+  const int i = multi_item(grids, n);
+  if (threadIdx.x == 0) g = gs[i];
+  __syncthreads();
+  nbr_gemm_zrun_body<T, RZ>(g, multi_vblock(grids[i]));
+}
+
+template <typename T, int RZ>
+cudaError_t launch_rz_multi(const NbrGemm* gs, const MultiGrid* grids, int n, long long blocks, cudaStream_t s) {
+  constexpr size_t smem = zrun_smem_bytes<T, RZ>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(nbr_gemm_zrun_multi_kernel<T, RZ>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (n <= 0 || blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  nbr_gemm_zrun_multi_kernel<T, RZ><<<(unsigned)blocks, kZrThreads, smem, s>>>(gs, grids, n);
+  return cudaGetLastError();
 }
 
 template <typename T, int RZ>
@@ -208,6 +240,28 @@ cudaError_t launch_nbr_gemm_zrun(const NbrGemm& g, int shape, cudaStream_t s) {
                                    g.accumulate, s);
 }
 
+template <typename T>
+void nbr_gemm_zrun_grid(const NbrGemm& g, int shape, unsigned out[3]) {
+  const int rz = zrun_rz<T>(shape);
+  out[0] = (unsigned)((long long)((g.grid[0] + kZrBX - 1) / kZrBX) * ((g.grid[1] + kZrBY - 1) / kZrBY) *
+                      ((g.grid[2] + rz - 1) / rz));
+  out[1] = (unsigned)g.ntiles;
+  out[2] = (unsigned)g.dsplit;
+}
+
+template <typename T>
+cudaError_t launch_nbr_gemm_zrun_multi(int shape, const NbrGemm* gs, const MultiGrid* grids, int n, long long blocks,
+                                       cudaStream_t s) {
+  return shape == 0 ? launch_rz_multi<T, zrun_rz<T>(0)>(gs, grids, n, blocks, s)
+                    : launch_rz_multi<T, zrun_rz<T>(1)>(gs, grids, n, blocks, s);
+}
+
+template void nbr_gemm_zrun_grid<float>(const NbrGemm&, int, unsigned[3]);
+template void nbr_gemm_zrun_grid<double>(const NbrGemm&, int, unsigned[3]);
+template cudaError_t launch_nbr_gemm_zrun_multi<float>(int, const NbrGemm*, const MultiGrid*, int, long long,
+                                                       cudaStream_t);
+template cudaError_t launch_nbr_gemm_zrun_multi<double>(int, const NbrGemm*, const MultiGrid*, int, long long,
+                                                        cudaStream_t);
 template cudaError_t launch_nbr_gemm_zrun<float>(const NbrGemm&, int, cudaStream_t);
 template cudaError_t launch_nbr_gemm_zrun<double>(const NbrGemm&, int, cudaStream_t);
 

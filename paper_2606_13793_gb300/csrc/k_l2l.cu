@@ -1,6 +1,7 @@
 // L2L on the CUDA cores (see tree_common.cuh for the layout and conventions).
 #include <cuda_bf16.h>
 
+#include "multi.cuh"
 #include "tree_common.cuh"
 
 namespace fmmgb {
@@ -15,11 +16,11 @@ using namespace tree;
 // harmonic components (c <= 1); the others are rebuilt from them first.
 // Lp = NULL: no parent locals (the coarsest level: only the rebuild).
 template <int P, typename Tp, typename Tc>
-__global__ void __launch_bounds__(kThreads) l2l_kernel(Level par, const Tp* __restrict__ Lp, Level child,
-                                                       Tc* __restrict__ Lc, int accumulate, int harm,
-                                                       const Tc* __restrict__ Lred) {
+__device__ __forceinline__ void l2l_body(const Level& par, const Tp* __restrict__ Lp, const Level& child,
+                                         Tc* __restrict__ Lc, int accumulate, int harm, const Tc* __restrict__ Lred,
+                                         const VBlock& vb) {
   constexpr int NC = ncoef_c(P);
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long t = (long long)vb.x * blockDim.x + threadIdx.x;
   const long long p = t >> 3;  // box of the parent level == parent block of the child level
   const int c = (int)(t & 7);
   if (p >= par.nbox) return;
@@ -73,6 +74,23 @@ __global__ void __launch_bounds__(kThreads) l2l_kernel(Level par, const Tp* __re
   }
 }
 
+template <int P, typename Tp, typename Tc>
+__global__ void __launch_bounds__(kThreads) l2l_kernel(Level par, const Tp* __restrict__ Lp, Level child,
+                                                       Tc* __restrict__ Lc, int accumulate, int harm,
+                                                       const Tc* __restrict__ Lred) {
+  l2l_body<P, Tp, Tc>(par, Lp, child, Lc, accumulate, harm, Lred, native_vblock());
+}
+
+// Many (parent level, child level) pairs in one launch (batched solves).
+template <int P, typename Tp, typename Tc>
+__global__ void __launch_bounds__(kThreads) l2l_multi_kernel(const L2lArgs* __restrict__ a,
+                                                             const MultiGrid* __restrict__ g, int n) {
+  const int i = multi_item(g, n);
+  const L2lArgs& x = a[i];
+  l2l_body<P, Tp, Tc>(x.par, static_cast<const Tp*>(x.Lp), x.child, static_cast<Tc*>(x.Lc), x.accumulate, x.harm,
+                      static_cast<const Tc*>(x.Lred), multi_vblock(g[i]));
+}
+
 }  // namespace
 
 template <typename Tp, typename Tc>
@@ -85,6 +103,18 @@ cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, cons
                                                                                           accumulate, harm, Lred)));
   return cudaGetLastError();
 }
+
+template <typename Tp, typename Tc>
+cudaError_t launch_l2l_multi(int p, const L2lArgs* args, const MultiGrid* grids, int n, long long blocks, int bs,
+                             cudaStream_t s) {
+  if (n == 0 || blocks == 0) return cudaSuccess;
+  FMM_ORDER_SWITCH(p, (l2l_multi_kernel<PP, Tp, Tc><<<(unsigned)blocks, bs, 0, s>>>(args, grids, n)));
+  return cudaGetLastError();
+}
+template cudaError_t launch_l2l_multi<float, float>(int, const L2lArgs*, const MultiGrid*, int, long long, int,
+                                                    cudaStream_t);
+template cudaError_t launch_l2l_multi<double, double>(int, const L2lArgs*, const MultiGrid*, int, long long, int,
+                                                      cudaStream_t);
 
 template cudaError_t launch_l2l<float, float>(const TreeTables&, const Level&, const float*, const Level&, float*, int,
                                               int, const float*, cudaStream_t);

@@ -1,6 +1,7 @@
 // Leaf evaluation (L2P + near sum + scaling) on the CUDA cores (see tree_common.cuh).
 #include <cuda_bf16.h>
 
+#include "multi.cuh"
 #include "tree_common.cuh"
 
 namespace fmmgb {
@@ -17,13 +18,12 @@ using namespace tree;
 // (128 registers, a few bytes spilled; 0.44 -> 0.37 ms at 512^3 against 169
 // registers and one block).
 template <int P, typename T>
-__global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(T) == 4) ? 2 : 1)
-    leaf_finish_kernel(Level leaf, const T* __restrict__ Lleaf,
-                                                               const T* __restrict__ near_box, int near_stride,
-                                                               const T* __restrict__ m2p, int nx, int ny, int b,
-                                                               T scale, T* __restrict__ phi) {
+__device__ __forceinline__ void leaf_finish_body(const Level& leaf, const T* __restrict__ Lleaf,
+                                                 const T* __restrict__ near_box, int near_stride,
+                                                 const T* __restrict__ m2p, int nx, int ny, int b, T scale,
+                                                 T* __restrict__ phi, const VBlock& vb) {
   constexpr int NC = ncoef_c(P);
-  const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long t = (long long)vb.x * kThreads + threadIdx.x;
   const Box B = box_of(leaf, t);
   if (!B.real) return;
   T L[NC];
@@ -107,6 +107,26 @@ __global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(T) == 4) ? 2 : 1)
       }
     }
   }
+}
+
+template <int P, typename T>
+__global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(T) == 4) ? 2 : 1)
+    leaf_finish_kernel(Level leaf, const T* __restrict__ Lleaf, const T* __restrict__ near_box, int near_stride,
+                       const T* __restrict__ m2p, int nx, int ny, int b, T scale, T* __restrict__ phi) {
+  leaf_finish_body<P, T>(leaf, Lleaf, near_box, near_stride, m2p, nx, ny, b, scale, phi, native_vblock());
+}
+
+// The leaf levels of many solves in one launch (batched solves).
+template <int P, typename T>
+__global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(T) == 4) ? 2 : 1)
+    leaf_finish_multi_kernel(const LeafArgs* __restrict__ a, const MultiGrid* __restrict__ g, int n) {
+  __shared__ LeafArgs x;  // the item's arguments, read by the body from shared memory
+  const int i = multi_item(g, n);
+  if (threadIdx.x == 0 && threadIdx.y == 0) x = a[i];
+  __syncthreads();
+  leaf_finish_body<P, T>(x.leaf, static_cast<const T*>(x.Lleaf), static_cast<const T*>(x.near_box), x.near_stride,
+                         static_cast<const T*>(x.m2p), x.nx, x.ny, x.b, (T)x.scale, static_cast<T*>(x.phi),
+                         multi_vblock(g[i]));
 }
 
 // Leaf evaluation with the analytic acceleration: also the gradient of the
@@ -295,6 +315,18 @@ cudaError_t launch_leaf_finish(const TreeTables& t, const Level& leaf, const T* 
                             leaf, Lleaf, near_box, near_stride, m2p, dims[0], dims[1], t.b, (T)scale, phi)));
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_leaf_finish_multi(int p, const LeafArgs* args, const MultiGrid* grids, int n, long long blocks,
+                                     cudaStream_t s) {
+  if (n == 0 || blocks == 0) return cudaSuccess;
+  FMM_ORDER_SWITCH(p, (leaf_finish_multi_kernel<PP, T><<<(unsigned)blocks, kThreads, 0, s>>>(args, grids, n)));
+  return cudaGetLastError();
+}
+template cudaError_t launch_leaf_finish_multi<float>(int, const LeafArgs*, const MultiGrid*, int, long long,
+                                                     cudaStream_t);
+template cudaError_t launch_leaf_finish_multi<double>(int, const LeafArgs*, const MultiGrid*, int, long long,
+                                                      cudaStream_t);
 
 template cudaError_t launch_leaf_finish<float>(const TreeTables&, const Level&, const float*, const float*, int,
                                                const float*, const int*, double, float*, cudaStream_t);

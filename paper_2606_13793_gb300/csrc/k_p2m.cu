@@ -1,6 +1,7 @@
 // P2M on the CUDA cores (see tree_common.cuh for the layout and conventions).
 #include <cuda_bf16.h>
 
+#include "multi.cuh"
 #include "tree_common.cuh"
 
 namespace fmmgb {
@@ -224,13 +225,12 @@ __device__ __forceinline__ void p2m_body(const Box& B, const T* __restrict__ rho
 // output is one contiguous run of parent rows: staged in shared memory and
 // written with 16-byte stores (FP32 rows, and the bf16 hi/lo planes).
 template <int P, typename T, bool DIP>
-__global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho, int nx, int ny, int b, Level leaf,
-                                                       T* __restrict__ Mleaf, __nv_bfloat16* __restrict__ Mhi,
-                                                       __nv_bfloat16* __restrict__ Mlo, T* __restrict__ rho_box,
-                                                       __nv_bfloat16* __restrict__ rhi,
-                                                       __nv_bfloat16* __restrict__ rlo, int* __restrict__ flag,
-                                                       int harm, T* __restrict__ Mfold, const T* __restrict__ dip,
-                                                       long long ncell) {
+__device__ __forceinline__ void p2m_block(const T* __restrict__ rho, int nx, int ny, int b, const Level& leaf,
+                                          T* __restrict__ Mleaf, __nv_bfloat16* __restrict__ Mhi,
+                                          __nv_bfloat16* __restrict__ Mlo, T* __restrict__ rho_box,
+                                          __nv_bfloat16* __restrict__ rhi, __nv_bfloat16* __restrict__ rlo,
+                                          int* __restrict__ flag, int harm, T* __restrict__ Mfold,
+                                          const T* __restrict__ dip, long long ncell, const VBlock& vb) {
   constexpr int NC = ncoef_c(P);
   constexpr int ROW = 8 * NC;     // values per parent row
   constexpr int ROWP = ROW + 8;   // staged row pitch
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho
   extern __shared__ __align__(16) unsigned char p2m_smem[];
   T* Ms = reinterpret_cast<T*>(p2m_smem);
   T* Mr = (harm && (Mhi || Mfold)) ? Ms + kP2mParents * ROWP : nullptr;
-  const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const long long t = (long long)vb.x * kThreads + threadIdx.x;
   const long long w = t >> 5;
   const Box B = box_of(leaf, (w >> 1) * 32 + (t & 31));
   if (B.par < leaf.npar) {
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho
       p2m_body<P, T, 0, DIP>(B, rho, nx, ny, b, leaf, Ms, Mr, rho_box, rhi, rlo, flag, dip, ncell);
   }
   __syncthreads();
-  const long long p0 = (long long)blockIdx.x * kP2mParents;
+  const long long p0 = (long long)vb.x * kP2mParents;
   const long long np = min((long long)kP2mParents, leaf.npar - p0);
   if (np <= 0) return;
   const int count = (int)np * ROW;  // a multiple of 8
@@ -284,6 +284,52 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho
       reinterpret_cast<uint4*>(Mlo + h0)[i] = *reinterpret_cast<const uint4*>(ll);
     }
   }
+}
+
+template <int P, typename T, bool DIP>
+__global__ void __launch_bounds__(kThreads) p2m_kernel(const T* __restrict__ rho, int nx, int ny, int b, Level leaf,
+                                                       T* __restrict__ Mleaf, __nv_bfloat16* __restrict__ Mhi,
+                                                       __nv_bfloat16* __restrict__ Mlo, T* __restrict__ rho_box,
+                                                       __nv_bfloat16* __restrict__ rhi,
+                                                       __nv_bfloat16* __restrict__ rlo, int* __restrict__ flag,
+                                                       int harm, T* __restrict__ Mfold, const T* __restrict__ dip,
+                                                       long long ncell) {
+  p2m_block<P, T, DIP>(rho, nx, ny, b, leaf, Mleaf, Mhi, Mlo, rho_box, rhi, rlo, flag, harm, Mfold, dip, ncell,
+                       native_vblock());
+}
+
+// The leaf levels of many solves in one launch (batched solves).
+template <int P, typename T>
+__global__ void __launch_bounds__(kThreads) p2m_multi_kernel(const P2mArgs* __restrict__ a,
+                                                             const MultiGrid* __restrict__ g, int n) {
+  __shared__ P2mArgs x;  // the item's arguments, read by the body from shared memory
+  const int i = multi_item(g, n);
+  if (threadIdx.x == 0 && threadIdx.y == 0) x = a[i];
+  __syncthreads();
+  p2m_block<P, T, false>(static_cast<const T*>(x.rho), x.nx, x.ny, x.b, x.leaf, static_cast<T*>(x.Mleaf),
+                         static_cast<__nv_bfloat16*>(x.Mhi), static_cast<__nv_bfloat16*>(x.Mlo),
+                         static_cast<T*>(x.rho_box), static_cast<__nv_bfloat16*>(x.rho_hi),
+                         static_cast<__nv_bfloat16*>(x.rho_lo), x.flag, x.harm, static_cast<T*>(x.Mfold), nullptr,
+                         x.ncell, multi_vblock(g[i]));
+}
+
+template <int P, typename T>
+cudaError_t p2m_multi_launch(const P2mArgs* args, const MultiGrid* grids, int n, long long blocks, int harm_rows,
+                             cudaStream_t s) {
+  constexpr size_t full = (size_t)kP2mParents * (8 * ncoef_c(P) + 8) * sizeof(T);
+  constexpr size_t red0 = (size_t)kP2mParents * (8 * nred_c(P) + 8) * sizeof(T);
+  constexpr size_t red = full + red0 <= 227 * 1024 ? red0 : 0;
+  if (harm_rows && red == 0) return cudaErrorInvalidValue;
+  const size_t smem = full + (harm_rows ? red : 0);
+  static bool attr = false;
+  if (!attr && full + red > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(p2m_multi_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(full + red));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  p2m_multi_kernel<P, T><<<(unsigned)blocks, kThreads, smem, s>>>(args, grids, n);
+  return cudaGetLastError();
 }
 
 template <int P, typename T, bool DIP>
@@ -337,6 +383,19 @@ cudaError_t launch_p2m(const TreeTables& t, const T* rho, const int dims[3], con
                             (long long)dims[0] * dims[1] * dims[2])));
   return e;
 }
+
+template <typename T>
+cudaError_t launch_p2m_multi(int p, const P2mArgs* args, const MultiGrid* grids, int n, long long blocks,
+                             int harm_rows, cudaStream_t s) {
+  if (n == 0 || blocks == 0) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  FMM_ORDER_SWITCH(p, (e = p2m_multi_launch<PP, T>(args, grids, n, blocks, harm_rows, s)));
+  return e;
+}
+template cudaError_t launch_p2m_multi<float>(int, const P2mArgs*, const MultiGrid*, int, long long, int,
+                                             cudaStream_t);
+template cudaError_t launch_p2m_multi<double>(int, const P2mArgs*, const MultiGrid*, int, long long, int,
+                                              cudaStream_t);
 
 template cudaError_t launch_p2m<float>(const TreeTables&, const float*, const int*, const Level&, float*, float*,
                                        void*, void*, void*, void*, int*, int, float*, cudaStream_t, const float*);
