@@ -51,6 +51,11 @@ def parse():
                     help="single: one n^3 lognormal field; batch: --batch Plummer fields of uneven sizes "
                          "(64/96/128/192)^3 solved as one CUDA graph")
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--batch-precision", default="fp32",
+                    help="precision of the batch's plans (fp32: the fused multi-field launches)")
+    ap.add_argument("--batch-mixed", type=int, default=1,
+                    help="batch workload: also time the same fields with bf16x3 plans (graph of per-field "
+                         "solves) and report it in config")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default CUDA-core contraction variants")
     ap.add_argument("--accel", default="fd", choices=["fd", "analytic"],
                     help="acceleration by the 5-point stencil of phi (fd) or from the expansions and pair forces")
@@ -568,7 +573,7 @@ def batch_main(args, fmm, inputs, torch, dist, rank, world):
     kernels each run one step kind over every field (the fused form).  Beside
     it: the same fields solved one after another without the graph, and the
     graph of per-field solves."""
-    prec = args.precision if args.precision != DEFAULT_PRECISION else "fp32"
+    prec = args.batch_precision
     p, b = args.order, args.leaf
     sizes = inputs.batch_sizes(args.batch, seed=2606 + rank)
     plans = [fmm.FMMPlan((s, s, s), p, b, prec, dx=1.0 / s) for s in sizes]
@@ -610,6 +615,22 @@ def batch_main(args, fmm, inputs, torch, dist, rank, world):
     per_field = fmm.BatchSolver(plans, autotune=False, fused=False)
     pf_ms = timed(lambda: per_field.solve(rhos, phis, accs))
     per_field.close()
+    mixed = None
+    if args.batch_mixed and prec != "bf16x3":
+        # the same fields with bf16x3 plans (tensor-core M2L and near field;
+        # the graph of per-field solves), error of field 0 against the FP32 run
+        mplans = [fmm.FMMPlan((s, s, s), p, b, "bf16x3", dx=1.0 / s) for s in sizes]
+        mb = fmm.BatchSolver(mplans, autotune=not args.no_autotune)
+        mphis = [q._empty() for q in mplans]
+        maccs = [q._empty((3,)) for q in mplans]
+        m_ms = timed(lambda: mb.solve(rhos, mphis, maccs))
+        mixed = {"mcells_s": cells * args.steps * world / (m_ms / 1e3) / 1e6, "ms_per_step": m_ms / args.steps,
+                 "launches": mb.launches(True), "fused": mb.fused == 1,
+                 "field0_phi_rel_diff_vs_fp32": float(torch.linalg.vector_norm((mphis[0] - phis[0]).double())
+                                                      / torch.linalg.vector_norm(phis[0].double()))}
+        mb.close()
+        for q in mplans:
+            q.close()
     with ClockSampler(gpu_index_for_smi(torch)) as clk:
         ms = timed(step)
     for q in plans:
@@ -651,6 +672,7 @@ def batch_main(args, fmm, inputs, torch, dist, rank, world):
                                        + (" of multi-field launches" if batch.fused == 1 else " of per-field solves"),
                            "fused": batch.fused == 1,
                            "per_field_graph_mcells_s": cells * args.steps * world / (pf_ms / 1e3) / 1e6,
+                           "bf16x3_batch": mixed,
                            "cells_per_step": cells, "size_counts": {str(s): sizes.count(s) for s in sorted(set(sizes))},
                            "precision": prec, "autotuned": not args.no_autotune,
                            "sequential_no_graph_mcells_s":

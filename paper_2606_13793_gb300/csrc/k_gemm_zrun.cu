@@ -43,6 +43,27 @@ struct Vec<double> {
   static constexpr int n = 2;
 };
 
+// Packed FP32 multiply-add (two lanes of IEEE fma, round to nearest: the
+// same results as two scalar fmaf): one instruction for two products halves
+// the issue slots of the FP32 kernel, which the scalar form spent almost
+// entirely on FMAs and shared-memory loads.
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_splat(float a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+  return r;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+
 template <int RZ>
 struct ZrHalo {
   static constexpr int hx = kZrBX + 2, hy = kZrBY + 2, hz = RZ + 2;
@@ -76,11 +97,17 @@ __device__ __forceinline__ void nbr_gemm_zrun_body(const NbrGemm& g, const VBloc
   const int nxy = 9 / g.dsplit;  // (dx, dy) pairs of this CTA
   const int xy0 = (g.dsplit > 1 ? (int)vb.z : 0) * nxy;
 
+  constexpr bool kPacked = sizeof(T) == 4;  // FP32: column pairs in packed registers
   T acc[RZ][kZrCT];
+  unsigned long long acc2[kPacked ? RZ : 1][kZrCT / 2];
 #pragma unroll
   for (int z = 0; z < RZ; ++z)
 #pragma unroll
     for (int c = 0; c < kZrCT; ++c) acc[z][c] = T(0);
+#pragma unroll
+  for (int z = 0; z < (kPacked ? RZ : 1); ++z)
+#pragma unroll
+    for (int c = 0; c < kZrCT / 2; ++c) acc2[z][c] = 0ull;  // +0.0f in both lanes
 
   for (int kc = 0; kc < K; kc += kZrKC) {
     // A halo, one vector of VN reduction values per load
@@ -118,22 +145,48 @@ __device__ __forceinline__ void nbr_gemm_zrun_body(const NbrGemm& g, const VBloc
         T a[RZ + 2];
 #pragma unroll
         for (int zz = 0; zz < RZ + 2; ++zz) a[zz] = Ab[k * H::stride + zz * H::hx * H::hy];
+        if constexpr (kPacked) {
+          unsigned long long a2[RZ + 2];
 #pragma unroll
-        for (int dz = 0; dz < 3; ++dz) {
-          T b[kZrCT];
-          const V* wv = reinterpret_cast<const V*>(Wb + (dz * kZrKC + k) * kNTile);
+          for (int zz = 0; zz < RZ + 2; ++zz) a2[zz] = f2_splat(a[zz]);
 #pragma unroll
-          for (int i = 0; i < kZrCT / VN; ++i) *reinterpret_cast<V*>(&b[i * VN]) = wv[i];
+          for (int dz = 0; dz < 3; ++dz) {
+            const ulonglong2* wv = reinterpret_cast<const ulonglong2*>(Wb + (dz * kZrKC + k) * kNTile);
+            const ulonglong2 w0 = wv[0], w1 = wv[1];  // columns (0,1) (2,3) | (4,5) (6,7)
+            const unsigned long long b2[4] = {w0.x, w0.y, w1.x, w1.y};
 #pragma unroll
-          for (int z = 0; z < RZ; ++z)
+            for (int z = 0; z < RZ; ++z)
 #pragma unroll
-            for (int c = 0; c < kZrCT; ++c) acc[z][c] = fma(a[z + dz], b[c], acc[z][c]);
+              for (int c = 0; c < kZrCT / 2; ++c) acc2[z][c] = f2_fma(a2[z + dz], b2[c], acc2[z][c]);
+          }
+        } else {
+#pragma unroll
+          for (int dz = 0; dz < 3; ++dz) {
+            T b[kZrCT];
+            const V* wv = reinterpret_cast<const V*>(Wb + (dz * kZrKC + k) * kNTile);
+#pragma unroll
+            for (int i = 0; i < kZrCT / VN; ++i) *reinterpret_cast<V*>(&b[i * VN]) = wv[i];
+#pragma unroll
+            for (int z = 0; z < RZ; ++z)
+#pragma unroll
+              for (int c = 0; c < kZrCT; ++c) acc[z][c] = fma(a[z + dz], b[c], acc[z][c]);
+          }
         }
       }
     }
     __syncthreads();
   }
 
+  if constexpr (kPacked) {
+#pragma unroll
+    for (int z = 0; z < RZ; ++z)
+#pragma unroll
+      for (int c = 0; c < kZrCT / 2; ++c) {
+        const float2 v = f2_unpack(acc2[z][c]);
+        acc[z][2 * c] = v.x;
+        acc[z][2 * c + 1] = v.y;
+      }
+  }
   const int col0 = tile * kNTile + cg * kZrCT;
   if (col0 >= g.n_cols) return;
   const int x = ox + xr, y = oy + yr;
@@ -160,12 +213,12 @@ __device__ __forceinline__ void nbr_gemm_zrun_body(const NbrGemm& g, const VBloc
 }
 
 template <typename T, int RZ>
-__global__ void __launch_bounds__(kZrThreads) nbr_gemm_zrun_kernel(NbrGemm g) {
+__global__ void __launch_bounds__(kZrThreads, 4) nbr_gemm_zrun_kernel(NbrGemm g) {
   nbr_gemm_zrun_body<T, RZ>(g, native_vblock());
 }
 
 template <typename T, int RZ>
-__global__ void __launch_bounds__(kZrThreads) nbr_gemm_zrun_multi_kernel(const NbrGemm* __restrict__ gs,
+__global__ void __launch_bounds__(kZrThreads, 4) nbr_gemm_zrun_multi_kernel(const NbrGemm* __restrict__ gs,
                                                                          const MultiGrid* __restrict__ grids, int n) {
   __shared__ NbrGemm g;  // the item's description, read by the body from shared memory
   const int i = multi_item(grids, n);
