@@ -342,20 +342,23 @@ class FMMPlan:
 
     TC_SCHEDULE = {"m2l": 0, "near": 1, "m2p": 2}
 
+    TC_SCHEDULE_NAMES = {0: "span", 1: "prefix", 2: "dedicated"}
+
     def tc_schedule(self, what: str):
-        """("prefix" | "span" | None, set of available schedules) of the
-        tensor-core contraction `what` ("m2l", "near" or "m2p")."""
+        """("prefix" | "span" | "dedicated" | None, set of available
+        schedules) of the tensor-core contraction `what` ("m2l", "near" or
+        "m2p"); "dedicated" is the leaf-4 near-field kernel."""
         pre, avail = ctypes.c_int(), ctypes.c_int()
         _check(self.lib, self.lib.fmm_plan_tc_schedule(self._h, self.TC_SCHEDULE[what], ctypes.byref(pre),
                                                         ctypes.byref(avail)))
-        names = {n for bit, n in ((1, "span"), (2, "prefix")) if avail.value & bit}
-        return ({1: "prefix", 0: "span"}.get(pre.value), names)
+        names = {n for bit, n in ((1, "span"), (2, "prefix"), (4, "dedicated")) if avail.value & bit}
+        return (self.TC_SCHEDULE_NAMES.get(pre.value), names)
 
     def set_tc_schedule(self, what: str, schedule: str):
-        if schedule not in ("prefix", "span"):
-            raise ValueError("schedule is 'prefix' or 'span'")
-        _check(self.lib, self.lib.fmm_plan_set_tc_schedule(self._h, self.TC_SCHEDULE[what],
-                                                            1 if schedule == "prefix" else 0))
+        code = {v: k for k, v in self.TC_SCHEDULE_NAMES.items()}.get(schedule)
+        if code is None:
+            raise ValueError("schedule is 'prefix', 'span' or 'dedicated'")
+        _check(self.lib, self.lib.fmm_plan_set_tc_schedule(self._h, self.TC_SCHEDULE[what], code))
 
     def debug_timeout(self):
         """Test hook: the next solve's first prefix-schedule M2L launch lets

@@ -19,8 +19,8 @@ LIB_NAME = "libfmm_gb300.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
 
 SOURCES = ["capi.cu", "k_tree.cu", "k_p2m.cu", "k_m2m.cu", "k_l2l.cu", "k_leaf.cu", "k_gemm_simt.cu", "k_gemm_zrun.cu", "k_fd.cu",
-           "k_m2l_tc.cu", "k_nbr_tc.cu"]
-HEADERS = ["fmm_internal.h", "tree_common.cuh", "tc_ptx.cuh"]
+           "k_m2l_tc.cu", "k_nbr_tc.cu", "k_near_tc.cu"]
+HEADERS = ["fmm_internal.h", "tree_common.cuh", "tc_ptx.cuh", "multi.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-Wall"]

@@ -247,6 +247,10 @@ struct fmm_plan_s {
   bool tp_m2l = false, tp_m2l_t = false, tp_m2p = false, tp_near = false;
   bool span_m2l = false, span_m2l_t = false, span_near = false, span_m2p = false;
   bool use_tp[3] = {true, false, true};
+  // the dedicated near-field kernel of leaf 4 (k_near_tc.cu), used when
+  // present unless another schedule is selected
+  bool near4 = false, use_near4 = true;
+  NearTcLaunch ntl{};
   bool inject_timeout = false;  // test hook (fmm_plan_debug_timeout): the next prefix launch starves its first stage
   TpLaunch tpl{}, tpl_t{}, tpm{}, tpn{};
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -1254,6 +1258,29 @@ double near_entry(int b, const int D[3], int s, int n) {
   return r2 == 0.0 ? 0.0 : r[q - 1] / (r2 * std::sqrt(r2));
 }
 
+// Weights of the dedicated leaf-4 near-field kernel (k_near_tc.cu): per
+// neighbour d the B operand's shared-memory image of W_d[k][n] =
+// near_entry(d, k, n): row n (target cell) of 128 B holds the 64 source
+// cells k, 16-byte chunks swizzled by (n mod 8); the bf16 hi plane, then the
+// lo plane (w - hi rounded to bf16).
+void near4_weights(std::vector<unsigned char>& W4) {
+  W4.assign((size_t)27 * kNtPieceBytes, 0);
+  for (int d = 0; d < 27; ++d) {
+    const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+    unsigned char* piece = W4.data() + (size_t)d * kNtPieceBytes;
+    for (int n = 0; n < 64; ++n)
+      for (int k = 0; k < 64; ++k) {
+        const double w = near_entry(4, D, k, n);
+        const uint16_t h = bf16_rn((float)w);
+        const uint16_t l = bf16_rn((float)(w - (double)bf16_to_f(h)));
+        const int byte = 2 * k;
+        const size_t o = (size_t)n * 128 + (size_t)((((byte >> 4) ^ (n & 7)) << 4) | (byte & 15));
+        std::memcpy(piece + o, &h, 2);
+        std::memcpy(piece + kNtPieceBytes / 2 + o, &l, 2);
+      }
+  }
+}
+
 // Near field (eq. direct) as the same contraction over leaf boxes: column n =
 // (component, target cell), reduction k = source cell of neighbour box d,
 // weight near_entry(d, k, n).
@@ -1981,6 +2008,18 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
       }
     }
   }
+  if (P->near_tc && P->b == 4 && P->near_comps == 1) {
+    std::vector<unsigned char> W4;
+    near4_weights(W4);
+    unsigned char* dw = nullptr;
+    if ((st = P->upload(W4, &dw, s))) return cleanup(st);
+    P->ntl.W = dw;
+    P->ntl.C = reinterpret_cast<float*>(P->arena + P->near_off);
+    for (int q = 0; q < 3; ++q) P->ntl.grid[q] = P->lev[P->L].n[q];
+    P->ntl.err = P->d_flag;
+    P->ntl.idesc = host_idesc(TC_BF16X3, 64);
+    P->near4 = true;
+  }
   if (P->near_tc) {
     // activation rows: the b^3 cell values of a leaf box (the output rows carry
     // near_comps x b^3 columns)
@@ -2218,6 +2257,19 @@ bool tc_prefix(fmm_plan_t P, int what) {
   return tp && (P->use_tp[what] || !span);
 }
 
+// Tensor-core near field: the dedicated leaf-4 kernel, or the prefix or span
+// schedule.
+fmm_status do_near_tc(fmm_plan_t P, cudaStream_t s) {
+  if (P->near4 && P->use_near4) {
+    CUDA_TRY(launch_near_tc4(P->ntl, P->map_near_hi, P->map_near_lo, s));
+  } else if (tc_prefix(P, TS_NEAR)) {
+    CUDA_TRY(launch_nbr_tc(P->tpn, P->map_near_hi, P->map_near_lo, s));
+  } else {
+    for (const TcLaunch& NL : P->tcn) CUDA_TRY(launch_m2l_tc(NL, P->map_near_hi, P->map_near_lo, s));
+  }
+  return FMM_OK;
+}
+
 // Final-stage M2P of the leaf level (tensor cores when the leaf level is on
 // them and the schedule fits, else the CUDA-core contraction).
 fmm_status do_m2p(fmm_plan_t P, cudaStream_t s) {
@@ -2401,10 +2453,7 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
     CUDA_TRY(launch_nbr_gemm<T>(g, s));
   } else if (P->near_tc) {
     StageTimer t(P, ST_NEAR_TC, s);
-    if (tc_prefix(P, TS_NEAR))
-      CUDA_TRY(launch_nbr_tc(P->tpn, P->map_near_hi, P->map_near_lo, s));
-    else
-      for (const TcLaunch& NL : P->tcn) CUDA_TRY(launch_m2l_tc(NL, P->map_near_hi, P->map_near_lo, s));
+    if ((st = do_near_tc(P, s))) return st;
   } else if (!near_side) {
     StageTimer t(P, ST_NEAR, s);
     CUDA_TRY(launch_nbr_gemm<T>(near_gemm(P), s));
@@ -2567,7 +2616,8 @@ int fmm_solve_launches(fmm_plan_t P, int with_accel) {
     if (l == 2 && L == 2 && P->m2p) n += 1;          // zero leaf locals (final-stage M2P, no parent far field)
     if (!P->lev[l].tc && P->m2l_choice[l].dsplit > 1 && !(l == L && P->m2p)) n += 1;  // partial-sum reduction
   }
-  n += P->near_tc ? (tc_prefix(P, TS_NEAR) ? 1 : (int)P->tcn.size()) + 1 : 2;  // near field + leaf finish
+  n += P->near_tc ? ((P->near4 && P->use_near4) || tc_prefix(P, TS_NEAR) ? 1 : (int)P->tcn.size()) + 1
+                   : 2;  // near field + leaf finish
   if (!P->near_tc && P->near_choice.dsplit > 1) n += 1;
   if (with_accel && P->near_comps == 1) n += 1;  // FD stencil (the analytic force comes with the leaf kernel)
   return n;
@@ -3284,7 +3334,7 @@ namespace {
 using SimtChoice = fmm_plan_s::SimtChoice;
 std::mutex g_tune_mu;
 std::map<std::string, SimtChoice> g_tune_cache;
-std::map<std::string, bool> g_tc_tune_cache;  // tensor-core schedule: prefix (true) or span
+std::map<std::string, int> g_tc_tune_cache;  // tensor-core schedule: 0 span, 1 prefix, 2 dedicated near field
 
 bool choice_valid(fmm_plan_t P, NbrGemm g, const std::vector<int>& tk, size_t es, SimtChoice c) {
   // FP64 levels of a tensor-core plan keep the small-footprint tile that can
@@ -3355,7 +3405,8 @@ fmm_status tune_one(fmm_plan_t P, NbrGemm g, const std::vector<int>& tk, const c
 fmm_status tune_tc(fmm_plan_t P, int what, cudaStream_t s) {
   const bool tp = what == TS_M2L ? P->tp_m2l : what == TS_NEAR ? P->tp_near : P->tp_m2p;
   const bool span = what == TS_M2L ? P->span_m2l : what == TS_NEAR ? P->span_near : P->span_m2p;
-  if (!tp || !span) return FMM_OK;
+  const bool ded = what == TS_NEAR && P->near4;  // the dedicated near-field kernel
+  if ((int)tp + (int)span + (int)ded < 2) return FMM_OK;
   int level = P->L;  // M2L: the finest tensor-core level (the M2P's level excluded)
   if (what == TS_M2L) {
     level = -1;
@@ -3367,23 +3418,23 @@ fmm_status tune_tc(fmm_plan_t P, int what, cudaStream_t s) {
   char key[160];
   std::snprintf(key, sizeof key, "tc%d/%d,%d,%d/%d/%d/%d/%d/%d", what, g[0], g[1], g[2], P->p, P->b, P->tc_kind,
                 P->harm ? 1 : 0, P->near_comps);
+  // candidate c: 0 span, 1 prefix, 2 the dedicated near-field kernel
+  auto select = [&](int c) {
+    P->use_tp[what] = c == 1;
+    if (what == TS_NEAR) P->use_near4 = c == 2;
+  };
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tc_tune_cache.find(key);
     if (it != g_tc_tune_cache.end()) {
-      P->use_tp[what] = it->second;
+      select(it->second);
       return FMM_OK;
     }
   }
   auto launch = [&]() -> fmm_status {
     if (what == TS_M2L) return do_m2l(P, level, s);
     if (what == TS_M2P) return do_m2p(P, s);
-    if (tc_prefix(P, TS_NEAR)) {
-      CUDA_TRY(launch_nbr_tc(P->tpn, P->map_near_hi, P->map_near_lo, s));
-    } else {
-      for (const TcLaunch& NL : P->tcn) CUDA_TRY(launch_m2l_tc(NL, P->map_near_hi, P->map_near_lo, s));
-    }
-    return FMM_OK;
+    return do_near_tc(P, s);
   };
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CUDA_TRY(cudaEventCreate(&e0));
@@ -3391,23 +3442,27 @@ fmm_status tune_tc(fmm_plan_t P, int what, cudaStream_t s) {
     cudaEventDestroy(e0);
     return fail(FMM_ERR_CUDA, "event creation failed");
   }
-  float ms[2] = {0.f, 0.f};
+  const bool have[3] = {span, tp, ded};
+  float ms[3] = {0.f, 0.f, 0.f};
+  int best = -1;
   fmm_status st = FMM_OK;
-  for (int prefix = 0; prefix < 2 && st == FMM_OK; ++prefix) {
-    P->use_tp[what] = prefix != 0;
+  for (int c = 0; c < 3 && st == FMM_OK; ++c) {
+    if (!have[c]) continue;
+    select(c);
     if ((st = launch())) break;  // warm-up
     if (cudaEventRecord(e0, s) != cudaSuccess) st = fail(FMM_ERR_CUDA, "event record failed");
     for (int r = 0; r < 3 && st == FMM_OK; ++r) st = launch();
     if (st == FMM_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                         cudaEventElapsedTime(&ms[prefix], e0, e1) != cudaSuccess))
+                         cudaEventElapsedTime(&ms[c], e0, e1) != cudaSuccess))
       st = fail(FMM_ERR_CUDA, "tensor-core schedule timing failed");
+    if (st == FMM_OK && (best < 0 || ms[c] < ms[best])) best = c;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != FMM_OK) return st;
-  P->use_tp[what] = ms[1] < ms[0];
+  select(best);
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tc_tune_cache[key] = P->use_tp[what];
+  g_tc_tune_cache[key] = best;
   return FMM_OK;
 }
 
@@ -3443,8 +3498,9 @@ extern "C" fmm_status fmm_plan_tc_schedule(fmm_plan_t P, int what, int* prefix, 
   if (!P || what < 0 || what > 2) return fail(FMM_ERR_ARG, "plan is NULL or `what` is not 0, 1 or 2");
   const bool tp = what == TS_M2L ? P->tp_m2l : what == TS_NEAR ? P->tp_near : P->tp_m2p;
   const bool span = what == TS_M2L ? P->span_m2l : what == TS_NEAR ? P->span_near : P->span_m2p;
-  if (available) *available = (span ? 1 : 0) | (tp ? 2 : 0);
-  if (prefix) *prefix = (tp || span) ? (tc_prefix(P, what) ? 1 : 0) : -1;
+  const bool ded = what == TS_NEAR && P->near4;
+  if (available) *available = (span ? 1 : 0) | (tp ? 2 : 0) | (ded ? 4 : 0);
+  if (prefix) *prefix = (ded && P->use_near4) ? 2 : (tp || span) ? (tc_prefix(P, what) ? 1 : 0) : -1;
   return FMM_OK;
 }
 
@@ -3463,11 +3519,19 @@ extern "C" fmm_status fmm_plan_set_tc_schedule(fmm_plan_t P, int what, int prefi
   if (!P || what < 0 || what > 2) return fail(FMM_ERR_ARG, "plan is NULL or `what` is not 0, 1 or 2");
   const bool tp = what == TS_M2L ? P->tp_m2l : what == TS_NEAR ? P->tp_near : P->tp_m2p;
   const bool span = what == TS_M2L ? P->span_m2l : what == TS_NEAR ? P->span_near : P->span_m2p;
+  if (prefix == 2) {  // the dedicated near-field kernel
+    if (what != TS_NEAR || !P->near4)
+      return fail(FMM_ERR_ARG, "the dedicated kernel exists for the near field of leaf-4 potential plans only");
+    P->use_near4 = true;
+    return FMM_OK;
+  }
+  if (prefix < 0 || prefix > 2) return fail(FMM_ERR_ARG, "schedule must be 0 (span), 1 (prefix) or 2 (dedicated)");
   if (prefix ? !tp : !span) return fail(FMM_ERR_ARG, "the %s schedule of that contraction does not exist in this plan",
                                         prefix ? "prefix" : "span");
   if (what == TS_M2L && P->asym && !(prefix ? P->tp_m2l_t : P->span_m2l_t))
     return fail(FMM_ERR_ARG, "the transposed M2L has no %s schedule", prefix ? "prefix" : "span");
   P->use_tp[what] = prefix != 0;
+  if (what == TS_NEAR) P->use_near4 = false;
   return FMM_OK;
 }
 

@@ -156,6 +156,23 @@ template <typename Tp, typename Tc>
 // of in the full rows
 cudaError_t launch_l2l(const TreeTables& t, const Level& par, const Tp* Lp, const Level& child, Tc* Lc, int accumulate,
                        int harm, const Tc* Lred, cudaStream_t s);
+// Near field of leaf-4 boxes on the tensor cores, bf16x3 (k_near_tc.cu):
+// W holds, per neighbour d = (dx+1) + 3 (dy+1) + 9 (dz+1), the 64 x 64
+// weights W_d[source cell][target cell] as the B operand's shared-memory
+// image: 64 rows (target cells) of 128 B (64 bf16 source cells), 16-byte
+// chunks swizzled by (row mod 8); the hi plane, then the lo plane.
+constexpr int kNtPieceBytes = 2 * 64 * 128;
+struct NearTcLaunch {
+  const unsigned char* W;  // device, 27 x kNtPieceBytes
+  float* C;                // device [leaf boxes][64], written (not accumulated)
+  int grid[3];             // leaf boxes per axis
+  int* err;                // plan flag: FMM_ERR_TIMEOUT bit and wait site
+  uint32_t idesc;          // MMA instruction descriptor, M = 128, N = 64, bf16 in, FP32 out
+};
+// map_hi / map_lo: the bf16 hi / lo density rows (64 values per leaf box),
+// box 64 x 8 x 18 x 1 with 128-byte swizzle (make_row_map).
+cudaError_t launch_near_tc4(const NearTcLaunch& L, const void* map_hi, const void* map_lo, cudaStream_t s);
+
 // Multi-item forms (batched solves, multi.cuh): args and grids are device
 // arrays of n items sorted by first block; blocks = the launch's total, bs
 // the block size every item's grid was computed with.

@@ -1336,8 +1336,59 @@ int harmonic_check() {
 
 }  // namespace
 
+// The dedicated leaf-4 near-field kernel (k_near_tc.cu): its weight image
+// decoded with the 128-byte swizzle the MMA reads (row n, 16-byte chunk
+// (2k / 16) xor (n mod 8)), hi + lo against near_entry, and its products
+// (hi*lo + lo*hi + hi*hi over the 27 neighbours, lo*lo dropped) emulated on
+// random densities against the FP64 contraction.
+int near4_check() {
+  std::vector<unsigned char> W4;
+  near4_weights(W4);
+  if (W4.size() != (size_t)27 * kNtPieceBytes) return std::printf("near4: image size %zu\n", W4.size()), 1;
+  auto rd = [&](int d, int plane, int n, int k) {
+    const size_t o = (size_t)d * kNtPieceBytes + (size_t)plane * (kNtPieceBytes / 2) + (size_t)n * 128 +
+                     (size_t)((((2 * k) >> 4) ^ (n & 7)) << 4) + (size_t)((2 * k) & 15);
+    uint16_t h;
+    std::memcpy(&h, W4.data() + o, 2);
+    return (double)bf16_to_f(h);
+  };
+  double split = 0.0;
+  for (int d = 0; d < 27; ++d) {
+    const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+    for (int n = 0; n < 64; ++n)
+      for (int k = 0; k < 64; ++k) {
+        const double w = near_entry(4, D, k, n);
+        split = std::max(split, std::fabs(rd(d, 0, n, k) + rd(d, 1, n, k) - w) / std::fabs(w));
+      }
+  }
+  std::mt19937 rng(4);
+  std::uniform_real_distribution<double> U(0.0, 1.0);
+  double worst = 0.0;
+  for (int trial = 0; trial < 4; ++trial) {
+    std::vector<double> A(27 * 64);
+    for (double& a : A) a = U(rng);
+    for (int n = 0; n < 64; ++n) {
+      double exact = 0.0, mag = 0.0, emul = 0.0;
+      for (int d = 0; d < 27; ++d) {
+        const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+        for (int k = 0; k < 64; ++k) {
+          const double a = A[d * 64 + k], w = near_entry(4, D, k, n);
+          const double ah = bf16_to_f(bf16_rn((float)a)), al = bf16_to_f(bf16_rn((float)(a - ah)));
+          exact += a * w;
+          mag += std::fabs(a * w);
+          emul += ah * rd(d, 1, n, k) + al * rd(d, 0, n, k) + ah * rd(d, 0, n, k);
+        }
+      }
+      worst = std::max(worst, std::fabs(emul - exact) / mag);
+    }
+  }
+  std::printf("near4: hi + lo vs weight %.2e, products vs FP64 %.2e of sum |terms|\n", split, worst);
+  return (split <= 1.0 / 65536.0 && worst <= 1e-5) ? 0 : 1;
+}
+
 int main(int argc, char** argv) {
   const std::string mode = argc > 1 ? argv[1] : "";
+  if (mode == "near4") return near4_check();
   if (mode == "plant") return planted_mistakes() ? 1 : 0;
   if (mode == "harmonic") return harmonic_check() ? 1 : 0;
   if (mode == "cuda-core") return cc_tiles_check() ? 1 : 0;

@@ -232,23 +232,30 @@ def test_tc_both_schedules_match_oracle(orc, case):
     else:
         ref_phi = orc.fmm_m2p(rho, 4, p)
     res = {}
-    for sched in ("span", "prefix"):
-        phi, acc, ran = _solve_with(rho.astype(np.float32), p, prec, {w: sched for w in ("m2l", "near", "m2p")},
-                                    final_stage)
+    for sched in ("span", "prefix", "dedicated"):
+        want = {w: sched for w in ("m2l", "near", "m2p")}
+        if sched == "dedicated":  # the leaf-4 near-field kernel beside the default M2L / M2P schedules
+            want = {"near": "dedicated"}
+        phi, acc, ran = _solve_with(rho.astype(np.float32), p, prec, want, final_stage)
         err = rel_l2(phi, ref_phi)
         print(f"{prec} p={p} {final_stage} {sched}: ran {ran}, phi rel err {err:.3e}")
         assert err <= TOL[prec]
         if final_stage == "m2l":
             assert rel_l2(acc, ref["accel"]) <= acc_tol(64, prec)
         res[sched] = (phi, ran)
-    if res["span"][1] != res["prefix"][1]:  # both forms ran somewhere: they agree closely
-        assert rel_l2(res["span"][0], res["prefix"][0]) <= (2e-6 if prec == "bf16x3" else 2e-4)
+    for a, b in (("span", "prefix"), ("span", "dedicated")):
+        if res[a][1] != res[b][1]:  # both forms ran somewhere: they agree closely
+            assert rel_l2(res[a][0], res[b][0]) <= (2e-6 if prec == "bf16x3" else 2e-4)
 
 
 def test_tc_schedule_selection_api():
     plan = fmm.FMMPlan((64, 64, 64), 6, 4, "bf16x3")
     cur, avail = plan.tc_schedule("near")
-    assert cur == "span" and avail == {"span", "prefix"}
+    assert cur == "dedicated" and avail == {"span", "prefix", "dedicated"}
+    plan.set_tc_schedule("near", "span")
+    assert plan.tc_schedule("near")[0] == "span"
+    with pytest.raises(fmm.FMMError):
+        plan.set_tc_schedule("m2l", "dedicated")
     cur, avail = plan.tc_schedule("m2l")
     assert cur == "prefix" and "prefix" in avail
     assert plan.tc_schedule("m2p")[0] is None  # final stage is M2L here

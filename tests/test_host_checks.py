@@ -95,6 +95,15 @@ def test_planted_prefix_mistakes_are_caught(host_check):
     assert "two owners on one ring: 40 of 40" in r.stdout
 
 
+def test_dedicated_near_field_weights_and_products(host_check):
+    """The leaf-4 near-field kernel's weight image (swizzled hi / lo planes)
+    decodes to the near-field weights, and its three products reproduce the
+    FP64 contraction to the split precision."""
+    r = _run(host_check, "near4")
+    print(r.stdout)
+    assert r.returncode == 0, r.stdout + r.stderr
+
+
 def test_harmonic_compression_is_exact(host_check):
     r = _run(host_check, "harmonic")
     assert r.returncode == 0, r.stdout + r.stderr
