@@ -288,18 +288,22 @@ fmm_status fmm_plan_autotune(fmm_plan_t plan, void* stream);
  * schedules with the same arithmetic: the span schedule (k_m2l_tc.cu: column
  * groups of one order range, one MMA per group and K step) and the prefix
  * schedule (k_nbr_tc.cu: all columns of a pass in one accumulator set, one
- * wide MMA per K step over the prefix of columns it feeds).  Where both
- * exist, a plan starts with the one measured faster on GB300 at 512^3 (M2L
- * and M2P: prefix; near field: span) and fmm_plan_autotune times both.
- *   fmm_plan_tc_schedule     : *available = bit 0 span, bit 1 prefix;
- *                              *prefix = 1 prefix, 0 span, -1 neither (the
- *                              contraction is not on the tensor cores).
- *                              Either pointer may be NULL.
- *   fmm_plan_set_tc_schedule : selects one; FMM_ERR_ARG if that schedule does
- *                              not exist for the contraction (or, for the M2L
- *                              of a plan with mult_order < order, for its
- *                              transposed form).
- * Both schedules give the same sums up to the order of the FP32 additions.
+ * wide MMA per K step over the prefix of columns it feeds).  The near field
+ * of leaf-4 plans without the analytic force also has a third, dedicated
+ * kernel (k_near_tc.cu: four row tiles per weight copy, one accumulation
+ * segment per neighbour column).  A plan starts with the one measured
+ * fastest on GB300 at 512^3 (M2L and M2P: prefix; near field: the dedicated
+ * kernel where it exists, else span) and fmm_plan_autotune times them all.
+ *   fmm_plan_tc_schedule     : *available = bit 0 span, bit 1 prefix, bit 2
+ *                              dedicated; *prefix = 2 dedicated, 1 prefix,
+ *                              0 span, -1 none (the contraction is not on the
+ *                              tensor cores).  Either pointer may be NULL.
+ *   fmm_plan_set_tc_schedule : selects one (`prefix` 0, 1 or 2 as above);
+ *                              FMM_ERR_ARG if that schedule does not exist
+ *                              for the contraction (or, for the M2L of a plan
+ *                              with mult_order < order, for its transposed
+ *                              form).
+ * All schedules give the same sums up to the order of the FP32 additions.
  * The paper has no counterpart.
  */
 fmm_status fmm_plan_tc_schedule(fmm_plan_t plan, int what, int* prefix, int* available);

@@ -2150,6 +2150,16 @@ struct StageTimer {
   }
 };
 
+// The last L2L (L - 1 -> leaf) runs inside the leaf kernel (potential-only
+// near field, M2L final stage, both levels in the data's type); the leaf
+// level's locals then stay the M2L's in memory.
+bool fused_down(fmm_plan_t P) {
+  const int L = P->L;
+  if (L < 3 || P->m2p || P->near_comps != 1) return false;
+  const int want = P->f64_data() ? 1 : 0;
+  return P->lev[L].f64 == want && P->lev[L - 1].f64 == want;
+}
+
 // Per-level dispatch helpers (a level's expansions are FP64 or FP32).
 fmm_status do_m2m(fmm_plan_t P, const TreeTables& tt, int l, cudaStream_t s) {
   const Level &c = P->lev[l], &q = P->lev[l - 1];
@@ -2463,7 +2473,8 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
     StageTimer t(P, ST_L2L, s);
     if ((st = do_l2l(P, tt, 2, s, 1))) return st;
   }
-  for (int l = 3; l <= L; ++l) {
+  const bool down = fused_down(P);
+  for (int l = 3; l <= (down ? L - 1 : L); ++l) {
     StageTimer t(P, ST_L2L, s);
     // with the final-stage M2P the leaf locals are the parent's shifted locals
     // alone (the adjoint's P2L wrote them first)
@@ -2482,11 +2493,18 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
   }
   {
     StageTimer t(P, ST_LEAF, s);
+    LeafDownArgs<T> da;
+    if (down) {  // do_l2l's arguments for the leaf level
+      da.par = P->lev[L - 1];
+      da.Lp = static_cast<const T*>(P->Lx(L - 1));
+      da.harm = harmonic_m2l_level(P, L) ? 1 : 0;
+      da.Lred = da.harm && P->lev[L].lred_off ? reinterpret_cast<const T*>(P->arena + P->lev[L].lred_off) : nullptr;
+    }
     CUDA_TRY(launch_leaf_finish<T>(tt, P->lev[L], static_cast<const T*>(P->Lx(L)), adj_g ? rho_box : near_box,
                                    P->b * P->b * P->b * (adj_g ? 1 : P->near_comps),
                                    (P->m2p && !p2l) ? reinterpret_cast<const T*>(P->arena + P->m2p_off) : nullptr,
                                    P->dims,
-                                   P->G * P->dx * P->dx, phi, s));
+                                   P->G * P->dx * P->dx, phi, s, down ? &da : nullptr));
   }
   if (accel) {
     StageTimer t(P, ST_FD, s);
@@ -2609,6 +2627,7 @@ int fmm_solve_launches(fmm_plan_t P, int with_accel) {
   const int L = P->L;
   int n = 1;                            // P2M (with the finite check)
   n += std::max(0, L - 2);              // M2M for l = L .. 3
+  if (fused_down(P)) n -= 1;            // the last L2L inside the leaf kernel
   if (L < 2) n += 1;                    // zero the leaf locals
   for (int l = 2; l <= L; ++l) {
     n += l >= 3 ? 2 : 1;                // M2L, and L2L below level 2
@@ -2688,6 +2707,25 @@ fmm_status fmm_debug_level(fmm_plan_t P, int what, int level, double* host_out, 
   CUDA_TRY(cudaMalloc(&tmp, count * sizeof(double)));
   const double h = (double)P->b * (double)(1LL << (P->L - level));
   const void* src = what == 0 ? P->M(level) : P->Lx(level);
+  void* full = nullptr;  // leaf locals with the fused last L2L: that L2L, into a copy of the M2L's locals
+  if (what == 1 && level == P->L && fused_down(P)) {
+    cudaError_t e = cudaMalloc(&full, lv.bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(full, P->Lx(level), lv.bytes, cudaMemcpyDeviceToDevice);
+    const Level& q = P->lev[level - 1];
+    const int harm = harmonic_m2l_level(P, level) ? 1 : 0;
+    const void* red = harm && lv.lred_off ? P->arena + lv.lred_off : nullptr;
+    if (e == cudaSuccess)
+      e = lv.f64 ? launch_l2l<double, double>(P->tables(), q, static_cast<const double*>(P->Lx(level - 1)), lv,
+                                              static_cast<double*>(full), 1, harm, static_cast<const double*>(red), 0)
+                 : launch_l2l<float, float>(P->tables(), q, static_cast<const float*>(P->Lx(level - 1)), lv,
+                                            static_cast<float*>(full), 1, harm, static_cast<const float*>(red), 0);
+    if (e != cudaSuccess) {
+      if (full) cudaFree(full);
+      cudaFree(tmp);
+      return fail(FMM_ERR_CUDA, "debug export failed: %s", cudaGetErrorString(e));
+    }
+    src = full;
+  }
   cudaError_t e = lv.f64 ? launch_export_level<double>(static_cast<const double*>(src), lv, what, h, P->d_mi, P->nc,
                                                        tmp, nullptr)
                          : launch_export_level<float>(static_cast<const float*>(src), lv, what, h, P->d_mi, P->nc, tmp,
@@ -2695,6 +2733,7 @@ fmm_status fmm_debug_level(fmm_plan_t P, int what, int level, double* host_out, 
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(host_out, tmp, count * sizeof(double), cudaMemcpyDeviceToHost);
   cudaFree(tmp);
+  if (full) cudaFree(full);
   if (e != cudaSuccess) return fail(FMM_ERR_CUDA, "debug export failed: %s", cudaGetErrorString(e));
   return FMM_OK;
 }

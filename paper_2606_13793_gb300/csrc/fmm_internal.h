@@ -135,11 +135,11 @@ struct TreeTables {
 // near field) when non-NULL.  Sets bit 0 of *flag for a non-finite density.
 // harm = 1: the planes hold the harmonic ((p+1)^2, c <= 1) components of the
 // folded multipoles (tree_common.cuh), rows of 8 (p+1)^2 values per parent.
-template <typename T>
 // Mfold (nullable, with harm): the folded components in the level's type,
 // rows of 8 (p+1)^2 values (the CUDA-core harmonic M2L reads them).
 // dip (nullable): dipole sources [3][cells], weights v_q adding v_q d/de_q (e^alpha)
 // (box units) per cell -- the transpose of the analytic force's L2P gradient.
+template <typename T>
 cudaError_t launch_p2m(const TreeTables& t, const T* rho, const int dims[3], const Level& leaf, T* Mleaf, T* rho_box,
                        void* Mhi, void* Mlo, void* rho_hi, void* rho_lo, int* flag, int harm, T* Mfold,
                        cudaStream_t s, const T* dip = nullptr);
@@ -264,11 +264,24 @@ template <typename T>
 cudaError_t launch_cells_to_boxes4(const T* w, const T* g, double sc, const int dims[3], const Level& leaf, int b,
                                    int parent_blocked, T* dst, cudaStream_t s);
 // near_box rows hold near_stride values per leaf box, the potential sums first.
-template <typename T>
 // m2p (nullable): final-stage M2P potentials, parent-blocked [parent][child][b^3], in the
 // leaf level's scaled units (multiplied by 1/b like the L2P term).
+// down (nullable): the last L2L (level L - 1 -> leaf, accumulate) done by the
+// leaf kernel in registers, with launch_l2l's arguments for that level pair
+// (type T on both); Lleaf then holds only the leaf level's M2L locals (full
+// rows, or the c <= 1 ones in Lleaf / in down->Lred with harm) and is not
+// written.
+template <typename T>
+struct LeafDownArgs {
+  Level par;
+  const T* Lp = nullptr;
+  int harm = 0;
+  const T* Lred = nullptr;
+};
+template <typename T>
 cudaError_t launch_leaf_finish(const TreeTables& t, const Level& leaf, const T* Lleaf, const T* near_box,
-                               int near_stride, const T* m2p, const int dims[3], double scale, T* phi, cudaStream_t s);
+                               int near_stride, const T* m2p, const int dims[3], double scale, T* phi, cudaStream_t s,
+                               const LeafDownArgs<T>* down = nullptr);
 // With the analytic acceleration: near_box rows are [potential, d/dx, d/dy,
 // d/dz] x b^3; accel = ascale (far gradient + near gradient).  m2p (nullable):
 // the final-stage M2P's [parent][child][potential, d/dx, d/dy, d/dz][b^3],

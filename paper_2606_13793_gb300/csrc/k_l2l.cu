@@ -24,54 +24,11 @@ __device__ __forceinline__ void l2l_body(const Level& par, const Tp* __restrict_
   const long long p = t >> 3;  // box of the parent level == parent block of the child level
   const int c = (int)(t & 7);
   if (p >= par.nbox) return;
-  const int px = (int)(p % par.n[0]);
-  const int py = (int)((p / par.n[0]) % par.n[1]);
-  const int pz = (int)(p / ((long long)par.n[0] * par.n[1]));
-  const long long gp = ((long long)(pz >> 1) * par.np[1] + (py >> 1)) * par.np[0] + (px >> 1);
-  const int cp = (px & 1) | ((py & 1) << 1) | ((pz & 1) << 2);
   Tp L[NC];
-  if (Lp) {
-    const Tp* src = Lp + gp * 8 * NC + cp;
-#pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      const int n = (k >= 1) + (k >= 4) + (k >= 10) + (k >= 20) + (k >= 35) + (k >= 56) + (k >= 84) + (k >= 120);
-      L[k] = src[k * 8] * Tp(1.0 / (double)(2 << n));  // 2^(-1-|gamma|)
-    }
-    Tp dp[P + 1];
-    powers<P, Tp>(half_offset<Tp>(c, 0), dp);
-    shift_down<P, 0, Tp>(L, dp);
-    powers<P, Tp>(half_offset<Tp>(c, 1), dp);
-    shift_down<P, 1, Tp>(L, dp);
-    powers<P, Tp>(half_offset<Tp>(c, 2), dp);
-    shift_down<P, 2, Tp>(L, dp);
-  } else {
-#pragma unroll
-    for (int k = 0; k < NC; ++k) L[k] = Tp(0);
-  }
   Tc* dst = Lc + p * 8 * NC + c;
-  if (accumulate && harm) {
-    // The M2L wrote only its c <= 1 locals (in the full rows, tensor cores, or
-    // in compact rows [parent][reduced coef][child], CUDA cores).  The
-    // parent's shifted locals are harmonic too (an exact re-expansion of a
-    // harmonic polynomial), so the sum is: add the c <= 1 values, then rebuild
-    // the c >= 2 components of the sum from the Laplace identity, in place.
-    constexpr int NR = nred_c(P);
-    const Tc* red = Lred ? Lred + p * 8 * NR + c : nullptr;
+  l2l_child<P, Tp, Tc>(L, par, Lp, p, c, accumulate, harm, dst, Lred);
 #pragma unroll
-    for (int n = 0; n <= P; ++n)
-#pragma unroll
-      for (int s = 0; s <= n; ++s)
-#pragma unroll
-        for (int cc = 0; cc <= 1 && cc <= s; ++cc)
-          L[cidx(n - s, s - cc, cc)] +=
-              Tp(red ? red[ridx(n - s, s - cc, cc) * 8] : dst[cidx(n - s, s - cc, cc) * 8]);
-    harmonic_expand<P, Tp>(L);
-#pragma unroll
-    for (int k = 0; k < NC; ++k) dst[k * 8] = Tc(L[k]);
-  } else {
-#pragma unroll
-    for (int k = 0; k < NC; ++k) dst[k * 8] = accumulate ? Tc(dst[k * 8] + Tc(L[k])) : Tc(L[k]);
-  }
+  for (int k = 0; k < NC; ++k) dst[k * 8] = Tc(L[k]);
 }
 
 template <int P, typename Tp, typename Tc>

@@ -21,15 +21,19 @@ template <int P, typename T>
 __device__ __forceinline__ void leaf_finish_body(const Level& leaf, const T* __restrict__ Lleaf,
                                                  const T* __restrict__ near_box, int near_stride,
                                                  const T* __restrict__ m2p, int nx, int ny, int b, T scale,
-                                                 T* __restrict__ phi, const VBlock& vb) {
+                                                 T* __restrict__ phi, const VBlock& vb, const LeafDownArgs<T>& down) {
   constexpr int NC = ncoef_c(P);
   const long long t = (long long)vb.x * kThreads + threadIdx.x;
   const Box B = box_of(leaf, t);
   if (!B.real) return;
   T L[NC];
   const T* src = Lleaf + B.par * 8 * NC + B.c;
+  if (down.Lp) {  // the last L2L, as its kernel computes it (the box's parent = B.par)
+    l2l_child<P, T, T>(L, down.par, down.Lp, B.par, B.c, 1, down.harm, src, down.Lred);
+  } else {
 #pragma unroll
-  for (int k = 0; k < NC; ++k) L[k] = src[k * 8];
+    for (int k = 0; k < NC; ++k) L[k] = src[k * 8];
+  }
   const T inv_b = T(1) / T(b);
   const long long box = ((long long)B.z * leaf.n[1] + B.y) * leaf.n[0] + B.x;
   const T* mp = m2p ? m2p + (B.par * 8 + B.c) * (long long)(b * b * b) : nullptr;
@@ -112,8 +116,9 @@ __device__ __forceinline__ void leaf_finish_body(const Level& leaf, const T* __r
 template <int P, typename T>
 __global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(T) == 4) ? 2 : 1)
     leaf_finish_kernel(Level leaf, const T* __restrict__ Lleaf, const T* __restrict__ near_box, int near_stride,
-                       const T* __restrict__ m2p, int nx, int ny, int b, T scale, T* __restrict__ phi) {
-  leaf_finish_body<P, T>(leaf, Lleaf, near_box, near_stride, m2p, nx, ny, b, scale, phi, native_vblock());
+                       const T* __restrict__ m2p, int nx, int ny, int b, T scale, T* __restrict__ phi,
+                       const LeafDownArgs<T> down) {
+  leaf_finish_body<P, T>(leaf, Lleaf, near_box, near_stride, m2p, nx, ny, b, scale, phi, native_vblock(), down);
 }
 
 // The leaf levels of many solves in one launch (batched solves).
@@ -126,7 +131,7 @@ __global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(T) == 4) ? 2 : 1)
   __syncthreads();
   leaf_finish_body<P, T>(x.leaf, static_cast<const T*>(x.Lleaf), static_cast<const T*>(x.near_box), x.near_stride,
                          static_cast<const T*>(x.m2p), x.nx, x.ny, x.b, (T)x.scale, static_cast<T*>(x.phi),
-                         multi_vblock(g[i]));
+                         multi_vblock(g[i]), LeafDownArgs<T>{});
 }
 
 // Leaf evaluation with the analytic acceleration: also the gradient of the
@@ -308,11 +313,14 @@ template cudaError_t launch_leaf_finish_grad<double>(const TreeTables&, const Le
 
 template <typename T>
 cudaError_t launch_leaf_finish(const TreeTables& t, const Level& leaf, const T* Lleaf, const T* near_box,
-                               int near_stride, const T* m2p, const int dims[3], double scale, T* phi, cudaStream_t s) {
+                               int near_stride, const T* m2p, const int dims[3], double scale, T* phi, cudaStream_t s,
+                               const LeafDownArgs<T>* down) {
   const long long threads = leaf.npar * 8;
   if (threads == 0) return cudaSuccess;
+  const LeafDownArgs<T> none{};
   FMM_ORDER_SWITCH(t.p, (leaf_finish_kernel<PP, T><<<grid_threads(threads), kThreads, 0, s>>>(
-                            leaf, Lleaf, near_box, near_stride, m2p, dims[0], dims[1], t.b, (T)scale, phi)));
+                            leaf, Lleaf, near_box, near_stride, m2p, dims[0], dims[1], t.b, (T)scale, phi,
+                            down ? *down : none)));
   return cudaGetLastError();
 }
 
@@ -329,9 +337,11 @@ template cudaError_t launch_leaf_finish_multi<double>(int, const LeafArgs*, cons
                                                       cudaStream_t);
 
 template cudaError_t launch_leaf_finish<float>(const TreeTables&, const Level&, const float*, const float*, int,
-                                               const float*, const int*, double, float*, cudaStream_t);
+                                               const float*, const int*, double, float*, cudaStream_t,
+                                               const LeafDownArgs<float>*);
 template cudaError_t launch_leaf_finish<double>(const TreeTables&, const Level&, const double*, const double*, int,
-                                                const double*, const int*, double, double*, cudaStream_t);
+                                                const double*, const int*, double, double*, cudaStream_t,
+                                                const LeafDownArgs<double>*);
 
 // Cells of every leaf box in parent-blocked order, [parent][child][b^3]
 // (phantom boxes zero): the rows of the final-stage M2P's transpose.

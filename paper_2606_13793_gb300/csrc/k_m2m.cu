@@ -28,67 +28,7 @@ __device__ __forceinline__ void m2m_body(const Level& child, const Tc* __restric
   const Tc* src = Mc + (live ? p : 0) * 8 * NC + c;
 #pragma unroll
   for (int k = 0; k < NC; ++k) M[k] = live ? Tp(src[k * 8]) : Tp(0);
-  Tp dp[P + 1];
-  powers<P, Tp>(half_offset<Tp>(c, 0), dp);
-  shift_up<P, 0, Tp>(M, dp);
-  powers<P, Tp>(half_offset<Tp>(c, 1), dp);
-  shift_up<P, 1, Tp>(M, dp);
-  powers<P, Tp>(half_offset<Tp>(c, 2), dp);
-  shift_up<P, 2, Tp>(M, dp);
-#pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    Tp v = M[k];
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    M[k] = v;
-  }
-  if (!live) return;
-  // box p of the parent level, inside its own parent block
-  const int px = (int)(p % par.n[0]);
-  const int py = (int)((p / par.n[0]) % par.n[1]);
-  const int pz = (int)(p / ((long long)par.n[0] * par.n[1]));
-  const long long gp = ((long long)(pz >> 1) * par.np[1] + (py >> 1)) * par.np[0] + (px >> 1);
-  const int cp = (px & 1) | ((py & 1) << 1) | ((pz & 1) << 2);
-  Tp* dst = Mp + gp * 8 * NC + cp;
-  const bool fold = harm && (Mhi || Mfold);
-  if (!fold) {
-    // sibling lanes share the writes: lane c stores coefficients c, c+8, ...
-#pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      if ((k & 7) != c) continue;
-      const int n = (k >= 1) + (k >= 4) + (k >= 10) + (k >= 20) + (k >= 35) + (k >= 56) + (k >= 84) + (k >= 120);
-      const Tp v = M[k] * Tp(1.0 / (double)(1 << n));  // 2^-|alpha|
-      dst[k * 8] = v;
-      if (Mhi) store_split(Mhi, Mlo, (size_t)(gp * 8 * NC + cp + k * 8), v);
-    }
-    return;
-  }
-  // harmonic rows: every lane scales and folds the whole expansion, then
-  // stores its share of the full row and of the (p+1)^2 folded components
-  // ([parent][reduced coef][child]) as bf16 planes and / or in the level's type
-#pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    const int n = (k >= 1) + (k >= 4) + (k >= 10) + (k >= 20) + (k >= 35) + (k >= 56) + (k >= 84) + (k >= 120);
-    M[k] *= Tp(1.0 / (double)(1 << n));  // 2^-|alpha|
-    if ((k & 7) == c) dst[k * 8] = M[k];
-  }
-  constexpr int NR = nred_c(P);
-  harmonic_fold<P, Tp>(M);
-  int r = 0;
-#pragma unroll
-  for (int n = 0; n <= P; ++n)
-#pragma unroll
-    for (int s = 0; s <= n; ++s)
-#pragma unroll
-      for (int cc = 0; cc <= 1 && cc <= s; ++cc) {
-        if ((r & 7) == c) {
-          const size_t o = (size_t)(gp * 8 * NR + cp + r * 8);
-          if (Mhi) store_split(Mhi, Mlo, o, M[cidx(n - s, s - cc, cc)]);
-          if (Mfold) Mfold[o] = M[cidx(n - s, s - cc, cc)];
-        }
-        ++r;
-      }
+  m2m_to_parent<P, Tp>(M, p, c, live, par, Mp, Mhi, Mlo, harm, Mfold);
 }
 
 template <int P, typename Tc, typename Tp>

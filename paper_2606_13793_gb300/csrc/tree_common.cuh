@@ -185,5 +185,136 @@ inline int small_grid_block(long long threads) { return threads < 152LL * kThrea
     default: return cudaErrorInvalidValue;                \
   }
 
+// M2M (Sec. 2.1, eq. M2M_general) of one child's scaled multipoles M (in
+// registers, overwritten) onto its parent p, a box of level `par`; lane c =
+// the child (lanes 8j .. 8j + 7 of a warp are one parent's 8 children, all 32
+// lanes take part in the shuffles), `live` false for padding lanes.  Writes
+// the parent's scaled multipoles 2^-|alpha| sum_children ... into Mp (its own
+// parent-blocked slot) and, when given, the bf16 hi / lo planes and the
+// folded harmonic rows.
+template <int P, typename Tp>
+__device__ __forceinline__ void m2m_to_parent(Tp (&M)[ncoef_c(P)], long long p, int c, bool live, const Level& par,
+                                              Tp* __restrict__ Mp, __nv_bfloat16* __restrict__ Mhi,
+                                              __nv_bfloat16* __restrict__ Mlo, int harm, Tp* __restrict__ Mfold) {
+  constexpr int NC = ncoef_c(P);
+  Tp dp[P + 1];
+  powers<P, Tp>(half_offset<Tp>(c, 0), dp);
+  shift_up<P, 0, Tp>(M, dp);
+  powers<P, Tp>(half_offset<Tp>(c, 1), dp);
+  shift_up<P, 1, Tp>(M, dp);
+  powers<P, Tp>(half_offset<Tp>(c, 2), dp);
+  shift_up<P, 2, Tp>(M, dp);
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    Tp v = M[k];
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    M[k] = v;
+  }
+  if (!live) return;
+  // box p of the parent level, inside its own parent block
+  const int px = (int)(p % par.n[0]);
+  const int py = (int)((p / par.n[0]) % par.n[1]);
+  const int pz = (int)(p / ((long long)par.n[0] * par.n[1]));
+  const long long gp = ((long long)(pz >> 1) * par.np[1] + (py >> 1)) * par.np[0] + (px >> 1);
+  const int cp = (px & 1) | ((py & 1) << 1) | ((pz & 1) << 2);
+  Tp* dst = Mp + gp * 8 * NC + cp;
+  const bool fold = harm && (Mhi || Mfold);
+  if (!fold) {
+    // sibling lanes share the writes: lane c stores coefficients c, c+8, ...
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      if ((k & 7) != c) continue;
+      const int n = (k >= 1) + (k >= 4) + (k >= 10) + (k >= 20) + (k >= 35) + (k >= 56) + (k >= 84) + (k >= 120);
+      const Tp v = M[k] * Tp(1.0 / (double)(1 << n));  // 2^-|alpha|
+      dst[k * 8] = v;
+      if (Mhi) store_split(Mhi, Mlo, (size_t)(gp * 8 * NC + cp + k * 8), v);
+    }
+    return;
+  }
+  // harmonic rows: every lane scales and folds the whole expansion, then
+  // stores its share of the full row and of the (p+1)^2 folded components
+  // ([parent][reduced coef][child]) as bf16 planes and / or in the level's type
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const int n = (k >= 1) + (k >= 4) + (k >= 10) + (k >= 20) + (k >= 35) + (k >= 56) + (k >= 84) + (k >= 120);
+    M[k] *= Tp(1.0 / (double)(1 << n));  // 2^-|alpha|
+    if ((k & 7) == c) dst[k * 8] = M[k];
+  }
+  constexpr int NR = nred_c(P);
+  harmonic_fold<P, Tp>(M);
+  int r = 0;
+#pragma unroll
+  for (int n = 0; n <= P; ++n)
+#pragma unroll
+    for (int s = 0; s <= n; ++s)
+#pragma unroll
+      for (int cc = 0; cc <= 1 && cc <= s; ++cc) {
+        if ((r & 7) == c) {
+          const size_t o = (size_t)(gp * 8 * NR + cp + r * 8);
+          if (Mhi) store_split(Mhi, Mlo, o, M[cidx(n - s, s - cc, cc)]);
+          if (Mfold) Mfold[o] = M[cidx(n - s, s - cc, cc)];
+        }
+        ++r;
+      }
+}
+
+// L2L (Sec. 2.3, eq. L2L) of the parent's scaled locals onto child c, plus
+// the child's own M2L locals, in registers: the arithmetic of one L2L thread
+// (k_l2l.cu).  p: the parent, a box of level `par`; Lp (NULL: no parent
+// locals) the parent level's locals; own = the child's row in the child
+// level's locals (stride 8: [coef][child]), read where the M2L wrote it
+// (accumulate = 1); harm = 1: the M2L wrote only its c <= 1 locals, in own
+// or, with Lred, in compact rows; the c >= 2 components are rebuilt.
+template <int P, typename Tp, typename Tc>
+__device__ __forceinline__ void l2l_child(Tp (&L)[ncoef_c(P)], const Level& par, const Tp* __restrict__ Lp,
+                                          long long p, int c, int accumulate, int harm, const Tc* own,
+                                          const Tc* __restrict__ Lred) {
+  constexpr int NC = ncoef_c(P);
+  if (Lp) {
+    const int px = (int)(p % par.n[0]);
+    const int py = (int)((p / par.n[0]) % par.n[1]);
+    const int pz = (int)(p / ((long long)par.n[0] * par.n[1]));
+    const long long gp = ((long long)(pz >> 1) * par.np[1] + (py >> 1)) * par.np[0] + (px >> 1);
+    const int cp = (px & 1) | ((py & 1) << 1) | ((pz & 1) << 2);
+    const Tp* src = Lp + gp * 8 * NC + cp;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const int n = (k >= 1) + (k >= 4) + (k >= 10) + (k >= 20) + (k >= 35) + (k >= 56) + (k >= 84) + (k >= 120);
+      L[k] = src[k * 8] * Tp(1.0 / (double)(2 << n));  // 2^(-1-|gamma|)
+    }
+    Tp dp[P + 1];
+    powers<P, Tp>(half_offset<Tp>(c, 0), dp);
+    shift_down<P, 0, Tp>(L, dp);
+    powers<P, Tp>(half_offset<Tp>(c, 1), dp);
+    shift_down<P, 1, Tp>(L, dp);
+    powers<P, Tp>(half_offset<Tp>(c, 2), dp);
+    shift_down<P, 2, Tp>(L, dp);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) L[k] = Tp(0);
+  }
+  if (accumulate && harm) {
+    // The parent's shifted locals are harmonic too (an exact re-expansion of
+    // a harmonic polynomial), so the sum is: add the c <= 1 values, then
+    // rebuild the c >= 2 components of the sum from the Laplace identity.
+    constexpr int NR = nred_c(P);
+    const Tc* red = Lred ? Lred + p * 8 * NR + c : nullptr;
+#pragma unroll
+    for (int n = 0; n <= P; ++n)
+#pragma unroll
+      for (int s = 0; s <= n; ++s)
+#pragma unroll
+        for (int cc = 0; cc <= 1 && cc <= s; ++cc)
+          L[cidx(n - s, s - cc, cc)] +=
+              Tp(red ? red[ridx(n - s, s - cc, cc) * 8] : own[cidx(n - s, s - cc, cc) * 8]);
+    harmonic_expand<P, Tp>(L);
+  } else if (accumulate) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) L[k] = Tp(Tc(own[k * 8]) + Tc(L[k]));
+  }
+}
+
 }  // namespace tree
 }  // namespace fmmgb
