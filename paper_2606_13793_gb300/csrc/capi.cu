@@ -3015,11 +3015,11 @@ void build_fused(fmm_batch_t B, const void* const* rho, void* const* phi, void* 
     }
     for (int sh = 0; sh < 4; ++sh) add_step(B, MK_GEMM, sh, 0, 0, a[sh], g[sh]);
   }
-  for (int l = 2; l <= maxL; ++l) {  // L2L, coarse to fine
+  for (int l = 2; l <= maxL; ++l) {  // L2L, coarse to fine (a fused leaf level's in the leaf kernel)
     std::vector<L2lArgs> a;
     std::vector<std::array<unsigned, 3>> g;
     for (fmm_plan_t P : B->plans) {
-      if (l > P->L) continue;
+      if (l > P->L || (l == P->L && fused_down(P))) continue;
       const bool harm = harmonic_m2l_level(P, l);
       if (l == 2 && !harm) continue;  // level-2 locals are its M2L alone
       const Level &q = P->lev[l - 1], &c = P->lev[l];
@@ -3051,6 +3051,13 @@ void build_fused(fmm_batch_t B, const void* const* rho, void* const* phi, void* 
       x.b = P->b;
       x.scale = P->G * P->dx * P->dx;
       x.phi = phi ? phi[i] : nullptr;
+      if (fused_down(P)) {  // run_solve's arguments for the leaf level's L2L
+        const int L = P->L;
+        x.par = P->lev[L - 1];
+        x.Lp = P->Lx(L - 1);
+        x.harm = harmonic_m2l_level(P, L) ? 1 : 0;
+        x.Lred = x.harm && P->lev[L].lred_off ? P->arena + P->lev[L].lred_off : nullptr;
+      }
       a.push_back(x);
       g.push_back(blocks_1d(x.leaf.npar * 8, 256));
     }

@@ -208,6 +208,11 @@ struct LeafArgs {
   int nx, ny, b;
   double scale;
   void* phi;
+  // the last L2L in the leaf kernel (launch_leaf_finish's `down`; Lp NULL: none)
+  Level par;
+  const void* Lp;
+  int harm;
+  const void* Lred;
 };
 template <typename T>
 cudaError_t launch_leaf_finish_multi(int p, const LeafArgs* args, const MultiGrid* grids, int n, long long blocks,

@@ -129,9 +129,14 @@ __global__ void __launch_bounds__(kThreads, (P <= 6 && sizeof(T) == 4) ? 2 : 1)
   const int i = multi_item(g, n);
   if (threadIdx.x == 0 && threadIdx.y == 0) x = a[i];
   __syncthreads();
+  LeafDownArgs<T> down;
+  down.par = x.par;
+  down.Lp = static_cast<const T*>(x.Lp);
+  down.harm = x.harm;
+  down.Lred = static_cast<const T*>(x.Lred);
   leaf_finish_body<P, T>(x.leaf, static_cast<const T*>(x.Lleaf), static_cast<const T*>(x.near_box), x.near_stride,
                          static_cast<const T*>(x.m2p), x.nx, x.ny, x.b, (T)x.scale, static_cast<T*>(x.phi),
-                         multi_vblock(g[i]), LeafDownArgs<T>{});
+                         multi_vblock(g[i]), down);
 }
 
 // Leaf evaluation with the analytic acceleration: also the gradient of the
