@@ -76,6 +76,30 @@ def test_tc_ragged_grid(orc, prec):
     assert rel_l2(phi, ref["phi"]) <= TOL[prec]
 
 
+@pytest.mark.parametrize("shape", [(84, 52, 28), (8, 8, 200), (200, 4, 4)])
+def test_tc_dedicated_near_field_partial_items(orc, shape):
+    """The leaf-4 near-field kernel on grids whose row tiles (8 x 16 x 1 leaf
+    boxes) are partial in x and y and whose tile count is not a multiple of
+    the four tiles of a work item (84 x 52 x 28 cells: 21 x 13 x 7 leaf boxes,
+    21 tiles, the last item one tile), with fewer items than SMs, and on
+    flat grids: against the oracle and against the span schedule."""
+    nx, ny, nz = shape
+    rho = inputs.plummer((nx, ny, nz), seed=19).astype(np.float64)  # [z][y][x]
+    ref = orc.fmm(rho, 4, 6)["phi"]
+    out = {}
+    for sched in ("dedicated", "span"):
+        plan = fmm.FMMPlan((nx, ny, nz), 6, 4, "bf16x3")
+        assert plan.tc_schedule("near")[0] == "dedicated"
+        plan.set_tc_schedule("near", sched)
+        phi = plan.solve(torch.from_numpy(rho.astype(np.float32)).cuda())
+        torch.cuda.synchronize()
+        plan.check()
+        out[sched] = phi.double().cpu().numpy()
+        plan.close()
+        assert rel_l2(out[sched], ref) <= TOL["bf16x3"], sched
+    assert rel_l2(out["dedicated"], out["span"]) <= 2e-6
+
+
 def test_tc_all_levels_on_tensor_cores(orc):
     """n_fp64_levels = 0: every M2L level (down to the 2x2x2 parent grid) on
     tcgen05.  The coarse levels carry the same-signed monopole bulk of phi,
