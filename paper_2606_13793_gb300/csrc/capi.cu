@@ -2852,8 +2852,8 @@ struct fmm_batch_s {
   size_t d_tab_cap = 0;
   // the contraction launches of the fused form run side by side: streams
   // and fork / join events
-  cudaStream_t fk[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t fev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t fk[4] = {nullptr, nullptr, nullptr, nullptr};  // one per contraction shape after the first
+  cudaEvent_t fev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -2921,11 +2921,11 @@ void add_step(fmm_batch_t B, int kind, int shape, int bs, int harm_rows, const s
 
 // Tile shape of a contraction inside the fused batch, where the other
 // fields fill the GPU: the z-run tiles of the longer run (the fastest per
-// row); a grid of at most 4 x 4 x 4 rows
-// takes the 4 x 4 x 4 tile (a z-run tile of 8 x 4 x RZ rows would be mostly
-// padding; the column-per-lane form is far slower per row in FP32).
+// row); a grid of at most 64 rows takes the tiny-grid form (shape 4: real
+// rows and in-grid neighbours only; the 4 x 4 x 4 tile took 3 ms of the
+// 64-field step on them, the column-per-lane form longer).
 int batch_shape(const NbrGemm& g, const std::vector<int>& tile_k) {
-  if (g.grid[0] <= 4 && g.grid[1] <= 4 && g.grid[2] <= 4) return 0;
+  if (nbr_gemm_tiny_fits(g)) return 4;
   if (!zrun_eligible(g, tile_k.data(), g.ntiles)) return g.shape;
   // RZ = 8 throughout: on the 12^3-row grids, where it pads a third more
   // rows than RZ = 4, the batch step measured the same either way, and one
@@ -2995,15 +2995,17 @@ void build_fused(fmm_batch_t B, const void* const* rho, void* const* phi, void* 
     add_step(B, MK_M2M, 0, bs, 0, a, g);
   }
   {  // M2L of every level and the near field: independent contractions
-    std::vector<NbrGemm> a[4];
-    std::vector<std::array<unsigned, 3>> g[4];
+    std::vector<NbrGemm> a[5];
+    std::vector<std::array<unsigned, 3>> g[5];
     auto add = [&](NbrGemm x, const std::vector<int>& tile_k) {
       x.dsplit = 1;  // the batch fills the GPU: no neighbour split, no partial sums
       x.partial = nullptr;
       x.max_blocks = 0;
       x.shape = batch_shape(x, tile_k);
       std::array<unsigned, 3> gr;
-      if (x.shape == 1 || x.shape == 2)
+      if (x.shape == 4)
+        gr = {(unsigned)x.ntiles, 1u, 1u};
+      else if (x.shape == 1 || x.shape == 2)
         nbr_gemm_zrun_grid<T>(x, x.shape - 1, gr.data());
       else
         nbr_gemm_simt_col_grid<T>(x, gr.data());
@@ -3014,7 +3016,7 @@ void build_fused(fmm_batch_t B, const void* const* rho, void* const* phi, void* 
       for (int l = 2; l <= P->L; ++l) add(m2l_gemm(P, l), P->h_m2l_tile_k);
       add(near_gemm(P), P->h_near_tile_k);
     }
-    for (int sh = 0; sh < 4; ++sh) add_step(B, MK_GEMM, sh, 0, 0, a[sh], g[sh]);
+    for (int sh : {4, 0, 1, 2, 3}) add_step(B, MK_GEMM, sh, 0, 0, a[sh], g[sh]);  // the latency-bound first
   }
   for (int l = 2; l <= maxL; ++l) {  // L2L, coarse to fine (a fused leaf level's in the leaf kernel)
     std::vector<L2lArgs> a;
@@ -3087,10 +3089,9 @@ void build_fused(fmm_batch_t B, const void* const* rho, void* const* phi, void* 
 
 // The steps in order, except that the contraction launches (independent of
 // one another) run side by side: the first on `s`, the others on the fork
-// streams, joined before the next step.  The first is the 4 x 4 x 4 tile
-// launch of the few-row grids: its blocks are long (a row's whole reduction
-// in one block) and few, so they start first and the z-run launches fill the
-// GPU around them instead of waiting for their tail.
+// streams, joined before the next step.  The first is the tiny-grid launch
+// (few long blocks, latency-bound), so its blocks start first and the z-run
+// launches fill the GPU around them instead of waiting for their tail.
 template <typename T>
 fmm_status run_fused(fmm_batch_t B, cudaStream_t s) {
   const int p = B->plans[0]->p;
@@ -3103,7 +3104,7 @@ fmm_status run_fused(fmm_batch_t B, cudaStream_t s) {
     cudaStream_t ls = s;
     if (st.kind == MK_GEMM && ngemm > 1) {
       if (nfork == 0) CUDA_TRY(cudaEventRecord(B->fev[0], s));
-      if (nfork > 0) {  // the fork streams (at most three more contraction shapes)
+      if (nfork > 0) {  // the fork streams (at most four more contraction shapes)
         ls = B->fk[nfork - 1];
         CUDA_TRY(cudaStreamWaitEvent(ls, B->fev[0], 0));
       }
@@ -3126,7 +3127,9 @@ fmm_status run_fused(fmm_batch_t B, cudaStream_t s) {
         break;
       case MK_GEMM: {
         const NbrGemm* gs = static_cast<const NbrGemm*>(a);
-        if (st.shape == 0)
+        if (st.shape == 4)
+          e = launch_nbr_gemm_tiny_multi<T>(gs, g, st.n, st.blocks, ls);
+        else if (st.shape == 0)
           e = launch_nbr_gemm_simt_multi<T>(gs, g, st.n, st.blocks, ls);
         else if (st.shape == 3)
           e = launch_nbr_gemm_col_multi<T>(gs, g, st.n, st.blocks, ls);

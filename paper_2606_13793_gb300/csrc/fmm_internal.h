@@ -114,6 +114,12 @@ cudaError_t launch_nbr_gemm_zrun_multi(int shape, const NbrGemm* gs, const Multi
                                        cudaStream_t s);
 template <typename T>
 void nbr_gemm_simt_col_grid(const NbrGemm& g, unsigned out[3]);
+// Grids of at most 64 rows (nbr_gemm_tiny_fits): one block per column tile
+// (an item's grid is ntiles x 1 x 1), in-grid neighbours only.
+bool nbr_gemm_tiny_fits(const NbrGemm& g);
+template <typename T>
+cudaError_t launch_nbr_gemm_tiny_multi(const NbrGemm* gs, const MultiGrid* grids, int n, long long blocks,
+                                       cudaStream_t s);
 template <typename T>
 void nbr_gemm_zrun_grid(const NbrGemm& g, int shape, unsigned out[3]);
 // C (+)= sum over nparts partial arrays of count values, in part order.

@@ -219,6 +219,90 @@ __global__ void __launch_bounds__(128) nbr_gemm_col_multi_kernel(const NbrGemm* 
   nbr_gemm_col_body<T>(g, multi_vblock(grids[i]));
 }
 
+// Grids of at most 64 rows (4 x 4 x 4, the coarse levels of small fields):
+// one block per column tile, a thread taking two rows and four columns and
+// summing over the in-grid neighbours only.  The level's useful
+// multiply-adds are few; the general tiles would spend most of theirs on
+// padded rows and out-of-grid neighbours, and their staged reduction chunks
+// (two barriers each) would set a long latency for little work.  No shared
+// memory: the rows and weights of such a level stay in L1 / L2.
+constexpr int kTinyRows = 64;
+constexpr int kTinyThreads = 256;  // 32 row pairs x 8 column groups of 4
+
+template <typename T>
+__device__ __forceinline__ void nbr_gemm_tiny_body(const NbrGemm& g, const VBlock vb) {
+  const int tile = vb.x;
+  const int cq = threadIdx.x & 7, r0 = threadIdx.x >> 3;
+  const int R = g.grid[0] * g.grid[1] * g.grid[2];
+  const int K = g.tile_k[tile];
+  const T* W0 = static_cast<const T*>(g.W) + g.tile_w[tile] + cq * 4;
+  const T* A = static_cast<const T*>(g.A);
+  T acc[2][4];
+  int rx[2], ry[2], rz[2];
+  bool live[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int r = r0 + 32 * i;
+    live[i] = r < R;
+    const int rr = live[i] ? r : 0;
+    rx[i] = rr % g.grid[0];
+    ry[i] = (rr / g.grid[0]) % g.grid[1];
+    rz[i] = rr / (g.grid[0] * g.grid[1]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[i][c] = T(0);
+  }
+  for (int d = 0; d < 27; ++d) {
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    bool v[2];
+    const T* ap[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int x = rx[i] + dx, y = ry[i] + dy, z = rz[i] + dz;
+      v[i] = live[i] && x >= 0 && y >= 0 && z >= 0 && x < g.grid[0] && y < g.grid[1] && z < g.grid[2];
+      ap[i] = A + (v[i] ? ((long long)(z * g.grid[1] + y) * g.grid[0] + x) * g.row_len : 0);
+    }
+    if (!v[0] && !v[1]) continue;
+    const T* w = W0 + (long long)d * K * kNTile;
+    for (int k = 0; k < K; ++k) {
+      const T* wk = w + (long long)k * kNTile;
+      const T w0 = __ldg(wk), w1 = __ldg(wk + 1), w2 = __ldg(wk + 2), w3 = __ldg(wk + 3);
+      const T a0 = v[0] ? __ldg(ap[0] + k) : T(0), a1 = v[1] ? __ldg(ap[1] + k) : T(0);
+      acc[0][0] = fma(a0, w0, acc[0][0]);
+      acc[0][1] = fma(a0, w1, acc[0][1]);
+      acc[0][2] = fma(a0, w2, acc[0][2]);
+      acc[0][3] = fma(a0, w3, acc[0][3]);
+      acc[1][0] = fma(a1, w0, acc[1][0]);
+      acc[1][1] = fma(a1, w1, acc[1][1]);
+      acc[1][2] = fma(a1, w2, acc[1][2]);
+      acc[1][3] = fma(a1, w3, acc[1][3]);
+    }
+  }
+  T* C = static_cast<T*>(g.C);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    if (!live[i]) continue;
+    const long long row = r0 + 32 * i;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int col = tile * kNTile + cq * 4 + c;
+      if (col >= g.n_cols) continue;
+      T* dst = C + row * g.n_cols + col;
+      *dst = g.accumulate ? (*dst + acc[i][c]) : acc[i][c];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTinyThreads) nbr_gemm_tiny_multi_kernel(const NbrGemm* __restrict__ gs,
+                                                                           const MultiGrid* __restrict__ grids,
+                                                                           int n) {
+  __shared__ NbrGemm g;  // the item's description, read by the body from shared memory
+  const int i = multi_item(grids, n);
+  if (threadIdx.x == 0) g = gs[i];
+  __syncthreads();
+  nbr_gemm_tiny_body<T>(g, multi_vblock(grids[i]));
+}
+
 // C (+)= sum over the neighbour-group partials, in group order.
 template <typename T>
 __global__ void reduce_partials_kernel(const T* __restrict__ part, int nparts, long long count, T* __restrict__ C,
@@ -295,6 +379,17 @@ cudaError_t launch_nbr_gemm_col_multi(const NbrGemm* gs, const MultiGrid* grids,
 }
 
 template <typename T>
+cudaError_t launch_nbr_gemm_tiny_multi(const NbrGemm* gs, const MultiGrid* grids, int n, long long blocks,
+                                       cudaStream_t s) {
+  if (n <= 0 || blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  nbr_gemm_tiny_multi_kernel<T><<<(unsigned)blocks, kTinyThreads, 0, s>>>(gs, grids, n);
+  return cudaGetLastError();
+}
+
+bool nbr_gemm_tiny_fits(const NbrGemm& g) { return (long long)g.grid[0] * g.grid[1] * g.grid[2] <= kTinyRows; }
+
+template <typename T>
 void nbr_gemm_simt_col_grid(const NbrGemm& g, unsigned out[3]) {
   const unsigned nd = g.dsplit > 1 ? 27u : 1u;
   if (g.shape == 3) {
@@ -313,6 +408,8 @@ template cudaError_t launch_nbr_gemm_simt_multi<float>(const NbrGemm*, const Mul
 template cudaError_t launch_nbr_gemm_simt_multi<double>(const NbrGemm*, const MultiGrid*, int, long long, cudaStream_t);
 template cudaError_t launch_nbr_gemm_col_multi<float>(const NbrGemm*, const MultiGrid*, int, long long, cudaStream_t);
 template cudaError_t launch_nbr_gemm_col_multi<double>(const NbrGemm*, const MultiGrid*, int, long long, cudaStream_t);
+template cudaError_t launch_nbr_gemm_tiny_multi<float>(const NbrGemm*, const MultiGrid*, int, long long, cudaStream_t);
+template cudaError_t launch_nbr_gemm_tiny_multi<double>(const NbrGemm*, const MultiGrid*, int, long long, cudaStream_t);
 template void nbr_gemm_simt_col_grid<float>(const NbrGemm&, unsigned[3]);
 template void nbr_gemm_simt_col_grid<double>(const NbrGemm&, unsigned[3]);
 template cudaError_t launch_nbr_gemm_simt<float>(const NbrGemm&, cudaStream_t);
