@@ -3016,7 +3016,7 @@ void build_fused(fmm_batch_t B, const void* const* rho, void* const* phi, void* 
       for (int l = 2; l <= P->L; ++l) add(m2l_gemm(P, l), P->h_m2l_tile_k);
       add(near_gemm(P), P->h_near_tile_k);
     }
-    for (int sh : {4, 0, 1, 2, 3}) add_step(B, MK_GEMM, sh, 0, 0, a[sh], g[sh]);  // the latency-bound first
+    for (int sh : {1, 0, 2, 3, 4}) add_step(B, MK_GEMM, sh, 0, 0, a[sh], g[sh]);  // the tiny-grid launch last
   }
   for (int l = 2; l <= maxL; ++l) {  // L2L, coarse to fine (a fused leaf level's in the leaf kernel)
     std::vector<L2lArgs> a;
@@ -3089,9 +3089,10 @@ void build_fused(fmm_batch_t B, const void* const* rho, void* const* phi, void* 
 
 // The steps in order, except that the contraction launches (independent of
 // one another) run side by side: the first on `s`, the others on the fork
-// streams, joined before the next step.  The first is the tiny-grid launch
-// (few long blocks, latency-bound), so its blocks start first and the z-run
-// launches fill the GPU around them instead of waiting for their tail.
+// streams, joined before the next step.  The z-run launch goes first and
+// the tiny-grid launch (few latency-bound blocks) last: its blocks then take
+// the SMs the z-run blocks free (27.9 -> 27.7 ms for the 64-field batch,
+// against starting them first).
 template <typename T>
 fmm_status run_fused(fmm_batch_t B, cudaStream_t s) {
   const int p = B->plans[0]->p;
