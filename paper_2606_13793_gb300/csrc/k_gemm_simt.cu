@@ -226,15 +226,23 @@ __global__ void __launch_bounds__(128) nbr_gemm_col_multi_kernel(const NbrGemm* 
 // padded rows and out-of-grid neighbours, and their staged reduction chunks
 // (two barriers each) would set a long latency for little work.  No shared
 // memory: the rows and weights of such a level stay in L1 / L2.
+// The reduction is split into kTinyKS parts over as many groups of 256
+// threads, added in part order at the end: the blocks are latency-bound, and
+// this divides their length.
 constexpr int kTinyRows = 64;
-constexpr int kTinyThreads = 256;  // 32 row pairs x 8 column groups of 4
+constexpr int kTinyKS = 4;
+constexpr int kTinyThreads = 256 * kTinyKS;  // per part: 32 row pairs x 8 column groups of 4
 
 template <typename T>
 __device__ __forceinline__ void nbr_gemm_tiny_body(const NbrGemm& g, const VBlock vb) {
+  __shared__ T part[(kTinyKS > 1 ? kTinyKS - 1 : 1) * 256 * 8];
   const int tile = vb.x;
-  const int cq = threadIdx.x & 7, r0 = threadIdx.x >> 3;
+  const int kp = threadIdx.x >> 8, tl = threadIdx.x & 255;  // reduction part, thread in the part
+  const int cq = tl & 7, r0 = tl >> 3;
   const int R = g.grid[0] * g.grid[1] * g.grid[2];
-  const int K = g.tile_k[tile];
+  const int Kt = g.tile_k[tile];
+  const int Kq = (Kt + kTinyKS - 1) / kTinyKS;
+  const int k0 = kp * Kq, k1 = min(Kt, k0 + Kq);
   const T* W0 = static_cast<const T*>(g.W) + g.tile_w[tile] + cq * 4;
   const T* A = static_cast<const T*>(g.A);
   T acc[2][4];
@@ -262,8 +270,8 @@ __device__ __forceinline__ void nbr_gemm_tiny_body(const NbrGemm& g, const VBloc
       ap[i] = A + (v[i] ? ((long long)(z * g.grid[1] + y) * g.grid[0] + x) * g.row_len : 0);
     }
     if (!v[0] && !v[1]) continue;
-    const T* w = W0 + (long long)d * K * kNTile;
-    for (int k = 0; k < K; ++k) {
+    const T* w = W0 + (long long)d * Kt * kNTile;
+    for (int k = k0; k < k1; ++k) {
       const T* wk = w + (long long)k * kNTile;
       const T w0 = __ldg(wk), w1 = __ldg(wk + 1), w2 = __ldg(wk + 2), w3 = __ldg(wk + 3);
       const T a0 = v[0] ? __ldg(ap[0] + k) : T(0), a1 = v[1] ? __ldg(ap[1] + k) : T(0);
@@ -276,6 +284,21 @@ __device__ __forceinline__ void nbr_gemm_tiny_body(const NbrGemm& g, const VBloc
       acc[1][2] = fma(a1, w2, acc[1][2]);
       acc[1][3] = fma(a1, w3, acc[1][3]);
     }
+  }
+  if (kTinyKS > 1) {  // parts 1 .. KS-1 hand their sums to part 0, which adds them in order
+    if (kp > 0) {
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) part[((kp - 1) * 256 + tl) * 8 + i * 4 + c] = acc[i][c];
+    }
+    __syncthreads();
+    if (kp > 0) return;
+    for (int q = 1; q < kTinyKS; ++q)
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[i][c] += part[((q - 1) * 256 + tl) * 8 + i * 4 + c];
   }
   T* C = static_cast<T*>(g.C);
 #pragma unroll
