@@ -2235,6 +2235,7 @@ NbrGemm m2l_gemm(fmm_plan_t P, int l) {
   g.shape = P->m2l_choice[l].shape;
   g.dsplit = P->m2l_choice[l].dsplit;
   g.partial = P->arena + P->part_off;
+  g.skip_center = 1;  // the interaction list holds no child of the same parent
   return g;
 }
 

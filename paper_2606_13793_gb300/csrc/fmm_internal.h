@@ -86,6 +86,8 @@ struct NbrGemm {
   int shape = 0;       // 0: 4x4x4 rows per CTA, 3: one column per lane (k_gemm_simt.cu);
                        // 1, 2: z-run tiles (k_gemm_zrun.cu)
   int max_blocks = 0;  // shape 0: at most this many CTAs, each looping over work items (0: one per item)
+  int skip_center = 0; // 1: W_d of the centre neighbour (d = 13) is all zero (the M2L: a parent's
+                       // children are each other's near neighbours), and the kernels skip it
 };
 
 template <typename T>

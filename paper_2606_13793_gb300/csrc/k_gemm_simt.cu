@@ -63,6 +63,7 @@ __device__ __forceinline__ void nbr_gemm_simt_body(const NbrGemm& g, const VBloc
     const int d0 = g.dsplit > 1 ? dgrp : 0;  // dsplit is 1 or 27 here
     const int d1 = g.dsplit > 1 ? d0 + 1 : 27;
     for (int d = d0; d < d1; ++d) {
+      if (d == 13 && g.skip_center) continue;  // the centre block is zero
       const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
       const T* Wd = W0 + (long long)d * K * kNTile;
       for (int kc = 0; kc < K; kc += KC) {
@@ -171,6 +172,7 @@ __device__ __forceinline__ void nbr_gemm_col_body(const NbrGemm& g, const VBlock
 #pragma unroll
   for (int i = 0; i < R; ++i) acc[i] = T(0);
   for (int d = d0; d < d1; ++d) {
+    if (d == 13 && g.skip_center) continue;  // the centre block is zero
     const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
     const T* ap[R];
     bool av[R];
@@ -260,6 +262,7 @@ __device__ __forceinline__ void nbr_gemm_tiny_body(const NbrGemm& g, const VBloc
     for (int c = 0; c < 4; ++c) acc[i][c] = T(0);
   }
   for (int d = 0; d < 27; ++d) {
+    if (d == 13 && g.skip_center) continue;  // the centre block is zero
     const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
     bool v[2];
     const T* ap[2];

@@ -151,6 +151,7 @@ __device__ __forceinline__ void nbr_gemm_zrun_body(const NbrGemm& g, const VBloc
           for (int zz = 0; zz < RZ + 2; ++zz) a2[zz] = f2_splat(a[zz]);
 #pragma unroll
           for (int dz = 0; dz < 3; ++dz) {
+            if (dz == 1 && xy == 4 && g.skip_center) continue;  // the centre block is zero
             const ulonglong2* wv = reinterpret_cast<const ulonglong2*>(Wb + (dz * kZrKC + k) * kNTile);
             const ulonglong2 w0 = wv[0], w1 = wv[1];  // columns (0,1) (2,3) | (4,5) (6,7)
             const unsigned long long b2[4] = {w0.x, w0.y, w1.x, w1.y};
@@ -162,6 +163,7 @@ __device__ __forceinline__ void nbr_gemm_zrun_body(const NbrGemm& g, const VBloc
         } else {
 #pragma unroll
           for (int dz = 0; dz < 3; ++dz) {
+            if (dz == 1 && xy == 4 && g.skip_center) continue;  // the centre block is zero
             T b[kZrCT];
             const V* wv = reinterpret_cast<const V*>(Wb + (dz * kZrKC + k) * kNTile);
 #pragma unroll
