@@ -1386,9 +1386,45 @@ int near4_check() {
   return (split <= 1.0 / 65536.0 && worst <= 1e-5) ? 0 : 1;
 }
 
+// The CUDA-core M2L kernels skip the centre neighbour's weight block
+// (NbrGemm::skip_center): it must be all zero, and no other block may be.
+// A parent's children are each other's near neighbours (Chebyshev distance
+// <= 1), so none is in another's interaction list (Sec. 2.2).
+int centre_check() {
+  int bad = 0;
+  for (int p : {2, 4, 6, 8})
+    for (bool harm : {false, true})
+      for (int lim = 0; lim < 3; ++lim) {  // symmetric orders; mult_order = p - 1; its transpose
+      MultiIndex mi;
+      mi.init(p);
+      if (lim == 1) mi.mo = p - 1;
+      if (lim == 2) mi.lo = p - 1;
+      TaylorTable tt;
+      tt.build(mi);
+      std::vector<double> W;
+      std::vector<int> tk;
+      std::vector<long long> tw;
+      m2l_weights<double>(mi, tt, W, tk, tw, true, harm);
+      long long centre = 0, zero_blocks = 0;
+      for (size_t t = 0; t < tk.size(); ++t)
+        for (int d = 0; d < 27; ++d) {
+          const double* blk = W.data() + tw[t] + (long long)d * tk[t] * kNTile;
+          long long nz = 0;
+          for (long long i = 0; i < (long long)tk[t] * kNTile; ++i) nz += blk[i] != 0.0;
+          if (d == 13) centre += nz;
+          else if (nz == 0 && t == 0) ++zero_blocks;
+        }
+      std::printf("centre: p=%d harm=%d limits %d: nonzero centre weights %lld, other zero blocks of tile 0 %lld\n",
+                  p, harm, lim, centre, zero_blocks);
+      bad += centre != 0 || zero_blocks != 0;
+      }
+  return bad ? 1 : 0;
+}
+
 int main(int argc, char** argv) {
   const std::string mode = argc > 1 ? argv[1] : "";
   if (mode == "near4") return near4_check();
+  if (mode == "centre") return centre_check();
   if (mode == "plant") return planted_mistakes() ? 1 : 0;
   if (mode == "harmonic") return harmonic_check() ? 1 : 0;
   if (mode == "cuda-core") return cc_tiles_check() ? 1 : 0;

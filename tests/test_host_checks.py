@@ -104,6 +104,14 @@ def test_dedicated_near_field_weights_and_products(host_check):
     assert r.returncode == 0, r.stdout + r.stderr
 
 
+def test_m2l_centre_neighbour_block_is_zero(host_check):
+    """The CUDA-core M2L kernels skip the centre neighbour's weights: all zero
+    for every order, Cartesian and harmonic, while every other neighbour
+    block holds interaction-list weights."""
+    r = _run(host_check, "centre")
+    assert r.returncode == 0, r.stdout + r.stderr
+
+
 def test_harmonic_compression_is_exact(host_check):
     r = _run(host_check, "harmonic")
     assert r.returncode == 0, r.stdout + r.stderr
