@@ -1386,6 +1386,147 @@ int near4_check() {
   return (split <= 1.0 / 65536.0 && worst <= 1e-5) ? 0 : 1;
 }
 
+// The dedicated near-field kernel's barrier protocol (k_near_tc.cu) replayed
+// on the CPU with the kernel's stage, group and set arithmetic: the
+// activation producer (boxes in (item, column, tile) order over a 3-stage
+// ring), the weight producer (one 3-piece group per column, two buffers), the
+// two issuers (tiles 0-1 / 2-3; the accumulator set of each column segment,
+// the group, their boxes; one commit per box, group and segment), the 16
+// epilogue warps (one hand-off per segment).  Work items hold 4 tiles, the
+// last one possibly fewer.  Each run picks actors at random with skewed
+// speeds; every wait must agree with the phase the protocol means and every
+// actor must finish.
+std::string simulate_near4(int nitems, int last_tiles, unsigned seed, int plant = 0) {
+  constexpr int nA = 3;
+  std::vector<SimBar> a_full(nA), a_empty(nA), w_full(2), w_empty(2), acc_full(2), acc_empty(2);
+  for (auto& b : w_empty) b.expected = 2;
+  for (auto& b : acc_full) b.expected = 2;
+  for (auto& b : acc_empty) b.expected = 16;
+  auto tiles_of = [&](int item) { return item == nitems - 1 ? last_tiles : 4; };
+  std::string err;
+  auto wait_ok = [&](const SimBar& b, int phase_index, uint32_t parity, const char* who) {
+    const bool intended = b.done > phase_index, hardware = b.hw(parity);
+    if (intended != hardware && err.empty())
+      err = std::string(who) + ": a parity wait that does not match its phase (" +
+            (hardware ? "passes early" : "would hang") + ")";
+    return intended && hardware;
+  };
+  // A producer: box sequence (item, g, t)
+  struct Box { int item, g, t; };
+  std::vector<Box> boxes;
+  for (int it = 0; it < nitems; ++it)
+    for (int g = 0; g < 9; ++g)
+      for (int t = 0; t < tiles_of(it); ++t) boxes.push_back({it, g, t});
+  size_t a_next = 0;
+  int w_next = 0;  // next group gi
+  const int ngroups = 9 * nitems;
+  struct Iss { int gi = 0, state = 0, t = 0; size_t ai = 0; };
+  Iss iss[2];
+  int epi[16] = {};
+  std::mt19937 rng(seed);
+  std::vector<double> speed(2 + 2 + 16);
+  for (double& v : speed) v = std::pow(10.0, (double)(rng() % 3));
+  for (int step = 0; step < 10000000 && err.empty(); ++step) {
+    auto try_actor = [&](int a, bool act) -> bool {
+      if (a == 0) {  // activation producer
+        if (a_next >= boxes.size()) return false;
+        const int sa = (int)(a_next % nA), use = (int)(a_next / nA);
+        if (!wait_ok(a_empty[sa], use - 1, (uint32_t)((use & 1) ^ 1), "activation producer")) return false;
+        if (act) a_full[sa].arrive(), ++a_next;
+        return true;
+      }
+      if (a == 1) {  // weight producer
+        if (w_next >= ngroups) return false;
+        const int wb = w_next & 1, use = w_next >> 1;
+        if (!wait_ok(w_empty[wb], use - 1, (uint32_t)((use & 1) ^ 1), "weight producer")) return false;
+        if (act) w_full[wb].arrive(), ++w_next;
+        return true;
+      }
+      if (a < 4) {  // issuer q
+        const int q = a - 2;
+        Iss& I = iss[q];
+        if (I.gi >= ngroups) return false;
+        const int item = I.gi / 9, set = I.gi & 1, use = I.gi >> 1;
+        if (I.state == 0) {
+          if (!wait_ok(acc_empty[set], use - 1, (uint32_t)((use & 1) ^ 1), "issuer (accumulators)")) return false;
+          if (act) I.state = 1;
+          return true;
+        }
+        if (I.state == 1) {
+          if (!wait_ok(w_full[I.gi & 1], I.gi >> 1, (uint32_t)((I.gi >> 1) & 1), "issuer (weights)")) return false;
+          if (act) I.state = 2, I.t = 0;
+          return true;
+        }
+        // state 2: the item's tiles in order (mine: wait and commit the box; every valid tile advances ai)
+        if (I.t < tiles_of(item)) {
+          if ((I.t >> 1) == q) {
+            const int sa = (int)(I.ai % nA), u = (int)(I.ai / nA);
+            if (!wait_ok(a_full[sa], u, (uint32_t)((u + (plant == 1)) & 1), "issuer (activations)")) return false;
+            if (act) a_empty[sa].arrive();
+          }
+          if (act) ++I.ai, ++I.t;
+          return true;
+        }
+        if (act) w_empty[I.gi & 1].arrive(), acc_full[set].arrive(), ++I.gi, I.state = 0;
+        return true;
+      }
+      const int e = a - 4;  // epilogue warp
+      if (epi[e] >= ngroups) return false;
+      const int set = epi[e] & 1, use = epi[e] >> 1;
+      if (!wait_ok(acc_full[set], use, (uint32_t)(use & 1), "epilogue")) return false;
+      if (act) {
+        if (!(plant == 2 && e == 0 && epi[e] % 9 != 8)) acc_empty[set].arrive();  // planted: one hand-off per item
+        ++epi[e];
+      }
+      return true;
+    };
+    std::vector<int> can;
+    for (int a = 0; a < 20; ++a)
+      if (try_actor(a, false)) can.push_back(a);
+    if (!err.empty()) break;
+    if (can.empty()) {
+      bool done = a_next >= boxes.size() && w_next >= ngroups && iss[0].gi >= ngroups && iss[1].gi >= ngroups;
+      for (int e = 0; e < 16; ++e) done = done && epi[e] >= ngroups;
+      if (!done) err = "deadlock";
+      break;
+    }
+    double tot = 0;
+    for (int a : can) tot += speed[a];
+    double r = tot * (rng() / (double)rng.max());
+    int pickd = can.back();
+    for (int a : can)
+      if ((r -= speed[a]) <= 0) {
+        pickd = a;
+        break;
+      }
+    try_actor(pickd, true);
+  }
+  return err;
+}
+
+int near4_protocol_check() {
+  int bad = 0, runs = 0;
+  for (int nitems : {1, 2, 3, 7})
+    for (int last : {1, 2, 3, 4})
+      for (unsigned seed = 1; seed <= 25; ++seed, ++runs) {
+        const std::string e = simulate_near4(nitems, last, seed * 7919u + nitems * 31u + last);
+        if (!e.empty()) {
+          if (bad < 5) std::printf("near4 protocol: %d items, last %d tiles, seed %u: %s\n", nitems, last, seed, e.c_str());
+          ++bad;
+        }
+      }
+  std::printf("near4 protocol: %d of %d randomised replays clean\n", runs - bad, runs);
+  // planted mistakes must be caught: a wrong parity on the issuers' activation
+  // wait; one epilogue warp handing back its accumulators once per item
+  for (int plant : {1, 2}) {
+    int caught = 0;
+    for (unsigned seed = 1; seed <= 10; ++seed) caught += !simulate_near4(3, 2, seed, plant).empty();
+    std::printf("near4 protocol: planted mistake %d caught in %d of 10 replays\n", plant, caught);
+    bad += caught == 0;
+  }
+  return bad ? 1 : 0;
+}
+
 // The CUDA-core M2L kernels skip the centre neighbour's weight block
 // (NbrGemm::skip_center): it must be all zero, and no other block may be.
 // A parent's children are each other's near neighbours (Chebyshev distance
@@ -1425,6 +1566,7 @@ int main(int argc, char** argv) {
   const std::string mode = argc > 1 ? argv[1] : "";
   if (mode == "near4") return near4_check();
   if (mode == "centre") return centre_check();
+  if (mode == "near4-protocol") return near4_protocol_check();
   if (mode == "plant") return planted_mistakes() ? 1 : 0;
   if (mode == "harmonic") return harmonic_check() ? 1 : 0;
   if (mode == "cuda-core") return cc_tiles_check() ? 1 : 0;

@@ -104,6 +104,14 @@ def test_dedicated_near_field_weights_and_products(host_check):
     assert r.returncode == 0, r.stdout + r.stderr
 
 
+def test_dedicated_near_field_barrier_protocol(host_check):
+    """The leaf-4 near-field kernel's rings and accumulator hand-offs replayed
+    with random interleavings: every parity wait matches its phase, nothing
+    deadlocks, for work lists whose last item has 1 to 4 tiles."""
+    r = _run(host_check, "near4-protocol")
+    assert r.returncode == 0, r.stdout + r.stderr
+
+
 def test_m2l_centre_neighbour_block_is_zero(host_check):
     """The CUDA-core M2L kernels skip the centre neighbour's weights: all zero
     for every order, Cartesian and harmonic, while every other neighbour
