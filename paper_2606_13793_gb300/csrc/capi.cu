@@ -2853,8 +2853,8 @@ struct fmm_batch_s {
   size_t d_tab_cap = 0;
   // the contraction launches of the fused form run side by side: streams
   // and fork / join events
-  cudaStream_t fk[4] = {nullptr, nullptr, nullptr, nullptr};  // one per contraction shape after the first
-  cudaEvent_t fev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t fk[5] = {};  // one per contraction shape after the first
+  cudaEvent_t fev[6] = {};
 };
 
 namespace {
@@ -2925,13 +2925,14 @@ void add_step(fmm_batch_t B, int kind, int shape, int bs, int harm_rows, const s
 // row); a grid of at most 64 rows takes the tiny-grid form (shape 4: real
 // rows and in-grid neighbours only; the 4 x 4 x 4 tile took 3 ms of the
 // 64-field step on them, the column-per-lane form longer).
-int batch_shape(const NbrGemm& g, const std::vector<int>& tile_k) {
+int batch_shape(const NbrGemm& g, const std::vector<int>& tile_k, bool fp32) {
   if (nbr_gemm_tiny_fits(g)) return 4;
   if (!zrun_eligible(g, tile_k.data(), g.ntiles)) return g.shape;
-  // RZ = 8 throughout: on the 12^3-row grids, where it pads a third more
-  // rows than RZ = 4, the batch step measured the same either way, and one
-  // shape keeps those items in one launch
-  return 1;
+  // FP32: RZ = 8, or RZ = 6 (shape 5) where it pads the z extent less (12^3
+  // and 6^3 rows: RZ = 8 pads them to 16 and 8); RZ = 4 pads like RZ = 6 at
+  // a lower rate per row (on the 12^3 grids it measured the same as RZ = 8)
+  const int z = g.grid[2];
+  return fp32 && (z + 5) / 6 * 6 < (z + 7) / 8 * 8 ? 5 : 1;
 }
 
 std::array<unsigned, 3> blocks_1d(long long threads, int bs) {
@@ -2996,16 +2997,18 @@ void build_fused(fmm_batch_t B, const void* const* rho, void* const* phi, void* 
     add_step(B, MK_M2M, 0, bs, 0, a, g);
   }
   {  // M2L of every level and the near field: independent contractions
-    std::vector<NbrGemm> a[5];
-    std::vector<std::array<unsigned, 3>> g[5];
+    std::vector<NbrGemm> a[6];
+    std::vector<std::array<unsigned, 3>> g[6];
     auto add = [&](NbrGemm x, const std::vector<int>& tile_k) {
       x.dsplit = 1;  // the batch fills the GPU: no neighbour split, no partial sums
       x.partial = nullptr;
       x.max_blocks = 0;
-      x.shape = batch_shape(x, tile_k);
+      x.shape = batch_shape(x, tile_k, sizeof(T) == 4);
       std::array<unsigned, 3> gr;
       if (x.shape == 4)
         gr = {(unsigned)x.ntiles, 1u, 1u};
+      else if (x.shape == 5)
+        nbr_gemm_zrun_grid<T>(x, 2, gr.data());
       else if (x.shape == 1 || x.shape == 2)
         nbr_gemm_zrun_grid<T>(x, x.shape - 1, gr.data());
       else
@@ -3017,7 +3020,7 @@ void build_fused(fmm_batch_t B, const void* const* rho, void* const* phi, void* 
       for (int l = 2; l <= P->L; ++l) add(m2l_gemm(P, l), P->h_m2l_tile_k);
       add(near_gemm(P), P->h_near_tile_k);
     }
-    for (int sh : {1, 0, 2, 3, 4}) add_step(B, MK_GEMM, sh, 0, 0, a[sh], g[sh]);  // the tiny-grid launch last
+    for (int sh : {1, 5, 0, 2, 3, 4}) add_step(B, MK_GEMM, sh, 0, 0, a[sh], g[sh]);  // the tiny-grid launch last
   }
   for (int l = 2; l <= maxL; ++l) {  // L2L, coarse to fine (a fused leaf level's in the leaf kernel)
     std::vector<L2lArgs> a;
@@ -3106,7 +3109,7 @@ fmm_status run_fused(fmm_batch_t B, cudaStream_t s) {
     cudaStream_t ls = s;
     if (st.kind == MK_GEMM && ngemm > 1) {
       if (nfork == 0) CUDA_TRY(cudaEventRecord(B->fev[0], s));
-      if (nfork > 0) {  // the fork streams (at most four more contraction shapes)
+      if (nfork > 0) {  // the fork streams (at most five more contraction shapes)
         ls = B->fk[nfork - 1];
         CUDA_TRY(cudaStreamWaitEvent(ls, B->fev[0], 0));
       }
@@ -3135,6 +3138,8 @@ fmm_status run_fused(fmm_batch_t B, cudaStream_t s) {
           e = launch_nbr_gemm_simt_multi<T>(gs, g, st.n, st.blocks, ls);
         else if (st.shape == 3)
           e = launch_nbr_gemm_col_multi<T>(gs, g, st.n, st.blocks, ls);
+        else if (st.shape == 5)
+          e = launch_nbr_gemm_zrun_multi<T>(2, gs, g, st.n, st.blocks, ls);
         else
           e = launch_nbr_gemm_zrun_multi<T>(st.shape - 1, gs, g, st.n, st.blocks, ls);
         break;

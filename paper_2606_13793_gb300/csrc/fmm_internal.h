@@ -111,6 +111,7 @@ cudaError_t launch_nbr_gemm_simt_multi(const NbrGemm* gs, const MultiGrid* grids
 template <typename T>
 cudaError_t launch_nbr_gemm_col_multi(const NbrGemm* gs, const MultiGrid* grids, int n, long long blocks,
                                       cudaStream_t s);
+// shape here: 0 / 1 as launch_nbr_gemm_zrun, 2 = a z run of 6 rows (FP32; 3 in FP64)
 template <typename T>
 cudaError_t launch_nbr_gemm_zrun_multi(int shape, const NbrGemm* gs, const MultiGrid* grids, int n, long long blocks,
                                        cudaStream_t s);

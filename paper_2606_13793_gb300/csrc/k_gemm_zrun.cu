@@ -271,11 +271,11 @@ template <typename T>
 constexpr int zrun_rz(int which);
 template <>
 constexpr int zrun_rz<float>(int which) {
-  return which == 0 ? 8 : 4;
+  return which == 0 ? 8 : which == 1 ? 4 : 6;
 }
 template <>
 constexpr int zrun_rz<double>(int which) {
-  return which == 0 ? 4 : 2;
+  return which == 0 ? 4 : which == 1 ? 2 : 3;
 }
 
 bool zrun_eligible(const NbrGemm& g, const int* tile_k_host, int ntiles) {
@@ -307,8 +307,9 @@ void nbr_gemm_zrun_grid(const NbrGemm& g, int shape, unsigned out[3]) {
 template <typename T>
 cudaError_t launch_nbr_gemm_zrun_multi(int shape, const NbrGemm* gs, const MultiGrid* grids, int n, long long blocks,
                                        cudaStream_t s) {
-  return shape == 0 ? launch_rz_multi<T, zrun_rz<T>(0)>(gs, grids, n, blocks, s)
-                    : launch_rz_multi<T, zrun_rz<T>(1)>(gs, grids, n, blocks, s);
+  return shape == 0   ? launch_rz_multi<T, zrun_rz<T>(0)>(gs, grids, n, blocks, s)
+         : shape == 1 ? launch_rz_multi<T, zrun_rz<T>(1)>(gs, grids, n, blocks, s)
+                      : launch_rz_multi<T, zrun_rz<T>(2)>(gs, grids, n, blocks, s);
 }
 
 template void nbr_gemm_zrun_grid<float>(const NbrGemm&, int, unsigned[3]);
