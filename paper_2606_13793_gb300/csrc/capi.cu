@@ -295,6 +295,10 @@ struct fmm_plan_s {
   size_t static_cap = 0, static_used = 0;
   bool static_keep_tables = false;
   bool no_split = false;
+  // Layout only (host checks of the batch tables): with static_base a
+  // placeholder address and static_keep_tables set, plan_init then touches
+  // no device memory.
+  bool dry = false;
 
   fmm_status dev_alloc(size_t bytes, void** out) {
     if (static_base) {
@@ -1658,7 +1662,8 @@ fmm_status plan_init(fmm_plan_t P, const int d3[3], double dx, double G, int ord
   void* arena = nullptr;
   if ((st = P->dev_alloc(P->arena_bytes, &arena))) return st;
   P->arena = static_cast<unsigned char*>(arena);
-  if (cudaMemsetAsync(arena, 0, P->arena_bytes, s) != cudaSuccess) return cleanup(fail(FMM_ERR_CUDA, "memset failed"));
+  if (!P->dry && cudaMemsetAsync(arena, 0, P->arena_bytes, s) != cudaSuccess)
+    return cleanup(fail(FMM_ERR_CUDA, "memset failed"));
 
   // tables
   std::vector<int8_t> mi8(3 * P->nc);

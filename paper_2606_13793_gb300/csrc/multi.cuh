@@ -21,10 +21,10 @@ __device__ __forceinline__ VBlock native_vblock() {
   return v;
 }
 
-// The item of this block: the last one whose first block is <= blockIdx.x
-// (items are sorted by their first block; n >= 1).
-__device__ __forceinline__ int multi_item(const MultiGrid* __restrict__ g, int n) {
-  const long long b = blockIdx.x;
+// The item of launch block b: the last one whose first block is <= b (items
+// are sorted by their first block; n >= 1).  Host callable for the checks of
+// the batch's tables.
+__host__ __device__ __forceinline__ int multi_item_at(const MultiGrid* __restrict__ g, int n, long long b) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -34,8 +34,9 @@ __device__ __forceinline__ int multi_item(const MultiGrid* __restrict__ g, int n
   return lo;
 }
 
-__device__ __forceinline__ VBlock multi_vblock(const MultiGrid& g) {
-  const long long l = (long long)blockIdx.x - g.start;
+// Block b of the launch as a block of item g's own grid.
+__host__ __device__ __forceinline__ VBlock multi_vblock_at(const MultiGrid& g, long long b) {
+  const long long l = b - g.start;
   VBlock v;
   v.gx = g.gx, v.gy = g.gy, v.gz = g.gz;
   v.x = (unsigned)(l % g.gx);
@@ -43,5 +44,11 @@ __device__ __forceinline__ VBlock multi_vblock(const MultiGrid& g) {
   v.z = (unsigned)(l / ((long long)g.gx * g.gy));
   return v;
 }
+
+__device__ __forceinline__ int multi_item(const MultiGrid* __restrict__ g, int n) {
+  return multi_item_at(g, n, (long long)blockIdx.x);
+}
+
+__device__ __forceinline__ VBlock multi_vblock(const MultiGrid& g) { return multi_vblock_at(g, (long long)blockIdx.x); }
 
 }  // namespace fmmgb

@@ -16,6 +16,10 @@
 //                         column, emulated MMAs, randomised protocol replays
 //   host_check prefix-plant  planted prefix-schedule mistakes, each caught
 //   host_check rounding   the FP32 accumulation-chain bound of each schedule
+//   host_check batch fp32|fp64 ORDER LEAF NX NY NZ [NX NY NZ ...]
+//                         the fused batch's launch and item tables for fields
+//                         of those grids (layout-only plans, no GPU)
+//   host_check batch-plant ...  planted table corruptions, each caught
 //
 // The library's plan packs every tensor-core contraction (M2L per level,
 // final-stage M2P, the near field) into passes of MMA spans, per-issuer
@@ -46,8 +50,12 @@
 // accumulator opened late, an accumulator opened by two spans, a ring smaller
 // than a span) and exits 0 only if every corruption is caught.
 #include "capi.cu"
+#include "multi.cuh"
 #include "tree_common.cuh"
 
+#include <array>
+#include <cstdint>
+#include <cstdlib>
 #include <cstdio>
 #include <cmath>
 #include <functional>
@@ -1562,8 +1570,412 @@ int centre_check() {
   return bad ? 1 : 0;
 }
 
+// ---------------------------------------------------------------------------
+// The fused batch's work tables.  Plans are built layout-only (placeholder
+// device addresses, no device work) and the library's build_fused writes the
+// steps and the item tables of one batched solve; the replay here checks:
+//  * the launches come in the order of the method's steps (P2M, M2M, M2L and
+//    near field, L2L, leaf evaluation, force), every field's M2M from its
+//    leaf level up to level 3 one level per launch, its L2L from level 2 down
+//    (the leaf level's in the leaf kernel where the plan fuses it), one
+//    absolute level per L2L launch, and every M2L level and near field of
+//    every field in exactly one contraction launch;
+//  * each launch's block ranges tile [0, blocks) with no gap or overlap, and
+//    every launch block maps (multi.cuh's lookup, as the kernels run it) to
+//    one block of one item's own grid;
+//  * each contraction item's tile form and grid: the tiny form for grids of
+//    at most 64 rows, the 6-row z-run where it pads z less than the 8-row run
+//    (FP32), and the z-run tiles (8 x 4 x RZ rows, one per column tile) cover
+//    every row of the item's grid once;
+//  * the leaf items carry the leaf-level L2L exactly where the plan fuses it,
+//    and every item reads and writes its own field's buffers.
+namespace batchcheck {
+
+constexpr int kBx = 8, kBy = 4;  // z-run tile extent in x and y (k_gemm_zrun.cu)
+
+struct Case {
+  std::vector<fmm_plan_t> plans;
+  std::vector<const void*> rho;
+  std::vector<void*> phi, acc;
+  bool f64 = false, accel = true;
+  ~Case() {
+    for (fmm_plan_t P : plans) delete P;
+  }
+};
+
+fmm_plan_t dry_plan(const int d3[3], int order, int leaf, bool f64, int index) {
+  fmm_opts o;
+  fmm_default_opts(&o);
+  o.precision = f64 ? FMM_FP64 : FMM_FP32;
+  o.accel = 1;
+  fmm_plan_t P = new fmm_plan_s();
+  // placeholder addresses: one 1 TB range per field, never dereferenced
+  P->static_base = reinterpret_cast<unsigned char*>((uintptr_t)(index + 1) << 40);
+  P->static_cap = (size_t)1 << 39;
+  P->static_keep_tables = true;
+  P->dry = true;
+  if (plan_init(P, d3, 1.0 / d3[0], 1.0, order, leaf, o, nullptr, 0) != FMM_OK) {
+    std::printf("batch: plan %dx%dx%d failed: %s\n", d3[0], d3[1], d3[2], fmm_last_error());
+    delete P;
+    return nullptr;
+  }
+  return P;
+}
+
+template <typename A>
+const A* items(const std::vector<unsigned char>& tab, const MultiStep& st) {
+  return reinterpret_cast<const A*>(tab.data() + st.args_off);
+}
+const MultiGrid* grids(const std::vector<unsigned char>& tab, const MultiStep& st) {
+  return reinterpret_cast<const MultiGrid*>(tab.data() + st.grids_off);
+}
+
+// The z-run length of a contraction tile form (the kernels' template RZ).
+int zrun_len(int shape, bool f64) { return shape == 5 ? (f64 ? 3 : 6) : (f64 ? 4 : 8); }
+
+// Every check above; the first failure is reported in *why.
+bool check(const Case& c, const std::vector<MultiStep>& steps, const std::vector<unsigned char>& tab,
+           std::string* why) {
+  auto fail = [&](const std::string& m) {
+    *why = m;
+    return false;
+  };
+  const int nf = (int)c.plans.size();
+  // --- order of the launches and block ranges ---
+  for (size_t k = 0; k < steps.size(); ++k) {
+    const MultiStep& st = steps[k];
+    if (k && st.kind < steps[k - 1].kind) return fail("launch " + std::to_string(k) + " out of step order");
+    if (st.n <= 0 || st.blocks <= 0 || st.blocks > 0x7fffffffLL) return fail("launch " + std::to_string(k) + " size");
+    if (st.args_off % 16 || st.grids_off % 16 || st.grids_off + st.n * sizeof(MultiGrid) > tab.size())
+      return fail("launch " + std::to_string(k) + " table placement");
+    const MultiGrid* g = grids(tab, st);
+    long long next = 0;
+    for (int i = 0; i < st.n; ++i) {
+      const long long nb = (long long)g[i].gx * g[i].gy * g[i].gz;
+      if (g[i].start != next || nb <= 0) return fail("launch " + std::to_string(k) + " block ranges");
+      next += nb;
+    }
+    if (next != st.blocks) return fail("launch " + std::to_string(k) + " block total");
+    std::vector<long long> seen(st.n, 0);
+    for (long long b = 0; b < st.blocks; ++b) {
+      const int i = multi_item_at(g, st.n, b);
+      const long long nb = (long long)g[i].gx * g[i].gy * g[i].gz;
+      const VBlock v = multi_vblock_at(g[i], b);
+      if (b < g[i].start || b >= g[i].start + nb || v.x >= v.gx || v.y >= v.gy || v.z >= v.gz ||
+          ((long long)v.z * v.gy + v.y) * v.gx + v.x != b - g[i].start)
+        return fail("launch " + std::to_string(k) + " block " + std::to_string(b) + " maps outside its item");
+      ++seen[i];
+    }
+    for (int i = 0; i < st.n; ++i)
+      if (seen[i] != (long long)g[i].gx * g[i].gy * g[i].gz) return fail("launch " + std::to_string(k) + " coverage");
+  }
+  // --- per field: which launch holds each of its steps ---
+  std::vector<int> p2m(nf, 0), leaf(nf, 0), fd(nf, 0), m2m_next(nf), l2l_next(nf, 1);
+  std::vector<std::vector<int>> gemm(nf);
+  for (int f = 0; f < nf; ++f) {
+    m2m_next[f] = c.plans[f]->L;
+    gemm[f].assign(c.plans[f]->L + 2, 0);  // levels 2 .. L, then the near field at L + 1
+  }
+  auto field_of = [&](const void* ptr) {
+    for (int f = 0; f < nf; ++f) {
+      const unsigned char* a = c.plans[f]->arena;
+      const unsigned char* q = static_cast<const unsigned char*>(ptr);
+      if (q >= a && q < a + c.plans[f]->arena_bytes) return f;
+    }
+    return -1;
+  };
+  int l2l_level_prev = 1;
+  for (size_t k = 0; k < steps.size(); ++k) {
+    const MultiStep& st = steps[k];
+    const MultiGrid* g = grids(tab, st);
+    const std::string at = "launch " + std::to_string(k);
+    if (st.kind == MK_P2M) {
+      const P2mArgs* a = items<P2mArgs>(tab, st);
+      for (int i = 0; i < st.n; ++i) {
+        const int f = field_of(a[i].Mleaf);
+        if (f < 0 || a[i].Mleaf != c.plans[f]->M(c.plans[f]->L) || a[i].rho != c.rho[f]) return fail(at + ": P2M item");
+        ++p2m[f];
+      }
+    } else if (st.kind == MK_M2M) {
+      const M2mArgs* a = items<M2mArgs>(tab, st);
+      for (int i = 0; i < st.n; ++i) {
+        const int f = field_of(a[i].Mc);
+        if (f < 0) return fail(at + ": M2M item of no field");
+        const fmm_plan_t P = c.plans[f];
+        const int l = m2m_next[f];
+        if (l < 3 || a[i].Mc != P->M(l) || a[i].Mp != P->M(l - 1)) return fail(at + ": M2M out of level order");
+        --m2m_next[f];
+      }
+    } else if (st.kind == MK_GEMM) {
+      const NbrGemm* a = items<NbrGemm>(tab, st);
+      for (int i = 0; i < st.n; ++i) {
+        const NbrGemm& x = a[i];
+        const int f = field_of(x.C);
+        if (f < 0) return fail(at + ": contraction of no field");
+        const fmm_plan_t P = c.plans[f];
+        int which = -1;
+        std::vector<int> tk;
+        for (int l = 2; l <= P->L; ++l)
+          if (x.C == m2l_gemm(P, l).C) which = l, tk = P->h_m2l_tile_k;
+        if (x.C == near_gemm(P).C) which = P->L + 1, tk = P->h_near_tile_k;
+        if (which < 0) return fail(at + ": contraction writes no level");
+        ++gemm[f][which];
+        const NbrGemm ref = which <= P->L ? m2l_gemm(P, which) : near_gemm(P);
+        if (x.A != ref.A || x.W != ref.W || x.ntiles != ref.ntiles || x.n_cols != ref.n_cols ||
+            x.row_len != ref.row_len || x.skip_center != ref.skip_center || x.grid[0] != ref.grid[0] ||
+            x.grid[1] != ref.grid[1] || x.grid[2] != ref.grid[2])
+          return fail(at + ": contraction differs from the plan's");
+        if (x.dsplit != 1 || x.partial) return fail(at + ": neighbour split inside the batch");
+        if (x.shape != st.shape) return fail(at + ": item of another tile form");
+        const long long rows = (long long)x.grid[0] * x.grid[1] * x.grid[2];
+        if (st.shape == 4) {
+          if (!nbr_gemm_tiny_fits(x) || rows > 64 || g[i].gx != (unsigned)x.ntiles || g[i].gy != 1 || g[i].gz != 1)
+            return fail(at + ": tiny-grid item");
+        } else if (st.shape == 1 || st.shape == 5) {
+          if (nbr_gemm_tiny_fits(x) || !zrun_eligible(x, tk.data(), x.ntiles)) return fail(at + ": z-run item");
+          const int z = x.grid[2];
+          const bool six = !c.f64 && (z + 5) / 6 * 6 < (z + 7) / 8 * 8;
+          if ((st.shape == 5) != six) return fail(at + ": z-run length not the one that pads z least");
+          const int rz = zrun_len(st.shape, c.f64);
+          const int ntx = (x.grid[0] + kBx - 1) / kBx, nty = (x.grid[1] + kBy - 1) / kBy;
+          const int ntz = (z + rz - 1) / rz;
+          if (g[i].gx != (unsigned)(ntx * nty * ntz) || g[i].gy != (unsigned)x.ntiles || g[i].gz != 1)
+            return fail(at + ": z-run grid");
+          // rows of each block as the kernel decomposes its block index
+          std::vector<unsigned char> hit(rows, 0);
+          for (unsigned bt = 0; bt < g[i].gx; ++bt) {
+            const int ox = (bt % ntx) * kBx, oy = ((bt / ntx) % nty) * kBy, oz = (bt / (ntx * nty)) * rz;
+            for (int dz = 0; dz < rz; ++dz)
+              for (int dy = 0; dy < kBy; ++dy)
+                for (int dx = 0; dx < kBx; ++dx) {
+                  const int xx = ox + dx, yy = oy + dy, zz = oz + dz;
+                  if (xx < x.grid[0] && yy < x.grid[1] && zz < z) ++hit[((long long)zz * x.grid[1] + yy) * x.grid[0] + xx];
+                }
+          }
+          for (long long r = 0; r < rows; ++r)
+            if (hit[r] != 1) return fail(at + ": z-run tiles cover a row " + std::to_string(hit[r]) + " times");
+        } else {
+          if (zrun_eligible(x, tk.data(), x.ntiles) || nbr_gemm_tiny_fits(x)) return fail(at + ": fallback tile form");
+        }
+      }
+    } else if (st.kind == MK_L2L) {
+      const L2lArgs* a = items<L2lArgs>(tab, st);
+      int level = -1;
+      for (int i = 0; i < st.n; ++i) {
+        const int f = field_of(a[i].Lc);
+        if (f < 0) return fail(at + ": L2L item of no field");
+        const fmm_plan_t P = c.plans[f];
+        int l = -1;
+        for (int q = 2; q <= P->L; ++q)
+          if (a[i].Lc == P->Lx(q)) l = q;
+        if (l < 0) return fail(at + ": L2L writes no level");
+        if (level < 0) level = l;
+        if (l != level) return fail(at + ": L2L launch over two levels");
+        // the field's previous L2L: level l - 1, or none before level 3 when
+        // level 2 needs no harmonic rebuild
+        if (!(l2l_next[f] == l - 1 || (l2l_next[f] == 1 && l == 3 && !harmonic_m2l_level(P, 2))))
+          return fail(at + ": L2L out of level order");
+        if (a[i].Lp != (l == 2 ? nullptr : P->Lx(l - 1))) return fail(at + ": L2L parent locals");
+        if (l == P->L && fused_down(P)) return fail(at + ": leaf-level L2L outside the leaf kernel");
+        l2l_next[f] = l;
+      }
+      if (level <= l2l_level_prev) return fail(at + ": L2L levels not coarse to fine");
+      l2l_level_prev = level;
+    } else if (st.kind == MK_LEAF) {
+      const LeafArgs* a = items<LeafArgs>(tab, st);
+      for (int i = 0; i < st.n; ++i) {
+        const int f = field_of(a[i].Lleaf);
+        if (f < 0) return fail(at + ": leaf item of no field");
+        const fmm_plan_t P = c.plans[f];
+        if (a[i].Lleaf != P->Lx(P->L) || a[i].phi != c.phi[f]) return fail(at + ": leaf buffers");
+        const bool down = fused_down(P);
+        if (down != (a[i].Lp != nullptr) || (down && a[i].Lp != P->Lx(P->L - 1)))
+          return fail(at + ": leaf-level L2L in the leaf kernel");
+        // the field's L2L chain must have reached the leaf level (the level
+        // above it where the leaf kernel runs the last L2L); level 2 needs
+        // none unless its locals are rebuilt from the compact rows
+        const int done = l2l_next[f] == 1 && !harmonic_m2l_level(P, 2) ? 2 : l2l_next[f];
+        if (done != (down ? P->L - 1 : P->L)) return fail(at + ": leaf before the field's last L2L");
+        ++leaf[f];
+      }
+    } else if (st.kind == MK_FD) {
+      for (int i = 0; i < st.n; ++i) {
+        const FdArgs& x = items<FdArgs>(tab, st)[i];
+        int f = -1;
+        for (int q = 0; q < nf; ++q)
+          if (x.phi == c.phi[q]) f = q;
+        if (f < 0 || x.accel != c.acc[f] || x.nx != c.plans[f]->dims[0] || x.ny != c.plans[f]->dims[1] ||
+            x.nz != c.plans[f]->dims[2])
+          return fail(at + ": force item");
+        ++fd[f];
+      }
+    }
+  }
+  for (int f = 0; f < nf; ++f) {
+    const fmm_plan_t P = c.plans[f];
+    const std::string who = "field " + std::to_string(f);
+    if (p2m[f] != 1 || leaf[f] != 1 || fd[f] != (c.accel ? 1 : 0)) return fail(who + ": P2M, leaf or force count");
+    if (m2m_next[f] != 2) return fail(who + ": M2M chain incomplete");
+    for (int w = 2; w <= P->L + 1; ++w)
+      if (gemm[f][w] != 1) return fail(who + ": contraction " + std::to_string(w) + " run " + std::to_string(gemm[f][w]) + " times");
+  }
+  return true;
+}
+
+// Builds the plans of one batch and its fused tables; 0 when every check
+// passes.  With plant, a corruption of the built tables must be caught
+// instead, each of the listed ones.
+int run(bool f64, int order, int leaf, const std::vector<std::array<int, 3>>& dims, bool plant) {
+  Case c;
+  c.f64 = f64;
+  c.accel = !f64;  // the fused form takes the stencil force in FP32 only
+  for (size_t i = 0; i < dims.size(); ++i) {
+    fmm_plan_t P = dry_plan(dims[i].data(), order, leaf, f64, (int)i);
+    if (!P) return 1;
+    c.plans.push_back(P);
+    c.rho.push_back(reinterpret_cast<const void*>((uintptr_t)(i + 1) << 32));
+    c.phi.push_back(reinterpret_cast<void*>(((uintptr_t)(i + 1) << 32) + ((uintptr_t)1 << 31)));
+    c.acc.push_back(c.accel ? reinterpret_cast<void*>(((uintptr_t)(i + 1) << 32) + ((uintptr_t)3 << 29)) : nullptr);
+  }
+  fmm_batch_s B;
+  B.plans = c.plans;
+  if (!batch_fusable_plans(&B, c.accel)) {
+    std::printf("batch: plans not fusable\n");
+    return 1;
+  }
+  if (f64)
+    build_fused<double>(&B, c.rho.data(), c.phi.data(), c.acc.data(), c.accel);
+  else
+    build_fused<float>(&B, c.rho.data(), c.phi.data(), c.acc.data(), c.accel);
+  long long blocks = 0;
+  int shapes[6] = {0, 0, 0, 0, 0, 0};
+  for (const MultiStep& st : B.steps) {
+    blocks += st.blocks;
+    if (st.kind == MK_GEMM) shapes[st.shape] += st.n;
+  }
+  std::string why;
+  if (!plant) {
+    const bool ok = check(c, B.steps, B.h_tab, &why);
+    std::printf("batch %s: %zu fields, %zu launches, %lld blocks, contraction items z-run8 %d z-run6 %d tiny %d other %d: %s\n",
+                f64 ? "fp64" : "fp32", dims.size(), B.steps.size(), blocks, shapes[1], shapes[5], shapes[4],
+                shapes[0] + shapes[2] + shapes[3], ok ? "ok" : why.c_str());
+    return ok ? 0 : 1;
+  }
+  // planted corruptions, each on a fresh copy of the tables
+  auto find = [&](int kind, int shape) {
+    for (size_t k = 0; k < B.steps.size(); ++k)
+      if (B.steps[k].kind == kind && (shape < 0 || B.steps[k].shape == shape)) return (int)k;
+    return -1;
+  };
+  int missed = 0, tried = 0;
+  auto expect_caught = [&](const char* what, std::vector<MultiStep> steps, std::vector<unsigned char> tab) {
+    std::string w;
+    const bool caught = !check(c, steps, tab, &w);
+    std::printf("batch plant: %-52s %s%s\n", what, caught ? "caught: " : "MISSED", caught ? w.c_str() : "");
+    missed += !caught;
+    ++tried;
+  };
+  {  // a gap between two items' block ranges
+    auto steps = B.steps;
+    auto tab = B.h_tab;
+    const int k = find(MK_P2M, -1);
+    reinterpret_cast<MultiGrid*>(tab.data() + steps[k].grids_off)[1].start += 1;
+    expect_caught("gap between two items' blocks", steps, tab);
+  }
+  {  // the launch size one block short
+    auto steps = B.steps;
+    const int k = find(MK_LEAF, -1);
+    steps[k].blocks -= 1;
+    expect_caught("launch one block short", steps, B.h_tab);
+  }
+  {  // a field's near field dropped from the contraction launches
+    auto steps = B.steps;
+    auto tab = B.h_tab;
+    const int k = find(MK_GEMM, 1);
+    MultiStep& st = steps[k];
+    const MultiGrid* g = grids(tab, st);
+    st.blocks -= (long long)g[st.n - 1].gx * g[st.n - 1].gy * g[st.n - 1].gz;
+    st.n -= 1;
+    expect_caught("one contraction item dropped", steps, tab);
+  }
+  if (find(MK_GEMM, 5) >= 0) {  // the 6-row items run with 8-row tiles
+    auto steps = B.steps;
+    auto tab = B.h_tab;
+    MultiStep& st = steps[find(MK_GEMM, 5)];
+    st.shape = 1;
+    NbrGemm* a = reinterpret_cast<NbrGemm*>(tab.data() + st.args_off);
+    for (int i = 0; i < st.n; ++i) a[i].shape = 1;
+    expect_caught("6-row z-run items given 8-row tiles", steps, tab);
+  }
+  {  // a z-run item's last slab of tiles dropped
+    auto steps = B.steps;
+    auto tab = B.h_tab;
+    MultiStep& st = steps[find(MK_GEMM, 1)];
+    MultiGrid* g = reinterpret_cast<MultiGrid*>(tab.data() + st.grids_off);
+    const NbrGemm* a = items<NbrGemm>(tab, st);
+    for (int i = 0; i < st.n; ++i) {
+      const unsigned slab = (unsigned)(((a[i].grid[0] + kBx - 1) / kBx) * ((a[i].grid[1] + kBy - 1) / kBy));
+      if (g[i].gx <= slab) continue;
+      const long long d = (long long)slab * g[i].gy * g[i].gz;
+      g[i].gx -= slab;
+      for (int j = i + 1; j < st.n; ++j) g[j].start -= d;
+      st.blocks -= d;
+      break;
+    }
+    expect_caught("z-run item without its last z slab", steps, tab);
+  }
+  {  // two L2L launches swapped
+    auto steps = B.steps;
+    const int k = find(MK_L2L, -1);
+    if (k >= 0 && k + 1 < (int)steps.size() && steps[k + 1].kind == MK_L2L) {
+      std::swap(steps[k], steps[k + 1]);
+      expect_caught("two L2L launches swapped", steps, B.h_tab);
+    }
+  }
+  {  // the leaf-level L2L left out of a fused leaf item
+    auto steps = B.steps;
+    auto tab = B.h_tab;
+    const int k = find(MK_LEAF, -1);
+    LeafArgs* a = reinterpret_cast<LeafArgs*>(tab.data() + steps[k].args_off);
+    for (int i = 0; i < steps[k].n; ++i)
+      if (a[i].Lp) {
+        a[i].Lp = nullptr;
+        break;
+      }
+    expect_caught("leaf item without its leaf-level L2L", steps, tab);
+  }
+  {  // the force step before the leaf evaluation
+    auto steps = B.steps;
+    const int k = find(MK_FD, -1), j = find(MK_LEAF, -1);
+    if (k >= 0) {
+      std::swap(steps[k], steps[j]);
+      expect_caught("force launch before the leaf evaluation", steps, B.h_tab);
+    }
+  }
+  {  // a contraction item reading another field's multipoles
+    auto steps = B.steps;
+    auto tab = B.h_tab;
+    const int k = find(MK_GEMM, 1);
+    NbrGemm* a = reinterpret_cast<NbrGemm*>(tab.data() + steps[k].args_off);
+    std::swap(a[0].A, a[1].A);
+    expect_caught("contraction items' inputs swapped", steps, tab);
+  }
+  std::printf("batch plant: %d of %d corruptions caught\n", tried - missed, tried);
+  return missed ? 1 : 0;
+}
+
+}  // namespace batchcheck
+
 int main(int argc, char** argv) {
   const std::string mode = argc > 1 ? argv[1] : "";
+  if (mode == "batch" || mode == "batch-plant") {
+    // batch fp32|fp64 ORDER LEAF NX NY NZ [NX NY NZ ...]
+    if (argc < 8 || (argc - 5) % 3) return 2;
+    std::vector<std::array<int, 3>> dims;
+    for (int i = 5; i + 2 < argc; i += 3) dims.push_back({std::atoi(argv[i]), std::atoi(argv[i + 1]), std::atoi(argv[i + 2])});
+    return batchcheck::run(std::string(argv[2]) == "fp64", std::atoi(argv[3]), std::atoi(argv[4]), dims,
+                           mode == "batch-plant");
+  }
   if (mode == "near4") return near4_check();
   if (mode == "centre") return centre_check();
   if (mode == "near4-protocol") return near4_protocol_check();

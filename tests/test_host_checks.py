@@ -20,7 +20,10 @@ tests/host_check.cu compiles the library's host code (capi.cu) and:
 * reads the CUDA-core M2L weight tiles (reductions cut to a prefix per tile)
   as the kernels do and checks they give the full contraction;
 * runs the kernels' separable M2M / L2L shift helpers on the host, compared
-  here with the oracle's M2M (eq. M2M_general) and L2L (eq. L2L).
+  here with the oracle's M2M (eq. M2M_general) and L2L (eq. L2L);
+* replays the fused batch's launch tables (Sec. 2.3's steps over many
+  fields, one launch per step kind) built from layout-only plans, with
+  planted table corruptions that must each be caught.
 """
 import itertools
 import math
@@ -118,6 +121,56 @@ def test_m2l_centre_neighbour_block_is_zero(host_check):
     block holds interaction-list weights."""
     r = _run(host_check, "centre")
     assert r.returncode == 0, r.stdout + r.stderr
+
+
+def _cubes(sizes):
+    return [str(v) for n in sizes for v in (n, n, n)]
+
+
+_BATCH_SETS = [
+    # the 64-field benchmark batch: sizes {64, 96, 128, 192}^3
+    ("fp32", 6, 4, None),
+    # uneven, non-cubic grids; grids of one leaf-box row; coarse grids of 12
+    # and 6 rows
+    ("fp32", 6, 4, ["84", "52", "28", "16", "16", "200", "32", "48", "64", "12", "12", "12", "8", "8", "16",
+                    "40", "24", "96"]),
+    ("fp32", 4, 2, ["28", "18", "66", "8", "8", "8", "64", "32", "16"]),
+    ("fp32", 8, 8, ["64", "64", "64", "128", "64", "32"]),
+    ("fp64", 6, 4, ["84", "52", "28", "16", "16", "200", "32", "48", "64", "12", "12", "12", "64", "64", "64"]),
+]
+
+
+@pytest.mark.parametrize("prec,order,leaf,dims", _BATCH_SETS)
+def test_fused_batch_tables(host_check, prec, order, leaf, dims):
+    """The fused batch's launches and item tables as the library builds them:
+    the method's step order per field, every M2L level and near field in one
+    contraction launch, block ranges that tile each launch and map back (by
+    the kernels' own lookup) to one block of one item, the tile form that
+    pads least, z-run tiles covering every row once, the leaf-level L2L in
+    the leaf kernel, each item on its own field's buffers."""
+    if dims is None:
+        from paper_2606_13793_gb300 import inputs
+        dims = _cubes(inputs.batch_sizes(64, seed=2606))
+    r = _run(host_check, "batch", prec, str(order), str(leaf), *dims)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert ": ok" in r.stdout
+    if len(dims) == 192:  # the benchmark batch: P2M, 3 M2M, 3 contraction, 4 L2L, leaf, force
+        assert " 14 launches" in r.stdout
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_planted_batch_table_mistakes_are_caught(host_check, prec):
+    """Corruptions of a built batch table (a gap between block ranges, a
+    launch one block short, a dropped contraction, 6-row items given 8-row
+    tiles, a missing z slab, L2L levels swapped, the leaf-level L2L left out,
+    the force before the leaf evaluation, two items' inputs swapped) must
+    each fail the replay."""
+    from paper_2606_13793_gb300 import inputs
+    dims = _cubes(inputs.batch_sizes(64, seed=2606)) if prec == "fp32" else _BATCH_SETS[4][3]
+    r = _run(host_check, "batch-plant", prec, "6", "4", *dims)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "MISSED" not in r.stdout
+    assert r.stdout.count("caught:") >= 7
 
 
 def test_harmonic_compression_is_exact(host_check):
