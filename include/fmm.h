@@ -205,6 +205,27 @@ fmm_status fmm_solve_adjoint(fmm_plan_t plan, const void* grad_phi, const void* 
 fmm_status fmm_solve_host(fmm_plan_t plan, const void* rho_host, void* phi_host, void* accel_host, void* stream);
 
 /*
+ * fmm_solve_host_many -- `count` independent densities through one plan,
+ * HOST buffers: field i's rho_host[i] is solved into phi_host[i] (and
+ * accel_host[i]), each with the plan's layout and element type
+ * ([nz][ny][nx], accel [3][nz][ny][nx]; FP32, FP64 for FMM_FP64 plans).  The
+ * results equal fmm_solve_host's field by field.  The copies overlap the
+ * solves: two device staging sets (owned by the plan, allocated by the first
+ * call, freed by fmm_plan_destroy), uploads on one copy stream and downloads
+ * on another, so that field i + 1's upload and field i's download run beside
+ * the solve of field i + 1; the solves themselves run one after another on
+ * `stream`, after the work already queued there.  A pointer may repeat (the
+ * same input or output buffer for several fields; output buffers that repeat
+ * hold the last such field).  Pinned host memory is needed for the overlap;
+ * pageable buffers work, without it.  Returns after every copy has finished,
+ * also on error.  accel_host NULL: no acceleration.  count = 0 does nothing.
+ * Errors: FMM_ERR_ARG (NULL plan or buffer, negative count), FMM_ERR_ALLOC,
+ * FMM_ERR_CUDA, and fmm_solve's.
+ */
+fmm_status fmm_solve_host_many(fmm_plan_t plan, int count, const void* const* rho_host, void* const* phi_host,
+                               void* const* accel_host, void* stream);
+
+/*
  * fmm_solve_static -- the same FP32 solve as fmm_solve (CUDA-core kernels,
  * FMM_FP32 arithmetic, 5-point accel), for callers that cannot allocate
  * device memory.  The paper has no counterpart: this entry point only

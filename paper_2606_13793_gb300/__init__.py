@@ -33,6 +33,7 @@ EXPORTS = [
     "fmm_solve",
     "fmm_solve_adjoint",
     "fmm_solve_host",
+    "fmm_solve_host_many",
     "fmm_check",
     "fmm_workspace_bytes",
     "fmm_solve_launches",
@@ -105,6 +106,8 @@ def load(path: str | None = None):
         lib.fmm_solve_adjoint.restype = i
         lib.fmm_solve_host.argtypes = [vp, vp, vp, vp, vp]
         lib.fmm_solve_host.restype = i
+        lib.fmm_solve_host_many.argtypes = [vp, i, vp, vp, vp, vp]
+        lib.fmm_solve_host_many.restype = i
         lib.fmm_check.argtypes = [vp]
         lib.fmm_check.restype = i
         lib.fmm_workspace_bytes.argtypes = [vp]
@@ -276,6 +279,36 @@ class FMMPlan:
 
         _check(self.lib, self.lib.fmm_solve_host(self._h, ptr(rho_host), ptr(phi_host), ptr(accel_host),
                                                  _stream_handle(stream)))
+
+    def solve_host_many(self, rhos, phis, accels=None, stream=None):
+        """Several densities through this plan with host buffers (lists of
+        numpy arrays or CPU tensors, pinned for the copies to overlap the
+        solves): rhos[i] -> phis[i] (and accels[i] [3][nz][ny][nx]).
+        Synchronous."""
+        import numpy as np
+
+        n = len(rhos)
+        if len(phis) != n or (accels is not None and len(accels) != n):
+            raise ValueError("rhos, phis and accels must have the same length")
+        esize = 8 if self.precision == "fp64" else 4
+        cells = self.shape[0] * self.shape[1] * self.shape[2]
+
+        def ptr(a, name, comps):
+            if hasattr(a, "data_ptr"):
+                if a.is_cuda or a.element_size() != esize or not a.is_contiguous() or a.numel() != comps * cells:
+                    raise ValueError(f"{name} must be a contiguous host buffer of {comps * cells} "
+                                     f"{esize}-byte values")
+                return a.data_ptr()
+            a = np.asarray(a)
+            if a.itemsize != esize or not a.flags.c_contiguous or a.size != comps * cells:
+                raise ValueError(f"{name} must be a contiguous host buffer of {comps * cells} {esize}-byte values")
+            return a.ctypes.data
+
+        arr = ctypes.c_void_p * max(n, 1)
+        r = arr(*[ptr(a, "rho", 1) for a in rhos])
+        f = arr(*[ptr(a, "phi", 1) for a in phis])
+        g = arr(*[ptr(a, "accel", 3) for a in accels]) if accels is not None else None
+        _check(self.lib, self.lib.fmm_solve_host_many(self._h, n, r, f, g, _stream_handle(stream)))
 
     def timing(self, enable: bool = True):
         """Start (clearing) or stop per-stage CUDA-event timing."""

@@ -204,10 +204,16 @@ struct fmm_plan_s {
   std::vector<int> h_m2l_tile_k, h_near_tile_k;
   alignas(64) unsigned char map_hi[kMaxLevels][128];
   alignas(64) unsigned char map_lo[kMaxLevels][128];
-  // host-buffer staging for fmm_solve_host
+  // host-buffer staging for fmm_solve_host (set 0) and fmm_solve_host_many
+  // (sets 0 and 1), its copy streams and events
   void* d_io_rho = nullptr;
   void* d_io_phi = nullptr;
   void* d_io_acc = nullptr;
+  void* d_io_rho1 = nullptr;
+  void* d_io_phi1 = nullptr;
+  void* d_io_acc1 = nullptr;
+  cudaStream_t io_in = nullptr, io_out = nullptr;
+  cudaEvent_t io_ev[7] = {};  // [b] uploaded, [2 + b] solved, [4 + b] downloaded (set b), [6] start
   cudaStream_t last_stream = nullptr;
   // side stream of the concurrent far field (CUDA-core M2L levels), fork/join events
   cudaStream_t side = nullptr;
@@ -343,9 +349,12 @@ struct fmm_plan_s {
     side = nullptr;
     for (void* d : allocs) cudaFree(d);
     allocs.clear();
-    if (d_io_rho) cudaFree(d_io_rho);
-    if (d_io_phi) cudaFree(d_io_phi);
-    if (d_io_acc) cudaFree(d_io_acc);
+    for (void* d : {d_io_rho, d_io_phi, d_io_acc, d_io_rho1, d_io_phi1, d_io_acc1})
+      if (d) cudaFree(d);
+    for (cudaEvent_t e : io_ev)
+      if (e) cudaEventDestroy(e);
+    if (io_in) cudaStreamDestroy(io_in);
+    if (io_out) cudaStreamDestroy(io_out);
   }
 };
 
@@ -2597,6 +2606,92 @@ fmm_status fmm_solve_host(fmm_plan_t P, const void* rho_host, void* phi_host, vo
   CUDA_TRY(cudaMemcpyAsync(phi_host, P->d_io_phi, bytes, cudaMemcpyDeviceToHost, s));
   if (accel_host) CUDA_TRY(cudaMemcpyAsync(accel_host, P->d_io_acc, 3 * bytes, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  return FMM_OK;
+}
+
+// Several independent densities through one plan with host buffers: two
+// staging sets, the uploads on one copy stream and the downloads on another,
+// so that field i + 1's upload and field i's download run beside field i + 1's
+// solve.  Set b = i % 2 serves field i; its hazards are waited on explicitly:
+// the upload of field i waits for the solve of field i - 2 (which read the
+// same rho staging), the solve of field i for that upload and for the
+// download of field i - 2 (which read the same phi / accel staging), the
+// download of field i for its solve.
+fmm_status fmm_solve_host_many(fmm_plan_t P, int count, const void* const* rho_host, void* const* phi_host,
+                               void* const* accel_host, void* stream) {
+  if (!P) return fail(FMM_ERR_ARG, "plan is NULL");
+  if (count < 0) return fail(FMM_ERR_ARG, "count %d is negative", count);
+  if (count == 0) return FMM_OK;
+  if (!rho_host || !phi_host) return fail(FMM_ERR_ARG, "the rho and phi pointer arrays must be non-NULL");
+  for (int i = 0; i < count; ++i)
+    if (!rho_host[i] || !phi_host[i] || (accel_host && !accel_host[i]))
+      return fail(FMM_ERR_ARG, "host buffer of field %d is NULL", i);
+  const bool acc = accel_host != nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)P->ncell() * P->esize();
+  auto stage = [](void** buf, size_t n) {
+    if (*buf) return true;
+    void* q = nullptr;
+    if (cudaMalloc(&q, n) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    *buf = q;
+    return true;
+  };
+  const bool two = count > 1;
+  if (!stage(&P->d_io_rho, bytes) || !stage(&P->d_io_phi, bytes) || (acc && !stage(&P->d_io_acc, 3 * bytes)) ||
+      (two && (!stage(&P->d_io_rho1, bytes) || !stage(&P->d_io_phi1, bytes) ||
+               (acc && !stage(&P->d_io_acc1, 3 * bytes)))))
+    return fail(FMM_ERR_ALLOC, "staging allocation failed");
+  if (!P->io_ev[6]) {  // created together, the start event last
+    bool ok = cudaStreamCreateWithFlags(&P->io_in, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&P->io_out, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t& e : P->io_ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {  // none kept: the next call starts over
+      cudaGetLastError();
+      for (cudaEvent_t& e : P->io_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+      }
+      if (P->io_in) cudaStreamDestroy(P->io_in);
+      if (P->io_out) cudaStreamDestroy(P->io_out);
+      P->io_in = P->io_out = nullptr;
+      return fail(FMM_ERR_CUDA, "copy stream or event creation failed");
+    }
+  }
+  void* const R[2] = {P->d_io_rho, P->d_io_rho1};
+  void* const F[2] = {P->d_io_phi, P->d_io_phi1};
+  void* const A[2] = {P->d_io_acc, P->d_io_acc1};
+  cudaEvent_t* const ev = P->io_ev;
+  fmm_status st = FMM_OK;
+  cudaError_t ce = cudaEventRecord(ev[6], s);  // the copies start after the work queued on `stream`
+  if (ce == cudaSuccess) ce = cudaStreamWaitEvent(P->io_in, ev[6], 0);
+  if (ce == cudaSuccess) ce = cudaStreamWaitEvent(P->io_out, ev[6], 0);
+  for (int i = 0; i < count && ce == cudaSuccess; ++i) {
+    const int b = i & 1;
+    if (i >= 2) ce = cudaStreamWaitEvent(P->io_in, ev[2 + b], 0);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(R[b], rho_host[i], bytes, cudaMemcpyHostToDevice, P->io_in);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ev[b], P->io_in);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, ev[b], 0);
+    if (ce == cudaSuccess && i >= 2) ce = cudaStreamWaitEvent(s, ev[4 + b], 0);
+    if (ce != cudaSuccess) break;
+    st = fmm_solve(P, R[b], F[b], acc ? A[b] : nullptr, stream);
+    if (st != FMM_OK) break;
+    ce = cudaEventRecord(ev[2 + b], s);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(P->io_out, ev[2 + b], 0);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(phi_host[i], F[b], bytes, cudaMemcpyDeviceToHost, P->io_out);
+    if (ce == cudaSuccess && acc)
+      ce = cudaMemcpyAsync(accel_host[i], A[b], 3 * bytes, cudaMemcpyDeviceToHost, P->io_out);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ev[4 + b], P->io_out);
+  }
+  // every copy drained before returning, after an error too
+  const cudaError_t e1 = cudaStreamSynchronize(P->io_in);
+  const cudaError_t e2 = cudaStreamSynchronize(s);
+  const cudaError_t e3 = cudaStreamSynchronize(P->io_out);
+  if (st != FMM_OK) return st;
+  if (ce == cudaSuccess) ce = e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3;
+  if (ce != cudaSuccess) return fail(FMM_ERR_CUDA, "CUDA error: %s", cudaGetErrorString(ce));
   return FMM_OK;
 }
 

@@ -223,6 +223,50 @@ def test_deterministic_and_host_path():
     plan.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_host_many_equals_device_solves(precision):
+    """fmm_solve_host_many (uploads and downloads on their own streams beside
+    the solves, two staging sets): every field bit-equal to its device
+    solve, with pinned and pageable buffers, a repeated input, one field
+    (one staging set), no accel, none at all, and fmm_solve_host after it."""
+    shape = (64, 48, 32)
+    plan = fmm.FMMPlan(shape, 6, 4, precision)
+    rhos = [inputs.plummer(shape, seed=40 + i) for i in range(4)]
+    rhos.append(rhos[1])  # the same input buffer twice
+    want = [plan.solve(torch.from_numpy(r).cuda(), accel=True) for r in rhos]
+    want = [(a.cpu().numpy(), g.cpu().numpy()) for a, g in want]
+    pin = [torch.from_numpy(r).pin_memory() for r in rhos]
+    phis = [torch.empty(r.shape, dtype=torch.float32).pin_memory() for r in rhos]
+    accs = [torch.empty((3,) + r.shape, dtype=torch.float32).pin_memory() for r in rhos]
+    def same(x, y):  # FP32: the solve is deterministic; bf16x3 held to 1e-6 of the field's scale
+        if precision == "fp32":
+            return np.array_equal(x, y)
+        return np.max(np.abs(x - y)) <= 1e-6 * np.max(np.abs(y))
+
+    plan.solve_host_many(pin, phis, accs)
+    for i, (a, g) in enumerate(want):
+        assert same(phis[i].numpy(), a), i
+        assert same(accs[i].numpy(), g), i
+    # pageable numpy buffers, no accel, repeated twice over
+    out = [np.zeros_like(r) for r in rhos[:3]]
+    plan.solve_host_many(rhos[:3], out)
+    plan.solve_host_many(rhos[:3], out)
+    for i in range(3):
+        assert same(out[i], want[i][0]), i
+    one_phi, one_acc = np.zeros_like(rhos[2]), np.zeros((3,) + rhos[2].shape, np.float32)
+    plan.solve_host_many([rhos[2]], [one_phi], [one_acc])
+    assert same(one_phi, want[2][0]) and same(one_acc, want[2][1])
+    plan.solve_host_many([], [])
+    h_phi, h_acc = np.zeros_like(rhos[0]), np.zeros((3,) + rhos[0].shape, np.float32)
+    plan.solve_host(rhos[0], h_phi, h_acc)
+    assert same(h_phi, want[0][0]) and same(h_acc, want[0][1])
+    with pytest.raises(ValueError):
+        plan.solve_host_many(rhos[:2], out[:1])
+    with pytest.raises(ValueError):
+        plan.solve_host_many([rhos[0][:16]], [out[0]])
+    plan.close()
+
+
 def test_bad_arguments_raise():
     plan = fmm.FMMPlan((16, 16, 16), 4, 4, "fp32")
     with pytest.raises(ValueError):
