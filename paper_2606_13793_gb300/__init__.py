@@ -299,7 +299,8 @@ class FMMPlan:
                     raise ValueError(f"{name} must be a contiguous host buffer of {comps * cells} "
                                      f"{esize}-byte values")
                 return a.data_ptr()
-            a = np.asarray(a)
+            if not isinstance(a, np.ndarray):
+                raise TypeError(f"{name} must be a numpy array or a CPU tensor")
             if a.itemsize != esize or not a.flags.c_contiguous or a.size != comps * cells:
                 raise ValueError(f"{name} must be a contiguous host buffer of {comps * cells} {esize}-byte values")
             return a.ctypes.data
