@@ -29,8 +29,8 @@
  *    enqueued on `stream` has finished, and must be 16-byte aligned.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
  *    is asynchronous on that stream unless stated otherwise; none allocates
- *    device memory after fmm_plan() (fmm_solve_host allocates its staging
- *    buffers on first use, see there).
+ *    device memory after fmm_plan() (fmm_solve_host and fmm_solve_host_many
+ *    allocate their staging buffers on first use, see there).
  *  - Argument errors are reported synchronously by the return code; the text
  *    of the most recent error of the calling thread is fmm_last_error().
  *  - Device-side conditions (non-finite input, a spin-wait that gave up) are
