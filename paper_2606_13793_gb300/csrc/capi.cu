@@ -2530,6 +2530,19 @@ fmm_status run_solve(fmm_plan_t P, const T* rho, T* phi, T* accel, cudaStream_t 
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// A host-solve staging buffer, allocated on first use (a failed allocation
+// leaves it NULL for the next call to retry).
+bool stage_alloc(void** buf, size_t n) {
+  if (*buf) return true;
+  void* q = nullptr;
+  if (cudaMalloc(&q, n) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  *buf = q;
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -2586,19 +2599,8 @@ fmm_status fmm_solve_host(fmm_plan_t P, const void* rho_host, void* phi_host, vo
   if (!rho_host || !phi_host) return fail(FMM_ERR_ARG, "rho and phi must be non-NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)P->ncell() * P->esize();
-  // staging buffers, allocated once each (a failed allocation leaves the
-  // others in place and is retried by the next call)
-  auto stage = [](void** buf, size_t n) {
-    if (*buf) return true;
-    void* q = nullptr;
-    if (cudaMalloc(&q, n) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    *buf = q;
-    return true;
-  };
-  if (!stage(&P->d_io_rho, bytes) || !stage(&P->d_io_phi, bytes) || (accel_host && !stage(&P->d_io_acc, 3 * bytes)))
+  if (!stage_alloc(&P->d_io_rho, bytes) || !stage_alloc(&P->d_io_phi, bytes) ||
+      (accel_host && !stage_alloc(&P->d_io_acc, 3 * bytes)))
     return fail(FMM_ERR_ALLOC, "staging allocation failed");
   CUDA_TRY(cudaMemcpyAsync(P->d_io_rho, rho_host, bytes, cudaMemcpyHostToDevice, s));
   fmm_status st = fmm_solve(P, P->d_io_rho, P->d_io_phi, accel_host ? P->d_io_acc : nullptr, stream);
@@ -2629,20 +2631,11 @@ fmm_status fmm_solve_host_many(fmm_plan_t P, int count, const void* const* rho_h
   const bool acc = accel_host != nullptr;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)P->ncell() * P->esize();
-  auto stage = [](void** buf, size_t n) {
-    if (*buf) return true;
-    void* q = nullptr;
-    if (cudaMalloc(&q, n) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    *buf = q;
-    return true;
-  };
   const bool two = count > 1;
-  if (!stage(&P->d_io_rho, bytes) || !stage(&P->d_io_phi, bytes) || (acc && !stage(&P->d_io_acc, 3 * bytes)) ||
-      (two && (!stage(&P->d_io_rho1, bytes) || !stage(&P->d_io_phi1, bytes) ||
-               (acc && !stage(&P->d_io_acc1, 3 * bytes)))))
+  if (!stage_alloc(&P->d_io_rho, bytes) || !stage_alloc(&P->d_io_phi, bytes) ||
+      (acc && !stage_alloc(&P->d_io_acc, 3 * bytes)) ||
+      (two && (!stage_alloc(&P->d_io_rho1, bytes) || !stage_alloc(&P->d_io_phi1, bytes) ||
+               (acc && !stage_alloc(&P->d_io_acc1, 3 * bytes)))))
     return fail(FMM_ERR_ALLOC, "staging allocation failed");
   if (!P->io_ev[6]) {  // created together, the start event last
     bool ok = cudaStreamCreateWithFlags(&P->io_in, cudaStreamNonBlocking) == cudaSuccess &&
