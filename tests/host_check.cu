@@ -1855,7 +1855,13 @@ int run(bool f64, int order, int leaf, const std::vector<std::array<int, 3>>& di
   }
   std::string why;
   if (!plant) {
-    const bool ok = check(c, B.steps, B.h_tab, &why);
+    bool ok = check(c, B.steps, B.h_tab, &why);
+    // the launch count the library reports for the batch is the schedule's
+    const int reported = fmm_batch_launches(&B, c.accel ? 1 : 0);
+    if (ok && reported != (int)B.steps.size()) {
+      ok = false;
+      why = "fmm_batch_launches reports " + std::to_string(reported);
+    }
     std::printf("batch %s: %zu fields, %zu launches, %lld blocks, contraction items z-run8 %d z-run6 %d tiny %d other %d: %s\n",
                 f64 ? "fp64" : "fp32", dims.size(), B.steps.size(), blocks, shapes[1], shapes[5], shapes[4],
                 shapes[0] + shapes[2] + shapes[3], ok ? "ok" : why.c_str());
