@@ -135,6 +135,38 @@ def algorithmic_counts(dims, leaf, p):
     return {"m2l_flop": m2l_flop, "near_flop": near_flop}
 
 
+def batch_contraction_flops(sizes, leaf, p):
+    """Algorithmic flops of one batch step's contractions: every M2L level of
+    every cubic field (the CUDA-core contraction on the (p+1)^2 harmonic
+    components from order 2 on) and every near field."""
+    total = 0
+    for s in sizes:
+        dims = (s, s, s)
+        lev = hierarchy(dims, leaf)
+        total += sum(m2l_flop_level(dims, leaf, p, l, p >= 2) for l in range(2, len(lev)))
+        total += algorithmic_counts(dims, leaf, p)["near_flop"]
+    return total
+
+
+def batch_roofline(sizes, leaf, p, precision, ms_per_step, peaks):
+    """Roofline of the fused batch's contraction launches (the z-run and the
+    tiny-grid multi-field launches, 92% of the launch list), timed as the
+    whole step: a lower bound on their rate, against the CUDA-core FMA peak
+    of the precision (FP32 from the unit counts and the maximum clock, FP64
+    nominal)."""
+    flop = batch_contraction_flops(sizes, leaf, p)
+    if precision == "fp64":
+        peak, note = 1.25, "FP64 1.25 TFLOP/s (nominal)"
+    else:
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        note = "FP32 FFMA 152 SMs x 128 lanes x 2 x max clock"
+    ach = flop / (ms_per_step / 1e3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+            "kernel": "nbr_gemm_zrun_multi + nbr_gemm_tiny_multi (contraction launches)",
+            "peak_source": "derived: " + note, "flop_per_step": flop,
+            "timing": "whole batch step (a lower bound on the contraction launches' rate)"}
+
+
 # ----------------------------------------------------------------- clocks ---
 
 class ClockSampler:
@@ -681,7 +713,9 @@ def batch_main(args, fmm, inputs, torch, dist, rank, world):
                                cells * args.steps * world / (seq_ms / 1e3) / 1e6,
                            "l2": "inputs larger than L2 (all fields together)",
                            "parallelism": f"replicas x{world}"},
-                "roofline": None, "cpu_baseline": None, "e2e": e2e,
+                "roofline": (batch_roofline(sizes, b, p, prec, ms / args.steps, measured_peaks()[0])
+                             if batch.fused == 1 else None),
+                "cpu_baseline": None, "e2e": e2e,
                 "gpu_launches": batch.launches(True) * args.steps, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     batch.close()

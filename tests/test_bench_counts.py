@@ -65,3 +65,24 @@ def test_near_field_pair_count():
                 boxes += 0 <= i + di < nx and 0 <= j + dj < ny and 0 <= k + dk < nz
         # every target cell against every cell of each neighbour box: one multiply-add each
         assert bench.algorithmic_counts(shape, b, 4)["near_flop"] == 2 * boxes * b ** 6
+
+
+def test_batch_roofline_counts():
+    """The batch roofline's flops are the per-field counts summed: M2L on the
+    harmonic pairs of every level plus every near field; its rate and
+    fraction follow from the step time (25.90 ms for the 64-field batch)."""
+    from paper_2606_13793_gb300 import inputs
+    sizes = inputs.batch_sizes(64, seed=2606)
+    want = 0
+    for s in sizes:
+        lev = bench.hierarchy((s, s, s), 4)
+        want += sum(bench.il_total(lev[l]) for l in range(2, len(lev))) * 2 * bench.m2l_pairs_harmonic(6)
+        want += bench.algorithmic_counts((s, s, s), 4, 6)["near_flop"]
+    assert bench.batch_contraction_flops(sizes, 4, 6) == want
+    r = bench.batch_roofline(sizes, 4, 6, "fp32", 25.90, {"sm_max_mhz": 2070.0})
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["flop_per_step"] == want
+    assert abs(r["achieved"] - want / 25.90e-3 / 1e12) < 1e-9
+    assert abs(r["peak"] - 80.547840) < 1e-6 and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert 0.3 < r["frac"] < 0.6  # 36.7 TFLOP/s of 80.5
+    r64 = bench.batch_roofline(sizes, 4, 6, "fp64", 100.0, {})
+    assert r64["peak"] == 1.25
