@@ -63,8 +63,9 @@ typedef enum {
   FMM_FP64 = 0,        /* every step in FP64 on the CUDA cores; data are double */
   FMM_FP32 = 1,        /* every step in FP32 on the CUDA cores ("plain")        */
   FMM_M2L_TF32 = 2,    /* M2L on tcgen05 tensor cores, TF32 inputs, FP32
-                          accumulation; the n_fp64_levels coarsest M2L levels in
-                          FP64; everything else FP32                            */
+                          accumulation; the n_fp64_levels coarsest M2L levels on
+                          the CUDA cores (FP32, or FP64 with coarse_fp32 = 0);
+                          everything else FP32                                  */
   FMM_M2L_BF16X3 = 3   /* as FMM_M2L_TF32 with the M2L operands split into
                           bf16 hi + lo parts and three products
                           (hi*hi + hi*lo + lo*hi), FP32 accumulation             */
@@ -78,8 +79,10 @@ typedef struct {
 
 typedef struct {
   int precision;      /* fmm_precision                                          */
-  int n_fp64_levels;  /* mixed precisions: coarsest M2L levels kept in FP64
-                         (levels 2 .. 1+n_fp64_levels); default 3               */
+  int n_fp64_levels;  /* mixed precisions: coarsest M2L levels kept off the
+                         tensor cores (levels 2 .. 1+n_fp64_levels, never the
+                         leaf level), in the precision coarse_fp32 selects;
+                         default 3                                              */
   int accel;          /* 0: no accel output; 1: accel = -grad(phi) by the
                          5-point stencil (App. C); 2: analytic accel, the
                          gradient of the leaf local expansions plus the
@@ -186,7 +189,8 @@ fmm_status fmm_solve(fmm_plan_t plan, const void* rho, void* phi, void* accel, v
  * multipole and local limits swapped.  Errors: FMM_ERR_ARG, FMM_ERR_CUDA.
  *
  * A plan runs one call at a time: fmm_solve, fmm_solve_adjoint,
- * fmm_solve_host and fmm_plan_autotune share the plan's workspace arena (and
+ * fmm_solve_host, fmm_solve_host_many and fmm_plan_autotune share the plan's
+ * workspace arena (and
  * the adjoint switches the plan's M2L weights for its duration), so calls on
  * one plan are made from one host thread at a time and ordered on one stream.
  * Separate plans are independent.
