@@ -190,9 +190,9 @@ fmm_status fmm_solve(fmm_plan_t plan, const void* rho, void* phi, void* accel, v
  *
  * A plan runs one call at a time: fmm_solve, fmm_solve_adjoint,
  * fmm_solve_host, fmm_solve_host_many and fmm_plan_autotune share the plan's
- * workspace arena (and
- * the adjoint switches the plan's M2L weights for its duration), so calls on
- * one plan are made from one host thread at a time and ordered on one stream.
+ * workspace arena (and the adjoint switches the plan's M2L weights for its
+ * duration), so calls on one plan are made from one host thread at a time and
+ * ordered on one stream.
  * Separate plans are independent.
  */
 fmm_status fmm_solve_adjoint(fmm_plan_t plan, const void* grad_phi, const void* grad_accel, void* grad_rho,
