@@ -77,6 +77,13 @@ def test_argument_validation_without_gpu(lib):
     assert lib.fmm_solve(None, None, None, None, None) == 1
     assert lib.fmm_solve_adjoint(None, None, None, None, None) == 1
     assert lib.fmm_check(None) == 1
+    assert lib.fmm_solve_host(None, None, None, None, None) == 1
+    assert lib.fmm_solve_host_many(None, 1, None, None, None, None) == 1
+    assert "plan is NULL" in lib.fmm_last_error().decode()
+    assert lib.fmm_batch_solve(None, None, None, None, None) == 1
+    assert lib.fmm_batch_launches(None, 1) == -1
+    assert lib.fmm_batch_is_fused(None) == -1
+    assert lib.fmm_batch_destroy(None) == 0
     assert lib.fmm_workspace_bytes(None) == 0
     assert lib.fmm_plan_leaf_level(None) == -1
     assert lib.fmm_plan_destroy(None) == 0
