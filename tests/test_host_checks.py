@@ -158,6 +158,31 @@ def test_fused_batch_tables(host_check, prec, order, leaf, dims):
         assert " 14 launches" in r.stdout
 
 
+def test_fused_batch_tables_random_sets(host_check):
+    """The same replay over seeded random batches: 1-6 fields of random
+    non-cubic extents up to 200 cells, orders 0-8, leaf 2, 4 or 8, FP32 (with
+    the stencil force: x extents a multiple of 4) and FP64."""
+    import random
+
+    rng = random.Random(2606)
+    ran = 0
+    for _ in range(40):
+        prec = rng.choice(["fp32", "fp64"])
+        p, leaf = rng.randint(0, 8), rng.choice([2, 4, 8])
+        dims = []
+        for _ in range(rng.randint(1, 6)):
+            d = [rng.randint(1, 200 // leaf) * leaf for _ in range(3)]
+            if prec == "fp32":
+                d[0] = (d[0] + 7) // 8 * 8
+            dims += [str(v) for v in d]
+        r = _run(host_check, "batch", prec, str(p), str(leaf), *dims)
+        if "not fusable" in r.stdout:  # a field of a single leaf level or too shallow
+            continue
+        assert r.returncode == 0 and ": ok" in r.stdout, (prec, p, leaf, dims, r.stdout + r.stderr)
+        ran += 1
+    assert ran >= 25
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_planted_batch_table_mistakes_are_caught(host_check, prec):
     """Corruptions of a built batch table (a gap between block ranges, a
